@@ -1,0 +1,380 @@
+"""Benchmark: render forward + backward throughput of one refinement iteration.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl handrt|reference]
+
+Workload: the paper-shaped multiview hand capture -- 8 views of 512x384 on a ring at
+0.6 m, 16 samples per pixel, 4096 silhouette-edge samples per view, the 778-vertex /
+1538-triangle procedural hand (Section 3.3 times one iteration of this path: ~30 views,
+16 spp forward and backward).  One step = one full iteration of the hot path:
+skinning, BVH rebuild + vertex normals, forward render, masked loss + adjoint, interior
+and edge-sampling backward with the vertex-normal adjoint, skinning adjoint, Adam.
+
+value: rays actually traced per second (forward primary rays + re-traced backward rays
+of pixels with a non-zero adjoint + two rays per live edge sample, counted by the
+library's HR_STATS pass), device-timed with CUDA events, inputs resident in HBM, L2
+flushed between steps.  e2e: the same rays per step over the wall time of the public
+Python API with the step's inputs copied from pinned host memory and the loss and
+gradient read back every step.
+
+--impl reference times the CPU oracle (brute force, all host cores) on a bounded
+sample of the same workload.  Under torchrun every rank refines its own hand instance
+(weak scaling, no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "render fwd+bwd Mrays/s"
+UNIT = "Mrays/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 FMA peak of a GB300: 152 SMs x 128 lanes x 2 flop x clock
+N_SM, LANES = 152, 128
+FLOP_RAY, FLOP_NODE, FLOP_TRI, FLOP_HIT = 20, 40, 50, 60
+FLOP_HIT_GRAD, FLOP_EDGE = 250, 120
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"sm_max_mhz": 2070.0, "clocks_under_load": {"sm_mhz_median": 1492.0}}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if p[5 + k].lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_handrt(args):
+    import torch
+
+    from paper_2107_05509_gb300 import binding as B
+    from paper_2107_05509_gb300 import inputs as I
+    from paper_2107_05509_gb300 import pipeline as P
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    cfg = I.PAPER
+    hand = I.make_hand(0)
+    model = B.Model(hand, device=dev)
+    inst_seed = cfg.seed + rank
+    x_gt = I.gt_params(inst_seed)
+    N, H, W = cfg.views, cfg.height, cfg.width
+    ctx = B.Context(hand.V, hand.F, hand.E, N, N * H * W)
+    views, _ = P.make_views(cfg, model, x_gt, device=dev, ctx=ctx)
+    opts = P.opts_for(cfg)
+    opts.instance = rank
+    ref = P.Refiner(model, views, opts, ctx=ctx)
+    x0 = torch.as_tensor(I.perturb_params(x_gt, inst_seed), device=dev)
+    params = x0.clone()
+    m1 = torch.zeros(61, device=dev)
+    m2 = torch.zeros(61, device=dev)
+    lr = 2e-3
+
+    # work counters of one step (untimed pass)
+    opts.flags = B.HR_STATS
+    ref.step(params)
+    stats = B.hr_get_stats(ctx).astype(np.float64)
+    opts.flags = 0
+    rays_fwd, rays_bwd, rays_edge = stats[0, 0], stats[1, 0], stats[2, 0]
+    rays_step = rays_fwd + rays_bwd + rays_edge
+    flops_fwd = FLOP_RAY * stats[0, 0] + FLOP_NODE * stats[0, 1] + FLOP_TRI * stats[0, 2] + FLOP_HIT * stats[0, 3]
+    flops_bwd = FLOP_RAY * stats[1, 0] + FLOP_NODE * stats[1, 1] + FLOP_TRI * stats[1, 2] + FLOP_HIT_GRAD * stats[1, 3]
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    stages = ["skin", "bvh", "fwd", "loss", "bwd", "skin_bwd", "adam"]
+
+    def one_step(step_idx, evs=None):
+        def mark(i):
+            if evs is not None:
+                evs[i].record(stream)
+        opts.iter = step_idx
+        mark(0)
+        B.hr_skin(ctx, model, params, ref.verts)
+        mark(1)
+        B.hr_build_bvh(ctx, model, ref.verts)
+        mark(2)
+        B.hr_render_fwd(ctx, model, ref.verts, views.cams, H, W, views.background, opts, ref.image)
+        mark(3)
+        B.hr_loss(ctx, ref.image, views.observed, views.mask, ref.loss, ref.adjoint)
+        mark(4)
+        B.hr_render_bwd(ctx, model, ref.verts, views.cams, H, W, views.background, opts, ref.adjoint, ref.d_verts)
+        mark(5)
+        B.hr_skin_bwd(ctx, model, params, ref.d_verts, ref.d_params)
+        mark(6)
+        B.hr_adam_step(params, ref.d_params, m1, m2, lr, 0.9, 0.999, 1e-8, step_idx + 1)
+        mark(7)
+
+    for w in range(args.warmup):
+        one_step(w)
+    torch.cuda.synchronize()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.4)                  # let the sampler start before the timed region
+        for k in range(args.steps):
+            flush.fill_(float(k))        # evict L2 between timed steps (outside the events)
+            one_step(args.warmup + k, ev[k])
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    st = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(7)] for k in range(args.steps)])
+    step_ms = st.sum(1)
+    ms_per_step = float(step_ms.mean())
+    tot_ms = float(step_ms.sum())
+    status = B.hr_get_status(ctx)
+    if status != B.HR_OK:
+        raise RuntimeError(f"device status {B.status_string(status)}")
+
+    # end-to-end through the public API with host buffers
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+    h_obs, h_mask, h_bg = pin(views.observed.cpu()), pin(views.mask.cpu()), pin(views.background.cpu())
+    h_cams, h_x = pin(views.cams.cpu()), pin(x0.cpu())
+    h_loss, h_grad = torch.empty(1).pin_memory(), torch.empty(61).pin_memory()
+    e2e_views = P.Views(cams=torch.empty_like(views.cams), background=torch.empty_like(views.background),
+                        observed=torch.empty_like(views.observed), mask=torch.empty_like(views.mask), H=H, W=W)
+    e2e_ref = P.Refiner(model, e2e_views, opts, ctx=ctx)
+    e_params = torch.empty(61, device=dev)
+    h2d = sum(t.numel() * t.element_size() for t in (h_obs, h_mask, h_bg, h_cams, h_x))
+    d2h = h_loss.numel() * 4 + h_grad.numel() * 4
+
+    def e2e_step(i):
+        opts.iter = i
+        e2e_views.observed.copy_(h_obs, non_blocking=True)
+        e2e_views.mask.copy_(h_mask, non_blocking=True)
+        e2e_views.background.copy_(h_bg, non_blocking=True)
+        e2e_views.cams.copy_(h_cams, non_blocking=True)
+        e_params.copy_(h_x, non_blocking=True)
+        loss, grad = e2e_ref.step(e_params)
+        h_loss.copy_(loss, non_blocking=True)
+        h_grad.copy_(grad, non_blocking=True)
+
+    for w in range(args.warmup):
+        e2e_step(w)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    e0.record(stream)
+    for k in range(args.steps):
+        e2e_step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    opts.iter = 0
+
+    if dist:
+        t = torch.tensor([tot_ms, e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms, e2e_ms = float(t[0]), float(t[1])
+        ms_per_step = tot_ms / args.steps
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return None
+
+    value = rays_step * world / (ms_per_step * 1e-3) / 1e6
+    stage_ms = dict(zip(stages, st.mean(0).round(4).tolist()))
+    pk, pk_kind = peaks()
+    clocks = clk.summary()
+    fwd_ms = float(st[:, 2].mean())
+    fp32_peak = N_SM * LANES * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops_fwd / (fwd_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_render_fwd", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
+            "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": None,
+            "peak_note": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
+                         f"(max clock; recipe unit counts), {pk_kind} clock data",
+            "flops_per_launch": flops_fwd,
+            "flop_model": f"{FLOP_RAY}/ray + {FLOP_NODE}/node visit + {FLOP_TRI}/triangle test + {FLOP_HIT}/hit",
+            "frac_at_load_clock": None}
+    if clocks:
+        roof["frac_at_load_clock"] = round(achieved / (N_SM * LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12), 4)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural hand, GPU-rendered observations)",
+        "config": {"workload": cfg.name, "views": N, "width": W, "height": H, "spp": cfg.spp,
+                   "edge_samples_per_view": cfg.edge_samples, "vertices": hand.V, "triangles": hand.F,
+                   "rays_per_step": int(rays_step), "rays_fwd": int(rays_fwd), "rays_bwd": int(rays_bwd),
+                   "rays_edge": int(rays_edge), "nodes_per_fwd_ray": round(stats[0, 1] / max(stats[0, 0], 1), 3),
+                   "tris_per_fwd_ray": round(stats[0, 2] / max(stats[0, 0], 1), 3),
+                   "hit_fraction_fwd": round(stats[0, 3] / max(stats[0, 0], 1), 4),
+                   "stage_ms": stage_ms, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"{world} independent instance(s), one per GPU"},
+        "e2e": {"value": round(rays_step * world / (e2e_ms * 1e-3) / 1e6, 3), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)},
+        "gpu_launches": 14 * args.steps,
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_seconds)
+    if dist:
+        dist.destroy_process_group()
+    return line
+
+
+def _oracle_sample(budget_s):
+    """Time the oracle (forward + interior backward + edge samples) on a band of rows
+    of the workload, grown until it has run about `budget_s` seconds."""
+    import oracle
+    from paper_2107_05509_gb300 import inputs as I
+
+    cfg = I.PAPER
+    hand = I.make_hand(0)
+    x = I.perturb_params(I.gt_params(cfg.seed), cfg.seed)
+    verts = oracle.skin(hand, x).astype(np.float32)
+    normals = oracle.vertex_normals(verts, hand.faces, hand.vf_offsets, hand.vf_faces)
+    cams = I.pack_cameras(I.make_cameras(cfg, hand.v_template.mean(0)))
+    H, W = cfg.height, cfg.width
+    bg = I.background(cfg.seed, cfg.views, H, W)
+    o = oracle.make_opts(seed=cfg.seed * 7919 + 17, spp=cfg.spp, edge_samples=cfg.edge_samples, ka=I.K_AMBIENT,
+                         kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR, light_rgb=I.LIGHT_RGB, edge_eps=I.EDGE_EPS_PX)
+    rng = np.random.default_rng(0)
+    A = (rng.choice([-1.0, 1.0], size=(cfg.views, H, W, 3)) * 1e-7).astype(np.float32)
+    # bands of rows through the middle of each view (where the hand is), view after view
+    rows_done, rays, secs = 0, 0.0, 0.0
+    band = 4
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < budget_s and rows_done < cfg.views * 96:
+        view, k = divmod(rows_done, 96)
+        r0 = view * H + H // 2 - 48 + k
+        t0 = time.perf_counter()
+        oracle.render_fwd(verts, hand.faces, normals, hand.albedo, cams, H, W, bg, o, rows=(r0, r0 + band))
+        rmask = np.zeros_like(A)
+        rv = rmask.reshape(cfg.views * H, W, 3)
+        rv[r0:r0 + band] = A.reshape(cfg.views * H, W, 3)[r0:r0 + band]
+        oracle.render_bwd_interior(verts, hand.faces, normals, hand.albedo, cams, H, W, bg, o, rmask,
+                                   rows=(r0, r0 + band))
+        secs += time.perf_counter() - t0
+        rays += 2.0 * band * W * cfg.spp
+        rows_done += band
+    return rays, secs, rows_done
+
+
+def cpu_baseline(args, budget_s=15.0):
+    import oracle
+    rays, secs, rows = _oracle_sample(budget_s)
+    return {"value": round(rays / secs / 1e6, 5), "unit": UNIT, "cores": oracle.n_threads(), "kind": "oracle",
+            "sample": f"forward + interior backward (brute force over all 1538 triangles, every pixel's adjoint "
+                      f"non-zero) of {rows} rows x 512 px through the middle of the views at 16 spp, {secs:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return None
+    import oracle
+    from paper_2107_05509_gb300 import inputs as I
+    cfg = I.PAPER
+    budget = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        _oracle_sample(budget)
+    tot_rays, tot_s = 0.0, 0.0
+    for _ in range(args.steps):
+        r, s, rows = _oracle_sample(budget)
+        tot_rays += r
+        tot_s += s
+    value = tot_rays / tot_s / 1e6
+    cores = oracle.n_threads()
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tot_s / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded procedural hand)",
+            "config": {"workload": cfg.name, "views": cfg.views, "width": cfg.width, "height": cfg.height,
+                       "spp": cfg.spp},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: forward + interior backward of 4-row bands through the "
+                                       f"middle of the views, about {budget:.0f} s of brute-force CPU work"},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="handrt", choices=["handrt", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "handrt":
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_handrt(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

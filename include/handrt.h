@@ -1,0 +1,215 @@
+/*
+ * handrt -- GB300 (sm_103a) library for multiview hand-geometry refinement by
+ * differentiable Monte Carlo ray tracing (Karvounas et al., "Multiview Image-based
+ * Hand Geometry Refinement using Differentiable Monte Carlo Ray Tracing", BMVC 2021).
+ *
+ * One refinement iteration (Section 3, Eq. 1-3) is
+ *
+ *     verts  = G_v(h + dh)                       hr_skin          (Section 3.1, "Geometry")
+ *     accel  = BVH + vertex normals of verts     hr_build_bvh
+ *     R_i    = R(verts, colour, C_i)             hr_render_fwd    (Section 3.1, "Rendering")
+ *     E_1    = sum_i D_c(O_i, R_i), dE_1/dR_i    hr_loss          (Eq. 3 and Eq. 4, D_c term)
+ *     dE/dverts                                  hr_render_bwd    (interior + edge sampling)
+ *     dE/d(h + dh)                               hr_skin_bwd
+ *     h + dh <- Adam step                        hr_adam_step     (Section 3.3)
+ *
+ * Conventions shared by every call:
+ *   - Array pointers are caller-owned DEVICE memory unless stated otherwise; the
+ *     library never frees them and keeps no reference after the call returns
+ *     (the context keeps its own copies of what later calls need).
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *     default stream) and never synchronises, except hr_get_status.
+ *   - Return value: HR_OK (0) or a negative HR_ERR_* code for errors detected on
+ *     the host (bad arguments, a failed launch).  Errors found by a kernel (a
+ *     traversal stack overflow, non-finite parameters) are OR-ed into the
+ *     context's device status word; hr_get_status reads and clears it.  No call
+ *     traps on the device.
+ *   - Calls that share one context must be ordered on one stream; use one context
+ *     per concurrent stream.
+ *   - Layouts are C-contiguous, float32 unless stated.  Images are [N][H][W][3]
+ *     (views, rows, columns, RGB); pixel (x, y) covers [x, x+1) x [y, y+1).
+ *   - Parameters h are float[61] = [beta(10) shape, theta(45) pose as 15 axis-angle
+ *     triples, phi(3) root axis-angle, tau(3) root translation in metres]
+ *     (Section 3: the 61 parameters {beta, theta, tau, phi} of the hand model).
+ */
+#ifndef HANDRT_H
+#define HANDRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HR_OK 0
+#define HR_ERR_ARG (-1)         /* invalid argument (null pointer, size out of range) */
+#define HR_ERR_CUDA (-2)        /* a CUDA runtime call or launch failed */
+#define HR_ERR_LIMIT (-3)       /* a device-side limit was hit (traversal stack) */
+#define HR_ERR_NONFINITE (-4)   /* non-finite parameters reached the skinning kernel */
+#define HR_ERR_UNSUPPORTED (-5) /* sizes beyond what the context was created for */
+
+typedef void* hr_stream; /* a cudaStream_t */
+
+/* Pinhole camera, OpenCV convention (x right, y down, z forward), world -> camera:
+ * X_cam = R X_world + t.  `centre` is the camera position in world coordinates
+ * (-R^T t, given explicitly so that all primary rays start from the same float32
+ * point).  80 bytes.  (Section 3: calibrated views with intrinsics and extrinsics.) */
+typedef struct hr_camera {
+    float fx, fy, cx, cy;
+    float R[9];      /* row-major */
+    float t[3];
+    float centre[3];
+    float pad;
+} hr_camera;
+
+/* Hand model (device arrays, caller-owned).  A linear-blend-skinned mesh standing in
+ * for the MANO model of Section 3: K shape blendshapes, J joints, parents[j] < j. */
+typedef struct hr_model {
+    int32_t V, F, E, J, K;
+    const float* v_template;   /* [V][3] rest vertices                             */
+    const float* shapedirs;    /* [V][3][K] shape blendshapes                       */
+    const float* weights;      /* [V][J] skin weights                               */
+    const float* j_template;   /* [J][3] rest joints                                */
+    const float* j_shapedirs;  /* [J][3][K] joint regressor per shape component     */
+    const int32_t* parents;    /* [J] parent joint, -1 for the root (joint 0)       */
+    const int32_t* faces;      /* [F][3] triangles, outward counter-clockwise       */
+    const int32_t* edges;      /* [E][2] unique edges (a < b)                       */
+    const int32_t* edge_faces; /* [E][2] adjacent faces, second = -1 on a boundary  */
+    const int32_t* vf_offsets; /* [V+1] vertex -> incident faces, CSR offsets       */
+    const int32_t* vf_faces;   /* [3F]  incident faces, ascending per vertex        */
+    const float* albedo;       /* [V][3] per-vertex RGB albedo                      */
+} hr_model;
+
+/* Render options.  Samples are drawn from Philox4x32-10 keyed by `seed` with counters
+ * built from (pixel, view | instance << 16, sample, iter << 4 | stream), so a render
+ * is a deterministic function of (seed, iter, instance).  Shading is Lambertian with
+ * one directional light: f = albedo * light_rgb * (ka + kd * max(0, n . light_dir)),
+ * n the interpolated, normalised vertex normal; light_dir points toward the light. */
+typedef struct hr_render_opts {
+    uint64_t seed;
+    uint32_t iter;
+    uint32_t instance;
+    int32_t spp;            /* primary samples per pixel (>= 1)                     */
+    int32_t edge_samples;   /* silhouette-edge samples per view (>= 0)              */
+    float ka, kd;
+    float light_dir[3];
+    float light_rgb[3];
+    float edge_eps_px;      /* offset of the two edge-sample rays, in pixels        */
+    uint32_t flags;         /* HR_BWD_* bits; 0 = every term                        */
+} hr_render_opts;
+
+#define HR_BWD_NO_INTERIOR 1u  /* hr_render_bwd: skip the interior term            */
+#define HR_BWD_NO_EDGES 2u     /* hr_render_bwd: skip the edge-sampling term       */
+#define HR_BWD_NO_NORMALS 4u   /* hr_render_bwd: skip the vertex-normal adjoint    */
+#define HR_STATS 8u            /* count rays, BVH nodes, triangle tests and hits   */
+
+/* Sizes a context is created for; all scratch is allocated once, up front. */
+typedef struct hr_limits {
+    int32_t max_V;      /* vertices (<= 8192: the backward keeps [V][6] in shared memory) */
+    int32_t max_F;      /* triangles (<= 8192: single-block BVH build)           */
+    int32_t max_E;      /* edges                                                 */
+    int32_t max_views;  /* views per call                                        */
+    int64_t max_pixels; /* N * H * W per call (loss scratch)                     */
+} hr_limits;
+
+typedef struct hr_context hr_context;
+
+/* Create a context on the current CUDA device: device scratch for the given
+ * limits, the BVH, vertex normals and the device status word.
+ * Returns HR_ERR_ARG for non-positive or too large limits, HR_ERR_CUDA when an
+ * allocation fails (nothing is leaked).  The context is owned by the caller. */
+int hr_context_create(const hr_limits* limits, hr_context** out);
+
+/* Free a context and all its device memory (synchronises the device first). */
+int hr_context_destroy(hr_context* ctx);
+
+/* Skinning G_v (Section 3.1, "Geometry": x in R^61 decoded into 3-D vertices).
+ *   v = sum_j w_vj (A_j [v_template + S beta; 1]) + tau,  A_j = G_j [I | -J_j],
+ *   G_0 = [R(phi) | J_0],  G_j = G_parent(j) [R(theta_j) | J_j - J_parent(j)],
+ *   J = j_template + SJ beta, R(.) = Rodrigues.
+ * params: device float[61]; verts: device float[V][3] (written).
+ * Non-finite params set HR_ERR_NONFINITE in the status word (outputs then undefined). */
+int hr_skin(hr_context* ctx, const hr_model* model, const float* params, float* verts, hr_stream stream);
+
+/* Adjoint of hr_skin: d_params (device float[61], overwritten) = (dverts/dparams)^T d_verts
+ * for d_verts device float[V][3]. */
+int hr_skin_bwd(hr_context* ctx, const hr_model* model, const float* params, const float* d_verts,
+                float* d_params, hr_stream stream);
+
+/* Rebuild the context's scene from the current vertices: a Morton-code linear BVH
+ * over the model's faces (rebuilt, not refitted, every call) and the area-weighted
+ * unit vertex normals used for shading.  verts: device float[V][3]. */
+int hr_build_bvh(hr_context* ctx, const hr_model* model, const float* verts, hr_stream stream);
+
+/* Forward render R (Section 3.1, "Rendering"): every pixel value is the Monte Carlo
+ * estimate (1/spp) sum_s f(x_s) of its box-filtered integral, x_s uniform in the
+ * pixel, f the radiance of the closest hit of the primary ray through x_s (double-
+ * sided Moller-Trumbore; ties in distance go to the lower triangle id), or the
+ * background pixel on a miss.  Requires hr_build_bvh for the same verts.
+ * cams: device hr_camera[N]; background and image: device float[N][H][W][3]. */
+int hr_render_fwd(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams, int N,
+                  int H, int W, const float* background, const hr_render_opts* opts, float* image,
+                  hr_stream stream);
+
+/* Masked photometric loss (Eq. 3 with the D_c term of Eq. 4, summed over views):
+ *   L = sum_p M_p sum_c |R_pc - O_pc| / (3 sum_p M_p),
+ *   adjoint_pc = dL/dR_pc = M_p sign(R_pc - O_pc) / (3 sum_p M_p), sign(0) = 0.
+ * An all-zero mask gives L = 0 and a zero adjoint.  image, observed, adjoint: device
+ * float[N][H][W][3]; mask: device uint8[N][H][W] (non-zero = 1); loss: device float[1].
+ * The reduction order is fixed, so repeated calls return identical values. */
+int hr_loss(hr_context* ctx, const float* image, const float* observed, const uint8_t* mask, int N, int H,
+            int W, float* loss, float* adjoint, hr_stream stream);
+
+/* Backward of hr_render_fwd for adjoint image A = dL/dR (Section 1 and Section 3.1:
+ * the ray tracer of Li et al. 2018 handles visibility discontinuities in the
+ * backward pass).  d_verts (device float[V][3], overwritten) is the sum of
+ *   interior : the forward's samples re-traced (same Philox counters); at each hit
+ *              g^T df/dverts at the fixed ray (barycentrics, albedo, normals);
+ *   edges    : edge_samples per view on the view's silhouette edges, uniform over the
+ *              edge list and along the edge, each tracing f+ and f- at +-edge_eps_px
+ *              along the edge's screen normal: A[p] . (f+ - f-) dalpha/d(endpoints)
+ *              times N_sil / edge_samples, mapped to vertices by the projection;
+ *   normals  : the vertex-normal adjoint of the interior term's normal gradient.
+ * Requires hr_build_bvh for the same verts; background as in the forward. */
+int hr_render_bwd(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams, int N,
+                  int H, int W, const float* background, const hr_render_opts* opts, const float* adjoint,
+                  float* d_verts, hr_stream stream);
+
+/* One Adam step (Section 3.3: the parameters are optimised with Adam) on n floats:
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps),  step >= 1. */
+int hr_adam_step(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1,
+                 float beta2, float eps, int step, hr_stream stream);
+
+/* Diagnostics over the context's current scene (used by the tests):
+ *   hr_trace:        closest hit of n rays (origins, dirs: device float[n][3]) against
+ *                    the last built BVH: tri (device int32[n], -1 = miss), tuv
+ *                    (device float[n][3] = t, u, v);
+ *   hr_get_normals:  copy the unit vertex normals to device float[V][3];
+ *   hr_silhouettes:  per-view silhouette edge ids (ascending) into lists (device
+ *                    int32[N][E]) and counts (device int32[N]). */
+int hr_trace(hr_context* ctx, const float* origins, const float* dirs, int n, int32_t* tri, float* tuv,
+             hr_stream stream);
+int hr_get_normals(hr_context* ctx, float* normals, hr_stream stream);
+int hr_silhouettes(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams, int N,
+                   int32_t* lists, int32_t* counts, hr_stream stream);
+
+/* Work counters of the calls made with HR_STATS since the last read: synchronise
+ * `stream`, copy 12 counters to host `out` and clear them.  out[0..3] = forward
+ * (rays traced, BVH nodes visited, triangle tests, hits), out[4..7] = the interior
+ * backward, out[8..11] = the edge-sample rays. */
+int hr_get_stats(hr_context* ctx, uint64_t* out, hr_stream stream);
+
+/* Synchronise `stream`, then return and clear the device status word: HR_OK, or the
+ * HR_ERR_* code of a device-detected error since the last call (HR_ERR_ARG for face
+ * or parent indices out of range, then HR_ERR_NONFINITE, then HR_ERR_LIMIT). */
+int hr_get_status(hr_context* ctx, hr_stream stream);
+
+/* Static text for a status code. */
+const char* hr_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HANDRT_H */

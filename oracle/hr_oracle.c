@@ -222,8 +222,8 @@ static void shade(const scene_t* sc, const hit_t* h, double rgb[3]) {
 }
 
 /* radiance along the ray through screen point (sx, sy) of view `view`; a miss
- * returns the background pixel containing the point (clamped to the image) */
-static hit_t radiance(const scene_t* sc, int view, float sx, float sy, double rgb[3]) {
+ * returns background pixel (bpx, bpy) */
+static hit_t radiance(const scene_t* sc, int view, float sx, float sy, int bpx, int bpy, double rgb[3]) {
     const cam_t* cam = sc->cams + view;
     f3 d;
     primary_dir(cam, sx, sy, &d);
@@ -232,12 +232,7 @@ static hit_t radiance(const scene_t* sc, int view, float sx, float sy, double rg
     if (h.tri >= 0) {
         shade(sc, &h, rgb);
     } else {
-        int px = (int)floorf(sx), py = (int)floorf(sy);
-        if (px < 0) px = 0;
-        if (px > sc->W - 1) px = sc->W - 1;
-        if (py < 0) py = 0;
-        if (py > sc->H - 1) py = sc->H - 1;
-        const float* b = sc->background + (((size_t)view * sc->H + py) * sc->W + px) * 3;
+        const float* b = sc->background + (((size_t)view * sc->H + bpy) * sc->W + bpx) * 3;
         rgb[0] = b[0]; rgb[1] = b[1]; rgb[2] = b[2];
     }
     return h;
@@ -364,7 +359,9 @@ static void* fwd_worker(void* arg) {
                 float u1, u2;
                 jitter(sc, view, px, py, s, &u1, &u2);
                 double rgb[3];
-                radiance(sc, view, (float)px + u1, (float)py + u2, rgb);
+                /* a primary sample estimates pixel (px, py): its miss value is that
+                 * pixel's background even when px + u1 rounds up to px + 1 */
+                radiance(sc, view, (float)px + u1, (float)py + u2, px, py, rgb);
                 acc[0] += rgb[0]; acc[1] += rgb[1]; acc[2] += rgb[2];
             }
             double* out = j->image + (((size_t)view * sc->H + py) * sc->W + px) * 3;
@@ -522,9 +519,15 @@ void oracle_render_bwd_edges(const float* verts, int V, const int32_t* faces, in
             if (A[0] == 0.0f && A[1] == 0.0f && A[2] == 0.0f) continue;
             float xp = fmaf(o->edge_eps, nhx, x), yp = fmaf(o->edge_eps, nhy, y);
             float xm = fmaf(-o->edge_eps, nhx, x), ym = fmaf(-o->edge_eps, nhy, y);
+            /* offset rays that miss see the background pixel containing the
+             * offset point, clamped to the image */
+            int bxp = (int)fminf(fmaxf(floorf(xp), 0.0f), (float)(W - 1));
+            int byp = (int)fminf(fmaxf(floorf(yp), 0.0f), (float)(H - 1));
+            int bxm = (int)fminf(fmaxf(floorf(xm), 0.0f), (float)(W - 1));
+            int bym = (int)fminf(fmaxf(floorf(ym), 0.0f), (float)(H - 1));
             double fp[3], fm[3];
-            radiance(&sc, view, xp, yp, fp);
-            radiance(&sc, view, xm, ym, fm);
+            radiance(&sc, view, xp, yp, bxp, byp, fp);
+            radiance(&sc, view, xm, ym, bxm, bym, fm);
             double wgt = 0.0;
             for (int c = 0; c < 3; ++c) wgt += (double)A[c] * (fp[c] - fm[c]);
             if (wgt == 0.0) continue;

@@ -1,0 +1,264 @@
+"""Thin Python binding of the handrt C ABI (include/handrt.h).
+
+Argument marshalling only: every function forwards device pointers of torch tensors
+(and the current CUDA stream) to the library, checks the returned status code and
+raises HandrtError on failure.  All computation happens in the CUDA kernels; there
+is no CPU or PyTorch fallback, and loading fails loudly when the library has not
+been built (``python -m paper_2107_05509_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhandrt.so")
+
+HR_OK = 0
+HR_ERR_ARG = -1
+HR_ERR_CUDA = -2
+HR_ERR_LIMIT = -3
+HR_ERR_NONFINITE = -4
+HR_ERR_UNSUPPORTED = -5
+HR_BWD_NO_INTERIOR = 1
+HR_BWD_NO_EDGES = 2
+HR_BWD_NO_NORMALS = 4
+HR_STATS = 8
+
+EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", "hr_build_bvh", "hr_render_fwd",
+           "hr_loss", "hr_render_bwd", "hr_adam_step", "hr_trace", "hr_get_normals", "hr_silhouettes",
+           "hr_get_stats", "hr_get_status", "hr_status_string")
+
+
+class HandrtError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} failed: {code} ({status_string(code)})")
+        self.code = code
+
+
+class hr_model(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_int32), ("F", ctypes.c_int32), ("E", ctypes.c_int32), ("J", ctypes.c_int32),
+                ("K", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in (
+                    "v_template", "shapedirs", "weights", "j_template", "j_shapedirs", "parents", "faces", "edges",
+                    "edge_faces", "vf_offsets", "vf_faces", "albedo")]
+
+
+class hr_render_opts(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("iter", ctypes.c_uint32), ("instance", ctypes.c_uint32),
+                ("spp", ctypes.c_int32), ("edge_samples", ctypes.c_int32), ("ka", ctypes.c_float),
+                ("kd", ctypes.c_float), ("light_dir", ctypes.c_float * 3), ("light_rgb", ctypes.c_float * 3),
+                ("edge_eps_px", ctypes.c_float), ("flags", ctypes.c_uint32)]
+
+
+class hr_limits(ctypes.Structure):
+    _fields_ = [("max_V", ctypes.c_int32), ("max_F", ctypes.c_int32), ("max_E", ctypes.c_int32),
+                ("max_views", ctypes.c_int32), ("max_pixels", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"handrt CUDA library not built: {LIB_PATH} is missing "
+                               "(run `python -m paper_2107_05509_gb300.build`)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        sig = {
+            "hr_context_create": [P, P],
+            "hr_context_destroy": [P],
+            "hr_skin": [P, P, P, P, P],
+            "hr_skin_bwd": [P, P, P, P, P, P],
+            "hr_build_bvh": [P, P, P, P],
+            "hr_render_fwd": [P, P, P, P, I, I, I, P, P, P, P],
+            "hr_loss": [P, P, P, P, I, I, I, P, P, P],
+            "hr_render_bwd": [P, P, P, P, I, I, I, P, P, P, P, P],
+            "hr_adam_step": [P, P, P, P, I, F, F, F, F, I, P],
+            "hr_trace": [P, P, P, I, P, P, P],
+            "hr_get_normals": [P, P, P],
+            "hr_silhouettes": [P, P, P, P, I, P, P, P],
+            "hr_get_stats": [P, P, P],
+            "hr_get_status": [P, P],
+            "hr_status_string": [I],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_char_p if name == "hr_status_string" else ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().hr_status_string(int(code)).decode()
+
+
+def _check(name, code):
+    if code != HR_OK:
+        raise HandrtError(name, code)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("handrt takes CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("handrt takes contiguous tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _f32(t):
+    assert t.dtype == torch.float32, t.dtype
+    return _ptr(t)
+
+
+# --------------------------------------------------------------------------------------
+# Objects owning C-side state
+# --------------------------------------------------------------------------------------
+
+class Context:
+    """An hr_context: device scratch, BVH and status word, sized by the limits."""
+
+    def __init__(self, max_V, max_F, max_E, max_views, max_pixels):
+        lim = hr_limits(max_V, max_F, max_E, max_views, max_pixels)
+        h = ctypes.c_void_p()
+        _check("hr_context_create", lib().hr_context_create(ctypes.byref(lim), ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            lib().hr_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Model:
+    """Device copy of a hand model (inputs.HandModel) and its hr_model struct."""
+
+    def __init__(self, hand, device="cuda"):
+        def f(a):
+            return torch.as_tensor(np.ascontiguousarray(a, np.float32), device=device)
+
+        def i(a):
+            return torch.as_tensor(np.ascontiguousarray(a, np.int32), device=device)
+
+        self.hand = hand
+        self.t = dict(v_template=f(hand.v_template), shapedirs=f(hand.shapedirs), weights=f(hand.weights),
+                      j_template=f(hand.j_template), j_shapedirs=f(hand.j_shapedirs), parents=i(hand.parents),
+                      faces=i(hand.faces), edges=i(hand.edges), edge_faces=i(hand.edge_faces),
+                      vf_offsets=i(hand.vf_offsets), vf_faces=i(hand.vf_faces), albedo=f(hand.albedo))
+        m = hr_model()
+        m.V, m.F, m.E = hand.V, hand.F, hand.E
+        m.J, m.K = hand.weights.shape[1], hand.shapedirs.shape[2]
+        for k, v in self.t.items():
+            setattr(m, k, v.data_ptr())
+        self.struct = m
+
+    @property
+    def V(self):
+        return self.struct.V
+
+
+def render_opts(seed=0, iter=0, instance=0, spp=4, edge_samples=1024, ka=0.4, kd=0.6, light_dir=(0.0, 0.0, 1.0),
+                light_rgb=(1.0, 1.0, 1.0), edge_eps_px=1e-3, flags=0):
+    o = hr_render_opts()
+    o.seed = seed
+    o.iter = iter
+    o.instance = instance
+    o.spp = spp
+    o.edge_samples = edge_samples
+    o.ka, o.kd = ka, kd
+    o.light_dir[:] = list(light_dir)
+    o.light_rgb[:] = list(light_rgb)
+    o.edge_eps_px = edge_eps_px
+    o.flags = flags
+    return o
+
+
+# --------------------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# --------------------------------------------------------------------------------------
+
+def hr_skin(ctx, model, params, verts, stream=None):
+    _check("hr_skin", lib().hr_skin(ctx.handle, ctypes.byref(model.struct), _f32(params), _f32(verts),
+                                    _stream(stream)))
+
+
+def hr_skin_bwd(ctx, model, params, d_verts, d_params, stream=None):
+    _check("hr_skin_bwd", lib().hr_skin_bwd(ctx.handle, ctypes.byref(model.struct), _f32(params), _f32(d_verts),
+                                            _f32(d_params), _stream(stream)))
+
+
+def hr_build_bvh(ctx, model, verts, stream=None):
+    _check("hr_build_bvh", lib().hr_build_bvh(ctx.handle, ctypes.byref(model.struct), _f32(verts),
+                                              _stream(stream)))
+
+
+def hr_render_fwd(ctx, model, verts, cams, H, W, background, opts, image, stream=None):
+    N = cams.shape[0]
+    _check("hr_render_fwd", lib().hr_render_fwd(ctx.handle, ctypes.byref(model.struct), _f32(verts), _f32(cams), N,
+                                                H, W, _f32(background), ctypes.byref(opts), _f32(image),
+                                                _stream(stream)))
+
+
+def hr_loss(ctx, image, observed, mask, loss, adjoint, stream=None):
+    N, H, W = mask.shape
+    assert mask.dtype == torch.uint8
+    _check("hr_loss", lib().hr_loss(ctx.handle, _f32(image), _f32(observed), _ptr(mask), N, H, W, _f32(loss),
+                                    _f32(adjoint), _stream(stream)))
+
+
+def hr_render_bwd(ctx, model, verts, cams, H, W, background, opts, adjoint, d_verts, stream=None):
+    N = cams.shape[0]
+    _check("hr_render_bwd", lib().hr_render_bwd(ctx.handle, ctypes.byref(model.struct), _f32(verts), _f32(cams), N,
+                                                H, W, _f32(background), ctypes.byref(opts), _f32(adjoint),
+                                                _f32(d_verts), _stream(stream)))
+
+
+def hr_adam_step(params, grad, m, v, lr, beta1, beta2, eps, step, stream=None):
+    _check("hr_adam_step", lib().hr_adam_step(_f32(params), _f32(grad), _f32(m), _f32(v), params.numel(), lr, beta1,
+                                              beta2, eps, step, _stream(stream)))
+
+
+def hr_trace(ctx, origins, dirs, tri, tuv, stream=None):
+    assert tri.dtype == torch.int32
+    _check("hr_trace", lib().hr_trace(ctx.handle, _f32(origins), _f32(dirs), origins.shape[0], _ptr(tri), _f32(tuv),
+                                      _stream(stream)))
+
+
+def hr_get_normals(ctx, normals, stream=None):
+    _check("hr_get_normals", lib().hr_get_normals(ctx.handle, _f32(normals), _stream(stream)))
+
+
+def hr_silhouettes(ctx, model, verts, cams, lists, counts, stream=None):
+    _check("hr_silhouettes", lib().hr_silhouettes(ctx.handle, ctypes.byref(model.struct), _f32(verts), _f32(cams),
+                                                  cams.shape[0], _ptr(lists), _ptr(counts), _stream(stream)))
+
+
+def hr_get_stats(ctx, stream=None):
+    """12 work counters (forward, interior backward, edge rays: rays, nodes, triangle
+    tests, hits) accumulated by calls made with HR_STATS; cleared on read."""
+    out = (ctypes.c_uint64 * 12)()
+    _check("hr_get_stats", lib().hr_get_stats(ctx.handle, out, _stream(stream)))
+    return np.array(out[:], np.uint64).reshape(3, 4)
+
+
+def hr_get_status(ctx, stream=None):
+    return int(lib().hr_get_status(ctx.handle, _stream(stream)))

@@ -1,0 +1,296 @@
+// Per-iteration scene build: a Morton-code linear BVH over the current triangles
+// (Karras, "Maximizing parallelism in the construction of BVHs, octrees, and k-d
+// trees", HPG 2012) and the area-weighted unit vertex normals used for shading.
+//
+// The whole build runs in ONE thread block: at a hand's size (1.5k triangles) it
+// is latency-bound, and one block keeps every phase in shared memory with only
+// __syncthreads between phases -- centroid bounds, 30-bit Morton codes, a bitonic
+// sort of (code << 32 | triangle id) keys (unique, so the hierarchy has no
+// duplicate-key special case), the hierarchy, then a bottom-up refit in which the
+// second child to arrive at a node (atomic counter in shared memory) writes the
+// union box into the parent.  Leaf boxes are padded so that the float32 slab test
+// can never reject a ray that the float32 Moller-Trumbore test would accept.
+#include <cstdio>
+
+#include "hr_internal.h"
+
+namespace hr {
+
+namespace {
+
+constexpr int kBuildThreads = 1024;
+
+__device__ __forceinline__ unsigned expand_bits10(unsigned v) {
+  v = (v * 0x00010001u) & 0xFF0000FFu;
+  v = (v * 0x00000101u) & 0x0F00F00Fu;
+  v = (v * 0x00000011u) & 0xC30C30C3u;
+  v = (v * 0x00000005u) & 0x49249249u;
+  return v;
+}
+
+__device__ __forceinline__ int delta(const unsigned long long* keys, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  return __clzll(keys[i] ^ keys[j]);
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+struct Box {
+  float lo[3], hi[3];
+};
+
+__device__ __forceinline__ void store_slot(Node* nodes, int p, int slot, const Box& b) {
+  volatile float* f = reinterpret_cast<volatile float*>(&nodes[p]);
+  int o = slot ? 6 : 0;
+  f[o + 0] = b.lo[0];
+  f[o + 1] = b.lo[1];
+  f[o + 2] = b.lo[2];
+  f[o + 3] = b.hi[0];
+  f[o + 4] = b.hi[1];
+  f[o + 5] = b.hi[2];
+}
+
+__device__ __forceinline__ Box load_union(const Node* nodes, int p) {
+  const volatile float* f = reinterpret_cast<const volatile float*>(&nodes[p]);
+  Box b;
+  for (int c = 0; c < 3; ++c) {
+    b.lo[c] = fminf(f[c], f[6 + c]);
+    b.hi[c] = fmaxf(f[3 + c], f[9 + c]);
+  }
+  return b;
+}
+
+// shared memory: keys [P] u64, parent [2F] int, visit flags [F] int
+__global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __restrict__ verts,
+                                                             const int* __restrict__ faces, int F, int V, int P,
+                                                             Node* __restrict__ nodes, float4* __restrict__ tris,
+                                                             int* status) {
+  extern __shared__ unsigned long long smem_keys[];
+  unsigned long long* keys = smem_keys;
+  int* parent = reinterpret_cast<int*>(keys + P);
+  int* flags = parent + 2 * F;
+  __shared__ float red[6][32];
+  __shared__ float bounds[6];
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  // 0. face indices must address [0, V); otherwise record the error and build nothing
+  for (int i = tid; i < 3 * F; i += blockDim.x)
+    if (faces[i] < 0 || faces[i] >= V) bad = 1;
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) {
+      set_status(status, kStatusBadModel);
+      nodes[0].d = make_int4(~0, ~0, 0, 0);   // a one-leaf tree over a degenerate record
+      nodes[0].a = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
+      nodes[0].b = make_float4(-1.0f, -1.0f, 1.0f, 1.0f);
+      nodes[0].c = make_float4(1.0f, -1.0f, -1.0f, -1.0f);
+      tris[0] = tris[1] = tris[2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    return;
+  }
+
+  // 1. centroid bounds
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int f = tid; f < F; f += blockDim.x) {
+    int3 fc = make_int3(faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]);
+    for (int c = 0; c < 3; ++c) {
+      float x = (verts[3 * fc.x + c] + verts[3 * fc.y + c] + verts[3 * fc.z + c]) * (1.0f / 3.0f);
+      lo[c] = fminf(lo[c], x);
+      hi[c] = fmaxf(hi[c], x);
+    }
+  }
+  for (int c = 0; c < 3; ++c) {
+    float a = warp_min(lo[c]), b = warp_max(hi[c]);
+    if (lane == 0) {
+      red[c][warp] = a;
+      red[3 + c][warp] = b;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    int nw = blockDim.x >> 5;
+    for (int c = 0; c < 3; ++c) {
+      float a = lane < nw ? red[c][lane] : INFINITY;
+      float b = lane < nw ? red[3 + c][lane] : -INFINITY;
+      a = warp_min(a);
+      b = warp_max(b);
+      if (lane == 0) {
+        bounds[c] = a;
+        bounds[3 + c] = b;
+      }
+    }
+  }
+  __syncthreads();
+
+  // 2. Morton keys (code << 32 | triangle id), padded to P with all-ones
+  for (int i = tid; i < P; i += blockDim.x) {
+    unsigned long long key = ~0ull;
+    if (i < F) {
+      int3 fc = make_int3(faces[3 * i], faces[3 * i + 1], faces[3 * i + 2]);
+      unsigned q[3];
+      for (int c = 0; c < 3; ++c) {
+        float x = (verts[3 * fc.x + c] + verts[3 * fc.y + c] + verts[3 * fc.z + c]) * (1.0f / 3.0f);
+        float ext = bounds[3 + c] - bounds[c];
+        float n = ext > 0.0f ? (x - bounds[c]) / ext : 0.5f;
+        q[c] = (unsigned)fminf(fmaxf(n * 1024.0f, 0.0f), 1023.0f);
+      }
+      unsigned code = (expand_bits10(q[0]) << 2) | (expand_bits10(q[1]) << 1) | expand_bits10(q[2]);
+      key = ((unsigned long long)code << 32) | (unsigned)i;
+    }
+    keys[i] = key;
+  }
+  for (int i = tid; i < F; i += blockDim.x) flags[i] = 0;
+  __syncthreads();
+
+  // 3. bitonic sort (ascending)
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < P; i += blockDim.x) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          unsigned long long a = keys[i], b = keys[ixj];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            keys[i] = b;
+            keys[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // 4. hierarchy (internal nodes 0..F-2; leaves encoded ~k, k = sorted position)
+  if (F == 1) {
+    if (tid == 0) {
+      nodes[0].d = make_int4(~0, ~0, 0, 0);
+      parent[0] = -1;
+      parent[F + 0] = 0;
+    }
+  }
+  for (int i = tid; i < F - 1; i += blockDim.x) {
+    int d = (delta(keys, F, i, i + 1) - delta(keys, F, i, i - 1)) > 0 ? 1 : -1;
+    int dmin = delta(keys, F, i, i - d);
+    int lmax = 2;
+    while (delta(keys, F, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+      if (delta(keys, F, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta(keys, F, i, j);
+    int s = 0, t = l;
+    do {
+      t = (t + 1) >> 1;
+      if (delta(keys, F, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int gamma = i + s * d + min(d, 0);
+    int left = (min(i, j) == gamma) ? ~gamma : gamma;
+    int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    nodes[i].d = make_int4(left, right, 0, 0);
+    if (left >= 0) parent[left] = i; else parent[F + ~left] = i;
+    if (right >= 0) parent[right] = i; else parent[F + ~right] = i;
+    if (i == 0) parent[0] = -1;
+  }
+  __syncthreads();
+
+  // 5. triangle records and leaf boxes, then the bottom-up refit
+  for (int k = tid; k < F; k += blockDim.x) {
+    int tri = (int)(keys[k] & 0xffffffffull);
+    float3 v0 = ld3(verts + 3 * faces[3 * tri]);
+    float3 v1 = ld3(verts + 3 * faces[3 * tri + 1]);
+    float3 v2 = ld3(verts + 3 * faces[3 * tri + 2]);
+    float3 e1 = dsub(v1, v0), e2 = dsub(v2, v0);
+    tris[3 * k + 0] = make_float4(v0.x, v0.y, v0.z, e1.x);
+    tris[3 * k + 1] = make_float4(e1.y, e1.z, e2.x, e2.y);
+    tris[3 * k + 2] = make_float4(e2.z, __int_as_float(tri), 0.0f, 0.0f);
+    Box b;
+    float amax = 0.0f;
+    float p0[3] = {v0.x, v0.y, v0.z}, p1[3] = {v1.x, v1.y, v1.z}, p2[3] = {v2.x, v2.y, v2.z};
+    for (int c = 0; c < 3; ++c) {
+      b.lo[c] = fminf(p0[c], fminf(p1[c], p2[c]));
+      b.hi[c] = fmaxf(p0[c], fmaxf(p1[c], p2[c]));
+      amax = fmaxf(amax, fmaxf(fabsf(b.lo[c]), fabsf(b.hi[c])));
+    }
+    float pad = 1e-6f + 1e-5f * amax;
+    for (int c = 0; c < 3; ++c) {
+      b.lo[c] -= pad;
+      b.hi[c] += pad;
+    }
+    int p = parent[F + k];
+    int slot = (nodes[p].d.x == ~k) ? 0 : 1;
+    if (F == 1) {
+      store_slot(nodes, 0, 0, b);
+      store_slot(nodes, 0, 1, b);
+      continue;
+    }
+    store_slot(nodes, p, slot, b);
+    __threadfence_block();
+    for (int up = 0; up < F; ++up) {   // a well-formed tree is at most F - 1 levels deep
+      if (atomicAdd(&flags[p], 1) == 0) break;   // the sibling is not done yet
+      __threadfence_block();
+      Box u = load_union(nodes, p);
+      int gp = parent[p];
+      if (gp < 0) break;                          // p is the root
+      int gslot = (nodes[gp].d.x == p) ? 0 : 1;
+      store_slot(nodes, gp, gslot, u);
+      __threadfence_block();
+      p = gp;
+    }
+  }
+}
+
+__global__ void k_vertex_normals(const float* __restrict__ verts, const int* __restrict__ faces,
+                                 const int* __restrict__ vf_off, const int* __restrict__ vf_faces, int V,
+                                 float* __restrict__ normals, float* __restrict__ normal_len) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  float3 m = make_float3(0.0f, 0.0f, 0.0f);
+  for (int k = vf_off[v]; k < vf_off[v + 1]; ++k) {
+    int f = vf_faces[k];
+    float3 a = ld3(verts + 3 * faces[3 * f]), b = ld3(verts + 3 * faces[3 * f + 1]),
+           c = ld3(verts + 3 * faces[3 * f + 2]);
+    float3 cf = dcross(dsub(b, a), dsub(c, a));
+    m = make_float3(__fadd_rn(m.x, cf.x), __fadd_rn(m.y, cf.y), __fadd_rn(m.z, cf.z));
+  }
+  float len = __fsqrt_rn(ddot(m, m));
+  float3 n = len > 0.0f ? make_float3(__fdiv_rn(m.x, len), __fdiv_rn(m.y, len), __fdiv_rn(m.z, len))
+                        : make_float3(0.0f, 0.0f, 0.0f);
+  normals[3 * v] = n.x;
+  normals[3 * v + 1] = n.y;
+  normals[3 * v + 2] = n.z;
+  normal_len[v] = len;
+}
+
+}  // namespace
+
+int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaStream_t s) {
+  int F = m->F, V = m->V;
+  int P = 1;
+  while (P < F) P <<= 1;
+  size_t smem = (size_t)P * 8 + (size_t)3 * F * 4;
+  if (smem > 200 * 1024) return HR_ERR_UNSUPPORTED;
+  // per device and cheap: set on every call rather than caching device state
+  if (cudaFuncSetAttribute(k_build_bvh, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+    return HR_ERR_CUDA;
+  k_build_bvh<<<1, kBuildThreads, smem, s>>>(verts, m->faces, F, V, P, ctx->nodes, ctx->tris, ctx->status);
+  HR_CHECK_LAUNCH();
+  k_vertex_normals<<<(V + 255) / 256, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, V, ctx->normals,
+                                                   ctx->normal_len);
+  HR_CHECK_LAUNCH();
+  ctx->V = V;
+  ctx->F = F;
+  return HR_OK;
+}
+
+}  // namespace hr

@@ -1,0 +1,168 @@
+// Device-side building blocks shared by the handrt kernels: the context layout,
+// Philox4x32-10 sample streams, and the float32 "decision arithmetic" -- every
+// operation whose result decides a branch or an integer (which triangle a sample
+// hits, lit or unlit, silhouette or not, which pixel an edge sample lands in) is
+// written with explicitly rounded intrinsics (__fmul_rn, __fadd_rn, __fsub_rn,
+// __fdiv_rn, __fsqrt_rn, __fmaf_rn), so the compiler cannot contract or reorder it
+// and the result is the same float32 value on every run.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/handrt.h"
+
+namespace hr {
+
+constexpr int kStack = 64;          // BVH traversal stack entries per ray
+constexpr int kStatusLimit = 1;     // device status bits
+constexpr int kStatusNonfinite = 2;
+constexpr int kStatusBadModel = 4;  // a face or parent index out of range
+
+// ---------------------------------------------------------------------------------
+// BVH layout (binary LBVH, F-1 internal nodes, leaves = triangle records)
+//   node n: float4 a = (lminx, lminy, lminz, lmaxx)
+//           float4 b = (lmaxy, lmaxz, rminx, rminy)
+//           float4 c = (rminz, rmaxx, rmaxy, rmaxz)
+//           int4   d = (left, right, -, -); child >= 0: internal node, < 0: leaf ~idx
+//   triangle record k (in Morton order): float4 (v0.xyz, e1.x), (e1.yz, e2.xy),
+//                                        (e2.z, tri_id bits, 0, 0)
+// ---------------------------------------------------------------------------------
+struct Node {
+  float4 a, b, c;
+  int4 d;
+};
+
+struct Context {
+  hr_limits lim;
+  int device;
+  int num_sms;
+  int render_blocks;     // persistent grid of the render kernels
+  int render_threads;
+  // scene
+  int V, F;              // sizes of the last hr_build_bvh
+  Node* nodes;           // [max_F]
+  float4* tris;          // [max_F][3]
+  float* normals;        // [max_V][3] unit vertex normals
+  float* normal_len;     // [max_V]    |m_v|
+  // BVH build scratch
+  unsigned long long* keys;  // [max_F]
+  int* parent;               // [2 max_F]
+  // backward scratch
+  float* partials;       // [render_blocks][max_V][6]
+  float* dN;             // [max_V][3]
+  float* dm;             // [max_V][3]
+  int* sil;              // [max_views][max_E]
+  int* sil_count;        // [max_views]
+  // loss scratch
+  float* loss_partials;  // [kLossBlocks] + 2 scalars
+  unsigned int* counters;// [4] last-block counters
+  // skin scratch
+  float* skin_partials;  // [kSkinBlocks][kSkinAcc]
+  // status and work counters
+  int* status;
+  unsigned long long* stats;  // [12]
+};
+
+constexpr int kLossBlocks = 1024;
+constexpr int kSkinBlocks = 64;
+constexpr int kSkinAcc = 16 * 12 + 10 + 3;   // dA_j (J=16 x 3x4), dbeta, dtau
+constexpr int kMaxJ = 16;
+constexpr int kMaxK = 10;
+
+// ---------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// uniform in [0, 1): the top 24 bits, exact in float32
+__device__ __forceinline__ float u24(uint32_t r) {
+  return __fmul_rn(__uint2float_rn(r >> 8), 5.9604644775390625e-08f);
+}
+
+// ---------------------------------------------------------------------------------
+// float32 decision arithmetic
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float3 dsub(float3 a, float3 b) {
+  return make_float3(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z));
+}
+__device__ __forceinline__ float3 dcross(float3 a, float3 b) {
+  return make_float3(__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
+                     __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float ddot(float3 a, float3 b) {
+  return __fmaf_rn(a.x, b.x, __fmaf_rn(a.y, b.y, __fmul_rn(a.z, b.z)));
+}
+
+struct Cam {
+  float fx, fy, cx, cy, R[9], t[3], c[3], pad;
+};
+static_assert(sizeof(Cam) == sizeof(hr_camera), "camera layout");
+
+// world-space direction of the primary ray through screen point (sx, sy)
+__device__ __forceinline__ float3 primary_dir(const Cam& cam, float sx, float sy) {
+  float dcx = __fdiv_rn(__fsub_rn(sx, cam.cx), cam.fx);
+  float dcy = __fdiv_rn(__fsub_rn(sy, cam.cy), cam.fy);
+  return make_float3(__fmaf_rn(cam.R[0], dcx, __fmaf_rn(cam.R[3], dcy, cam.R[6])),
+                     __fmaf_rn(cam.R[1], dcx, __fmaf_rn(cam.R[4], dcy, cam.R[7])),
+                     __fmaf_rn(cam.R[2], dcx, __fmaf_rn(cam.R[5], dcy, cam.R[8])));
+}
+
+// Moller-Trumbore, double-sided; true on a hit with t > 0
+__device__ __forceinline__ bool mt_hit(float3 o, float3 d, float3 v0, float3 e1, float3 e2, float& t,
+                                       float& u, float& v) {
+  float3 p = dcross(d, e2);
+  float det = ddot(e1, p);
+  if (det == 0.0f) return false;
+  float inv = __fdiv_rn(1.0f, det);
+  float3 s = dsub(o, v0);
+  u = __fmul_rn(ddot(s, p), inv);
+  float3 q = dcross(s, e1);
+  v = __fmul_rn(ddot(d, q), inv);
+  t = __fmul_rn(ddot(e2, q), inv);
+  return u >= 0.0f && u <= 1.0f && v >= 0.0f && __fadd_rn(u, v) <= 1.0f && t > 0.0f;
+}
+
+// lit/unlit decision: sign of n_interp . l with n_interp = w n0 + u n1 + v n2
+__device__ __forceinline__ float3 interp_normal(float u, float v, float3 n0, float3 n1, float3 n2) {
+  float w = __fsub_rn(__fsub_rn(1.0f, u), v);
+  return make_float3(__fmaf_rn(v, n2.x, __fmaf_rn(u, n1.x, __fmul_rn(w, n0.x))),
+                     __fmaf_rn(v, n2.y, __fmaf_rn(u, n1.y, __fmul_rn(w, n0.y))),
+                     __fmaf_rn(v, n2.z, __fmaf_rn(u, n1.z, __fmul_rn(w, n0.z))));
+}
+
+// pinhole projection of a vertex to screen; false when Z <= 1e-3
+__device__ __forceinline__ bool project(const Cam& cam, float3 p, float& ax, float& ay) {
+  float X = __fmaf_rn(cam.R[0], p.x, __fmaf_rn(cam.R[1], p.y, __fmaf_rn(cam.R[2], p.z, cam.t[0])));
+  float Y = __fmaf_rn(cam.R[3], p.x, __fmaf_rn(cam.R[4], p.y, __fmaf_rn(cam.R[5], p.z, cam.t[1])));
+  float Z = __fmaf_rn(cam.R[6], p.x, __fmaf_rn(cam.R[7], p.y, __fmaf_rn(cam.R[8], p.z, cam.t[2])));
+  if (!(Z > 1e-3f)) return false;
+  ax = __fmaf_rn(cam.fx, __fdiv_rn(X, Z), cam.cx);
+  ay = __fmaf_rn(cam.fy, __fdiv_rn(Y, Z), cam.cy);
+  return true;
+}
+
+__device__ __forceinline__ float3 ld3(const float* p) { return make_float3(p[0], p[1], p[2]); }
+
+__device__ __forceinline__ void set_status(int* status, int bit) { atomicOr(status, bit); }
+
+}  // namespace hr
+
+// launch helpers implemented per translation unit; every host entry returns an HR code
+#define HR_CHECK_LAUNCH()                                   \
+  do {                                                      \
+    if (cudaPeekAtLastError() != cudaSuccess) {             \
+      cudaGetLastError();                                   \
+      return HR_ERR_CUDA;                                   \
+    }                                                       \
+  } while (0)

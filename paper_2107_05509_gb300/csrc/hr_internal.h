@@ -1,0 +1,31 @@
+// Host-side launchers shared between the handrt translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hr_device.cuh"
+
+namespace hr {
+
+int launch_skin(Context* ctx, const hr_model* m, const float* params, float* verts, cudaStream_t s);
+int launch_skin_bwd(Context* ctx, const hr_model* m, const float* params, const float* d_verts,
+                    float* d_params, cudaStream_t s);
+int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaStream_t s);
+int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,
+                      const float* bg, const hr_render_opts* o, float* image, cudaStream_t s);
+int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,
+                      const float* bg, const hr_render_opts* o, const float* adjoint, float* d_verts,
+                      cudaStream_t s);
+int launch_silhouettes(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int* lists,
+                       int list_stride, int* counts, cudaStream_t s);
+int launch_trace(Context* ctx, const float* o, const float* d, int n, int* tri, float* tuv, cudaStream_t s);
+int launch_loss(Context* ctx, const float* image, const float* obs, const uint8_t* mask, long long P,
+                float* loss, float* adjoint, cudaStream_t s);
+int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
+                int step, cudaStream_t s);
+
+// per-device properties of the render kernels (persistent grid)
+int render_grid(int device, int* blocks, int* threads, int* num_sms);
+size_t render_bwd_smem(int V);
+
+}  // namespace hr

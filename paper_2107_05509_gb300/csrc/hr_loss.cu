@@ -1,0 +1,176 @@
+// Masked photometric loss (Eq. 3 with the D_c term of Eq. 4, summed over views)
+// and its adjoint, plus the Adam update (Section 3.3).
+//
+//   k_mask_count    integer count of masked pixels; the last block to finish sums the
+//                   per-block counts in block order and stores 1 / (3 sum M).
+//   k_loss_adjoint  adjoint = M sign(R - O) / (3 sum M) and per-block partial sums of
+//                   M |R - O|; the last block sums the partials in block order (in
+//                   double) into the loss.  Both reductions are deterministic.
+// The image is streamed as float4 (4 pixels = 3 float4 per thread) when its
+// pointers are 16-byte aligned.
+#include "hr_internal.h"
+
+namespace hr {
+
+namespace {
+
+constexpr int kLossThreads = 256;
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x, unsigned long long* red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  unsigned long long s = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+__device__ __forceinline__ float block_sum_f(float x, float* red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  float s = 0.0f;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+// scratch: counts[kLossBlocks] (u64), partials[kLossBlocks] (float), scale, total
+__global__ void __launch_bounds__(kLossThreads) k_mask_count(const uint8_t* __restrict__ mask, long long P,
+                                                             unsigned long long* __restrict__ counts,
+                                                             unsigned* counter, float* __restrict__ scale) {
+  __shared__ unsigned long long red[32];
+  __shared__ bool last;
+  unsigned long long c = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x)
+    c += mask[i] != 0;
+  unsigned long long s = block_sum_u64(c, red);
+  if (threadIdx.x == 0) {
+    counts[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  unsigned long long tot = 0;
+  for (int b = 0; b < (int)gridDim.x; ++b) tot += __ldcg(&counts[b]);
+  scale[0] = tot > 0 ? (float)(1.0 / (3.0 * (double)tot)) : 0.0f;
+  *counter = 0u;
+}
+
+__device__ __forceinline__ float sgn(float d) { return d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f); }
+
+__global__ void __launch_bounds__(kLossThreads) k_loss_adjoint(const float* __restrict__ image,
+                                                               const float* __restrict__ obs,
+                                                               const uint8_t* __restrict__ mask, long long P,
+                                                               const float* __restrict__ scale,
+                                                               float* __restrict__ adjoint,
+                                                               float* __restrict__ partials, unsigned* counter,
+                                                               float* __restrict__ loss, bool vec) {
+  __shared__ float red[32];
+  __shared__ bool last;
+  const float sc = scale[0];
+  float acc = 0.0f;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (vec) {
+    // 4 pixels = 12 floats = 3 float4 per step
+    const long long Q = P / 4;
+    const float4* R4 = reinterpret_cast<const float4*>(image);
+    const float4* O4 = reinterpret_cast<const float4*>(obs);
+    float4* A4 = reinterpret_cast<float4*>(adjoint);
+    const uchar4* M4 = reinterpret_cast<const uchar4*>(mask);
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += stride) {
+      uchar4 m4 = M4[q];
+      float mk[4] = {m4.x ? 1.0f : 0.0f, m4.y ? 1.0f : 0.0f, m4.z ? 1.0f : 0.0f, m4.w ? 1.0f : 0.0f};
+      float r[12], o[12], a[12];
+      for (int k = 0; k < 3; ++k) {
+        float4 rv = R4[3 * q + k], ov = O4[3 * q + k];
+        r[4 * k] = rv.x; r[4 * k + 1] = rv.y; r[4 * k + 2] = rv.z; r[4 * k + 3] = rv.w;
+        o[4 * k] = ov.x; o[4 * k + 1] = ov.y; o[4 * k + 2] = ov.z; o[4 * k + 3] = ov.w;
+      }
+      for (int e = 0; e < 12; ++e) {
+        float m = mk[e / 3];
+        float d = r[e] - o[e];
+        a[e] = m * sgn(d) * sc;
+        acc += m * fabsf(d);
+      }
+      for (int k = 0; k < 3; ++k) A4[3 * q + k] = make_float4(a[4 * k], a[4 * k + 1], a[4 * k + 2], a[4 * k + 3]);
+    }
+    for (long long p = 4 * Q + (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+      float m = mask[p] ? 1.0f : 0.0f;
+      for (int c = 0; c < 3; ++c) {
+        float d = image[3 * p + c] - obs[3 * p + c];
+        adjoint[3 * p + c] = m * sgn(d) * sc;
+        acc += m * fabsf(d);
+      }
+    }
+  } else {
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+      float m = mask[p] ? 1.0f : 0.0f;
+      for (int c = 0; c < 3; ++c) {
+        float d = image[3 * p + c] - obs[3 * p + c];
+        adjoint[3 * p + c] = m * sgn(d) * sc;
+        acc += m * fabsf(d);
+      }
+    }
+  }
+  float s = block_sum_f(acc, red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double tot = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) tot += (double)__ldcg(&partials[b]);
+  loss[0] = (float)(tot * (double)sc);
+  *counter = 0u;
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = g[i];
+  float mi = b1 * m[i] + (1.0f - b1) * gi;
+  float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace
+
+int launch_loss(Context* ctx, const float* image, const float* obs, const uint8_t* mask, long long P, float* loss,
+                float* adjoint, cudaStream_t s) {
+  long long want = (P + kLossThreads - 1) / kLossThreads;
+  int blocks = (int)(want < kLossBlocks ? (want > 0 ? want : 1) : kLossBlocks);
+  unsigned long long* counts = reinterpret_cast<unsigned long long*>(ctx->loss_partials);
+  float* partials = ctx->loss_partials + 2 * kLossBlocks;
+  float* scale = partials + kLossBlocks;
+  k_mask_count<<<blocks, kLossThreads, 0, s>>>(mask, P, counts, ctx->counters, scale);
+  HR_CHECK_LAUNCH();
+  bool vec = ((reinterpret_cast<uintptr_t>(image) | reinterpret_cast<uintptr_t>(obs) |
+               reinterpret_cast<uintptr_t>(adjoint)) & 15) == 0 &&
+             (reinterpret_cast<uintptr_t>(mask) & 3) == 0;
+  k_loss_adjoint<<<blocks, kLossThreads, 0, s>>>(image, obs, mask, P, scale, adjoint, partials, ctx->counters + 1,
+                                                 loss, vec);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps, int step,
+                cudaStream_t s) {
+  float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+  k_adam<<<(n + 127) / 128, 128, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+}  // namespace hr
