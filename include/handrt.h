@@ -47,6 +47,7 @@ extern "C" {
 #define HR_ERR_LIMIT (-3)       /* a device-side limit was hit (traversal stack) */
 #define HR_ERR_NONFINITE (-4)   /* non-finite parameters reached the skinning kernel */
 #define HR_ERR_UNSUPPORTED (-5) /* sizes beyond what the context was created for */
+#define HR_ERR_INTERNAL (-6)    /* a kernel read an internal index out of range and skipped it */
 
 typedef void* hr_stream; /* a cudaStream_t */
 
@@ -89,7 +90,7 @@ typedef struct hr_render_opts {
     uint64_t seed;
     uint32_t iter;
     uint32_t instance;
-    int32_t spp;            /* primary samples per pixel (>= 1)                     */
+    int32_t spp;            /* primary samples per pixel, 1 .. 65536                */
     int32_t edge_samples;   /* silhouette-edge samples per view (>= 0)              */
     float ka, kd;
     float light_dir[3];
@@ -109,13 +110,15 @@ typedef struct hr_limits {
     int32_t max_F;      /* triangles (<= 8192: single-block BVH build)           */
     int32_t max_E;      /* edges                                                 */
     int32_t max_views;  /* views per call                                        */
-    int64_t max_pixels; /* N * H * W per call (loss scratch)                     */
+    int32_t max_width;  /* image width W per call                                */
+    int32_t max_height; /* image height H per call                               */
 } hr_limits;
 
 typedef struct hr_context hr_context;
 
 /* Create a context on the current CUDA device: device scratch for the given
- * limits, the BVH, vertex normals and the device status word.
+ * limits (the BVH, vertex normals, the render kernels' per-sub-tile candidate pool
+ * and work items, reduction partials) and the device status word.
  * Returns HR_ERR_ARG for non-positive or too large limits, HR_ERR_CUDA when an
  * allocation fails (nothing is leaked).  The context is owned by the caller. */
 int hr_context_create(const hr_limits* limits, hr_context** out);
@@ -195,14 +198,17 @@ int hr_silhouettes(hr_context* ctx, const hr_model* model, const float* verts, c
                    int32_t* lists, int32_t* counts, hr_stream stream);
 
 /* Work counters of the calls made with HR_STATS since the last read: synchronise
- * `stream`, copy 12 counters to host `out` and clear them.  out[0..3] = forward
- * (rays traced, BVH nodes visited, triangle tests, hits), out[4..7] = the interior
- * backward, out[8..11] = the edge-sample rays. */
+ * `stream`, copy 18 counters to host `out` and clear them.  out[0..5] = forward,
+ * out[6..11] = the interior backward, out[12..17] = the edge-sample rays, each
+ * (estimator samples resolved, rays made individually, BVH nodes visited,
+ * Moller-Trumbore tests, hits, candidate screen-box tests).  A sample is resolved
+ * without its own ray when its sub-tile's frustum misses the scene. */
 int hr_get_stats(hr_context* ctx, uint64_t* out, hr_stream stream);
 
 /* Synchronise `stream`, then return and clear the device status word: HR_OK, or the
  * HR_ERR_* code of a device-detected error since the last call (HR_ERR_ARG for face
- * or parent indices out of range, then HR_ERR_NONFINITE, then HR_ERR_LIMIT). */
+ * or parent indices out of range, then HR_ERR_INTERNAL, HR_ERR_NONFINITE,
+ * HR_ERR_LIMIT). */
 int hr_get_status(hr_context* ctx, hr_stream stream);
 
 /* Static text for a status code. */

@@ -23,6 +23,7 @@ HR_ERR_CUDA = -2
 HR_ERR_LIMIT = -3
 HR_ERR_NONFINITE = -4
 HR_ERR_UNSUPPORTED = -5
+HR_ERR_INTERNAL = -6
 HR_BWD_NO_INTERIOR = 1
 HR_BWD_NO_EDGES = 2
 HR_BWD_NO_NORMALS = 4
@@ -55,7 +56,7 @@ class hr_render_opts(ctypes.Structure):
 
 class hr_limits(ctypes.Structure):
     _fields_ = [("max_V", ctypes.c_int32), ("max_F", ctypes.c_int32), ("max_E", ctypes.c_int32),
-                ("max_views", ctypes.c_int32), ("max_pixels", ctypes.c_int64)]
+                ("max_views", ctypes.c_int32), ("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32)]
 
 
 _lib = None
@@ -131,8 +132,8 @@ def _f32(t):
 class Context:
     """An hr_context: device scratch, BVH and status word, sized by the limits."""
 
-    def __init__(self, max_V, max_F, max_E, max_views, max_pixels):
-        lim = hr_limits(max_V, max_F, max_E, max_views, max_pixels)
+    def __init__(self, max_V, max_F, max_E, max_views, max_width, max_height):
+        lim = hr_limits(max_V, max_F, max_E, max_views, max_width, max_height)
         h = ctypes.c_void_p()
         _check("hr_context_create", lib().hr_context_create(ctypes.byref(lim), ctypes.byref(h)))
         self.handle = h
@@ -253,11 +254,13 @@ def hr_silhouettes(ctx, model, verts, cams, lists, counts, stream=None):
 
 
 def hr_get_stats(ctx, stream=None):
-    """12 work counters (forward, interior backward, edge rays: rays, nodes, triangle
-    tests, hits) accumulated by calls made with HR_STATS; cleared on read."""
-    out = (ctypes.c_uint64 * 12)()
+    """Work counters [3][6] (forward, interior backward, edge rays) x (estimator
+    samples resolved, rays made individually, BVH nodes visited, Moller-Trumbore
+    tests, hits, candidate screen-box tests) accumulated by calls made with
+    HR_STATS; cleared on read."""
+    out = (ctypes.c_uint64 * 18)()
     _check("hr_get_stats", lib().hr_get_stats(ctx.handle, out, _stream(stream)))
-    return np.array(out[:], np.uint64).reshape(3, 4)
+    return np.array(out[:], np.uint64).reshape(3, 6)
 
 
 def hr_get_status(ctx, stream=None):

@@ -2,6 +2,7 @@
 // declared in include/handrt.h.  Every entry point returns an HR_* code and never
 // throws; device-side errors go to the context's status word.
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -13,7 +14,7 @@ using hr::Context;
 namespace {
 
 struct Alloc {
-  void** slots[32];
+  void** slots[40];
   int n = 0;
 };
 
@@ -32,7 +33,8 @@ bool dev_alloc(T** p, size_t count, Alloc& list) {
 void free_ctx(Context* c) {
   void* ptrs[] = {c->nodes, c->tris,          c->normals,      c->normal_len, c->partials,
                   c->dN,    c->dm,            c->sil,          c->sil_count,  c->loss_partials,
-                  c->counters, c->skin_partials, c->status, c->keys, c->parent, c->stats};
+                  c->counters, c->skin_partials, c->status, c->keys, c->parent, c->stats, c->tile_counters,
+                  c->pool_bb, c->pool_z, c->pool_rec, c->st_info, c->items, c->item_part, c->extra, c->work_ctr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -48,12 +50,11 @@ bool model_ok(const hr_model* m, const Context* c) {
 }
 
 bool opts_ok(const hr_render_opts* o) {
-  return o && o->spp >= 1 && o->spp <= (1 << 20) && o->edge_samples >= 0 && o->edge_eps_px > 0.0f;
+  return o && o->spp >= 1 && o->spp <= 65536 && o->edge_samples >= 0 && o->edge_eps_px > 0.0f;
 }
 
 bool image_ok(const Context* c, int N, int H, int W) {
-  return N >= 1 && H >= 1 && W >= 1 && N <= c->lim.max_views && W <= 65536 && H <= 65536 &&
-         (long long)H * W <= (1ll << 31) / 3 && (long long)N * H * W <= c->lim.max_pixels;
+  return N >= 1 && H >= 1 && W >= 1 && N <= c->lim.max_views && W <= c->lim.max_width && H <= c->lim.max_height;
 }
 
 }  // namespace
@@ -63,9 +64,12 @@ extern "C" {
 int hr_context_create(const hr_limits* lim, hr_context** out) {
   if (!lim || !out) return HR_ERR_ARG;
   *out = nullptr;
-  if (lim->max_V <= 0 || lim->max_F <= 0 || lim->max_E <= 0 || lim->max_views <= 0 || lim->max_pixels <= 0)
+  if (lim->max_V <= 0 || lim->max_F <= 0 || lim->max_E <= 0 || lim->max_views <= 0 || lim->max_width <= 0 ||
+      lim->max_height <= 0)
     return HR_ERR_ARG;
-  if (lim->max_V > 8192 || lim->max_F > 8192 || lim->max_views > 65535) return HR_ERR_UNSUPPORTED;
+  if (lim->max_V > 8192 || lim->max_F > 8192 || lim->max_views > 65535 || lim->max_width > 16384 ||
+      lim->max_height > 16384 || (long long)lim->max_views * lim->max_width * lim->max_height > (1ll << 31) / 3)
+    return HR_ERR_UNSUPPORTED;
   Context* c = new (std::nothrow) Context();
   if (!c) return HR_ERR_CUDA;
   std::memset(c, 0, sizeof(Context));
@@ -80,16 +84,24 @@ int hr_context_create(const hr_limits* lim, hr_context** out) {
   }
   Alloc a;
   const size_t V = lim->max_V, F = lim->max_F;
+  const size_t subtiles = (size_t)hr::subtiles_for(lim->max_views, lim->max_width, lim->max_height);
+  c->pool_cap = (int)std::min<size_t>((size_t)1 << 28, 16 * subtiles + 4096);
+  c->item_cap = (int)std::min<size_t>((size_t)1 << 26, 2 * subtiles + 1024);
   bool ok = dev_alloc(&c->nodes, F, a) && dev_alloc(&c->tris, 3 * F, a) && dev_alloc(&c->normals, 3 * V, a) &&
             dev_alloc(&c->normal_len, V, a) && dev_alloc(&c->partials, (size_t)c->render_blocks * 6 * V, a) &&
             dev_alloc(&c->dN, 3 * V, a) && dev_alloc(&c->dm, 3 * V, a) &&
             dev_alloc(&c->sil, (size_t)lim->max_views * lim->max_E, a) &&
             dev_alloc(&c->sil_count, (size_t)lim->max_views, a) &&
             dev_alloc(&c->loss_partials, (size_t)4 * hr::kLossBlocks + 8, a) && dev_alloc(&c->counters, 8, a) &&
-            dev_alloc(&c->skin_partials, (size_t)hr::kSkinBlocks * hr::kSkinAcc, a) && dev_alloc(&c->status, 1, a) && dev_alloc(&c->stats, 12, a);
+            dev_alloc(&c->skin_partials, (size_t)hr::kSkinBlocks * hr::kSkinAcc, a) && dev_alloc(&c->status, 1, a) && dev_alloc(&c->stats, 3 * hr::kStatsPer, a) &&
+            dev_alloc(&c->tile_counters, 4, a) && dev_alloc(&c->pool_bb, c->pool_cap, a) &&
+            dev_alloc(&c->pool_z, c->pool_cap, a) && dev_alloc(&c->pool_rec, c->pool_cap, a) &&
+            dev_alloc(&c->st_info, subtiles, a) && dev_alloc(&c->items, c->item_cap, a) &&
+            dev_alloc(&c->item_part, (size_t)c->item_cap * 32, a) && dev_alloc(&c->extra, 6 * V, a) &&
+            dev_alloc(&c->work_ctr, 4, a);
   if (ok) ok = cudaMemset(c->counters, 0, 8 * sizeof(unsigned)) == cudaSuccess &&
                cudaMemset(c->status, 0, sizeof(int)) == cudaSuccess &&
-               cudaMemset(c->stats, 0, 12 * sizeof(unsigned long long)) == cudaSuccess &&
+               cudaMemset(c->stats, 0, 3 * hr::kStatsPer * sizeof(unsigned long long)) == cudaSuccess &&
                cudaMemset(c->nodes, 0, F * sizeof(hr::Node)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -196,8 +208,9 @@ int hr_get_stats(hr_context* ctx, uint64_t* out, hr_stream stream) {
   if (!c || !out) return HR_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaStreamSynchronize(s) != cudaSuccess ||
-      cudaMemcpy(out, c->stats, 12 * sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemset(c->stats, 0, 12 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMemcpy(out, c->stats, 3 * hr::kStatsPer * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
+          cudaSuccess ||
+      cudaMemset(c->stats, 0, 3 * hr::kStatsPer * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     return HR_ERR_CUDA;
   }
@@ -219,6 +232,7 @@ int hr_get_status(hr_context* ctx, hr_stream stream) {
     return HR_ERR_CUDA;
   }
   if (host & hr::kStatusBadModel) return HR_ERR_ARG;
+  if (host & hr::kStatusIndex) return HR_ERR_INTERNAL;
   if (host & hr::kStatusNonfinite) return HR_ERR_NONFINITE;
   if (host & hr::kStatusLimit) return HR_ERR_LIMIT;
   return HR_OK;
@@ -232,6 +246,7 @@ const char* hr_status_string(int code) {
     case HR_ERR_LIMIT: return "device limit reached (BVH traversal stack)";
     case HR_ERR_NONFINITE: return "non-finite parameters";
     case HR_ERR_UNSUPPORTED: return "size beyond the context's limits";
+    case HR_ERR_INTERNAL: return "internal index out of range (access skipped)";
     default: return "unknown status";
   }
 }

@@ -18,6 +18,7 @@ constexpr int kStack = 64;          // BVH traversal stack entries per ray
 constexpr int kStatusLimit = 1;     // device status bits
 constexpr int kStatusNonfinite = 2;
 constexpr int kStatusBadModel = 4;  // a face or parent index out of range
+constexpr int kStatusIndex = 8;     // an internal index read from device memory out of range
 
 // ---------------------------------------------------------------------------------
 // BVH layout (binary LBVH, F-1 internal nodes, leaves = triangle records)
@@ -48,6 +49,17 @@ struct Context {
   // BVH build scratch
   unsigned long long* keys;  // [max_F]
   int* parent;               // [2 max_F]
+  // sub-tile candidate pool and work items of the render kernels
+  float4* pool_bb;       // [pool_cap]
+  float* pool_z;         // [pool_cap]
+  int* pool_rec;         // [pool_cap]
+  int pool_cap;
+  int2* st_info;         // [max_subtiles]
+  int4* items;           // [item_cap]
+  float4* item_part;     // [item_cap][32]
+  int item_cap;
+  float* extra;          // [max_V][6]
+  unsigned* work_ctr;    // [4]
   // backward scratch
   float* partials;       // [render_blocks][max_V][6]
   float* dN;             // [max_V][3]
@@ -56,15 +68,17 @@ struct Context {
   int* sil_count;        // [max_views]
   // loss scratch
   float* loss_partials;  // [kLossBlocks] + 2 scalars
-  unsigned int* counters;// [4] last-block counters
+  unsigned int* counters;// [8] last-block counters
+  unsigned int* tile_counters;  // [4] dynamic tile schedulers of the render kernels
   // skin scratch
   float* skin_partials;  // [kSkinBlocks][kSkinAcc]
   // status and work counters
   int* status;
-  unsigned long long* stats;  // [12]
+  unsigned long long* stats;  // [3][kStatsPer]
 };
 
 constexpr int kLossBlocks = 1024;
+constexpr int kStatsPer = 6;   // samples, rays, BVH nodes, triangle tests, hits, candidate box tests
 constexpr int kSkinBlocks = 64;
 constexpr int kSkinAcc = 16 * 12 + 10 + 3;   // dA_j (J=16 x 3x4), dbeta, dtau
 constexpr int kMaxJ = 16;

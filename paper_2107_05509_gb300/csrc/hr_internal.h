@@ -27,5 +27,6 @@ int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, f
 // per-device properties of the render kernels (persistent grid)
 int render_grid(int device, int* blocks, int* threads, int* num_sms);
 size_t render_bwd_smem(int V);
+int subtiles_for(int views, int W, int H);
 
 }  // namespace hr

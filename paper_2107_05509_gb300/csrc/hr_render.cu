@@ -2,19 +2,36 @@
 // with edge sampling for the visibility discontinuities (the renderer of Li et al.
 // 2018 that the paper builds on; Section 1 and Section 3.1).
 //
-//   k_render_fwd       persistent blocks over 16x8 pixel tiles; per sample: Philox
-//                      jitter -> primary ray -> LBVH traversal -> Moller-Trumbore ->
-//                      Lambertian shading; per pixel the sample mean.
-//   k_render_bwd       the same samples re-traced (no hit records are stored); at each
-//                      hit the derivative of the shaded value w.r.t. the triangle's
-//                      vertices (through the barycentrics at the fixed ray) and its
-//                      vertex normals, accumulated in shared memory per block and
-//                      written as one partial per block.
-//   k_reduce_partials  fixed-order sum of the per-block partials (deterministic).
-//   k_silhouettes      per view, the edges whose two faces face opposite ways as seen
-//                      from the camera (plus boundary edges), compacted in id order.
-//   k_edge_samples     the boundary term: samples on silhouette edges, f+ and f- by
-//                      two traced rays, mapped to vertices by the projection Jacobian.
+// Primary rays of a pinhole camera are coherent, so the forward and the interior
+// backward work on 8x4-pixel sub-tiles, one warp per sub-tile, in three steps:
+//
+//   k_gather       the warp traverses the LBVH once with the sub-tile's frustum
+//                  (breadth-first, one frontier node per lane) and collects the
+//                  leaf triangles it reaches -- the only ones any sample ray of the
+//                  sub-tile can hit -- with their screen boxes, sorted by their
+//                  nearest camera depth, into a candidate pool; the sub-tile is
+//                  split into 1-16 work items of consecutive samples (more for
+//                  sub-tiles with more candidates: a palm seen edge-on has over a
+//                  hundred), so no single warp holds up the launch.  Sub-tiles that
+//                  no ray can hit are finished here (forward: background).
+//   k_shade_fwd    warps take work items; each lane (pixel) makes its samples
+//                  (Philox jitter), runs the same float32 Moller-Trumbore test and
+//                  closest-hit rule as a per-ray traversal on the candidates whose
+//                  box contains the sample, in depth order, and stops when no lane
+//                  can still find a nearer hit; shades, and writes per-item sums.
+//   k_combine_fwd  sums each sub-tile's items in item order (deterministic).
+//   k_shade_bwd    the same samples re-traced (no hit records are kept between
+//                  the passes); every hit is differentiated at the fixed ray and the
+//                  gradient accumulated per triangle in registers, per block in
+//                  shared memory, and written as one partial per block.
+//   k_reduce_partials  fixed-order sum of the block partials.
+//
+// Per-ray LBVH traversal (trace) serves the edge-sample rays, the hr_trace entry
+// point and sub-tiles whose candidates exceed the pool.
+//   k_silhouettes  per view, edges whose faces face opposite ways from the camera
+//                  (plus boundary edges), compacted in edge order.
+//   k_edge_samples the boundary term: samples on silhouette edges, f+ and f- by
+//                  two traced rays, mapped to vertices by the projection Jacobian.
 //   k_normal_dm / k_normal_gather   adjoint of the area-weighted vertex normals.
 #include "hr_internal.h"
 
@@ -22,7 +39,24 @@ namespace hr {
 
 namespace {
 
-constexpr int kTileW = 16, kTileH = 8, kRenderThreads = kTileW * kTileH;
+constexpr int kRenderThreads = 128;   // 4 warps per block
+constexpr int kWarps = kRenderThreads / 32;
+constexpr int kBwdMinBlocks = 6;
+constexpr int kBlocksPerSm = 8;       // persistent grid; backward partials are sized for it
+static_assert(kBwdMinBlocks <= kBlocksPerSm, "backward partials are sized for kBlocksPerSm blocks per SM");
+constexpr int kSubW = 8, kSubH = 4;   // sub-tile; lane = pixel
+constexpr int kLeafCap = 512;         // candidates per sub-tile
+constexpr int kFrontCap = 64;         // breadth-first frontier per level
+constexpr int kMaxChunks = 16;        // work items per sub-tile
+
+// Self-check of an index read from device memory (BVH children, candidate records,
+// pool offsets, work items): out of range sets a status bit and the caller skips
+// the access.
+__device__ __forceinline__ bool in_range(int* status, long long i, long long lo, long long hi) {
+  if (i >= lo && i < hi) return true;
+  set_status(status, kStatusIndex);
+  return false;
+}
 
 struct Hit {
   int tri;
@@ -40,11 +74,23 @@ __device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, flo
   return tmin <= tmax;
 }
 
+// reciprocal for the slab tests only (never for a hit decision): the approximate
+// reciprocal is off by a couple of ulp, far inside the padding of the leaf boxes
 __device__ __forceinline__ float safe_inv(float d) {
-  return 1.0f / (fabsf(d) > 1e-20f ? d : copysignf(1e-20f, d));
+  return __fdividef(1.0f, fabsf(d) > 1e-20f ? d : copysignf(1e-20f, d));
 }
 
-__device__ __forceinline__ void isect(const float4* __restrict__ tris, int k, float3 o, float3 d, Hit& h) {
+// work counters of the statistics build (HR_STATS): estimator samples resolved,
+// rays made individually, BVH nodes visited, Moller-Trumbore tests, hits, candidate
+// screen-box tests
+struct Counts {
+  unsigned samples = 0, rays = 0, nodes = 0, tris = 0, hits = 0, cands = 0;
+};
+
+template <bool STATS>
+__device__ __forceinline__ void isect(const float4* __restrict__ tris, int k, float3 o, float3 d, Hit& h,
+                                      Counts& cnt) {
+  if (STATS) ++cnt.tris;
   float4 a = __ldg(&tris[3 * k]), b = __ldg(&tris[3 * k + 1]), c = __ldg(&tris[3 * k + 2]);
   float3 v0 = make_float3(a.x, a.y, a.z), e1 = make_float3(a.w, b.x, b.y), e2 = make_float3(b.z, b.w, c.x);
   int id = __float_as_int(c.y);
@@ -59,15 +105,9 @@ __device__ __forceinline__ void isect(const float4* __restrict__ tris, int k, fl
   }
 }
 
-// per-thread work counters of the statistics build (HR_STATS)
-struct Counts {
-  unsigned rays = 0, nodes = 0, tris = 0, hits = 0;
-};
-
-// closest hit against the LBVH (root = internal node 0); ties in t -> lower id
-// At most `max_visits` internal nodes are visited (each node of a well-formed tree is
-// visited at most once, so F-1 is never exceeded); past it the status records a
-// limit error and the ray returns what it has.
+// Closest hit against the LBVH (root = internal node 0); ties in t go to the lower
+// triangle id.  At most `max_visits` internal nodes are visited (a well-formed tree
+// never needs more than F - 1); past it the status records a limit error.
 template <bool STATS>
 __device__ Hit trace(const Node* __restrict__ nodes, const float4* __restrict__ tris, float3 o, float3 d,
                      int* status, Counts& cnt, int max_visits) {
@@ -89,13 +129,11 @@ __device__ Hit trace(const Node* __restrict__ nodes, const float4* __restrict__ 
     bool hl = slab(a.x, a.y, a.z, a.w, b.x, b.y, o, inv, h.t, tl);
     bool hrr = slab(b.z, b.w, c.x, c.y, c.z, c.w, o, inv, h.t, tr);
     if (hl && dd.x < 0) {
-      if (STATS) ++cnt.tris;
-      isect(tris, ~dd.x, o, d, h);
+      isect<STATS>(tris, ~dd.x, o, d, h, cnt);
       hl = false;
     }
     if (hrr && dd.y < 0) {
-      if (STATS) ++cnt.tris;
-      isect(tris, ~dd.y, o, d, h);
+      isect<STATS>(tris, ~dd.y, o, d, h, cnt);
       hrr = false;
     }
     if (hl && hrr) {
@@ -119,18 +157,14 @@ __device__ Hit trace(const Node* __restrict__ nodes, const float4* __restrict__ 
       node = stack[--sp];
     }
   }
-  if (STATS) {
-    ++cnt.rays;
-    cnt.hits += h.tri >= 0;
-  }
   return h;
 }
 
 template <bool STATS>
 __device__ __forceinline__ void flush_counts(const Counts& c, unsigned long long* out) {
   if (!STATS) return;
-  unsigned v[4] = {c.rays, c.nodes, c.tris, c.hits};
-  for (int k = 0; k < 4; ++k) {
+  unsigned v[kStatsPer] = {c.samples, c.rays, c.nodes, c.tris, c.hits, c.cands};
+  for (int k = 0; k < kStatsPer; ++k) {
     unsigned long long x = v[k];
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(out + k, x);
@@ -140,6 +174,20 @@ __device__ __forceinline__ void flush_counts(const Counts& c, unsigned long long
 struct Shading {
   float3 l, lrgb;
   float ka, kd;
+};
+
+// candidate pool and work items shared by the gather / shade / combine kernels
+struct Work {
+  float4* bb;      // [pool] screen box (x0, y0, x1, y1) of the candidate
+  float* z;        // [pool] nearest camera depth (sorted within a sub-tile)
+  int* rec;        // [pool] triangle record
+  int pool_cap;
+  int2* st;        // [sub-tiles] (pool offset, K): K = 0 no ray can hit, K < 0 per-ray traversal
+  int4* items;     // [items] (sub-tile, chunk, chunks, first item of the sub-tile)
+  int item_cap;
+  float4* part;    // [items][32] forward per-item sums (r, g, b, misses)
+  float* extra;    // [6V] backward contributions made outside the shading blocks
+  unsigned* ctr;   // [4] sub-tile counter, pool fill, item fill, item counter
 };
 
 struct RenderArgs {
@@ -157,7 +205,8 @@ struct RenderArgs {
   uint32_t iter4;    // iter << 4
   Shading sh;
   int* status;
-  int max_visits;   // F (internal nodes are F - 1)
+  int max_visits;    // F + 1
+  Work wk;
 };
 
 __device__ __forceinline__ float3 shade(const RenderArgs& a, const Hit& h) {
@@ -191,57 +240,21 @@ __device__ __forceinline__ void jitter(const RenderArgs& a, int view, int px, in
   u2 = u24(r.y);
 }
 
-// radiance through screen point (sx, sy); a miss returns background pixel (bx, by)
+// radiance through screen point (sx, sy) by per-ray traversal; a miss returns
+// background pixel (bx, by)
 template <bool STATS>
 __device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, int view, float sx, float sy, int bx,
                                            int by, Counts& cnt) {
   float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
   float3 d = primary_dir(cam, sx, sy);
+  if (STATS) {
+    ++cnt.samples;
+    ++cnt.rays;
+  }
   Hit h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
+  if (STATS) cnt.hits += h.tri >= 0;
   if (h.tri >= 0) return shade(a, h);
   return ld3(a.bg + 3 * (((size_t)view * a.H + by) * a.W + bx));
-}
-
-template <bool STATS>
-__global__ void __launch_bounds__(kRenderThreads) k_render_fwd(RenderArgs a, float* __restrict__ image,
-                                                               unsigned long long* stats) {
-  Counts cnt;
-  const int tx = (a.W + kTileW - 1) / kTileW, ty = (a.H + kTileH - 1) / kTileH;
-  const int per_view = tx * ty, total = a.N * per_view;
-  const float inv_spp = 1.0f / (float)a.spp;
-  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    int view = tile / per_view, rem = tile - view * per_view;
-    int py = (rem / tx) * kTileH + (threadIdx.x / kTileW);
-    int px = (rem % tx) * kTileW + (threadIdx.x % kTileW);
-    if (px >= a.W || py >= a.H) continue;
-    Cam cam = load_cam(a.cams, view);
-    float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
-    size_t pix = ((size_t)view * a.H + py) * a.W + px;
-    float3 acc = make_float3(0.0f, 0.0f, 0.0f);
-    int misses = 0;
-    for (int s = 0; s < a.spp; ++s) {
-      float u1, u2;
-      jitter(a, view, px, py, s, u1, u2);
-      float3 d = primary_dir(cam, __fadd_rn((float)px, u1), __fadd_rn((float)py, u2));
-      Hit h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
-      if (h.tri >= 0) {
-        float3 f = shade(a, h);
-        acc.x += f.x;
-        acc.y += f.y;
-        acc.z += f.z;
-      } else {
-        ++misses;
-      }
-    }
-    // misses contribute background * (misses / spp): a pixel whose samples all miss
-    // is exactly its background value
-    float fm = __fdiv_rn((float)misses, (float)a.spp);
-    float3 bgc = misses ? ld3(a.bg + 3 * pix) : make_float3(0.0f, 0.0f, 0.0f);
-    image[3 * pix] = acc.x * inv_spp + bgc.x * fm;
-    image[3 * pix + 1] = acc.y * inv_spp + bgc.y * fm;
-    image[3 * pix + 2] = acc.z * inv_spp + bgc.z * fm;
-  }
-  flush_counts<STATS>(cnt, stats);
 }
 
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
@@ -255,13 +268,241 @@ __device__ __forceinline__ void add3(float* dst, int i, float x, float y, float 
   atomicAdd(&dst[3 * i + 2], z);
 }
 
+// ---------------------------------------------------------------------------------
+// sub-tiles, frustum gathering
+// ---------------------------------------------------------------------------------
+struct SubTile {
+  int view, x0, y0;
+};
+
+__device__ __forceinline__ int subtile_count(const RenderArgs& a) {
+  return a.N * ((a.W + kSubW - 1) / kSubW) * ((a.H + kSubH - 1) / kSubH);
+}
+
+__device__ __forceinline__ SubTile subtile(const RenderArgs& a, int st) {
+  const int nsx = (a.W + kSubW - 1) / kSubW, nsy = (a.H + kSubH - 1) / kSubH;
+  SubTile t;
+  t.view = st / (nsx * nsy);
+  int rem = st - t.view * nsx * nsy;
+  t.x0 = (rem % nsx) * kSubW;
+  t.y0 = (rem / nsx) * kSubH;
+  return t;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
+
+__device__ __forceinline__ int warp_append(bool want, int value, int* arr, int count, int cap, bool& ovf) {
+  unsigned b = __ballot_sync(0xffffffffu, want);
+  int idx = count + __popc(b & lanemask_lt());
+  if (want && idx < cap) arr[idx] = value;
+  int n = count + __popc(b);
+  if (n > cap) ovf = true;
+  return n;
+}
+
+__device__ __forceinline__ bool box_in_frustum(const float4* pl, float lx, float ly, float lz, float hx, float hy,
+                                               float hz) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    float4 p = pl[i];
+    float x = p.x >= 0.0f ? hx : lx, y = p.y >= 0.0f ? hy : ly, z = p.z >= 0.0f ? hz : lz;
+    if (p.x * x + p.y * y + p.z * z < p.w) return false;
+  }
+  return true;
+}
+
+struct GatherSmem {        // per warp
+  int leaf[kLeafCap];
+  float key[kLeafCap];
+  int idx[kLeafCap];
+  int front[2][kFrontCap];
+  float4 pl[5];
+};
+
+// screen box (padded by half a pixel; unbounded if a vertex is not in front of the
+// camera) and nearest camera depth of triangle record k
+__device__ __forceinline__ void project_record(const RenderArgs& a, const Cam& cam, int k, float4& bb, float& zmin) {
+  float4 t0 = __ldg(&a.tris[3 * k]), t1 = __ldg(&a.tris[3 * k + 1]), t2 = __ldg(&a.tris[3 * k + 2]);
+  float3 v[3] = {make_float3(t0.x, t0.y, t0.z), make_float3(t0.x + t0.w, t0.y + t1.x, t0.z + t1.y),
+                 make_float3(t0.x + t1.z, t0.y + t1.w, t0.z + t2.x)};
+  float bx0 = INFINITY, by0 = INFINITY, bx1 = -INFINITY, by1 = -INFINITY;
+  zmin = INFINITY;
+  bool front = true;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    float X = cam.R[0] * v[m].x + cam.R[1] * v[m].y + cam.R[2] * v[m].z + cam.t[0];
+    float Y = cam.R[3] * v[m].x + cam.R[4] * v[m].y + cam.R[5] * v[m].z + cam.t[1];
+    float Z = cam.R[6] * v[m].x + cam.R[7] * v[m].y + cam.R[8] * v[m].z + cam.t[2];
+    zmin = fminf(zmin, Z);
+    front = front && Z > 1e-4f;
+    float iz = 1.0f / Z;
+    float sx = cam.fx * X * iz + cam.cx, sy = cam.fy * Y * iz + cam.cy;
+    bx0 = fminf(bx0, sx);
+    bx1 = fmaxf(bx1, sx);
+    by0 = fminf(by0, sy);
+    by1 = fmaxf(by1, sy);
+  }
+  if (front) {
+    bb = make_float4(bx0 - 0.5f, by0 - 0.5f, bx1 + 0.5f, by1 + 0.5f);
+  } else {
+    bb = make_float4(-INFINITY, -INFINITY, INFINITY, INFINITY);
+    zmin = -INFINITY;
+  }
+}
+
+// Frustum traversal for the sub-tile with pixels [x0, x0+8) x [y0, y0+4): the four
+// planes through the camera centre and the rectangle padded by half a pixel, and
+// the camera's forward plane.  Leaves into gs.leaf; returns their count, or -1 when
+// the sub-tile needs more than kLeafCap candidates or kFrontCap frontier nodes.
+template <bool STATS>
+__device__ int frustum_leaves(const RenderArgs& a, const Cam& cam, int x0, int y0, GatherSmem& gs, Counts& cnt) {
+  const int lane = threadIdx.x & 31;
+  if (lane < 5) {
+    float ax = __fdividef((float)x0 - 0.5f - cam.cx, cam.fx);
+    float bx = __fdividef((float)(x0 + kSubW) + 0.5f - cam.cx, cam.fx);
+    float ay = __fdividef((float)y0 - 0.5f - cam.cy, cam.fy);
+    float by = __fdividef((float)(y0 + kSubH) + 0.5f - cam.cy, cam.fy);
+    float3 nc = lane == 0   ? make_float3(1.0f, 0.0f, -ax)
+                : lane == 1 ? make_float3(-1.0f, 0.0f, bx)
+                : lane == 2 ? make_float3(0.0f, 1.0f, -ay)
+                : lane == 3 ? make_float3(0.0f, -1.0f, by)
+                            : make_float3(0.0f, 0.0f, 1.0f);
+    float3 nw = make_float3(cam.R[0] * nc.x + cam.R[3] * nc.y + cam.R[6] * nc.z,
+                            cam.R[1] * nc.x + cam.R[4] * nc.y + cam.R[7] * nc.z,
+                            cam.R[2] * nc.x + cam.R[5] * nc.y + cam.R[8] * nc.z);
+    gs.pl[lane] = make_float4(nw.x, nw.y, nw.z, nw.x * cam.c[0] + nw.y * cam.c[1] + nw.z * cam.c[2]);
+  }
+  if (lane == 0) gs.front[0][0] = 0;
+  __syncwarp();
+  int n = 1, cur = 0, K = 0, levels = 0;
+  bool ovf = false;
+  while (n > 0 && !ovf) {
+    int nn = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + lane;
+      bool kl = false, kr = false;
+      int cl = 0, cr = 0;
+      if (i < n) {
+        int node = gs.front[cur][i];
+        if (!in_range(a.status, node, 0, a.max_visits)) node = 0;
+        const float4* np = reinterpret_cast<const float4*>(a.nodes + node);
+        float4 p = __ldg(np), q = __ldg(np + 1), r = __ldg(np + 2);
+        int4 dd = __ldg(reinterpret_cast<const int4*>(np + 3));
+        if (STATS) ++cnt.nodes;
+        kl = box_in_frustum(gs.pl, p.x, p.y, p.z, p.w, q.x, q.y);
+        kr = box_in_frustum(gs.pl, q.z, q.w, r.x, r.y, r.z, r.w);
+        cl = dd.x;
+        cr = dd.y;
+        if (cl == cr) kr = false;   // a one-triangle tree stores its leaf twice
+      }
+      nn = warp_append(kl && cl >= 0, cl, gs.front[cur ^ 1], nn, kFrontCap, ovf);
+      nn = warp_append(kr && cr >= 0, cr, gs.front[cur ^ 1], nn, kFrontCap, ovf);
+      K = warp_append(kl && cl < 0, ~cl, gs.leaf, K, kLeafCap, ovf);
+      K = warp_append(kr && cr < 0, ~cr, gs.leaf, K, kLeafCap, ovf);
+    }
+    __syncwarp();
+    cur ^= 1;
+    n = nn;
+    if (++levels > a.max_visits) {   // deeper than any well-formed tree: report and stop
+      if (lane == 0) set_status(a.status, kStatusLimit);
+      ovf = true;
+    }
+  }
+  return ovf ? -1 : K;
+}
+
+__device__ __forceinline__ int chunks_for(int K, int spp) {
+  int c = K < 0 ? kMaxChunks : K / 16;
+  return max(1, min(min(c, kMaxChunks), spp));
+}
+
+// closest hit of the primary ray through (sx, sy) among the K pool candidates at
+// `off`; `live` lanes take part, the others only vote
+template <bool STATS>
+__device__ __forceinline__ Hit closest_candidate(const RenderArgs& a, int off, int K, bool live, float sx, float sy,
+                                                 float3 o, float3 d, Counts& cnt) {
+  Hit h{-1, INFINITY, 0.0f, 0.0f};
+  for (int c = 0; c < K; ++c) {
+    if (!in_range(a.status, off + c, 0, a.wk.pool_cap)) break;
+    const float zm = __ldg(&a.wk.z[off + c]);
+    // no remaining candidate can be nearer than this lane's hit (t >= its depth)
+    const bool done = !live || h.t < zm - (1e-4f * fabsf(zm) + 1e-6f);
+    if (__all_sync(0xffffffffu, done)) break;
+    if (done) continue;
+    const float4 bb = __ldg(&a.wk.bb[off + c]);
+    if (STATS) ++cnt.cands;
+    if (sx >= bb.x && sx <= bb.z && sy >= bb.y && sy <= bb.w) {
+      const int k = __ldg(&a.wk.rec[off + c]);
+      if (in_range(a.status, k, 0, a.max_visits - 1)) isect<STATS>(a.tris, k, o, d, h, cnt);
+    }
+  }
+  return h;
+}
+
+// Radiance sums of samples [s0, s1) of this lane's pixel (all lanes call it).
+template <bool STATS>
+__device__ __forceinline__ void shade_samples(const RenderArgs& a, const SubTile& t, const Cam& cam, int off, int K,
+                                              int s0, int s1, float3& acc, int& misses, Counts& cnt) {
+  const int lane = threadIdx.x & 31;
+  const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
+  const bool valid = px < a.W && py < a.H;
+  const float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
+  for (int s = s0; s < s1; ++s) {
+    float sx = 0.0f, sy = 0.0f;
+    if (valid) {
+      float u1, u2;
+      jitter(a, t.view, px, py, s, u1, u2);
+      sx = __fadd_rn((float)px, u1);
+      sy = __fadd_rn((float)py, u2);
+      if (STATS) {
+        ++cnt.samples;
+        ++cnt.rays;
+      }
+    }
+    const float3 d = primary_dir(cam, sx, sy);
+    Hit h{-1, INFINITY, 0.0f, 0.0f};
+    if (K > 0)
+      h = closest_candidate<STATS>(a, off, K, valid, sx, sy, o, d, cnt);
+    else if (valid)
+      h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
+    if (h.tri >= 0) {
+      if (STATS) ++cnt.hits;
+      float3 f = shade(a, h);
+      acc.x += f.x;
+      acc.y += f.y;
+      acc.z += f.z;
+    } else {
+      ++misses;
+    }
+  }
+}
+
+__device__ __forceinline__ void write_pixel(const RenderArgs& a, const SubTile& t, float3 acc, int misses,
+                                            float* __restrict__ image) {
+  const int lane = threadIdx.x & 31;
+  const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
+  if (px >= a.W || py >= a.H) return;
+  // misses contribute background * (misses / spp): a pixel whose samples all miss is
+  // exactly its background value
+  const size_t pix = ((size_t)t.view * a.H + py) * a.W + px;
+  const float fm = __fdiv_rn((float)misses, (float)a.spp);
+  const float inv_spp = 1.0f / (float)a.spp;
+  float3 bgc = misses ? ld3(a.bg + 3 * pix) : make_float3(0.0f, 0.0f, 0.0f);
+  image[3 * pix] = acc.x * inv_spp + bgc.x * fm;
+  image[3 * pix + 1] = acc.y * inv_spp + bgc.y * fm;
+  image[3 * pix + 2] = acc.z * inv_spp + bgc.z * fm;
+}
+
 // dL/dverts (through u, v at the fixed ray) and dL/dnormals of one shaded hit with
-// upstream g = dL/df, accumulated into shared sdV = [V][3], sdN = [V][3]
-__device__ __forceinline__ void hit_grad(const RenderArgs& a, const Hit& h, float3 o, float3 d, float3 g,
-                                         float* sdV, float* sdN) {
-  int i0 = __ldg(&a.faces[3 * h.tri]), i1 = __ldg(&a.faces[3 * h.tri + 1]), i2 = __ldg(&a.faces[3 * h.tri + 2]);
-  float3 n0 = ld3(a.normals + 3 * i0), n1 = ld3(a.normals + 3 * i1), n2 = ld3(a.normals + 3 * i2);
-  float3 a0 = ld3(a.albedo + 3 * i0), a1 = ld3(a.albedo + 3 * i1), a2 = ld3(a.albedo + 3 * i2);
+// upstream g = dL/df: dv[0..8] = dL/d(v0, v1, v2), dn[0..8] = dL/d(n0, n1, n2)
+struct HitGrad {
+  float dv[9], dn[9];
+};
+
+__device__ __forceinline__ void hit_grad(const RenderArgs& a, const Hit& h, const int3 f, float3 o, float3 d,
+                                         float3 g, HitGrad& out) {
+  float3 n0 = ld3(a.normals + 3 * f.x), n1 = ld3(a.normals + 3 * f.y), n2 = ld3(a.normals + 3 * f.z);
+  float3 a0 = ld3(a.albedo + 3 * f.x), a1 = ld3(a.albedo + 3 * f.y), a2 = ld3(a.albedo + 3 * f.z);
   const float u = h.u, v = h.v, w = 1.0f - u - v;
   float3 nm = interp_normal(u, v, n0, n1, n2);
   bool lit = ddot(nm, a.sh.l) > 0.0f;
@@ -270,86 +511,346 @@ __device__ __forceinline__ void hit_grad(const RenderArgs& a, const Hit& h, floa
   float sigma = lit ? dot3(nh, a.sh.l) : 0.0f;
   float k = a.sh.ka + a.sh.kd * sigma;
   float3 dalb = make_float3(g.x * a.sh.lrgb.x * k, g.y * a.sh.lrgb.y * k, g.z * a.sh.lrgb.z * k);
-  float3 alb = make_float3(w * a0.x + u * a1.x + v * a2.x, w * a0.y + u * a1.y + v * a2.y,
-                           w * a0.z + u * a1.z + v * a2.z);
   float gu = dalb.x * (a1.x - a0.x) + dalb.y * (a1.y - a0.y) + dalb.z * (a1.z - a0.z);
   float gv = dalb.x * (a2.x - a0.x) + dalb.y * (a2.y - a0.y) + dalb.z * (a2.z - a0.z);
+  float3 dnm = make_float3(0.0f, 0.0f, 0.0f);
   if (lit) {
+    float3 alb = make_float3(w * a0.x + u * a1.x + v * a2.x, w * a0.y + u * a1.y + v * a2.y,
+                             w * a0.z + u * a1.z + v * a2.z);
     float dsig = a.sh.kd * (g.x * alb.x * a.sh.lrgb.x + g.y * alb.y * a.sh.lrgb.y + g.z * alb.z * a.sh.lrgb.z);
     float3 dnh = make_float3(dsig * a.sh.l.x, dsig * a.sh.l.y, dsig * a.sh.l.z);
     float pr = dot3(nh, dnh);
-    float3 dnm = make_float3((dnh.x - nh.x * pr) * inv_len, (dnh.y - nh.y * pr) * inv_len,
-                             (dnh.z - nh.z * pr) * inv_len);
+    dnm = make_float3((dnh.x - nh.x * pr) * inv_len, (dnh.y - nh.y * pr) * inv_len, (dnh.z - nh.z * pr) * inv_len);
     gu += dnm.x * (n1.x - n0.x) + dnm.y * (n1.y - n0.y) + dnm.z * (n1.z - n0.z);
     gv += dnm.x * (n2.x - n0.x) + dnm.y * (n2.y - n0.y) + dnm.z * (n2.z - n0.z);
-    add3(sdN, i0, w * dnm.x, w * dnm.y, w * dnm.z);
-    add3(sdN, i1, u * dnm.x, u * dnm.y, u * dnm.z);
-    add3(sdN, i2, v * dnm.x, v * dnm.y, v * dnm.z);
   }
+  out.dn[0] = w * dnm.x; out.dn[1] = w * dnm.y; out.dn[2] = w * dnm.z;
+  out.dn[3] = u * dnm.x; out.dn[4] = u * dnm.y; out.dn[5] = u * dnm.z;
+  out.dn[6] = v * dnm.x; out.dn[7] = v * dnm.y; out.dn[8] = v * dnm.z;
   // barycentrics at the fixed ray: u = [s,d,e2]/D, v = [d,s,e1]/D, D = [e1,d,e2]
-  float3 p0 = ld3(a.verts + 3 * i0), p1 = ld3(a.verts + 3 * i1), p2 = ld3(a.verts + 3 * i2);
+  float3 p0 = ld3(a.verts + 3 * f.x), p1 = ld3(a.verts + 3 * f.y), p2 = ld3(a.verts + 3 * f.z);
   float3 s = make_float3(o.x - p0.x, o.y - p0.y, o.z - p0.z);
   float3 e1 = make_float3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z);
   float3 e2 = make_float3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z);
   float3 dxe2 = cross3(d, e2), e1xd = cross3(e1, d), dxs = cross3(d, s);
   float invD = 1.0f / dot3(e1, dxe2);
   float uv = gu * u + gv * v;
-  float3 gs = make_float3((gu * dxe2.x + gv * e1xd.x) * invD, (gu * dxe2.y + gv * e1xd.y) * invD,
-                          (gu * dxe2.z + gv * e1xd.z) * invD);
-  float3 ge1 = make_float3((gv * dxs.x - uv * dxe2.x) * invD, (gv * dxs.y - uv * dxe2.y) * invD,
-                           (gv * dxs.z - uv * dxe2.z) * invD);
-  float3 ge2 = make_float3((-gu * dxs.x - uv * e1xd.x) * invD, (-gu * dxs.y - uv * e1xd.y) * invD,
-                           (-gu * dxs.z - uv * e1xd.z) * invD);
-  add3(sdV, i1, ge1.x, ge1.y, ge1.z);
-  add3(sdV, i2, ge2.x, ge2.y, ge2.z);
-  add3(sdV, i0, -(gs.x + ge1.x + ge2.x), -(gs.y + ge1.y + ge2.y), -(gs.z + ge1.z + ge2.z));
+  float gs[3] = {(gu * dxe2.x + gv * e1xd.x) * invD, (gu * dxe2.y + gv * e1xd.y) * invD,
+                 (gu * dxe2.z + gv * e1xd.z) * invD};
+  float ge1[3] = {(gv * dxs.x - uv * dxe2.x) * invD, (gv * dxs.y - uv * dxe2.y) * invD,
+                  (gv * dxs.z - uv * dxe2.z) * invD};
+  float ge2[3] = {(-gu * dxs.x - uv * e1xd.x) * invD, (-gu * dxs.y - uv * e1xd.y) * invD,
+                  (-gu * dxs.z - uv * e1xd.z) * invD};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    out.dv[c] = -(gs[c] + ge1[c] + ge2[c]);
+    out.dv[3 + c] = ge1[c];
+    out.dv[6 + c] = ge2[c];
+  }
 }
 
-// interior term; shared memory: sdV [V][3] then sdN [V][3]; one partial per block
+__device__ __forceinline__ void flush_tri(int3 f, const HitGrad& acc, float* dV, float* dN) {
+  add3(dV, f.x, acc.dv[0], acc.dv[1], acc.dv[2]);
+  add3(dV, f.y, acc.dv[3], acc.dv[4], acc.dv[5]);
+  add3(dV, f.z, acc.dv[6], acc.dv[7], acc.dv[8]);
+  add3(dN, f.x, acc.dn[0], acc.dn[1], acc.dn[2]);
+  add3(dN, f.y, acc.dn[3], acc.dn[4], acc.dn[5]);
+  add3(dN, f.z, acc.dn[6], acc.dn[7], acc.dn[8]);
+}
+
+// Gradient of samples [s0, s1) of this lane's pixel (upstream g, `live` lanes only;
+// all lanes call it), added to dV [V][3] / dN [V][3] per run of hits on one triangle.
 template <bool STATS>
-__global__ void __launch_bounds__(kRenderThreads) k_render_bwd(RenderArgs a, const float* __restrict__ adjoint,
-                                                               float* __restrict__ partials,
-                                                               unsigned long long* stats) {
-  extern __shared__ float sacc[];
+__device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile& t, const Cam& cam, int off, int K,
+                                             int s0, int s1, bool live, float3 g, float* dV, float* dN, Counts& cnt) {
+  const int lane = threadIdx.x & 31;
+  const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
+  const float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
+  int cur = -1;
+  int3 cf = make_int3(0, 0, 0);
+  HitGrad acc;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc.dv[c] = acc.dn[c] = 0.0f;
+  for (int s = s0; s < s1; ++s) {
+    float sx = 0.0f, sy = 0.0f;
+    if (live) {
+      float u1, u2;
+      jitter(a, t.view, px, py, s, u1, u2);
+      sx = __fadd_rn((float)px, u1);
+      sy = __fadd_rn((float)py, u2);
+      if (STATS) {
+        ++cnt.samples;
+        ++cnt.rays;
+      }
+    }
+    const float3 d = primary_dir(cam, sx, sy);
+    Hit h{-1, INFINITY, 0.0f, 0.0f};
+    if (K > 0)
+      h = closest_candidate<STATS>(a, off, K, live, sx, sy, o, d, cnt);
+    else if (live)
+      h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
+    if (h.tri < 0) continue;
+    if (STATS) ++cnt.hits;
+    if (h.tri != cur) {
+      if (cur >= 0) {
+        flush_tri(cf, acc, dV, dN);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc.dv[c] = acc.dn[c] = 0.0f;
+      }
+      cur = h.tri;
+      cf = make_int3(__ldg(&a.faces[3 * cur]), __ldg(&a.faces[3 * cur + 1]), __ldg(&a.faces[3 * cur + 2]));
+    }
+    HitGrad hg;
+    hit_grad(a, h, cf, o, d, g, hg);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      acc.dv[c] += hg.dv[c];
+      acc.dn[c] += hg.dn[c];
+    }
+  }
+  if (cur >= 0) flush_tri(cf, acc, dV, dN);
+}
+
+// this lane's upstream gradient dL/df / spp; `live` = non-zero adjoint
+__device__ __forceinline__ float3 lane_adjoint(const RenderArgs& a, const SubTile& t, const float* __restrict__ adjoint,
+                                               bool& live) {
+  const int lane = threadIdx.x & 31;
+  const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
+  live = false;
+  if (px >= a.W || py >= a.H) return make_float3(0.0f, 0.0f, 0.0f);
+  float3 g = ld3(adjoint + 3 * (((size_t)t.view * a.H + py) * a.W + px));
+  live = g.x != 0.0f || g.y != 0.0f || g.z != 0.0f;
+  const float inv_spp = 1.0f / (float)a.spp;
+  return make_float3(g.x * inv_spp, g.y * inv_spp, g.z * inv_spp);
+}
+
+// One warp per sub-tile: candidates into the pool, work items for the sub-tile.
+// BWD: only sub-tiles with a non-zero adjoint; their zero-candidate case has no
+// gradient.  FWD: zero-candidate sub-tiles are written (background) here.  When the
+// pool or the item table is full the warp does the sub-tile's work itself.
+template <bool BWD, bool STATS>
+__global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a, const float* __restrict__ adjoint,
+                                                          float* __restrict__ image, unsigned long long* stats) {
+  __shared__ GatherSmem gsm[kWarps];
+  GatherSmem& gs = gsm[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
   Counts cnt;
+  const int total = subtile_count(a);
+  for (;;) {
+    int st = 0;
+    if (lane == 0) st = (int)atomicAdd(&a.wk.ctr[0], 1u);
+    st = __shfl_sync(0xffffffffu, st, 0);
+    if (st >= total) break;
+    const SubTile t = subtile(a, st);
+    bool live = true;
+    float3 g = make_float3(0.0f, 0.0f, 0.0f);
+    if (BWD) {
+      g = lane_adjoint(a, t, adjoint, live);
+      if (!__any_sync(0xffffffffu, live)) {
+        if (lane == 0) a.wk.st[st] = make_int2(0, 0);
+        continue;
+      }
+    }
+    const Cam cam = load_cam(a.cams, t.view);
+    int K = frustum_leaves<STATS>(a, cam, t.x0, t.y0, gs, cnt);
+    if (K == 0) {
+      if (lane == 0) a.wk.st[st] = make_int2(0, 0);
+      const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
+      const bool valid = px < a.W && py < a.H && live;
+      if (STATS && valid) cnt.samples += a.spp;   // resolved by the frustum test
+      if (!BWD) write_pixel(a, t, make_float3(0.0f, 0.0f, 0.0f), a.spp, image);
+      continue;
+    }
+    int off = 0;
+    if (K > 0) {
+      // sort the candidates by nearest depth (bitonic, padded with +inf)
+      for (int j = lane; j < K; j += 32) {
+        float4 bb;
+        float zm;
+        int k = gs.leaf[j];
+        if (!in_range(a.status, k, 0, a.max_visits - 1)) k = 0;
+        gs.leaf[j] = k;
+        project_record(a, cam, k, bb, zm);
+        gs.key[j] = zm;
+        gs.idx[j] = j;
+      }
+      int P = 1;
+      while (P < K) P <<= 1;
+      for (int j = K + lane; j < P; j += 32) {
+        gs.key[j] = INFINITY;
+        gs.idx[j] = 0;
+      }
+      __syncwarp();
+      for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = lane; i < P; i += 32) {
+            int ixj = i ^ j;
+            if (ixj > i) {
+              float zi = gs.key[i], zj = gs.key[ixj];
+              bool up = (i & k) == 0;
+              if ((zi > zj) == up) {
+                gs.key[i] = zj;
+                gs.key[ixj] = zi;
+                int q = gs.idx[i];
+                gs.idx[i] = gs.idx[ixj];
+                gs.idx[ixj] = q;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+      if (lane == 0) off = (int)atomicAdd(&a.wk.ctr[1], (unsigned)K);
+      off = __shfl_sync(0xffffffffu, off, 0);
+      if (off + K <= a.wk.pool_cap) {
+        for (int c = lane; c < K; c += 32) {
+          int j = gs.idx[c];
+          if (!in_range(a.status, j, 0, K)) j = 0;
+          const int k = gs.leaf[j];
+          float4 bb;
+          float zm;
+          project_record(a, cam, k, bb, zm);
+          a.wk.bb[off + c] = bb;
+          a.wk.z[off + c] = zm;
+          a.wk.rec[off + c] = k;
+        }
+      } else {
+        K = -1;   // pool full: per-ray traversal for this sub-tile
+      }
+    }
+    const int C = chunks_for(K, a.spp);
+    int first = 0;
+    if (lane == 0) first = (int)atomicAdd(&a.wk.ctr[2], (unsigned)C);
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (lane == 0) a.wk.st[st] = make_int2(off, K);
+    if (first + C <= a.wk.item_cap) {
+      for (int c = lane; c < C; c += 32) a.wk.items[first + c] = make_int4(st, c, C, first);
+    } else {
+      // item table full: blank the reserved slots that exist, and this warp does
+      // the whole sub-tile itself
+      for (int c = lane; c < C; c += 32)
+        if (first + c < a.wk.item_cap) a.wk.items[first + c] = make_int4(-1, 0, 0, 0);
+      __threadfence_block();
+      if (BWD) {
+        grad_samples<STATS>(a, t, cam, off, K, 0, a.spp, live, g, a.wk.extra, a.wk.extra + 3 * a.V, cnt);
+      } else {
+        float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+        int misses = 0;
+        shade_samples<STATS>(a, t, cam, off, K, 0, a.spp, acc, misses, cnt);
+        write_pixel(a, t, acc, misses, image);
+      }
+    }
+    __syncwarp();
+  }
+  flush_counts<STATS>(cnt, stats);
+}
+
+__device__ __forceinline__ int item_count(const RenderArgs& a) {
+  return (int)min(*reinterpret_cast<volatile unsigned*>(&a.wk.ctr[2]), (unsigned)a.wk.item_cap);
+}
+
+__device__ __forceinline__ void item_samples(int c, int C, int spp, int& s0, int& s1) {
+  s0 = (int)((long long)c * spp / C);
+  s1 = (int)((long long)(c + 1) * spp / C);
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a, unsigned long long* stats) {
+  const int lane = threadIdx.x & 31;
+  Counts cnt;
+  const int n = item_count(a);
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = (int)atomicAdd(&a.wk.ctr[3], 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n) break;
+    const int4 item = a.wk.items[it];
+    if (item.x < 0) continue;   // a blanked slot
+    if (!in_range(a.status, item.x, 0, subtile_count(a))) continue;
+    const SubTile t = subtile(a, item.x);
+    int2 pk = a.wk.st[item.x];
+    if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
+    const Cam cam = load_cam(a.cams, t.view);
+    int s0, s1;
+    item_samples(item.y, item.z, a.spp, s0, s1);
+    float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+    int misses = 0;
+    shade_samples<STATS>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
+    a.wk.part[(size_t)it * 32 + lane] = make_float4(acc.x, acc.y, acc.z, (float)misses);
+  }
+  flush_counts<STATS>(cnt, stats);
+}
+
+// one warp per sub-tile with items: its item sums in item order, then the pixel
+__global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, float* __restrict__ image) {
+  const int lane = threadIdx.x & 31;
+  const int n = item_count(a);
+  const int nw = gridDim.x * kWarps;
+  for (int it = blockIdx.x * kWarps + (threadIdx.x >> 5); it < n; it += nw) {
+    const int4 item = a.wk.items[it];
+    if (item.x < 0 || item.y != 0) continue;
+    if (!in_range(a.status, item.x, 0, subtile_count(a)) ||
+        !in_range(a.status, (long long)item.w + item.z - 1, 0, a.wk.item_cap))
+      continue;
+    float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+    float misses = 0.0f;
+    for (int c = 0; c < item.z; ++c) {
+      float4 p = a.wk.part[(size_t)(item.w + c) * 32 + lane];
+      acc.x += p.x;
+      acc.y += p.y;
+      acc.z += p.z;
+      misses += p.w;
+    }
+    write_pixel(a, subtile(a, item.x), acc, (int)misses, image);
+  }
+}
+
+// interior term: warps take work items; the block accumulates dV/dN in shared
+// memory (sdV [V][3], sdN [V][3]) and writes one partial per block
+template <bool STATS>
+__global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(RenderArgs a,
+                                                                             const float* __restrict__ adjoint,
+                                                                             float* __restrict__ partials,
+                                                                             unsigned long long* stats) {
+  extern __shared__ float sacc[];
   float* sdV = sacc;
   float* sdN = sacc + 3 * a.V;
-  for (int i = threadIdx.x; i < 6 * a.V; i += blockDim.x) sacc[i] = 0.0f;
+  const int lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < 6 * a.V; i += kRenderThreads) sacc[i] = 0.0f;
   __syncthreads();
-  const int tx = (a.W + kTileW - 1) / kTileW, ty = (a.H + kTileH - 1) / kTileH;
-  const int per_view = tx * ty, total = a.N * per_view;
-  const float inv_spp = 1.0f / (float)a.spp;
-  for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    int view = tile / per_view, rem = tile - view * per_view;
-    int py = (rem / tx) * kTileH + (threadIdx.x / kTileW);
-    int px = (rem % tx) * kTileW + (threadIdx.x % kTileW);
-    if (px >= a.W || py >= a.H) continue;
-    size_t pix = ((size_t)view * a.H + py) * a.W + px;
-    float3 A = ld3(adjoint + 3 * pix);
-    if (A.x == 0.0f && A.y == 0.0f && A.z == 0.0f) continue;
-    float3 g = make_float3(A.x * inv_spp, A.y * inv_spp, A.z * inv_spp);
-    Cam cam = load_cam(a.cams, view);
-    float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
-    for (int s = 0; s < a.spp; ++s) {
-      float u1, u2;
-      jitter(a, view, px, py, s, u1, u2);
-      float3 d = primary_dir(cam, __fadd_rn((float)px, u1), __fadd_rn((float)py, u2));
-      Hit h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
-      if (h.tri >= 0) hit_grad(a, h, o, d, g, sdV, sdN);
-    }
+  Counts cnt;
+  const int n = item_count(a);
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = (int)atomicAdd(&a.wk.ctr[3], 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n) break;
+    const int4 item = a.wk.items[it];
+    if (item.x < 0) continue;   // a blanked slot
+    if (!in_range(a.status, item.x, 0, subtile_count(a))) continue;
+    const SubTile t = subtile(a, item.x);
+    int2 pk = a.wk.st[item.x];
+    if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
+    bool live;
+    const float3 g = lane_adjoint(a, t, adjoint, live);
+    const Cam cam = load_cam(a.cams, t.view);
+    int s0, s1;
+    item_samples(item.y, item.z, a.spp, s0, s1);
+    grad_samples<STATS>(a, t, cam, pk.x, pk.y, s0, s1, live, g, sdV, sdN, cnt);
   }
   flush_counts<STATS>(cnt, stats);
   __syncthreads();
   float* out = partials + (size_t)blockIdx.x * 6 * a.V;
-  for (int i = threadIdx.x; i < 6 * a.V; i += blockDim.x) out[i] = sacc[i];
+  for (int i = threadIdx.x; i < 6 * a.V; i += kRenderThreads) out[i] = sacc[i];
 }
 
-// d_verts[i] = sum_b partials[b][i] (i < 3V), dN[i-3V] = ... (fixed block order)
-__global__ void k_reduce_partials(const float* __restrict__ partials, int nblocks, int V, float* __restrict__ d_verts,
-                                  float* __restrict__ dN) {
+// d_verts[i] = extra[i] + sum_b partials[b][i] (i < 3V), dN[i-3V] likewise, in
+// fixed block order
+__global__ void k_reduce_partials(const float* __restrict__ partials, const float* __restrict__ extra, int nblocks,
+                                  int V, float* __restrict__ d_verts, float* __restrict__ dN) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 6 * V) return;
-  float acc = 0.0f;
+  float acc = extra[i];
   for (int b = 0; b < nblocks; ++b) acc += partials[(size_t)b * 6 * V + i];
   if (i < 3 * V) d_verts[i] = acc;
   else dN[i - 3 * V] = acc;
@@ -446,10 +947,9 @@ __global__ void k_edge_samples(RenderArgs a, const float* __restrict__ adjoint, 
   float3 fp = radiance<STATS>(a, cam, view, xp, yp, bxp, byp, cnt);
   float3 fm = radiance<STATS>(a, cam, view, xm, ym, bxm, bym, cnt);
   if (STATS) {
-    atomicAdd(stats + 0, (unsigned long long)cnt.rays);
-    atomicAdd(stats + 1, (unsigned long long)cnt.nodes);
-    atomicAdd(stats + 2, (unsigned long long)cnt.tris);
-    atomicAdd(stats + 3, (unsigned long long)cnt.hits);
+    unsigned v[kStatsPer] = {cnt.samples, cnt.rays, cnt.nodes, cnt.tris, cnt.hits, cnt.cands};
+    for (int q = 0; q < kStatsPer; ++q)
+      if (v[q]) atomicAdd(stats + q, (unsigned long long)v[q]);
   }
   float wgt = (A.x * (fp.x - fm.x) + A.y * (fp.y - fm.y) + A.z * (fp.z - fm.z)) * ((float)nsil / (float)Ne);
   if (wgt == 0.0f) return;
@@ -534,6 +1034,7 @@ __global__ void k_trace(const Node* __restrict__ nodes, const float4* __restrict
   tuv[3 * i + 2] = h.v;
 }
 
+
 RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,
                      const float* bg, const hr_render_opts* o) {
   RenderArgs a;
@@ -559,6 +1060,16 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.sh.kd = o->kd;
   a.status = ctx->status;
   a.max_visits = ctx->F + 1;
+  a.wk.bb = ctx->pool_bb;
+  a.wk.z = ctx->pool_z;
+  a.wk.rec = ctx->pool_rec;
+  a.wk.pool_cap = ctx->pool_cap;
+  a.wk.st = ctx->st_info;
+  a.wk.items = ctx->items;
+  a.wk.item_cap = ctx->item_cap;
+  a.wk.part = ctx->item_part;
+  a.wk.extra = ctx->extra;
+  a.wk.ctr = ctx->work_ctr;
   return a;
 }
 
@@ -569,21 +1080,31 @@ int render_grid(int device, int* blocks, int* threads, int* num_sms) {
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return HR_ERR_CUDA;
   *num_sms = sms;
   *threads = kRenderThreads;
-  *blocks = sms * 8;
+  *blocks = sms * kBlocksPerSm;
   return HR_OK;
 }
 
 size_t render_bwd_smem(int V) { return (size_t)6 * V * sizeof(float); }
 
+int subtiles_for(int views, int W, int H) { return views * ((W + kSubW - 1) / kSubW) * ((H + kSubH - 1) / kSubH); }
+
 int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,
                       const float* bg, const hr_render_opts* o, float* image, cudaStream_t s) {
   RenderArgs a = make_args(ctx, m, verts, cams, N, H, W, bg, o);
-  long long tiles = (long long)N * ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
-  int blocks = (int)(tiles < ctx->render_blocks ? tiles : ctx->render_blocks);
-  if (o->flags & HR_STATS)
-    k_render_fwd<true><<<blocks, kRenderThreads, 0, s>>>(a, image, ctx->stats);
+  const bool st = o->flags & HR_STATS;
+  if (cudaMemsetAsync(ctx->work_ctr, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return HR_ERR_CUDA;
+  const int blocks = ctx->render_blocks;
+  if (st)
+    k_gather<false, true><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, ctx->stats);
   else
-    k_render_fwd<false><<<blocks, kRenderThreads, 0, s>>>(a, image, nullptr);
+    k_gather<false, false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, nullptr);
+  HR_CHECK_LAUNCH();
+  if (st)
+    k_shade_fwd<true><<<blocks, kRenderThreads, 0, s>>>(a, ctx->stats);
+  else
+    k_shade_fwd<false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr);
+  HR_CHECK_LAUNCH();
+  k_combine_fwd<<<blocks, kRenderThreads, 0, s>>>(a, image);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -603,16 +1124,25 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
   const bool interior = !(o->flags & HR_BWD_NO_INTERIOR);
   const bool edges = !(o->flags & HR_BWD_NO_EDGES) && o->edge_samples > 0;
   const bool normals = !(o->flags & HR_BWD_NO_NORMALS) && interior;
+  const bool st = o->flags & HR_STATS;
   if (interior) {
-    size_t smem = render_bwd_smem(V);
-    const bool st = o->flags & HR_STATS;
-    auto kern = st ? k_render_bwd<true> : k_render_bwd<false>;
+    if (cudaMemsetAsync(ctx->work_ctr, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemsetAsync(ctx->extra, 0, sizeof(float) * 6 * V, s) != cudaSuccess)
+      return HR_ERR_CUDA;
+    if (st)
+      k_gather<true, true><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr,
+                                                                          ctx->stats + kStatsPer);
+    else
+      k_gather<true, false><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
+    HR_CHECK_LAUNCH();
+    const size_t smem = render_bwd_smem(V);
+    auto kern = st ? k_shade_bwd<true> : k_shade_bwd<false>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return HR_ERR_CUDA;
-    int blocks = ctx->render_blocks;
-    kern<<<blocks, kRenderThreads, smem, s>>>(a, adjoint, ctx->partials, st ? ctx->stats + 4 : nullptr);
+    const int blocks = ctx->num_sms * kBwdMinBlocks;
+    kern<<<blocks, kRenderThreads, smem, s>>>(a, adjoint, ctx->partials, st ? ctx->stats + kStatsPer : nullptr);
     HR_CHECK_LAUNCH();
-    k_reduce_partials<<<(6 * V + 255) / 256, 256, 0, s>>>(ctx->partials, blocks, V, d_verts, ctx->dN);
+    k_reduce_partials<<<(6 * V + 255) / 256, 256, 0, s>>>(ctx->partials, ctx->extra, blocks, V, d_verts, ctx->dN);
     HR_CHECK_LAUNCH();
   } else {
     if (cudaMemsetAsync(d_verts, 0, sizeof(float) * 3 * V, s) != cudaSuccess) return HR_ERR_CUDA;
@@ -621,9 +1151,10 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     int rc = launch_silhouettes(ctx, m, verts, cams, N, ctx->sil, ctx->lim.max_E, ctx->sil_count, s);
     if (rc != HR_OK) return rc;
     long long n = (long long)N * o->edge_samples;
-    auto kern = (o->flags & HR_STATS) ? k_edge_samples<true> : k_edge_samples<false>;
+    auto kern = st ? k_edge_samples<true> : k_edge_samples<false>;
     kern<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count,
-                                                     o->edge_samples, o->edge_eps_px, d_verts, ctx->stats + 8);
+                                                     o->edge_samples, o->edge_eps_px, d_verts,
+                                                     ctx->stats + 2 * kStatsPer);
     HR_CHECK_LAUNCH();
   }
   if (normals) {

@@ -47,7 +47,7 @@ class Refiner:
         self.opts = opts
         N, H, W = views.N, views.H, views.W
         hand = model.hand
-        self.ctx = ctx or B.Context(hand.V, hand.F, hand.E, max(N, 1), N * H * W)
+        self.ctx = ctx or B.Context(hand.V, hand.F, hand.E, max(N, 1), W, H)
         dev = views.cams.device
         self.verts = torch.empty((hand.V, 3), device=dev)
         self.image = torch.empty((N, H, W, 3), device=dev)
@@ -128,7 +128,7 @@ def make_views(cfg: I.SceneConfig, model: B.Model, x_gt, device="cuda", ctx=None
     bg_np = I.background(cfg.seed, cfg.views, cfg.height, cfg.width)
     bg = torch.as_tensor(bg_np, device=device)
     N, H, W = cfg.views, cfg.height, cfg.width
-    ctx = ctx or B.Context(hand.V, hand.F, hand.E, N, N * H * W)
+    ctx = ctx or B.Context(hand.V, hand.F, hand.E, N, W, H)
     verts = torch.empty((hand.V, 3), device=device)
     p = torch.as_tensor(np.asarray(x_gt, np.float32), device=device)
     B.hr_skin(ctx, model, p, verts)

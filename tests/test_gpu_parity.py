@@ -26,7 +26,7 @@ def B():
 
 def _ctx(B, sc):
     h = hand()
-    return B.Context(h.V, h.F, h.E, sc.N, sc.N * sc.H * sc.W)
+    return B.Context(h.V, h.F, h.E, sc.N, sc.W, sc.H)
 
 
 def _t(a, dtype=None):
