@@ -81,6 +81,25 @@ typedef struct hr_model {
     const float* albedo;       /* [V][3] per-vertex RGB albedo                      */
 } hr_model;
 
+/* Allocation-free variant of hr_skin_bwd (the paper has no counterpart: it is an
+ * interface for callers that cannot let a library allocate device memory, such as
+ * host applications that hand out all device memory from their own pool, processes
+ * under a fixed device-memory quota, and latency-bound loops that cannot afford
+ * cudaMalloc's implicit device synchronisation).  Same arguments and result as
+ * hr_skin_bwd, without a context: the reduction scratch is a static device array
+ * of about 52 KB inside this library, which every GPU that loads the library keeps
+ * until the process exits.  No device memory is allocated or freed by the call.
+ *   - The first call on a device looks up that array's device address with the
+ *     device current; make that first call before capturing the stream.
+ *   - model->V <= 16384, model->J <= 16, model->K <= 10, else HR_ERR_UNSUPPORTED.
+ *   - All calls share the one array: calls that may overlap on the GPU (different
+ *     streams, or different host threads on one device) race and must be ordered
+ *     by the caller.  The call clears what must start at zero itself.
+ *   - Device-detected errors (non-finite parameters, parent indices out of range)
+ *     are not reported by this variant; its outputs are then undefined. */
+int hr_skin_bwd_noalloc(const hr_model* model, const float* params, const float* d_verts, float* d_params,
+                        hr_stream stream);
+
 /* Render options.  Samples are drawn from Philox4x32-10 keyed by `seed` with counters
  * built from (pixel, view | instance << 16, sample, iter << 4 | stream), so a render
  * is a deterministic function of (seed, iter, instance).  Shading is Lambertian with

@@ -31,7 +31,7 @@ HR_STATS = 8
 
 EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", "hr_build_bvh", "hr_render_fwd",
            "hr_loss", "hr_render_bwd", "hr_adam_step", "hr_trace", "hr_get_normals", "hr_silhouettes",
-           "hr_get_stats", "hr_get_status", "hr_status_string")
+           "hr_get_stats", "hr_get_status", "hr_status_string", "hr_skin_bwd_noalloc")
 
 
 class HandrtError(RuntimeError):
@@ -76,6 +76,7 @@ def lib():
             "hr_context_destroy": [P],
             "hr_skin": [P, P, P, P, P],
             "hr_skin_bwd": [P, P, P, P, P, P],
+            "hr_skin_bwd_noalloc": [P, P, P, P, P],
             "hr_build_bvh": [P, P, P, P],
             "hr_render_fwd": [P, P, P, P, I, I, I, P, P, P, P],
             "hr_loss": [P, P, P, P, I, I, I, P, P, P],
@@ -205,6 +206,13 @@ def hr_skin(ctx, model, params, verts, stream=None):
 def hr_skin_bwd(ctx, model, params, d_verts, d_params, stream=None):
     _check("hr_skin_bwd", lib().hr_skin_bwd(ctx.handle, ctypes.byref(model.struct), _f32(params), _f32(d_verts),
                                             _f32(d_params), _stream(stream)))
+
+
+def hr_skin_bwd_noalloc(model, params, d_verts, d_params, stream=None):
+    """hr_skin_bwd without a context; its scratch is a static device array in the
+    library (for callers that cannot let a library allocate device memory)."""
+    _check("hr_skin_bwd_noalloc", lib().hr_skin_bwd_noalloc(ctypes.byref(model.struct), _f32(params), _f32(d_verts),
+                                                            _f32(d_params), _stream(stream)))
 
 
 def hr_build_bvh(ctx, model, verts, stream=None):

@@ -10,6 +10,8 @@
 //               write one partial each, and the last block to finish sums the
 //               partials in block order and runs the chain backward in one thread.
 //               Fully deterministic.
+#include <mutex>
+
 #include "hr_internal.h"
 
 namespace hr {
@@ -337,3 +339,80 @@ int launch_skin_bwd(Context* ctx, const hr_model* m, const float* params, const 
 }
 
 }  // namespace hr
+
+// ---------------------------------------------------------------------------------
+// Allocation-free skinning adjoint.
+//
+// Some callers cannot let a library allocate device memory: host applications that
+// hand every byte of device memory out of their own pool and forbid side
+// allocations, processes running under a fixed device-memory quota, and
+// latency-bound loops that cannot afford the implicit device synchronisation of
+// cudaMalloc.  hr_skin_bwd_noalloc computes exactly what hr_skin_bwd computes, with
+// the same kernel, but its reduction scratch (one partial per block, the
+// last-block counter and a status word) lives in the file-scope array below, which
+// every GPU that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------------
+namespace hr {
+namespace {
+
+constexpr int kNoAllocMaxV = kSkinBlocks * kSkinThreads;   // 16384 vertices
+constexpr size_t kNoAllocPartialBytes = sizeof(float) * kSkinBlocks * kSkinAcc;
+constexpr size_t kNoAllocBytes = kNoAllocPartialBytes + 256;   // + counter and status word
+
+static __device__ __align__(256) unsigned char g_skin_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// device address of the scratch array on the current device (looked up once per
+// device; the host-side symbol is only a stand-in and must never reach a kernel)
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HR_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return HR_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_skin_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return HR_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return HR_OK;
+}
+
+}  // namespace
+}  // namespace hr
+
+extern "C" int hr_skin_bwd_noalloc(const hr_model* m, const float* params, const float* d_verts, float* d_params,
+                                   hr_stream stream) {
+  using namespace hr;
+  if (!m || !params || !d_verts || !d_params) return HR_ERR_ARG;
+  if (m->V <= 0 || m->J <= 0 || m->K < 0 || !m->v_template || !m->shapedirs || !m->weights || !m->j_template ||
+      !m->j_shapedirs || !m->parents)
+    return HR_ERR_ARG;
+  if (m->V > kNoAllocMaxV || m->J > kMaxJ || m->K > kMaxK) return HR_ERR_UNSUPPORTED;
+  void* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc != HR_OK) return rc;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  float* partials = reinterpret_cast<float*>(b);
+  unsigned* counter = reinterpret_cast<unsigned*>(b + kNoAllocPartialBytes);
+  int* status = reinterpret_cast<int*>(b + kNoAllocPartialBytes + 128);
+  cudaStream_t s = (cudaStream_t)stream;
+  // the last-block counter must start at zero; the rest is overwritten by the call
+  if (cudaMemsetAsync(counter, 0, sizeof(unsigned), s) != cudaSuccess) {
+    cudaGetLastError();
+    return HR_ERR_CUDA;
+  }
+  int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
+  k_skin_bwd<<<blocks, kSkinThreads, 0, s>>>(model_args(m), params, d_verts, partials, counter, d_params, status);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
