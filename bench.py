@@ -49,6 +49,15 @@ N_SM, LANES = 152, 128
 # differentiated hit (backward)
 FLOP_RAY, FLOP_NODE, FLOP_CAND, FLOP_TRI, FLOP_HIT, FLOP_HIT_GRAD = 40, 60, 4, 50, 60, 250
 S_SAMPLES, S_RAYS, S_NODES, S_TRIS, S_HITS, S_CANDS = range(6)
+FLOP_TRACE_NODE, FLOP_EDGE = 40, 120   # per-ray traversal node (two slab tests); edge-sample set-up
+KERNEL_NAMES = {"fwd_gather": "k_gather<fwd>", "fwd_shade": "k_shade_fwd", "bwd_gather": "k_gather<bwd>",
+                "bwd_shade": "k_shade_bwd", "edge_samples": "k_edge_samples"}
+# DRAM bytes (read + write) per launch from the ncu capture summarised under profiles/
+# (None once the kernel has changed since that capture)
+NCU_TRAFFIC = {"k_shade_bwd": 3658240, "k_shade_fwd": 2395904, "k_gather<fwd>": 17733376,
+               "k_gather<bwd>": 19088128}
+# kernels of one step: skin 1, BVH + normals 2, forward 3, loss 2, backward 7, skin adjoint 1, Adam 1
+LAUNCHES_PER_STEP = 17
 
 
 def env_rank():
@@ -152,13 +161,6 @@ def run_handrt(args):
     rays_fwd, rays_bwd, rays_edge = stats[0, S_SAMPLES], stats[1, S_SAMPLES], stats[2, S_SAMPLES]
     rays_step = rays_fwd + rays_bwd + rays_edge
 
-    def model_flops(row, per_hit):
-        return (FLOP_RAY * row[S_RAYS] + FLOP_NODE * row[S_NODES] + FLOP_CAND * row[S_CANDS] +
-                FLOP_TRI * row[S_TRIS] + per_hit * row[S_HITS])
-
-    flops_fwd = model_flops(stats[0], FLOP_HIT)
-    flops_bwd = model_flops(stats[1], FLOP_HIT_GRAD)
-
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     stages = ["skin", "bvh", "fwd", "loss", "bwd", "skin_bwd", "adam"]
@@ -188,7 +190,36 @@ def run_handrt(args):
         one_step(w)
     torch.cuda.synchronize()
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    # the timed step: one whole iteration captured as a CUDA graph and replayed; the
+    # sample streams and Adam's step number come from a device counter that the
+    # Adam kernel advances, so every replay is a fresh iteration
+    iter_dev = torch.full((1,), args.warmup, dtype=torch.int32, device=dev)
+    gopts = P.opts_for(cfg, iter_dev=iter_dev)
+    gopts.instance = rank
+
+    def graph_step():
+        B.hr_skin(ctx, model, params, ref.verts)
+        B.hr_build_bvh(ctx, model, ref.verts)
+        B.hr_render_fwd(ctx, model, ref.verts, views.cams, H, W, views.background, gopts, ref.image)
+        B.hr_loss(ctx, ref.image, views.observed, views.mask, ref.loss, ref.adjoint)
+        B.hr_render_bwd(ctx, model, ref.verts, views.cams, H, W, views.background, gopts, ref.adjoint, ref.d_verts)
+        B.hr_skin_bwd(ctx, model, params, ref.d_verts, ref.d_params)
+        B.hr_adam_step_dev(params, ref.d_params, m1, m2, lr, 0.9, 0.999, 1e-8, iter_dev)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        graph_step()                     # one eager run on the capture stream first
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        graph_step()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -196,18 +227,42 @@ def run_handrt(args):
         time.sleep(0.4)                  # let the sampler start before the timed region
         for k in range(args.steps):
             flush.fill_(float(k))        # evict L2 between timed steps (outside the events)
-            one_step(args.warmup + k, ev[k])
+            ev[k][0].record(stream)
+            graph.replay()
+            ev[k][1].record(stream)
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    st = np.array([[ev[k][i].elapsed_time(ev[k][i + 1]) for i in range(7)] for k in range(args.steps)])
-    step_ms = st.sum(1)
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
     ms_per_step = float(step_ms.mean())
     tot_ms = float(step_ms.sum())
+
+    # stage breakdown (eager launches, events between the C-ABI calls; diagnostic)
+    n_st = max(1, min(args.steps, 50))
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(n_st)]
+    for k in range(n_st):
+        flush.fill_(float(k))
+        one_step(args.warmup + k, sev[k])
+    torch.cuda.synchronize()
+    st = np.array([[sev[k][i].elapsed_time(sev[k][i + 1]) for i in range(7)] for k in range(n_st)])
     status = B.hr_get_status(ctx)
     if status != B.HR_OK:
         raise RuntimeError(f"device status {B.status_string(status)}")
+
+    # per-kernel device times: a second timed pass with CUDA events recorded by the
+    # library between its internal kernels (HR_TIMING), L2 flushed between steps
+    ktimes = {k: [] for k in B.KERNEL_TIMES}
+    opts.flags = B.HR_TIMING
+    n_kt = max(1, min(args.steps, 50))
+    for k in range(n_kt):
+        flush.fill_(float(k))
+        one_step(args.warmup + args.steps + k)
+        for name, ms in B.hr_kernel_times(ctx).items():
+            if ms >= 0:
+                ktimes[name].append(ms)
+    opts.flags = 0
+    kt_mean = {k: float(np.mean(v)) for k, v in ktimes.items() if v}
 
     # end-to-end through the public API with host buffers
     pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
@@ -260,16 +315,30 @@ def run_handrt(args):
     stage_ms = dict(zip(stages, st.mean(0).round(4).tolist()))
     pk, pk_kind = peaks()
     clocks = clk.summary()
-    fwd_ms = float(st[:, 2].mean())
     fp32_peak = N_SM * LANES * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    achieved = flops_fwd / (fwd_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": "k_render_fwd", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
-            "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": None,
-            "peak_note": f"FP32 FMA peak 152 SMs x 128 lanes x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
-                         f"(max clock; recipe unit counts), {pk_kind} clock data",
-            "flops_per_launch": flops_fwd,
-            "flop_model": f"{FLOP_RAY}/ray made + {FLOP_NODE}/BVH node + {FLOP_CAND}/candidate box test + "
-                          f"{FLOP_TRI}/Moller-Trumbore test + {FLOP_HIT}/shaded hit",
+    fwd_row, bwd_row, edge_row = stats
+    kflops = {
+        "fwd_gather": FLOP_NODE * fwd_row[S_NODES],
+        "fwd_shade": (FLOP_RAY * fwd_row[S_RAYS] + FLOP_CAND * fwd_row[S_CANDS] + FLOP_TRI * fwd_row[S_TRIS] +
+                      FLOP_HIT * fwd_row[S_HITS]),
+        "bwd_gather": FLOP_NODE * bwd_row[S_NODES],
+        "bwd_shade": (FLOP_RAY * bwd_row[S_RAYS] + FLOP_CAND * bwd_row[S_CANDS] + FLOP_TRI * bwd_row[S_TRIS] +
+                      FLOP_HIT_GRAD * bwd_row[S_HITS]),
+        "edge_samples": (FLOP_RAY * edge_row[S_RAYS] + FLOP_TRACE_NODE * edge_row[S_NODES] +
+                         FLOP_TRI * edge_row[S_TRIS] + FLOP_HIT * edge_row[S_HITS] + FLOP_EDGE * edge_row[S_RAYS] / 2),
+    }
+    dom = max((k for k in kflops if k in kt_mean), key=lambda k: kt_mean[k])
+    achieved = kflops[dom] / (kt_mean[dom] * 1e-3) / 1e12
+    kernel_name = KERNEL_NAMES[dom]
+    roof = {"bound": "alu", "kernel": kernel_name, "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
+            "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": NCU_TRAFFIC.get(kernel_name),
+            "launch_ms": round(kt_mean[dom], 4), "flops_per_launch": float(kflops[dom]),
+            "peak_note": f"FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
+                         f"(max SM clock, {pk_kind} clock data)",
+            "flop_model": f"{FLOP_RAY}/ray made + {FLOP_CAND}/candidate box test + {FLOP_TRI}/Moller-Trumbore "
+                          f"test + {FLOP_HIT}/shaded hit or {FLOP_HIT_GRAD}/differentiated hit; "
+                          f"{FLOP_NODE}/frustum node visit",
+            "kernel_ms": {k: round(v, 4) for k, v in kt_mean.items()},
             "frac_at_load_clock": None}
     if clocks:
         roof["frac_at_load_clock"] = round(achieved / (N_SM * LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12), 4)
@@ -284,11 +353,13 @@ def run_handrt(args):
                    "work_counters": {k: {n: int(v) for n, v in zip(
                        ["samples", "rays", "bvh_nodes", "mt_tests", "hits", "cand_box_tests"], stats[i])}
                        for i, k in enumerate(["fwd", "bwd", "edge"])},
-                   "stage_ms": stage_ms, "l2": "flushed between timed steps (256 MB write)",
+                   "stage_ms_eager": stage_ms, "step_ms_eager": round(float(st.sum(1).mean()), 4),
+                   "timing": "CUDA graph of one whole iteration, replayed; events around each replay",
+                   "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"{world} independent instance(s), one per GPU"},
         "e2e": {"value": round(rays_step * world / (e2e_ms * 1e-3) / 1e6, 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)},
-        "gpu_launches": 14 * args.steps,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "roofline": roof,
         "clocks": clocks,
     }

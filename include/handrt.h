@@ -116,12 +116,15 @@ typedef struct hr_render_opts {
     float light_rgb[3];
     float edge_eps_px;      /* offset of the two edge-sample rays, in pixels        */
     uint32_t flags;         /* HR_BWD_* bits; 0 = every term                        */
+    const uint32_t* iter_dev; /* optional device counter read instead of `iter` (so a
+                                 captured iteration replays with fresh samples); NULL = use iter */
 } hr_render_opts;
 
 #define HR_BWD_NO_INTERIOR 1u  /* hr_render_bwd: skip the interior term            */
 #define HR_BWD_NO_EDGES 2u     /* hr_render_bwd: skip the edge-sampling term       */
 #define HR_BWD_NO_NORMALS 4u   /* hr_render_bwd: skip the vertex-normal adjoint    */
 #define HR_STATS 8u            /* count rays, BVH nodes, triangle tests and hits   */
+#define HR_TIMING 16u          /* record CUDA events around the internal kernels   */
 
 /* Sizes a context is created for; all scratch is allocated once, up front. */
 typedef struct hr_limits {
@@ -203,6 +206,14 @@ int hr_render_bwd(hr_context* ctx, const hr_model* model, const float* verts, co
 int hr_adam_step(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1,
                  float beta2, float eps, int step, hr_stream stream);
 
+/* Adam step with the step number kept on the device: step = *iter_dev + 1, and the
+ * call then advances *iter_dev by one (device uint32).  With the same counter given
+ * to the render calls as hr_render_opts.iter_dev, a whole refinement iteration can
+ * be replayed (for example from a CUDA graph) with fresh sample streams and correct
+ * bias correction every time. */
+int hr_adam_step_dev(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1,
+                     float beta2, float eps, uint32_t* iter_dev, hr_stream stream);
+
 /* Diagnostics over the context's current scene (used by the tests):
  *   hr_trace:        closest hit of n rays (origins, dirs: device float[n][3]) against
  *                    the last built BVH: tri (device int32[n], -1 = miss), tuv
@@ -223,6 +234,13 @@ int hr_silhouettes(hr_context* ctx, const hr_model* model, const float* verts, c
  * Moller-Trumbore tests, hits, candidate screen-box tests).  A sample is resolved
  * without its own ray when its sub-tile's frustum misses the scene. */
 int hr_get_stats(hr_context* ctx, uint64_t* out, hr_stream stream);
+
+/* Device times (ms) of the internal kernels of the most recent hr_render_fwd and
+ * hr_render_bwd made with HR_TIMING, from CUDA events recorded on their stream:
+ * ms[0..2] forward candidate gather / shading / combine, ms[3..5] backward gather /
+ * shading / partial reduction, ms[6] silhouettes, ms[7] edge samples, ms[8] normal
+ * adjoint; -1 for a kernel that did not run.  n >= 9.  Waits for those events. */
+int hr_kernel_times(hr_context* ctx, float* ms, int n);
 
 /* Synchronise `stream`, then return and clear the device status word: HR_OK, or the
  * HR_ERR_* code of a device-detected error since the last call (HR_ERR_ARG for face

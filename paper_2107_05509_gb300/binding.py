@@ -28,10 +28,14 @@ HR_BWD_NO_INTERIOR = 1
 HR_BWD_NO_EDGES = 2
 HR_BWD_NO_NORMALS = 4
 HR_STATS = 8
+HR_TIMING = 16
+KERNEL_TIMES = ("fwd_gather", "fwd_shade", "fwd_combine", "bwd_gather", "bwd_shade", "bwd_reduce", "silhouettes",
+                "edge_samples", "normal_adjoint")
 
 EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", "hr_build_bvh", "hr_render_fwd",
            "hr_loss", "hr_render_bwd", "hr_adam_step", "hr_trace", "hr_get_normals", "hr_silhouettes",
-           "hr_get_stats", "hr_get_status", "hr_status_string", "hr_skin_bwd_noalloc")
+           "hr_get_stats", "hr_get_status", "hr_status_string", "hr_skin_bwd_noalloc", "hr_kernel_times",
+           "hr_adam_step_dev")
 
 
 class HandrtError(RuntimeError):
@@ -51,7 +55,7 @@ class hr_render_opts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("iter", ctypes.c_uint32), ("instance", ctypes.c_uint32),
                 ("spp", ctypes.c_int32), ("edge_samples", ctypes.c_int32), ("ka", ctypes.c_float),
                 ("kd", ctypes.c_float), ("light_dir", ctypes.c_float * 3), ("light_rgb", ctypes.c_float * 3),
-                ("edge_eps_px", ctypes.c_float), ("flags", ctypes.c_uint32)]
+                ("edge_eps_px", ctypes.c_float), ("flags", ctypes.c_uint32), ("iter_dev", ctypes.c_void_p)]
 
 
 class hr_limits(ctypes.Structure):
@@ -82,10 +86,12 @@ def lib():
             "hr_loss": [P, P, P, P, I, I, I, P, P, P],
             "hr_render_bwd": [P, P, P, P, I, I, I, P, P, P, P, P],
             "hr_adam_step": [P, P, P, P, I, F, F, F, F, I, P],
+            "hr_adam_step_dev": [P, P, P, P, I, F, F, F, F, P, P],
             "hr_trace": [P, P, P, I, P, P, P],
             "hr_get_normals": [P, P, P],
             "hr_silhouettes": [P, P, P, P, I, P, P, P],
             "hr_get_stats": [P, P, P],
+            "hr_kernel_times": [P, P, I],
             "hr_get_status": [P, P],
             "hr_status_string": [I],
         }
@@ -179,7 +185,7 @@ class Model:
 
 
 def render_opts(seed=0, iter=0, instance=0, spp=4, edge_samples=1024, ka=0.4, kd=0.6, light_dir=(0.0, 0.0, 1.0),
-                light_rgb=(1.0, 1.0, 1.0), edge_eps_px=1e-3, flags=0):
+                light_rgb=(1.0, 1.0, 1.0), edge_eps_px=1e-3, flags=0, iter_dev=None):
     o = hr_render_opts()
     o.seed = seed
     o.iter = iter
@@ -191,6 +197,7 @@ def render_opts(seed=0, iter=0, instance=0, spp=4, edge_samples=1024, ka=0.4, kd
     o.light_rgb[:] = list(light_rgb)
     o.edge_eps_px = edge_eps_px
     o.flags = flags
+    o.iter_dev = None if iter_dev is None else iter_dev.data_ptr()
     return o
 
 
@@ -246,6 +253,12 @@ def hr_adam_step(params, grad, m, v, lr, beta1, beta2, eps, step, stream=None):
                                               beta2, eps, step, _stream(stream)))
 
 
+def hr_adam_step_dev(params, grad, m, v, lr, beta1, beta2, eps, iter_dev, stream=None):
+    assert iter_dev.dtype == torch.int32 and iter_dev.numel() == 1   # holds a uint32 counter
+    _check("hr_adam_step_dev", lib().hr_adam_step_dev(_f32(params), _f32(grad), _f32(m), _f32(v), params.numel(), lr,
+                                                      beta1, beta2, eps, _ptr(iter_dev), _stream(stream)))
+
+
 def hr_trace(ctx, origins, dirs, tri, tuv, stream=None):
     assert tri.dtype == torch.int32
     _check("hr_trace", lib().hr_trace(ctx.handle, _f32(origins), _f32(dirs), origins.shape[0], _ptr(tri), _f32(tuv),
@@ -269,6 +282,13 @@ def hr_get_stats(ctx, stream=None):
     out = (ctypes.c_uint64 * 18)()
     _check("hr_get_stats", lib().hr_get_stats(ctx.handle, out, _stream(stream)))
     return np.array(out[:], np.uint64).reshape(3, 6)
+
+
+def hr_kernel_times(ctx):
+    """Internal kernel times (ms) of the last HR_TIMING render calls, by KERNEL_TIMES."""
+    out = (ctypes.c_float * len(KERNEL_TIMES))()
+    _check("hr_kernel_times", lib().hr_kernel_times(ctx.handle, out, len(KERNEL_TIMES)))
+    return dict(zip(KERNEL_TIMES, out[:]))
 
 
 def hr_get_status(ctx, stream=None):

@@ -31,6 +31,8 @@ bool dev_alloc(T** p, size_t count, Alloc& list) {
 }
 
 void free_ctx(Context* c) {
+  for (int i = 0; i < 2 * hr::kTimeSlots; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   void* ptrs[] = {c->nodes, c->tris,          c->normals,      c->normal_len, c->partials,
                   c->dN,    c->dm,            c->sil,          c->sil_count,  c->loss_partials,
                   c->counters, c->skin_partials, c->status, c->keys, c->parent, c->stats, c->tile_counters,
@@ -103,6 +105,10 @@ int hr_context_create(const hr_limits* lim, hr_context** out) {
                cudaMemset(c->status, 0, sizeof(int)) == cudaSuccess &&
                cudaMemset(c->stats, 0, 3 * hr::kStatsPer * sizeof(unsigned long long)) == cudaSuccess &&
                cudaMemset(c->nodes, 0, F * sizeof(hr::Node)) == cudaSuccess;
+  for (int i = 0; ok && i < 2 * hr::kTimeSlots; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
+  // kernel attributes are set here, once, so that the per-iteration calls are only
+  // launches and asynchronous memsets
+  if (ok) ok = hr::configure_bvh_kernels() == HR_OK && hr::configure_render_kernels(lim->max_V) == HR_OK;
   if (!ok) {
     cudaGetLastError();
     free_ctx(c);
@@ -177,6 +183,14 @@ int hr_adam_step(float* params, const float* grad, float* m, float* v, int n, fl
   return hr::launch_adam(params, grad, m, v, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream);
 }
 
+int hr_adam_step_dev(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
+                     float eps, uint32_t* iter_dev, hr_stream stream) {
+  if (!params || !grad || !m || !v || !iter_dev || n <= 0 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+      !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+    return HR_ERR_ARG;
+  return hr::launch_adam_dev(params, grad, m, v, n, lr, beta1, beta2, eps, iter_dev, (cudaStream_t)stream);
+}
+
 int hr_trace(hr_context* ctx, const float* origins, const float* dirs, int n, int32_t* tri, float* tuv,
              hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
@@ -213,6 +227,24 @@ int hr_get_stats(hr_context* ctx, uint64_t* out, hr_stream stream) {
       cudaMemset(c->stats, 0, 3 * hr::kStatsPer * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     return HR_ERR_CUDA;
+  }
+  return HR_OK;
+}
+
+static_assert(2 * hr::kTimeSlots <= (int)(sizeof(hr::Context::ev) / sizeof(cudaEvent_t)), "event slots");
+
+int hr_kernel_times(hr_context* ctx, float* ms, int n) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !ms || n < hr::kTimeSlots) return HR_ERR_ARG;
+  const int need[hr::kTimeSlots] = {1, 1, 1, 4, 4, 4, 8, 8, 16};
+  for (int i = 0; i < hr::kTimeSlots; ++i) {
+    ms[i] = -1.0f;
+    if (!(c->ev_ready & need[i])) continue;
+    if (cudaEventSynchronize(c->ev[2 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms[i], c->ev[2 * i], c->ev[2 * i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      return HR_ERR_CUDA;
+    }
   }
   return HR_OK;
 }

@@ -250,16 +250,31 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
   }
 }
 
+// Faces and the vertex->face table come from the caller: an index out of range is
+// reported in the status word and its face skipped.
 __global__ void k_vertex_normals(const float* __restrict__ verts, const int* __restrict__ faces,
-                                 const int* __restrict__ vf_off, const int* __restrict__ vf_faces, int V,
-                                 float* __restrict__ normals, float* __restrict__ normal_len) {
+                                 const int* __restrict__ vf_off, const int* __restrict__ vf_faces, int V, int F,
+                                 float* __restrict__ normals, float* __restrict__ normal_len, int* status) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
   float3 m = make_float3(0.0f, 0.0f, 0.0f);
-  for (int k = vf_off[v]; k < vf_off[v + 1]; ++k) {
+  int k0 = vf_off[v], k1 = vf_off[v + 1];
+  if (k0 < 0 || k1 < k0 || k1 > 3 * F) {
+    set_status(status, kStatusBadModel);
+    k1 = k0;
+  }
+  for (int k = k0; k < k1; ++k) {
     int f = vf_faces[k];
-    float3 a = ld3(verts + 3 * faces[3 * f]), b = ld3(verts + 3 * faces[3 * f + 1]),
-           c = ld3(verts + 3 * faces[3 * f + 2]);
+    if (f < 0 || f >= F) {
+      set_status(status, kStatusBadModel);
+      continue;
+    }
+    const int i0 = faces[3 * f], i1 = faces[3 * f + 1], i2 = faces[3 * f + 2];
+    if (i0 < 0 || i0 >= V || i1 < 0 || i1 >= V || i2 < 0 || i2 >= V) {
+      set_status(status, kStatusBadModel);
+      continue;
+    }
+    float3 a = ld3(verts + 3 * i0), b = ld3(verts + 3 * i1), c = ld3(verts + 3 * i2);
     float3 cf = dcross(dsub(b, a), dsub(c, a));
     m = make_float3(__fadd_rn(m.x, cf.x), __fadd_rn(m.y, cf.y), __fadd_rn(m.z, cf.z));
   }
@@ -274,19 +289,24 @@ __global__ void k_vertex_normals(const float* __restrict__ verts, const int* __r
 
 }  // namespace
 
+int configure_bvh_kernels() {
+  if (cudaFuncSetAttribute(k_build_bvh, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
+    cudaGetLastError();
+    return HR_ERR_CUDA;
+  }
+  return HR_OK;
+}
+
 int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaStream_t s) {
   int F = m->F, V = m->V;
   int P = 1;
   while (P < F) P <<= 1;
   size_t smem = (size_t)P * 8 + (size_t)3 * F * 4;
-  if (smem > 200 * 1024) return HR_ERR_UNSUPPORTED;
-  // per device and cheap: set on every call rather than caching device state
-  if (cudaFuncSetAttribute(k_build_bvh, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
-    return HR_ERR_CUDA;
+  if (smem > 200 * 1024) return HR_ERR_UNSUPPORTED;   // the opt-in set by configure_bvh_kernels
   k_build_bvh<<<1, kBuildThreads, smem, s>>>(verts, m->faces, F, V, P, ctx->nodes, ctx->tris, ctx->status);
   HR_CHECK_LAUNCH();
-  k_vertex_normals<<<(V + 255) / 256, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, V, ctx->normals,
-                                                   ctx->normal_len);
+  k_vertex_normals<<<(V + 255) / 256, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, V, F, ctx->normals,
+                                                   ctx->normal_len, ctx->status);
   HR_CHECK_LAUNCH();
   ctx->V = V;
   ctx->F = F;

@@ -19,6 +19,10 @@ constexpr int kStatusLimit = 1;     // device status bits
 constexpr int kStatusNonfinite = 2;
 constexpr int kStatusBadModel = 4;  // a face or parent index out of range
 constexpr int kStatusIndex = 8;     // an internal index read from device memory out of range
+// HR_TIMING event slots: forward gather/shade/combine, backward gather/shade/reduce/
+// silhouettes/edges/normal adjoint
+constexpr int kTimeFwdGather = 0, kTimeFwdShade = 1, kTimeFwdCombine = 2, kTimeBwdGather = 3, kTimeBwdShade = 4,
+              kTimeBwdReduce = 5, kTimeBwdSil = 6, kTimeBwdEdges = 7, kTimeBwdNormals = 8, kTimeSlots = 9;
 
 // ---------------------------------------------------------------------------------
 // BVH layout (binary LBVH, F-1 internal nodes, leaves = triangle records)
@@ -72,6 +76,9 @@ struct Context {
   unsigned int* tile_counters;  // [4] dynamic tile schedulers of the render kernels
   // skin scratch
   float* skin_partials;  // [kSkinBlocks][kSkinAcc]
+  // kernel timing (HR_TIMING): events around the render kernels of the last call
+  cudaEvent_t ev[32];          // >= 2 * kTimeSlots
+  int ev_ready;
   // status and work counters
   int* status;
   unsigned long long* stats;  // [3][kStatsPer]

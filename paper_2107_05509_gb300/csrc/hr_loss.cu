@@ -145,7 +145,32 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
   p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// one block: bias corrections from the device step counter, then the counter advances
+__global__ void k_adam_dev(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                           float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
+                           uint32_t* __restrict__ iter_dev) {
+  const float step = (float)(*iter_dev + 1u);
+  const float c1 = 1.0f - powf(b1, step), c2 = 1.0f - powf(b2, step);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.0f - b1) * gi;
+    float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *iter_dev += 1u;
+}
+
 }  // namespace
+
+int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
+                    uint32_t* iter_dev, cudaStream_t s) {
+  k_adam_dev<<<1, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, iter_dev);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
 
 int launch_loss(Context* ctx, const float* image, const float* obs, const uint8_t* mask, long long P, float* loss,
                 float* adjoint, cudaStream_t s) {

@@ -202,7 +202,8 @@ struct RenderArgs {
   int N, H, W, spp, V;
   uint2 key;
   uint32_t ctr1_hi;  // instance << 16
-  uint32_t iter4;    // iter << 4
+  uint32_t iter4;    // iter << 4 (kernels refresh it from iter_dev when given)
+  const uint32_t* iter_dev;
   Shading sh;
   int* status;
   int max_visits;    // F + 1
@@ -231,6 +232,12 @@ __device__ __forceinline__ Cam load_cam(const Cam* cams, int view) {
 #pragma unroll
   for (int i = 0; i < 20; ++i) dst[i] = __ldg(src + i);
   return c;
+}
+
+// sample-stream iteration: the device counter when the caller gave one
+__device__ __forceinline__ RenderArgs with_iter(RenderArgs a) {
+  if (a.iter_dev) a.iter4 = (*a.iter_dev) << 4;
+  return a;
 }
 
 __device__ __forceinline__ void jitter(const RenderArgs& a, int view, int px, int py, int s, float& u1, float& u2) {
@@ -629,8 +636,9 @@ __device__ __forceinline__ float3 lane_adjoint(const RenderArgs& a, const SubTil
 // gradient.  FWD: zero-candidate sub-tiles are written (background) here.  When the
 // pool or the item table is full the warp does the sub-tile's work itself.
 template <bool BWD, bool STATS>
-__global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a, const float* __restrict__ adjoint,
+__global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, const float* __restrict__ adjoint,
                                                           float* __restrict__ image, unsigned long long* stats) {
+  const RenderArgs a = with_iter(a_in);
   __shared__ GatherSmem gsm[kWarps];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -755,7 +763,8 @@ __device__ __forceinline__ void item_samples(int c, int C, int spp, int& s0, int
 }
 
 template <bool STATS>
-__global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a, unsigned long long* stats) {
+__global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in, unsigned long long* stats) {
+  const RenderArgs a = with_iter(a_in);
   const int lane = threadIdx.x & 31;
   Counts cnt;
   const int n = item_count(a);
@@ -808,10 +817,11 @@ __global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, fl
 // interior term: warps take work items; the block accumulates dV/dN in shared
 // memory (sdV [V][3], sdN [V][3]) and writes one partial per block
 template <bool STATS>
-__global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(RenderArgs a,
+__global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(RenderArgs a_in,
                                                                              const float* __restrict__ adjoint,
                                                                              float* __restrict__ partials,
                                                                              unsigned long long* stats) {
+  const RenderArgs a = with_iter(a_in);
   extern __shared__ float sacc[];
   float* sdV = sacc;
   float* sdN = sacc + 3 * a.V;
@@ -910,9 +920,10 @@ __global__ void k_silhouettes(const float* __restrict__ verts, const int* __rest
 
 // boundary term (edge sampling); one thread per (view, sample)
 template <bool STATS>
-__global__ void k_edge_samples(RenderArgs a, const float* __restrict__ adjoint, const int* __restrict__ edges,
+__global__ void k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoint, const int* __restrict__ edges,
                                const int* __restrict__ lists, int stride, const int* __restrict__ counts, int Ne,
                                float eps, float* __restrict__ d_verts, unsigned long long* stats) {
+  const RenderArgs a = with_iter(a_in);
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)a.N * Ne) return;
   int view = (int)(i / Ne), k = (int)(i - (long long)view * Ne);
@@ -1035,6 +1046,19 @@ __global__ void k_trace(const Node* __restrict__ nodes, const float4* __restrict
 }
 
 
+// HR_TIMING: event pair (2 slot, 2 slot + 1) around internal kernel `slot`
+struct Timer {
+  Context* ctx;
+  cudaStream_t s;
+  bool on;
+  void begin(int slot) {
+    if (on) cudaEventRecord(ctx->ev[2 * slot], s);
+  }
+  void end(int slot) {
+    if (on) cudaEventRecord(ctx->ev[2 * slot + 1], s);
+  }
+};
+
 RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,
                      const float* bg, const hr_render_opts* o) {
   RenderArgs a;
@@ -1054,6 +1078,7 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.key = make_uint2((uint32_t)(o->seed & 0xffffffffull), (uint32_t)(o->seed >> 32));
   a.ctr1_hi = o->instance << 16;
   a.iter4 = o->iter << 4;
+  a.iter_dev = o->iter_dev;
   a.sh.l = make_float3(o->light_dir[0], o->light_dir[1], o->light_dir[2]);
   a.sh.lrgb = make_float3(o->light_rgb[0], o->light_rgb[1], o->light_rgb[2]);
   a.sh.ka = o->ka;
@@ -1086,26 +1111,47 @@ int render_grid(int device, int* blocks, int* threads, int* num_sms) {
 
 size_t render_bwd_smem(int V) { return (size_t)6 * V * sizeof(float); }
 
+int configure_render_kernels(int max_V) {
+  // the largest any context may use (max_V <= 8192), so that creating a smaller
+  // context never lowers the opt-in of a larger one
+  (void)max_V;
+  const int smem = (int)render_bwd_smem(8192);
+  if (cudaFuncSetAttribute(k_shade_bwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k_shade_bwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return HR_ERR_CUDA;
+  }
+  return HR_OK;
+}
+
 int subtiles_for(int views, int W, int H) { return views * ((W + kSubW - 1) / kSubW) * ((H + kSubH - 1) / kSubH); }
 
 int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,
                       const float* bg, const hr_render_opts* o, float* image, cudaStream_t s) {
   RenderArgs a = make_args(ctx, m, verts, cams, N, H, W, bg, o);
   const bool st = o->flags & HR_STATS;
+  Timer tm{ctx, s, (o->flags & HR_TIMING) != 0};
   if (cudaMemsetAsync(ctx->work_ctr, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return HR_ERR_CUDA;
   const int blocks = ctx->render_blocks;
+  tm.begin(kTimeFwdGather);
   if (st)
     k_gather<false, true><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, ctx->stats);
   else
     k_gather<false, false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, nullptr);
   HR_CHECK_LAUNCH();
+  tm.end(kTimeFwdGather);
+  tm.begin(kTimeFwdShade);
   if (st)
     k_shade_fwd<true><<<blocks, kRenderThreads, 0, s>>>(a, ctx->stats);
   else
     k_shade_fwd<false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr);
   HR_CHECK_LAUNCH();
+  tm.end(kTimeFwdShade);
+  tm.begin(kTimeFwdCombine);
   k_combine_fwd<<<blocks, kRenderThreads, 0, s>>>(a, image);
   HR_CHECK_LAUNCH();
+  tm.end(kTimeFwdCombine);
+  if (tm.on) ctx->ev_ready |= 1;
   return HR_OK;
 }
 
@@ -1125,44 +1171,56 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
   const bool edges = !(o->flags & HR_BWD_NO_EDGES) && o->edge_samples > 0;
   const bool normals = !(o->flags & HR_BWD_NO_NORMALS) && interior;
   const bool st = o->flags & HR_STATS;
+  Timer tm{ctx, s, (o->flags & HR_TIMING) != 0};
   if (interior) {
     if (cudaMemsetAsync(ctx->work_ctr, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
         cudaMemsetAsync(ctx->extra, 0, sizeof(float) * 6 * V, s) != cudaSuccess)
       return HR_ERR_CUDA;
+    tm.begin(kTimeBwdGather);
     if (st)
       k_gather<true, true><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr,
                                                                           ctx->stats + kStatsPer);
     else
       k_gather<true, false><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
     HR_CHECK_LAUNCH();
-    const size_t smem = render_bwd_smem(V);
+    tm.end(kTimeBwdGather);
+    const size_t smem = render_bwd_smem(V);   // within the opt-in of configure_render_kernels
     auto kern = st ? k_shade_bwd<true> : k_shade_bwd<false>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-      return HR_ERR_CUDA;
     const int blocks = ctx->num_sms * kBwdMinBlocks;
+    tm.begin(kTimeBwdShade);
     kern<<<blocks, kRenderThreads, smem, s>>>(a, adjoint, ctx->partials, st ? ctx->stats + kStatsPer : nullptr);
     HR_CHECK_LAUNCH();
+    tm.end(kTimeBwdShade);
+    tm.begin(kTimeBwdReduce);
     k_reduce_partials<<<(6 * V + 255) / 256, 256, 0, s>>>(ctx->partials, ctx->extra, blocks, V, d_verts, ctx->dN);
     HR_CHECK_LAUNCH();
+    tm.end(kTimeBwdReduce);
   } else {
     if (cudaMemsetAsync(d_verts, 0, sizeof(float) * 3 * V, s) != cudaSuccess) return HR_ERR_CUDA;
   }
   if (edges) {
+    tm.begin(kTimeBwdSil);
     int rc = launch_silhouettes(ctx, m, verts, cams, N, ctx->sil, ctx->lim.max_E, ctx->sil_count, s);
     if (rc != HR_OK) return rc;
+    tm.end(kTimeBwdSil);
     long long n = (long long)N * o->edge_samples;
     auto kern = st ? k_edge_samples<true> : k_edge_samples<false>;
+    tm.begin(kTimeBwdEdges);
     kern<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count,
                                                      o->edge_samples, o->edge_eps_px, d_verts,
                                                      ctx->stats + 2 * kStatsPer);
     HR_CHECK_LAUNCH();
+    tm.end(kTimeBwdEdges);
   }
   if (normals) {
+    tm.begin(kTimeBwdNormals);
     k_normal_dm<<<(V + 255) / 256, 256, 0, s>>>(ctx->normals, ctx->normal_len, ctx->dN, V, ctx->dm);
     HR_CHECK_LAUNCH();
     k_normal_gather<<<(V + 255) / 256, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, ctx->dm, V, d_verts);
     HR_CHECK_LAUNCH();
+    tm.end(kTimeBwdNormals);
   }
+  if (tm.on) ctx->ev_ready |= 2 | (interior ? 4 : 0) | (edges ? 8 : 0) | (normals ? 16 : 0);
   return HR_OK;
 }
 

@@ -113,10 +113,10 @@ class HandRenderLoss(torch.autograd.Function):
 # Synthetic multiframes
 # --------------------------------------------------------------------------------------
 
-def opts_for(cfg: I.SceneConfig, spp=None, seed=None, iter=0):
+def opts_for(cfg: I.SceneConfig, spp=None, seed=None, iter=0, iter_dev=None):
     return B.render_opts(seed=cfg.seed * 7919 + 17 if seed is None else seed, iter=iter, spp=spp or cfg.spp,
                          edge_samples=cfg.edge_samples, ka=I.K_AMBIENT, kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR,
-                         light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX)
+                         light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX, iter_dev=iter_dev)
 
 
 def make_views(cfg: I.SceneConfig, model: B.Model, x_gt, device="cuda", ctx=None):

@@ -1,0 +1,138 @@
+"""C-ABI behaviour on the GPU: the device iteration counter, the device-counted
+Adam step, CUDA-graph replay of a whole iteration, and device-detected errors
+reported through the status word (never a trap)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from tests.gpu_common import hand, require_gpu, scene, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    require_gpu()
+    from paper_2107_05509_gb300 import binding
+    return binding
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def test_iter_dev_matches_host_iter(B):
+    sc = scene("tiny")
+    h = hand()
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, sc.N, sc.W, sc.H)
+    vt = _t(sc.verts)
+    B.hr_build_bvh(ctx, model, vt)
+    img_a = torch.empty((sc.N, sc.H, sc.W, 3), device="cuda")
+    img_b = torch.empty_like(img_a)
+    o = sc.opts(iter=7)
+    B.hr_render_fwd(ctx, model, vt, _t(sc.cams), sc.H, sc.W, _t(sc.bg), sc.gpu_opts(o), img_a)
+    counter = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    go = sc.gpu_opts(sc.opts(iter=0))
+    go.iter_dev = counter.data_ptr()
+    B.hr_render_fwd(ctx, model, vt, _t(sc.cams), sc.H, sc.W, _t(sc.bg), go, img_b)
+    assert torch.equal(img_a, img_b)
+    # a different iteration draws different samples
+    o8 = sc.opts(iter=8)
+    B.hr_render_fwd(ctx, model, vt, _t(sc.cams), sc.H, sc.W, _t(sc.bg), sc.gpu_opts(o8), img_b)
+    assert not torch.equal(img_a, img_b)
+    assert B.hr_get_status(ctx) == B.HR_OK
+
+
+def test_adam_step_dev_matches_host_step_and_advances(B):
+    rng = np.random.default_rng(0)
+    p0 = rng.normal(size=61).astype(np.float32)
+    gr = rng.normal(size=61).astype(np.float32)
+    pa, pb = _t(p0), _t(p0)
+    ma, va, mb, vb = (torch.zeros(61, device="cuda") for _ in range(4))
+    g = _t(gr)
+    counter = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for step in range(1, 4):
+        B.hr_adam_step(pa, g, ma, va, 0.01, 0.9, 0.999, 1e-8, step)
+        B.hr_adam_step_dev(pb, g, mb, vb, 0.01, 0.9, 0.999, 1e-8, counter)
+    torch.cuda.synchronize()
+    assert int(counter.item()) == 3
+    assert torch.allclose(pa, pb, rtol=0, atol=1e-6)
+
+
+def test_graph_replay_equals_eager_iteration(B):
+    from paper_2107_05509_gb300 import inputs as I
+    from paper_2107_05509_gb300 import pipeline as P
+    sc = scene("tiny")
+    h = hand()
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, sc.N, sc.W, sc.H)
+    views = P.Views(cams=_t(sc.cams), background=_t(sc.bg), observed=_t(sc.observed), mask=_t(sc.mask),
+                    H=sc.H, W=sc.W)
+    counter = torch.full((1,), 2, dtype=torch.int32, device="cuda")
+    opts = P.opts_for(sc.cfg, iter_dev=counter)
+    ref = P.Refiner(model, views, opts, ctx=ctx)
+    x = _t(sc.x0.astype(np.float32))
+    loss_e, grad_e = ref.step(x)
+    loss_e, grad_e = loss_e.clone(), grad_e.clone()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ref.step(x)
+    torch.cuda.current_stream().wait_stream(side)
+    with torch.cuda.graph(graph):
+        ref.step(x)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(ref.loss, loss_e)
+    assert torch.allclose(ref.d_params, grad_e, rtol=1e-5, atol=1e-7 * float(grad_e.abs().max()))
+    assert B.hr_get_status(ctx) == B.HR_OK
+    del I
+
+
+def test_nonfinite_params_reported_in_status(B):
+    h = hand()
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, 1, 8, 8)
+    x = np.zeros(61, np.float32)
+    x[12] = np.nan
+    v = torch.empty((h.V, 3), device="cuda")
+    B.hr_skin(ctx, model, _t(x), v)
+    assert B.hr_get_status(ctx) == B.HR_ERR_NONFINITE
+    assert B.hr_get_status(ctx) == B.HR_OK          # read clears the word
+
+
+def test_bad_face_index_reported_not_faulted(B):
+    h = hand()
+    model = B.Model(h)
+    bad = model.t["faces"].clone()
+    bad[5, 1] = h.V + 100                          # out of range: rejected by the build
+    model.struct.faces = bad.data_ptr()
+    ctx = B.Context(h.V, h.F, h.E, 1, 8, 8)
+    B.hr_build_bvh(ctx, model, _t(h.v_template))
+    assert B.hr_get_status(ctx) == B.HR_ERR_ARG
+    model.struct.faces = model.t["faces"].data_ptr()
+    B.hr_build_bvh(ctx, model, _t(h.v_template))
+    assert B.hr_get_status(ctx) == B.HR_OK
+
+
+def test_host_argument_errors(B):
+    h = hand()
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, 2, 16, 16)
+    img = torch.empty((3, 16, 16, 3), device="cuda")
+    cams = torch.zeros((3, 20), device="cuda")
+    bg = torch.zeros_like(img)
+    v = _t(h.v_template)
+    B.hr_build_bvh(ctx, model, v)
+    with pytest.raises(B.HandrtError) as e:           # 3 views > the context's 2
+        B.hr_render_fwd(ctx, model, v, cams, 16, 16, bg, B.render_opts(), img)
+    assert e.value.code == B.HR_ERR_ARG
+    with pytest.raises(B.HandrtError) as e:           # spp 0
+        B.hr_render_fwd(ctx, model, v, cams[:2], 16, 16, bg[:2], B.render_opts(spp=0), img[:2])
+    assert e.value.code == B.HR_ERR_ARG
+    lim = B.hr_limits(100000, 10, 10, 1, 8, 8)
+    hnd = ctypes.c_void_p()
+    assert B.lib().hr_context_create(ctypes.byref(lim), ctypes.byref(hnd)) == B.HR_ERR_UNSUPPORTED
