@@ -54,10 +54,15 @@ __global__ void __launch_bounds__(kLossThreads) k_mask_count(const uint8_t* __re
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
-  unsigned long long tot = 0;
-  for (int b = 0; b < (int)gridDim.x; ++b) tot += __ldcg(&counts[b]);
+  // the last block: each thread sums a strided set of block counts, then a fixed
+  // pairing tree (integer sums, exact in any order anyway)
+  unsigned long long part = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) part += __ldcg(&counts[b]);
+  __syncthreads();
+  unsigned long long tot = block_sum_u64(part, red);
+  if (threadIdx.x != 0) return;
   scale[0] = tot > 0 ? (float)(1.0 / (3.0 * (double)tot)) : 0.0f;
   *counter = 0u;
 }
@@ -125,11 +130,21 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_adjoint(const float* __re
     last = atomicAdd(counter, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last) return;
   __threadfence();
-  double tot = 0.0;
-  for (int b = 0; b < (int)gridDim.x; ++b) tot += (double)__ldcg(&partials[b]);
-  loss[0] = (float)(tot * (double)sc);
+  // the last block: thread i sums partials i, i + blockDim, ... in order (double),
+  // then a fixed pairing tree over the threads -- the same order on every call
+  __shared__ double dred[kLossThreads];
+  double part = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) part += (double)__ldcg(&partials[b]);
+  dred[threadIdx.x] = part;
+  __syncthreads();
+  for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+    if (threadIdx.x < w) dred[threadIdx.x] += dred[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  loss[0] = (float)(dred[0] * (double)sc);
   *counter = 0u;
 }
 

@@ -247,22 +247,6 @@ __device__ __forceinline__ void jitter(const RenderArgs& a, int view, int px, in
   u2 = u24(r.y);
 }
 
-// radiance through screen point (sx, sy) by per-ray traversal; a miss returns
-// background pixel (bx, by)
-template <bool STATS>
-__device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, int view, float sx, float sy, int bx,
-                                           int by, Counts& cnt) {
-  float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
-  float3 d = primary_dir(cam, sx, sy);
-  if (STATS) {
-    ++cnt.samples;
-    ++cnt.rays;
-  }
-  Hit h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
-  if (STATS) cnt.hits += h.tri >= 0;
-  if (h.tri >= 0) return shade(a, h);
-  return ld3(a.bg + 3 * (((size_t)view * a.H + by) * a.W + bx));
-}
 
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
@@ -444,6 +428,48 @@ __device__ __forceinline__ Hit closest_candidate(const RenderArgs& a, int off, i
     }
   }
   return h;
+}
+
+// closest hit among the pool candidates at `off` for one ray on its own (no warp
+// votes): candidates are sorted by nearest depth, so the first one farther than the
+// hit so far ends the search
+template <bool STATS>
+__device__ __forceinline__ Hit closest_candidate_1(const RenderArgs& a, int off, int K, float sx, float sy, float3 o,
+                                                   float3 d, Counts& cnt) {
+  Hit h{-1, INFINITY, 0.0f, 0.0f};
+  for (int c = 0; c < K; ++c) {
+    if (!in_range(a.status, off + c, 0, a.wk.pool_cap)) break;
+    const float zm = __ldg(&a.wk.z[off + c]);
+    if (h.t < zm - (1e-4f * fabsf(zm) + 1e-6f)) break;
+    const float4 bb = __ldg(&a.wk.bb[off + c]);
+    if (STATS) ++cnt.cands;
+    if (sx >= bb.x && sx <= bb.z && sy >= bb.y && sy <= bb.w) {
+      const int k = __ldg(&a.wk.rec[off + c]);
+      if (in_range(a.status, k, 0, a.max_visits - 1)) isect<STATS>(a.tris, k, o, d, h, cnt);
+    }
+  }
+  return h;
+}
+
+// radiance through screen point (sx, sy) of a sub-tile whose candidates are (off, K)
+// (K < 0: per-ray traversal); a miss returns background pixel (bx, by)
+template <bool STATS>
+__device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, int view, float sx, float sy, int bx,
+                                           int by, int off, int K, Counts& cnt) {
+  float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
+  float3 d = primary_dir(cam, sx, sy);
+  if (STATS) {
+    ++cnt.samples;
+    ++cnt.rays;
+  }
+  Hit h{-1, INFINITY, 0.0f, 0.0f};
+  if (K > 0)
+    h = closest_candidate_1<STATS>(a, off, K, sx, sy, o, d, cnt);
+  else if (K < 0)
+    h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
+  if (STATS) cnt.hits += h.tri >= 0;
+  if (h.tri >= 0) return shade(a, h);
+  return ld3(a.bg + 3 * (((size_t)view * a.H + by) * a.W + bx));
 }
 
 // Radiance sums of samples [s0, s1) of this lane's pixel (all lanes call it).
@@ -954,9 +980,15 @@ __global__ void k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoin
   int byp = (int)fminf(fmaxf(floorf(yp), 0.0f), (float)(a.H - 1));
   int bxm = (int)fminf(fmaxf(floorf(xm), 0.0f), (float)(a.W - 1));
   int bym = (int)fminf(fmaxf(floorf(ym), 0.0f), (float)(a.H - 1));
+  // the candidates of the sub-tile holding the centre pixel serve both offset rays:
+  // its frustum is padded by half a pixel and the offsets are far smaller
+  const int nsx = (a.W + kSubW - 1) / kSubW, nsy = (a.H + kSubH - 1) / kSubH;
+  const int st = view * nsx * nsy + (py / kSubH) * nsx + (px / kSubW);
+  int2 pk = a.wk.st[st];
+  if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
   Counts cnt;
-  float3 fp = radiance<STATS>(a, cam, view, xp, yp, bxp, byp, cnt);
-  float3 fm = radiance<STATS>(a, cam, view, xm, ym, bxm, bym, cnt);
+  float3 fp = radiance<STATS>(a, cam, view, xp, yp, bxp, byp, pk.x, pk.y, cnt);
+  float3 fm = radiance<STATS>(a, cam, view, xm, ym, bxm, bym, pk.x, pk.y, cnt);
   if (STATS) {
     unsigned v[kStatsPer] = {cnt.samples, cnt.rays, cnt.nodes, cnt.tris, cnt.hits, cnt.cands};
     for (int q = 0; q < kStatsPer; ++q)
@@ -1172,7 +1204,9 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
   const bool normals = !(o->flags & HR_BWD_NO_NORMALS) && interior;
   const bool st = o->flags & HR_STATS;
   Timer tm{ctx, s, (o->flags & HR_TIMING) != 0};
-  if (interior) {
+  if (interior || edges) {
+    // candidates of the sub-tiles with a non-zero adjoint: the interior shader's work
+    // items, and the edge rays' candidate lists
     if (cudaMemsetAsync(ctx->work_ctr, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
         cudaMemsetAsync(ctx->extra, 0, sizeof(float) * 6 * V, s) != cudaSuccess)
       return HR_ERR_CUDA;
@@ -1184,6 +1218,8 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
       k_gather<true, false><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdGather);
+  }
+  if (interior) {
     const size_t smem = render_bwd_smem(V);   // within the opt-in of configure_render_kernels
     auto kern = st ? k_shade_bwd<true> : k_shade_bwd<false>;
     const int blocks = ctx->num_sms * kBwdMinBlocks;

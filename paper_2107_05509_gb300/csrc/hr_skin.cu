@@ -104,44 +104,53 @@ struct ModelArgs {
   int V, J, K;
 };
 
-// one thread: the forward kinematic chain into shared memory
+// the forward kinematic chain into shared memory, called by every thread of the
+// block: per-joint work (shaped joint, local rotation) in parallel, then one thread
+// composes parents before children
 __device__ void build_chain(const ModelArgs& m, const float* __restrict__ params, Chain& ch, int* status) {
-  bool finite = true;
-  for (int i = 0; i < 61; ++i) finite = finite && isfinite(params[i]);
-  if (!finite) set_status(status, kStatusNonfinite);
-  for (int k = 0; k < m.K; ++k) ch.beta[k] = params[k];
-  for (int c = 0; c < 3; ++c) ch.tau[c] = params[58 + c];
-  for (int j = 0; j < m.J; ++j)
-    for (int c = 0; c < 3; ++c) {
-      float acc = m.j_template[3 * j + c];
-      for (int k = 0; k < m.K; ++k) acc += m.j_shapedirs[(3 * j + c) * m.K + k] * ch.beta[k];
-      ch.J[j][c] = acc;
-    }
-  for (int j = 0; j < m.J; ++j) {
+  const int tid = threadIdx.x;
+  if (tid < 61 && !isfinite(params[tid])) set_status(status, kStatusNonfinite);
+  if (tid < m.K) ch.beta[tid] = params[tid];
+  if (tid < 3) ch.tau[tid] = params[58 + tid];
+  __syncthreads();
+  if (tid < 3 * m.J) {
+    const int j = tid / 3, c = tid % 3;
+    float acc = m.j_template[3 * j + c];
+    for (int k = 0; k < m.K; ++k) acc += m.j_shapedirs[(3 * j + c) * m.K + k] * ch.beta[k];
+    ch.J[j][c] = acc;
+  }
+  if (tid >= 64 && tid < 64 + m.J) {
+    const int j = tid - 64;
     const float* r = (j == 0) ? params + 55 : params + 10 + 3 * (j - 1);
     float rr[3] = {r[0], r[1], r[2]};
     rodrigues(rr, ch.Rl[j]);
-    int p = m.parents[j];
-    if (p >= j || p < -1 || (j == 0) != (p < 0)) {   // parents must precede children; only joint 0 is a root
-      set_status(status, kStatusBadModel);
-      p = j == 0 ? -1 : 0;
-    }
-    if (p < 0) {
-      for (int i = 0; i < 9; ++i) ch.RG[j][i] = ch.Rl[j][i];
-      for (int c = 0; c < 3; ++c) ch.tG[j][c] = ch.J[j][c];
-    } else {
-      matmul3(ch.RG[p], ch.Rl[j], ch.RG[j]);
-      for (int a = 0; a < 3; ++a) {
-        float acc = ch.tG[p][a];
-        for (int b = 0; b < 3; ++b) acc += ch.RG[p][3 * a + b] * (ch.J[j][b] - ch.J[p][b]);
-        ch.tG[j][a] = acc;
-      }
-    }
-    for (int i = 0; i < 9; ++i) ch.RA[j][i] = ch.RG[j][i];
-    for (int a = 0; a < 3; ++a)
-      ch.tA[j][a] = ch.tG[j][a] -
-                    (ch.RG[j][3 * a] * ch.J[j][0] + ch.RG[j][3 * a + 1] * ch.J[j][1] + ch.RG[j][3 * a + 2] * ch.J[j][2]);
   }
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < m.J; ++j) {
+      int p = m.parents[j];
+      if (p >= j || p < -1 || (j == 0) != (p < 0)) {   // parents must precede children; only joint 0 is a root
+        set_status(status, kStatusBadModel);
+        p = j == 0 ? -1 : 0;
+      }
+      if (p < 0) {
+        for (int i = 0; i < 9; ++i) ch.RG[j][i] = ch.Rl[j][i];
+        for (int c = 0; c < 3; ++c) ch.tG[j][c] = ch.J[j][c];
+      } else {
+        matmul3(ch.RG[p], ch.Rl[j], ch.RG[j]);
+        for (int a = 0; a < 3; ++a) {
+          float acc = ch.tG[p][a];
+          for (int b = 0; b < 3; ++b) acc += ch.RG[p][3 * a + b] * (ch.J[j][b] - ch.J[p][b]);
+          ch.tG[j][a] = acc;
+        }
+      }
+      for (int i = 0; i < 9; ++i) ch.RA[j][i] = ch.RG[j][i];
+      for (int a = 0; a < 3; ++a)
+        ch.tA[j][a] = ch.tG[j][a] - (ch.RG[j][3 * a] * ch.J[j][0] + ch.RG[j][3 * a + 1] * ch.J[j][1] +
+                                     ch.RG[j][3 * a + 2] * ch.J[j][2]);
+    }
+  }
+  __syncthreads();
 }
 
 __device__ __forceinline__ float3 shaped_vertex(const ModelArgs& m, const Chain& ch, int v) {
@@ -158,8 +167,7 @@ __device__ __forceinline__ float3 shaped_vertex(const ModelArgs& m, const Chain&
 __global__ void __launch_bounds__(kSkinThreads) k_skin(ModelArgs m, const float* __restrict__ params,
                                                        float* __restrict__ verts, int* status) {
   __shared__ Chain ch;
-  if (threadIdx.x == 0) build_chain(m, params, ch, status);
-  __syncthreads();
+  build_chain(m, params, ch, status);
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < m.V; v += gridDim.x * blockDim.x) {
     float3 p = shaped_vertex(m, ch, v);
     float out[3] = {ch.tau[0], ch.tau[1], ch.tau[2]};
@@ -192,9 +200,8 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const fl
   __shared__ float bacc[kSkinAcc];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) build_chain(m, params, ch, status);
   for (int i = lane; i < kSkinAcc; i += 32) wacc[warp][i] = 0.0f;
-  __syncthreads();
+  build_chain(m, params, ch, status);
   const int nv_iter = (m.V + gridDim.x * blockDim.x - 1) / (gridDim.x * blockDim.x);
   for (int it = 0; it < nv_iter; ++it) {
     int v = (it * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
@@ -249,60 +256,66 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const fl
     bacc[i] = s;
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  *counter = 0u;
-  // chain backward (one thread)
-  float dRG[kMaxJ][9], dtG[kMaxJ][3], dJ[kMaxJ][3], dRl[kMaxJ][9];
-  for (int j = 0; j < m.J; ++j) {
-    const float* dRA = &bacc[12 * j];
-    const float* dtA = &bacc[12 * j + 9];
-    for (int a = 0; a < 3; ++a) {
-      for (int b = 0; b < 3; ++b) dRG[j][3 * a + b] = dRA[3 * a + b] - dtA[a] * ch.J[j][b];
-      dtG[j][a] = dtA[a];
-      dJ[j][a] = -(ch.RG[j][a] * dtA[0] + ch.RG[j][3 + a] * dtA[1] + ch.RG[j][6 + a] * dtA[2]);
+  // chain backward: one thread walks children before parents; the per-joint
+  // Rodrigues gradients and the shape gradient then run in parallel
+  __shared__ float sdRl[kMaxJ][9];
+  __shared__ float sdJ[kMaxJ][3];
+  if (threadIdx.x == 0) {
+    *counter = 0u;
+    float dRG[kMaxJ][9], dtG[kMaxJ][3];
+    for (int j = 0; j < m.J; ++j) {
+      const float* dRA = &bacc[12 * j];
+      const float* dtA = &bacc[12 * j + 9];
+      for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < 3; ++b) dRG[j][3 * a + b] = dRA[3 * a + b] - dtA[a] * ch.J[j][b];
+        dtG[j][a] = dtA[a];
+        sdJ[j][a] = -(ch.RG[j][a] * dtA[0] + ch.RG[j][3 + a] * dtA[1] + ch.RG[j][6 + a] * dtA[2]);
+      }
+    }
+    for (int j = m.J - 1; j >= 0; --j) {
+      int p = m.parents[j];
+      if (p >= j || p < -1 || (j == 0) != (p < 0)) p = j == 0 ? -1 : 0;   // reported by build_chain
+      if (p < 0) {
+        for (int i = 0; i < 9; ++i) sdRl[j][i] = dRG[j][i];
+        for (int a = 0; a < 3; ++a) sdJ[j][a] += dtG[j][a];
+        continue;
+      }
+      const float* Rp = ch.RG[p];
+      // dRl_j = Rp^T dRG_j
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+          sdRl[j][3 * a + b] = Rp[a] * dRG[j][b] + Rp[3 + a] * dRG[j][3 + b] + Rp[6 + a] * dRG[j][6 + b];
+      // dRG_p += dRG_j Rl_j^T + dtG_j (J_j - J_p)^T
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+          dRG[p][3 * a + b] += dRG[j][3 * a] * ch.Rl[j][3 * b] + dRG[j][3 * a + 1] * ch.Rl[j][3 * b + 1] +
+                               dRG[j][3 * a + 2] * ch.Rl[j][3 * b + 2] + dtG[j][a] * (ch.J[j][b] - ch.J[p][b]);
+      for (int a = 0; a < 3; ++a) {
+        float rt = Rp[a] * dtG[j][0] + Rp[3 + a] * dtG[j][1] + Rp[6 + a] * dtG[j][2];
+        dtG[p][a] += dtG[j][a];
+        sdJ[j][a] += rt;
+        sdJ[p][a] -= rt;
+      }
     }
   }
-  for (int j = m.J - 1; j >= 0; --j) {
-    int p = m.parents[j];
-    if (p >= j || p < -1 || (j == 0) != (p < 0)) p = j == 0 ? -1 : 0;   // reported by build_chain
-    if (p < 0) {
-      for (int i = 0; i < 9; ++i) dRl[j][i] = dRG[j][i];
-      for (int a = 0; a < 3; ++a) dJ[j][a] += dtG[j][a];
-      continue;
-    }
-    const float* Rp = ch.RG[p];
-    // dRl_j = Rp^T dRG_j
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b)
-        dRl[j][3 * a + b] = Rp[a] * dRG[j][b] + Rp[3 + a] * dRG[j][3 + b] + Rp[6 + a] * dRG[j][6 + b];
-    // dRG_p += dRG_j Rl_j^T + dtG_j (J_j - J_p)^T
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b)
-        dRG[p][3 * a + b] += dRG[j][3 * a] * ch.Rl[j][3 * b] + dRG[j][3 * a + 1] * ch.Rl[j][3 * b + 1] +
-                             dRG[j][3 * a + 2] * ch.Rl[j][3 * b + 2] + dtG[j][a] * (ch.J[j][b] - ch.J[p][b]);
-    for (int a = 0; a < 3; ++a) {
-      float rt = Rp[a] * dtG[j][0] + Rp[3 + a] * dtG[j][1] + Rp[6 + a] * dtG[j][2];
-      dtG[p][a] += dtG[j][a];
-      dJ[j][a] += rt;
-      dJ[p][a] -= rt;
-    }
-  }
-  float out[3];
-  float phi[3] = {params[55], params[56], params[57]};
-  rodrigues_grad(phi, dRl[0], out);
-  for (int c = 0; c < 3; ++c) dparams[55 + c] = out[c];
-  for (int j = 1; j < m.J; ++j) {
-    float r[3] = {params[10 + 3 * (j - 1)], params[11 + 3 * (j - 1)], params[12 + 3 * (j - 1)]};
-    rodrigues_grad(r, dRl[j], out);
-    for (int c = 0; c < 3; ++c) dparams[10 + 3 * (j - 1) + c] = out[c];
-  }
-  for (int k = 0; k < m.K; ++k) {
+  __syncthreads();
+  const int tid = threadIdx.x;
+  if (tid < m.J) {
+    const int j = tid;
+    const float* r = (j == 0) ? params + 55 : params + 10 + 3 * (j - 1);
+    float rr[3] = {r[0], r[1], r[2]}, out[3];
+    rodrigues_grad(rr, sdRl[j], out);
+    float* dst = (j == 0) ? dparams + 55 : dparams + 10 + 3 * (j - 1);
+    for (int c = 0; c < 3; ++c) dst[c] = out[c];
+  } else if (tid >= 32 && tid < 32 + m.K) {
+    const int k = tid - 32;
     float s = bacc[16 * 12 + k];
     for (int j = 0; j < m.J; ++j)
-      for (int c = 0; c < 3; ++c) s += m.j_shapedirs[(3 * j + c) * m.K + k] * dJ[j][c];
+      for (int c = 0; c < 3; ++c) s += m.j_shapedirs[(3 * j + c) * m.K + k] * sdJ[j][c];
     dparams[k] = s;
+  } else if (tid >= 64 && tid < 67) {
+    dparams[58 + tid - 64] = bacc[16 * 12 + 10 + tid - 64];
   }
-  for (int c = 0; c < 3; ++c) dparams[58 + c] = bacc[16 * 12 + 10 + c];
 }
 
 ModelArgs model_args(const hr_model* m) {
