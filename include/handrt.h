@@ -210,11 +210,86 @@ int hr_adam_step(float* params, const float* grad, float* m, float* v, int n, fl
  * call then advances *iter_dev by one (device uint32).  With the same counter given
  * to the render calls as hr_render_opts.iter_dev, a whole refinement iteration can
  * be replayed (for example from a CUDA graph) with fresh sample streams and correct
- * bias correction every time. */
+ * bias correction every time.  lr_scale (device float[scale_len], or NULL) gives
+ * entry i the step size lr * lr_scale[i % scale_len]: parameters of different units
+ * (radians, shape coefficients, metres) get their own step, and scale_len = 61
+ * repeats one scale over the instances of a batch. */
 int hr_adam_step_dev(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1,
-                     float beta2, float eps, uint32_t* iter_dev, hr_stream stream);
+                     float beta2, float eps, const float* lr_scale, int scale_len, uint32_t* iter_dev,
+                     hr_stream stream);
 
-/* Diagnostics over the context's current scene (used by the tests):
+/* Mean vertex error epsilon_v (Section 4.1: mean Euclidean distance between the
+ * vertices of the estimate and of the ground truth), per instance, in metres:
+ * out[row * n + i] = mean_v |verts[i][v] - ref[i][v]| for verts, ref device
+ * float[n][V][3].  row = *iter_dev when iter_dev (device uint32) is given, else 0;
+ * rows >= `rows` are not written (out: device float[rows][n]), so one call in a
+ * captured iteration records the error trajectory.  Summed in a fixed order. */
+int hr_vertex_error(const float* verts, const float* ref, int V, int n, float* out, const uint32_t* iter_dev,
+                    int rows, hr_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * Batches: many hand instances refined together.  Each instance has its own
+ * parameters, cameras, resolution (shared by its views), samples per pixel and edge
+ * samples per view; all share one hand model (topology, blendshapes, weights,
+ * albedo).  A batch context fixes that layout once; every batch call then runs all
+ * instances in ONE launch per kernel (skinning, one BVH build block per instance, the
+ * render kernels over all views' sub-tiles, per-instance loss reductions), so a whole
+ * iteration of all instances is a short fixed sequence of launches that a CUDA graph
+ * can capture.  Device arrays of a batch are the per-instance arrays concatenated in
+ * instance order:
+ *   params, d_params   float[n][61]
+ *   verts, d_verts     float[n][V][3]
+ *   cams               hr_camera[sum_i views_i], instance-major
+ *   images, background,
+ *   observed, adjoint  float[P][3], P = sum_i views_i H_i W_i; instance i's views are
+ *                      [N_i][H_i][W_i][3] starting at pixel pixel_offsets[i]
+ *   mask               uint8[P]
+ *   loss               float[n]
+ * Samples of instance i use hr_instance_desc.instance as the Philox instance field,
+ * so instance i renders exactly what a single-instance context renders with
+ * hr_render_opts.instance = that value, its spp and edge_samples (up to float32
+ * summation order in the backward).  Single-instance calls on a batch context, and
+ * batch calls on a single-instance context, return HR_ERR_ARG.
+ * --------------------------------------------------------------------------------- */
+typedef struct hr_instance_desc {
+    int32_t views;          /* N_i >= 1                                              */
+    int32_t width, height;  /* W_i, H_i of all its views                             */
+    int32_t spp;            /* primary samples per pixel, 1 .. 65536                 */
+    int32_t edge_samples;   /* silhouette-edge samples per view (>= 0)               */
+    uint32_t instance;      /* Philox instance field, < 65536                        */
+} hr_instance_desc;
+
+/* Create a batch context on the current CUDA device for the n instances of `desc`
+ * (host array).  limits->max_V, max_F, max_E bound the model as for
+ * hr_context_create (the view and image fields are not used).  All scratch is
+ * allocated here, once.  HR_ERR_ARG for invalid descriptors, HR_ERR_UNSUPPORTED for
+ * layouts beyond 2^27 sub-tiles of 8x4 pixels, HR_ERR_CUDA when an allocation fails.
+ * Destroy with hr_context_destroy. */
+int hr_batch_create(const hr_limits* limits, const hr_instance_desc* desc, int n, hr_context** out);
+
+/* Host copies of the layout: view_offsets[i] = first camera of instance i,
+ * pixel_offsets[i] = first pixel of instance i (host arrays of n + 1; the last
+ * entries are the totals). */
+int hr_batch_layout(hr_context* ctx, int32_t* view_offsets, int64_t* pixel_offsets);
+
+/* The single-instance calls above, over every instance of a batch.  opts supplies the
+ * seed, iteration (or iter_dev), shading, edge offset and flags; spp, edge_samples and
+ * the instance field come from the descriptors.  hr_loss_batch writes one loss per
+ * instance (each the mean over that instance's own masked pixel-channels). */
+int hr_skin_batch(hr_context* ctx, const hr_model* model, const float* params, float* verts, hr_stream stream);
+int hr_skin_bwd_batch(hr_context* ctx, const hr_model* model, const float* params, const float* d_verts,
+                      float* d_params, hr_stream stream);
+int hr_build_bvh_batch(hr_context* ctx, const hr_model* model, const float* verts, hr_stream stream);
+int hr_render_fwd_batch(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams,
+                        const float* background, const hr_render_opts* opts, float* image, hr_stream stream);
+int hr_loss_batch(hr_context* ctx, const float* image, const float* observed, const uint8_t* mask, float* loss,
+                  float* adjoint, hr_stream stream);
+int hr_render_bwd_batch(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams,
+                        const float* background, const hr_render_opts* opts, const float* adjoint, float* d_verts,
+                        hr_stream stream);
+
+/* Diagnostics over the context's current scene (used by the tests; on a batch
+ * context they see instance 0):
  *   hr_trace:        closest hit of n rays (origins, dirs: device float[n][3]) against
  *                    the last built BVH: tri (device int32[n], -1 = miss), tuv
  *                    (device float[n][3] = t, u, v);

@@ -35,7 +35,8 @@ KERNEL_TIMES = ("fwd_gather", "fwd_shade", "fwd_combine", "bwd_gather", "bwd_sha
 EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", "hr_build_bvh", "hr_render_fwd",
            "hr_loss", "hr_render_bwd", "hr_adam_step", "hr_trace", "hr_get_normals", "hr_silhouettes",
            "hr_get_stats", "hr_get_status", "hr_status_string", "hr_skin_bwd_noalloc", "hr_kernel_times",
-           "hr_adam_step_dev")
+           "hr_adam_step_dev", "hr_vertex_error", "hr_batch_create", "hr_batch_layout", "hr_skin_batch",
+           "hr_skin_bwd_batch", "hr_build_bvh_batch", "hr_render_fwd_batch", "hr_loss_batch", "hr_render_bwd_batch")
 
 
 class HandrtError(RuntimeError):
@@ -56,6 +57,11 @@ class hr_render_opts(ctypes.Structure):
                 ("spp", ctypes.c_int32), ("edge_samples", ctypes.c_int32), ("ka", ctypes.c_float),
                 ("kd", ctypes.c_float), ("light_dir", ctypes.c_float * 3), ("light_rgb", ctypes.c_float * 3),
                 ("edge_eps_px", ctypes.c_float), ("flags", ctypes.c_uint32), ("iter_dev", ctypes.c_void_p)]
+
+
+class hr_instance_desc(ctypes.Structure):
+    _fields_ = [("views", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("spp", ctypes.c_int32), ("edge_samples", ctypes.c_int32), ("instance", ctypes.c_uint32)]
 
 
 class hr_limits(ctypes.Structure):
@@ -86,7 +92,16 @@ def lib():
             "hr_loss": [P, P, P, P, I, I, I, P, P, P],
             "hr_render_bwd": [P, P, P, P, I, I, I, P, P, P, P, P],
             "hr_adam_step": [P, P, P, P, I, F, F, F, F, I, P],
-            "hr_adam_step_dev": [P, P, P, P, I, F, F, F, F, P, P],
+            "hr_adam_step_dev": [P, P, P, P, I, F, F, F, F, P, I, P, P],
+            "hr_vertex_error": [P, P, I, I, P, P, I, P],
+            "hr_batch_create": [P, P, I, P],
+            "hr_batch_layout": [P, P, P],
+            "hr_skin_batch": [P, P, P, P, P],
+            "hr_skin_bwd_batch": [P, P, P, P, P, P],
+            "hr_build_bvh_batch": [P, P, P, P],
+            "hr_render_fwd_batch": [P, P, P, P, P, P, P, P],
+            "hr_loss_batch": [P, P, P, P, P, P, P],
+            "hr_render_bwd_batch": [P, P, P, P, P, P, P, P, P],
             "hr_trace": [P, P, P, I, P, P, P],
             "hr_get_normals": [P, P, P],
             "hr_silhouettes": [P, P, P, P, I, P, P, P],
@@ -155,6 +170,36 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+class Batch(Context):
+    """A batch context (hr_batch_create) for instances described by
+    (views, width, height, spp, edge_samples, instance) tuples; `view_offsets` and
+    `pixel_offsets` (numpy, n + 1 entries) locate each instance in the concatenated
+    camera and image arrays."""
+
+    def __init__(self, max_V, max_F, max_E, descs):
+        lim = hr_limits(max_V, max_F, max_E, 0, 0, 0)
+        n = len(descs)
+        arr = (hr_instance_desc * n)(*[hr_instance_desc(*map(int, d)) for d in descs])
+        h = ctypes.c_void_p()
+        _check("hr_batch_create", lib().hr_batch_create(ctypes.byref(lim), arr, n, ctypes.byref(h)))
+        self.handle = h
+        self.n = n
+        self.descs = [tuple(int(x) for x in d) for d in descs]
+        vo = (ctypes.c_int32 * (n + 1))()
+        po = (ctypes.c_int64 * (n + 1))()
+        _check("hr_batch_layout", lib().hr_batch_layout(h, vo, po))
+        self.view_offsets = np.array(vo[:], np.int64)
+        self.pixel_offsets = np.array(po[:], np.int64)
+
+    @property
+    def total_views(self):
+        return int(self.view_offsets[-1])
+
+    @property
+    def total_pixels(self):
+        return int(self.pixel_offsets[-1])
 
 
 class Model:
@@ -253,10 +298,59 @@ def hr_adam_step(params, grad, m, v, lr, beta1, beta2, eps, step, stream=None):
                                               beta2, eps, step, _stream(stream)))
 
 
-def hr_adam_step_dev(params, grad, m, v, lr, beta1, beta2, eps, iter_dev, stream=None):
+def hr_adam_step_dev(params, grad, m, v, lr, beta1, beta2, eps, iter_dev, lr_scale=None, stream=None):
+    """lr_scale: optional device float tensor; entry i steps by lr * lr_scale[i % len]."""
     assert iter_dev.dtype == torch.int32 and iter_dev.numel() == 1   # holds a uint32 counter
+    n_scale = 0 if lr_scale is None else lr_scale.numel()
     _check("hr_adam_step_dev", lib().hr_adam_step_dev(_f32(params), _f32(grad), _f32(m), _f32(v), params.numel(), lr,
-                                                      beta1, beta2, eps, _ptr(iter_dev), _stream(stream)))
+                                                      beta1, beta2, eps, None if lr_scale is None else _f32(lr_scale),
+                                                      n_scale, _ptr(iter_dev), _stream(stream)))
+
+
+def hr_vertex_error(verts, ref, out, iter_dev=None, stream=None):
+    """epsilon_v per instance (metres): verts, ref [n][V][3] (or [V][3]); out [rows][n],
+    row = *iter_dev (0 without a counter)."""
+    V = verts.shape[-2]
+    n = verts.numel() // (3 * V)
+    rows = out.numel() // n
+    _check("hr_vertex_error", lib().hr_vertex_error(_f32(verts), _f32(ref), V, n, _f32(out),
+                                                    None if iter_dev is None else _ptr(iter_dev), rows,
+                                                    _stream(stream)))
+
+
+# batches (hr_batch_create): concatenated per-instance arrays, see include/handrt.h
+
+def hr_skin_batch(ctx, model, params, verts, stream=None):
+    _check("hr_skin_batch", lib().hr_skin_batch(ctx.handle, ctypes.byref(model.struct), _f32(params), _f32(verts),
+                                                _stream(stream)))
+
+
+def hr_skin_bwd_batch(ctx, model, params, d_verts, d_params, stream=None):
+    _check("hr_skin_bwd_batch", lib().hr_skin_bwd_batch(ctx.handle, ctypes.byref(model.struct), _f32(params),
+                                                        _f32(d_verts), _f32(d_params), _stream(stream)))
+
+
+def hr_build_bvh_batch(ctx, model, verts, stream=None):
+    _check("hr_build_bvh_batch", lib().hr_build_bvh_batch(ctx.handle, ctypes.byref(model.struct), _f32(verts),
+                                                          _stream(stream)))
+
+
+def hr_render_fwd_batch(ctx, model, verts, cams, background, opts, image, stream=None):
+    _check("hr_render_fwd_batch", lib().hr_render_fwd_batch(ctx.handle, ctypes.byref(model.struct), _f32(verts),
+                                                            _f32(cams), _f32(background), ctypes.byref(opts),
+                                                            _f32(image), _stream(stream)))
+
+
+def hr_loss_batch(ctx, image, observed, mask, loss, adjoint, stream=None):
+    assert mask.dtype == torch.uint8
+    _check("hr_loss_batch", lib().hr_loss_batch(ctx.handle, _f32(image), _f32(observed), _ptr(mask), _f32(loss),
+                                                _f32(adjoint), _stream(stream)))
+
+
+def hr_render_bwd_batch(ctx, model, verts, cams, background, opts, adjoint, d_verts, stream=None):
+    _check("hr_render_bwd_batch", lib().hr_render_bwd_batch(ctx.handle, ctypes.byref(model.struct), _f32(verts),
+                                                            _f32(cams), _f32(background), ctypes.byref(opts),
+                                                            _f32(adjoint), _f32(d_verts), _stream(stream)))
 
 
 def hr_trace(ctx, origins, dirs, tri, tuv, stream=None):

@@ -33,12 +33,14 @@ bool dev_alloc(T** p, size_t count, Alloc& list) {
 void free_ctx(Context* c) {
   for (int i = 0; i < 2 * hr::kTimeSlots; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
-  void* ptrs[] = {c->nodes, c->tris,          c->normals,      c->normal_len, c->partials,
-                  c->dN,    c->dm,            c->sil,          c->sil_count,  c->loss_partials,
-                  c->counters, c->skin_partials, c->status, c->keys, c->parent, c->stats, c->tile_counters,
-                  c->pool_bb, c->pool_z, c->pool_rec, c->st_info, c->items, c->item_part, c->extra, c->work_ctr};
+  void* ptrs[] = {c->nodes,   c->tris,    c->normals,   c->normal_len, c->partials,      c->dN,
+                  c->dm,      c->sil,     c->sil_count, c->loss_partials, c->counters,   c->skin_partials,
+                  c->status,  c->stats,   c->pool_bb,   c->pool_z,     c->pool_rec,      c->st_info,
+                  c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  delete[] c->hvt;
+  delete[] c->hit;
   delete c;
 }
 
@@ -59,23 +61,21 @@ bool image_ok(const Context* c, int N, int H, int W) {
   return N >= 1 && H >= 1 && W >= 1 && N <= c->lim.max_views && W <= c->lim.max_width && H <= c->lim.max_height;
 }
 
-}  // namespace
+bool limits_ok(const hr_limits* lim, bool batch) {
+  if (lim->max_V <= 0 || lim->max_F <= 0 || lim->max_E <= 0) return false;
+  if (batch) return true;
+  return lim->max_views > 0 && lim->max_width > 0 && lim->max_height > 0;
+}
 
-extern "C" {
-
-int hr_context_create(const hr_limits* lim, hr_context** out) {
-  if (!lim || !out) return HR_ERR_ARG;
-  *out = nullptr;
-  if (lim->max_V <= 0 || lim->max_F <= 0 || lim->max_E <= 0 || lim->max_views <= 0 || lim->max_width <= 0 ||
-      lim->max_height <= 0)
-    return HR_ERR_ARG;
-  if (lim->max_V > 8192 || lim->max_F > 8192 || lim->max_views > 65535 || lim->max_width > 16384 ||
-      lim->max_height > 16384 || (long long)lim->max_views * lim->max_width * lim->max_height > (1ll << 31) / 3)
-    return HR_ERR_UNSUPPORTED;
+// Allocate a context for `n` instances whose views hold `views` views, `subtiles`
+// sub-tiles and `items` work-item slots in all (single instance: the limits' maxima).
+int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_t items, int loss_blocks,
+               Context** out) {
   Context* c = new (std::nothrow) Context();
   if (!c) return HR_ERR_CUDA;
   std::memset(c, 0, sizeof(Context));
   c->lim = *lim;
+  c->n_inst = n;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     delete c;
     return HR_ERR_CUDA;
@@ -85,26 +85,28 @@ int hr_context_create(const hr_limits* lim, hr_context** out) {
     return HR_ERR_CUDA;
   }
   Alloc a;
-  const size_t V = lim->max_V, F = lim->max_F;
-  const size_t subtiles = (size_t)hr::subtiles_for(lim->max_views, lim->max_width, lim->max_height);
+  const size_t V = lim->max_V, F = lim->max_F, ni = (size_t)n;
   c->pool_cap = (int)std::min<size_t>((size_t)1 << 28, 16 * subtiles + 4096);
-  c->item_cap = (int)std::min<size_t>((size_t)1 << 26, 2 * subtiles + 1024);
-  bool ok = dev_alloc(&c->nodes, F, a) && dev_alloc(&c->tris, 3 * F, a) && dev_alloc(&c->normals, 3 * V, a) &&
-            dev_alloc(&c->normal_len, V, a) && dev_alloc(&c->partials, (size_t)c->render_blocks * 6 * V, a) &&
-            dev_alloc(&c->dN, 3 * V, a) && dev_alloc(&c->dm, 3 * V, a) &&
-            dev_alloc(&c->sil, (size_t)lim->max_views * lim->max_E, a) &&
-            dev_alloc(&c->sil_count, (size_t)lim->max_views, a) &&
-            dev_alloc(&c->loss_partials, (size_t)4 * hr::kLossBlocks + 8, a) && dev_alloc(&c->counters, 8, a) &&
-            dev_alloc(&c->skin_partials, (size_t)hr::kSkinBlocks * hr::kSkinAcc, a) && dev_alloc(&c->status, 1, a) && dev_alloc(&c->stats, 3 * hr::kStatsPer, a) &&
-            dev_alloc(&c->tile_counters, 4, a) && dev_alloc(&c->pool_bb, c->pool_cap, a) &&
-            dev_alloc(&c->pool_z, c->pool_cap, a) && dev_alloc(&c->pool_rec, c->pool_cap, a) &&
-            dev_alloc(&c->st_info, subtiles, a) && dev_alloc(&c->items, c->item_cap, a) &&
-            dev_alloc(&c->item_part, (size_t)c->item_cap * 32, a) && dev_alloc(&c->extra, 6 * V, a) &&
-            dev_alloc(&c->work_ctr, 4, a);
-  if (ok) ok = cudaMemset(c->counters, 0, 8 * sizeof(unsigned)) == cudaSuccess &&
+  c->item_cap = (int)items;
+  c->loss_blocks = loss_blocks;
+  const size_t partial_blocks = n == 1 ? (size_t)c->render_blocks : 1;   // single-instance backward only
+  const size_t nviews = views;
+  bool ok = dev_alloc(&c->nodes, ni * F, a) && dev_alloc(&c->tris, ni * 3 * F, a) &&
+            dev_alloc(&c->normals, ni * 3 * V, a) && dev_alloc(&c->normal_len, ni * V, a) &&
+            dev_alloc(&c->partials, partial_blocks * 6 * V, a) && dev_alloc(&c->dN, ni * 3 * V, a) &&
+            dev_alloc(&c->dm, ni * 3 * V, a) && dev_alloc(&c->sil, nviews * lim->max_E, a) &&
+            dev_alloc(&c->sil_count, nviews, a) &&
+            dev_alloc(&c->loss_partials, ni * hr::kLossStride(c->loss_blocks), a) &&
+            dev_alloc(&c->counters, ni * 4, a) && dev_alloc(&c->skin_partials, ni * hr::kSkinBlocks * hr::kSkinAcc, a) &&
+            dev_alloc(&c->status, 1, a) && dev_alloc(&c->stats, 3 * hr::kStatsPer, a) &&
+            dev_alloc(&c->pool_bb, c->pool_cap, a) && dev_alloc(&c->pool_z, c->pool_cap, a) &&
+            dev_alloc(&c->pool_rec, c->pool_cap, a) && dev_alloc(&c->st_info, subtiles, a) &&
+            dev_alloc(&c->items, c->item_cap, a) && dev_alloc(&c->item_part, (size_t)c->item_cap * 32, a) &&
+            dev_alloc(&c->extra, ni * 6 * V, a) && dev_alloc(&c->work_ctr, 2 + 2 * ni, a);
+  if (ok) ok = cudaMemset(c->counters, 0, ni * 4 * sizeof(unsigned)) == cudaSuccess &&
                cudaMemset(c->status, 0, sizeof(int)) == cudaSuccess &&
                cudaMemset(c->stats, 0, 3 * hr::kStatsPer * sizeof(unsigned long long)) == cudaSuccess &&
-               cudaMemset(c->nodes, 0, F * sizeof(hr::Node)) == cudaSuccess;
+               cudaMemset(c->nodes, 0, ni * F * sizeof(hr::Node)) == cudaSuccess;
   for (int i = 0; ok && i < 2 * hr::kTimeSlots; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
   // kernel attributes are set here, once, so that the per-iteration calls are only
   // launches and asynchronous memsets
@@ -114,7 +116,126 @@ int hr_context_create(const hr_limits* lim, hr_context** out) {
     free_ctx(c);
     return HR_ERR_CUDA;
   }
+  *out = c;
+  return HR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hr_context_create(const hr_limits* lim, hr_context** out) {
+  if (!lim || !out) return HR_ERR_ARG;
+  *out = nullptr;
+  if (!limits_ok(lim, false)) return HR_ERR_ARG;
+  if (lim->max_V > 8192 || lim->max_F > 8192 || lim->max_views > 65535 || lim->max_width > 16384 ||
+      lim->max_height > 16384 || (long long)lim->max_views * lim->max_width * lim->max_height > (1ll << 31) / 3)
+    return HR_ERR_UNSUPPORTED;
+  const size_t subtiles = (size_t)hr::subtiles_for(lim->max_views, lim->max_width, lim->max_height);
+  Context* c = nullptr;
+  int rc = create_ctx(lim, 1, (size_t)lim->max_views, subtiles,
+                      std::min<size_t>((size_t)1 << 26, 2 * subtiles + 1024), hr::kLossBlocks, &c);
+  if (rc != HR_OK) return rc;
   *out = reinterpret_cast<hr_context*>(c);
+  return HR_OK;
+}
+
+int hr_batch_create(const hr_limits* lim, const hr_instance_desc* desc, int n, hr_context** out) {
+  if (!lim || !desc || !out || n < 1) return HR_ERR_ARG;
+  *out = nullptr;
+  if (!limits_ok(lim, true)) return HR_ERR_ARG;
+  if (lim->max_V > 8192 || lim->max_F > 8192 || n > 65536) return HR_ERR_UNSUPPORTED;
+  long long views = 0, subtiles = 0, pixels = 0, items = 0;
+  for (int i = 0; i < n; ++i) {
+    const hr_instance_desc& d = desc[i];
+    if (d.views < 1 || d.width < 1 || d.height < 1 || d.spp < 1 || d.spp > 65536 || d.edge_samples < 0)
+      return HR_ERR_ARG;
+    if (d.views > 65535 || d.width > 16384 || d.height > 16384 || d.instance > 65535u) return HR_ERR_UNSUPPORTED;
+    const long long st = (long long)d.views * hr::subtiles_for(1, d.width, d.height);
+    views += d.views;
+    subtiles += st;
+    pixels += (long long)d.views * d.width * d.height;
+    items += 2 * st + 64;
+  }
+  if (subtiles > (1ll << 27) || items > (1ll << 28) || views > (1ll << 24)) return HR_ERR_UNSUPPORTED;
+  hr::ViewRec* hv = new (std::nothrow) hr::ViewRec[views];
+  hr::InstRec* hi = new (std::nothrow) hr::InstRec[n];
+  if (!hv || !hi) {
+    delete[] hv;
+    delete[] hi;
+    return HR_ERR_CUDA;
+  }
+  int g = 0, st0 = 0, ib = 0, max_ne = 0;
+  long long pix0 = 0;
+  bool vec = true;
+  for (int i = 0; i < n; ++i) {
+    const hr_instance_desc& d = desc[i];
+    hr::InstRec& r = hi[i];
+    r.view0 = g;
+    r.nviews = d.views;
+    r.pix0 = pix0;
+    r.ctr1_hi = d.instance << 16;
+    r.spp = d.spp;
+    r.ne = d.edge_samples;
+    r.st0 = st0;
+    const int per_view = hr::subtiles_for(1, d.width, d.height);
+    r.nst = d.views * per_view;
+    r.ibase = ib;
+    r.icap = 2 * r.nst + 64;
+    ib += r.icap;
+    vec = vec && (pix0 % 4) == 0;
+    for (int v = 0; v < d.views; ++v, ++g) {
+      hr::ViewRec& w = hv[g];
+      w.inst = i;
+      w.ctr1 = (uint32_t)v | (d.instance << 16);
+      w.H = d.height;
+      w.W = d.width;
+      w.spp = d.spp;
+      w.ne = d.edge_samples;
+      w.st0 = st0;
+      w.nsx = hr::subtile_columns(d.width);
+      w.pix0 = pix0;
+      st0 += per_view;
+      pix0 += (long long)d.width * d.height;
+    }
+    r.npix = pix0 - r.pix0;
+    max_ne = std::max(max_ne, d.edge_samples);
+  }
+  Context* c = nullptr;
+  int rc = create_ctx(lim, n, (size_t)views, (size_t)subtiles, (size_t)items, hr::kLossBlocksBatch, &c);
+  if (rc != HR_OK) {
+    delete[] hv;
+    delete[] hi;
+    return rc;
+  }
+  c->hvt = hv;
+  c->hit = hi;
+  c->nviews = (int)views;
+  c->total_st = (int)subtiles;
+  c->total_pix = pixels;
+  c->max_ne = max_ne;
+  c->loss_vec = vec;
+  if (cudaMalloc(reinterpret_cast<void**>(&c->vt), sizeof(hr::ViewRec) * views) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&c->it), sizeof(hr::InstRec) * n) != cudaSuccess ||
+      cudaMemcpy(c->vt, hv, sizeof(hr::ViewRec) * views, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->it, hi, sizeof(hr::InstRec) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    free_ctx(c);
+    return HR_ERR_CUDA;
+  }
+  *out = reinterpret_cast<hr_context*>(c);
+  return HR_OK;
+}
+
+int hr_batch_layout(hr_context* ctx, int32_t* view_offsets, int64_t* pixel_offsets) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !c->vt || !view_offsets || !pixel_offsets) return HR_ERR_ARG;
+  for (int i = 0; i < c->n_inst; ++i) {
+    view_offsets[i] = c->hit[i].view0;
+    pixel_offsets[i] = c->hit[i].pix0;
+  }
+  view_offsets[c->n_inst] = c->nviews;
+  pixel_offsets[c->n_inst] = c->total_pix;
   return HR_OK;
 }
 
@@ -128,27 +249,27 @@ int hr_context_destroy(hr_context* ctx) {
 
 int hr_skin(hr_context* ctx, const hr_model* model, const float* params, float* verts, hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
-  if (!c || !model_ok(model, c) || !params || !verts) return HR_ERR_ARG;
+  if (!c || c->vt || !model_ok(model, c) || !params || !verts) return HR_ERR_ARG;
   return hr::launch_skin(c, model, params, verts, (cudaStream_t)stream);
 }
 
 int hr_skin_bwd(hr_context* ctx, const hr_model* model, const float* params, const float* d_verts, float* d_params,
                 hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
-  if (!c || !model_ok(model, c) || !params || !d_verts || !d_params) return HR_ERR_ARG;
+  if (!c || c->vt || !model_ok(model, c) || !params || !d_verts || !d_params) return HR_ERR_ARG;
   return hr::launch_skin_bwd(c, model, params, d_verts, d_params, (cudaStream_t)stream);
 }
 
 int hr_build_bvh(hr_context* ctx, const hr_model* model, const float* verts, hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
-  if (!c || !model_ok(model, c) || !verts) return HR_ERR_ARG;
+  if (!c || c->vt || !model_ok(model, c) || !verts) return HR_ERR_ARG;
   return hr::launch_build_bvh(c, model, verts, (cudaStream_t)stream);
 }
 
 int hr_render_fwd(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams, int N, int H,
                   int W, const float* background, const hr_render_opts* opts, float* image, hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
-  if (!c || !model_ok(model, c) || !verts || !cams || !background || !image || !opts_ok(opts) ||
+  if (!c || c->vt || !model_ok(model, c) || !verts || !cams || !background || !image || !opts_ok(opts) ||
       !image_ok(c, N, H, W))
     return HR_ERR_ARG;
   if (c->F != model->F || c->V != model->V) return HR_ERR_ARG;  // hr_build_bvh first
@@ -159,7 +280,7 @@ int hr_render_fwd(hr_context* ctx, const hr_model* model, const float* verts, co
 int hr_loss(hr_context* ctx, const float* image, const float* observed, const uint8_t* mask, int N, int H, int W,
             float* loss, float* adjoint, hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
-  if (!c || !image || !observed || !mask || !loss || !adjoint || !image_ok(c, N, H, W)) return HR_ERR_ARG;
+  if (!c || c->vt || !image || !observed || !mask || !loss || !adjoint || !image_ok(c, N, H, W)) return HR_ERR_ARG;
   return hr::launch_loss(c, image, observed, mask, (long long)N * H * W, loss, adjoint, (cudaStream_t)stream);
 }
 
@@ -167,12 +288,68 @@ int hr_render_bwd(hr_context* ctx, const hr_model* model, const float* verts, co
                   int W, const float* background, const hr_render_opts* opts, const float* adjoint, float* d_verts,
                   hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
-  if (!c || !model_ok(model, c) || !verts || !cams || !background || !adjoint || !d_verts || !opts_ok(opts) ||
-      !image_ok(c, N, H, W))
+  if (!c || c->vt || !model_ok(model, c) || !verts || !cams || !background || !adjoint || !d_verts ||
+      !opts_ok(opts) || !image_ok(c, N, H, W))
     return HR_ERR_ARG;
   if (c->F != model->F || c->V != model->V) return HR_ERR_ARG;
   return hr::launch_render_bwd(c, model, verts, reinterpret_cast<const Cam*>(cams), N, H, W, background, opts,
                                adjoint, d_verts, (cudaStream_t)stream);
+}
+
+// ---- batches: the same steps over every instance of a batch context, one launch each
+int hr_skin_batch(hr_context* ctx, const hr_model* model, const float* params, float* verts, hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !c->vt || !model_ok(model, c) || !params || !verts) return HR_ERR_ARG;
+  return hr::launch_skin(c, model, params, verts, (cudaStream_t)stream);
+}
+
+int hr_skin_bwd_batch(hr_context* ctx, const hr_model* model, const float* params, const float* d_verts,
+                      float* d_params, hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !c->vt || !model_ok(model, c) || !params || !d_verts || !d_params) return HR_ERR_ARG;
+  return hr::launch_skin_bwd(c, model, params, d_verts, d_params, (cudaStream_t)stream);
+}
+
+int hr_build_bvh_batch(hr_context* ctx, const hr_model* model, const float* verts, hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !c->vt || !model_ok(model, c) || !verts) return HR_ERR_ARG;
+  return hr::launch_build_bvh(c, model, verts, (cudaStream_t)stream);
+}
+
+int hr_render_fwd_batch(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams,
+                        const float* background, const hr_render_opts* opts, float* image, hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !c->vt || !model_ok(model, c) || !verts || !cams || !background || !image || !opts ||
+      !(opts->edge_eps_px > 0.0f))
+    return HR_ERR_ARG;
+  if (c->F != model->F || c->V != model->V) return HR_ERR_ARG;  // hr_build_bvh_batch first
+  return hr::launch_render_fwd(c, model, verts, reinterpret_cast<const Cam*>(cams), 0, 0, 0, background, opts,
+                               image, (cudaStream_t)stream);
+}
+
+int hr_loss_batch(hr_context* ctx, const float* image, const float* observed, const uint8_t* mask, float* loss,
+                  float* adjoint, hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !c->vt || !image || !observed || !mask || !loss || !adjoint) return HR_ERR_ARG;
+  return hr::launch_loss(c, image, observed, mask, c->total_pix, loss, adjoint, (cudaStream_t)stream);
+}
+
+int hr_render_bwd_batch(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams,
+                        const float* background, const hr_render_opts* opts, const float* adjoint, float* d_verts,
+                        hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !c->vt || !model_ok(model, c) || !verts || !cams || !background || !adjoint || !d_verts || !opts ||
+      !(opts->edge_eps_px > 0.0f))
+    return HR_ERR_ARG;
+  if (c->F != model->F || c->V != model->V) return HR_ERR_ARG;
+  return hr::launch_render_bwd(c, model, verts, reinterpret_cast<const Cam*>(cams), 0, 0, 0, background, opts,
+                               adjoint, d_verts, (cudaStream_t)stream);
+}
+
+int hr_vertex_error(const float* verts, const float* ref, int V, int n, float* out, const uint32_t* iter_dev,
+                    int rows, hr_stream stream) {
+  if (!verts || !ref || !out || V < 1 || n < 1 || rows < 1) return HR_ERR_ARG;
+  return hr::launch_vertex_error(verts, ref, V, n, out, iter_dev, rows, (cudaStream_t)stream);
 }
 
 int hr_adam_step(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
@@ -184,11 +361,12 @@ int hr_adam_step(float* params, const float* grad, float* m, float* v, int n, fl
 }
 
 int hr_adam_step_dev(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
-                     float eps, uint32_t* iter_dev, hr_stream stream) {
+                     float eps, const float* lr_scale, int scale_len, uint32_t* iter_dev, hr_stream stream) {
   if (!params || !grad || !m || !v || !iter_dev || n <= 0 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
-      !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+      !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) || (lr_scale && scale_len < 1))
     return HR_ERR_ARG;
-  return hr::launch_adam_dev(params, grad, m, v, n, lr, beta1, beta2, eps, iter_dev, (cudaStream_t)stream);
+  return hr::launch_adam_dev(params, grad, m, v, n, lr, beta1, beta2, eps, lr_scale, scale_len, iter_dev,
+                             (cudaStream_t)stream);
 }
 
 int hr_trace(hr_context* ctx, const float* origins, const float* dirs, int n, int32_t* tri, float* tuv,

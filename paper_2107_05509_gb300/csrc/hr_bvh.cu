@@ -2,14 +2,18 @@
 // (Karras, "Maximizing parallelism in the construction of BVHs, octrees, and k-d
 // trees", HPG 2012) and the area-weighted unit vertex normals used for shading.
 //
-// The whole build runs in ONE thread block: at a hand's size (1.5k triangles) it
-// is latency-bound, and one block keeps every phase in shared memory with only
+// Each instance's build runs in ONE thread block (a batch builds all instances in
+// one launch, one block each): at a hand's size (1.5k triangles) a build is
+// latency-bound, and one block keeps every phase in shared memory with only
 // __syncthreads between phases -- centroid bounds, 30-bit Morton codes, a bitonic
 // sort of (code << 32 | triangle id) keys (unique, so the hierarchy has no
 // duplicate-key special case), the hierarchy, then a bottom-up refit in which the
 // second child to arrive at a node (atomic counter in shared memory) writes the
-// union box into the parent.  Leaf boxes are padded so that the float32 slab test
-// can never reject a ray that the float32 Moller-Trumbore test would accept.
+// union box into the parent.  When the nodes fit next to the keys (F up to ~2400) the
+// hierarchy and the refit run on a shared-memory copy of the nodes that is written
+// out once at the end, so the refit's dependent loads cost shared-memory latency.
+// Leaf boxes are padded so that the float32 slab test can never reject a ray that
+// the float32 Moller-Trumbore test would accept.
 #include <cstdio>
 
 #include "hr_internal.h"
@@ -19,6 +23,7 @@ namespace hr {
 namespace {
 
 constexpr int kBuildThreads = 1024;
+constexpr int kBuildSmemCap = 200 * 1024;   // opt-in of k_build_bvh
 
 __device__ __forceinline__ unsigned expand_bits10(unsigned v) {
   v = (v * 0x00010001u) & 0xFF0000FFu;
@@ -67,15 +72,27 @@ __device__ __forceinline__ Box load_union(const Node* nodes, int p) {
   return b;
 }
 
-// shared memory: keys [P] u64, parent [2F] int, visit flags [F] int
-__global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __restrict__ verts,
+// shared memory: keys [P] u64, parent [2F] int, visit flags [F] int, then (when
+// `snodes`) the max(F - 1, 1) nodes.  One block per instance: blockIdx.x selects the instance's
+// vertices ([V][3] at blockIdx.x * 3V), nodes ([node_stride] per instance) and
+// triangle records ([3 node_stride] float4 per instance).
+__global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __restrict__ verts_all,
                                                              const int* __restrict__ faces, int F, int V, int P,
-                                                             Node* __restrict__ nodes, float4* __restrict__ tris,
-                                                             int* status) {
+                                                             int node_stride, bool snodes,
+                                                             Node* __restrict__ nodes_all,
+                                                             float4* __restrict__ tris_all, int* status) {
   extern __shared__ unsigned long long smem_keys[];
   unsigned long long* keys = smem_keys;
   int* parent = reinterpret_cast<int*>(keys + P);
   int* flags = parent + 2 * F;
+  const float* verts = verts_all + (size_t)blockIdx.x * 3 * V;
+  Node* gnodes = nodes_all + (size_t)blockIdx.x * node_stride;
+  float4* tris = tris_all + (size_t)blockIdx.x * 3 * node_stride;
+  // the node array the hierarchy and refit work on (16-byte aligned after flags)
+  Node* nodes = gnodes;
+  if (snodes)
+    nodes = reinterpret_cast<Node*>(reinterpret_cast<char*>(smem_keys) +
+                                    (((size_t)P * 8 + (size_t)3 * F * 4 + 15) & ~(size_t)15));
   __shared__ float red[6][32];
   __shared__ float bounds[6];
 
@@ -91,10 +108,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
   if (bad) {
     if (tid == 0) {
       set_status(status, kStatusBadModel);
-      nodes[0].d = make_int4(~0, ~0, 0, 0);   // a one-leaf tree over a degenerate record
-      nodes[0].a = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
-      nodes[0].b = make_float4(-1.0f, -1.0f, 1.0f, 1.0f);
-      nodes[0].c = make_float4(1.0f, -1.0f, -1.0f, -1.0f);
+      gnodes[0].d = make_int4(~0, ~0, 0, 0);   // a one-leaf tree over a degenerate record
+      gnodes[0].a = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
+      gnodes[0].b = make_float4(-1.0f, -1.0f, 1.0f, 1.0f);
+      gnodes[0].c = make_float4(1.0f, -1.0f, -1.0f, -1.0f);
       tris[0] = tris[1] = tris[2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     return;
@@ -248,15 +265,26 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
       p = gp;
     }
   }
+  if (snodes) {
+    __syncthreads();
+    const int nn = F > 1 ? F - 1 : 1;
+    const float4* src = reinterpret_cast<const float4*>(nodes);
+    float4* dst = reinterpret_cast<float4*>(gnodes);
+    for (int i = tid; i < 4 * nn; i += blockDim.x) dst[i] = src[i];
+  }
 }
 
 // Faces and the vertex->face table come from the caller: an index out of range is
 // reported in the status word and its face skipped.
-__global__ void k_vertex_normals(const float* __restrict__ verts, const int* __restrict__ faces,
+// Batched: blockIdx.y selects the instance ([V][3] vertices and normals, [V] lengths).
+__global__ void k_vertex_normals(const float* __restrict__ verts_all, const int* __restrict__ faces,
                                  const int* __restrict__ vf_off, const int* __restrict__ vf_faces, int V, int F,
-                                 float* __restrict__ normals, float* __restrict__ normal_len, int* status) {
+                                 float* __restrict__ normals_all, float* __restrict__ normal_len_all, int* status) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
+  const float* verts = verts_all + (size_t)blockIdx.y * 3 * V;
+  float* normals = normals_all + (size_t)blockIdx.y * 3 * V;
+  float* normal_len = normal_len_all + (size_t)blockIdx.y * V;
   float3 m = make_float3(0.0f, 0.0f, 0.0f);
   int k0 = vf_off[v], k1 = vf_off[v + 1];
   if (k0 < 0 || k1 < k0 || k1 > 3 * F) {
@@ -290,7 +318,8 @@ __global__ void k_vertex_normals(const float* __restrict__ verts, const int* __r
 }  // namespace
 
 int configure_bvh_kernels() {
-  if (cudaFuncSetAttribute(k_build_bvh, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_build_bvh, cudaFuncAttributeMaxDynamicSharedMemorySize, kBuildSmemCap) !=
+      cudaSuccess) {
     cudaGetLastError();
     return HR_ERR_CUDA;
   }
@@ -302,11 +331,16 @@ int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaSt
   int P = 1;
   while (P < F) P <<= 1;
   size_t smem = (size_t)P * 8 + (size_t)3 * F * 4;
-  if (smem > 200 * 1024) return HR_ERR_UNSUPPORTED;   // the opt-in set by configure_bvh_kernels
-  k_build_bvh<<<1, kBuildThreads, smem, s>>>(verts, m->faces, F, V, P, ctx->nodes, ctx->tris, ctx->status);
+  if (smem > (size_t)kBuildSmemCap) return HR_ERR_UNSUPPORTED;
+  const size_t with_nodes = ((smem + 15) & ~(size_t)15) + (size_t)(F > 1 ? F - 1 : 1) * sizeof(Node);
+  const bool snodes = with_nodes <= (size_t)kBuildSmemCap;
+  if (snodes) smem = with_nodes;
+  k_build_bvh<<<ctx->n_inst, kBuildThreads, smem, s>>>(verts, m->faces, F, V, P, ctx->lim.max_F, snodes,
+                                                       ctx->nodes, ctx->tris, ctx->status);
   HR_CHECK_LAUNCH();
-  k_vertex_normals<<<(V + 255) / 256, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, V, F, ctx->normals,
-                                                   ctx->normal_len, ctx->status);
+  k_vertex_normals<<<dim3((V + 255) / 256, ctx->n_inst), 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces,
+                                                                      V, F, ctx->normals, ctx->normal_len,
+                                                                      ctx->status);
   HR_CHECK_LAUNCH();
   ctx->V = V;
   ctx->F = F;

@@ -38,44 +38,75 @@ struct Node {
   int4 d;
 };
 
+// Batch layout (hr_batch_create): instances of one hand model, each with its own
+// parameters, cameras, resolution, samples per pixel and edge samples.  Views are
+// numbered instance-major; sub-tiles and pixels are numbered view-major within that,
+// so every per-instance buffer is one contiguous range.
+struct ViewRec {
+  int inst;         // instance of this view
+  uint32_t ctr1;    // Philox counter word: view index within the instance | instance << 16
+  int H, W;
+  int spp;
+  int ne;           // edge samples of this view
+  int st0;          // first sub-tile of the view (global numbering)
+  int nsx;          // sub-tiles per row
+  long long pix0;   // first pixel of the view (global numbering)
+};
+struct InstRec {
+  int view0, nviews;   // global views [view0, view0 + nviews)
+  long long pix0, npix;
+  uint32_t ctr1_hi;    // Philox instance field << 16
+  int spp, ne;
+  int ibase, icap;     // the instance's region of the work-item table
+  int st0, nst;        // the instance's sub-tiles
+};
+
 struct Context {
   hr_limits lim;
+  // batch layout: n_inst == 1 and vt == nullptr for a single-instance context
+  int n_inst;
+  int nviews;
+  int total_st;
+  long long total_pix;
+  int max_ne;            // largest edge-sample count of a view
+  bool loss_vec;         // every instance's first pixel is a multiple of 4
+  ViewRec* vt;           // device [nviews]
+  InstRec* it;           // device [n_inst]
+  ViewRec* hvt;          // host copies
+  InstRec* hit;
   int device;
   int num_sms;
   int render_blocks;     // persistent grid of the render kernels
   int render_threads;
-  // scene
+  // scene, one per instance (per-instance arrays are [n_inst][...], contiguous)
   int V, F;              // sizes of the last hr_build_bvh
-  Node* nodes;           // [max_F]
-  float4* tris;          // [max_F][3]
-  float* normals;        // [max_V][3] unit vertex normals
-  float* normal_len;     // [max_V]    |m_v|
-  // BVH build scratch
-  unsigned long long* keys;  // [max_F]
-  int* parent;               // [2 max_F]
+  Node* nodes;           // [n_inst][max_F]
+  float4* tris;          // [n_inst][max_F][3]
+  float* normals;        // [n_inst][max_V][3] unit vertex normals
+  float* normal_len;     // [n_inst][max_V]    |m_v|
   // sub-tile candidate pool and work items of the render kernels
   float4* pool_bb;       // [pool_cap]
   float* pool_z;         // [pool_cap]
   int* pool_rec;         // [pool_cap]
   int pool_cap;
-  int2* st_info;         // [max_subtiles]
-  int4* items;           // [item_cap]
+  int2* st_info;         // [sub-tiles]
+  int4* items;           // [item_cap], one region per instance
   float4* item_part;     // [item_cap][32]
   int item_cap;
-  float* extra;          // [max_V][6]
-  unsigned* work_ctr;    // [4]
+  float* extra;          // [n_inst][max_V][6]
+  unsigned* work_ctr;    // [2 + 2 n_inst]
   // backward scratch
-  float* partials;       // [render_blocks][max_V][6]
-  float* dN;             // [max_V][3]
-  float* dm;             // [max_V][3]
-  int* sil;              // [max_views][max_E]
-  int* sil_count;        // [max_views]
-  // loss scratch
-  float* loss_partials;  // [kLossBlocks] + 2 scalars
-  unsigned int* counters;// [8] last-block counters
-  unsigned int* tile_counters;  // [4] dynamic tile schedulers of the render kernels
+  float* partials;       // [render_blocks][max_V][6] (single-instance contexts)
+  float* dN;             // [n_inst][max_V][3]
+  float* dm;             // [n_inst][max_V][3]
+  int* sil;              // [views][max_E]
+  int* sil_count;        // [views]
+  // loss scratch: per instance kLossStride(loss_blocks) floats
+  float* loss_partials;
+  int loss_blocks;       // blocks per instance of the loss kernels
+  unsigned int* counters;// [n_inst][4] last-block counters (mask count, loss, skin adjoint)
   // skin scratch
-  float* skin_partials;  // [kSkinBlocks][kSkinAcc]
+  float* skin_partials;  // [n_inst][kSkinBlocks][kSkinAcc]
   // kernel timing (HR_TIMING): events around the render kernels of the last call
   cudaEvent_t ev[32];          // >= 2 * kTimeSlots
   int ev_ready;
@@ -84,7 +115,10 @@ struct Context {
   unsigned long long* stats;  // [3][kStatsPer]
 };
 
-constexpr int kLossBlocks = 1024;
+constexpr int kLossBlocks = 1024;        // loss blocks of a single-instance context
+constexpr int kLossBlocksBatch = 128;    // per instance in a batch
+// per-instance loss scratch: block counts (u64), block sums, 1 / (3 sum M), padding
+__host__ __device__ constexpr int kLossStride(int blocks) { return 4 * blocks + 8; }
 constexpr int kStatsPer = 6;   // samples, rays, BVH nodes, triangle tests, hits, candidate box tests
 constexpr int kSkinBlocks = 64;
 constexpr int kSkinAcc = 16 * 12 + 10 + 3;   // dA_j (J=16 x 3x4), dbeta, dtau

@@ -24,12 +24,15 @@ int launch_loss(Context* ctx, const float* image, const float* obs, const uint8_
 int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
                 int step, cudaStream_t s);
 int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
-                    uint32_t* iter_dev, cudaStream_t s);
+                    const float* lr_scale, int scale_len, uint32_t* iter_dev, cudaStream_t s);
+int launch_vertex_error(const float* verts, const float* ref, int V, int n, float* out, const uint32_t* iter_dev,
+                        int rows, cudaStream_t s);
 
 // per-device properties of the render kernels (persistent grid)
 int render_grid(int device, int* blocks, int* threads, int* num_sms);
 size_t render_bwd_smem(int V);
 int subtiles_for(int views, int W, int H);
+int subtile_columns(int W);
 // one-time kernel attributes (shared-memory opt-in) on the current device
 int configure_bvh_kernels();
 int configure_render_kernels(int max_V);

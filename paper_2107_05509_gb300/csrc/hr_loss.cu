@@ -7,7 +7,9 @@
 //                   M |R - O|; the last block sums the partials in block order (in
 //                   double) into the loss.  Both reductions are deterministic.
 // The image is streamed as float4 (4 pixels = 3 float4 per thread) when its
-// pointers are 16-byte aligned.
+// pointers are 16-byte aligned.  A batch reduces every instance separately (its own
+// mean over its own masked pixels): grid row blockIdx.y is instance y, whose pixels
+// are one contiguous range, with its own partials and last-block counters.
 #include "hr_internal.h"
 
 namespace hr {
@@ -38,14 +40,34 @@ __device__ __forceinline__ float block_sum_f(float x, float* red) {
   return s;
 }
 
-// scratch: counts[kLossBlocks] (u64), partials[kLossBlocks] (float), scale, total
-__global__ void __launch_bounds__(kLossThreads) k_mask_count(const uint8_t* __restrict__ mask, long long P,
-                                                             unsigned long long* __restrict__ counts,
-                                                             unsigned* counter, float* __restrict__ scale) {
+// pixel range of grid row blockIdx.y: the instance's from the batch table, else [0, P)
+__device__ __forceinline__ void inst_range(const InstRec* it, long long P, long long& p0, long long& n) {
+  if (it) {
+    p0 = it[blockIdx.y].pix0;
+    n = it[blockIdx.y].npix;
+  } else {
+    p0 = 0;
+    n = P;
+  }
+}
+
+// per-instance scratch (lstride floats): counts[blocks] (u64), partials[blocks],
+// scale; counters [4] per instance: 0 mask count, 1 loss
+__global__ void __launch_bounds__(kLossThreads) k_mask_count(const uint8_t* __restrict__ mask_all,
+                                                             const InstRec* __restrict__ it, long long P,
+                                                             float* __restrict__ scratch_all, int lstride,
+                                                             unsigned* counters_all) {
   __shared__ unsigned long long red[32];
   __shared__ bool last;
+  long long p0, n;
+  inst_range(it, P, p0, n);
+  const uint8_t* mask = mask_all + p0;
+  float* scratch = scratch_all + (size_t)blockIdx.y * lstride;
+  unsigned long long* counts = reinterpret_cast<unsigned long long*>(scratch);
+  float* scale = scratch + 3 * gridDim.x;
+  unsigned* counter = counters_all + 4 * blockIdx.y;
   unsigned long long c = 0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x)
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     c += mask[i] != 0;
   unsigned long long s = block_sum_u64(c, red);
   if (threadIdx.x == 0) {
@@ -69,16 +91,27 @@ __global__ void __launch_bounds__(kLossThreads) k_mask_count(const uint8_t* __re
 
 __device__ __forceinline__ float sgn(float d) { return d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f); }
 
-__global__ void __launch_bounds__(kLossThreads) k_loss_adjoint(const float* __restrict__ image,
-                                                               const float* __restrict__ obs,
-                                                               const uint8_t* __restrict__ mask, long long P,
-                                                               const float* __restrict__ scale,
-                                                               float* __restrict__ adjoint,
-                                                               float* __restrict__ partials, unsigned* counter,
-                                                               float* __restrict__ loss, bool vec) {
+__global__ void __launch_bounds__(kLossThreads) k_loss_adjoint(const float* __restrict__ image_all,
+                                                               const float* __restrict__ obs_all,
+                                                               const uint8_t* __restrict__ mask_all,
+                                                               const InstRec* __restrict__ it, long long P,
+                                                               float* __restrict__ scratch_all, int lstride,
+                                                               unsigned* counters_all,
+                                                               float* __restrict__ adjoint_all,
+                                                               float* __restrict__ loss_all, bool vec) {
   __shared__ float red[32];
   __shared__ bool last;
-  const float sc = scale[0];
+  long long p0;
+  inst_range(it, P, p0, P);
+  const float* image = image_all + 3 * p0;
+  const float* obs = obs_all + 3 * p0;
+  const uint8_t* mask = mask_all + p0;
+  float* adjoint = adjoint_all + 3 * p0;
+  float* scratch = scratch_all + (size_t)blockIdx.y * lstride;
+  float* partials = scratch + 2 * gridDim.x;
+  const float sc = scratch[3 * gridDim.x];
+  unsigned* counter = counters_all + 4 * blockIdx.y + 1;
+  float* loss = loss_all + blockIdx.y;
   float acc = 0.0f;
   const long long stride = (long long)gridDim.x * blockDim.x;
   if (vec) {
@@ -160,10 +193,11 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
   p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// one block: bias corrections from the device step counter, then the counter advances
+// one block: bias corrections from the device step counter, then the counter
+// advances; entry i steps by lr * lr_scale[i % scale_len] when a scale is given
 __global__ void k_adam_dev(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
-                           uint32_t* __restrict__ iter_dev) {
+                           const float* __restrict__ lr_scale, int scale_len, uint32_t* __restrict__ iter_dev) {
   const float step = (float)(*iter_dev + 1u);
   const float c1 = 1.0f - powf(b1, step), c2 = 1.0f - powf(b2, step);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -172,35 +206,78 @@ __global__ void k_adam_dev(float* __restrict__ p, const float* __restrict__ g, f
     float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    const float li = lr_scale ? lr * lr_scale[i % scale_len] : lr;
+    p[i] -= li * (mi / c1) / (sqrtf(vi / c2) + eps);
   }
   __syncthreads();
   if (threadIdx.x == 0) *iter_dev += 1u;
 }
 
+// epsilon_v of instance blockIdx.x: mean over vertices of |verts - ref| (metres),
+// summed in a fixed order, into out[row][instance] with row = *iter_dev (row 0 when
+// no counter is given); rows past the table are not written
+constexpr int kErrThreads = 256;
+__global__ void __launch_bounds__(kErrThreads) k_vertex_error(const float* __restrict__ verts,
+                                                             const float* __restrict__ ref, int V,
+                                                             float* __restrict__ out, const uint32_t* iter_dev,
+                                                             int rows) {
+  __shared__ double red[kErrThreads];
+  const size_t o = (size_t)blockIdx.x * 3 * V;
+  double acc = 0.0;
+  for (int v = threadIdx.x; v < V; v += kErrThreads) {
+    const double dx = (double)verts[o + 3 * v] - ref[o + 3 * v];
+    const double dy = (double)verts[o + 3 * v + 1] - ref[o + 3 * v + 1];
+    const double dz = (double)verts[o + 3 * v + 2] - ref[o + 3 * v + 2];
+    acc += sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kErrThreads >> 1; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const unsigned row = iter_dev ? *iter_dev : 0u;
+  if (row < (unsigned)rows) out[(size_t)row * gridDim.x + blockIdx.x] = (float)(red[0] / V);
+}
+
 }  // namespace
 
 int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
-                    uint32_t* iter_dev, cudaStream_t s) {
-  k_adam_dev<<<1, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, iter_dev);
+                    const float* lr_scale, int scale_len, uint32_t* iter_dev, cudaStream_t s) {
+  k_adam_dev<<<1, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, lr_scale, scale_len, iter_dev);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_vertex_error(const float* verts, const float* ref, int V, int n, float* out, const uint32_t* iter_dev,
+                        int rows, cudaStream_t s) {
+  k_vertex_error<<<n, kErrThreads, 0, s>>>(verts, ref, V, out, iter_dev, rows);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
 
 int launch_loss(Context* ctx, const float* image, const float* obs, const uint8_t* mask, long long P, float* loss,
                 float* adjoint, cudaStream_t s) {
-  long long want = (P + kLossThreads - 1) / kLossThreads;
-  int blocks = (int)(want < kLossBlocks ? (want > 0 ? want : 1) : kLossBlocks);
-  unsigned long long* counts = reinterpret_cast<unsigned long long*>(ctx->loss_partials);
-  float* partials = ctx->loss_partials + 2 * kLossBlocks;
-  float* scale = partials + kLossBlocks;
-  k_mask_count<<<blocks, kLossThreads, 0, s>>>(mask, P, counts, ctx->counters, scale);
-  HR_CHECK_LAUNCH();
+  int blocks;
   bool vec = ((reinterpret_cast<uintptr_t>(image) | reinterpret_cast<uintptr_t>(obs) |
                reinterpret_cast<uintptr_t>(adjoint)) & 15) == 0 &&
              (reinterpret_cast<uintptr_t>(mask) & 3) == 0;
-  k_loss_adjoint<<<blocks, kLossThreads, 0, s>>>(image, obs, mask, P, scale, adjoint, partials, ctx->counters + 1,
-                                                 loss, vec);
+  if (ctx->vt) {   // a batch: every instance's range, its own reduction
+    blocks = ctx->loss_blocks;
+    vec = vec && ctx->loss_vec;
+    P = 0;
+  } else {
+    long long want = (P + kLossThreads - 1) / kLossThreads;
+    blocks = (int)(want < kLossBlocks ? (want > 0 ? want : 1) : kLossBlocks);
+  }
+  const int lstride = kLossStride(ctx->loss_blocks);
+  const dim3 grid(blocks, ctx->vt ? ctx->n_inst : 1);
+  const InstRec* it = ctx->vt ? ctx->it : nullptr;
+  k_mask_count<<<grid, kLossThreads, 0, s>>>(mask, it, P, ctx->loss_partials, lstride, ctx->counters);
+  HR_CHECK_LAUNCH();
+  k_loss_adjoint<<<grid, kLossThreads, 0, s>>>(image, obs, mask, it, P, ctx->loss_partials, lstride, ctx->counters,
+                                               adjoint, loss, vec);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }

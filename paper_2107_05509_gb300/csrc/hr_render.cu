@@ -33,6 +33,15 @@
 //   k_edge_samples the boundary term: samples on silhouette edges, f+ and f- by
 //                  two traced rays, mapped to vertices by the projection Jacobian.
 //   k_normal_dm / k_normal_gather   adjoint of the area-weighted vertex normals.
+//
+// Batches (hr_batch_create): every kernel runs over all instances of the batch in
+// one launch.  Sub-tiles are numbered over all views of all instances (a view table
+// maps a sub-tile to its view, instance, resolution and samples per pixel); each
+// instance has its own BVH, vertices, normals and region of the work-item table.
+// Forward warps take items instance after instance; backward blocks take them
+// instance after instance too and add their shared-memory sums into the instance's
+// gradient when they move on.  A single-instance call is a batch of one with a
+// uniform view layout (no table).
 #include "hr_internal.h"
 
 namespace hr {
@@ -186,20 +195,26 @@ struct Work {
   int4* items;     // [items] (sub-tile, chunk, chunks, first item of the sub-tile)
   int item_cap;
   float4* part;    // [items][32] forward per-item sums (r, g, b, misses)
-  float* extra;    // [6V] backward contributions made outside the shading blocks
-  unsigned* ctr;   // [4] sub-tile counter, pool fill, item fill, item counter
+  float* extra;    // [n_inst][6V] backward sums: shading blocks of a batch, and work
+                   // done outside the shading blocks
+  unsigned* ctr;   // [2 + 2 n_inst] sub-tile counter, pool fill, then per instance
+                   // item fill and item counter
 };
 
 struct RenderArgs {
-  const Node* nodes;
-  const float4* tris;
-  const float* verts;
+  const Node* nodes;       // instance 0; instance i at + i node_stride
+  const float4* tris;      // instance i at + 3 i node_stride
+  const float* verts;      // instance i at + 3 i V
   const int* faces;
-  const float* normals;
+  const float* normals;    // instance i at + 3 i V
   const float* albedo;
-  const Cam* cams;
+  const Cam* cams;         // [views]
   const float* bg;
-  int N, H, W, spp, V;
+  int N, H, W, spp, V;     // uniform layout (single instance)
+  const ViewRec* vt;       // batch view table, nullptr = uniform layout
+  const InstRec* it;       // batch instance table
+  int n_inst, nviews, total_st;
+  int node_stride;
   uint2 key;
   uint32_t ctr1_hi;  // instance << 16
   uint32_t iter4;    // iter << 4 (kernels refresh it from iter_dev when given)
@@ -240,9 +255,25 @@ __device__ __forceinline__ RenderArgs with_iter(RenderArgs a) {
   return a;
 }
 
-__device__ __forceinline__ void jitter(const RenderArgs& a, int view, int px, int py, int s, float& u1, float& u2) {
-  uint4 r = philox4x32_10(make_uint4((uint32_t)(py * a.W + px), (uint32_t)view | a.ctr1_hi, (uint32_t)s, a.iter4),
-                          a.key);
+// the same arguments with the scene pointers of instance `inst`
+__device__ __forceinline__ RenderArgs for_inst(RenderArgs a, int inst) {
+  a.nodes += (size_t)inst * a.node_stride;
+  a.tris += (size_t)inst * 3 * a.node_stride;
+  a.verts += (size_t)inst * 3 * a.V;
+  a.normals += (size_t)inst * 3 * a.V;
+  return a;
+}
+
+// work-item region of an instance
+__device__ __forceinline__ int inst_ibase(const RenderArgs& a, int inst) { return a.vt ? a.it[inst].ibase : 0; }
+__device__ __forceinline__ int inst_icap(const RenderArgs& a, int inst) {
+  return a.vt ? a.it[inst].icap : a.wk.item_cap;
+}
+
+// sample s of pixel (px, py) of a view of width W whose counter word is ctr1
+__device__ __forceinline__ void jitter(const RenderArgs& a, uint32_t ctr1, int W, int px, int py, int s, float& u1,
+                                       float& u2) {
+  uint4 r = philox4x32_10(make_uint4((uint32_t)(py * W + px), ctr1, (uint32_t)s, a.iter4), a.key);
   u1 = u24(r.x);
   u2 = u24(r.y);
 }
@@ -263,18 +294,65 @@ __device__ __forceinline__ void add3(float* dst, int i, float x, float y, float 
 // sub-tiles, frustum gathering
 // ---------------------------------------------------------------------------------
 struct SubTile {
-  int view, x0, y0;
+  int view;          // global view (camera index)
+  int inst;          // instance
+  int x0, y0;
+  int H, W, spp;
+  uint32_t ctr1;     // Philox counter word of the view
+  long long pix0;    // first pixel of the view
 };
 
-__device__ __forceinline__ int subtile_count(const RenderArgs& a) {
-  return a.N * ((a.W + kSubW - 1) / kSubW) * ((a.H + kSubH - 1) / kSubH);
+__device__ __forceinline__ int subtile_count(const RenderArgs& a) { return a.total_st; }
+
+// global view holding sub-tile st: binary search of the view table (views are in
+// sub-tile order)
+__device__ __forceinline__ int view_of_subtile(const RenderArgs& a, int st) {
+  int lo = 0, hi = a.nviews - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&a.vt[mid].st0) <= st) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// the view of global view index g (uniform layout: computed)
+__device__ __forceinline__ void view_info(const RenderArgs& a, int g, SubTile& t, int& st0, int& nsx) {
+  t.view = g;
+  if (a.vt) {
+    const ViewRec* v = a.vt + g;
+    t.inst = __ldg(&v->inst);
+    t.ctr1 = __ldg(&v->ctr1);
+    t.H = __ldg(&v->H);
+    t.W = __ldg(&v->W);
+    t.spp = __ldg(&v->spp);
+    t.pix0 = __ldg(&v->pix0);
+    st0 = __ldg(&v->st0);
+    nsx = __ldg(&v->nsx);
+  } else {
+    t.inst = 0;
+    t.ctr1 = (uint32_t)g | a.ctr1_hi;
+    t.H = a.H;
+    t.W = a.W;
+    t.spp = a.spp;
+    t.pix0 = (long long)g * a.H * a.W;
+    nsx = (a.W + kSubW - 1) / kSubW;
+    st0 = g * nsx * ((a.H + kSubH - 1) / kSubH);
+  }
 }
 
 __device__ __forceinline__ SubTile subtile(const RenderArgs& a, int st) {
-  const int nsx = (a.W + kSubW - 1) / kSubW, nsy = (a.H + kSubH - 1) / kSubH;
   SubTile t;
-  t.view = st / (nsx * nsy);
-  int rem = st - t.view * nsx * nsy;
+  int g;
+  if (a.vt) {
+    g = view_of_subtile(a, st);
+  } else {
+    const int nsx = (a.W + kSubW - 1) / kSubW, nsy = (a.H + kSubH - 1) / kSubH;
+    g = st / (nsx * nsy);
+  }
+  int st0, nsx;
+  view_info(a, g, t, st0, nsx);
+  const int rem = st - st0;
   t.x0 = (rem % nsx) * kSubW;
   t.y0 = (rem / nsx) * kSubH;
   return t;
@@ -452,10 +530,11 @@ __device__ __forceinline__ Hit closest_candidate_1(const RenderArgs& a, int off,
 }
 
 // radiance through screen point (sx, sy) of a sub-tile whose candidates are (off, K)
-// (K < 0: per-ray traversal); a miss returns background pixel (bx, by)
+// (K < 0: per-ray traversal); a miss returns background pixel (bx, by) of the view
+// whose first pixel is pix0 and width W.  `a` holds the instance's scene pointers.
 template <bool STATS>
-__device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, int view, float sx, float sy, int bx,
-                                           int by, int off, int K, Counts& cnt) {
+__device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, long long pix0, int W, float sx,
+                                           float sy, int bx, int by, int off, int K, Counts& cnt) {
   float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
   float3 d = primary_dir(cam, sx, sy);
   if (STATS) {
@@ -469,7 +548,7 @@ __device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, 
     h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
   if (STATS) cnt.hits += h.tri >= 0;
   if (h.tri >= 0) return shade(a, h);
-  return ld3(a.bg + 3 * (((size_t)view * a.H + by) * a.W + bx));
+  return ld3(a.bg + 3 * (pix0 + (size_t)by * W + bx));
 }
 
 // Radiance sums of samples [s0, s1) of this lane's pixel (all lanes call it).
@@ -478,13 +557,13 @@ __device__ __forceinline__ void shade_samples(const RenderArgs& a, const SubTile
                                               int s0, int s1, float3& acc, int& misses, Counts& cnt) {
   const int lane = threadIdx.x & 31;
   const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
-  const bool valid = px < a.W && py < a.H;
+  const bool valid = px < t.W && py < t.H;
   const float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
   for (int s = s0; s < s1; ++s) {
     float sx = 0.0f, sy = 0.0f;
     if (valid) {
       float u1, u2;
-      jitter(a, t.view, px, py, s, u1, u2);
+      jitter(a, t.ctr1, t.W, px, py, s, u1, u2);
       sx = __fadd_rn((float)px, u1);
       sy = __fadd_rn((float)py, u2);
       if (STATS) {
@@ -514,12 +593,12 @@ __device__ __forceinline__ void write_pixel(const RenderArgs& a, const SubTile& 
                                             float* __restrict__ image) {
   const int lane = threadIdx.x & 31;
   const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
-  if (px >= a.W || py >= a.H) return;
+  if (px >= t.W || py >= t.H) return;
   // misses contribute background * (misses / spp): a pixel whose samples all miss is
   // exactly its background value
-  const size_t pix = ((size_t)t.view * a.H + py) * a.W + px;
-  const float fm = __fdiv_rn((float)misses, (float)a.spp);
-  const float inv_spp = 1.0f / (float)a.spp;
+  const size_t pix = t.pix0 + (size_t)py * t.W + px;
+  const float fm = __fdiv_rn((float)misses, (float)t.spp);
+  const float inv_spp = 1.0f / (float)t.spp;
   float3 bgc = misses ? ld3(a.bg + 3 * pix) : make_float3(0.0f, 0.0f, 0.0f);
   image[3 * pix] = acc.x * inv_spp + bgc.x * fm;
   image[3 * pix + 1] = acc.y * inv_spp + bgc.y * fm;
@@ -608,7 +687,7 @@ __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile&
     float sx = 0.0f, sy = 0.0f;
     if (live) {
       float u1, u2;
-      jitter(a, t.view, px, py, s, u1, u2);
+      jitter(a, t.ctr1, t.W, px, py, s, u1, u2);
       sx = __fadd_rn((float)px, u1);
       sy = __fadd_rn((float)py, u2);
       if (STATS) {
@@ -650,32 +729,35 @@ __device__ __forceinline__ float3 lane_adjoint(const RenderArgs& a, const SubTil
   const int lane = threadIdx.x & 31;
   const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
   live = false;
-  if (px >= a.W || py >= a.H) return make_float3(0.0f, 0.0f, 0.0f);
-  float3 g = ld3(adjoint + 3 * (((size_t)t.view * a.H + py) * a.W + px));
+  if (px >= t.W || py >= t.H) return make_float3(0.0f, 0.0f, 0.0f);
+  float3 g = ld3(adjoint + 3 * (t.pix0 + (size_t)py * t.W + px));
   live = g.x != 0.0f || g.y != 0.0f || g.z != 0.0f;
-  const float inv_spp = 1.0f / (float)a.spp;
+  const float inv_spp = 1.0f / (float)t.spp;
   return make_float3(g.x * inv_spp, g.y * inv_spp, g.z * inv_spp);
 }
 
-// One warp per sub-tile: candidates into the pool, work items for the sub-tile.
+// One warp per sub-tile: candidates into the pool, work items for the sub-tile (in
+// its instance's region of the item table).
 // BWD: only sub-tiles with a non-zero adjoint; their zero-candidate case has no
 // gradient.  FWD: zero-candidate sub-tiles are written (background) here.  When the
-// pool or the item table is full the warp does the sub-tile's work itself.
+// pool or the item region is full the warp does the sub-tile's work itself.
 template <bool BWD, bool STATS>
 __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, const float* __restrict__ adjoint,
                                                           float* __restrict__ image, unsigned long long* stats) {
-  const RenderArgs a = with_iter(a_in);
+  const RenderArgs a0 = with_iter(a_in);
   __shared__ GatherSmem gsm[kWarps];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   Counts cnt;
-  const int total = subtile_count(a);
+  const int total = subtile_count(a0);
   for (;;) {
     int st = 0;
-    if (lane == 0) st = (int)atomicAdd(&a.wk.ctr[0], 1u);
+    if (lane == 0) st = (int)atomicAdd(&a0.wk.ctr[0], 1u);
     st = __shfl_sync(0xffffffffu, st, 0);
     if (st >= total) break;
-    const SubTile t = subtile(a, st);
+    const SubTile t = subtile(a0, st);
+    if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
+    const RenderArgs a = for_inst(a0, t.inst);
     bool live = true;
     float3 g = make_float3(0.0f, 0.0f, 0.0f);
     if (BWD) {
@@ -690,9 +772,9 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
     if (K == 0) {
       if (lane == 0) a.wk.st[st] = make_int2(0, 0);
       const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
-      const bool valid = px < a.W && py < a.H && live;
-      if (STATS && valid) cnt.samples += a.spp;   // resolved by the frustum test
-      if (!BWD) write_pixel(a, t, make_float3(0.0f, 0.0f, 0.0f), a.spp, image);
+      const bool valid = px < t.W && py < t.H && live;
+      if (STATS && valid) cnt.samples += t.spp;   // resolved by the frustum test
+      if (!BWD) write_pixel(a, t, make_float3(0.0f, 0.0f, 0.0f), t.spp, image);
       continue;
     }
     int off = 0;
@@ -752,25 +834,27 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
         K = -1;   // pool full: per-ray traversal for this sub-tile
       }
     }
-    const int C = chunks_for(K, a.spp);
+    const int C = chunks_for(K, t.spp);
+    const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
     int first = 0;
-    if (lane == 0) first = (int)atomicAdd(&a.wk.ctr[2], (unsigned)C);
+    if (lane == 0) first = (int)atomicAdd(&a.wk.ctr[2 + 2 * t.inst], (unsigned)C);
     first = __shfl_sync(0xffffffffu, first, 0);
     if (lane == 0) a.wk.st[st] = make_int2(off, K);
-    if (first + C <= a.wk.item_cap) {
-      for (int c = lane; c < C; c += 32) a.wk.items[first + c] = make_int4(st, c, C, first);
+    if (first + C <= icap) {
+      for (int c = lane; c < C; c += 32) a.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
     } else {
-      // item table full: blank the reserved slots that exist, and this warp does
+      // item region full: blank the reserved slots that exist, and this warp does
       // the whole sub-tile itself
       for (int c = lane; c < C; c += 32)
-        if (first + c < a.wk.item_cap) a.wk.items[first + c] = make_int4(-1, 0, 0, 0);
+        if (first + c < icap) a.wk.items[ibase + first + c] = make_int4(-1, 0, 0, 0);
       __threadfence_block();
       if (BWD) {
-        grad_samples<STATS>(a, t, cam, off, K, 0, a.spp, live, g, a.wk.extra, a.wk.extra + 3 * a.V, cnt);
+        float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
+        grad_samples<STATS>(a, t, cam, off, K, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
       } else {
         float3 acc = make_float3(0.0f, 0.0f, 0.0f);
         int misses = 0;
-        shade_samples<STATS>(a, t, cam, off, K, 0, a.spp, acc, misses, cnt);
+        shade_samples<STATS>(a, t, cam, off, K, 0, t.spp, acc, misses, cnt);
         write_pixel(a, t, acc, misses, image);
       }
     }
@@ -779,8 +863,9 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
   flush_counts<STATS>(cnt, stats);
 }
 
-__device__ __forceinline__ int item_count(const RenderArgs& a) {
-  return (int)min(*reinterpret_cast<volatile unsigned*>(&a.wk.ctr[2]), (unsigned)a.wk.item_cap);
+// items of an instance's region that the gather filled
+__device__ __forceinline__ int item_count(const RenderArgs& a, int inst) {
+  return (int)min(*reinterpret_cast<volatile unsigned*>(&a.wk.ctr[2 + 2 * inst]), (unsigned)inst_icap(a, inst));
 }
 
 __device__ __forceinline__ void item_samples(int c, int C, int spp, int& s0, int& s1) {
@@ -788,30 +873,52 @@ __device__ __forceinline__ void item_samples(int c, int C, int spp, int& s0, int
   s1 = (int)((long long)(c + 1) * spp / C);
 }
 
+// fetch the next work item of instance `inst` (lane 0 takes it, the warp shares it);
+// -1 when the instance's region is exhausted
+__device__ __forceinline__ int next_item(const RenderArgs& a, int inst, int n) {
+  int it = 0;
+  if ((threadIdx.x & 31) == 0) it = (int)atomicAdd(&a.wk.ctr[3 + 2 * inst], 1u);
+  it = __shfl_sync(0xffffffffu, it, 0);
+  return it < n ? it : -1;
+}
+
+// the sub-tile and candidate list of item `gi` (global index); false for a blanked or
+// corrupt item
+__device__ __forceinline__ bool load_item(const RenderArgs& a, int gi, int4& item, SubTile& t, int2& pk) {
+  item = a.wk.items[gi];
+  if (item.x < 0) return false;   // a blanked slot
+  if (!in_range(a.status, item.x, 0, subtile_count(a))) return false;
+  t = subtile(a, item.x);
+  if (!in_range(a.status, t.inst, 0, a.n_inst)) return false;
+  pk = a.wk.st[item.x];
+  if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
+  return true;
+}
+
+// warps take work items, instance after instance
 template <bool STATS>
 __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in, unsigned long long* stats) {
-  const RenderArgs a = with_iter(a_in);
+  const RenderArgs a0 = with_iter(a_in);
   const int lane = threadIdx.x & 31;
   Counts cnt;
-  const int n = item_count(a);
-  for (;;) {
-    int it = 0;
-    if (lane == 0) it = (int)atomicAdd(&a.wk.ctr[3], 1u);
-    it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= n) break;
-    const int4 item = a.wk.items[it];
-    if (item.x < 0) continue;   // a blanked slot
-    if (!in_range(a.status, item.x, 0, subtile_count(a))) continue;
-    const SubTile t = subtile(a, item.x);
-    int2 pk = a.wk.st[item.x];
-    if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
-    const Cam cam = load_cam(a.cams, t.view);
-    int s0, s1;
-    item_samples(item.y, item.z, a.spp, s0, s1);
-    float3 acc = make_float3(0.0f, 0.0f, 0.0f);
-    int misses = 0;
-    shade_samples<STATS>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
-    a.wk.part[(size_t)it * 32 + lane] = make_float4(acc.x, acc.y, acc.z, (float)misses);
+  for (int inst = 0; inst < a0.n_inst; ++inst) {
+    const int n = item_count(a0, inst), ibase = inst_ibase(a0, inst);
+    const RenderArgs a = for_inst(a0, inst);
+    for (;;) {
+      const int it = next_item(a, inst, n);
+      if (it < 0) break;
+      int4 item;
+      SubTile t;
+      int2 pk;
+      if (!load_item(a, ibase + it, item, t, pk) || t.inst != inst) continue;
+      const Cam cam = load_cam(a.cams, t.view);
+      int s0, s1;
+      item_samples(item.y, item.z, t.spp, s0, s1);
+      float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+      int misses = 0;
+      shade_samples<STATS>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
+      a.wk.part[(size_t)(ibase + it) * 32 + lane] = make_float4(acc.x, acc.y, acc.z, (float)misses);
+    }
   }
   flush_counts<STATS>(cnt, stats);
 }
@@ -819,87 +926,111 @@ __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in
 // one warp per sub-tile with items: its item sums in item order, then the pixel
 __global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, float* __restrict__ image) {
   const int lane = threadIdx.x & 31;
-  const int n = item_count(a);
   const int nw = gridDim.x * kWarps;
-  for (int it = blockIdx.x * kWarps + (threadIdx.x >> 5); it < n; it += nw) {
-    const int4 item = a.wk.items[it];
-    if (item.x < 0 || item.y != 0) continue;
-    if (!in_range(a.status, item.x, 0, subtile_count(a)) ||
-        !in_range(a.status, (long long)item.w + item.z - 1, 0, a.wk.item_cap))
-      continue;
-    float3 acc = make_float3(0.0f, 0.0f, 0.0f);
-    float misses = 0.0f;
-    for (int c = 0; c < item.z; ++c) {
-      float4 p = a.wk.part[(size_t)(item.w + c) * 32 + lane];
-      acc.x += p.x;
-      acc.y += p.y;
-      acc.z += p.z;
-      misses += p.w;
+  for (int inst = 0; inst < a.n_inst; ++inst) {
+    const int n = item_count(a, inst), ibase = inst_ibase(a, inst);
+    for (int it = blockIdx.x * kWarps + (threadIdx.x >> 5); it < n; it += nw) {
+      const int4 item = a.wk.items[ibase + it];
+      if (item.x < 0 || item.y != 0) continue;
+      if (!in_range(a.status, item.x, 0, subtile_count(a)) ||
+          !in_range(a.status, (long long)item.w + item.z - 1, ibase, ibase + inst_icap(a, inst)))
+        continue;
+      float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+      float misses = 0.0f;
+      for (int c = 0; c < item.z; ++c) {
+        float4 p = a.wk.part[(size_t)(item.w + c) * 32 + lane];
+        acc.x += p.x;
+        acc.y += p.y;
+        acc.z += p.z;
+        misses += p.w;
+      }
+      write_pixel(a, subtile(a, item.x), acc, (int)misses, image);
     }
-    write_pixel(a, subtile(a, item.x), acc, (int)misses, image);
   }
 }
 
 // interior term: warps take work items; the block accumulates dV/dN in shared
-// memory (sdV [V][3], sdN [V][3]) and writes one partial per block
-template <bool STATS>
+// memory (sdV [V][3], sdN [V][3]).  Single instance (BATCH false): one partial per
+// block, summed in block order by k_reduce_partials.  Batch: the block works through
+// the instances in order and, when every warp is done with one, adds its non-zero
+// sums into that instance's extra [6V] (global atomics) and clears them.
+template <bool STATS, bool BATCH>
 __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(RenderArgs a_in,
                                                                              const float* __restrict__ adjoint,
                                                                              float* __restrict__ partials,
                                                                              unsigned long long* stats) {
-  const RenderArgs a = with_iter(a_in);
+  const RenderArgs a0 = with_iter(a_in);
   extern __shared__ float sacc[];
   float* sdV = sacc;
-  float* sdN = sacc + 3 * a.V;
-  const int lane = threadIdx.x & 31;
-  for (int i = threadIdx.x; i < 6 * a.V; i += kRenderThreads) sacc[i] = 0.0f;
+  float* sdN = sacc + 3 * a0.V;
+  for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) sacc[i] = 0.0f;
   __syncthreads();
   Counts cnt;
-  const int n = item_count(a);
-  for (;;) {
-    int it = 0;
-    if (lane == 0) it = (int)atomicAdd(&a.wk.ctr[3], 1u);
-    it = __shfl_sync(0xffffffffu, it, 0);
-    if (it >= n) break;
-    const int4 item = a.wk.items[it];
-    if (item.x < 0) continue;   // a blanked slot
-    if (!in_range(a.status, item.x, 0, subtile_count(a))) continue;
-    const SubTile t = subtile(a, item.x);
-    int2 pk = a.wk.st[item.x];
-    if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
-    bool live;
-    const float3 g = lane_adjoint(a, t, adjoint, live);
-    const Cam cam = load_cam(a.cams, t.view);
-    int s0, s1;
-    item_samples(item.y, item.z, a.spp, s0, s1);
-    grad_samples<STATS>(a, t, cam, pk.x, pk.y, s0, s1, live, g, sdV, sdN, cnt);
+  for (int inst = 0; inst < a0.n_inst; ++inst) {
+    const int n = item_count(a0, inst), ibase = inst_ibase(a0, inst);
+    const RenderArgs a = for_inst(a0, inst);
+    int did = 0;
+    for (;;) {
+      const int it = next_item(a, inst, n);
+      if (it < 0) break;
+      int4 item;
+      SubTile t;
+      int2 pk;
+      if (!load_item(a, ibase + it, item, t, pk) || t.inst != inst) continue;
+      bool live;
+      const float3 g = lane_adjoint(a, t, adjoint, live);
+      const Cam cam = load_cam(a.cams, t.view);
+      int s0, s1;
+      item_samples(item.y, item.z, t.spp, s0, s1);
+      grad_samples<STATS>(a, t, cam, pk.x, pk.y, s0, s1, live, g, sdV, sdN, cnt);
+      did = 1;
+    }
+    if (BATCH) {
+      if (__syncthreads_or(did)) {
+        float* dst = a0.wk.extra + (size_t)inst * 6 * a0.V;
+        for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) {
+          const float v = sacc[i];
+          if (v != 0.0f) {
+            atomicAdd(dst + i, v);
+            sacc[i] = 0.0f;
+          }
+        }
+        __syncthreads();
+      }
+    }
   }
   flush_counts<STATS>(cnt, stats);
+  if (BATCH) return;
   __syncthreads();
-  float* out = partials + (size_t)blockIdx.x * 6 * a.V;
-  for (int i = threadIdx.x; i < 6 * a.V; i += kRenderThreads) out[i] = sacc[i];
+  float* out = partials + (size_t)blockIdx.x * 6 * a0.V;
+  for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) out[i] = sacc[i];
 }
 
 // d_verts[i] = extra[i] + sum_b partials[b][i] (i < 3V), dN[i-3V] likewise, in
-// fixed block order
-__global__ void k_reduce_partials(const float* __restrict__ partials, const float* __restrict__ extra, int nblocks,
-                                  int V, float* __restrict__ d_verts, float* __restrict__ dN) {
+// fixed block order.  blockIdx.y selects the instance (a batch has no partials).
+__global__ void k_reduce_partials(const float* __restrict__ partials, const float* __restrict__ extra_all,
+                                  int nblocks, int V, float* __restrict__ d_verts_all, float* __restrict__ dN_all) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 6 * V) return;
+  const float* extra = extra_all + (size_t)blockIdx.y * 6 * V;
+  float* d_verts = d_verts_all + (size_t)blockIdx.y * 3 * V;
+  float* dN = dN_all + (size_t)blockIdx.y * 3 * V;
   float acc = extra[i];
   for (int b = 0; b < nblocks; ++b) acc += partials[(size_t)b * 6 * V + i];
   if (i < 3 * V) d_verts[i] = acc;
   else dN[i - 3 * V] = acc;
 }
 
-// per view: silhouette flags in edge order, compacted by a block-wide scan
-__global__ void k_silhouettes(const float* __restrict__ verts, const int* __restrict__ faces,
+// per view: silhouette flags in edge order, compacted by a block-wide scan.  In a
+// batch the view's instance (view table) selects the vertices ([V][3] per instance).
+__global__ void k_silhouettes(const float* __restrict__ verts_all, const int* __restrict__ faces,
                               const int* __restrict__ edges, const int* __restrict__ edge_faces, int E,
-                              const Cam* __restrict__ cams, int* __restrict__ lists, int stride,
-                              int* __restrict__ counts) {
+                              const Cam* __restrict__ cams, const ViewRec* __restrict__ vt, int V,
+                              int* __restrict__ lists, int stride, int* __restrict__ counts) {
   __shared__ int warp_tot[32];
   __shared__ int base;
   const int view = blockIdx.x;
+  const float* verts = verts_all + (vt ? (size_t)__ldg(&vt[view].inst) * 3 * V : 0);
   Cam cam = load_cam(cams, view);
   float3 c = make_float3(cam.c[0], cam.c[1], cam.c[2]);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -944,18 +1075,27 @@ __global__ void k_silhouettes(const float* __restrict__ verts, const int* __rest
   if (threadIdx.x == 0) counts[view] = base;
 }
 
-// boundary term (edge sampling); one thread per (view, sample)
+// boundary term (edge sampling); one thread per (view, sample): thread i is sample
+// i % Ne_max of global view i / Ne_max (views with fewer samples skip the rest)
 template <bool STATS>
 __global__ void k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoint, const int* __restrict__ edges,
-                               const int* __restrict__ lists, int stride, const int* __restrict__ counts, int Ne,
-                               float eps, float* __restrict__ d_verts, unsigned long long* stats) {
-  const RenderArgs a = with_iter(a_in);
+                               const int* __restrict__ lists, int stride, const int* __restrict__ counts, int Ne_max,
+                               float eps, float* __restrict__ d_verts_all, unsigned long long* stats) {
+  const RenderArgs a0 = with_iter(a_in);
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)a.N * Ne) return;
-  int view = (int)(i / Ne), k = (int)(i - (long long)view * Ne);
+  if (i >= (long long)a0.nviews * Ne_max) return;
+  const int view = (int)(i / Ne_max), k = (int)(i - (long long)view * Ne_max);
+  SubTile vw;
+  int st0, nsx;
+  view_info(a0, view, vw, st0, nsx);
+  const int Ne = a0.vt ? __ldg(&a0.vt[view].ne) : Ne_max;
+  if (k >= Ne) return;
+  if (!in_range(a0.status, vw.inst, 0, a0.n_inst)) return;
+  const RenderArgs a = for_inst(a0, vw.inst);
+  float* d_verts = d_verts_all + (size_t)vw.inst * 3 * a.V;
   int nsil = counts[view];
   if (nsil == 0) return;
-  uint4 r = philox4x32_10(make_uint4((uint32_t)k, (uint32_t)view | a.ctr1_hi, 0u, a.iter4 | 1u), a.key);
+  uint4 r = philox4x32_10(make_uint4((uint32_t)k, vw.ctr1, 0u, a.iter4 | 1u), a.key);
   int si = (int)__umulhi(r.x, (uint32_t)nsil);
   float t = u24(r.y);
   int e = lists[(size_t)view * stride + si];
@@ -970,25 +1110,25 @@ __global__ void k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoin
   if (!(len > 0.0f)) return;
   float nhx = __fdiv_rn(nx, len), nhy = __fdiv_rn(ny, len);
   float fxp = floorf(x), fyp = floorf(y);
-  if (fxp < 0.0f || fyp < 0.0f || fxp >= (float)a.W || fyp >= (float)a.H) return;
+  const int W = vw.W, H = vw.H;
+  if (fxp < 0.0f || fyp < 0.0f || fxp >= (float)W || fyp >= (float)H) return;
   int px = (int)fxp, py = (int)fyp;
-  float3 A = ld3(adjoint + 3 * (((size_t)view * a.H + py) * a.W + px));
+  float3 A = ld3(adjoint + 3 * (vw.pix0 + (size_t)py * W + px));
   if (A.x == 0.0f && A.y == 0.0f && A.z == 0.0f) return;
   float xp = __fmaf_rn(eps, nhx, x), yp = __fmaf_rn(eps, nhy, y);
   float xm = __fmaf_rn(-eps, nhx, x), ym = __fmaf_rn(-eps, nhy, y);
-  int bxp = (int)fminf(fmaxf(floorf(xp), 0.0f), (float)(a.W - 1));
-  int byp = (int)fminf(fmaxf(floorf(yp), 0.0f), (float)(a.H - 1));
-  int bxm = (int)fminf(fmaxf(floorf(xm), 0.0f), (float)(a.W - 1));
-  int bym = (int)fminf(fmaxf(floorf(ym), 0.0f), (float)(a.H - 1));
+  int bxp = (int)fminf(fmaxf(floorf(xp), 0.0f), (float)(W - 1));
+  int byp = (int)fminf(fmaxf(floorf(yp), 0.0f), (float)(H - 1));
+  int bxm = (int)fminf(fmaxf(floorf(xm), 0.0f), (float)(W - 1));
+  int bym = (int)fminf(fmaxf(floorf(ym), 0.0f), (float)(H - 1));
   // the candidates of the sub-tile holding the centre pixel serve both offset rays:
   // its frustum is padded by half a pixel and the offsets are far smaller
-  const int nsx = (a.W + kSubW - 1) / kSubW, nsy = (a.H + kSubH - 1) / kSubH;
-  const int st = view * nsx * nsy + (py / kSubH) * nsx + (px / kSubW);
+  const int st = st0 + (py / kSubH) * nsx + (px / kSubW);
   int2 pk = a.wk.st[st];
   if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
   Counts cnt;
-  float3 fp = radiance<STATS>(a, cam, view, xp, yp, bxp, byp, pk.x, pk.y, cnt);
-  float3 fm = radiance<STATS>(a, cam, view, xm, ym, bxm, bym, pk.x, pk.y, cnt);
+  float3 fp = radiance<STATS>(a, cam, vw.pix0, W, xp, yp, bxp, byp, pk.x, pk.y, cnt);
+  float3 fm = radiance<STATS>(a, cam, vw.pix0, W, xm, ym, bxm, bym, pk.x, pk.y, cnt);
   if (STATS) {
     unsigned v[kStatsPer] = {cnt.samples, cnt.rays, cnt.nodes, cnt.tris, cnt.hits, cnt.cands};
     for (int q = 0; q < kStatsPer; ++q)
@@ -1016,11 +1156,14 @@ __global__ void k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoin
   }
 }
 
-// dm_v = (I - n n^T) dN_v / |m_v|
-__global__ void k_normal_dm(const float* __restrict__ normals, const float* __restrict__ normal_len,
-                            const float* __restrict__ dN, int V, float* __restrict__ dm) {
+// dm_v = (I - n n^T) dN_v / |m_v|; blockIdx.y selects the instance
+__global__ void k_normal_dm(const float* __restrict__ normals_all, const float* __restrict__ normal_len_all,
+                            const float* __restrict__ dN_all, int V, float* __restrict__ dm_all) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
+  const size_t o = (size_t)blockIdx.y * V;
+  const float *normals = normals_all + 3 * o, *normal_len = normal_len_all + o, *dN = dN_all + 3 * o;
+  float* dm = dm_all + 3 * o;
   float len = normal_len[v];
   float3 n = ld3(normals + 3 * v), g = ld3(dN + 3 * v);
   float3 r = make_float3(0.0f, 0.0f, 0.0f);
@@ -1034,12 +1177,16 @@ __global__ void k_normal_dm(const float* __restrict__ normals, const float* __re
   dm[3 * v + 2] = r.z;
 }
 
-// d_verts[v] += sum over incident faces of d(e1 x e2)/dv . dc_f, dc_f = sum of dm over f
-__global__ void k_normal_gather(const float* __restrict__ verts, const int* __restrict__ faces,
+// d_verts[v] += sum over incident faces of d(e1 x e2)/dv . dc_f, dc_f = sum of dm
+// over f; blockIdx.y selects the instance
+__global__ void k_normal_gather(const float* __restrict__ verts_all, const int* __restrict__ faces,
                                 const int* __restrict__ vf_off, const int* __restrict__ vf_faces,
-                                const float* __restrict__ dm, int V, float* __restrict__ d_verts) {
+                                const float* __restrict__ dm_all, int V, float* __restrict__ d_verts_all) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
+  const size_t o = (size_t)blockIdx.y * 3 * V;
+  const float *verts = verts_all + o, *dm = dm_all + o;
+  float* d_verts = d_verts_all + o;
   float3 acc = make_float3(0.0f, 0.0f, 0.0f);
   for (int k = vf_off[v]; k < vf_off[v + 1]; ++k) {
     int f = vf_faces[k];
@@ -1127,6 +1274,20 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.wk.part = ctx->item_part;
   a.wk.extra = ctx->extra;
   a.wk.ctr = ctx->work_ctr;
+  a.node_stride = ctx->lim.max_F;
+  if (ctx->vt) {
+    a.vt = ctx->vt;
+    a.it = ctx->it;
+    a.n_inst = ctx->n_inst;
+    a.nviews = ctx->nviews;
+    a.total_st = ctx->total_st;
+  } else {
+    a.vt = nullptr;
+    a.it = nullptr;
+    a.n_inst = 1;
+    a.nviews = N;
+    a.total_st = subtiles_for(N, W, H);
+  }
   return a;
 }
 
@@ -1148,8 +1309,14 @@ int configure_render_kernels(int max_V) {
   // context never lowers the opt-in of a larger one
   (void)max_V;
   const int smem = (int)render_bwd_smem(8192);
-  if (cudaFuncSetAttribute(k_shade_bwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-      cudaFuncSetAttribute(k_shade_bwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+  if (cudaFuncSetAttribute(k_shade_bwd<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_shade_bwd<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_shade_bwd<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_shade_bwd<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+          cudaSuccess) {
     cudaGetLastError();
     return HR_ERR_CUDA;
   }
@@ -1157,13 +1324,15 @@ int configure_render_kernels(int max_V) {
 }
 
 int subtiles_for(int views, int W, int H) { return views * ((W + kSubW - 1) / kSubW) * ((H + kSubH - 1) / kSubH); }
+int subtile_columns(int W) { return (W + kSubW - 1) / kSubW; }
 
 int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,
                       const float* bg, const hr_render_opts* o, float* image, cudaStream_t s) {
   RenderArgs a = make_args(ctx, m, verts, cams, N, H, W, bg, o);
   const bool st = o->flags & HR_STATS;
   Timer tm{ctx, s, (o->flags & HR_TIMING) != 0};
-  if (cudaMemsetAsync(ctx->work_ctr, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return HR_ERR_CUDA;
+  if (cudaMemsetAsync(ctx->work_ctr, 0, (2 + 2 * a.n_inst) * sizeof(unsigned), s) != cudaSuccess)
+    return HR_ERR_CUDA;
   const int blocks = ctx->render_blocks;
   tm.begin(kTimeFwdGather);
   if (st)
@@ -1189,7 +1358,8 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
 
 int launch_silhouettes(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int* lists,
                        int list_stride, int* counts, cudaStream_t s) {
-  k_silhouettes<<<N, 512, 0, s>>>(verts, m->faces, m->edges, m->edge_faces, m->E, cams, lists, list_stride, counts);
+  k_silhouettes<<<N, 512, 0, s>>>(verts, m->faces, m->edges, m->edge_faces, m->E, cams, ctx->vt, m->V, lists,
+                                  list_stride, counts);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -1198,17 +1368,19 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
                       const float* bg, const hr_render_opts* o, const float* adjoint, float* d_verts,
                       cudaStream_t s) {
   RenderArgs a = make_args(ctx, m, verts, cams, N, H, W, bg, o);
-  const int V = m->V;
+  const int V = m->V, ni = a.n_inst, nv = a.nviews;
+  const bool batch = ctx->vt != nullptr;
+  const int Ne = batch ? ctx->max_ne : o->edge_samples;
   const bool interior = !(o->flags & HR_BWD_NO_INTERIOR);
-  const bool edges = !(o->flags & HR_BWD_NO_EDGES) && o->edge_samples > 0;
+  const bool edges = !(o->flags & HR_BWD_NO_EDGES) && Ne > 0;
   const bool normals = !(o->flags & HR_BWD_NO_NORMALS) && interior;
   const bool st = o->flags & HR_STATS;
   Timer tm{ctx, s, (o->flags & HR_TIMING) != 0};
   if (interior || edges) {
     // candidates of the sub-tiles with a non-zero adjoint: the interior shader's work
     // items, and the edge rays' candidate lists
-    if (cudaMemsetAsync(ctx->work_ctr, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
-        cudaMemsetAsync(ctx->extra, 0, sizeof(float) * 6 * V, s) != cudaSuccess)
+    if (cudaMemsetAsync(ctx->work_ctr, 0, (2 + 2 * ni) * sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemsetAsync(ctx->extra, 0, sizeof(float) * 6 * V * ni, s) != cudaSuccess)
       return HR_ERR_CUDA;
     tm.begin(kTimeBwdGather);
     if (st)
@@ -1221,38 +1393,40 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
   }
   if (interior) {
     const size_t smem = render_bwd_smem(V);   // within the opt-in of configure_render_kernels
-    auto kern = st ? k_shade_bwd<true> : k_shade_bwd<false>;
+    auto kern = batch ? (st ? k_shade_bwd<true, true> : k_shade_bwd<false, true>)
+                      : (st ? k_shade_bwd<true, false> : k_shade_bwd<false, false>);
     const int blocks = ctx->num_sms * kBwdMinBlocks;
     tm.begin(kTimeBwdShade);
     kern<<<blocks, kRenderThreads, smem, s>>>(a, adjoint, ctx->partials, st ? ctx->stats + kStatsPer : nullptr);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdShade);
     tm.begin(kTimeBwdReduce);
-    k_reduce_partials<<<(6 * V + 255) / 256, 256, 0, s>>>(ctx->partials, ctx->extra, blocks, V, d_verts, ctx->dN);
+    k_reduce_partials<<<dim3((6 * V + 255) / 256, ni), 256, 0, s>>>(ctx->partials, ctx->extra, batch ? 0 : blocks, V,
+                                                                    d_verts, ctx->dN);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdReduce);
   } else {
-    if (cudaMemsetAsync(d_verts, 0, sizeof(float) * 3 * V, s) != cudaSuccess) return HR_ERR_CUDA;
+    if (cudaMemsetAsync(d_verts, 0, sizeof(float) * 3 * V * ni, s) != cudaSuccess) return HR_ERR_CUDA;
   }
   if (edges) {
     tm.begin(kTimeBwdSil);
-    int rc = launch_silhouettes(ctx, m, verts, cams, N, ctx->sil, ctx->lim.max_E, ctx->sil_count, s);
+    int rc = launch_silhouettes(ctx, m, verts, cams, nv, ctx->sil, ctx->lim.max_E, ctx->sil_count, s);
     if (rc != HR_OK) return rc;
     tm.end(kTimeBwdSil);
-    long long n = (long long)N * o->edge_samples;
+    long long n = (long long)nv * Ne;
     auto kern = st ? k_edge_samples<true> : k_edge_samples<false>;
     tm.begin(kTimeBwdEdges);
     kern<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count,
-                                                     o->edge_samples, o->edge_eps_px, d_verts,
-                                                     ctx->stats + 2 * kStatsPer);
+                                                     Ne, o->edge_eps_px, d_verts, ctx->stats + 2 * kStatsPer);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdEdges);
   }
   if (normals) {
     tm.begin(kTimeBwdNormals);
-    k_normal_dm<<<(V + 255) / 256, 256, 0, s>>>(ctx->normals, ctx->normal_len, ctx->dN, V, ctx->dm);
+    const dim3 g((V + 255) / 256, ni);
+    k_normal_dm<<<g, 256, 0, s>>>(ctx->normals, ctx->normal_len, ctx->dN, V, ctx->dm);
     HR_CHECK_LAUNCH();
-    k_normal_gather<<<(V + 255) / 256, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, ctx->dm, V, d_verts);
+    k_normal_gather<<<g, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, ctx->dm, V, d_verts);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdNormals);
   }

@@ -164,9 +164,12 @@ __device__ __forceinline__ float3 shaped_vertex(const ModelArgs& m, const Chain&
   return make_float3(p[0], p[1], p[2]);
 }
 
-__global__ void __launch_bounds__(kSkinThreads) k_skin(ModelArgs m, const float* __restrict__ params,
-                                                       float* __restrict__ verts, int* status) {
+// blockIdx.y selects the instance: params [61] and verts [V][3] of instance y
+__global__ void __launch_bounds__(kSkinThreads) k_skin(ModelArgs m, const float* __restrict__ params_all,
+                                                       float* __restrict__ verts_all, int* status) {
   __shared__ Chain ch;
+  const float* params = params_all + (size_t)blockIdx.y * 61;
+  float* verts = verts_all + (size_t)blockIdx.y * 3 * m.V;
   build_chain(m, params, ch, status);
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < m.V; v += gridDim.x * blockDim.x) {
     float3 p = shaped_vertex(m, ch, v);
@@ -190,12 +193,20 @@ __device__ __forceinline__ float warp_sum(float x) {
 }
 
 // accumulator layout: [j*12 + 0..8] dRA_j (row-major), [j*12 + 9..11] dtA_j,
-// [16*12 + k] dbeta_k (blendshape part), [16*12 + 10 + c] dtau_c
-__global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const float* __restrict__ params,
-                                                           const float* __restrict__ dverts,
-                                                           float* __restrict__ partials, unsigned* counter,
-                                                           float* __restrict__ dparams, int* status) {
+// [16*12 + k] dbeta_k (blendshape part), [16*12 + 10 + c] dtau_c.
+// blockIdx.y selects the instance: params / dparams [61], dverts [V][3], partials
+// [kSkinBlocks][kSkinAcc] and the last-block counter at counter_all + y * cstride.
+__global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const float* __restrict__ params_all,
+                                                           const float* __restrict__ dverts_all,
+                                                           float* __restrict__ partials_all, unsigned* counter_all,
+                                                           int cstride, float* __restrict__ dparams_all,
+                                                           int* status) {
   __shared__ Chain ch;
+  const float* params = params_all + (size_t)blockIdx.y * 61;
+  const float* dverts = dverts_all + (size_t)blockIdx.y * 3 * m.V;
+  float* partials = partials_all + (size_t)blockIdx.y * kSkinBlocks * kSkinAcc;
+  unsigned* counter = counter_all + (size_t)blockIdx.y * cstride;
+  float* dparams = dparams_all + (size_t)blockIdx.y * 61;
   __shared__ float wacc[kSkinThreads / 32][kSkinAcc];
   __shared__ float bacc[kSkinAcc];
   __shared__ bool last;
@@ -336,7 +347,7 @@ ModelArgs model_args(const hr_model* m) {
 
 int launch_skin(Context* ctx, const hr_model* m, const float* params, float* verts, cudaStream_t s) {
   int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
-  k_skin<<<blocks, kSkinThreads, 0, s>>>(model_args(m), params, verts, ctx->status);
+  k_skin<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, verts, ctx->status);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -345,8 +356,8 @@ int launch_skin_bwd(Context* ctx, const hr_model* m, const float* params, const 
                     cudaStream_t s) {
   int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
   if (blocks > kSkinBlocks) blocks = kSkinBlocks;
-  k_skin_bwd<<<blocks, kSkinThreads, 0, s>>>(model_args(m), params, d_verts, ctx->skin_partials,
-                                             ctx->counters + 2, d_params, ctx->status);
+  k_skin_bwd<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, d_verts, ctx->skin_partials,
+                                                                ctx->counters + 2, 4, d_params, ctx->status);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -425,7 +436,7 @@ extern "C" int hr_skin_bwd_noalloc(const hr_model* m, const float* params, const
     return HR_ERR_CUDA;
   }
   int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
-  k_skin_bwd<<<blocks, kSkinThreads, 0, s>>>(model_args(m), params, d_verts, partials, counter, d_params, status);
+  k_skin_bwd<<<blocks, kSkinThreads, 0, s>>>(model_args(m), params, d_verts, partials, counter, 0, d_params, status);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }

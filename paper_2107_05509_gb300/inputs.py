@@ -62,6 +62,28 @@ PAPER = SceneConfig("paper-8x512x384-16spp", views=8, width=512, height=384, spp
                     azimuths_deg=tuple(45.0 * k for k in range(8)), seed=1000)
 CONFIGS = {0: TINY, 1: PAPER}
 
+# Batched workload: independently seeded instances with their own view count,
+# resolution (W, H) and samples per pixel; 4096 edge samples per view.
+BATCH_RESOLUTIONS = ((256, 256), (512, 384), (512, 512))
+
+
+def batch_configs(n: int = 64, seed_base: int = 2000, views=(4, 16), spp=(8, 32), edge_samples: int = 4096):
+    """n instance scene configs: instance i has seed seed_base + i, a view count
+    uniform in [views[0], views[1]], a resolution drawn from BATCH_RESOLUTIONS, spp
+    uniform in [spp[0], spp[1]], cameras on a ring at 0.6 m (elevation 30 degrees,
+    evenly spaced azimuths from a random start)."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(np.random.SeedSequence([seed_base + i, 77]))
+        nv = int(rng.integers(views[0], views[1] + 1))
+        w, h = BATCH_RESOLUTIONS[int(rng.integers(0, len(BATCH_RESOLUTIONS)))]
+        s = int(rng.integers(spp[0], spp[1] + 1))
+        az0 = float(rng.uniform(0.0, 360.0))
+        out.append(SceneConfig(f"batch{seed_base}-{i}-{nv}x{w}x{h}-{s}spp", views=nv, width=w, height=h, spp=s,
+                               edge_samples=edge_samples, elevation_deg=30.0,
+                               azimuths_deg=tuple(az0 + 360.0 * k / nv for k in range(nv)), seed=seed_base + i))
+    return out
+
 
 # ----------------------------------------------------------------------------------
 # Procedural hand mesh

@@ -141,3 +141,130 @@ def make_views(cfg: I.SceneConfig, model: B.Model, x_gt, device="cuda", ctx=None
     mask = I.coverage_mask(clean_np, bg_np, cfg.mask_dilate_px)
     return Views(cams=cams, background=bg, observed=torch.as_tensor(obs, device=device),
                  mask=torch.as_tensor(mask, device=device), H=H, W=W), verts
+
+
+# --------------------------------------------------------------------------------------
+# Batches: many instances refined together, one launch per kernel per iteration
+# --------------------------------------------------------------------------------------
+
+# Adam step sizes per parameter group [beta(10), theta(45), phi(3), tau(3)]: shape
+# coefficients, radians, radians, metres (Adam's step is about lr whatever the
+# gradient's scale, so each group gets a step in its own unit)
+LR_GROUPS = (0.1, 0.02, 0.02, 1e-3)
+
+
+def lr_scale_vector(groups=LR_GROUPS, device="cuda"):
+    s = np.empty(I.N_PARAMS, np.float32)
+    s[I.P_BETA:I.P_BETA + I.N_SHAPE] = groups[0]
+    s[I.P_THETA:I.P_THETA + I.N_POSE] = groups[1]
+    s[I.P_THETA + I.N_POSE:I.P_TAU] = groups[2]
+    s[I.P_TAU:I.P_TAU + 3] = groups[3]
+    return torch.as_tensor(s, device=device)
+
+
+@dataclasses.dataclass
+class BatchViews:
+    """Device-resident observations of a batch, concatenated in instance order."""
+    cams: torch.Tensor        # [views][20]
+    background: torch.Tensor  # [P][3]
+    observed: torch.Tensor    # [P][3]
+    mask: torch.Tensor        # [P] uint8
+
+
+def make_batch_views(cfgs, model: B.Model, x_gts, device="cuda"):
+    """Observations of every instance (the recipe of make_views: the GT render at
+    cfg.obs_spp with the instance's own Philox instance field, plus noise, and the
+    dilated coverage mask), concatenated in instance order."""
+    hand = model.hand
+    cams, bgs, obss, masks = [], [], [], []
+    for i, (cfg, x) in enumerate(zip(cfgs, x_gts)):
+        N, H, W = cfg.views, cfg.height, cfg.width
+        ctx = B.Context(hand.V, hand.F, hand.E, N, W, H)
+        c = torch.as_tensor(I.pack_cameras(I.make_cameras(cfg, hand.v_template.mean(0))), device=device)
+        bg_np = I.background(cfg.seed, N, H, W)
+        bg = torch.as_tensor(bg_np, device=device)
+        verts = torch.empty((hand.V, 3), device=device)
+        B.hr_skin(ctx, model, torch.as_tensor(np.asarray(x, np.float32), device=device), verts)
+        B.hr_build_bvh(ctx, model, verts)
+        clean = torch.empty((N, H, W, 3), device=device)
+        o = opts_for(cfg, spp=cfg.obs_spp, seed=cfg.seed * 7919 + 1)
+        o.instance = i
+        B.hr_render_fwd(ctx, model, verts, c, H, W, bg, o, clean)
+        clean_np = clean.cpu().numpy()
+        ctx.close()
+        cams.append(c)
+        bgs.append(bg.reshape(-1, 3))
+        obss.append(torch.as_tensor(I.add_noise(clean_np, cfg.seed, cfg.noise_sigma).reshape(-1, 3), device=device))
+        masks.append(torch.as_tensor(I.coverage_mask(clean_np, bg_np, cfg.mask_dilate_px).reshape(-1),
+                                     device=device))
+    return BatchViews(cams=torch.cat(cams), background=torch.cat(bgs), observed=torch.cat(obss),
+                      mask=torch.cat(masks))
+
+
+class BatchRefiner:
+    """Plain refinement of every instance of a batch at once.  One iteration is
+    hr_skin_batch -> hr_build_bvh_batch -> hr_render_fwd_batch -> hr_loss_batch ->
+    hr_render_bwd_batch -> hr_skin_bwd_batch -> hr_adam_step_dev, plus (with ground
+    truth vertices) hr_vertex_error into the error table: a fixed sequence of launches
+    over all instances that capture() records once as a CUDA graph."""
+
+    def __init__(self, model: B.Model, batch: B.Batch, views: BatchViews, seed=17, lr=1.0, lr_groups=LR_GROUPS,
+                 ref_verts=None, max_iters=1024, device="cuda"):
+        self.model, self.batch, self.views = model, batch, views
+        n, V, P = batch.n, model.V, batch.total_pixels
+        self.counter = torch.zeros(1, dtype=torch.int32, device=device)
+        self.opts = B.render_opts(seed=seed, ka=I.K_AMBIENT, kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR,
+                                  light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX, iter_dev=self.counter)
+        self.params = torch.zeros((n, I.N_PARAMS), device=device)
+        self.verts = torch.empty((n, V, 3), device=device)
+        self.image = torch.empty((P, 3), device=device)
+        self.adjoint = torch.empty((P, 3), device=device)
+        self.loss = torch.zeros(n, device=device)
+        self.d_verts = torch.empty((n, V, 3), device=device)
+        self.d_params = torch.empty((n, I.N_PARAMS), device=device)
+        self.m1 = torch.zeros_like(self.params)
+        self.m2 = torch.zeros_like(self.params)
+        self.lr = float(lr)
+        self.lr_scale = lr_scale_vector(lr_groups, device)
+        self.ref_verts = ref_verts
+        self.err = torch.full((max_iters, n), float("nan"), device=device)
+        self.graph = None
+
+    def reset(self, params):
+        self.params.copy_(params)
+        self.m1.zero_()
+        self.m2.zero_()
+        self.counter.zero_()
+        self.err.fill_(float("nan"))
+
+    def iteration(self, stream=None):
+        bt, m, v = self.batch, self.model, self.views
+        B.hr_skin_batch(bt, m, self.params, self.verts, stream)
+        if self.ref_verts is not None:
+            B.hr_vertex_error(self.verts, self.ref_verts, self.err, self.counter, stream)
+        B.hr_build_bvh_batch(bt, m, self.verts, stream)
+        B.hr_render_fwd_batch(bt, m, self.verts, v.cams, v.background, self.opts, self.image, stream)
+        B.hr_loss_batch(bt, self.image, v.observed, v.mask, self.loss, self.adjoint, stream)
+        B.hr_render_bwd_batch(bt, m, self.verts, v.cams, v.background, self.opts, self.adjoint, self.d_verts, stream)
+        B.hr_skin_bwd_batch(bt, m, self.params, self.d_verts, self.d_params, stream)
+        B.hr_adam_step_dev(self.params, self.d_params, self.m1, self.m2, self.lr, 0.9, 0.999, 1e-8, self.counter,
+                           lr_scale=self.lr_scale, stream=stream)
+
+    def capture(self):
+        """Record one iteration as a CUDA graph (warm up first: the first launches of
+        a process load the kernels)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        saved = (self.params.clone(), self.m1.clone(), self.m2.clone(), self.counter.clone())
+        with torch.cuda.stream(s):
+            self.iteration(s)
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.iteration(s)
+        self.graph = g
+        self.params.copy_(saved[0])
+        self.m1.copy_(saved[1])
+        self.m2.copy_(saved[2])
+        self.counter.copy_(saved[3])
+        return g

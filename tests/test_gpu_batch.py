@@ -1,0 +1,189 @@
+"""GPU parity of the batched path: several hand instances with different view
+counts, ragged resolutions, samples per pixel and edge-sample counts go through the
+batch entry points in one launch per kernel, and every instance is compared with the
+CPU oracle run on that instance alone (its own Philox instance field, spp and edge
+samples).  Same bars as the single-instance parity tests."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_05509_gb300 import inputs as I
+from tests.gpu_common import grad_ok, hand, pixel_ok, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+# (views, width, height, spp, edge samples, Philox instance, azimuth offset, seed)
+DESCS = [
+    (2, 64, 48, 4, 512, 5, 0.0, 11),
+    (3, 37, 29, 3, 300, 9, 40.0, 12),    # ragged: neither size a multiple of the 8x4 sub-tile
+    (1, 72, 64, 2, 0, 2, 200.0, 13),     # no edge samples
+]
+
+
+class Inst:
+    def __init__(self, d):
+        N, W, H, spp, ne, inst, az0, seed = d
+        h = hand()
+        cfg = I.SceneConfig(f"batch-{seed}", views=N, width=W, height=H, spp=spp, edge_samples=ne,
+                            elevation_deg=20.0, azimuths_deg=tuple(az0 + 90.0 * k for k in range(N)), seed=seed)
+        cams = I.pack_cameras(I.make_cameras(cfg, h.v_template.mean(0)))
+        for c in cams:   # zoom in so that the hand fills the small images
+            c[0:2] *= 2.5
+        self.N, self.W, self.H, self.spp, self.ne, self.inst = N, W, H, spp, ne, inst
+        self.cams = cams
+        self.bg = I.background(seed, N, H, W)
+        self.x = I.perturb_params(I.gt_params(seed), seed).astype(np.float32)
+        self.verts = oracle.skin(h, self.x).astype(np.float32)
+        self.normals = oracle.vertex_normals(self.verts, h.faces, h.vf_offsets, h.vf_faces)
+        self.opts = oracle.make_opts(seed=4242, iter=3, instance=inst, spp=spp, edge_samples=ne, ka=I.K_AMBIENT,
+                                     kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR, light_rgb=I.LIGHT_RGB,
+                                     edge_eps=I.EDGE_EPS_PX)
+        self.ref = oracle.render_fwd(self.verts, h.faces, self.normals, h.albedo, cams, H, W, self.bg, self.opts)
+        self.observed = I.add_noise(self.bg, seed, 0.05)
+        self.mask = np.ones((N, H, W), np.uint8)
+        self.mask[:, : H // 3] = 0   # a partial mask
+
+
+@pytest.fixture(scope="module")
+def setup():
+    require_gpu()
+    from paper_2107_05509_gb300 import binding as B
+    h = hand()
+    insts = [Inst(d) for d in DESCS]
+    bt = B.Batch(h.V, h.F, h.E, [(i.N, i.W, i.H, i.spp, i.ne, i.inst) for i in insts])
+    model = B.Model(h)
+    return B, h, insts, bt, model
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _cat(arrs, shape_tail):
+    return np.concatenate([np.asarray(a, np.float32).reshape((-1,) + shape_tail) for a in arrs])
+
+
+def _gopts(B, o, flags=0):
+    return B.render_opts(seed=o.seed_lo | (o.seed_hi << 32), iter=o.iter, ka=o.ka, kd=o.kd,
+                         light_dir=tuple(o.light_dir), light_rgb=tuple(o.light_rgb), edge_eps_px=o.edge_eps,
+                         flags=flags)
+
+
+def test_layout(setup):
+    B, h, insts, bt, model = setup
+    assert list(bt.view_offsets) == list(np.cumsum([0] + [i.N for i in insts]))
+    assert list(bt.pixel_offsets) == list(np.cumsum([0] + [i.N * i.H * i.W for i in insts]))
+
+
+def test_batch_skin_and_adjoint(setup):
+    B, h, insts, bt, model = setup
+    n = len(insts)
+    params = _t(np.stack([i.x for i in insts]))
+    verts = torch.empty((n, h.V, 3), device="cuda")
+    B.hr_skin_batch(bt, model, params, verts)
+    g = verts.cpu().numpy()
+    for k, i in enumerate(insts):
+        assert np.abs(g[k] - oracle.skin(h, i.x)).max() < 2e-6
+    rng = np.random.default_rng(1)
+    dV = rng.normal(0, 1, (n, h.V, 3)).astype(np.float32)
+    dp = torch.empty((n, 61), device="cuda")
+    B.hr_skin_bwd_batch(bt, model, params, _t(dV), dp)
+    gp = dp.cpu().numpy()
+    for k, i in enumerate(insts):
+        ok = grad_ok(gp[k], oracle.skin_bwd(h, i.x, dV[k]))
+        assert ok.all(), (k, np.argwhere(~ok))
+    assert B.hr_get_status(bt) == B.HR_OK
+
+
+def test_batch_forward_loss_backward(setup):
+    B, h, insts, bt, model = setup
+    n = len(insts)
+    verts = _t(np.stack([i.verts for i in insts]))
+    cams = _t(_cat([i.cams for i in insts], (I.CAM_FLOATS,)))
+    bg = _t(_cat([i.bg for i in insts], (3,)))
+    obs = _t(_cat([i.observed for i in insts], (3,)))
+    mask = _t(np.concatenate([i.mask.reshape(-1) for i in insts]))
+    P = bt.total_pixels
+    img = torch.empty((P, 3), device="cuda")
+    go = _gopts(B, insts[0].opts)
+    B.hr_build_bvh_batch(bt, model, verts)
+    B.hr_render_fwd_batch(bt, model, verts, cams, bg, go, img)
+    g_img = img.cpu().numpy()
+    po = bt.pixel_offsets
+    for k, i in enumerate(insts):
+        gi = g_img[po[k]:po[k + 1]].reshape(i.N, i.H, i.W, 3)
+        ok = pixel_ok(gi, i.ref)
+        assert ok.all(), (k, np.argwhere(~ok)[:5], np.abs(gi - i.ref).max())
+    # per-instance loss and adjoint of the oracle's render
+    ref_img = _t(_cat([i.ref.astype(np.float32) for i in insts], (3,)))
+    loss = torch.zeros(n, device="cuda")
+    adj = torch.empty((P, 3), device="cuda")
+    B.hr_loss_batch(bt, ref_img, obs, mask, loss, adj)
+    L = loss.cpu().numpy()
+    A = adj.cpu().numpy()
+    A_refs = []
+    for k, i in enumerate(insts):
+        L_ref, A_ref = oracle.loss(i.ref.astype(np.float32), i.observed, i.mask)
+        assert abs(L[k] - L_ref) <= 1e-5 * abs(L_ref), (k, L[k], L_ref)
+        a = A[po[k]:po[k + 1]].reshape(i.N, i.H, i.W, 3)
+        assert np.array_equal(np.sign(a), np.sign(A_ref))
+        assert np.abs(a - A_ref).max() <= 1e-7 * np.abs(A_ref).max()
+        A_refs.append(A_ref.astype(np.float32))
+    # backward of the oracle's adjoint, every term, per instance
+    dv = torch.empty((n, h.V, 3), device="cuda")
+    B.hr_render_bwd_batch(bt, model, verts, cams, bg, go, _t(_cat(A_refs, (3,))), dv)
+    gd = dv.cpu().numpy()
+    for k, i in enumerate(insts):
+        ref, _ = oracle.render_bwd(h, i.verts, i.cams, i.H, i.W, i.bg, i.opts, A_refs[k], normals=i.normals)
+        assert np.abs(ref).max() > 0
+        ok = grad_ok(gd[k], ref)
+        assert ok.all(), (k, np.argwhere(~ok)[:5], gd[k][~ok][:5], ref[~ok][:5])
+    assert B.hr_get_status(bt) == B.HR_OK
+
+
+def test_batch_of_one_equals_single_context(setup):
+    """A one-instance batch renders the same image, bit for bit, as a single-instance
+    context given that instance's spp, edge samples and instance field."""
+    B, h, insts, bt, model = setup
+    i = insts[1]
+    b1 = B.Batch(h.V, h.F, h.E, [(i.N, i.W, i.H, i.spp, i.ne, i.inst)])
+    ctx = B.Context(h.V, h.F, h.E, i.N, i.W, i.H)
+    v = _t(i.verts)
+    cams, bg = _t(i.cams), _t(i.bg)
+    a = torch.empty((i.N, i.H, i.W, 3), device="cuda")
+    b = torch.empty_like(a)
+    B.hr_build_bvh(ctx, model, v)
+    o = i.opts
+    single = B.render_opts(seed=o.seed_lo | (o.seed_hi << 32), iter=o.iter, instance=o.instance, spp=o.spp,
+                           edge_samples=o.edge_samples, ka=o.ka, kd=o.kd, light_dir=tuple(o.light_dir),
+                           light_rgb=tuple(o.light_rgb), edge_eps_px=o.edge_eps)
+    B.hr_render_fwd(ctx, model, v, cams, i.H, i.W, bg, single, a)
+    B.hr_build_bvh_batch(b1, model, v.reshape(1, h.V, 3))
+    B.hr_render_fwd_batch(b1, model, v.reshape(1, h.V, 3), cams, bg, _gopts(B, o), b.reshape(-1, 3))
+    assert torch.equal(a, b)
+    assert B.hr_get_status(ctx) == B.HR_OK and B.hr_get_status(b1) == B.HR_OK
+
+
+def test_batch_calls_reject_single_context(setup):
+    B, h, insts, bt, model = setup
+    i = insts[0]
+    ctx = B.Context(h.V, h.F, h.E, i.N, i.W, i.H)
+    v = _t(i.verts)
+    with pytest.raises(B.HandrtError):
+        B.hr_build_bvh_batch(ctx, model, v)
+    with pytest.raises(B.HandrtError):
+        B.hr_build_bvh(bt, model, v)
+
+
+def test_vertex_error_matches_oracle(setup):
+    B, h, insts, bt, model = setup
+    n = len(insts)
+    a = np.stack([i.verts for i in insts])
+    b = np.stack([oracle.skin(h, I.gt_params(7 + k)).astype(np.float32) for k in range(n)])
+    out = torch.full((4, n), -1.0, device="cuda")
+    ctr = torch.full((1,), 2, dtype=torch.int32, device="cuda")
+    B.hr_vertex_error(_t(a), _t(b), out, ctr)
+    got = out.cpu().numpy()
+    for k in range(n):
+        assert abs(got[2, k] * 1e3 - oracle.vertex_error_mm(a[k], b[k])) <= 1e-5 * oracle.vertex_error_mm(a[k], b[k])
+    assert (got[[0, 1, 3]] == -1.0).all()   # only row *iter_dev is written
