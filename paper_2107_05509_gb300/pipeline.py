@@ -56,9 +56,10 @@ class Refiner:
         self.d_verts = torch.empty((hand.V, 3), device=dev)
         self.d_params = torch.empty(61, device=dev)
 
-    def forward(self, params, stream=None):
+    def forward(self, params, stream=None, skin=True):
         ctx, m, v = self.ctx, self.model, self.views
-        B.hr_skin(ctx, m, params, self.verts, stream)
+        if skin:
+            B.hr_skin(ctx, m, params, self.verts, stream)
         B.hr_build_bvh(ctx, m, self.verts, stream)
         B.hr_render_fwd(ctx, m, self.verts, v.cams, v.H, v.W, v.background, self.opts, self.image, stream)
         B.hr_loss(ctx, self.image, v.observed, v.mask, self.loss, self.adjoint, stream)
@@ -268,3 +269,45 @@ class BatchRefiner:
         self.m2.copy_(saved[2])
         self.counter.copy_(saved[3])
         return g
+
+
+class PlainRefiner:
+    """Plain per-instance refinement through the single-instance calls, one
+    iteration captured as a CUDA graph: hr_skin -> (hr_vertex_error) -> hr_build_bvh
+    -> hr_render_fwd -> hr_loss -> hr_render_bwd -> hr_skin_bwd -> hr_adam_step_dev
+    with per-group step sizes; the device counter advances the sample streams."""
+
+    def __init__(self, model: B.Model, views: Views, cfg: I.SceneConfig, instance=0, seed=17, lr=1.0,
+                 lr_groups=LR_GROUPS, ref_verts=None, max_iters=1024, ctx=None, device="cuda"):
+        self.counter = torch.zeros(1, dtype=torch.int32, device=device)
+        opts = B.render_opts(seed=seed, instance=instance, spp=cfg.spp, edge_samples=cfg.edge_samples,
+                             ka=I.K_AMBIENT, kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR, light_rgb=I.LIGHT_RGB,
+                             edge_eps_px=I.EDGE_EPS_PX, iter_dev=self.counter)
+        self.r = Refiner(model, views, opts, ctx=ctx)
+        self.params = torch.zeros(I.N_PARAMS, device=device)
+        self.m1 = torch.zeros_like(self.params)
+        self.m2 = torch.zeros_like(self.params)
+        self.lr = float(lr)
+        self.lr_scale = lr_scale_vector(lr_groups, device)
+        self.ref_verts = ref_verts
+        self.err = torch.full((max_iters, 1), float("nan"), device=device)
+        self.graph = None
+
+    def reset(self, params):
+        self.params.copy_(params)
+        self.m1.zero_()
+        self.m2.zero_()
+        self.counter.zero_()
+        self.err.fill_(float("nan"))
+
+    def iteration(self, stream=None):
+        r = self.r
+        B.hr_skin(r.ctx, r.model, self.params, r.verts, stream)
+        if self.ref_verts is not None:
+            B.hr_vertex_error(r.verts, self.ref_verts, self.err, self.counter, stream)
+        r.forward(self.params, stream, skin=False)
+        r.backward(self.params, stream)
+        B.hr_adam_step_dev(self.params, r.d_params, self.m1, self.m2, self.lr, 0.9, 0.999, 1e-8, self.counter,
+                           lr_scale=self.lr_scale, stream=stream)
+
+    capture = BatchRefiner.capture
