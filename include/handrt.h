@@ -48,6 +48,7 @@ extern "C" {
 #define HR_ERR_NONFINITE (-4)   /* non-finite parameters reached the skinning kernel */
 #define HR_ERR_UNSUPPORTED (-5) /* sizes beyond what the context was created for */
 #define HR_ERR_INTERNAL (-6)    /* a kernel read an internal index out of range and skipped it */
+#define HR_ERR_TIMEOUT (-7)     /* a bounded device-side wait ran out; that kernel's work was abandoned */
 
 typedef void* hr_stream; /* a cudaStream_t */
 
@@ -288,6 +289,19 @@ int hr_render_bwd_batch(hr_context* ctx, const hr_model* model, const float* ver
                         const float* background, const hr_render_opts* opts, const float* adjoint, float* d_verts,
                         hr_stream stream);
 
+/* BF16 matrix product on the tensor cores (tcgen05, float32 accumulation), the
+ * building block of the learned proposal network:
+ *   C[M][N] = act(A[M][K] B[N][K]^T + bias[N]),  act = ReLU when relu != 0.
+ * A, B: device bf16, row-major with K contiguous and row pitches lda, ldb (elements;
+ * multiples of 8, base addresses 16-byte aligned); K a multiple of 64.  bias: device
+ * float[N] or NULL.  C: device bf16 (out_bf16 != 0) or float32, row pitch ldc.
+ * splits > 1 divides K among that many CTAs per output tile (for long K) and needs
+ * split_buf, device float[splits][M][N]; the partials are summed in split order.
+ * A bounded wait that runs out sets HR_ERR_TIMEOUT in the context's status word. */
+int hr_gemm_bf16(hr_context* ctx, const void* A, int lda, const void* B, int ldb, int M, int N, int K,
+                 const float* bias, int relu, void* C, int ldc, int out_bf16, int splits, float* split_buf,
+                 hr_stream stream);
+
 /* Diagnostics over the context's current scene (used by the tests; on a batch
  * context they see instance 0):
  *   hr_trace:        closest hit of n rays (origins, dirs: device float[n][3]) against
@@ -320,7 +334,7 @@ int hr_kernel_times(hr_context* ctx, float* ms, int n);
 /* Synchronise `stream`, then return and clear the device status word: HR_OK, or the
  * HR_ERR_* code of a device-detected error since the last call (HR_ERR_ARG for face
  * or parent indices out of range, then HR_ERR_INTERNAL, HR_ERR_NONFINITE,
- * HR_ERR_LIMIT). */
+ * HR_ERR_LIMIT, HR_ERR_TIMEOUT). */
 int hr_get_status(hr_context* ctx, hr_stream stream);
 
 /* Static text for a status code. */

@@ -24,6 +24,7 @@ HR_ERR_LIMIT = -3
 HR_ERR_NONFINITE = -4
 HR_ERR_UNSUPPORTED = -5
 HR_ERR_INTERNAL = -6
+HR_ERR_TIMEOUT = -7
 HR_BWD_NO_INTERIOR = 1
 HR_BWD_NO_EDGES = 2
 HR_BWD_NO_NORMALS = 4
@@ -36,7 +37,8 @@ EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", 
            "hr_loss", "hr_render_bwd", "hr_adam_step", "hr_trace", "hr_get_normals", "hr_silhouettes",
            "hr_get_stats", "hr_get_status", "hr_status_string", "hr_skin_bwd_noalloc", "hr_kernel_times",
            "hr_adam_step_dev", "hr_vertex_error", "hr_batch_create", "hr_batch_layout", "hr_skin_batch",
-           "hr_skin_bwd_batch", "hr_build_bvh_batch", "hr_render_fwd_batch", "hr_loss_batch", "hr_render_bwd_batch")
+           "hr_skin_bwd_batch", "hr_build_bvh_batch", "hr_render_fwd_batch", "hr_loss_batch", "hr_render_bwd_batch",
+           "hr_gemm_bf16")
 
 
 class HandrtError(RuntimeError):
@@ -102,6 +104,7 @@ def lib():
             "hr_render_fwd_batch": [P, P, P, P, P, P, P, P],
             "hr_loss_batch": [P, P, P, P, P, P, P],
             "hr_render_bwd_batch": [P, P, P, P, P, P, P, P, P],
+            "hr_gemm_bf16": [P, P, I, P, I, I, I, I, P, I, P, I, I, I, P, P],
             "hr_trace": [P, P, P, I, P, P, P],
             "hr_get_normals": [P, P, P],
             "hr_silhouettes": [P, P, P, P, I, P, P, P],
@@ -316,6 +319,21 @@ def hr_vertex_error(verts, ref, out, iter_dev=None, stream=None):
     _check("hr_vertex_error", lib().hr_vertex_error(_f32(verts), _f32(ref), V, n, _f32(out),
                                                     None if iter_dev is None else _ptr(iter_dev), rows,
                                                     _stream(stream)))
+
+
+def hr_gemm_bf16(ctx, A, Bm, C, bias=None, relu=False, splits=1, split_buf=None, stream=None):
+    """C = act(A Bm^T + bias) on the tensor cores: A [M][K], Bm [N][K] bf16 (row
+    pitch = stride(0)), C [M][N] bf16 or float32."""
+    assert A.dtype == torch.bfloat16 and Bm.dtype == torch.bfloat16 and A.stride(1) == 1 and Bm.stride(1) == 1
+    assert C.dtype in (torch.bfloat16, torch.float32) and C.stride(1) == 1
+    M, K = A.shape
+    N = Bm.shape[0]
+    assert Bm.shape[1] == K and C.shape[0] == M and C.shape[1] >= N
+    ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    _check("hr_gemm_bf16", lib().hr_gemm_bf16(ctx.handle, ptr(A), A.stride(0), ptr(Bm), Bm.stride(0), M, N, K,
+                                              None if bias is None else _f32(bias), int(bool(relu)), ptr(C),
+                                              C.stride(0), int(C.dtype == torch.bfloat16), int(splits),
+                                              None if split_buf is None else _f32(split_buf), _stream(stream)))
 
 
 # batches (hr_batch_create): concatenated per-instance arrays, see include/handrt.h

@@ -110,7 +110,9 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
   for (int i = 0; ok && i < 2 * hr::kTimeSlots; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
   // kernel attributes are set here, once, so that the per-iteration calls are only
   // launches and asynchronous memsets
-  if (ok) ok = hr::configure_bvh_kernels() == HR_OK && hr::configure_render_kernels(lim->max_V) == HR_OK;
+  if (ok)
+    ok = hr::configure_bvh_kernels() == HR_OK && hr::configure_render_kernels(lim->max_V) == HR_OK &&
+         hr::configure_gemm_kernels() == HR_OK;
   if (!ok) {
     cudaGetLastError();
     free_ctx(c);
@@ -352,6 +354,15 @@ int hr_vertex_error(const float* verts, const float* ref, int V, int n, float* o
   return hr::launch_vertex_error(verts, ref, V, n, out, iter_dev, rows, (cudaStream_t)stream);
 }
 
+int hr_gemm_bf16(hr_context* ctx, const void* A, int lda, const void* B, int ldb, int M, int N, int K,
+                 const float* bias, int relu, void* C, int ldc, int out_bf16, int splits, float* split_buf,
+                 hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !A || !B || !C || ldc < N) return HR_ERR_ARG;
+  return hr::launch_gemm(A, lda, B, ldb, M, N, K, bias, relu, C, ldc, out_bf16, splits, split_buf, c->status,
+                         (cudaStream_t)stream);
+}
+
 int hr_adam_step(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
                  float eps, int step, hr_stream stream) {
   if (!params || !grad || !m || !v || n <= 0 || step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
@@ -445,6 +456,7 @@ int hr_get_status(hr_context* ctx, hr_stream stream) {
   if (host & hr::kStatusIndex) return HR_ERR_INTERNAL;
   if (host & hr::kStatusNonfinite) return HR_ERR_NONFINITE;
   if (host & hr::kStatusLimit) return HR_ERR_LIMIT;
+  if (host & hr::kStatusTimeout) return HR_ERR_TIMEOUT;
   return HR_OK;
 }
 
@@ -457,6 +469,7 @@ const char* hr_status_string(int code) {
     case HR_ERR_NONFINITE: return "non-finite parameters";
     case HR_ERR_UNSUPPORTED: return "size beyond the context's limits";
     case HR_ERR_INTERNAL: return "internal index out of range (access skipped)";
+    case HR_ERR_TIMEOUT: return "a bounded device wait ran out (work abandoned)";
     default: return "unknown status";
   }
 }

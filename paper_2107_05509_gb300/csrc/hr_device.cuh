@@ -19,6 +19,7 @@ constexpr int kStatusLimit = 1;     // device status bits
 constexpr int kStatusNonfinite = 2;
 constexpr int kStatusBadModel = 4;  // a face or parent index out of range
 constexpr int kStatusIndex = 8;     // an internal index read from device memory out of range
+constexpr int kStatusTimeout = 16;  // a bounded device-side wait ran out
 // HR_TIMING event slots: forward gather/shade/combine, backward gather/shade/reduce/
 // silhouettes/edges/normal adjoint
 constexpr int kTimeFwdGather = 0, kTimeFwdShade = 1, kTimeFwdCombine = 2, kTimeBwdGather = 3, kTimeBwdShade = 4,

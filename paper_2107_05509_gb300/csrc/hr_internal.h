@@ -28,6 +28,12 @@ int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float l
 int launch_vertex_error(const float* verts, const float* ref, int V, int n, float* out, const uint32_t* iter_dev,
                         int rows, cudaStream_t s);
 
+// bf16 tensor-core GEMM C = act(A B^T + bias) (hr_gemm.cu); splits > 1 needs
+// split_buf of splits * M * N floats
+int launch_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, const float* bias, int relu,
+                void* C, int ldc, int out_bf16, int splits, float* split_buf, int* status, cudaStream_t s);
+int configure_gemm_kernels();
+
 // per-device properties of the render kernels (persistent grid)
 int render_grid(int device, int* blocks, int* threads, int* num_sms);
 size_t render_bwd_smem(int V);
