@@ -302,6 +302,67 @@ int hr_gemm_bf16(hr_context* ctx, const void* A, int lda, const void* B, int ldb
                  const float* bias, int relu, void* C, int ldc, int out_bf16, int splits, float* split_buf,
                  hr_stream stream);
 
+/* ---------------------------------------------------------------------------------
+ * Learned proposal (an extension: the paper refines by gradient descent alone).  A
+ * small network maps per-view residual images of an estimate to a parameter update;
+ * refinement takes its proposals first and keeps each instance's best candidate by
+ * the photometric loss, so the plain method stays the fallback and the judge.
+ *
+ * Network, per view of each of B instances with `views` views (B * views a multiple
+ * of 4), all weights and activations bf16 with float32 accumulation on the tensor
+ * cores (hr_gemm_bf16):
+ *   input   128x128x8: 2x2 means of a 256x256 render R and observation O, as
+ *           (R - O, O, 0, 0)
+ *   conv    five 3x3 convolutions, stride 2, padding 1, ReLU: 8->32, 32->64, 64->128,
+ *           128->128, 128->128 (output 4x4x128)
+ *   view    ReLU(Wv [features(2048), camera R (9), camera centre / 0.6 m (3), 0] + bv),
+ *           256 per view; the maximum over the instance's views
+ *   head    ReLU(W1 . + b1) (256), W2 . + b2 (61) times the per-group scales
+ *           (0.5 shape, 0.1 rad pose, 0.1 rad root rotation, 0.005 m translation)
+ * Parameters: one float32 vector of hr_net_param_count() entries: per layer W [N][K]
+ * row-major then b [N], for the five convolutions (K = 9 Cin rounded up to 64, tap-
+ * major then channel: k = (3 ky + kx) Cin + c, the padding columns zero), the view
+ * layer (K = 2112), W1 (K = 256), W2 (N = 64: rows 61-63 zero).
+ * --------------------------------------------------------------------------------- */
+typedef struct hr_net hr_net;
+
+int hr_net_param_count(void);
+/* Allocate a network for B instances of `views` views (all scratch up front). */
+int hr_net_create(int B, int views, hr_net** out);
+int hr_net_destroy(hr_net* net);
+/* Load parameters (device float[hr_net_param_count()]) and reset the Adam moments. */
+int hr_net_set_params(hr_net* net, const float* params, hr_stream stream);
+/* Copy the parameters and/or the last gradient (device float[count], either NULL). */
+int hr_net_get_params(hr_net* net, float* params, float* grads, hr_stream stream);
+/* Inputs from renders and observations: device float[B * views][H][W][3] with
+ * W = H = 256 (instances' views consecutive). */
+int hr_net_inputs(hr_net* net, const float* render, const float* observed, int W, int H, hr_stream stream);
+/* Inputs given directly: device bf16[B * views][128][128][8]. */
+int hr_net_set_inputs_bf16(hr_net* net, const void* x0, hr_stream stream);
+/* Forward: out[b] = base[b] + delta[b] (device float[B][61]; base NULL = 0).
+ * cams: device hr_camera[B * views]. */
+int hr_net_forward(hr_net* net, const float* cams, const float* base, float* out, hr_stream stream);
+/* Backward of the last forward for d_out = dL/d delta (device float[B][61]): the
+ * parameter gradient, kept in the network (hr_net_get_params). */
+int hr_net_backward(hr_net* net, const float* d_out, hr_stream stream);
+/* Adam step (step >= 1) on the parameters with the last gradient. */
+int hr_net_adam(hr_net* net, float lr, float beta1, float beta2, float eps, int step, hr_stream stream);
+/* Synchronise and return/clear the network's status (HR_OK or HR_ERR_TIMEOUT). */
+int hr_net_status(hr_net* net, hr_stream stream);
+
+/* Training loss of the proposal: loss[i] = (1/V) sum_v |verts[i][v] - ref[i][v]|^2 and,
+ * when d_verts is given, d_verts = d((1/n) sum_i loss[i]) / d verts (device arrays
+ * float[n][V][3], loss float[n]). */
+int hr_vertex_mse(const float* verts, const float* ref, int V, int n, float* loss, float* d_verts,
+                  hr_stream stream);
+/* image[i] += sigma * N(0, 1) for i < n (Philox4x32-10 keyed by seed, Box-Muller). */
+int hr_add_noise(float* image, int64_t n, float sigma, uint64_t seed, hr_stream stream);
+/* Per instance i < n, the candidate with the lowest loss (the earliest on ties):
+ * params[i] = candidates[k*][i] for candidates device float[K][n][61], losses float[K][n];
+ * chosen (device int32[n] or NULL) receives k*. */
+int hr_select_best(const float* candidates, const float* losses, int K, int n, float* params, int32_t* chosen,
+                   hr_stream stream);
+
 /* Diagnostics over the context's current scene (used by the tests; on a batch
  * context they see instance 0):
  *   hr_trace:        closest hit of n rays (origins, dirs: device float[n][3]) against

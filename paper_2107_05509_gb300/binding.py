@@ -38,7 +38,9 @@ EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", 
            "hr_get_stats", "hr_get_status", "hr_status_string", "hr_skin_bwd_noalloc", "hr_kernel_times",
            "hr_adam_step_dev", "hr_vertex_error", "hr_batch_create", "hr_batch_layout", "hr_skin_batch",
            "hr_skin_bwd_batch", "hr_build_bvh_batch", "hr_render_fwd_batch", "hr_loss_batch", "hr_render_bwd_batch",
-           "hr_gemm_bf16")
+           "hr_gemm_bf16", "hr_net_param_count", "hr_net_create", "hr_net_destroy", "hr_net_set_params",
+           "hr_net_get_params", "hr_net_inputs", "hr_net_set_inputs_bf16", "hr_net_forward", "hr_net_backward",
+           "hr_net_adam", "hr_net_status", "hr_vertex_mse", "hr_add_noise", "hr_select_best")
 
 
 class HandrtError(RuntimeError):
@@ -105,6 +107,20 @@ def lib():
             "hr_loss_batch": [P, P, P, P, P, P, P],
             "hr_render_bwd_batch": [P, P, P, P, P, P, P, P, P],
             "hr_gemm_bf16": [P, P, I, P, I, I, I, I, P, I, P, I, I, I, P, P],
+            "hr_net_param_count": [],
+            "hr_net_create": [I, I, P],
+            "hr_net_destroy": [P],
+            "hr_net_set_params": [P, P, P],
+            "hr_net_get_params": [P, P, P, P],
+            "hr_net_inputs": [P, P, P, I, I, P],
+            "hr_net_set_inputs_bf16": [P, P, P],
+            "hr_net_forward": [P, P, P, P, P],
+            "hr_net_backward": [P, P, P],
+            "hr_net_adam": [P, F, F, F, F, I, P],
+            "hr_net_status": [P, P],
+            "hr_vertex_mse": [P, P, I, I, P, P, P],
+            "hr_add_noise": [P, ctypes.c_int64, F, ctypes.c_uint64, P],
+            "hr_select_best": [P, P, I, I, P, P, P],
             "hr_trace": [P, P, P, I, P, P, P],
             "hr_get_normals": [P, P, P],
             "hr_silhouettes": [P, P, P, P, I, P, P, P],
@@ -334,6 +350,75 @@ def hr_gemm_bf16(ctx, A, Bm, C, bias=None, relu=False, splits=1, split_buf=None,
                                               None if bias is None else _f32(bias), int(bool(relu)), ptr(C),
                                               C.stride(0), int(C.dtype == torch.bfloat16), int(splits),
                                               None if split_buf is None else _f32(split_buf), _stream(stream)))
+
+
+class Net:
+    """The proposal network (hr_net_*) for B instances of `views` views."""
+
+    def __init__(self, B, views):
+        h = ctypes.c_void_p()
+        _check("hr_net_create", lib().hr_net_create(int(B), int(views), ctypes.byref(h)))
+        self.handle = h
+        self.B, self.views = int(B), int(views)
+        self.P = int(lib().hr_net_param_count())
+
+    def close(self):
+        if self.handle:
+            lib().hr_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params, stream=None):
+        assert params.numel() == self.P
+        _check("hr_net_set_params", lib().hr_net_set_params(self.handle, _f32(params), _stream(stream)))
+
+    def get_params(self, params=None, grads=None, stream=None):
+        _check("hr_net_get_params", lib().hr_net_get_params(self.handle, None if params is None else _f32(params),
+                                                            None if grads is None else _f32(grads), _stream(stream)))
+
+    def inputs(self, render, observed, W=256, H=256, stream=None):
+        _check("hr_net_inputs", lib().hr_net_inputs(self.handle, _f32(render), _f32(observed), W, H,
+                                                    _stream(stream)))
+
+    def set_inputs_bf16(self, x0, stream=None):
+        assert x0.dtype == torch.bfloat16
+        _check("hr_net_set_inputs_bf16", lib().hr_net_set_inputs_bf16(self.handle, _ptr(x0), _stream(stream)))
+
+    def forward(self, cams, out, base=None, stream=None):
+        _check("hr_net_forward", lib().hr_net_forward(self.handle, _f32(cams), None if base is None else _f32(base),
+                                                      _f32(out), _stream(stream)))
+
+    def backward(self, d_out, stream=None):
+        _check("hr_net_backward", lib().hr_net_backward(self.handle, _f32(d_out), _stream(stream)))
+
+    def adam(self, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check("hr_net_adam", lib().hr_net_adam(self.handle, lr, beta1, beta2, eps, int(step), _stream(stream)))
+
+    def status(self, stream=None):
+        return int(lib().hr_net_status(self.handle, _stream(stream)))
+
+
+def hr_vertex_mse(verts, ref, loss, d_verts=None, stream=None):
+    V = verts.shape[-2]
+    n = verts.numel() // (3 * V)
+    _check("hr_vertex_mse", lib().hr_vertex_mse(_f32(verts), _f32(ref), V, n, _f32(loss),
+                                                None if d_verts is None else _f32(d_verts), _stream(stream)))
+
+
+def hr_add_noise(image, sigma, seed, stream=None):
+    _check("hr_add_noise", lib().hr_add_noise(_f32(image), image.numel(), float(sigma), int(seed), _stream(stream)))
+
+
+def hr_select_best(candidates, losses, params, chosen=None, stream=None):
+    K, n = losses.shape
+    assert chosen is None or chosen.dtype == torch.int32
+    _check("hr_select_best", lib().hr_select_best(_f32(candidates), _f32(losses), K, n, _f32(params),
+                                                  None if chosen is None else _ptr(chosen), _stream(stream)))
 
 
 # batches (hr_batch_create): concatenated per-instance arrays, see include/handrt.h

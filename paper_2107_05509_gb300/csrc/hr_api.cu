@@ -363,6 +363,24 @@ int hr_gemm_bf16(hr_context* ctx, const void* A, int lda, const void* B, int ldb
                          (cudaStream_t)stream);
 }
 
+int hr_vertex_mse(const float* verts, const float* ref, int V, int n, float* loss, float* d_verts,
+                  hr_stream stream) {
+  if (!verts || !ref || !loss || V < 1 || n < 1) return HR_ERR_ARG;
+  return hr::launch_vertex_mse(verts, ref, V, n, loss, d_verts, (cudaStream_t)stream);
+}
+
+int hr_add_noise(float* image, int64_t n, float sigma, uint64_t seed, hr_stream stream) {
+  if (!image || n < 0) return HR_ERR_ARG;
+  if (n == 0) return HR_OK;
+  return hr::launch_add_noise(image, n, sigma, seed, (cudaStream_t)stream);
+}
+
+int hr_select_best(const float* candidates, const float* losses, int K, int n, float* params, int32_t* chosen,
+                   hr_stream stream) {
+  if (!candidates || !losses || !params || K < 1 || n < 1) return HR_ERR_ARG;
+  return hr::launch_select_best(candidates, losses, K, n, params, chosen, (cudaStream_t)stream);
+}
+
 int hr_adam_step(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1, float beta2,
                  float eps, int step, hr_stream stream) {
   if (!params || !grad || !m || !v || n <= 0 || step < 1 || !(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) ||

@@ -25,6 +25,10 @@ int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, f
                 int step, cudaStream_t s);
 int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
                     const float* lr_scale, int scale_len, uint32_t* iter_dev, cudaStream_t s);
+int launch_vertex_mse(const float* a, const float* b, int V, int n, float* loss, float* grad, cudaStream_t s);
+int launch_add_noise(float* img, long long n, float sigma, uint64_t seed, cudaStream_t s);
+int launch_select_best(const float* cand, const float* losses, int K, int n, float* out, int* chosen,
+                       cudaStream_t s);
 int launch_vertex_error(const float* verts, const float* ref, int V, int n, float* out, const uint32_t* iter_dev,
                         int rows, cudaStream_t s);
 

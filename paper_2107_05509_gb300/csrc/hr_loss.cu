@@ -241,11 +241,94 @@ __global__ void __launch_bounds__(kErrThreads) k_vertex_error(const float* __res
   if (row < (unsigned)rows) out[(size_t)row * gridDim.x + blockIdx.x] = (float)(red[0] / V);
 }
 
+// training loss of the proposal network: per instance (block) the mean squared
+// vertex distance L_i = (1/V) sum_v |a - b|^2 (fixed-order sum), and the gradient of
+// (1/n) sum_i L_i with respect to a
+__global__ void __launch_bounds__(kErrThreads) k_vertex_mse(const float* __restrict__ a, const float* __restrict__ b,
+                                                           int V, float* __restrict__ loss,
+                                                           float* __restrict__ grad) {
+  __shared__ double red[kErrThreads];
+  const size_t o = (size_t)blockIdx.x * 3 * V;
+  const float sc = 2.0f / ((float)V * (float)gridDim.x);
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < 3 * V; i += kErrThreads) {
+    const float d = a[o + i] - b[o + i];
+    acc += (double)d * d;
+    if (grad) grad[o + i] = sc * d;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kErrThreads >> 1; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[blockIdx.x] = (float)(red[0] / V);
+}
+
+// image[i] += sigma * N(0, 1): Philox4x32-10 keyed by seed, counter (i / 4, 0, 0, 0),
+// two Box-Muller pairs per counter
+__global__ void k_add_noise(float* __restrict__ img, long long n, float sigma, uint2 key) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (4 * t >= n) return;
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0u, 0u), key);
+  const float u[4] = {((r.x >> 8) + 1) * 5.9604644775390625e-08f, (r.y >> 8) * 5.9604644775390625e-08f,
+                      ((r.z >> 8) + 1) * 5.9604644775390625e-08f, (r.w >> 8) * 5.9604644775390625e-08f};
+  float z[4];
+  for (int k = 0; k < 2; ++k) {
+    const float rad = sqrtf(-2.0f * logf(u[2 * k]));
+    float sn, cs;
+    sincospif(2.0f * u[2 * k + 1], &sn, &cs);
+    z[2 * k] = rad * cs;
+    z[2 * k + 1] = rad * sn;
+  }
+  for (int k = 0; k < 4 && 4 * t + k < n; ++k) img[4 * t + k] += sigma * z[k];
+}
+
+// per instance, the candidate with the lowest loss (the earliest on ties) of K
+// candidates: out[i] = cand[k*][i], losses [K][n], cand [K][n][61]
+__global__ void k_select_best(const float* __restrict__ cand, const float* __restrict__ losses, int K, int n,
+                              float* __restrict__ out, int* __restrict__ chosen) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  int best = 0;
+  float bl = losses[i];
+  for (int k = 1; k < K; ++k) {
+    const float l = losses[(size_t)k * n + i];
+    if (l < bl) {
+      bl = l;
+      best = k;
+    }
+  }
+  for (int j = threadIdx.x; j < 61; j += blockDim.x) out[(size_t)i * 61 + j] = cand[((size_t)best * n + i) * 61 + j];
+  if (chosen && threadIdx.x == 0) chosen[i] = best;
+}
+
 }  // namespace
 
 int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
                     const float* lr_scale, int scale_len, uint32_t* iter_dev, cudaStream_t s) {
   k_adam_dev<<<1, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, lr_scale, scale_len, iter_dev);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_vertex_mse(const float* a, const float* b, int V, int n, float* loss, float* grad, cudaStream_t s) {
+  k_vertex_mse<<<n, kErrThreads, 0, s>>>(a, b, V, loss, grad);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_add_noise(float* img, long long n, float sigma, uint64_t seed, cudaStream_t s) {
+  const long long t = (n + 3) / 4;
+  k_add_noise<<<(unsigned)((t + 255) / 256), 256, 0, s>>>(img, n, sigma,
+                                                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_select_best(const float* cand, const float* losses, int K, int n, float* out, int* chosen,
+                       cudaStream_t s) {
+  k_select_best<<<n, 64, 0, s>>>(cand, losses, K, n, out, chosen);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
