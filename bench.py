@@ -368,7 +368,6 @@ def run_handrt(args):
     }
     if not args.no_refine and world == 1:
         line["refinement"] = run_refinement(args, dev)
-        line["gpu_launches_refinement"] = LAUNCHES_BATCH_ITER * (args.refine_iters + 4)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_seconds)
     if dist:
@@ -382,26 +381,21 @@ def _first_at_or_below(err_mm, thr=1.0):
     return int(ok[0]) if ok.size else -1
 
 
-def run_refinement(args, dev):
-    """Time-to-1 mm: the batched workload (independently seeded instances with 4-16
-    views at 256x256 / 512x384 / 512x512 and 8-32 spp) refined two ways from the same
-    initial estimates with the same sample streams -- all instances together through
-    the batch calls (one CUDA graph per iteration), and plain per-instance
-    refinement through the single-instance calls, instance after instance (one CUDA
-    graph per instance).  The mean vertex error epsilon_v (Section 4.1) is recorded
-    on the device every iteration; time-to-1 mm is the device time until the mean
-    over instances is <= 1 mm ("mean") and until every instance has been <= 1 mm
-    ("each", per-instance stopping for the plain pipeline)."""
+def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
+    """Refine the instances of `cfgs` from the same initial estimates with the same
+    sample streams: plain per-instance refinement through the single-instance calls,
+    instance after instance (one CUDA graph each); all instances together through the
+    batch calls (one CUDA graph per iteration); and, with `learned` parameters, the
+    batch preceded by the learned proposal steps.  The mean vertex error epsilon_v
+    (Section 4.1) is recorded on the device every iteration."""
     import torch
 
     from paper_2107_05509_gb300 import binding as B
     from paper_2107_05509_gb300 import inputs as I
     from paper_2107_05509_gb300 import pipeline as P
 
-    n, iters = args.batch_instances, args.refine_iters
-    hand = I.make_hand(0)
-    model = B.Model(hand, device=dev)
-    cfgs = I.batch_configs(n)
+    n = len(cfgs)
+    hand = model.hand
     x_gt = [I.gt_params(c.seed) for c in cfgs]
     x0 = torch.as_tensor(np.stack([I.perturb_params(x, c.seed) for x, c in zip(x_gt, cfgs)]), device=dev)
     views = P.make_batch_views(cfgs, model, x_gt, device=dev)
@@ -423,19 +417,42 @@ def run_refinement(args, dev):
     g = R.capture()
     for _ in range(3):
         g.replay()
-    R.reset(x0)
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 1)]
-    ev[0].record()
-    for k in range(iters):
-        g.replay()
-        ev[k + 1].record()
-    torch.cuda.synchronize()
-    dt_b = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(iters)])
-    err_b = R.err[:iters].cpu().numpy() * 1e3
-    status = B.hr_get_status(bt)
-    if status != B.HR_OK:
-        raise RuntimeError(f"batch device status {B.status_string(status)}")
+
+    def run_batch(pre=None):
+        R.reset(x0)
+        torch.cuda.synchronize()
+        pre_ms = 0.0
+        if pre is not None:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pre()
+            e1.record()
+            torch.cuda.synchronize()
+            pre_ms = e0.elapsed_time(e1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 1)]
+        ev[0].record()
+        for k in range(iters):
+            g.replay()
+            ev[k + 1].record()
+        torch.cuda.synchronize()
+        dt = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(iters)])
+        err = R.err[:iters].cpu().numpy() * 1e3
+        status = B.hr_get_status(bt)
+        if status != B.HR_OK:
+            raise RuntimeError(f"batch device status {B.status_string(status)}")
+        return err, dt, pre_ms
+
+    err_b, dt_b, _ = run_batch()
+    res_learned = None
+    if learned is not None:
+        from paper_2107_05509_gb300 import proposal as PR
+        prop = PR.Proposer(R, learned, steps=proposal_steps)
+        prop.run()                       # warm-up of the network's kernels
+        err_l, dt_l, pre_ms = run_batch(prop.run)
+        chosen = prop.chosen.cpu().numpy()
+        if prop.net.status() != B.HR_OK:
+            raise RuntimeError("proposal network status")
+        res_learned = (err_l, dt_l, pre_ms, chosen)
 
     # plain per-instance refinement, instance after instance
     err_p = np.full((iters, n), np.nan)
@@ -462,43 +479,75 @@ def run_refinement(args, dev):
             raise RuntimeError("plain refinement device status")
         pr.r.ctx.close()
 
-    def summary(err, dt, per_instance_time):
+    def summary(err, dt, sequential, pre_ms=0.0):
         mean = err.mean(1)
         k = _first_at_or_below(mean)
         firsts = np.array([_first_at_or_below(err[:, i]) for i in range(err.shape[1])])
+        cap = np.where(firsts >= 0, firsts, err.shape[0] - 1)
         out = {"iters_to_mean_1mm": k, "mean_err_mm_at_start": round(float(mean[0]), 3),
                "mean_err_mm_at_end": round(float(mean[-1]), 4),
                "instances_at_or_below_1mm_at_end": int((err[-1] <= 1.0).sum()),
                "instances_never_1mm": int((firsts < 0).sum())}
-        if per_instance_time:
-            # plain: every instance runs k iterations, instance after instance
-            out["time_to_mean_1mm_ms"] = round(float(dt[:k + 1].sum()), 2) if k >= 0 else None
-            cap = np.where(firsts >= 0, firsts, err.shape[0] - 1)
+        # plain: every instance runs its iterations instance after instance (dt [iters][n])
+        out["time_to_mean_1mm_ms"] = round(pre_ms + float(dt[:k + 1].sum()), 2) if k >= 0 else None
+        if sequential:
             out["time_to_each_1mm_ms"] = round(float(sum(dt[:cap[i] + 1, i].sum() for i in range(err.shape[1]))), 2)
         else:
-            out["time_to_mean_1mm_ms"] = round(float(dt[:k + 1].sum()), 2) if k >= 0 else None
-            last = int(np.max(np.where(firsts >= 0, firsts, err.shape[0] - 1)))
-            out["time_to_each_1mm_ms"] = round(float(dt[:last + 1].sum()), 2)
+            out["time_to_each_1mm_ms"] = round(pre_ms + float(dt[:int(cap.max()) + 1].sum()), 2)
         return out
 
     sb = summary(err_b, dt_b, False)
     sp = summary(err_p, dt_p, True)
     sb["ms_per_iter"] = round(float(np.median(dt_b)), 3)
+    sb["value"] = round(rays / (float(np.median(dt_b)) * 1e-3) / 1e6, 1)
+    sb["unit"] = UNIT
+    sb["rays_per_iter"] = int(rays)
+    sb["launches_per_iter"] = LAUNCHES_BATCH_ITER
     sp["ms_per_iter_sum_over_instances"] = round(float(np.median(dt_p.sum(1))), 3)
-    res = {
-        "workload": f"batch-{n}x(4-16 views, 256x256|512x384|512x512, 8-32 spp, 4096 edge samples/view)",
-        "instances": n, "views": int(bt.total_views), "pixels": int(bt.total_pixels), "iterations": iters,
-        "batched": dict(sb, rays_per_iter=int(rays),
-                        value=round(rays / (float(np.median(dt_b)) * 1e-3) / 1e6, 1), unit=UNIT,
-                        launches_per_iter=LAUNCHES_BATCH_ITER),
-        "plain_sequential": sp,
-        "adam_lr_per_group": {"shape": P.LR_GROUPS[0], "pose_rad": P.LR_GROUPS[1], "root_rot_rad": P.LR_GROUPS[2],
-                              "trans_m": P.LR_GROUPS[3]},
-    }
-    if sb["time_to_mean_1mm_ms"] and sp["time_to_mean_1mm_ms"]:
-        res["speedup_time_to_mean_1mm"] = round(sp["time_to_mean_1mm_ms"] / sb["time_to_mean_1mm_ms"], 3)
-    res["speedup_time_to_each_1mm"] = round(sp["time_to_each_1mm_ms"] / sb["time_to_each_1mm_ms"], 3)
+    res = {"instances": n, "views": int(bt.total_views), "pixels": int(bt.total_pixels), "iterations": iters,
+           "plain_sequential": sp, "batched": sb}
+    if res_learned is not None:
+        err_l, dt_l, pre_ms, chosen = res_learned
+        sl = summary(err_l, dt_l, False, pre_ms)
+        sl["proposal_steps"] = proposal_steps
+        sl["proposal_ms"] = round(pre_ms, 3)
+        sl["instances_taking_a_proposal"] = int((chosen > 0).sum())
+        res["batched_learned"] = sl
+    for name in ("batched", "batched_learned"):
+        if name in res and res[name]["time_to_mean_1mm_ms"] and sp["time_to_mean_1mm_ms"]:
+            res[f"speedup_time_to_mean_1mm_{name}_vs_plain"] = round(
+                sp["time_to_mean_1mm_ms"] / res[name]["time_to_mean_1mm_ms"], 3)
     return res
+
+
+def run_refinement(args, dev):
+    """Time-to-1 mm on two batched workloads: (1) heterogeneous instances (4-16 views
+    at 256x256 / 512x384 / 512x512, 8-32 spp): plain per-instance vs batched; (2) the
+    learned proposal's rig (8 views at 256x256, 16 spp): plain vs batched vs batched
+    with the learned proposal steps first."""
+    from paper_2107_05509_gb300 import binding as B
+    from paper_2107_05509_gb300 import inputs as I
+    from paper_2107_05509_gb300 import pipeline as P
+    from paper_2107_05509_gb300 import proposal as PR
+    import dataclasses
+
+    n, iters = args.batch_instances, args.refine_iters
+    hand = I.make_hand(0)
+    model = B.Model(hand, device=dev)
+    het = refine_compare(I.batch_configs(n), model, dev, iters)
+    het["workload"] = f"batch-{n}x(4-16 views, 256x256|512x384|512x512, 8-32 spp, 4096 edge samples/view)"
+    rig = [dataclasses.replace(PR.RIG, seed=PR.RIG.seed + 100 + i, name=f"{PR.RIG.name}-{i}") for i in range(n)]
+    learned, meta = PR.load_weights()
+    lr = refine_compare(rig, model, dev, iters, learned=learned)
+    lr["workload"] = f"rig-{n}x(8 views 256x256, 16 spp, 4096 edge samples/view)"
+    lr["proposal_training"] = {k: meta[k] for k in ("pairs", "steps", "seconds", "heldout_eps_v_mm") if k in meta}
+    return {"heterogeneous": het, "learned_rig": lr,
+            "adam_lr_per_group": {"shape": P.LR_GROUPS[0], "pose_rad": P.LR_GROUPS[1],
+                                  "root_rot_rad": P.LR_GROUPS[2], "trans_m": P.LR_GROUPS[3]},
+            "criterion": "time_to_mean_1mm: device time until the mean over instances of epsilon_v <= 1 mm "
+                         "(plain: every instance refined that many iterations, one after another); "
+                         "time_to_each_1mm: until every instance has been <= 1 mm (plain: per-instance "
+                         "stopping), iteration cap counted for instances that never get there"}
 
 
 def _oracle_sample(budget_s):
