@@ -368,6 +368,7 @@ def run_handrt(args):
     }
     if not args.no_refine and world == 1:
         line["refinement"] = run_refinement(args, dev)
+        line["tensor"] = run_tensor(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_seconds)
     if dist:
@@ -550,6 +551,68 @@ def run_refinement(args, dev):
                          "stopping), iteration cap counted for instances that never get there"}
 
 
+def run_tensor(dev, steps=20):
+    """The bf16 tensor-core GEMM (tcgen05) on the proposal network's largest shapes and
+    on a square product, and one training step of the network (B = 128 instances x 8
+    views: two batched renders, forward, backward, Adam)."""
+    import torch
+
+    from paper_2107_05509_gb300 import binding as B
+    from paper_2107_05509_gb300 import inputs as I
+    from paper_2107_05509_gb300 import proposal as PR
+
+    pk, pk_kind = peaks()
+    ctx = B.Context(8, 8, 8, 1, 8, 8)
+    out = {}
+    shapes = {"conv1_fwd": (4194304, 32, 128), "conv4_fwd": (65536, 128, 1152), "view_fwd": (1024, 256, 2112),
+              "square_8192": (8192, 8192, 8192)}
+    g = torch.Generator(device=dev).manual_seed(0)
+    for name, (M, N, K) in shapes.items():
+        A = torch.randn(M, K, device=dev, generator=g).to(torch.bfloat16)
+        Bm = torch.randn(N, K, device=dev, generator=g).to(torch.bfloat16)
+        C = torch.empty(M, N, device=dev, dtype=torch.bfloat16)
+        for _ in range(3):
+            B.hr_gemm_bf16(ctx, A, Bm, C)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            a.record()
+            B.hr_gemm_bf16(ctx, A, Bm, C)
+            b.record()
+        torch.cuda.synchronize()
+        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        out[name] = {"M": M, "N": N, "K": K, "ms": round(ms, 4), "TFLOP/s": round(tf, 1)}
+        del A, Bm, C
+    if B.hr_get_status(ctx) != B.HR_OK:
+        raise RuntimeError("gemm status")
+    sq = out["square_8192"]
+    peak = pk.get("bf16_tflops", 1900.0)
+    roof = {"bound": "tensor", "kernel": "k_gemm_bf16<128>", "achieved": sq["TFLOP/s"], "peak": peak,
+            "unit": "TFLOP/s", "frac": round(sq["TFLOP/s"] / peak, 4), "traffic": None,
+            "peak_note": f"dense bf16, cuBLAS 8192^3 burst ({pk_kind})", "shape": "8192 x 8192 x 8192"}
+    # one training step of the proposal network
+    hand = I.make_hand(0)
+    model = B.Model(hand, device=dev)
+    tr = PR.Trainer(model, batch=128, seed=1)
+    tr.set_params(PR.init_params(1))
+    for _ in range(3):
+        tr.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_st = 10
+    e0.record()
+    for _ in range(n_st):
+        tr.step()
+    e1.record()
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / n_st
+    ctx.close()
+    return {"gemm": out, "roofline_tensor": roof,
+            "proposal_train_step": {"instances": 128, "views": 8, "ms": round(step_ms, 3),
+                                    "pairs_per_s": round(128 / (step_ms * 1e-3), 1)}}
+
+
 def _oracle_sample(budget_s):
     """Time the oracle (forward + interior backward + edge samples) on a band of rows
     of the workload, grown until it has run about `budget_s` seconds."""
@@ -636,9 +699,15 @@ def main():
     ap.add_argument("--no-refine", action="store_true", help="skip the time-to-1 mm refinement comparison")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--refine-iters", type=int, default=150)
+    ap.add_argument("--gemm-only", action="store_true", help="only the tensor-core GEMM timings (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "handrt":
         args.warmup = 3
+    if args.gemm_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_tensor(torch.device("cuda", 0))), flush=True)
+        return
     line = run_reference(args) if args.impl == "reference" else run_handrt(args)
     if line is not None:
         print(json.dumps(line), flush=True)
