@@ -157,10 +157,10 @@ def run_handrt(args):
     lr = 2e-3
 
     # work counters of one step (untimed pass)
-    opts.flags = B.HR_STATS
+    opts.flags = B.HR_STATS | B.HR_BWD_REUSE_FWD
     ref.step(params)
     stats = B.hr_get_stats(ctx).astype(np.float64)
-    opts.flags = 0
+    opts.flags = B.HR_BWD_REUSE_FWD
     rays_fwd, rays_bwd, rays_edge = stats[0, S_SAMPLES], stats[1, S_SAMPLES], stats[2, S_SAMPLES]
     rays_step = rays_fwd + rays_bwd + rays_edge
 
@@ -256,7 +256,7 @@ def run_handrt(args):
     # per-kernel device times: a second timed pass with CUDA events recorded by the
     # library between its internal kernels (HR_TIMING), L2 flushed between steps
     ktimes = {k: [] for k in B.KERNEL_TIMES}
-    opts.flags = B.HR_TIMING
+    opts.flags = B.HR_TIMING | B.HR_BWD_REUSE_FWD
     n_kt = max(1, min(args.steps, 50))
     for k in range(n_kt):
         flush.fill_(float(k))
@@ -264,7 +264,7 @@ def run_handrt(args):
         for name, ms in B.hr_kernel_times(ctx).items():
             if ms >= 0:
                 ktimes[name].append(ms)
-    opts.flags = 0
+    opts.flags = B.HR_BWD_REUSE_FWD
     kt_mean = {k: float(np.mean(v)) for k, v in ktimes.items() if v}
 
     # end-to-end through the public API with host buffers
@@ -408,10 +408,10 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
 
     # work counters of one batched iteration
     R.reset(x0)
-    R.opts.flags = B.HR_STATS
+    R.opts.flags = B.HR_STATS | B.HR_BWD_REUSE_FWD
     R.iteration()
     stats = B.hr_get_stats(bt).astype(np.float64)
-    R.opts.flags = 0
+    R.opts.flags = B.HR_BWD_REUSE_FWD
     rays = float(stats[:, S_SAMPLES].sum())
 
     R.reset(x0)

@@ -126,6 +126,12 @@ typedef struct hr_render_opts {
 #define HR_BWD_NO_NORMALS 4u   /* hr_render_bwd: skip the vertex-normal adjoint    */
 #define HR_STATS 8u            /* count rays, BVH nodes, triangle tests and hits   */
 #define HR_TIMING 16u          /* record CUDA events around the internal kernels   */
+#define HR_BWD_REUSE_FWD 32u   /* hr_render_bwd: take the candidate lists of the last
+                                  hr_render_fwd on this context instead of traversing
+                                  the BVH again -- honoured only when that forward used
+                                  the same vertex and camera pointers, sizes and spp and
+                                  no hr_build_bvh came after it; the caller guarantees
+                                  that the contents of both arrays are unchanged      */
 
 /* Sizes a context is created for; all scratch is allocated once, up front. */
 typedef struct hr_limits {

@@ -344,6 +344,8 @@ int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaSt
   HR_CHECK_LAUNCH();
   ctx->V = V;
   ctx->F = F;
+  ++ctx->bvh_gen;
+  ctx->fwd_valid = false;
   return HR_OK;
 }
 

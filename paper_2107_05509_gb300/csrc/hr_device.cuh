@@ -81,6 +81,14 @@ struct Context {
   int render_threads;
   // scene, one per instance (per-instance arrays are [n_inst][...], contiguous)
   int V, F;              // sizes of the last hr_build_bvh
+  unsigned bvh_gen;      // builds so far
+  // the last forward render (its candidate pool serves a backward with
+  // HR_BWD_REUSE_FWD): vertices, cameras, sizes and the build it used
+  const void* fwd_verts;
+  const void* fwd_cams;
+  int fwd_N, fwd_H, fwd_W, fwd_spp;
+  unsigned fwd_gen;
+  bool fwd_valid;
   Node* nodes;           // [n_inst][max_F]
   float4* tris;          // [n_inst][max_F][3]
   float* normals;        // [n_inst][max_V][3] unit vertex normals

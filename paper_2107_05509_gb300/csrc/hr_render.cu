@@ -50,7 +50,7 @@ namespace {
 
 constexpr int kRenderThreads = 128;   // 4 warps per block
 constexpr int kWarps = kRenderThreads / 32;
-constexpr int kBwdMinBlocks = 6;
+constexpr int kBwdMinBlocks = 5;
 constexpr int kBlocksPerSm = 8;       // persistent grid; backward partials are sized for it
 static_assert(kBwdMinBlocks <= kBlocksPerSm, "backward partials are sized for kBlocksPerSm blocks per SM");
 constexpr int kSubW = 8, kSubH = 4;   // sub-tile; lane = pixel
@@ -863,6 +863,50 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
   flush_counts<STATS>(cnt, stats);
 }
 
+// The backward's work items from the forward's candidate lists (HR_BWD_REUSE_FWD):
+// one warp per sub-tile with candidates and a non-zero adjoint allocates its items in
+// its instance's region; when the region is full the warp does the sub-tile itself.
+template <bool STATS>
+__global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, const float* __restrict__ adjoint,
+                                                             unsigned long long* stats) {
+  const RenderArgs a0 = with_iter(a_in);
+  const int lane = threadIdx.x & 31;
+  Counts cnt;
+  const int total = subtile_count(a0);
+  const int nw = gridDim.x * kWarps;
+  for (int st = blockIdx.x * kWarps + (threadIdx.x >> 5); st < total; st += nw) {
+    int2 pk = a0.wk.st[st];
+    const SubTile t = subtile(a0, st);
+    if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
+    const RenderArgs a = for_inst(a0, t.inst);
+    bool live;
+    const float3 g = lane_adjoint(a, t, adjoint, live);
+    if (!__any_sync(0xffffffffu, live)) continue;
+    if (pk.y == 0) {   // no ray of the sub-tile can hit: no interior gradient
+      if (STATS && live) cnt.samples += t.spp;
+      continue;
+    }
+    if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
+    const int C = chunks_for(pk.y, t.spp);
+    const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
+    int first = 0;
+    if (lane == 0) first = (int)atomicAdd(&a.wk.ctr[2 + 2 * t.inst], (unsigned)C);
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (first + C <= icap) {
+      for (int c = lane; c < C; c += 32) a.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
+    } else {
+      for (int c = lane; c < C; c += 32)
+        if (first + c < icap) a.wk.items[ibase + first + c] = make_int4(-1, 0, 0, 0);
+      __threadfence_block();
+      const Cam cam = load_cam(a.cams, t.view);
+      float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
+      grad_samples<STATS>(a, t, cam, pk.x, pk.y, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
+    }
+    __syncwarp();
+  }
+  flush_counts<STATS>(cnt, stats);
+}
+
 // items of an instance's region that the gather filled
 __device__ __forceinline__ int item_count(const RenderArgs& a, int inst) {
   return (int)min(*reinterpret_cast<volatile unsigned*>(&a.wk.ctr[2 + 2 * inst]), (unsigned)inst_icap(a, inst));
@@ -1006,19 +1050,32 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
   for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) out[i] = sacc[i];
 }
 
-// d_verts[i] = extra[i] + sum_b partials[b][i] (i < 3V), dN[i-3V] likewise, in
-// fixed block order.  blockIdx.y selects the instance (a batch has no partials).
-__global__ void k_reduce_partials(const float* __restrict__ partials, const float* __restrict__ extra_all,
-                                  int nblocks, int V, float* __restrict__ d_verts_all, float* __restrict__ dN_all) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 6 * V) return;
+// d_verts[i] = extra[i] + sum_b partials[b][i] (i < 3V), dN[i-3V] likewise.  A block
+// covers 32 entries with 16 groups of threads: group g sums partials g, g + 16, ...
+// in order, then the 16 group sums are added in group order (a fixed order for every
+// call).  blockIdx.y selects the instance (a batch has no partials).
+constexpr int kRedEntries = 32, kRedGroups = 16;
+__global__ void __launch_bounds__(kRedEntries * kRedGroups) k_reduce_partials(
+    const float* __restrict__ partials, const float* __restrict__ extra_all, int nblocks, int V,
+    float* __restrict__ d_verts_all, float* __restrict__ dN_all) {
+  __shared__ float red[kRedGroups][kRedEntries];
+  const int j = threadIdx.x % kRedEntries, g = threadIdx.x / kRedEntries;
+  const int i = blockIdx.x * kRedEntries + j;
+  float acc = 0.0f;
+  if (i < 6 * V) {
+#pragma unroll 4
+    for (int b = g; b < nblocks; b += kRedGroups) acc += partials[(size_t)b * 6 * V + i];
+  }
+  red[g][j] = acc;
+  __syncthreads();
+  if (g != 0 || i >= 6 * V) return;
   const float* extra = extra_all + (size_t)blockIdx.y * 6 * V;
   float* d_verts = d_verts_all + (size_t)blockIdx.y * 3 * V;
   float* dN = dN_all + (size_t)blockIdx.y * 3 * V;
-  float acc = extra[i];
-  for (int b = 0; b < nblocks; ++b) acc += partials[(size_t)b * 6 * V + i];
-  if (i < 3 * V) d_verts[i] = acc;
-  else dN[i - 3 * V] = acc;
+  float tot = extra[i];
+  for (int q = 0; q < kRedGroups; ++q) tot += red[q][j];
+  if (i < 3 * V) d_verts[i] = tot;
+  else dN[i - 3 * V] = tot;
 }
 
 // per view: silhouette flags in edge order, compacted by a block-wide scan.  In a
@@ -1075,15 +1132,94 @@ __global__ void k_silhouettes(const float* __restrict__ verts_all, const int* __
   if (threadIdx.x == 0) counts[view] = base;
 }
 
-// boundary term (edge sampling); one thread per (view, sample): thread i is sample
-// i % Ne_max of global view i / Ne_max (views with fewer samples skip the rest)
+// closest hit among the pool candidates at `off` for one ray, searched by the whole
+// warp: lane l tests candidate base + l of each group of 32 (depth-sorted), the warp
+// keeps the nearest (t, then the lower triangle id), and stops at the first group
+// whose nearest depth is beyond the hit found so far -- the same hit as testing the
+// candidates one by one in depth order.  Every lane returns the same hit.
 template <bool STATS>
-__global__ void k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoint, const int* __restrict__ edges,
-                               const int* __restrict__ lists, int stride, const int* __restrict__ counts, int Ne_max,
-                               float eps, float* __restrict__ d_verts_all, unsigned long long* stats) {
+__device__ __forceinline__ Hit closest_candidate_warp(const RenderArgs& a, int off, int K, float sx, float sy,
+                                                      float3 o, float3 d, Counts& cnt) {
+  const int lane = threadIdx.x & 31;
+  Hit h{-1, INFINITY, 0.0f, 0.0f};
+  for (int base = 0; base < K; base += 32) {
+    if (!in_range(a.status, off + base, 0, a.wk.pool_cap)) break;
+    const float z0 = __ldg(&a.wk.z[off + base]);
+    if (h.t < z0 - (1e-4f * fabsf(z0) + 1e-6f)) break;   // uniform: h is the warp's hit
+    Hit m{-1, INFINITY, 0.0f, 0.0f};
+    const int c = base + lane;
+    if (c < K && in_range(a.status, off + c, 0, a.wk.pool_cap)) {
+      const float zm = __ldg(&a.wk.z[off + c]);
+      if (!(h.t < zm - (1e-4f * fabsf(zm) + 1e-6f))) {
+        const float4 bb = __ldg(&a.wk.bb[off + c]);
+        if (STATS) ++cnt.cands;
+        if (sx >= bb.x && sx <= bb.z && sy >= bb.y && sy <= bb.w) {
+          const int k = __ldg(&a.wk.rec[off + c]);
+          if (in_range(a.status, k, 0, a.max_visits - 1)) isect<STATS>(a.tris, k, o, d, m, cnt);
+        }
+      }
+    }
+    // warp minimum of (t, id)
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+      const float t2 = __shfl_xor_sync(0xffffffffu, m.t, sh);
+      const int i2 = __shfl_xor_sync(0xffffffffu, m.tri, sh);
+      const float u2 = __shfl_xor_sync(0xffffffffu, m.u, sh);
+      const float v2 = __shfl_xor_sync(0xffffffffu, m.v, sh);
+      if (i2 >= 0 && (m.tri < 0 || t2 < m.t || (t2 == m.t && i2 < m.tri))) {
+        m.t = t2;
+        m.tri = i2;
+        m.u = u2;
+        m.v = v2;
+      }
+    }
+    if (m.tri >= 0 && (m.t < h.t || (m.t == h.t && m.tri < h.tri))) h = m;
+  }
+  return h;
+}
+
+// radiance through (sx, sy) for the whole warp (every lane returns the same value)
+template <bool STATS>
+__device__ __forceinline__ float3 radiance_warp(const RenderArgs& a, const Cam& cam, long long pix0, int W, float sx,
+                                                float sy, int bx, int by, int off, int K, Counts& cnt) {
+  const float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
+  const float3 d = primary_dir(cam, sx, sy);
+  const int lane = threadIdx.x & 31;
+  if (STATS && lane == 0) {
+    ++cnt.samples;
+    ++cnt.rays;
+  }
+  Hit h{-1, INFINITY, 0.0f, 0.0f};
+  if (K > 0) {
+    h = closest_candidate_warp<STATS>(a, off, K, sx, sy, o, d, cnt);
+  } else if (K < 0) {
+    Counts c0;
+    if (lane == 0) h = trace<STATS>(a.nodes, a.tris, o, d, a.status, STATS ? cnt : c0, a.max_visits);
+    h.tri = __shfl_sync(0xffffffffu, h.tri, 0);
+    h.t = __shfl_sync(0xffffffffu, h.t, 0);
+    h.u = __shfl_sync(0xffffffffu, h.u, 0);
+    h.v = __shfl_sync(0xffffffffu, h.v, 0);
+  }
+  if (STATS && lane == 0) cnt.hits += h.tri >= 0;
+  if (h.tri >= 0) return shade(a, h);
+  return ld3(a.bg + 3 * (pix0 + (size_t)by * W + bx));
+}
+
+// boundary term (edge sampling); one warp per (view, sample): warp i is sample
+// i % Ne_max of global view i / Ne_max (views with fewer samples skip the rest).  The
+// lanes compute the sample's set-up redundantly (same values, broadcast loads), search
+// the candidates of both offset rays together, and lanes 0-5 add the six results.
+template <bool STATS>
+__global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoint,
+                                                                 const int* __restrict__ edges,
+                                                                 const int* __restrict__ lists, int stride,
+                                                                 const int* __restrict__ counts, int Ne_max, float eps,
+                                                                 float* __restrict__ d_verts_all,
+                                                                 unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)a0.nviews * Ne_max) return;
+  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= (long long)a0.nviews * Ne_max) return;   // whole warps leave together
   const int view = (int)(i / Ne_max), k = (int)(i - (long long)view * Ne_max);
   SubTile vw;
   int st0, nsx;
@@ -1127,33 +1263,30 @@ __global__ void k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoin
   int2 pk = a.wk.st[st];
   if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
   Counts cnt;
-  float3 fp = radiance<STATS>(a, cam, vw.pix0, W, xp, yp, bxp, byp, pk.x, pk.y, cnt);
-  float3 fm = radiance<STATS>(a, cam, vw.pix0, W, xm, ym, bxm, bym, pk.x, pk.y, cnt);
+  float3 fp = radiance_warp<STATS>(a, cam, vw.pix0, W, xp, yp, bxp, byp, pk.x, pk.y, cnt);
+  float3 fm = radiance_warp<STATS>(a, cam, vw.pix0, W, xm, ym, bxm, bym, pk.x, pk.y, cnt);
   if (STATS) {
     unsigned v[kStatsPer] = {cnt.samples, cnt.rays, cnt.nodes, cnt.tris, cnt.hits, cnt.cands};
-    for (int q = 0; q < kStatsPer; ++q)
-      if (v[q]) atomicAdd(stats + q, (unsigned long long)v[q]);
+    for (int q = 0; q < kStatsPer; ++q) {
+      unsigned long long xq = v[q];
+      for (int o2 = 16; o2 > 0; o2 >>= 1) xq += __shfl_down_sync(0xffffffffu, xq, o2);
+      if (lane == 0 && xq) atomicAdd(stats + q, xq);
+    }
   }
   float wgt = (A.x * (fp.x - fm.x) + A.y * (fp.y - fm.y) + A.z * (fp.z - fm.z)) * ((float)nsil / (float)Ne);
-  if (wgt == 0.0f) return;
+  if (wgt == 0.0f || lane >= 6) return;
   float dax = wgt * (by - y), day = wgt * (x - bx), dbx = wgt * (y - ay), dby = wgt * (ax - x);
-  // projection Jacobians d(screen)/d(vertex)
-  float3 pv[2] = {va, vb};
-  float g2[2][2] = {{dax, day}, {dbx, dby}};
-  int ids[2] = {ia, ib};
-  for (int q = 0; q < 2; ++q) {
-    float3 p = pv[q];
-    float X = cam.R[0] * p.x + cam.R[1] * p.y + cam.R[2] * p.z + cam.t[0];
-    float Y = cam.R[3] * p.x + cam.R[4] * p.y + cam.R[5] * p.z + cam.t[1];
-    float Z = cam.R[6] * p.x + cam.R[7] * p.y + cam.R[8] * p.z + cam.t[2];
-    float iz = 1.0f / Z;
-    float gx = g2[q][0] * cam.fx * iz, gy = g2[q][1] * cam.fy * iz;
-    float gz = -(gx * X + gy * Y) * iz;
-    // J^T g = R^T (gx, gy, gz)
-    atomicAdd(&d_verts[3 * ids[q]], cam.R[0] * gx + cam.R[3] * gy + cam.R[6] * gz);
-    atomicAdd(&d_verts[3 * ids[q] + 1], cam.R[1] * gx + cam.R[4] * gy + cam.R[7] * gz);
-    atomicAdd(&d_verts[3 * ids[q] + 2], cam.R[2] * gx + cam.R[5] * gy + cam.R[8] * gz);
-  }
+  // projection Jacobian of endpoint q = lane / 3, coordinate lane % 3: J^T g = R^T (gx, gy, gz)
+  const int q = lane / 3, comp = lane % 3;
+  const float3 p = q == 0 ? va : vb;
+  const float g2x = q == 0 ? dax : dbx, g2y = q == 0 ? day : dby;
+  float X = cam.R[0] * p.x + cam.R[1] * p.y + cam.R[2] * p.z + cam.t[0];
+  float Y = cam.R[3] * p.x + cam.R[4] * p.y + cam.R[5] * p.z + cam.t[1];
+  float Z = cam.R[6] * p.x + cam.R[7] * p.y + cam.R[8] * p.z + cam.t[2];
+  float iz = 1.0f / Z;
+  float gx = g2x * cam.fx * iz, gy = g2y * cam.fy * iz;
+  float gz = -(gx * X + gy * Y) * iz;
+  atomicAdd(&d_verts[3 * (q == 0 ? ia : ib) + comp], cam.R[comp] * gx + cam.R[3 + comp] * gy + cam.R[6 + comp] * gz);
 }
 
 // dm_v = (I - n n^T) dN_v / |m_v|; blockIdx.y selects the instance
@@ -1353,6 +1486,14 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   HR_CHECK_LAUNCH();
   tm.end(kTimeFwdCombine);
   if (tm.on) ctx->ev_ready |= 1;
+  ctx->fwd_verts = verts;
+  ctx->fwd_cams = cams;
+  ctx->fwd_N = N;
+  ctx->fwd_H = H;
+  ctx->fwd_W = W;
+  ctx->fwd_spp = o->spp;
+  ctx->fwd_gen = ctx->bvh_gen;
+  ctx->fwd_valid = true;
   return HR_OK;
 }
 
@@ -1382,12 +1523,23 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     if (cudaMemsetAsync(ctx->work_ctr, 0, (2 + 2 * ni) * sizeof(unsigned), s) != cudaSuccess ||
         cudaMemsetAsync(ctx->extra, 0, sizeof(float) * 6 * V * ni, s) != cudaSuccess)
       return HR_ERR_CUDA;
+    // the forward's candidate lists still describe this scene when it used the same
+    // vertices, cameras and sizes after the last build
+    const bool reuse = (o->flags & HR_BWD_REUSE_FWD) && ctx->fwd_valid && ctx->fwd_verts == verts &&
+                       ctx->fwd_cams == cams && ctx->fwd_N == N && ctx->fwd_H == H && ctx->fwd_W == W &&
+                       (batch || ctx->fwd_spp == o->spp) && ctx->fwd_gen == ctx->bvh_gen;
     tm.begin(kTimeBwdGather);
-    if (st)
+    if (reuse) {
+      if (st)
+        k_items_bwd<true><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, ctx->stats + kStatsPer);
+      else
+        k_items_bwd<false><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr);
+    } else if (st) {
       k_gather<true, true><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr,
                                                                           ctx->stats + kStatsPer);
-    else
+    } else {
       k_gather<true, false><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
+    }
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdGather);
   }
@@ -1401,8 +1553,8 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdShade);
     tm.begin(kTimeBwdReduce);
-    k_reduce_partials<<<dim3((6 * V + 255) / 256, ni), 256, 0, s>>>(ctx->partials, ctx->extra, batch ? 0 : blocks, V,
-                                                                    d_verts, ctx->dN);
+    k_reduce_partials<<<dim3((6 * V + kRedEntries - 1) / kRedEntries, ni), kRedEntries * kRedGroups, 0, s>>>(
+        ctx->partials, ctx->extra, batch ? 0 : blocks, V, d_verts, ctx->dN);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdReduce);
   } else {
@@ -1413,11 +1565,12 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     int rc = launch_silhouettes(ctx, m, verts, cams, nv, ctx->sil, ctx->lim.max_E, ctx->sil_count, s);
     if (rc != HR_OK) return rc;
     tm.end(kTimeBwdSil);
-    long long n = (long long)nv * Ne;
+    const long long n = (long long)nv * Ne * 32;   // one warp per edge sample
     auto kern = st ? k_edge_samples<true> : k_edge_samples<false>;
     tm.begin(kTimeBwdEdges);
-    kern<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count,
-                                                     Ne, o->edge_eps_px, d_verts, ctx->stats + 2 * kStatsPer);
+    kern<<<(unsigned)((n + kRenderThreads - 1) / kRenderThreads), kRenderThreads, 0, s>>>(
+        a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count, Ne, o->edge_eps_px, d_verts,
+        ctx->stats + 2 * kStatsPer);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdEdges);
   }

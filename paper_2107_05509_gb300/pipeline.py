@@ -114,10 +114,12 @@ class HandRenderLoss(torch.autograd.Function):
 # Synthetic multiframes
 # --------------------------------------------------------------------------------------
 
-def opts_for(cfg: I.SceneConfig, spp=None, seed=None, iter=0, iter_dev=None):
+def opts_for(cfg: I.SceneConfig, spp=None, seed=None, iter=0, iter_dev=None, flags=B.HR_BWD_REUSE_FWD):
+    """Render options of a workload; the backward reuses the forward's candidate lists
+    (a refinement iteration renders and differentiates the same scene)."""
     return B.render_opts(seed=cfg.seed * 7919 + 17 if seed is None else seed, iter=iter, spp=spp or cfg.spp,
                          edge_samples=cfg.edge_samples, ka=I.K_AMBIENT, kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR,
-                         light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX, iter_dev=iter_dev)
+                         light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX, iter_dev=iter_dev, flags=flags)
 
 
 def make_views(cfg: I.SceneConfig, model: B.Model, x_gt, device="cuda", ctx=None):
@@ -215,7 +217,8 @@ class BatchRefiner:
         n, V, P = batch.n, model.V, batch.total_pixels
         self.counter = torch.zeros(1, dtype=torch.int32, device=device)
         self.opts = B.render_opts(seed=seed, ka=I.K_AMBIENT, kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR,
-                                  light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX, iter_dev=self.counter)
+                                  light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX, iter_dev=self.counter,
+                                  flags=B.HR_BWD_REUSE_FWD)
         self.params = torch.zeros((n, I.N_PARAMS), device=device)
         self.verts = torch.empty((n, V, 3), device=device)
         self.image = torch.empty((P, 3), device=device)
@@ -282,7 +285,7 @@ class PlainRefiner:
         self.counter = torch.zeros(1, dtype=torch.int32, device=device)
         opts = B.render_opts(seed=seed, instance=instance, spp=cfg.spp, edge_samples=cfg.edge_samples,
                              ka=I.K_AMBIENT, kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR, light_rgb=I.LIGHT_RGB,
-                             edge_eps_px=I.EDGE_EPS_PX, iter_dev=self.counter)
+                             edge_eps_px=I.EDGE_EPS_PX, iter_dev=self.counter, flags=B.HR_BWD_REUSE_FWD)
         self.r = Refiner(model, views, opts, ctx=ctx)
         self.params = torch.zeros(I.N_PARAMS, device=device)
         self.m1 = torch.zeros_like(self.params)

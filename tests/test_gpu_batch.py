@@ -131,13 +131,18 @@ def test_batch_forward_loss_backward(setup):
         A_refs.append(A_ref.astype(np.float32))
     # backward of the oracle's adjoint, every term, per instance
     dv = torch.empty((n, h.V, 3), device="cuda")
-    B.hr_render_bwd_batch(bt, model, verts, cams, bg, go, _t(_cat(A_refs, (3,))), dv)
-    gd = dv.cpu().numpy()
-    for k, i in enumerate(insts):
-        ref, _ = oracle.render_bwd(h, i.verts, i.cams, i.H, i.W, i.bg, i.opts, A_refs[k], normals=i.normals)
-        assert np.abs(ref).max() > 0
-        ok = grad_ok(gd[k], ref)
-        assert ok.all(), (k, np.argwhere(~ok)[:5], gd[k][~ok][:5], ref[~ok][:5])
+    A_all = _t(_cat(A_refs, (3,)))
+    refs = [oracle.render_bwd(h, i.verts, i.cams, i.H, i.W, i.bg, i.opts, A_refs[k], normals=i.normals)[0]
+            for k, i in enumerate(insts)]
+    # a traversal of its own, and the forward's candidate lists (HR_BWD_REUSE_FWD)
+    for flags in (0, B.HR_BWD_REUSE_FWD):
+        B.hr_render_bwd_batch(bt, model, verts, cams, bg, _gopts(B, insts[0].opts, flags), A_all, dv)
+        gd = dv.cpu().numpy()
+        for k, i in enumerate(insts):
+            ref = refs[k]
+            assert np.abs(ref).max() > 0
+            ok = grad_ok(gd[k], ref)
+            assert ok.all(), (flags, k, np.argwhere(~ok)[:5], gd[k][~ok][:5], ref[~ok][:5])
     assert B.hr_get_status(bt) == B.HR_OK
 
 

@@ -166,6 +166,39 @@ def test_render_bwd_terms_match_oracle(B, model, name):
 
 
 @pytest.mark.parametrize("name", SCENES)
+def test_render_bwd_reusing_forward_candidates(B, model, name):
+    """HR_BWD_REUSE_FWD: the backward takes the forward's candidate lists (no second
+    frustum traversal: the work counters show fewer node visits -- only rays of
+    sub-tiles whose lists overflowed the pool traverse) and gives the same total
+    gradient against the oracle; after a rebuild the flag is ignored."""
+    sc = scene(name)
+    h = hand()
+    ctx = _ctx(B, sc)
+    A = _bwd_inputs(sc)
+    o = sc.opts()
+    vt, cams, bg = _t(sc.verts), _t(sc.cams), _t(sc.bg)
+    ref_total, _ = oracle.render_bwd(h, sc.verts, sc.cams, sc.H, sc.W, sc.bg, o, A, normals=sc.normals)
+    img = torch.empty((sc.N, sc.H, sc.W, 3), device="cuda")
+    dv = torch.empty((h.V, 3), device="cuda")
+    B.hr_build_bvh(ctx, model, vt)
+    B.hr_render_fwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o), img)
+    B.hr_get_stats(ctx)
+    B.hr_render_bwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o, B.HR_BWD_REUSE_FWD | B.HR_STATS), _t(A),
+                    dv)
+    nodes_reused = int(B.hr_get_stats(ctx)[1][2])
+    g = dv.cpu().numpy()
+    ok = grad_ok(g, ref_total)
+    assert ok.all(), (np.argwhere(~ok)[:5], g[~ok][:5], ref_total[~ok][:5])
+    # a rebuild invalidates the forward's lists: the flag falls back to a traversal
+    B.hr_build_bvh(ctx, model, vt)
+    B.hr_render_bwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o, B.HR_BWD_REUSE_FWD | B.HR_STATS), _t(A),
+                    dv)
+    assert int(B.hr_get_stats(ctx)[1][2]) > nodes_reused
+    assert grad_ok(dv.cpu().numpy(), ref_total).all()
+    assert B.hr_get_status(ctx) == B.HR_OK
+
+
+@pytest.mark.parametrize("name", SCENES)
 def test_skin_bwd_matches_oracle(B, model, name):
     sc = scene(name)
     h = hand()
