@@ -6,8 +6,9 @@ Workload: the paper-shaped multiview hand capture -- 8 views of 512x384 on a rin
 0.6 m, 16 samples per pixel, 4096 silhouette-edge samples per view, the 778-vertex /
 1538-triangle procedural hand (Section 3.3 times one iteration of this path: ~30 views,
 16 spp forward and backward).  One step = one full iteration of the hot path:
-skinning, BVH rebuild + vertex normals, forward render, masked loss + adjoint, interior
-and edge-sampling backward with the vertex-normal adjoint, skinning adjoint, Adam.
+skinning, BVH (rebuilt every 8th iteration, refitted in between) + vertex normals,
+forward render, masked loss + adjoint, interior and edge-sampling backward with the
+vertex-normal adjoint, skinning adjoint, Adam.
 
 value: estimator samples resolved per second -- forward: every pixel sample of every
 view (N x H x W x spp); backward: every sample of the pixels with a non-zero adjoint;
@@ -202,7 +203,7 @@ def run_handrt(args):
 
     def graph_step():
         B.hr_skin(ctx, model, params, ref.verts)
-        B.hr_build_bvh(ctx, model, ref.verts)
+        B.hr_update_bvh(ctx, model, ref.verts, iter_dev, P.REBUILD_EVERY)
         B.hr_render_fwd(ctx, model, ref.verts, views.cams, H, W, views.background, gopts, ref.image)
         B.hr_loss(ctx, ref.image, views.observed, views.mask, ref.loss, ref.adjoint)
         B.hr_render_bwd(ctx, model, ref.verts, views.cams, H, W, views.background, gopts, ref.adjoint, ref.d_verts)

@@ -173,6 +173,18 @@ int hr_skin_bwd(hr_context* ctx, const hr_model* model, const float* params, con
  * unit vertex normals used for shading.  verts: device float[V][3]. */
 int hr_build_bvh(hr_context* ctx, const hr_model* model, const float* verts, hr_stream stream);
 
+/* Rebuild or refit: with iter_dev (device uint32) and rebuild_every > 1, the tree is
+ * rebuilt when *iter_dev is a multiple of rebuild_every (or when this context has no
+ * tree of the model's faces yet) and otherwise refitted -- the topology and leaf
+ * order of the last build kept, triangle records and boxes recomputed from verts --
+ * the choice taken on the device, so a captured iteration replays it.  Any tree whose
+ * boxes contain their children gives the same hits and candidate sets, so refitting
+ * changes speed only.  iter_dev NULL or rebuild_every = 1: hr_build_bvh.  Works on
+ * single-instance and batch contexts (verts [n][V][3] for a batch); the vertex
+ * normals are recomputed every call. */
+int hr_update_bvh(hr_context* ctx, const hr_model* model, const float* verts, const uint32_t* iter_dev,
+                  int rebuild_every, hr_stream stream);
+
 /* Forward render R (Section 3.1, "Rendering"): every pixel value is the Monte Carlo
  * estimate (1/spp) sum_s f(x_s) of its box-filtered integral, x_s uniform in the
  * pixel, f the radiance of the closest hit of the primary ray through x_s (double-

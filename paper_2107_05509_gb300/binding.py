@@ -41,7 +41,7 @@ EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", 
            "hr_skin_bwd_batch", "hr_build_bvh_batch", "hr_render_fwd_batch", "hr_loss_batch", "hr_render_bwd_batch",
            "hr_gemm_bf16", "hr_net_param_count", "hr_net_create", "hr_net_destroy", "hr_net_set_params",
            "hr_net_get_params", "hr_net_inputs", "hr_net_set_inputs_bf16", "hr_net_forward", "hr_net_backward",
-           "hr_net_adam", "hr_net_status", "hr_vertex_mse", "hr_add_noise", "hr_select_best")
+           "hr_net_adam", "hr_net_status", "hr_vertex_mse", "hr_add_noise", "hr_select_best", "hr_update_bvh")
 
 
 class HandrtError(RuntimeError):
@@ -93,6 +93,7 @@ def lib():
             "hr_skin_bwd": [P, P, P, P, P, P],
             "hr_skin_bwd_noalloc": [P, P, P, P, P],
             "hr_build_bvh": [P, P, P, P],
+            "hr_update_bvh": [P, P, P, P, I, P],
             "hr_render_fwd": [P, P, P, P, I, I, I, P, P, P, P],
             "hr_loss": [P, P, P, P, I, I, I, P, P, P],
             "hr_render_bwd": [P, P, P, P, I, I, I, P, P, P, P, P],
@@ -290,6 +291,15 @@ def hr_skin_bwd_noalloc(model, params, d_verts, d_params, stream=None):
 def hr_build_bvh(ctx, model, verts, stream=None):
     _check("hr_build_bvh", lib().hr_build_bvh(ctx.handle, ctypes.byref(model.struct), _f32(verts),
                                               _stream(stream)))
+
+
+def hr_update_bvh(ctx, model, verts, iter_dev=None, rebuild_every=1, stream=None):
+    """Rebuild when *iter_dev % rebuild_every == 0 (decided on the device), refit
+    otherwise; single-instance or batch context."""
+    assert iter_dev is None or (iter_dev.dtype == torch.int32 and iter_dev.numel() == 1)
+    _check("hr_update_bvh", lib().hr_update_bvh(ctx.handle, ctypes.byref(model.struct), _f32(verts),
+                                                None if iter_dev is None else _ptr(iter_dev), int(rebuild_every),
+                                                _stream(stream)))
 
 
 def hr_render_fwd(ctx, model, verts, cams, H, W, background, opts, image, stream=None):

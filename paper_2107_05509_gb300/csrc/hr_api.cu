@@ -36,7 +36,8 @@ void free_ctx(Context* c) {
   void* ptrs[] = {c->nodes,   c->tris,    c->normals,   c->normal_len, c->partials,      c->dN,
                   c->dm,      c->sil,     c->sil_count, c->loss_partials, c->counters,   c->skin_partials,
                   c->status,  c->stats,   c->pool_bb,   c->pool_z,     c->pool_rec,      c->st_info,
-                  c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it};
+                  c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it,
+                  c->bvh_parent, c->bvh_valid};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete[] c->hvt;
@@ -102,11 +103,13 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
             dev_alloc(&c->pool_bb, c->pool_cap, a) && dev_alloc(&c->pool_z, c->pool_cap, a) &&
             dev_alloc(&c->pool_rec, c->pool_cap, a) && dev_alloc(&c->st_info, subtiles, a) &&
             dev_alloc(&c->items, c->item_cap, a) && dev_alloc(&c->item_part, (size_t)c->item_cap * 32, a) &&
-            dev_alloc(&c->extra, ni * 6 * V, a) && dev_alloc(&c->work_ctr, 2 + 2 * ni, a);
+            dev_alloc(&c->extra, ni * 6 * V, a) && dev_alloc(&c->work_ctr, 2 + 2 * ni, a) &&
+            dev_alloc(&c->bvh_parent, ni * 2 * F, a) && dev_alloc(&c->bvh_valid, ni, a);
   if (ok) ok = cudaMemset(c->counters, 0, ni * 4 * sizeof(unsigned)) == cudaSuccess &&
                cudaMemset(c->status, 0, sizeof(int)) == cudaSuccess &&
                cudaMemset(c->stats, 0, 3 * hr::kStatsPer * sizeof(unsigned long long)) == cudaSuccess &&
-               cudaMemset(c->nodes, 0, ni * F * sizeof(hr::Node)) == cudaSuccess;
+               cudaMemset(c->nodes, 0, ni * F * sizeof(hr::Node)) == cudaSuccess &&
+               cudaMemset(c->bvh_valid, 0, ni * sizeof(int)) == cudaSuccess;
   for (int i = 0; ok && i < 2 * hr::kTimeSlots; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
   // kernel attributes are set here, once, so that the per-iteration calls are only
   // launches and asynchronous memsets
@@ -266,6 +269,13 @@ int hr_build_bvh(hr_context* ctx, const hr_model* model, const float* verts, hr_
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || c->vt || !model_ok(model, c) || !verts) return HR_ERR_ARG;
   return hr::launch_build_bvh(c, model, verts, (cudaStream_t)stream);
+}
+
+int hr_update_bvh(hr_context* ctx, const hr_model* model, const float* verts, const uint32_t* iter_dev,
+                  int rebuild_every, hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !model_ok(model, c) || !verts || rebuild_every < 1) return HR_ERR_ARG;
+  return hr::launch_update_bvh(c, model, verts, iter_dev, rebuild_every, (cudaStream_t)stream);
 }
 
 int hr_render_fwd(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams, int N, int H,

@@ -14,6 +14,13 @@
 // out once at the end, so the refit's dependent loads cost shared-memory latency.
 // Leaf boxes are padded so that the float32 slab test can never reject a ray that
 // the float32 Moller-Trumbore test would accept.
+//
+// Refit (hr_update_bvh): between full rebuilds the tree keeps its topology and leaf
+// order, and only the triangle records and boxes are recomputed bottom-up.  Any tree
+// whose boxes contain their children gives the same hits and the same candidate sets
+// (a leaf reaches a frustum exactly when its own padded box does), so refitting
+// changes speed, not results; the decision (*iter_dev % rebuild_every) is taken on
+// the device, so a captured iteration replays it.
 #include <cstdio>
 
 #include "hr_internal.h"
@@ -80,7 +87,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
                                                              const int* __restrict__ faces, int F, int V, int P,
                                                              int node_stride, bool snodes,
                                                              Node* __restrict__ nodes_all,
-                                                             float4* __restrict__ tris_all, int* status) {
+                                                             float4* __restrict__ tris_all,
+                                                             int* __restrict__ parent_all, int* __restrict__ valid,
+                                                             const uint32_t* iter_dev, int rebuild_every,
+                                                             int* status) {
   extern __shared__ unsigned long long smem_keys[];
   unsigned long long* keys = smem_keys;
   int* parent = reinterpret_cast<int*>(keys + P);
@@ -98,132 +108,153 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
+  int* gparent = parent_all + (size_t)blockIdx.x * 2 * node_stride;
+  // refit when a tree of these faces exists and this is not a rebuild iteration
+  const bool refit = rebuild_every > 1 && iter_dev && valid[blockIdx.x] == 1 && (*iter_dev % rebuild_every) != 0;
+  if (refit) {
+    const int nn = F > 1 ? F - 1 : 1;
+    if (snodes) {
+      const float4* src = reinterpret_cast<const float4*>(gnodes);
+      float4* dst = reinterpret_cast<float4*>(nodes);
+      for (int i = tid; i < 4 * nn; i += blockDim.x) dst[i] = src[i];
+    }
+    for (int i = tid; i < 2 * F; i += blockDim.x) parent[i] = gparent[i];
+    for (int i = tid; i < F; i += blockDim.x) flags[i] = 0;
+    __syncthreads();
+  }
   __shared__ int bad;
   if (tid == 0) bad = 0;
   __syncthreads();
-  // 0. face indices must address [0, V); otherwise record the error and build nothing
-  for (int i = tid; i < 3 * F; i += blockDim.x)
-    if (faces[i] < 0 || faces[i] >= V) bad = 1;
-  __syncthreads();
-  if (bad) {
-    if (tid == 0) {
-      set_status(status, kStatusBadModel);
-      gnodes[0].d = make_int4(~0, ~0, 0, 0);   // a one-leaf tree over a degenerate record
-      gnodes[0].a = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
-      gnodes[0].b = make_float4(-1.0f, -1.0f, 1.0f, 1.0f);
-      gnodes[0].c = make_float4(1.0f, -1.0f, -1.0f, -1.0f);
-      tris[0] = tris[1] = tris[2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    }
-    return;
-  }
-
-  // 1. centroid bounds
-  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int f = tid; f < F; f += blockDim.x) {
-    int3 fc = make_int3(faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]);
-    for (int c = 0; c < 3; ++c) {
-      float x = (verts[3 * fc.x + c] + verts[3 * fc.y + c] + verts[3 * fc.z + c]) * (1.0f / 3.0f);
-      lo[c] = fminf(lo[c], x);
-      hi[c] = fmaxf(hi[c], x);
-    }
-  }
-  for (int c = 0; c < 3; ++c) {
-    float a = warp_min(lo[c]), b = warp_max(hi[c]);
-    if (lane == 0) {
-      red[c][warp] = a;
-      red[3 + c][warp] = b;
-    }
-  }
-  __syncthreads();
-  if (warp == 0) {
-    int nw = blockDim.x >> 5;
-    for (int c = 0; c < 3; ++c) {
-      float a = lane < nw ? red[c][lane] : INFINITY;
-      float b = lane < nw ? red[3 + c][lane] : -INFINITY;
-      a = warp_min(a);
-      b = warp_max(b);
-      if (lane == 0) {
-        bounds[c] = a;
-        bounds[3 + c] = b;
+  if (!refit) {   // block-uniform: phases 0-4 of a full build
+    // 0. face indices must address [0, V); otherwise record the error and build nothing
+    for (int i = tid; i < 3 * F; i += blockDim.x)
+      if (faces[i] < 0 || faces[i] >= V) bad = 1;
+    __syncthreads();
+    if (bad) {
+      if (tid == 0) {
+        set_status(status, kStatusBadModel);
+        gnodes[0].d = make_int4(~0, ~0, 0, 0);   // a one-leaf tree over a degenerate record
+        gnodes[0].a = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
+        gnodes[0].b = make_float4(-1.0f, -1.0f, 1.0f, 1.0f);
+        gnodes[0].c = make_float4(1.0f, -1.0f, -1.0f, -1.0f);
+        tris[0] = tris[1] = tris[2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       }
+      return;
     }
-  }
-  __syncthreads();
 
-  // 2. Morton keys (code << 32 | triangle id), padded to P with all-ones
-  for (int i = tid; i < P; i += blockDim.x) {
-    unsigned long long key = ~0ull;
-    if (i < F) {
-      int3 fc = make_int3(faces[3 * i], faces[3 * i + 1], faces[3 * i + 2]);
-      unsigned q[3];
+    // 1. centroid bounds
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int f = tid; f < F; f += blockDim.x) {
+      int3 fc = make_int3(faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]);
       for (int c = 0; c < 3; ++c) {
         float x = (verts[3 * fc.x + c] + verts[3 * fc.y + c] + verts[3 * fc.z + c]) * (1.0f / 3.0f);
-        float ext = bounds[3 + c] - bounds[c];
-        float n = ext > 0.0f ? (x - bounds[c]) / ext : 0.5f;
-        q[c] = (unsigned)fminf(fmaxf(n * 1024.0f, 0.0f), 1023.0f);
+        lo[c] = fminf(lo[c], x);
+        hi[c] = fmaxf(hi[c], x);
       }
-      unsigned code = (expand_bits10(q[0]) << 2) | (expand_bits10(q[1]) << 1) | expand_bits10(q[2]);
-      key = ((unsigned long long)code << 32) | (unsigned)i;
     }
-    keys[i] = key;
-  }
-  for (int i = tid; i < F; i += blockDim.x) flags[i] = 0;
-  __syncthreads();
-
-  // 3. bitonic sort (ascending)
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < P; i += blockDim.x) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          unsigned long long a = keys[i], b = keys[ixj];
-          bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            keys[i] = b;
-            keys[ixj] = a;
-          }
+    for (int c = 0; c < 3; ++c) {
+      float a = warp_min(lo[c]), b = warp_max(hi[c]);
+      if (lane == 0) {
+        red[c][warp] = a;
+        red[3 + c][warp] = b;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int nw = blockDim.x >> 5;
+      for (int c = 0; c < 3; ++c) {
+        float a = lane < nw ? red[c][lane] : INFINITY;
+        float b = lane < nw ? red[3 + c][lane] : -INFINITY;
+        a = warp_min(a);
+        b = warp_max(b);
+        if (lane == 0) {
+          bounds[c] = a;
+          bounds[3 + c] = b;
         }
       }
-      __syncthreads();
     }
-  }
+    __syncthreads();
 
-  // 4. hierarchy (internal nodes 0..F-2; leaves encoded ~k, k = sorted position)
-  if (F == 1) {
-    if (tid == 0) {
-      nodes[0].d = make_int4(~0, ~0, 0, 0);
-      parent[0] = -1;
-      parent[F + 0] = 0;
+    // 2. Morton keys (code << 32 | triangle id), padded to P with all-ones
+    for (int i = tid; i < P; i += blockDim.x) {
+      unsigned long long key = ~0ull;
+      if (i < F) {
+        int3 fc = make_int3(faces[3 * i], faces[3 * i + 1], faces[3 * i + 2]);
+        unsigned q[3];
+        for (int c = 0; c < 3; ++c) {
+          float x = (verts[3 * fc.x + c] + verts[3 * fc.y + c] + verts[3 * fc.z + c]) * (1.0f / 3.0f);
+          float ext = bounds[3 + c] - bounds[c];
+          float n = ext > 0.0f ? (x - bounds[c]) / ext : 0.5f;
+          q[c] = (unsigned)fminf(fmaxf(n * 1024.0f, 0.0f), 1023.0f);
+        }
+        unsigned code = (expand_bits10(q[0]) << 2) | (expand_bits10(q[1]) << 1) | expand_bits10(q[2]);
+        key = ((unsigned long long)code << 32) | (unsigned)i;
+      }
+      keys[i] = key;
     }
-  }
-  for (int i = tid; i < F - 1; i += blockDim.x) {
-    int d = (delta(keys, F, i, i + 1) - delta(keys, F, i, i - 1)) > 0 ? 1 : -1;
-    int dmin = delta(keys, F, i, i - d);
-    int lmax = 2;
-    while (delta(keys, F, i, i + lmax * d) > dmin) lmax <<= 1;
-    int l = 0;
-    for (int t = lmax >> 1; t >= 1; t >>= 1)
-      if (delta(keys, F, i, i + (l + t) * d) > dmin) l += t;
-    int j = i + l * d;
-    int dnode = delta(keys, F, i, j);
-    int s = 0, t = l;
-    do {
-      t = (t + 1) >> 1;
-      if (delta(keys, F, i, i + (s + t) * d) > dnode) s += t;
-    } while (t > 1);
-    int gamma = i + s * d + min(d, 0);
-    int left = (min(i, j) == gamma) ? ~gamma : gamma;
-    int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
-    nodes[i].d = make_int4(left, right, 0, 0);
-    if (left >= 0) parent[left] = i; else parent[F + ~left] = i;
-    if (right >= 0) parent[right] = i; else parent[F + ~right] = i;
-    if (i == 0) parent[0] = -1;
-  }
-  __syncthreads();
+    for (int i = tid; i < F; i += blockDim.x) flags[i] = 0;
+    __syncthreads();
 
-  // 5. triangle records and leaf boxes, then the bottom-up refit
+    // 3. bitonic sort (ascending)
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < P; i += blockDim.x) {
+          int ixj = i ^ j;
+          if (ixj > i) {
+            unsigned long long a = keys[i], b = keys[ixj];
+            bool up = (i & k) == 0;
+            if ((a > b) == up) {
+              keys[i] = b;
+              keys[ixj] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+
+    // 4. hierarchy (internal nodes 0..F-2; leaves encoded ~k, k = sorted position)
+    if (F == 1) {
+      if (tid == 0) {
+        nodes[0].d = make_int4(~0, ~0, 0, 0);
+        parent[0] = -1;
+        parent[F + 0] = 0;
+      }
+    }
+    for (int i = tid; i < F - 1; i += blockDim.x) {
+      int d = (delta(keys, F, i, i + 1) - delta(keys, F, i, i - 1)) > 0 ? 1 : -1;
+      int dmin = delta(keys, F, i, i - d);
+      int lmax = 2;
+      while (delta(keys, F, i, i + lmax * d) > dmin) lmax <<= 1;
+      int l = 0;
+      for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, F, i, i + (l + t) * d) > dmin) l += t;
+      int j = i + l * d;
+      int dnode = delta(keys, F, i, j);
+      int s = 0, t = l;
+      do {
+        t = (t + 1) >> 1;
+        if (delta(keys, F, i, i + (s + t) * d) > dnode) s += t;
+      } while (t > 1);
+      int gamma = i + s * d + min(d, 0);
+      int left = (min(i, j) == gamma) ? ~gamma : gamma;
+      int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+      nodes[i].d = make_int4(left, right, 0, 0);
+      if (left >= 0) parent[left] = i; else parent[F + ~left] = i;
+      if (right >= 0) parent[right] = i; else parent[F + ~right] = i;
+      if (i == 0) parent[0] = -1;
+    }
+    __syncthreads();
+
+  }
+  // 5. triangle records and leaf boxes, then the bottom-up refit (a refit reads the
+  // leaf order from the previous records)
   for (int k = tid; k < F; k += blockDim.x) {
-    int tri = (int)(keys[k] & 0xffffffffull);
+    int tri = refit ? __float_as_int(tris[3 * k + 2].y) : (int)(keys[k] & 0xffffffffull);
+    if (tri < 0 || tri >= F) {   // a corrupt record: skip it (reported)
+      set_status(status, kStatusIndex);
+      continue;
+    }
     float3 v0 = ld3(verts + 3 * faces[3 * tri]);
     float3 v1 = ld3(verts + 3 * faces[3 * tri + 1]);
     float3 v2 = ld3(verts + 3 * faces[3 * tri + 2]);
@@ -265,12 +296,16 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
       p = gp;
     }
   }
+  __syncthreads();
   if (snodes) {
-    __syncthreads();
     const int nn = F > 1 ? F - 1 : 1;
     const float4* src = reinterpret_cast<const float4*>(nodes);
     float4* dst = reinterpret_cast<float4*>(gnodes);
     for (int i = tid; i < 4 * nn; i += blockDim.x) dst[i] = src[i];
+  }
+  if (!refit) {   // keep the topology for later refits
+    for (int i = tid; i < 2 * F; i += blockDim.x) gparent[i] = parent[i];
+    if (tid == 0) valid[blockIdx.x] = 1;
   }
 }
 
@@ -327,6 +362,11 @@ int configure_bvh_kernels() {
 }
 
 int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaStream_t s) {
+  return launch_update_bvh(ctx, m, verts, nullptr, 1, s);
+}
+
+int launch_update_bvh(Context* ctx, const hr_model* m, const float* verts, const uint32_t* iter_dev,
+                      int rebuild_every, cudaStream_t s) {
   int F = m->F, V = m->V;
   int P = 1;
   while (P < F) P <<= 1;
@@ -335,8 +375,14 @@ int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaSt
   const size_t with_nodes = ((smem + 15) & ~(size_t)15) + (size_t)(F > 1 ? F - 1 : 1) * sizeof(Node);
   const bool snodes = with_nodes <= (size_t)kBuildSmemCap;
   if (snodes) smem = with_nodes;
+  // a refit needs a tree built over these faces by this context
+  if (ctx->bvh_faces != m->faces || ctx->F != F) {
+    if (cudaMemsetAsync(ctx->bvh_valid, 0, sizeof(int) * ctx->n_inst, s) != cudaSuccess) return HR_ERR_CUDA;
+    ctx->bvh_faces = m->faces;
+  }
   k_build_bvh<<<ctx->n_inst, kBuildThreads, smem, s>>>(verts, m->faces, F, V, P, ctx->lim.max_F, snodes,
-                                                       ctx->nodes, ctx->tris, ctx->status);
+                                                       ctx->nodes, ctx->tris, ctx->bvh_parent, ctx->bvh_valid,
+                                                       iter_dev, rebuild_every, ctx->status);
   HR_CHECK_LAUNCH();
   k_vertex_normals<<<dim3((V + 255) / 256, ctx->n_inst), 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces,
                                                                       V, F, ctx->normals, ctx->normal_len,

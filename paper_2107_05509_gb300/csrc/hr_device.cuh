@@ -82,6 +82,9 @@ struct Context {
   // scene, one per instance (per-instance arrays are [n_inst][...], contiguous)
   int V, F;              // sizes of the last hr_build_bvh
   unsigned bvh_gen;      // builds so far
+  int* bvh_parent;       // [n_inst][2 max_F] parents of the internal nodes and leaves
+  int* bvh_valid;        // [n_inst] 1 once a tree of bvh_faces exists (refits need it)
+  const int* bvh_faces;  // the face array of the last build
   // the last forward render (its candidate pool serves a backward with
   // HR_BWD_REUSE_FWD): vertices, cameras, sizes and the build it used
   const void* fwd_verts;

@@ -11,6 +11,8 @@ int launch_skin(Context* ctx, const hr_model* m, const float* params, float* ver
 int launch_skin_bwd(Context* ctx, const hr_model* m, const float* params, const float* d_verts,
                     float* d_params, cudaStream_t s);
 int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaStream_t s);
+int launch_update_bvh(Context* ctx, const hr_model* m, const float* verts, const uint32_t* iter_dev,
+                      int rebuild_every, cudaStream_t s);
 int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,
                       const float* bg, const hr_render_opts* o, float* image, cudaStream_t s);
 int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,

@@ -50,7 +50,7 @@ namespace {
 
 constexpr int kRenderThreads = 128;   // 4 warps per block
 constexpr int kWarps = kRenderThreads / 32;
-constexpr int kBwdMinBlocks = 5;
+constexpr int kBwdMinBlocks = 4;
 constexpr int kBlocksPerSm = 8;       // persistent grid; backward partials are sized for it
 static_assert(kBwdMinBlocks <= kBlocksPerSm, "backward partials are sized for kBlocksPerSm blocks per SM");
 constexpr int kSubW = 8, kSubH = 4;   // sub-tile; lane = pixel
@@ -508,6 +508,59 @@ __device__ __forceinline__ Hit closest_candidate(const RenderArgs& a, int off, i
   return h;
 }
 
+// closest hits of a lane's S rays (same origin) among the K pool candidates at `off`:
+// the candidate's depth, screen box and triangle record are loaded once for all S
+// rays; `live[j]` rays take part, the others only vote.  Each ray gets exactly the hit
+// the one-ray search gives it.
+template <bool STATS, int S>
+__device__ __forceinline__ void closest_candidates(const RenderArgs& a, int off, int K, const bool (&live)[S],
+                                                   const float (&sx)[S], const float (&sy)[S], float3 o,
+                                                   const float3 (&d)[S], Hit (&h)[S], Counts& cnt) {
+#pragma unroll
+  for (int j = 0; j < S; ++j) h[j] = Hit{-1, INFINITY, 0.0f, 0.0f};
+  for (int c = 0; c < K; ++c) {
+    if (!in_range(a.status, off + c, 0, a.wk.pool_cap)) break;
+    const float zm = __ldg(&a.wk.z[off + c]);
+    const float zlim = zm - (1e-4f * fabsf(zm) + 1e-6f);
+    bool want[S];
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      want[j] = live[j] && !(h[j].t < zlim);
+      any = any || want[j];
+    }
+    if (!__any_sync(0xffffffffu, any)) break;
+    if (!any) continue;
+    const float4 bb = __ldg(&a.wk.bb[off + c]);
+    bool inside = false;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (STATS && want[j]) ++cnt.cands;
+      want[j] = want[j] && sx[j] >= bb.x && sx[j] <= bb.z && sy[j] >= bb.y && sy[j] <= bb.w;
+      inside = inside || want[j];
+    }
+    if (!inside) continue;
+    const int k = __ldg(&a.wk.rec[off + c]);
+    if (!in_range(a.status, k, 0, a.max_visits - 1)) continue;
+    const float4 ta = __ldg(&a.tris[3 * k]), tb = __ldg(&a.tris[3 * k + 1]), tc = __ldg(&a.tris[3 * k + 2]);
+    const float3 v0 = make_float3(ta.x, ta.y, ta.z), e1 = make_float3(ta.w, tb.x, tb.y),
+                 e2 = make_float3(tb.z, tb.w, tc.x);
+    const int id = __float_as_int(tc.y);
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (!want[j]) continue;
+      if (STATS) ++cnt.tris;
+      float t, u, v;
+      if (mt_hit(o, d[j], v0, e1, e2, t, u, v) && (t < h[j].t || (t == h[j].t && id < h[j].tri))) {
+        h[j].tri = id;
+        h[j].t = t;
+        h[j].u = u;
+        h[j].v = v;
+      }
+    }
+  }
+}
+
 // closest hit among the pool candidates at `off` for one ray on its own (no warp
 // votes): candidates are sorted by nearest depth, so the first one farther than the
 // hit so far ends the search
@@ -551,40 +604,59 @@ __device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, 
   return ld3(a.bg + 3 * (pix0 + (size_t)by * W + bx));
 }
 
-// Radiance sums of samples [s0, s1) of this lane's pixel (all lanes call it).
+// Radiance sums of samples [s0, s1) of this lane's pixel (all lanes call it), traced
+// kRaysPerLane at a time; the radiance is added in sample order.
+constexpr int kRaysPerLane = 4;
 template <bool STATS>
 __device__ __forceinline__ void shade_samples(const RenderArgs& a, const SubTile& t, const Cam& cam, int off, int K,
                                               int s0, int s1, float3& acc, int& misses, Counts& cnt) {
+  constexpr int S = kRaysPerLane;
   const int lane = threadIdx.x & 31;
   const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
   const bool valid = px < t.W && py < t.H;
   const float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
-  for (int s = s0; s < s1; ++s) {
-    float sx = 0.0f, sy = 0.0f;
-    if (valid) {
-      float u1, u2;
-      jitter(a, t.ctr1, t.W, px, py, s, u1, u2);
-      sx = __fadd_rn((float)px, u1);
-      sy = __fadd_rn((float)py, u2);
-      if (STATS) {
-        ++cnt.samples;
-        ++cnt.rays;
+  for (int sb = s0; sb < s1; sb += S) {
+    bool live[S];
+    float sx[S], sy[S];
+    float3 d[S];
+    Hit h[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      live[j] = valid && sb + j < s1;
+      sx[j] = sy[j] = 0.0f;
+      if (live[j]) {
+        float u1, u2;
+        jitter(a, t.ctr1, t.W, px, py, sb + j, u1, u2);
+        sx[j] = __fadd_rn((float)px, u1);
+        sy[j] = __fadd_rn((float)py, u2);
+        if (STATS) {
+          ++cnt.samples;
+          ++cnt.rays;
+        }
+      }
+      d[j] = primary_dir(cam, sx[j], sy[j]);
+    }
+    if (K > 0) {
+      closest_candidates<STATS, S>(a, off, K, live, sx, sy, o, d, h, cnt);
+    } else {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        h[j] = Hit{-1, INFINITY, 0.0f, 0.0f};
+        if (live[j]) h[j] = trace<STATS>(a.nodes, a.tris, o, d[j], a.status, cnt, a.max_visits);
       }
     }
-    const float3 d = primary_dir(cam, sx, sy);
-    Hit h{-1, INFINITY, 0.0f, 0.0f};
-    if (K > 0)
-      h = closest_candidate<STATS>(a, off, K, valid, sx, sy, o, d, cnt);
-    else if (valid)
-      h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
-    if (h.tri >= 0) {
-      if (STATS) ++cnt.hits;
-      float3 f = shade(a, h);
-      acc.x += f.x;
-      acc.y += f.y;
-      acc.z += f.z;
-    } else {
-      ++misses;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (!(valid && sb + j < s1)) continue;
+      if (h[j].tri >= 0) {
+        if (STATS) ++cnt.hits;
+        float3 f = shade(a, h[j]);
+        acc.x += f.x;
+        acc.y += f.y;
+        acc.z += f.z;
+      } else {
+        ++misses;
+      }
     }
   }
 }
@@ -671,10 +743,12 @@ __device__ __forceinline__ void flush_tri(int3 f, const HitGrad& acc, float* dV,
 }
 
 // Gradient of samples [s0, s1) of this lane's pixel (upstream g, `live` lanes only;
-// all lanes call it), added to dV [V][3] / dN [V][3] per run of hits on one triangle.
+// all lanes call it), traced kRaysPerLane at a time and differentiated in sample
+// order; added to dV [V][3] / dN [V][3] per run of hits on one triangle.
 template <bool STATS>
 __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile& t, const Cam& cam, int off, int K,
                                              int s0, int s1, bool live, float3 g, float* dV, float* dN, Counts& cnt) {
+  constexpr int S = kRaysPerLane;
   const int lane = threadIdx.x & 31;
   const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
   const float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
@@ -683,41 +757,56 @@ __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile&
   HitGrad acc;
 #pragma unroll
   for (int c = 0; c < 9; ++c) acc.dv[c] = acc.dn[c] = 0.0f;
-  for (int s = s0; s < s1; ++s) {
-    float sx = 0.0f, sy = 0.0f;
-    if (live) {
-      float u1, u2;
-      jitter(a, t.ctr1, t.W, px, py, s, u1, u2);
-      sx = __fadd_rn((float)px, u1);
-      sy = __fadd_rn((float)py, u2);
-      if (STATS) {
-        ++cnt.samples;
-        ++cnt.rays;
+  for (int sb = s0; sb < s1; sb += S) {
+    bool lv[S];
+    float sx[S], sy[S];
+    float3 d[S];
+    Hit h[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      lv[j] = live && sb + j < s1;
+      sx[j] = sy[j] = 0.0f;
+      if (lv[j]) {
+        float u1, u2;
+        jitter(a, t.ctr1, t.W, px, py, sb + j, u1, u2);
+        sx[j] = __fadd_rn((float)px, u1);
+        sy[j] = __fadd_rn((float)py, u2);
+        if (STATS) {
+          ++cnt.samples;
+          ++cnt.rays;
+        }
+      }
+      d[j] = primary_dir(cam, sx[j], sy[j]);
+    }
+    if (K > 0) {
+      closest_candidates<STATS, S>(a, off, K, lv, sx, sy, o, d, h, cnt);
+    } else {
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        h[j] = Hit{-1, INFINITY, 0.0f, 0.0f};
+        if (lv[j]) h[j] = trace<STATS>(a.nodes, a.tris, o, d[j], a.status, cnt, a.max_visits);
       }
     }
-    const float3 d = primary_dir(cam, sx, sy);
-    Hit h{-1, INFINITY, 0.0f, 0.0f};
-    if (K > 0)
-      h = closest_candidate<STATS>(a, off, K, live, sx, sy, o, d, cnt);
-    else if (live)
-      h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
-    if (h.tri < 0) continue;
-    if (STATS) ++cnt.hits;
-    if (h.tri != cur) {
-      if (cur >= 0) {
-        flush_tri(cf, acc, dV, dN);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) acc.dv[c] = acc.dn[c] = 0.0f;
+    for (int j = 0; j < S; ++j) {
+      if (!lv[j] || h[j].tri < 0) continue;
+      if (STATS) ++cnt.hits;
+      if (h[j].tri != cur) {
+        if (cur >= 0) {
+          flush_tri(cf, acc, dV, dN);
+#pragma unroll
+          for (int c = 0; c < 9; ++c) acc.dv[c] = acc.dn[c] = 0.0f;
+        }
+        cur = h[j].tri;
+        cf = make_int3(__ldg(&a.faces[3 * cur]), __ldg(&a.faces[3 * cur + 1]), __ldg(&a.faces[3 * cur + 2]));
       }
-      cur = h.tri;
-      cf = make_int3(__ldg(&a.faces[3 * cur]), __ldg(&a.faces[3 * cur + 1]), __ldg(&a.faces[3 * cur + 2]));
-    }
-    HitGrad hg;
-    hit_grad(a, h, cf, o, d, g, hg);
+      HitGrad hg;
+      hit_grad(a, h[j], cf, o, d[j], g, hg);
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      acc.dv[c] += hg.dv[c];
-      acc.dn[c] += hg.dn[c];
+      for (int c = 0; c < 9; ++c) {
+        acc.dv[c] += hg.dv[c];
+        acc.dn[c] += hg.dn[c];
+      }
     }
   }
   if (cur >= 0) flush_tri(cf, acc, dV, dN);

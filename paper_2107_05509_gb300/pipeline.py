@@ -56,11 +56,12 @@ class Refiner:
         self.d_verts = torch.empty((hand.V, 3), device=dev)
         self.d_params = torch.empty(61, device=dev)
 
-    def forward(self, params, stream=None, skin=True):
+    def forward(self, params, stream=None, skin=True, build=True):
         ctx, m, v = self.ctx, self.model, self.views
         if skin:
             B.hr_skin(ctx, m, params, self.verts, stream)
-        B.hr_build_bvh(ctx, m, self.verts, stream)
+        if build:
+            B.hr_build_bvh(ctx, m, self.verts, stream)
         B.hr_render_fwd(ctx, m, self.verts, v.cams, v.H, v.W, v.background, self.opts, self.image, stream)
         B.hr_loss(ctx, self.image, v.observed, v.mask, self.loss, self.adjoint, stream)
         return self.loss
@@ -150,6 +151,9 @@ def make_views(cfg: I.SceneConfig, model: B.Model, x_gt, device="cuda", ctx=None
 # Batches: many instances refined together, one launch per kernel per iteration
 # --------------------------------------------------------------------------------------
 
+# iterations per full BVH rebuild in the captured refinement loops (refits between)
+REBUILD_EVERY = 8
+
 # Adam step sizes per parameter group [beta(10), theta(45), phi(3), tau(3)]: shape
 # coefficients, radians, radians, metres (Adam's step is about lr whatever the
 # gradient's scale, so each group gets a step in its own unit)
@@ -206,7 +210,7 @@ def make_batch_views(cfgs, model: B.Model, x_gts, device="cuda"):
 
 class BatchRefiner:
     """Plain refinement of every instance of a batch at once.  One iteration is
-    hr_skin_batch -> hr_build_bvh_batch -> hr_render_fwd_batch -> hr_loss_batch ->
+    hr_skin_batch -> hr_update_bvh -> hr_render_fwd_batch -> hr_loss_batch ->
     hr_render_bwd_batch -> hr_skin_bwd_batch -> hr_adam_step_dev, plus (with ground
     truth vertices) hr_vertex_error into the error table: a fixed sequence of launches
     over all instances that capture() records once as a CUDA graph."""
@@ -246,7 +250,7 @@ class BatchRefiner:
         B.hr_skin_batch(bt, m, self.params, self.verts, stream)
         if self.ref_verts is not None:
             B.hr_vertex_error(self.verts, self.ref_verts, self.err, self.counter, stream)
-        B.hr_build_bvh_batch(bt, m, self.verts, stream)
+        B.hr_update_bvh(bt, m, self.verts, self.counter, REBUILD_EVERY, stream)
         B.hr_render_fwd_batch(bt, m, self.verts, v.cams, v.background, self.opts, self.image, stream)
         B.hr_loss_batch(bt, self.image, v.observed, v.mask, self.loss, self.adjoint, stream)
         B.hr_render_bwd_batch(bt, m, self.verts, v.cams, v.background, self.opts, self.adjoint, self.d_verts, stream)
@@ -276,7 +280,7 @@ class BatchRefiner:
 
 class PlainRefiner:
     """Plain per-instance refinement through the single-instance calls, one
-    iteration captured as a CUDA graph: hr_skin -> (hr_vertex_error) -> hr_build_bvh
+    iteration captured as a CUDA graph: hr_skin -> (hr_vertex_error) -> hr_update_bvh
     -> hr_render_fwd -> hr_loss -> hr_render_bwd -> hr_skin_bwd -> hr_adam_step_dev
     with per-group step sizes; the device counter advances the sample streams."""
 
@@ -308,7 +312,8 @@ class PlainRefiner:
         B.hr_skin(r.ctx, r.model, self.params, r.verts, stream)
         if self.ref_verts is not None:
             B.hr_vertex_error(r.verts, self.ref_verts, self.err, self.counter, stream)
-        r.forward(self.params, stream, skin=False)
+        B.hr_update_bvh(r.ctx, r.model, r.verts, self.counter, REBUILD_EVERY, stream)
+        r.forward(self.params, stream, skin=False, build=False)
         r.backward(self.params, stream)
         B.hr_adam_step_dev(self.params, r.d_params, self.m1, self.m2, self.lr, 0.9, 0.999, 1e-8, self.counter,
                            lr_scale=self.lr_scale, stream=stream)

@@ -136,3 +136,46 @@ def test_host_argument_errors(B):
     lim = B.hr_limits(100000, 10, 10, 1, 8, 8)
     hnd = ctypes.c_void_p()
     assert B.lib().hr_context_create(ctypes.byref(lim), ctypes.byref(hnd)) == B.HR_ERR_UNSUPPORTED
+
+
+def test_refit_gives_the_rebuilt_tree_results(B):
+    """hr_update_bvh refits the previous tree (topology of another pose) on device
+    iterations that are not multiples of rebuild_every: the render and the closest
+    hits equal those of a full rebuild over the same vertices, bit for bit, and the
+    render matches the oracle."""
+    import oracle
+    from tests.gpu_common import pixel_ok
+    sc = scene("tiny")
+    h = hand()
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, sc.N, sc.W, sc.H)
+    v_a = _t(sc.verts)
+    vb_np = oracle.skin(h, sc.x_gt).astype(np.float32)     # another pose, same faces
+    v_b = _t(vb_np)
+    cams, bg = _t(sc.cams), _t(sc.bg)
+    o = sc.gpu_opts(sc.opts())
+    img_refit = torch.empty((sc.N, sc.H, sc.W, 3), device="cuda")
+    img_full = torch.empty_like(img_refit)
+    rng = np.random.default_rng(2)
+    nray = 4096
+    cam = sc.cams[rng.integers(0, sc.N, nray)]
+    orig = _t(cam[:, 16:19].copy())
+    dirs = _t((vb_np[rng.integers(0, h.V, nray)] - cam[:, 16:19]).astype(np.float32))
+    tri_r = torch.empty(nray, dtype=torch.int32, device="cuda")
+    tri_f = torch.empty_like(tri_r)
+    tuv_r = torch.empty((nray, 3), device="cuda")
+    tuv_f = torch.empty_like(tuv_r)
+    B.hr_build_bvh(ctx, model, v_a)
+    counter = torch.full((1,), 3, dtype=torch.int32, device="cuda")
+    B.hr_update_bvh(ctx, model, v_b, counter, 8)            # 3 % 8 != 0: refit
+    B.hr_render_fwd(ctx, model, v_b, cams, sc.H, sc.W, bg, o, img_refit)
+    B.hr_trace(ctx, orig, dirs, tri_r, tuv_r)
+    B.hr_build_bvh(ctx, model, v_b)
+    B.hr_render_fwd(ctx, model, v_b, cams, sc.H, sc.W, bg, o, img_full)
+    B.hr_trace(ctx, orig, dirs, tri_f, tuv_f)
+    assert torch.equal(img_refit, img_full)
+    assert torch.equal(tri_r, tri_f) and torch.equal(tuv_r, tuv_f)
+    n_b = oracle.vertex_normals(vb_np, h.faces, h.vf_offsets, h.vf_faces)
+    ref = oracle.render_fwd(vb_np, h.faces, n_b, h.albedo, sc.cams, sc.H, sc.W, sc.bg, sc.opts())
+    assert pixel_ok(img_refit.cpu().numpy(), ref).all()
+    assert B.hr_get_status(ctx) == B.HR_OK
