@@ -51,12 +51,12 @@ N_SM, LANES = 152, 128
 FLOP_RAY, FLOP_NODE, FLOP_CAND, FLOP_TRI, FLOP_HIT, FLOP_HIT_GRAD = 40, 60, 4, 50, 60, 250
 S_SAMPLES, S_RAYS, S_NODES, S_TRIS, S_HITS, S_CANDS = range(6)
 FLOP_TRACE_NODE, FLOP_EDGE = 40, 120   # per-ray traversal node (two slab tests); edge-sample set-up
-KERNEL_NAMES = {"fwd_gather": "k_gather<fwd>", "fwd_shade": "k_shade_fwd", "bwd_gather": "k_gather<bwd>",
+KERNEL_NAMES = {"fwd_gather": "k_gather<fwd>", "fwd_shade": "k_shade_fwd", "bwd_gather": "k_items_bwd",
                 "bwd_shade": "k_shade_bwd", "edge_samples": "k_edge_samples"}
 # DRAM bytes (read + write) per launch from the ncu capture summarised under profiles/
 # (None once the kernel has changed since that capture)
-NCU_TRAFFIC = {"k_shade_bwd": 3658240, "k_shade_fwd": 2395904, "k_gather<fwd>": 17733376,
-               "k_gather<bwd>": 19088128}
+NCU_TRAFFIC = {"k_shade_bwd": 3755264, "k_shade_fwd": 2433536, "k_gather<fwd>": 17760512,
+               "k_items_bwd": 19331584, "k_edge_samples": 2976512}
 # kernels of one step: skin 1, BVH + normals 2, forward 3, loss 2, backward 7, skin adjoint 1, Adam 1
 LAUNCHES_PER_STEP = 17
 # a batched iteration: the same kernels (one launch each over all instances) plus the
