@@ -194,6 +194,13 @@ def run_handrt(args):
         one_step(w)
     torch.cuda.synchronize()
 
+    # launch shapes of the render kernels for this workload (the project's autotuner;
+    # untimed, before the graph is captured)
+    tune_params = params.clone()
+    tuning, tune_start_ms, tune_best_ms = P.autotune(
+        ctx, lambda: ref.step(tune_params), P.workload_key(model, [(N, W, H, cfg.spp, cfg.edge_samples)]),
+        cache=False)
+
     # the timed step: one whole iteration captured as a CUDA graph and replayed; the
     # sample streams and Adam's step number come from a device counter that the
     # Adam kernel advances, so every replay is a fresh iteration
@@ -359,6 +366,8 @@ def run_handrt(args):
                        for i, k in enumerate(["fwd", "bwd", "edge"])},
                    "stage_ms_eager": stage_ms, "step_ms_eager": round(float(st.sum(1).mean()), 4),
                    "timing": "CUDA graph of one whole iteration, replayed; events around each replay",
+                   "tuning": tuning, "tuning_fwd_bwd_ms": {"default": round(tune_start_ms, 4),
+                                                            "tuned": round(tune_best_ms, 4)},
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"{world} independent instance(s), one per GPU"},
         "e2e": {"value": round(rays_step * world / (e2e_ms * 1e-3) / 1e6, 3), "unit": UNIT,
@@ -415,6 +424,19 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
     R.opts.flags = B.HR_BWD_REUSE_FWD
     rays = float(stats[:, S_SAMPLES].sum())
 
+    # launch shapes: the batch context and every plain context tuned by the same
+    # autotuner (instances of one layout share the result)
+    memo = {}
+
+    def tune(ctx, run, layout):
+        key = P.workload_key(model, layout)
+        if key in memo:
+            ctx.set_tuning(**memo[key])
+        else:
+            memo[key] = P.autotune(ctx, run, key, cache=False)[0]
+
+    R.reset(x0)
+    tune(bt, R.render_pass, [(c.views, c.width, c.height, c.spp, c.edge_samples) for c in cfgs])
     R.reset(x0)
     g = R.capture()
     for _ in range(3):
@@ -467,6 +489,8 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
                      mask=views.mask[po[i]:po[i + 1]].reshape(c.views, c.height, c.width), H=c.height, W=c.width)
         pr = P.PlainRefiner(model, v1, c, instance=i, ref_verts=ref[i], max_iters=iters + 8, device=dev)
         pr.reset(x0[i])
+        tune(pr.r.ctx, pr.render_pass, [(c.views, c.width, c.height, c.spp, c.edge_samples)])
+        pr.reset(x0[i])
         gi = pr.capture()
         pr.reset(x0[i])
         evi = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 1)]
@@ -506,6 +530,7 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
     sb["rays_per_iter"] = int(rays)
     sb["launches_per_iter"] = LAUNCHES_BATCH_ITER
     sp["ms_per_iter_sum_over_instances"] = round(float(np.median(dt_p.sum(1))), 3)
+    sb["tuning"] = bt.get_tuning()
     res = {"instances": n, "views": int(bt.total_views), "pixels": int(bt.total_pixels), "iterations": iters,
            "plain_sequential": sp, "batched": sb}
     if res_learned is not None:

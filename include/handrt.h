@@ -145,6 +145,23 @@ typedef struct hr_limits {
 
 typedef struct hr_context hr_context;
 
+/* Launch shapes of the render kernels (hr_set_tuning; see pipeline.autotune for the
+ * project's autotuner, which times candidates on a workload and caches the best):
+ *   rays_per_lane      samples each lane traces together against a candidate (1, 2, 4)
+ *   cand_per_chunk     candidates per work item when splitting a sub-tile (>= 1)
+ *   max_chunks         work items per sub-tile at most (1 .. 16)
+ *   blocks_per_sm      persistent blocks per SM of the gather / forward kernels (1 .. 8)
+ *   bwd_blocks_per_sm  persistent blocks per SM of the backward shader (1 .. 8)
+ * Every setting gives the same results (the backward up to float32 summation order);
+ * only the speed changes.  Defaults: 4, 16, 16, 8, 4. */
+typedef struct hr_tuning {
+    int32_t rays_per_lane;
+    int32_t cand_per_chunk;
+    int32_t max_chunks;
+    int32_t blocks_per_sm;
+    int32_t bwd_blocks_per_sm;
+} hr_tuning;
+
 /* Create a context on the current CUDA device: device scratch for the given
  * limits (the BVH, vertex normals, the render kernels' per-sub-tile candidate pool
  * and work items, reduction partials) and the device status word.
@@ -154,6 +171,10 @@ int hr_context_create(const hr_limits* limits, hr_context** out);
 
 /* Free a context and all its device memory (synchronises the device first). */
 int hr_context_destroy(hr_context* ctx);
+
+/* Set / read the context's launch shapes (HR_ERR_ARG for values out of range). */
+int hr_set_tuning(hr_context* ctx, const hr_tuning* tuning);
+int hr_get_tuning(hr_context* ctx, hr_tuning* tuning);
 
 /* Skinning G_v (Section 3.1, "Geometry": x in R^61 decoded into 3-D vertices).
  *   v = sum_j w_vj (A_j [v_template + S beta; 1]) + tau,  A_j = G_j [I | -J_j],

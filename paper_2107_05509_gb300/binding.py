@@ -41,7 +41,8 @@ EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", 
            "hr_skin_bwd_batch", "hr_build_bvh_batch", "hr_render_fwd_batch", "hr_loss_batch", "hr_render_bwd_batch",
            "hr_gemm_bf16", "hr_net_param_count", "hr_net_create", "hr_net_destroy", "hr_net_set_params",
            "hr_net_get_params", "hr_net_inputs", "hr_net_set_inputs_bf16", "hr_net_forward", "hr_net_backward",
-           "hr_net_adam", "hr_net_status", "hr_vertex_mse", "hr_add_noise", "hr_select_best", "hr_update_bvh")
+           "hr_net_adam", "hr_net_status", "hr_vertex_mse", "hr_add_noise", "hr_select_best", "hr_update_bvh",
+           "hr_set_tuning", "hr_get_tuning")
 
 
 class HandrtError(RuntimeError):
@@ -69,6 +70,11 @@ class hr_instance_desc(ctypes.Structure):
                 ("spp", ctypes.c_int32), ("edge_samples", ctypes.c_int32), ("instance", ctypes.c_uint32)]
 
 
+class hr_tuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("rays_per_lane", "cand_per_chunk", "max_chunks", "blocks_per_sm",
+                                              "bwd_blocks_per_sm")]
+
+
 class hr_limits(ctypes.Structure):
     _fields_ = [("max_V", ctypes.c_int32), ("max_F", ctypes.c_int32), ("max_E", ctypes.c_int32),
                 ("max_views", ctypes.c_int32), ("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32)]
@@ -94,6 +100,8 @@ def lib():
             "hr_skin_bwd_noalloc": [P, P, P, P, P],
             "hr_build_bvh": [P, P, P, P],
             "hr_update_bvh": [P, P, P, P, I, P],
+            "hr_set_tuning": [P, P],
+            "hr_get_tuning": [P, P],
             "hr_render_fwd": [P, P, P, P, I, I, I, P, P, P, P],
             "hr_loss": [P, P, P, P, I, I, I, P, P, P],
             "hr_render_bwd": [P, P, P, P, I, I, I, P, P, P, P, P],
@@ -185,6 +193,19 @@ class Context:
         if self.handle:
             lib().hr_context_destroy(self.handle)
             self.handle = None
+
+    def set_tuning(self, **kw):
+        """Set launch shapes (hr_tuning fields); unspecified fields keep their value."""
+        t = hr_tuning()
+        _check("hr_get_tuning", lib().hr_get_tuning(self.handle, ctypes.byref(t)))
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check("hr_set_tuning", lib().hr_set_tuning(self.handle, ctypes.byref(t)))
+
+    def get_tuning(self):
+        t = hr_tuning()
+        _check("hr_get_tuning", lib().hr_get_tuning(self.handle, ctypes.byref(t)))
+        return {n: int(getattr(t, n)) for n, _ in hr_tuning._fields_}
 
     def __del__(self):
         try:

@@ -77,8 +77,9 @@ struct Context {
   InstRec* hit;
   int device;
   int num_sms;
-  int render_blocks;     // persistent grid of the render kernels
+  int render_blocks;     // largest persistent grid of the render kernels
   int render_threads;
+  hr_tuning tune;        // launch shapes (hr_set_tuning)
   // scene, one per instance (per-instance arrays are [n_inst][...], contiguous)
   int V, F;              // sizes of the last hr_build_bvh
   unsigned bvh_gen;      // builds so far

@@ -50,13 +50,12 @@ namespace {
 
 constexpr int kRenderThreads = 128;   // 4 warps per block
 constexpr int kWarps = kRenderThreads / 32;
-constexpr int kBwdMinBlocks = 4;
-constexpr int kBlocksPerSm = 8;       // persistent grid; backward partials are sized for it
-static_assert(kBwdMinBlocks <= kBlocksPerSm, "backward partials are sized for kBlocksPerSm blocks per SM");
+constexpr int kBwdMinBlocks = 4;      // launch bound of the backward shader (128 registers)
+constexpr int kBlocksPerSm = 8;       // largest persistent grid; backward partials are sized for it
 constexpr int kSubW = 8, kSubH = 4;   // sub-tile; lane = pixel
 constexpr int kLeafCap = 512;         // candidates per sub-tile
 constexpr int kFrontCap = 64;         // breadth-first frontier per level
-constexpr int kMaxChunks = 16;        // work items per sub-tile
+constexpr int kMaxChunks = 16;        // work items per sub-tile (largest setting)
 
 // Self-check of an index read from device memory (BVH children, candidate records,
 // pool offsets, work items): out of range sets a status bit and the caller skips
@@ -215,6 +214,7 @@ struct RenderArgs {
   const InstRec* it;       // batch instance table
   int n_inst, nviews, total_st;
   int node_stride;
+  int cand_per_chunk, max_chunks;   // work-item split (tuning)
   uint2 key;
   uint32_t ctr1_hi;  // instance << 16
   uint32_t iter4;    // iter << 4 (kernels refresh it from iter_dev when given)
@@ -480,9 +480,11 @@ __device__ int frustum_leaves(const RenderArgs& a, const Cam& cam, int x0, int y
   return ovf ? -1 : K;
 }
 
-__device__ __forceinline__ int chunks_for(int K, int spp) {
-  int c = K < 0 ? kMaxChunks : K / 16;
-  return max(1, min(min(c, kMaxChunks), spp));
+// work items of a sub-tile with K candidates (K < 0: per-ray traversal): one per
+// `cand_per_chunk` candidates, at most max_chunks and spp
+__device__ __forceinline__ int chunks_for(const RenderArgs& a, int K, int spp) {
+  int c = K < 0 ? a.max_chunks : K / a.cand_per_chunk;
+  return max(1, min(min(c, a.max_chunks), spp));
 }
 
 // closest hit of the primary ray through (sx, sy) among the K pool candidates at
@@ -605,12 +607,11 @@ __device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, 
 }
 
 // Radiance sums of samples [s0, s1) of this lane's pixel (all lanes call it), traced
-// kRaysPerLane at a time; the radiance is added in sample order.
-constexpr int kRaysPerLane = 4;
-template <bool STATS>
+// S at a time (the tuning's rays per lane); the radiance is added in sample order.
+constexpr int kRaysPerLane = 4;   // for the gather kernels' fall-back paths
+template <bool STATS, int S>
 __device__ __forceinline__ void shade_samples(const RenderArgs& a, const SubTile& t, const Cam& cam, int off, int K,
                                               int s0, int s1, float3& acc, int& misses, Counts& cnt) {
-  constexpr int S = kRaysPerLane;
   const int lane = threadIdx.x & 31;
   const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
   const bool valid = px < t.W && py < t.H;
@@ -743,12 +744,11 @@ __device__ __forceinline__ void flush_tri(int3 f, const HitGrad& acc, float* dV,
 }
 
 // Gradient of samples [s0, s1) of this lane's pixel (upstream g, `live` lanes only;
-// all lanes call it), traced kRaysPerLane at a time and differentiated in sample
-// order; added to dV [V][3] / dN [V][3] per run of hits on one triangle.
-template <bool STATS>
+// all lanes call it), traced S at a time and differentiated in sample order; added to
+// dV [V][3] / dN [V][3] per run of hits on one triangle.
+template <bool STATS, int S>
 __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile& t, const Cam& cam, int off, int K,
                                              int s0, int s1, bool live, float3 g, float* dV, float* dN, Counts& cnt) {
-  constexpr int S = kRaysPerLane;
   const int lane = threadIdx.x & 31;
   const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
   const float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
         K = -1;   // pool full: per-ray traversal for this sub-tile
       }
     }
-    const int C = chunks_for(K, t.spp);
+    const int C = chunks_for(a, K, t.spp);
     const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
     int first = 0;
     if (lane == 0) first = (int)atomicAdd(&a.wk.ctr[2 + 2 * t.inst], (unsigned)C);
@@ -939,11 +939,11 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
       __threadfence_block();
       if (BWD) {
         float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
-        grad_samples<STATS>(a, t, cam, off, K, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
+        grad_samples<STATS, kRaysPerLane>(a, t, cam, off, K, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
       } else {
         float3 acc = make_float3(0.0f, 0.0f, 0.0f);
         int misses = 0;
-        shade_samples<STATS>(a, t, cam, off, K, 0, t.spp, acc, misses, cnt);
+        shade_samples<STATS, kRaysPerLane>(a, t, cam, off, K, 0, t.spp, acc, misses, cnt);
         write_pixel(a, t, acc, misses, image);
       }
     }
@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, c
       continue;
     }
     if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
-    const int C = chunks_for(pk.y, t.spp);
+    const int C = chunks_for(a, pk.y, t.spp);
     const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
     int first = 0;
     if (lane == 0) first = (int)atomicAdd(&a.wk.ctr[2 + 2 * t.inst], (unsigned)C);
@@ -989,7 +989,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, c
       __threadfence_block();
       const Cam cam = load_cam(a.cams, t.view);
       float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
-      grad_samples<STATS>(a, t, cam, pk.x, pk.y, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
+      grad_samples<STATS, kRaysPerLane>(a, t, cam, pk.x, pk.y, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
     }
     __syncwarp();
   }
@@ -1028,8 +1028,8 @@ __device__ __forceinline__ bool load_item(const RenderArgs& a, int gi, int4& ite
   return true;
 }
 
-// warps take work items, instance after instance
-template <bool STATS>
+// warps take work items, instance after instance; S samples per lane at a time
+template <bool STATS, int S>
 __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in, unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
   const int lane = threadIdx.x & 31;
@@ -1049,7 +1049,7 @@ __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in
       item_samples(item.y, item.z, t.spp, s0, s1);
       float3 acc = make_float3(0.0f, 0.0f, 0.0f);
       int misses = 0;
-      shade_samples<STATS>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
+      shade_samples<STATS, S>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
       a.wk.part[(size_t)(ibase + it) * 32 + lane] = make_float4(acc.x, acc.y, acc.z, (float)misses);
     }
   }
@@ -1087,7 +1087,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, fl
 // block, summed in block order by k_reduce_partials.  Batch: the block works through
 // the instances in order and, when every warp is done with one, adds its non-zero
 // sums into that instance's extra [6V] (global atomics) and clears them.
-template <bool STATS, bool BATCH>
+template <bool STATS, bool BATCH, int S>
 __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(RenderArgs a_in,
                                                                              const float* __restrict__ adjoint,
                                                                              float* __restrict__ partials,
@@ -1115,7 +1115,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
       const Cam cam = load_cam(a.cams, t.view);
       int s0, s1;
       item_samples(item.y, item.z, t.spp, s0, s1);
-      grad_samples<STATS>(a, t, cam, pk.x, pk.y, s0, s1, live, g, sdV, sdN, cnt);
+      grad_samples<STATS, S>(a, t, cam, pk.x, pk.y, s0, s1, live, g, sdV, sdN, cnt);
       did = 1;
     }
     if (BATCH) {
@@ -1497,6 +1497,8 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.wk.extra = ctx->extra;
   a.wk.ctr = ctx->work_ctr;
   a.node_stride = ctx->lim.max_F;
+  a.cand_per_chunk = ctx->tune.cand_per_chunk;
+  a.max_chunks = ctx->tune.max_chunks;
   if (ctx->vt) {
     a.vt = ctx->vt;
     a.it = ctx->it;
@@ -1526,19 +1528,25 @@ int render_grid(int device, int* blocks, int* threads, int* num_sms) {
 
 size_t render_bwd_smem(int V) { return (size_t)6 * V * sizeof(float); }
 
+template <bool STATS, bool BATCH, int S>
+bool set_bwd_smem(int smem) {
+  return cudaFuncSetAttribute(k_shade_bwd<STATS, BATCH, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+         cudaSuccess;
+}
+
+template <bool STATS, bool BATCH>
+bool set_bwd_smem_all(int smem) {
+  return set_bwd_smem<STATS, BATCH, 1>(smem) && set_bwd_smem<STATS, BATCH, 2>(smem) &&
+         set_bwd_smem<STATS, BATCH, 4>(smem);
+}
+
 int configure_render_kernels(int max_V) {
   // the largest any context may use (max_V <= 8192), so that creating a smaller
   // context never lowers the opt-in of a larger one
   (void)max_V;
   const int smem = (int)render_bwd_smem(8192);
-  if (cudaFuncSetAttribute(k_shade_bwd<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_shade_bwd<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_shade_bwd<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k_shade_bwd<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-          cudaSuccess) {
+  if (!set_bwd_smem_all<true, false>(smem) || !set_bwd_smem_all<false, false>(smem) ||
+      !set_bwd_smem_all<true, true>(smem) || !set_bwd_smem_all<false, true>(smem)) {
     cudaGetLastError();
     return HR_ERR_CUDA;
   }
@@ -1555,7 +1563,7 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   Timer tm{ctx, s, (o->flags & HR_TIMING) != 0};
   if (cudaMemsetAsync(ctx->work_ctr, 0, (2 + 2 * a.n_inst) * sizeof(unsigned), s) != cudaSuccess)
     return HR_ERR_CUDA;
-  const int blocks = ctx->render_blocks;
+  const int blocks = ctx->num_sms * ctx->tune.blocks_per_sm;
   tm.begin(kTimeFwdGather);
   if (st)
     k_gather<false, true><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, ctx->stats);
@@ -1564,10 +1572,12 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   HR_CHECK_LAUNCH();
   tm.end(kTimeFwdGather);
   tm.begin(kTimeFwdShade);
-  if (st)
-    k_shade_fwd<true><<<blocks, kRenderThreads, 0, s>>>(a, ctx->stats);
-  else
-    k_shade_fwd<false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr);
+  {
+    const int S = ctx->tune.rays_per_lane;
+    auto kern = st ? (S == 1 ? k_shade_fwd<true, 1> : (S == 2 ? k_shade_fwd<true, 2> : k_shade_fwd<true, 4>))
+                   : (S == 1 ? k_shade_fwd<false, 1> : (S == 2 ? k_shade_fwd<false, 2> : k_shade_fwd<false, 4>));
+    kern<<<blocks, kRenderThreads, 0, s>>>(a, st ? ctx->stats : nullptr);
+  }
   HR_CHECK_LAUNCH();
   tm.end(kTimeFwdShade);
   tm.begin(kTimeFwdCombine);
@@ -1620,23 +1630,28 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     tm.begin(kTimeBwdGather);
     if (reuse) {
       if (st)
-        k_items_bwd<true><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, ctx->stats + kStatsPer);
+        k_items_bwd<true><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, ctx->stats + kStatsPer);
       else
-        k_items_bwd<false><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr);
+        k_items_bwd<false><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, nullptr);
     } else if (st) {
-      k_gather<true, true><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr,
+      k_gather<true, true><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, nullptr,
                                                                           ctx->stats + kStatsPer);
     } else {
-      k_gather<true, false><<<ctx->render_blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
+      k_gather<true, false><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
     }
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdGather);
   }
   if (interior) {
     const size_t smem = render_bwd_smem(V);   // within the opt-in of configure_render_kernels
-    auto kern = batch ? (st ? k_shade_bwd<true, true> : k_shade_bwd<false, true>)
-                      : (st ? k_shade_bwd<true, false> : k_shade_bwd<false, false>);
-    const int blocks = ctx->num_sms * kBwdMinBlocks;
+    const int S = ctx->tune.rays_per_lane;
+#define HR_BWD_KERNEL(B_) \
+  (st ? (S == 1 ? k_shade_bwd<true, B_, 1> : (S == 2 ? k_shade_bwd<true, B_, 2> : k_shade_bwd<true, B_, 4>)) \
+      : (S == 1 ? k_shade_bwd<false, B_, 1> : (S == 2 ? k_shade_bwd<false, B_, 2> : k_shade_bwd<false, B_, 4>)))
+    auto kern = batch ? HR_BWD_KERNEL(true) : HR_BWD_KERNEL(false);
+#undef HR_BWD_KERNEL
+    // the block partials are sized for kBlocksPerSm blocks per SM
+    const int blocks = ctx->num_sms * ctx->tune.bwd_blocks_per_sm;
     tm.begin(kTimeBwdShade);
     kern<<<blocks, kRenderThreads, smem, s>>>(a, adjoint, ctx->partials, st ? ctx->stats + kStatsPer : nullptr);
     HR_CHECK_LAUNCH();

@@ -15,6 +15,8 @@ forward renders and keeps the adjoint image, the backward re-traces the samples
 from __future__ import annotations
 
 import dataclasses
+import json
+import os
 
 import numpy as np
 import torch
@@ -258,6 +260,16 @@ class BatchRefiner:
         B.hr_adam_step_dev(self.params, self.d_params, self.m1, self.m2, self.lr, 0.9, 0.999, 1e-8, self.counter,
                            lr_scale=self.lr_scale, stream=stream)
 
+    def render_pass(self, stream=None):
+        """Forward and backward of the current parameters without an update (what the
+        autotuner times)."""
+        bt, m, v = self.batch, self.model, self.views
+        B.hr_skin_batch(bt, m, self.params, self.verts, stream)
+        B.hr_build_bvh_batch(bt, m, self.verts, stream)
+        B.hr_render_fwd_batch(bt, m, self.verts, v.cams, v.background, self.opts, self.image, stream)
+        B.hr_loss_batch(bt, self.image, v.observed, v.mask, self.loss, self.adjoint, stream)
+        B.hr_render_bwd_batch(bt, m, self.verts, v.cams, v.background, self.opts, self.adjoint, self.d_verts, stream)
+
     def capture(self):
         """Record one iteration as a CUDA graph (warm up first: the first launches of
         a process load the kernels)."""
@@ -318,4 +330,91 @@ class PlainRefiner:
         B.hr_adam_step_dev(self.params, r.d_params, self.m1, self.m2, self.lr, 0.9, 0.999, 1e-8, self.counter,
                            lr_scale=self.lr_scale, stream=stream)
 
+    def render_pass(self, stream=None):
+        self.r.step(self.params, stream)
+
     capture = BatchRefiner.capture
+
+
+# --------------------------------------------------------------------------------------
+# Autotuner of the render kernels' launch shapes
+# --------------------------------------------------------------------------------------
+
+TUNING_SPACE = {
+    "rays_per_lane": (1, 2, 4),
+    "cand_per_chunk": (8, 16, 32),
+    "max_chunks": (8, 16),
+    "blocks_per_sm": (4, 6, 8),
+    "bwd_blocks_per_sm": (2, 3, 4, 6),
+}
+
+
+def tuning_cache_path():
+    return os.environ.get("HANDRT_TUNING_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "handrt",
+                                                              "tuning.json"))
+
+
+def workload_key(model: B.Model, layout) -> str:
+    """Cache key: device, mesh size and the view layout ((views, W, H, spp, edge
+    samples) per instance)."""
+    name = torch.cuda.get_device_name().replace(" ", "_")
+    return f"{name}|V{model.V}|F{model.struct.F}|" + ";".join("x".join(str(int(x)) for x in d) for d in layout)
+
+
+def _time_ms(run, reps):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    run()   # warm-up: first launch of a new kernel variant loads it
+    for a, b in ev:
+        a.record()
+        run()
+        b.record()
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in ev]))
+
+
+def autotune(ctx: B.Context, run, key: str, reps=3, space=TUNING_SPACE, cache=True, log=None):
+    """Pick the context's launch shapes for a workload: coordinate descent over
+    `space` from the cached (else current) setting -- each parameter in turn takes the
+    value with the lowest median device time of `run()` (one render forward + backward
+    of the workload) with the others fixed, two sweeps -- then set the best and cache
+    it under `key`.  Returns (tuning, ms of the start setting, ms of the best)."""
+    path = tuning_cache_path()
+    table = {}
+    if cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                table = json.load(f)
+        except (OSError, ValueError):
+            table = {}
+    if cache and key in table:
+        ctx.set_tuning(**table[key]["tuning"])
+        return table[key]["tuning"], table[key]["start_ms"], table[key]["best_ms"]
+    best = ctx.get_tuning()
+    start_ms = best_ms = _time_ms(run, reps)
+    for _sweep in range(2):
+        changed = False
+        for name, values in space.items():
+            for v in values:
+                if v == best[name]:
+                    continue
+                trial = dict(best, **{name: v})
+                ctx.set_tuning(**trial)
+                ms = _time_ms(run, reps)
+                if log:
+                    log(f"tune {trial}: {ms:.4f} ms")
+                if ms < best_ms * 0.99:
+                    best, best_ms, changed = trial, ms, True
+            ctx.set_tuning(**best)
+        if not changed:
+            break
+    ctx.set_tuning(**best)
+    if cache:
+        table[key] = {"tuning": best, "start_ms": start_ms, "best_ms": best_ms}
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path + ".tmp", "w") as f:
+                json.dump(table, f, indent=1)
+            os.replace(path + ".tmp", path)
+        except OSError:
+            pass
+    return best, start_ms, best_ms

@@ -179,3 +179,38 @@ def test_refit_gives_the_rebuilt_tree_results(B):
     ref = oracle.render_fwd(vb_np, h.faces, n_b, h.albedo, sc.cams, sc.H, sc.W, sc.bg, sc.opts())
     assert pixel_ok(img_refit.cpu().numpy(), ref).all()
     assert B.hr_get_status(ctx) == B.HR_OK
+
+
+def test_tunings_keep_results(B):
+    """Every launch-shape setting renders and differentiates to the oracle's values
+    (work-item splits change only the float32 summation grouping); invalid settings
+    are refused on the host."""
+    import oracle
+    from tests.gpu_common import grad_ok, pixel_ok
+    sc = scene("ragged")
+    h = hand()
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, sc.N, sc.W, sc.H)
+    vt, cams, bg = _t(sc.verts), _t(sc.cams), _t(sc.bg)
+    o = sc.opts()
+    ref = oracle.render_fwd(sc.verts, h.faces, sc.normals, h.albedo, sc.cams, sc.H, sc.W, sc.bg, o)
+    _, A = oracle.loss(ref.astype(np.float32), sc.observed, sc.mask)
+    A = A.astype(np.float32)
+    g_ref, _ = oracle.render_bwd(h, sc.verts, sc.cams, sc.H, sc.W, sc.bg, o, A, normals=sc.normals)
+    img = torch.empty((sc.N, sc.H, sc.W, 3), device="cuda")
+    dv = torch.empty((h.V, 3), device="cuda")
+    B.hr_build_bvh(ctx, model, vt)
+    for t in ({"rays_per_lane": 1, "cand_per_chunk": 8, "max_chunks": 16, "blocks_per_sm": 4, "bwd_blocks_per_sm": 2},
+              {"rays_per_lane": 2, "cand_per_chunk": 32, "max_chunks": 8, "blocks_per_sm": 8, "bwd_blocks_per_sm": 6},
+              {"rays_per_lane": 4, "cand_per_chunk": 1, "max_chunks": 1, "blocks_per_sm": 1, "bwd_blocks_per_sm": 1}):
+        ctx.set_tuning(**t)
+        assert ctx.get_tuning() == t
+        B.hr_render_fwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o), img)
+        assert pixel_ok(img.cpu().numpy(), ref).all(), t
+        B.hr_render_bwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o, B.HR_BWD_REUSE_FWD), _t(A), dv)
+        assert grad_ok(dv.cpu().numpy(), g_ref).all(), t
+    for bad in ({"rays_per_lane": 3}, {"max_chunks": 17}, {"blocks_per_sm": 0}, {"bwd_blocks_per_sm": 9},
+                {"cand_per_chunk": 0}):
+        with pytest.raises(B.HandrtError):
+            ctx.set_tuning(**bad)
+    assert B.hr_get_status(ctx) == B.HR_OK
