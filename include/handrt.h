@@ -135,8 +135,10 @@ typedef struct hr_render_opts {
 
 /* Sizes a context is created for; all scratch is allocated once, up front. */
 typedef struct hr_limits {
-    int32_t max_V;      /* vertices (<= 8192: the backward keeps [V][6] in shared memory) */
-    int32_t max_F;      /* triangles (<= 8192: single-block BVH build)           */
+    int32_t max_V;      /* vertices (<= 65536; up to 8192 the backward sums in shared
+                           memory, beyond that with global atomics)             */
+    int32_t max_F;      /* triangles (<= 65536; the BVH build runs in one block per
+                           instance up to ~2400, in a multi-block build beyond)  */
     int32_t max_E;      /* edges                                                 */
     int32_t max_views;  /* views per call                                        */
     int32_t max_width;  /* image width W per call                                */

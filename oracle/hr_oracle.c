@@ -261,8 +261,8 @@ static double dot_d(const double a[3], const double b[3]) { return a[0] * b[0] +
 
 /* For a hit of the ray (o, d) and upstream weights g[3] = dL/df, add dL/dverts of
  * the triangle (through the barycentrics at the fixed ray) to dV and dL/dnormals
- * to dN.  Barycentrics: u = [s,d,e2]/[e1,d,e2], v = [d,s,e1]/[e1,d,e2] with
- * s = o - v0, e1 = v1 - v0, e2 = v2 - v0 and [a,b,c] = a.(b x c). */
+ * to dN.  Barycentrics of the hit: (1-u-v) v0 + u v1 + v v2 = o + t d, with
+ * e1 = v1 - v0, e2 = v2 - v0 and [a,b,c] = a.(b x c). */
 static void interior_grad(const scene_t* sc, const hit_t* h, f3 o32, f3 d32, const double g[3],
                           double* dV, double* dN) {
     const int32_t* f = sc->faces + 3 * h->tri;
@@ -310,28 +310,30 @@ static void interior_grad(const scene_t* sc, const hit_t* h, f3 o32, f3 d32, con
         dN[3 * f[1] + c] += u * dnm[c];
         dN[3 * f[2] + c] += v * dnm[c];
     }
-    /* barycentric derivatives at the fixed ray */
+    /* barycentric derivatives at the fixed ray: the hit solves
+     * (1-u-v) v0 + u v1 + v v2 = o + t d, so moving vertex k by dp changes (u, v, t)
+     * by -M^-1 (w_k dp) with M = [e1, e2, -d] and w = (1-u-v, u, v).  Rows 0 and 1 of
+     * M^-1 are (d x e2) / D and (e1 x d) / D with D = e1 . (d x e2), hence
+     *   dL/dv_k = -w_k (gu (d x e2) + gv (e1 x d)) / D.
+     * (The equivalent form through s = o - v0 holds only when (u, v) solve the
+     * system exactly; with the float32 hit's (u, v) it loses ~|s| / |e| of their
+     * precision, while this one depends on them linearly.) */
     double dd[3] = {d32.x, d32.y, d32.z};
-    double s[3], e1[3], e2[3];
+    double e1[3], e2[3];
     for (int c = 0; c < 3; ++c) {
-        s[c] = (double)(&o32.x)[c] - P[0][c];
         e1[c] = (double)P[1][c] - P[0][c];
         e2[c] = (double)P[2][c] - P[0][c];
     }
-    double dxe2[3], e1xd[3], dxs[3];
+    (void)o32;
+    double dxe2[3], e1xd[3];
     cross_d(dd, e2, dxe2);        /* d x e2 */
     cross_d(e1, dd, e1xd);        /* e1 x d */
-    cross_d(dd, s, dxs);          /* d x s  */
     double D = dot_d(e1, dxe2);   /* [e1, d, e2] */
-    double sxd[3] = {-dxs[0], -dxs[1], -dxs[2]};   /* s x d */
-    double uv = gu * u + gv * v;
     for (int c = 0; c < 3; ++c) {
-        double g_s = (gu * dxe2[c] + gv * e1xd[c]) / D;
-        double g_e1 = (gv * dxs[c] - uv * dxe2[c]) / D;
-        double g_e2 = (gu * sxd[c] - uv * e1xd[c]) / D;
-        dV[3 * f[1] + c] += g_e1;
-        dV[3 * f[2] + c] += g_e2;
-        dV[3 * f[0] + c] -= g_s + g_e1 + g_e2;
+        double q = (gu * dxe2[c] + gv * e1xd[c]) / D;
+        dV[3 * f[0] + c] -= w * q;
+        dV[3 * f[1] + c] -= u * q;
+        dV[3 * f[2] + c] -= v * q;
     }
 }
 

@@ -37,7 +37,8 @@ void free_ctx(Context* c) {
                   c->dm,      c->sil,     c->sil_count, c->loss_partials, c->counters,   c->skin_partials,
                   c->status,  c->stats,   c->pool_bb,   c->pool_z,     c->pool_rec,      c->st_info,
                   c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it,
-                  c->bvh_parent, c->bvh_valid};
+                  c->bvh_parent, c->bvh_valid, c->bvh_keys, c->bvh_flags, c->bvh_bounds, c->bvh_bad,
+                  c->bvh_mode, c->extra64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete[] c->hvt;
@@ -91,7 +92,8 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
   c->pool_cap = (int)std::min<size_t>((size_t)1 << 28, 16 * subtiles + 4096);
   c->item_cap = (int)items;
   c->loss_blocks = loss_blocks;
-  const size_t partial_blocks = n == 1 ? (size_t)c->render_blocks : 1;   // single-instance backward only
+  // block partials: single-instance backward with shared-memory sums (V <= 8192)
+  const size_t partial_blocks = (n == 1 && V <= 8192) ? (size_t)c->render_blocks : 1;
   const size_t nviews = views;
   bool ok = dev_alloc(&c->nodes, ni * F, a) && dev_alloc(&c->tris, ni * 3 * F, a) &&
             dev_alloc(&c->normals, ni * 3 * V, a) && dev_alloc(&c->normal_len, ni * V, a) &&
@@ -105,7 +107,14 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
             dev_alloc(&c->pool_rec, c->pool_cap, a) && dev_alloc(&c->st_info, subtiles, a) &&
             dev_alloc(&c->items, c->item_cap, a) && dev_alloc(&c->item_part, (size_t)c->item_cap * 32, a) &&
             dev_alloc(&c->extra, ni * 6 * V, a) && dev_alloc(&c->work_ctr, 2 + 2 * ni, a) &&
-            dev_alloc(&c->bvh_parent, ni * 2 * F, a) && dev_alloc(&c->bvh_valid, ni, a);
+            dev_alloc(&c->bvh_parent, ni * 2 * F, a) && dev_alloc(&c->bvh_valid, ni, a) &&
+            dev_alloc(&c->bvh_bounds, ni * 6, a) && dev_alloc(&c->bvh_bad, ni, a) && dev_alloc(&c->bvh_mode, ni, a);
+  // keys of the multi-block build, for meshes beyond one block's shared memory
+  c->bvh_pmax = 1;
+  while ((size_t)c->bvh_pmax < F) c->bvh_pmax <<= 1;
+  if (ok && F > 2048)
+    ok = dev_alloc(&c->bvh_keys, ni * (size_t)c->bvh_pmax, a) && dev_alloc(&c->bvh_flags, ni * F, a);
+  if (ok && V > 8192) ok = dev_alloc(&c->extra64, ni * 6 * V, a);
   if (ok) ok = cudaMemset(c->counters, 0, ni * 4 * sizeof(unsigned)) == cudaSuccess &&
                cudaMemset(c->status, 0, sizeof(int)) == cudaSuccess &&
                cudaMemset(c->stats, 0, 3 * hr::kStatsPer * sizeof(unsigned long long)) == cudaSuccess &&
@@ -134,7 +143,7 @@ int hr_context_create(const hr_limits* lim, hr_context** out) {
   if (!lim || !out) return HR_ERR_ARG;
   *out = nullptr;
   if (!limits_ok(lim, false)) return HR_ERR_ARG;
-  if (lim->max_V > 8192 || lim->max_F > 8192 || lim->max_views > 65535 || lim->max_width > 16384 ||
+  if (lim->max_V > 65536 || lim->max_F > 65536 || lim->max_views > 65535 || lim->max_width > 16384 ||
       lim->max_height > 16384 || (long long)lim->max_views * lim->max_width * lim->max_height > (1ll << 31) / 3)
     return HR_ERR_UNSUPPORTED;
   const size_t subtiles = (size_t)hr::subtiles_for(lim->max_views, lim->max_width, lim->max_height);
@@ -150,7 +159,7 @@ int hr_batch_create(const hr_limits* lim, const hr_instance_desc* desc, int n, h
   if (!lim || !desc || !out || n < 1) return HR_ERR_ARG;
   *out = nullptr;
   if (!limits_ok(lim, true)) return HR_ERR_ARG;
-  if (lim->max_V > 8192 || lim->max_F > 8192 || n > 65536) return HR_ERR_UNSUPPORTED;
+  if (lim->max_V > 65536 || lim->max_F > 65536 || n > 65536) return HR_ERR_UNSUPPORTED;
   long long views = 0, subtiles = 0, pixels = 0, items = 0;
   for (int i = 0; i < n; ++i) {
     const hr_instance_desc& d = desc[i];

@@ -350,6 +350,264 @@ __global__ void k_vertex_normals(const float* __restrict__ verts_all, const int*
   normal_len[v] = len;
 }
 
+
+// ---------------------------------------------------------------------------------
+// Multi-block build for meshes whose keys do not fit one block's shared memory
+// (F above ~2400 with the nodes, ~25k without): the same Morton codes, hierarchy and
+// refit over global memory, one instance per grid row, the keys sorted by a bitonic
+// network whose stages below 2048 run in shared memory.
+// ---------------------------------------------------------------------------------
+constexpr int kSortChunk = 2048;    // keys sorted per block in shared memory
+constexpr int kGridThreads = 256;
+
+// float <-> order-preserving unsigned (for atomicMin / atomicMax of floats)
+__device__ __forceinline__ unsigned f2o(float f) {
+  unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(unsigned u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// per instance: refit (mode 1) or full build (mode 0), decided once per call before
+// the other kernels read it; a full build marks the tree valid for later refits
+// (a build over bad faces clears that again) and resets the bounds and the bad flag
+__global__ void k_lb_decide(int* __restrict__ mode, int* __restrict__ valid, unsigned* __restrict__ bounds_all,
+                            int* __restrict__ bad_all, const uint32_t* iter_dev, int rebuild_every) {
+  const int inst = blockIdx.x;
+  const bool refit = rebuild_every > 1 && iter_dev && valid[inst] == 1 && (*iter_dev % rebuild_every) != 0;
+  mode[inst] = refit ? 1 : 0;
+  if (refit) return;
+  valid[inst] = 1;
+  bad_all[inst] = 0;
+  for (int c = 0; c < 3; ++c) {
+    bounds_all[inst * 6 + c] = 0xFFFFFFFFu;
+    bounds_all[inst * 6 + 3 + c] = 0u;
+  }
+}
+
+// centroid bounds (ordered unsigned, [n][6]: min xyz, max xyz) and face validation
+__global__ void k_lb_bounds(const float* __restrict__ verts_all, const int* __restrict__ faces, int F, int V,
+                            unsigned* __restrict__ bounds_all, int* __restrict__ bad_all, const int* mode,
+                            int* status) {
+  if (mode[blockIdx.y]) return;
+  const float* verts = verts_all + (size_t)blockIdx.y * 3 * V;
+  unsigned* bounds = bounds_all + blockIdx.y * 6;
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < F; f += gridDim.x * blockDim.x) {
+    const int i0 = faces[3 * f], i1 = faces[3 * f + 1], i2 = faces[3 * f + 2];
+    if (i0 < 0 || i0 >= V || i1 < 0 || i1 >= V || i2 < 0 || i2 >= V) {
+      set_status(status, kStatusBadModel);
+      bad_all[blockIdx.y] = 1;
+      continue;
+    }
+    for (int c = 0; c < 3; ++c) {
+      const float x = (verts[3 * i0 + c] + verts[3 * i1 + c] + verts[3 * i2 + c]) * (1.0f / 3.0f);
+      lo[c] = fminf(lo[c], x);
+      hi[c] = fmaxf(hi[c], x);
+    }
+  }
+  for (int c = 0; c < 3; ++c) {
+    const float a = warp_min(lo[c]), b = warp_max(hi[c]);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&bounds[c], f2o(a));
+      atomicMax(&bounds[3 + c], f2o(b));
+    }
+  }
+}
+
+// keys[i] = morton << 32 | i for i < F, all ones up to P
+__global__ void k_lb_morton(const float* __restrict__ verts_all, const int* __restrict__ faces, int F, int V, int P,
+                            const unsigned* __restrict__ bounds_all, const int* __restrict__ bad_all,
+                            unsigned long long* __restrict__ keys_all, const int* mode) {
+  if (mode[blockIdx.y]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  unsigned long long* keys = keys_all + (size_t)blockIdx.y * P;
+  unsigned long long key = ~0ull;
+  if (i < F && !bad_all[blockIdx.y]) {
+    const float* verts = verts_all + (size_t)blockIdx.y * 3 * V;
+    const unsigned* bo = bounds_all + blockIdx.y * 6;
+    const int i0 = faces[3 * i], i1 = faces[3 * i + 1], i2 = faces[3 * i + 2];
+    unsigned q[3];
+    for (int c = 0; c < 3; ++c) {
+      const float x = (verts[3 * i0 + c] + verts[3 * i1 + c] + verts[3 * i2 + c]) * (1.0f / 3.0f);
+      const float l = o2f(bo[c]), ext = o2f(bo[3 + c]) - l;
+      const float nrm = ext > 0.0f ? (x - l) / ext : 0.5f;
+      q[c] = (unsigned)fminf(fmaxf(nrm * 1024.0f, 0.0f), 1023.0f);
+    }
+    const unsigned code = (expand_bits10(q[0]) << 2) | (expand_bits10(q[1]) << 1) | expand_bits10(q[2]);
+    key = ((unsigned long long)code << 32) | (unsigned)i;
+  }
+  keys[i] = key;
+}
+
+// bitonic stages (k, j) with j < kSortChunk of one 2048-key chunk, in shared memory;
+// first = true runs every stage k = 2 .. kSortChunk, otherwise the j-stages of one k
+__global__ void __launch_bounds__(1024) k_lb_sort_local(unsigned long long* __restrict__ keys_all, int P, int k_outer,
+                                                        bool first, const int* mode) {
+  if (mode[blockIdx.y]) return;
+  __shared__ unsigned long long sk[kSortChunk];
+  unsigned long long* keys = keys_all + (size_t)blockIdx.y * P;
+  const int base = blockIdx.x * kSortChunk;
+  for (int t = threadIdx.x; t < kSortChunk; t += blockDim.x) sk[t] = keys[base + t];
+  __syncthreads();
+  const int k_lo = first ? 2 : k_outer, k_hi = first ? kSortChunk : k_outer;
+  for (int k = k_lo; k <= k_hi; k <<= 1) {
+    for (int j = min(k, kSortChunk) >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < kSortChunk; t += blockDim.x) {
+        const int l = t ^ j;
+        if (l > t) {
+          const bool up = ((base + t) & k) == 0;
+          const unsigned long long x = sk[t], y = sk[l];
+          if ((x > y) == up) {
+            sk[t] = y;
+            sk[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < kSortChunk; t += blockDim.x) keys[base + t] = sk[t];
+}
+
+// one bitonic stage (k, j) with j >= kSortChunk over global memory
+__global__ void k_lb_sort_global(unsigned long long* __restrict__ keys_all, int P, int k, int j, const int* mode) {
+  if (mode[blockIdx.y]) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P) return;
+  const int l = t ^ j;
+  if (l <= t) return;
+  unsigned long long* keys = keys_all + (size_t)blockIdx.y * P;
+  const bool up = (t & k) == 0;
+  const unsigned long long x = keys[t], y = keys[l];
+  if ((x > y) == up) {
+    keys[t] = y;
+    keys[l] = x;
+  }
+}
+
+// Karras hierarchy over the sorted keys (internal nodes 0..F-2, leaves ~k)
+__global__ void k_lb_hierarchy(const unsigned long long* __restrict__ keys_all, int F, int P, int node_stride,
+                               Node* __restrict__ nodes_all, int* __restrict__ parent_all, const int* mode) {
+  if (mode[blockIdx.y]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long* keys = keys_all + (size_t)blockIdx.y * P;
+  Node* nodes = nodes_all + (size_t)blockIdx.y * node_stride;
+  int* parent = parent_all + (size_t)blockIdx.y * 2 * node_stride;
+  if (F == 1) {
+    if (i == 0) {
+      nodes[0].d = make_int4(~0, ~0, 0, 0);
+      parent[0] = -1;
+      parent[F] = 0;
+    }
+    return;
+  }
+  if (i >= F - 1) return;
+  int d = (delta(keys, F, i, i + 1) - delta(keys, F, i, i - 1)) > 0 ? 1 : -1;
+  int dmin = delta(keys, F, i, i - d);
+  int lmax = 2;
+  while (delta(keys, F, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, F, i, i + (l + t) * d) > dmin) l += t;
+  int j = i + l * d;
+  int dnode = delta(keys, F, i, j);
+  int s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta(keys, F, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int gamma = i + s * d + min(d, 0);
+  int left = (min(i, j) == gamma) ? ~gamma : gamma;
+  int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+  nodes[i].d = make_int4(left, right, 0, 0);
+  if (left >= 0) parent[left] = i; else parent[F + ~left] = i;
+  if (right >= 0) parent[right] = i; else parent[F + ~right] = i;
+  if (i == 0) parent[0] = -1;
+}
+
+// triangle records and leaf boxes, then the bottom-up refit with global flags (zeroed
+// before the launch); a refit takes the leaf order from the previous records
+__global__ void k_lb_leaves(const float* __restrict__ verts_all, const int* __restrict__ faces, int F, int V,
+                            int P, int node_stride, const unsigned long long* __restrict__ keys_all,
+                            Node* __restrict__ nodes_all, float4* __restrict__ tris_all,
+                            const int* __restrict__ parent_all, int* __restrict__ flags_all, int* __restrict__ valid,
+                            const int* __restrict__ bad_all, const int* mode, int* status) {
+  const bool refit = mode[blockIdx.y] == 1;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  Node* nodes = nodes_all + (size_t)blockIdx.y * node_stride;
+  float4* tris = tris_all + (size_t)blockIdx.y * 3 * node_stride;
+  if (!refit && bad_all[blockIdx.y]) {   // bad faces: the degenerate one-leaf tree
+    if (k == 0) {
+      nodes[0].d = make_int4(~0, ~0, 0, 0);
+      nodes[0].a = make_float4(1.0f, 1.0f, 1.0f, -1.0f);
+      nodes[0].b = make_float4(-1.0f, -1.0f, 1.0f, 1.0f);
+      nodes[0].c = make_float4(1.0f, -1.0f, -1.0f, -1.0f);
+      tris[0] = tris[1] = tris[2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      valid[blockIdx.y] = 0;
+    }
+    return;
+  }
+  if (k >= F) return;
+  const float* verts = verts_all + (size_t)blockIdx.y * 3 * V;
+  const int* parent = parent_all + (size_t)blockIdx.y * 2 * node_stride;
+  int* flags = flags_all + (size_t)blockIdx.y * node_stride;
+  const unsigned long long* keys = keys_all + (size_t)blockIdx.y * P;
+  const int tri = refit ? __float_as_int(tris[3 * k + 2].y) : (int)(keys[k] & 0xffffffffull);
+  if (tri < 0 || tri >= F) {
+    set_status(status, kStatusIndex);
+    return;
+  }
+  float3 v0 = ld3(verts + 3 * faces[3 * tri]);
+  float3 v1 = ld3(verts + 3 * faces[3 * tri + 1]);
+  float3 v2 = ld3(verts + 3 * faces[3 * tri + 2]);
+  float3 e1 = dsub(v1, v0), e2 = dsub(v2, v0);
+  tris[3 * k + 0] = make_float4(v0.x, v0.y, v0.z, e1.x);
+  tris[3 * k + 1] = make_float4(e1.y, e1.z, e2.x, e2.y);
+  tris[3 * k + 2] = make_float4(e2.z, __int_as_float(tri), 0.0f, 0.0f);
+  Box b;
+  float amax = 0.0f;
+  float p0[3] = {v0.x, v0.y, v0.z}, p1[3] = {v1.x, v1.y, v1.z}, p2[3] = {v2.x, v2.y, v2.z};
+  for (int c = 0; c < 3; ++c) {
+    b.lo[c] = fminf(p0[c], fminf(p1[c], p2[c]));
+    b.hi[c] = fmaxf(p0[c], fmaxf(p1[c], p2[c]));
+    amax = fmaxf(amax, fmaxf(fabsf(b.lo[c]), fabsf(b.hi[c])));
+  }
+  const float pad = 1e-6f + 1e-5f * amax;
+  for (int c = 0; c < 3; ++c) {
+    b.lo[c] -= pad;
+    b.hi[c] += pad;
+  }
+  if (F == 1) {
+    store_slot(nodes, 0, 0, b);
+    store_slot(nodes, 0, 1, b);
+    return;
+  }
+  int p = parent[F + k];
+  if (p < 0 || p >= F - 1) {
+    set_status(status, kStatusIndex);
+    return;
+  }
+  store_slot(nodes, p, (nodes[p].d.x == ~k) ? 0 : 1, b);
+  __threadfence();
+  for (int up = 0; up < F; ++up) {   // a well-formed tree is at most F - 1 levels deep
+    if (atomicAdd(&flags[p], 1) == 0) break;
+    __threadfence();
+    Box u = load_union(nodes, p);
+    const int gp = parent[p];
+    if (gp < 0) break;
+    if (gp >= F - 1) {
+      set_status(status, kStatusIndex);
+      break;
+    }
+    store_slot(nodes, gp, (nodes[gp].d.x == p) ? 0 : 1, u);
+    __threadfence();
+    p = gp;
+  }
+}
+
 }  // namespace
 
 int configure_bvh_kernels() {
@@ -358,6 +616,55 @@ int configure_bvh_kernels() {
     cudaGetLastError();
     return HR_ERR_CUDA;
   }
+  return HR_OK;
+}
+
+// the multi-block build (keys beyond one block's shared memory)
+int launch_build_bvh_grid(Context* ctx, const hr_model* m, const float* verts, const uint32_t* iter_dev,
+                          int rebuild_every, int P, cudaStream_t s) {
+  const int F = m->F, V = m->V, ni = ctx->n_inst, ns = ctx->lim.max_F;
+  if (P > ctx->bvh_pmax) return HR_ERR_UNSUPPORTED;
+  if (ctx->bvh_faces != m->faces || ctx->F != F) {
+    if (cudaMemsetAsync(ctx->bvh_valid, 0, sizeof(int) * ni, s) != cudaSuccess) return HR_ERR_CUDA;
+    ctx->bvh_faces = m->faces;
+  }
+  k_lb_decide<<<ni, 1, 0, s>>>(ctx->bvh_mode, ctx->bvh_valid, ctx->bvh_bounds, ctx->bvh_bad, iter_dev,
+                               rebuild_every);
+  HR_CHECK_LAUNCH();
+  const unsigned fb = (unsigned)((F + kGridThreads - 1) / kGridThreads);
+  k_lb_bounds<<<dim3(fb < 64 ? fb : 64, ni), kGridThreads, 0, s>>>(verts, m->faces, F, V, ctx->bvh_bounds,
+                                                                   ctx->bvh_bad, ctx->bvh_mode, ctx->status);
+  HR_CHECK_LAUNCH();
+  const dim3 gp((unsigned)((P + kGridThreads - 1) / kGridThreads), ni);
+  k_lb_morton<<<gp, kGridThreads, 0, s>>>(verts, m->faces, F, V, P, ctx->bvh_bounds, ctx->bvh_bad, ctx->bvh_keys,
+                                          ctx->bvh_mode);
+  HR_CHECK_LAUNCH();
+  const dim3 gc((unsigned)(P / kSortChunk), ni);
+  k_lb_sort_local<<<gc, 1024, 0, s>>>(ctx->bvh_keys, P, 0, true, ctx->bvh_mode);
+  HR_CHECK_LAUNCH();
+  for (int k = 2 * kSortChunk; k <= P; k <<= 1) {
+    for (int j = k >> 1; j >= kSortChunk; j >>= 1) {
+      k_lb_sort_global<<<gp, kGridThreads, 0, s>>>(ctx->bvh_keys, P, k, j, ctx->bvh_mode);
+      HR_CHECK_LAUNCH();
+    }
+    k_lb_sort_local<<<gc, 1024, 0, s>>>(ctx->bvh_keys, P, k, false, ctx->bvh_mode);
+    HR_CHECK_LAUNCH();
+  }
+  k_lb_hierarchy<<<dim3(fb, ni), kGridThreads, 0, s>>>(ctx->bvh_keys, F, P, ns, ctx->nodes, ctx->bvh_parent,
+                                                       ctx->bvh_mode);
+  HR_CHECK_LAUNCH();
+  if (cudaMemsetAsync(ctx->bvh_flags, 0, sizeof(int) * (size_t)ni * ns, s) != cudaSuccess) return HR_ERR_CUDA;
+  k_lb_leaves<<<dim3(fb, ni), kGridThreads, 0, s>>>(verts, m->faces, F, V, P, ns, ctx->bvh_keys, ctx->nodes,
+                                                    ctx->tris, ctx->bvh_parent, ctx->bvh_flags, ctx->bvh_valid,
+                                                    ctx->bvh_bad, ctx->bvh_mode, ctx->status);
+  HR_CHECK_LAUNCH();
+  k_vertex_normals<<<dim3((V + 255) / 256, ni), 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, V, F,
+                                                             ctx->normals, ctx->normal_len, ctx->status);
+  HR_CHECK_LAUNCH();
+  ctx->V = V;
+  ctx->F = F;
+  ++ctx->bvh_gen;
+  ctx->fwd_valid = false;
   return HR_OK;
 }
 
@@ -371,7 +678,7 @@ int launch_update_bvh(Context* ctx, const hr_model* m, const float* verts, const
   int P = 1;
   while (P < F) P <<= 1;
   size_t smem = (size_t)P * 8 + (size_t)3 * F * 4;
-  if (smem > (size_t)kBuildSmemCap) return HR_ERR_UNSUPPORTED;
+  if (smem > (size_t)kBuildSmemCap) return launch_build_bvh_grid(ctx, m, verts, iter_dev, rebuild_every, P, s);
   const size_t with_nodes = ((smem + 15) & ~(size_t)15) + (size_t)(F > 1 ? F - 1 : 1) * sizeof(Node);
   const bool snodes = with_nodes <= (size_t)kBuildSmemCap;
   if (snodes) smem = with_nodes;

@@ -86,6 +86,13 @@ struct Context {
   int* bvh_parent;       // [n_inst][2 max_F] parents of the internal nodes and leaves
   int* bvh_valid;        // [n_inst] 1 once a tree of bvh_faces exists (refits need it)
   const int* bvh_faces;  // the face array of the last build
+  // multi-block build (meshes beyond one block's shared memory)
+  int bvh_pmax;                  // keys per instance (power of two >= max_F)
+  unsigned long long* bvh_keys;  // [n_inst][bvh_pmax]
+  int* bvh_flags;                // [n_inst][max_F] refit arrival counters
+  unsigned* bvh_bounds;          // [n_inst][6] centroid bounds (order-preserving)
+  int* bvh_bad;                  // [n_inst] a face index out of range
+  int* bvh_mode;                 // [n_inst] this call: 1 refit, 0 full build
   // the last forward render (its candidate pool serves a backward with
   // HR_BWD_REUSE_FWD): vertices, cameras, sizes and the build it used
   const void* fwd_verts;
@@ -107,6 +114,7 @@ struct Context {
   float4* item_part;     // [item_cap][32]
   int item_cap;
   float* extra;          // [n_inst][max_V][6]
+  double* extra64;       // [n_inst][max_V][6] backward sums when max_V > 8192
   unsigned* work_ctr;    // [2 + 2 n_inst]
   // backward scratch
   float* partials;       // [render_blocks][max_V][6] (single-instance contexts)

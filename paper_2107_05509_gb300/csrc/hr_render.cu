@@ -42,6 +42,8 @@
 // instance after instance too and add their shared-memory sums into the instance's
 // gradient when they move on.  A single-instance call is a batch of one with a
 // uniform view layout (no table).
+#include <type_traits>
+
 #include "hr_internal.h"
 
 namespace hr {
@@ -194,6 +196,8 @@ struct Work {
   int4* items;     // [items] (sub-tile, chunk, chunks, first item of the sub-tile)
   int item_cap;
   float4* part;    // [items][32] forward per-item sums (r, g, b, misses)
+  double* extra64; // [n_inst][6V] backward sums of meshes beyond shared memory (float64
+                   // atomics: long runs of cancelling contributions)
   float* extra;    // [n_inst][6V] backward sums: shading blocks of a batch, and work
                    // done outside the shading blocks
   unsigned* ctr;   // [2 + 2 n_inst] sub-tile counter, pool fill, then per instance
@@ -284,7 +288,8 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-__device__ __forceinline__ void add3(float* dst, int i, float x, float y, float z) {
+template <class T>
+__device__ __forceinline__ void add3(T* dst, int i, float x, float y, float z) {
   atomicAdd(&dst[3 * i], x);
   atomicAdd(&dst[3 * i + 1], y);
   atomicAdd(&dst[3 * i + 2], z);
@@ -684,7 +689,7 @@ struct HitGrad {
   float dv[9], dn[9];
 };
 
-__device__ __forceinline__ void hit_grad(const RenderArgs& a, const Hit& h, const int3 f, float3 o, float3 d,
+__device__ __forceinline__ void hit_grad(const RenderArgs& a, const Hit& h, const int3 f, float3 d,
                                          float3 g, HitGrad& out) {
   float3 n0 = ld3(a.normals + 3 * f.x), n1 = ld3(a.normals + 3 * f.y), n2 = ld3(a.normals + 3 * f.z);
   float3 a0 = ld3(a.albedo + 3 * f.x), a1 = ld3(a.albedo + 3 * f.y), a2 = ld3(a.albedo + 3 * f.z);
@@ -712,29 +717,28 @@ __device__ __forceinline__ void hit_grad(const RenderArgs& a, const Hit& h, cons
   out.dn[0] = w * dnm.x; out.dn[1] = w * dnm.y; out.dn[2] = w * dnm.z;
   out.dn[3] = u * dnm.x; out.dn[4] = u * dnm.y; out.dn[5] = u * dnm.z;
   out.dn[6] = v * dnm.x; out.dn[7] = v * dnm.y; out.dn[8] = v * dnm.z;
-  // barycentrics at the fixed ray: u = [s,d,e2]/D, v = [d,s,e1]/D, D = [e1,d,e2]
+  // barycentrics at the fixed ray: moving vertex k by dp moves the hit's (u, v, t)
+  // by -M^-1 (w_k dp) with M = [e1, e2, -d] and weights (w, u, v), so
+  // dL/dp_k = -w_k (gu (d x e2) + gv (e1 x d)) / D, D = e1 . (d x e2) -- written with
+  // the triangle's edges and the ray direction only (the camera-to-triangle offset,
+  // ~1000x an edge, cancels out of the algebra and would cost float32 digits)
   float3 p0 = ld3(a.verts + 3 * f.x), p1 = ld3(a.verts + 3 * f.y), p2 = ld3(a.verts + 3 * f.z);
-  float3 s = make_float3(o.x - p0.x, o.y - p0.y, o.z - p0.z);
   float3 e1 = make_float3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z);
   float3 e2 = make_float3(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z);
-  float3 dxe2 = cross3(d, e2), e1xd = cross3(e1, d), dxs = cross3(d, s);
+  float3 dxe2 = cross3(d, e2), e1xd = cross3(e1, d);
   float invD = 1.0f / dot3(e1, dxe2);
-  float uv = gu * u + gv * v;
-  float gs[3] = {(gu * dxe2.x + gv * e1xd.x) * invD, (gu * dxe2.y + gv * e1xd.y) * invD,
-                 (gu * dxe2.z + gv * e1xd.z) * invD};
-  float ge1[3] = {(gv * dxs.x - uv * dxe2.x) * invD, (gv * dxs.y - uv * dxe2.y) * invD,
-                  (gv * dxs.z - uv * dxe2.z) * invD};
-  float ge2[3] = {(-gu * dxs.x - uv * e1xd.x) * invD, (-gu * dxs.y - uv * e1xd.y) * invD,
-                  (-gu * dxs.z - uv * e1xd.z) * invD};
+  float q[3] = {(gu * dxe2.x + gv * e1xd.x) * invD, (gu * dxe2.y + gv * e1xd.y) * invD,
+                (gu * dxe2.z + gv * e1xd.z) * invD};
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    out.dv[c] = -(gs[c] + ge1[c] + ge2[c]);
-    out.dv[3 + c] = ge1[c];
-    out.dv[6 + c] = ge2[c];
+    out.dv[c] = -w * q[c];
+    out.dv[3 + c] = -u * q[c];
+    out.dv[6 + c] = -v * q[c];
   }
 }
 
-__device__ __forceinline__ void flush_tri(int3 f, const HitGrad& acc, float* dV, float* dN) {
+template <class T>
+__device__ __forceinline__ void flush_tri(int3 f, const HitGrad& acc, T* dV, T* dN) {
   add3(dV, f.x, acc.dv[0], acc.dv[1], acc.dv[2]);
   add3(dV, f.y, acc.dv[3], acc.dv[4], acc.dv[5]);
   add3(dV, f.z, acc.dv[6], acc.dv[7], acc.dv[8]);
@@ -746,9 +750,9 @@ __device__ __forceinline__ void flush_tri(int3 f, const HitGrad& acc, float* dV,
 // Gradient of samples [s0, s1) of this lane's pixel (upstream g, `live` lanes only;
 // all lanes call it), traced S at a time and differentiated in sample order; added to
 // dV [V][3] / dN [V][3] per run of hits on one triangle.
-template <bool STATS, int S>
+template <bool STATS, int S, class T>
 __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile& t, const Cam& cam, int off, int K,
-                                             int s0, int s1, bool live, float3 g, float* dV, float* dN, Counts& cnt) {
+                                             int s0, int s1, bool live, float3 g, T* dV, T* dN, Counts& cnt) {
   const int lane = threadIdx.x & 31;
   const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
   const float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
@@ -801,7 +805,7 @@ __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile&
         cf = make_int3(__ldg(&a.faces[3 * cur]), __ldg(&a.faces[3 * cur + 1]), __ldg(&a.faces[3 * cur + 2]));
       }
       HitGrad hg;
-      hit_grad(a, h[j], cf, o, d[j], g, hg);
+      hit_grad(a, h[j], cf, d[j], g, hg);
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
         acc.dv[c] += hg.dv[c];
@@ -1082,26 +1086,38 @@ __global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, fl
   }
 }
 
-// interior term: warps take work items; the block accumulates dV/dN in shared
-// memory (sdV [V][3], sdN [V][3]).  Single instance (BATCH false): one partial per
-// block, summed in block order by k_reduce_partials.  Batch: the block works through
-// the instances in order and, when every warp is done with one, adds its non-zero
-// sums into that instance's extra [6V] (global atomics) and clears them.
-template <bool STATS, bool BATCH, int S>
+// interior term: warps take work items.  ACC selects where the gradient collects:
+//   kAccPartials  the block accumulates dV/dN in shared memory (sdV [V][3], sdN [V][3])
+//                 and writes one partial per block, summed in block order by
+//                 k_reduce_partials (single instance)
+//   kAccFlush     shared memory as above; the block works through the instances in
+//                 order and, when every warp is done with one, adds its non-zero sums
+//                 into that instance's extra [6V] (global atomics) and clears them
+//   kAccGlobal    meshes whose [V][6] sums exceed shared memory: every run of hits on
+//                 one triangle is added straight into the instance's extra [6V]
+constexpr int kAccPartials = 0, kAccFlush = 1, kAccGlobal = 2;
+template <bool STATS, int ACC, int S>
 __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(RenderArgs a_in,
                                                                              const float* __restrict__ adjoint,
                                                                              float* __restrict__ partials,
                                                                              unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
   extern __shared__ float sacc[];
-  float* sdV = sacc;
-  float* sdN = sacc + 3 * a0.V;
-  for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) sacc[i] = 0.0f;
-  __syncthreads();
+  if (ACC != kAccGlobal) {
+    for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) sacc[i] = 0.0f;
+    __syncthreads();
+  }
   Counts cnt;
   for (int inst = 0; inst < a0.n_inst; ++inst) {
     const int n = item_count(a0, inst), ibase = inst_ibase(a0, inst);
     const RenderArgs a = for_inst(a0, inst);
+    typedef typename std::conditional<ACC == kAccGlobal, double, float>::type AccT;
+    AccT* sdV;
+    if constexpr (ACC == kAccGlobal)
+      sdV = a0.wk.extra64 + (size_t)inst * 6 * a0.V;
+    else
+      sdV = sacc;
+    AccT* sdN = sdV + 3 * a0.V;
     int did = 0;
     for (;;) {
       const int it = next_item(a, inst, n);
@@ -1118,7 +1134,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
       grad_samples<STATS, S>(a, t, cam, pk.x, pk.y, s0, s1, live, g, sdV, sdN, cnt);
       did = 1;
     }
-    if (BATCH) {
+    if (ACC == kAccFlush) {
       if (__syncthreads_or(did)) {
         float* dst = a0.wk.extra + (size_t)inst * 6 * a0.V;
         for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) {
@@ -1133,7 +1149,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
     }
   }
   flush_counts<STATS>(cnt, stats);
-  if (BATCH) return;
+  if (ACC != kAccPartials) return;
   __syncthreads();
   float* out = partials + (size_t)blockIdx.x * 6 * a0.V;
   for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) out[i] = sacc[i];
@@ -1145,8 +1161,8 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
 // call).  blockIdx.y selects the instance (a batch has no partials).
 constexpr int kRedEntries = 32, kRedGroups = 16;
 __global__ void __launch_bounds__(kRedEntries * kRedGroups) k_reduce_partials(
-    const float* __restrict__ partials, const float* __restrict__ extra_all, int nblocks, int V,
-    float* __restrict__ d_verts_all, float* __restrict__ dN_all) {
+    const float* __restrict__ partials, const float* __restrict__ extra_all, const double* __restrict__ extra64_all,
+    int nblocks, int V, float* __restrict__ d_verts_all, float* __restrict__ dN_all) {
   __shared__ float red[kRedGroups][kRedEntries];
   const int j = threadIdx.x % kRedEntries, g = threadIdx.x / kRedEntries;
   const int i = blockIdx.x * kRedEntries + j;
@@ -1162,6 +1178,7 @@ __global__ void __launch_bounds__(kRedEntries * kRedGroups) k_reduce_partials(
   float* d_verts = d_verts_all + (size_t)blockIdx.y * 3 * V;
   float* dN = dN_all + (size_t)blockIdx.y * 3 * V;
   float tot = extra[i];
+  if (extra64_all) tot = (float)(extra64_all[(size_t)blockIdx.y * 6 * V + i] + (double)tot);
   for (int q = 0; q < kRedGroups; ++q) tot += red[q][j];
   if (i < 3 * V) d_verts[i] = tot;
   else dN[i - 3 * V] = tot;
@@ -1495,6 +1512,7 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.wk.item_cap = ctx->item_cap;
   a.wk.part = ctx->item_part;
   a.wk.extra = ctx->extra;
+  a.wk.extra64 = ctx->extra64;
   a.wk.ctr = ctx->work_ctr;
   a.node_stride = ctx->lim.max_F;
   a.cand_per_chunk = ctx->tune.cand_per_chunk;
@@ -1528,16 +1546,16 @@ int render_grid(int device, int* blocks, int* threads, int* num_sms) {
 
 size_t render_bwd_smem(int V) { return (size_t)6 * V * sizeof(float); }
 
-template <bool STATS, bool BATCH, int S>
+template <bool STATS, int ACC, int S>
 bool set_bwd_smem(int smem) {
-  return cudaFuncSetAttribute(k_shade_bwd<STATS, BATCH, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+  return cudaFuncSetAttribute(k_shade_bwd<STATS, ACC, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
          cudaSuccess;
 }
 
-template <bool STATS, bool BATCH>
+template <bool STATS, int ACC>
 bool set_bwd_smem_all(int smem) {
-  return set_bwd_smem<STATS, BATCH, 1>(smem) && set_bwd_smem<STATS, BATCH, 2>(smem) &&
-         set_bwd_smem<STATS, BATCH, 4>(smem);
+  return set_bwd_smem<STATS, ACC, 1>(smem) && set_bwd_smem<STATS, ACC, 2>(smem) &&
+         set_bwd_smem<STATS, ACC, 4>(smem);
 }
 
 int configure_render_kernels(int max_V) {
@@ -1545,8 +1563,8 @@ int configure_render_kernels(int max_V) {
   // context never lowers the opt-in of a larger one
   (void)max_V;
   const int smem = (int)render_bwd_smem(8192);
-  if (!set_bwd_smem_all<true, false>(smem) || !set_bwd_smem_all<false, false>(smem) ||
-      !set_bwd_smem_all<true, true>(smem) || !set_bwd_smem_all<false, true>(smem)) {
+  if (!set_bwd_smem_all<true, kAccPartials>(smem) || !set_bwd_smem_all<false, kAccPartials>(smem) ||
+      !set_bwd_smem_all<true, kAccFlush>(smem) || !set_bwd_smem_all<false, kAccFlush>(smem)) {
     cudaGetLastError();
     return HR_ERR_CUDA;
   }
@@ -1643,12 +1661,20 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     tm.end(kTimeBwdGather);
   }
   if (interior) {
-    const size_t smem = render_bwd_smem(V);   // within the opt-in of configure_render_kernels
+    // shared-memory sums up to the opt-in of configure_render_kernels (V <= 8192),
+    // global float64 atomics beyond
+    const bool global_acc = render_bwd_smem(V) > render_bwd_smem(8192);
+    if (global_acc && (!ctx->extra64 ||
+                       cudaMemsetAsync(ctx->extra64, 0, sizeof(double) * 6 * V * ni, s) != cudaSuccess))
+      return ctx->extra64 ? HR_ERR_CUDA : HR_ERR_UNSUPPORTED;
+    const size_t smem = global_acc ? 0 : render_bwd_smem(V);
+    const int acc = global_acc ? kAccGlobal : (batch ? kAccFlush : kAccPartials);
     const int S = ctx->tune.rays_per_lane;
-#define HR_BWD_KERNEL(B_) \
-  (st ? (S == 1 ? k_shade_bwd<true, B_, 1> : (S == 2 ? k_shade_bwd<true, B_, 2> : k_shade_bwd<true, B_, 4>)) \
-      : (S == 1 ? k_shade_bwd<false, B_, 1> : (S == 2 ? k_shade_bwd<false, B_, 2> : k_shade_bwd<false, B_, 4>)))
-    auto kern = batch ? HR_BWD_KERNEL(true) : HR_BWD_KERNEL(false);
+#define HR_BWD_KERNEL(A_) \
+  (st ? (S == 1 ? k_shade_bwd<true, A_, 1> : (S == 2 ? k_shade_bwd<true, A_, 2> : k_shade_bwd<true, A_, 4>)) \
+      : (S == 1 ? k_shade_bwd<false, A_, 1> : (S == 2 ? k_shade_bwd<false, A_, 2> : k_shade_bwd<false, A_, 4>)))
+    auto kern = acc == kAccGlobal ? HR_BWD_KERNEL(kAccGlobal)
+                                  : (acc == kAccFlush ? HR_BWD_KERNEL(kAccFlush) : HR_BWD_KERNEL(kAccPartials));
 #undef HR_BWD_KERNEL
     // the block partials are sized for kBlocksPerSm blocks per SM
     const int blocks = ctx->num_sms * ctx->tune.bwd_blocks_per_sm;
@@ -1658,7 +1684,8 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     tm.end(kTimeBwdShade);
     tm.begin(kTimeBwdReduce);
     k_reduce_partials<<<dim3((6 * V + kRedEntries - 1) / kRedEntries, ni), kRedEntries * kRedGroups, 0, s>>>(
-        ctx->partials, ctx->extra, batch ? 0 : blocks, V, d_verts, ctx->dN);
+        ctx->partials, ctx->extra, acc == kAccGlobal ? ctx->extra64 : nullptr, acc == kAccPartials ? blocks : 0, V,
+        d_verts, ctx->dN);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdReduce);
   } else {

@@ -85,6 +85,13 @@ def batch_configs(n: int = 64, seed_base: int = 2000, views=(4, 16), spp=(8, 32)
     return out
 
 
+# Scale workload: the hand Loop-subdivided twice (12,337 vertices, 24,608 triangles),
+# 16 views of 1024 x 1024, 64 spp, 32768 edge samples per view.
+SCALE = SceneConfig("scale-16x1024x1024-64spp", views=16, width=1024, height=1024, spp=64,
+                    edge_samples=32768, elevation_deg=30.0, azimuths_deg=tuple(22.5 * k for k in range(16)),
+                    seed=4000)
+
+
 # ----------------------------------------------------------------------------------
 # Procedural hand mesh
 # ----------------------------------------------------------------------------------
@@ -497,3 +504,80 @@ LIGHT_RGB = (1.0, 1.0, 1.0)
 K_AMBIENT = 0.4
 K_DIFFUSE = 0.6
 EDGE_EPS_PX = 1e-3
+
+
+# ----------------------------------------------------------------------------------
+# Loop subdivision (the scale workload's finer hand)
+# ----------------------------------------------------------------------------------
+
+def loop_subdivision_matrix(faces, n_verts):
+    """Sparse linear map (rows of (index, weight) per new vertex) of one Loop
+    subdivision step, and the new faces.  New vertex i < n_verts is the even (old)
+    vertex: interior (1 - n b) v + b sum(neighbours), b = (5/8 - (3/8 + cos(2 pi / n)
+    / 4)^2) / n (Loop 1987); boundary 3/4 v + 1/8 (its two boundary neighbours).  New
+    vertex n_verts + e is the odd vertex on edge e = (a, b): interior 3/8 (a + b) +
+    1/8 (c + d) with c, d opposite the edge; boundary (a + b) / 2.  Each face splits
+    into four with the orientation kept."""
+    faces = np.asarray(faces, np.int64)
+    edges, edge_faces, _, _ = mesh_topology(faces, n_verts)
+    eidx = {(int(a), int(b)): i for i, (a, b) in enumerate(edges)}
+    nbrs = [set() for _ in range(n_verts)]
+    bnd_nbrs = [[] for _ in range(n_verts)]
+    for i, (a, b) in enumerate(edges):
+        a, b = int(a), int(b)
+        nbrs[a].add(b)
+        nbrs[b].add(a)
+        if edge_faces[i, 1] < 0:
+            bnd_nbrs[a].append(b)
+            bnd_nbrs[b].append(a)
+    rows = []
+    for v in range(n_verts):
+        if bnd_nbrs[v]:
+            b1, b2 = bnd_nbrs[v][:2]
+            rows.append([(v, 0.75), (b1, 0.125), (b2, 0.125)])
+        else:
+            n = len(nbrs[v])
+            beta = (5.0 / 8.0 - (3.0 / 8.0 + 0.25 * np.cos(2.0 * np.pi / n)) ** 2) / n
+            rows.append([(v, 1.0 - n * beta)] + [(u, beta) for u in sorted(nbrs[v])])
+    for i, (a, b) in enumerate(edges):
+        a, b = int(a), int(b)
+        if edge_faces[i, 1] < 0:
+            rows.append([(a, 0.5), (b, 0.5)])
+            continue
+        opp = []
+        for fi in edge_faces[i]:
+            f = faces[fi]
+            opp.append(int([x for x in f if x != a and x != b][0]))
+        rows.append([(a, 0.375), (b, 0.375), (opp[0], 0.125), (opp[1], 0.125)])
+    new_faces = []
+    for f in faces:
+        a, b, c = (int(x) for x in f)
+        ab = n_verts + eidx[(min(a, b), max(a, b))]
+        bc = n_verts + eidx[(min(b, c), max(b, c))]
+        ca = n_verts + eidx[(min(c, a), max(c, a))]
+        new_faces += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]
+    return rows, np.asarray(new_faces, np.int32)
+
+
+def _apply_rows(rows, x):
+    x = np.asarray(x, np.float64)
+    out = np.zeros((len(rows),) + x.shape[1:])
+    for i, r in enumerate(rows):
+        for j, w in r:
+            out[i] += w * x[j]
+    return out
+
+
+def subdivide_hand(hand: HandModel, levels: int = 2) -> HandModel:
+    """The hand after `levels` Loop subdivisions: positions, shape blendshapes, skin
+    weights and albedo all follow the same (affine, rows summing to one) linear map;
+    the skeleton and joint regressor are unchanged."""
+    v, sd, w, alb, faces = hand.v_template, hand.shapedirs, hand.weights, hand.albedo, hand.faces
+    for _ in range(levels):
+        rows, faces = loop_subdivision_matrix(faces, v.shape[0])
+        v, sd, w, alb = (_apply_rows(rows, a) for a in (v, sd, w, alb))
+    edges, edge_faces, vf_off, vf = mesh_topology(faces, v.shape[0])
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)
+    return HandModel(v_template=f32(v), shapedirs=f32(sd), weights=f32(w), j_template=hand.j_template,
+                     j_shapedirs=hand.j_shapedirs, parents=hand.parents, faces=np.ascontiguousarray(faces, np.int32),
+                     edges=edges, edge_faces=edge_faces, vf_offsets=vf_off, vf_faces=vf, albedo=f32(alb))

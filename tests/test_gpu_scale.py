@@ -1,0 +1,113 @@
+"""Parity on the scale workload's mesh: the hand Loop-subdivided twice (12,337
+vertices, 24,608 triangles), beyond the one-block BVH build's shared memory and the
+backward's shared-memory sums, so the multi-block build (bitonic sort with global
+stages, grid hierarchy, global refit) and the global-atomic backward run.  Inputs at a
+size the brute-force oracle finishes in seconds; outputs compared on sampled rows."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_05509_gb300 import inputs as I
+from tests.gpu_common import grad_ok, pixel_ok, require_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def fine_hand():
+    return I.subdivide_hand(I.make_hand(0), 2)
+
+
+@pytest.fixture(scope="module")
+def setup():
+    require_gpu()
+    from paper_2107_05509_gb300 import binding as B
+    h = fine_hand()
+    assert (h.V, h.F) == (12337, 24608)
+    cfg = I.SceneConfig("scale-test", views=2, width=128, height=96, spp=4, edge_samples=2048, elevation_deg=25.0,
+                        azimuths_deg=(30.0, 160.0), seed=4100)
+    cams = I.pack_cameras(I.make_cameras(cfg, h.v_template.mean(0)))
+    for c in cams:
+        c[0:2] *= 2.5
+    x = I.perturb_params(I.gt_params(cfg.seed), cfg.seed).astype(np.float32)
+    verts = oracle.skin(h, x).astype(np.float32)
+    normals = oracle.vertex_normals(verts, h.faces, h.vf_offsets, h.vf_faces)
+    bg = I.background(cfg.seed, cfg.views, cfg.height, cfg.width)
+    o = oracle.make_opts(seed=77, spp=cfg.spp, edge_samples=cfg.edge_samples, ka=I.K_AMBIENT, kd=I.K_DIFFUSE,
+                         light_dir=I.LIGHT_DIR, light_rgb=I.LIGHT_RGB, edge_eps=I.EDGE_EPS_PX)
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, cfg.views, cfg.width, cfg.height)
+    return B, h, cfg, cams, x, verts, normals, bg, o, model, ctx
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _go(B, o, flags=0):
+    return B.render_opts(seed=o.seed_lo | (o.seed_hi << 32), iter=o.iter, spp=o.spp, edge_samples=o.edge_samples,
+                         ka=o.ka, kd=o.kd, light_dir=tuple(o.light_dir), light_rgb=tuple(o.light_rgb),
+                         edge_eps_px=o.edge_eps, flags=flags)
+
+
+def test_scale_skin_build_trace(setup):
+    B, h, cfg, cams, x, verts, normals, bg, o, model, ctx = setup
+    v = torch.empty((h.V, 3), device="cuda")
+    B.hr_skin(ctx, model, _t(x), v)
+    assert np.abs(v.cpu().numpy() - oracle.skin(h, x)).max() < 2e-6
+    vt = _t(verts)
+    B.hr_build_bvh(ctx, model, vt)
+    n = torch.empty((h.V, 3), device="cuda")
+    B.hr_get_normals(ctx, n)
+    assert np.array_equal(n.cpu().numpy(), normals)
+    rng = np.random.default_rng(5)
+    nray = 3000
+    cam = cams[rng.integers(0, cfg.views, nray)]
+    orig = cam[:, 16:19].copy()
+    d = (verts[rng.integers(0, h.V, nray)] + rng.normal(0, 0.002, (nray, 3)) - orig).astype(np.float32)
+    tri = torch.empty(nray, dtype=torch.int32, device="cuda")
+    tuv = torch.empty((nray, 3), device="cuda")
+    rtri, rtuv = oracle.closest_hits(orig, d, verts, h.faces)
+    B.hr_trace(ctx, _t(orig), _t(d), tri, tuv)
+    assert (rtri >= 0).mean() > 0.3
+    assert np.array_equal(tri.cpu().numpy(), rtri)
+    # a refit of this topology over another pose traces the same as a rebuild
+    v2 = oracle.skin(h, I.gt_params(cfg.seed)).astype(np.float32)
+    d2 = (v2[rng.integers(0, h.V, nray)] - orig).astype(np.float32)
+    counter = torch.full((1,), 5, dtype=torch.int32, device="cuda")
+    B.hr_update_bvh(ctx, model, _t(v2), counter, 8)
+    B.hr_trace(ctx, _t(orig), _t(d2), tri, tuv)
+    rtri2, _ = oracle.closest_hits(orig, d2, v2, h.faces)
+    assert np.array_equal(tri.cpu().numpy(), rtri2)
+    assert B.hr_get_status(ctx) == B.HR_OK
+
+
+def test_scale_render_forward_backward(setup):
+    B, h, cfg, cams, x, verts, normals, bg, o, model, ctx = setup
+    N, H, W = cfg.views, cfg.height, cfg.width
+    vt, ct, bt = _t(verts), _t(cams), _t(bg)
+    B.hr_build_bvh(ctx, model, vt)
+    img = torch.empty((N, H, W, 3), device="cuda")
+    B.hr_render_fwd(ctx, model, vt, ct, H, W, bt, _go(B, o), img)
+    g = img.cpu().numpy()
+    for v in range(N):
+        for r in (H // 3, H // 2, (2 * H) // 3):
+            ref = oracle.render_fwd(verts, h.faces, normals, h.albedo, cams, H, W, bg, o,
+                                    rows=(v * H + r, v * H + r + 1))
+            ok = pixel_ok(g[v, r], ref[v, r])
+            assert ok.all(), (v, r, np.argwhere(~ok)[:5])
+    # gradient of an adjoint on every 6th row: interior (global-atomic sums), edges,
+    # normal adjoint, with and without the forward's candidate lists
+    rng = np.random.default_rng(6)
+    A = np.zeros((N, H, W, 3), np.float32)
+    A[:, ::6] = rng.choice([-1.0, 1.0], size=A[:, ::6].shape).astype(np.float32) * 1e-5
+    ref, _ = oracle.render_bwd(h, verts, cams, H, W, bg, o, A, normals=normals)
+    dv = torch.empty((h.V, 3), device="cuda")
+    for flags in (0, B.HR_BWD_REUSE_FWD):
+        B.hr_render_bwd(ctx, model, vt, ct, H, W, bt, _go(B, o, flags), _t(A), dv)
+        gg = dv.cpu().numpy()
+        ok = grad_ok(gg, ref)
+        assert ok.all(), (flags, np.argwhere(~ok)[:5], gg[~ok][:5], ref[~ok][:5])
+    assert B.hr_get_status(ctx) == B.HR_OK

@@ -43,3 +43,27 @@ def test_camera_rig_looks_at_hand():
         P = R @ target + c[13:16]
         assert abs(P[0]) < 1e-6 and abs(P[1]) < 1e-6 and abs(P[2] - 0.6) < 1e-6
         assert np.allclose(-R.T @ c[13:16], c[16:19], atol=1e-6)
+
+
+def test_loop_subdivision_of_the_hand():
+    """Two Loop subdivisions: V + E new vertices per level (778 -> 3093 -> 12337), four
+    faces per face, the one wrist loop kept (16 -> 64 boundary edges), Euler
+    characteristic unchanged, orientation consistent (every interior edge traversed once
+    each way), skin weights still a partition of unity, the surface inside the coarse
+    mesh's bounding box (Loop's rules are convex combinations)."""
+    h = I.make_hand(0)
+    s = I.subdivide_hand(h, 2)
+    assert (s.V, s.F) == (12337, 24608)
+    assert int((s.edge_faces[:, 1] < 0).sum()) == 64
+    assert s.V - s.E + s.F == h.V - h.E + h.F
+    directed = {}
+    for f in s.faces:
+        for k in range(3):
+            e = (int(f[k]), int(f[(k + 1) % 3]))
+            assert e not in directed
+            directed[e] = True
+    interior = sum(1 for (a, b) in directed if (b, a) in directed) // 2
+    assert interior == int((s.edge_faces[:, 1] >= 0).sum())
+    assert np.abs(s.weights.sum(1) - 1.0).max() < 1e-5
+    lo, hi = h.v_template.min(0), h.v_template.max(0)
+    assert (s.v_template >= lo - 1e-6).all() and (s.v_template <= hi + 1e-6).all()
