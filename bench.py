@@ -379,6 +379,7 @@ def run_handrt(args):
     if not args.no_refine and world == 1:
         line["refinement"] = run_refinement(args, dev)
         line["tensor"] = run_tensor(dev)
+        line["scale"] = run_scale(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_seconds)
     if dist:
@@ -575,6 +576,66 @@ def run_refinement(args, dev):
                          "(plain: every instance refined that many iterations, one after another); "
                          "time_to_each_1mm: until every instance has been <= 1 mm (plain: per-instance "
                          "stopping), iteration cap counted for instances that never get there"}
+
+
+def run_scale(dev, iters=10):
+    """The scale workload: the hand Loop-subdivided twice (12,337 vertices, 24,608
+    triangles; multi-block BVH build, float64-atomic backward sums), 16 views of
+    1024 x 1024, 64 spp, 32768 edge samples per view.  One refinement iteration
+    (skinning, BVH update, forward, loss, backward, skinning adjoint, Adam) captured as
+    a CUDA graph, replayed `iters` times; inputs (1.2 GB of images) exceed L2."""
+    import torch
+
+    from paper_2107_05509_gb300 import binding as B
+    from paper_2107_05509_gb300 import inputs as I
+    from paper_2107_05509_gb300 import pipeline as P
+
+    cfg = I.SCALE
+    hand = I.subdivide_hand(I.make_hand(0), 2)
+    model = B.Model(hand, device=dev)
+    x_gt = I.gt_params(cfg.seed)
+    ctx = B.Context(hand.V, hand.F, hand.E, cfg.views, cfg.width, cfg.height)
+    views, _ = P.make_views(cfg, model, x_gt, device=dev, ctx=ctx)
+    ref = torch.empty((hand.V, 3), device=dev)
+    B.hr_skin(ctx, model, torch.as_tensor(x_gt, device=dev), ref)
+    pr = P.PlainRefiner(model, views, cfg, ctx=ctx, ref_verts=ref, max_iters=iters + 8, device=dev)
+    x0 = torch.as_tensor(I.perturb_params(x_gt, cfg.seed), device=dev)
+    pr.reset(x0)
+    tuning, t0, t1 = P.autotune(ctx, pr.render_pass,
+                                P.workload_key(model, [(cfg.views, cfg.width, cfg.height, cfg.spp,
+                                                        cfg.edge_samples)]), cache=False)
+    pr.r.opts.flags = B.HR_STATS | B.HR_BWD_REUSE_FWD
+    pr.render_pass()
+    stats = B.hr_get_stats(ctx).astype(np.float64)
+    pr.r.opts.flags = B.HR_BWD_REUSE_FWD
+    rays = float(stats[:, S_SAMPLES].sum())
+    pr.reset(x0)
+    g = pr.capture()
+    pr.reset(x0)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
+    for a, b in ev:
+        a.record()
+        g.replay()
+        b.record()
+    torch.cuda.synchronize()
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    pr.r.opts.flags = B.HR_TIMING | B.HR_BWD_REUSE_FWD
+    pr.render_pass()
+    kt = B.hr_kernel_times(ctx)
+    pr.r.opts.flags = B.HR_BWD_REUSE_FWD
+    status = B.hr_get_status(ctx)
+    if status != B.HR_OK:
+        raise RuntimeError(f"scale device status {B.status_string(status)}")
+    err = pr.err[:iters + 2, 0].cpu().numpy() * 1e3
+    ctx.close()
+    return {"workload": cfg.name, "vertices": hand.V, "triangles": hand.F, "views": cfg.views,
+            "width": cfg.width, "height": cfg.height, "spp": cfg.spp, "edge_samples_per_view": cfg.edge_samples,
+            "ms_per_iter": round(ms, 3), "rays_per_iter": int(rays), "value": round(rays / (ms * 1e-3) / 1e6, 1),
+            "unit": UNIT, "kernel_ms": {k: round(v, 4) for k, v in kt.items() if v >= 0}, "tuning": tuning,
+            "eps_v_mm_first_iters": [round(float(e), 3) for e in err[:4]]}
 
 
 def run_tensor(dev, steps=20):
