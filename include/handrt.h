@@ -80,6 +80,8 @@ typedef struct hr_model {
     const int32_t* vf_offsets; /* [V+1] vertex -> incident faces, CSR offsets       */
     const int32_t* vf_faces;   /* [3F]  incident faces, ascending per vertex        */
     const float* albedo;       /* [V][3] per-vertex RGB albedo                      */
+    const float* uv;           /* [V][2] texture coordinates in [0, 1]^2, or NULL;
+                                  used when the render options give a texture        */
 } hr_model;
 
 /* Allocation-free variant of hr_skin_bwd (the paper has no counterpart: it is an
@@ -119,6 +121,16 @@ typedef struct hr_render_opts {
     uint32_t flags;         /* HR_BWD_* bits; 0 = every term                        */
     const uint32_t* iter_dev; /* optional device counter read instead of `iter` (so a
                                  captured iteration replays with fresh samples); NULL = use iter */
+    /* Albedo texture (optional; needs model->uv).  When given, the albedo of a hit is
+     * the bilinear lookup of `texture` (device float[tex_h][tex_w][3], texel (i, j)
+     * centred at ((i + 0.5) / tex_w, (j + 0.5) / tex_h), clamp-to-edge) at the
+     * interpolated uv, instead of the interpolated per-vertex albedo.  The texel
+     * coordinates x = uv_x tex_w - 0.5, y = uv_y tex_h - 0.5 and their floors are
+     * float32 decisions.  hr_render_bwd adds dL/dtexture into d_texture (device
+     * float[tex_h][tex_w][3], accumulated: the caller clears it) when it is not NULL. */
+    const float* texture;
+    int32_t tex_w, tex_h;
+    float* d_texture;
 } hr_render_opts;
 
 #define HR_BWD_NO_INTERIOR 1u  /* hr_render_bwd: skip the interior term            */

@@ -40,7 +40,7 @@ def lib():
         L.oracle_silhouettes.argtypes = [P, P, P, P, i, P, P]
         L.oracle_silhouettes.restype = i
         L.oracle_render_fwd.argtypes = [P, i, P, i, P, P, P, i, i, i, P, P, P, i, i, i, i, i]
-        L.oracle_render_bwd_interior.argtypes = [P, i, P, i, P, P, P, i, i, i, P, P, P, P, P, i, i, i, i, i]
+        L.oracle_render_bwd_interior.argtypes = [P, i, P, i, P, P, P, i, i, i, P, P, P, P, P, P, i, i, i, i, i]
         L.oracle_render_bwd_edges.argtypes = [P, i, P, i, P, P, P, i, i, i, P, P, P, P, P, P, i, P, i, i]
         _lib = L
     return _lib
@@ -82,12 +82,22 @@ class Opts(ctypes.Structure):
     _fields_ = [("seed_lo", ctypes.c_uint32), ("seed_hi", ctypes.c_uint32), ("iter", ctypes.c_uint32),
                 ("instance", ctypes.c_uint32), ("spp", ctypes.c_int32), ("edge_samples", ctypes.c_int32),
                 ("ka", ctypes.c_float), ("kd", ctypes.c_float), ("light_dir", ctypes.c_float * 3),
-                ("light_rgb", ctypes.c_float * 3), ("edge_eps", ctypes.c_float)]
+                ("light_rgb", ctypes.c_float * 3), ("edge_eps", ctypes.c_float),
+                ("texture", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("tex_w", ctypes.c_int32),
+                ("tex_h", ctypes.c_int32)]
 
 
 def make_opts(seed=0, iter=0, instance=0, spp=4, edge_samples=1024, ka=0.4, kd=0.6,
-              light_dir=(0.0, 0.0, 1.0), light_rgb=(1.0, 1.0, 1.0), edge_eps=1e-3):
+              light_dir=(0.0, 0.0, 1.0), light_rgb=(1.0, 1.0, 1.0), edge_eps=1e-3, texture=None, uv=None):
+    """Render options; with `texture` ([H][W][3]) and `uv` ([V][2]) the albedo is the
+    bilinear texture lookup at the hit's interpolated uv."""
     o = Opts()
+    if texture is not None:
+        o._tex = np.ascontiguousarray(texture, np.float32)
+        o._uv = np.ascontiguousarray(uv, np.float32)
+        o.texture = o._tex.ctypes.data
+        o.uv = o._uv.ctypes.data
+        o.tex_h, o.tex_w = o._tex.shape[0], o._tex.shape[1]
     o.seed_lo = seed & 0xFFFFFFFF
     o.seed_hi = (seed >> 32) & 0xFFFFFFFF
     o.iter = iter
@@ -152,7 +162,9 @@ def render_fwd(verts, faces, normals, albedo, cams, H, W, background, opts, thre
 
 
 def render_bwd_interior(verts, faces, normals, albedo, cams, H, W, background, opts, adjoint,
-                        threads=None, rows=None, cols=None):
+                        threads=None, rows=None, cols=None, d_texture=None):
+    """(dV, dN); with a texture in `opts`, dL/dtexture is added into d_texture
+    (float64 [H_t][W_t][3]) when given."""
     v, f, n, a = _f32(verts), _i32(faces), _f32(normals), _f32(albedo)
     cams = _f32(cams)
     N = cams.shape[0]
@@ -161,8 +173,12 @@ def render_bwd_interior(verts, faces, normals, albedo, cams, H, W, background, o
     dN = np.zeros((v.shape[0], 3), np.float64)
     r0, r1 = rows if rows else (0, N * H)
     c0, c1 = cols if cols else (0, W)
+    dT = d_texture if d_texture is not None else None
+    if dT is not None:
+        assert dT.dtype == np.float64 and dT.flags.c_contiguous
     lib().oracle_render_bwd_interior(_p(v), v.shape[0], _p(f), f.shape[0], _p(n), _p(a), _p(cams), N, H, W,
                                      _p(bg), ctypes.byref(opts), _p(A), _p(dV), _p(dN),
+                                     None if dT is None else dT.ctypes.data_as(ctypes.c_void_p),
                                      threads or n_threads(), r0, r1, c0, c1)
     return dV, dN
 
@@ -220,12 +236,13 @@ def normal_adjoint(verts, faces, dN):
     return dV
 
 
-def render_bwd(hand, verts, cams, H, W, background, opts, adjoint, normals=None, threads=None):
-    """Full dL/dverts = interior + edge sampling + normal adjoint (float64)."""
+def render_bwd(hand, verts, cams, H, W, background, opts, adjoint, normals=None, threads=None, d_texture=None):
+    """Full dL/dverts = interior + edge sampling + normal adjoint (float64); with a
+    texture, dL/dtexture (interior only: the texture moves no edge) into d_texture."""
     if normals is None:
         normals = vertex_normals(verts, hand.faces, hand.vf_offsets, hand.vf_faces)
     dVi, dN = render_bwd_interior(verts, hand.faces, normals, hand.albedo, cams, H, W, background, opts,
-                                  adjoint, threads=threads)
+                                  adjoint, threads=threads, d_texture=d_texture)
     sl, sc = silhouette_lists(verts, hand.faces, hand.edges, hand.edge_faces, cams)
     dVe = render_bwd_edges(verts, hand.faces, normals, hand.albedo, cams, H, W, background, opts, adjoint,
                            hand.edges, sl, sc)

@@ -180,7 +180,43 @@ typedef struct {
     uint32_t seed_lo, seed_hi, iter, instance;
     int32_t spp, edge_samples;
     float ka, kd, light_dir[3], light_rgb[3], edge_eps;
+    const float* texture;     /* [tex_h][tex_w][3] albedo texture, or NULL: per-vertex albedo */
+    const float* uv;          /* [V][2] texture coordinates */
+    int32_t tex_w, tex_h;
 } opts_t;
+
+/* Bilinear albedo texture at the hit's interpolated uv: texel (i, j) is centred at
+ * ((i + 0.5) / W, (j + 0.5) / H), addressing clamps to the edge.  The interpolated uv
+ * and the texel coordinates x = uv_x W - 0.5, y = uv_y H - 0.5 (whose floors pick the
+ * texels) are float32 decisions; the weights are the fractional parts. */
+typedef struct { int i0, i1, j0, j1; double fx, fy; } texs_t;
+
+static int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+static texs_t tex_coords(const opts_t* o, const int32_t* f, float u, float v) {
+    float w = (1.0f - u) - v;
+    const float *t0 = o->uv + 2 * f[0], *t1 = o->uv + 2 * f[1], *t2 = o->uv + 2 * f[2];
+    float ux = fmaf(v, t2[0], fmaf(u, t1[0], w * t0[0]));
+    float uy = fmaf(v, t2[1], fmaf(u, t1[1], w * t0[1]));
+    float x = fmaf(ux, (float)o->tex_w, -0.5f), y = fmaf(uy, (float)o->tex_h, -0.5f);
+    float xf = floorf(x), yf = floorf(y);
+    texs_t ts;
+    ts.fx = (double)(x - xf);
+    ts.fy = (double)(y - yf);
+    int xi = (int)fminf(fmaxf(xf, -1.0f), (float)o->tex_w), yi = (int)fminf(fmaxf(yf, -1.0f), (float)o->tex_h);
+    ts.i0 = clampi(xi, 0, o->tex_w - 1);
+    ts.i1 = clampi(xi + 1, 0, o->tex_w - 1);
+    ts.j0 = clampi(yi, 0, o->tex_h - 1);
+    ts.j1 = clampi(yi + 1, 0, o->tex_h - 1);
+    return ts;
+}
+
+static double texel(const opts_t* o, int i, int j, int c) { return o->texture[((size_t)j * o->tex_w + i) * 3 + c]; }
+
+static double tex_albedo(const opts_t* o, const texs_t* ts, int c) {
+    return (1.0 - ts->fy) * ((1.0 - ts->fx) * texel(o, ts->i0, ts->j0, c) + ts->fx * texel(o, ts->i1, ts->j0, c)) +
+           ts->fy * ((1.0 - ts->fx) * texel(o, ts->i0, ts->j1, c) + ts->fx * texel(o, ts->i1, ts->j1, c));
+}
 
 typedef struct {
     const float* verts; int V;
@@ -215,8 +251,10 @@ static void shade(const scene_t* sc, const hit_t* h, double rgb[3]) {
         }
         sigma = ndl / sqrt(len2);
     }
+    texs_t ts;
+    if (sc->o->texture) ts = tex_coords(sc->o, f, h->u, h->v);
     for (int c = 0; c < 3; ++c) {
-        double alb = w * a0[c] + u * a1[c] + v * a2[c];
+        double alb = sc->o->texture ? tex_albedo(sc->o, &ts, c) : w * a0[c] + u * a1[c] + v * a2[c];
         rgb[c] = alb * (double)sc->o->light_rgb[c] * ((double)sc->o->ka + (double)sc->o->kd * sigma);
     }
 }
@@ -264,7 +302,7 @@ static double dot_d(const double a[3], const double b[3]) { return a[0] * b[0] +
  * to dN.  Barycentrics of the hit: (1-u-v) v0 + u v1 + v v2 = o + t d, with
  * e1 = v1 - v0, e2 = v2 - v0 and [a,b,c] = a.(b x c). */
 static void interior_grad(const scene_t* sc, const hit_t* h, f3 o32, f3 d32, const double g[3],
-                          double* dV, double* dN) {
+                          double* dV, double* dN, double* dT) {
     const int32_t* f = sc->faces + 3 * h->tri;
     const float* P[3] = {sc->verts + 3 * f[0], sc->verts + 3 * f[1], sc->verts + 3 * f[2]};
     const float *n0 = sc->normals + 3 * f[0], *n1 = sc->normals + 3 * f[1], *n2 = sc->normals + 3 * f[2];
@@ -288,10 +326,12 @@ static void interior_grad(const scene_t* sc, const hit_t* h, f3 o32, f3 d32, con
     for (int c = 0; c < 3; ++c) { nh[c] = nm[c] / len; ndl += nh[c] * op->light_dir[c]; }
     double sigma = lit ? ndl : 0.0;
 
-    /* dL/dalbedo_interp (per channel) and dL/dsigma */
+    /* dL/dalbedo (per channel) and dL/dsigma */
+    texs_t ts;
+    if (op->texture) ts = tex_coords(op, f, h->u, h->v);
     double dalb[3], dsig = 0.0;
     for (int c = 0; c < 3; ++c) {
-        double alb = w * a0[c] + u * a1[c] + v * a2[c];
+        double alb = op->texture ? tex_albedo(op, &ts, c) : w * a0[c] + u * a1[c] + v * a2[c];
         dalb[c] = g[c] * op->light_rgb[c] * (op->ka + op->kd * sigma);
         dsig += g[c] * alb * op->light_rgb[c] * op->kd;
     }
@@ -303,9 +343,31 @@ static void interior_grad(const scene_t* sc, const hit_t* h, f3 o32, f3 d32, con
         for (int c = 0; c < 3; ++c) dnm[c] = (dnh[c] - nh[c] * proj) / len;
     }
     double gu = 0.0, gv = 0.0;
+    if (op->texture) {
+        /* albedo = bilinear(T, uv(u, v)): dL/dT at the four texels, and dL/duv through
+         * the texel coordinates (x = uv_x W - 0.5) to (u, v) */
+        double wt[4] = {(1.0 - ts.fx) * (1.0 - ts.fy), ts.fx * (1.0 - ts.fy), (1.0 - ts.fx) * ts.fy, ts.fx * ts.fy};
+        int ii[4] = {ts.i0, ts.i1, ts.i0, ts.i1}, jj[4] = {ts.j0, ts.j0, ts.j1, ts.j1};
+        double dax = 0.0, day = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            for (int q = 0; q < 4; ++q) if (dT) dT[((size_t)jj[q] * op->tex_w + ii[q]) * 3 + c] += wt[q] * dalb[c];
+            dax += dalb[c] * ((1.0 - ts.fy) * (texel(op, ts.i1, ts.j0, c) - texel(op, ts.i0, ts.j0, c)) +
+                              ts.fy * (texel(op, ts.i1, ts.j1, c) - texel(op, ts.i0, ts.j1, c)));
+            day += dalb[c] * ((1.0 - ts.fx) * (texel(op, ts.i0, ts.j1, c) - texel(op, ts.i0, ts.j0, c)) +
+                              ts.fx * (texel(op, ts.i1, ts.j1, c) - texel(op, ts.i1, ts.j0, c)));
+        }
+        double dux = dax * op->tex_w, duy = day * op->tex_h;
+        const float *q0 = op->uv + 2 * f[0], *q1 = op->uv + 2 * f[1], *q2 = op->uv + 2 * f[2];
+        gu += dux * ((double)q1[0] - q0[0]) + duy * ((double)q1[1] - q0[1]);
+        gv += dux * ((double)q2[0] - q0[0]) + duy * ((double)q2[1] - q0[1]);
+    }
     for (int c = 0; c < 3; ++c) {
-        gu += dalb[c] * ((double)a1[c] - a0[c]) + dnm[c] * ((double)n1[c] - n0[c]);
-        gv += dalb[c] * ((double)a2[c] - a0[c]) + dnm[c] * ((double)n2[c] - n0[c]);
+        if (!op->texture) {
+            gu += dalb[c] * ((double)a1[c] - a0[c]);
+            gv += dalb[c] * ((double)a2[c] - a0[c]);
+        }
+        gu += dnm[c] * ((double)n1[c] - n0[c]);
+        gv += dnm[c] * ((double)n2[c] - n0[c]);
         dN[3 * f[0] + c] += w * dnm[c];
         dN[3 * f[1] + c] += u * dnm[c];
         dN[3 * f[2] + c] += v * dnm[c];
@@ -347,6 +409,7 @@ typedef struct {
     double* image;             /* forward output [N][H][W][3] (NULL in backward) */
     const float* adjoint;      /* backward input [N][H][W][3] */
     double* dV; double* dN;    /* private accumulators [V][3] */
+    double* dT;                /* private texture accumulator [tex_h][tex_w][3] or NULL */
     int col0, col1;            /* column range */
 } job_t;
 
@@ -390,7 +453,7 @@ static void* bwd_worker(void* arg) {
                 f3 d;
                 primary_dir(cam, (float)px + u1, (float)py + u2, &d);
                 hit_t h = closest_hit(o, d, sc->verts, sc->faces, sc->F);
-                if (h.tri >= 0) interior_grad(sc, &h, o, d, g, j->dV, j->dN);
+                if (h.tri >= 0) interior_grad(sc, &h, o, d, g, j->dV, j->dN, j->dT);
             }
         }
     }
@@ -398,13 +461,14 @@ static void* bwd_worker(void* arg) {
 }
 
 static void run_jobs(const scene_t* sc, int nthreads, int row0, int row1, int col0, int col1, double* image,
-                     const float* adjoint, double* dV, double* dN, void* (*fn)(void*)) {
+                     const float* adjoint, double* dV, double* dN, double* dT, void* (*fn)(void*)) {
     if (nthreads < 1) nthreads = 1;
     int rows = row1 - row0;
     if (nthreads > rows) nthreads = rows > 0 ? rows : 1;
     pthread_t* th = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
     job_t* jobs = (job_t*)calloc((size_t)nthreads, sizeof(job_t));
     size_t nv = (size_t)sc->V * 3;
+    size_t nt = dT ? (size_t)sc->o->tex_w * sc->o->tex_h * 3 : 0;
     for (int t = 0; t < nthreads; ++t) {
         jobs[t].sc = sc;
         jobs[t].item0 = row0 + (int)((long)rows * t / nthreads);
@@ -416,6 +480,7 @@ static void run_jobs(const scene_t* sc, int nthreads, int row0, int row1, int co
             jobs[t].dV = (double*)calloc(nv, sizeof(double));
             jobs[t].dN = (double*)calloc(nv, sizeof(double));
         }
+        if (nt) jobs[t].dT = (double*)calloc(nt, sizeof(double));
         pthread_create(&th[t], NULL, fn, &jobs[t]);
     }
     for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
@@ -424,6 +489,10 @@ static void run_jobs(const scene_t* sc, int nthreads, int row0, int row1, int co
             for (size_t i = 0; i < nv; ++i) { dV[i] += jobs[t].dV[i]; dN[i] += jobs[t].dN[i]; }
             free(jobs[t].dV); free(jobs[t].dN);
         }
+    }
+    for (int t = 0; t < nthreads && nt; ++t) {
+        for (size_t i = 0; i < nt; ++i) dT[i] += jobs[t].dT[i];
+        free(jobs[t].dT);
     }
     free(th); free(jobs);
 }
@@ -442,18 +511,19 @@ void oracle_render_fwd(const float* verts, int V, const int32_t* faces, int F, c
                        const opts_t* o, double* image, int nthreads, int row0, int row1, int col0, int col1) {
     scene_t sc;
     make_scene(&sc, verts, V, faces, F, normals, albedo, cams, N, H, W, background, o);
-    run_jobs(&sc, nthreads, row0, row1, col0, col1, image, NULL, NULL, NULL, fwd_worker);
+    run_jobs(&sc, nthreads, row0, row1, col0, col1, image, NULL, NULL, NULL, NULL, fwd_worker);
 }
 
 /* Interior backward: re-trace the forward's samples and accumulate dL/dV (through
- * the barycentrics) and dL/dN (vertex normals) for adjoint image A = dL/dI. */
+ * the barycentrics), dL/dN (vertex normals) and, with a texture, dL/dtexture (dT, or
+ * NULL) for adjoint image A = dL/dI. */
 void oracle_render_bwd_interior(const float* verts, int V, const int32_t* faces, int F, const float* normals,
                                 const float* albedo, const float* cams, int N, int H, int W,
                                 const float* background, const opts_t* o, const float* adjoint, double* dV,
-                                double* dN, int nthreads, int row0, int row1, int col0, int col1) {
+                                double* dN, double* dT, int nthreads, int row0, int row1, int col0, int col1) {
     scene_t sc;
     make_scene(&sc, verts, V, faces, F, normals, albedo, cams, N, H, W, background, o);
-    run_jobs(&sc, nthreads, row0, row1, col0, col1, NULL, adjoint, dV, dN, bwd_worker);
+    run_jobs(&sc, nthreads, row0, row1, col0, col1, NULL, adjoint, dV, dN, o->texture ? dT : NULL, bwd_worker);
 }
 
 /* project a vertex; returns 0 when it is not in front of the camera */

@@ -55,14 +55,16 @@ class hr_model(ctypes.Structure):
     _fields_ = [("V", ctypes.c_int32), ("F", ctypes.c_int32), ("E", ctypes.c_int32), ("J", ctypes.c_int32),
                 ("K", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in (
                     "v_template", "shapedirs", "weights", "j_template", "j_shapedirs", "parents", "faces", "edges",
-                    "edge_faces", "vf_offsets", "vf_faces", "albedo")]
+                    "edge_faces", "vf_offsets", "vf_faces", "albedo", "uv")]
 
 
 class hr_render_opts(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("iter", ctypes.c_uint32), ("instance", ctypes.c_uint32),
                 ("spp", ctypes.c_int32), ("edge_samples", ctypes.c_int32), ("ka", ctypes.c_float),
                 ("kd", ctypes.c_float), ("light_dir", ctypes.c_float * 3), ("light_rgb", ctypes.c_float * 3),
-                ("edge_eps_px", ctypes.c_float), ("flags", ctypes.c_uint32), ("iter_dev", ctypes.c_void_p)]
+                ("edge_eps_px", ctypes.c_float), ("flags", ctypes.c_uint32), ("iter_dev", ctypes.c_void_p),
+                ("texture", ctypes.c_void_p), ("tex_w", ctypes.c_int32), ("tex_h", ctypes.c_int32),
+                ("d_texture", ctypes.c_void_p)]
 
 
 class hr_instance_desc(ctypes.Structure):
@@ -259,6 +261,8 @@ class Model:
                       j_template=f(hand.j_template), j_shapedirs=f(hand.j_shapedirs), parents=i(hand.parents),
                       faces=i(hand.faces), edges=i(hand.edges), edge_faces=i(hand.edge_faces),
                       vf_offsets=i(hand.vf_offsets), vf_faces=i(hand.vf_faces), albedo=f(hand.albedo))
+        if getattr(hand, "uv", None) is not None:
+            self.t["uv"] = f(hand.uv)
         m = hr_model()
         m.V, m.F, m.E = hand.V, hand.F, hand.E
         m.J, m.K = hand.weights.shape[1], hand.shapedirs.shape[2]
@@ -272,7 +276,10 @@ class Model:
 
 
 def render_opts(seed=0, iter=0, instance=0, spp=4, edge_samples=1024, ka=0.4, kd=0.6, light_dir=(0.0, 0.0, 1.0),
-                light_rgb=(1.0, 1.0, 1.0), edge_eps_px=1e-3, flags=0, iter_dev=None):
+                light_rgb=(1.0, 1.0, 1.0), edge_eps_px=1e-3, flags=0, iter_dev=None, texture=None, d_texture=None):
+    """Render options; texture: device float [H_t][W_t][3] albedo texture (needs the
+    model's uv); d_texture: device float buffer of the same shape that the backward adds
+    dL/dtexture into."""
     o = hr_render_opts()
     o.seed = seed
     o.iter = iter
@@ -285,6 +292,13 @@ def render_opts(seed=0, iter=0, instance=0, spp=4, edge_samples=1024, ka=0.4, kd
     o.edge_eps_px = edge_eps_px
     o.flags = flags
     o.iter_dev = None if iter_dev is None else iter_dev.data_ptr()
+    if texture is not None:
+        assert texture.is_cuda and texture.is_contiguous() and texture.dtype == torch.float32
+        o.texture = texture.data_ptr()
+        o.tex_h, o.tex_w = int(texture.shape[0]), int(texture.shape[1])
+    if d_texture is not None:
+        assert d_texture.is_cuda and d_texture.is_contiguous() and d_texture.dtype == torch.float32
+        o.d_texture = d_texture.data_ptr()
     return o
 
 

@@ -55,6 +55,11 @@ bool model_ok(const hr_model* m, const Context* c) {
          m->edges && m->edge_faces && m->vf_offsets && m->vf_faces && m->albedo;
 }
 
+// a texture needs its size and the model's texture coordinates
+bool tex_ok(const hr_render_opts* o, const hr_model* m) {
+  return !o->texture || (m && m->uv && o->tex_w >= 1 && o->tex_h >= 1 && o->tex_w <= 16384 && o->tex_h <= 16384);
+}
+
 bool opts_ok(const hr_render_opts* o) {
   return o && o->spp >= 1 && o->spp <= 65536 && o->edge_samples >= 0 && o->edge_eps_px > 0.0f;
 }
@@ -310,7 +315,7 @@ int hr_render_fwd(hr_context* ctx, const hr_model* model, const float* verts, co
                   int W, const float* background, const hr_render_opts* opts, float* image, hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || c->vt || !model_ok(model, c) || !verts || !cams || !background || !image || !opts_ok(opts) ||
-      !image_ok(c, N, H, W))
+      !image_ok(c, N, H, W) || !tex_ok(opts, model))
     return HR_ERR_ARG;
   if (c->F != model->F || c->V != model->V) return HR_ERR_ARG;  // hr_build_bvh first
   return hr::launch_render_fwd(c, model, verts, reinterpret_cast<const Cam*>(cams), N, H, W, background, opts, image,
@@ -329,7 +334,7 @@ int hr_render_bwd(hr_context* ctx, const hr_model* model, const float* verts, co
                   hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || c->vt || !model_ok(model, c) || !verts || !cams || !background || !adjoint || !d_verts ||
-      !opts_ok(opts) || !image_ok(c, N, H, W))
+      !opts_ok(opts) || !image_ok(c, N, H, W) || !tex_ok(opts, model))
     return HR_ERR_ARG;
   if (c->F != model->F || c->V != model->V) return HR_ERR_ARG;
   return hr::launch_render_bwd(c, model, verts, reinterpret_cast<const Cam*>(cams), N, H, W, background, opts,
@@ -360,7 +365,7 @@ int hr_render_fwd_batch(hr_context* ctx, const hr_model* model, const float* ver
                         const float* background, const hr_render_opts* opts, float* image, hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || !c->vt || !model_ok(model, c) || !verts || !cams || !background || !image || !opts ||
-      !(opts->edge_eps_px > 0.0f))
+      !(opts->edge_eps_px > 0.0f) || !tex_ok(opts, model))
     return HR_ERR_ARG;
   if (c->F != model->F || c->V != model->V) return HR_ERR_ARG;  // hr_build_bvh_batch first
   return hr::launch_render_fwd(c, model, verts, reinterpret_cast<const Cam*>(cams), 0, 0, 0, background, opts,
@@ -379,7 +384,7 @@ int hr_render_bwd_batch(hr_context* ctx, const hr_model* model, const float* ver
                         hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || !c->vt || !model_ok(model, c) || !verts || !cams || !background || !adjoint || !d_verts || !opts ||
-      !(opts->edge_eps_px > 0.0f))
+      !(opts->edge_eps_px > 0.0f) || !tex_ok(opts, model))
     return HR_ERR_ARG;
   if (c->F != model->F || c->V != model->V) return HR_ERR_ARG;
   return hr::launch_render_bwd(c, model, verts, reinterpret_cast<const Cam*>(cams), 0, 0, 0, background, opts,

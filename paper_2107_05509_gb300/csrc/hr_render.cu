@@ -219,6 +219,10 @@ struct RenderArgs {
   int n_inst, nviews, total_st;
   int node_stride;
   int cand_per_chunk, max_chunks;   // work-item split (tuning)
+  const float* uv;        // [V][2] texture coordinates (shared by all instances)
+  const float* tex;       // [tex_h][tex_w][3] albedo texture, or null: per-vertex albedo
+  int tex_w, tex_h;
+  float* d_tex;           // dL/dtexture (accumulated), or null
   uint2 key;
   uint32_t ctr1_hi;  // instance << 16
   uint32_t iter4;    // iter << 4 (kernels refresh it from iter_dev when given)
@@ -229,6 +233,46 @@ struct RenderArgs {
   Work wk;
 };
 
+// bilinear texture lookup at the interpolated uv of a hit: texel coordinates
+// x = uv_x W - 0.5, y = uv_y H - 0.5 and their floors are float32 decisions; the
+// four texels (clamped to the edge) and their weights
+struct TexSample {
+  int i0, i1, j0, j1;
+  float fx, fy;
+};
+__device__ __forceinline__ TexSample tex_coords(const RenderArgs& a, int3 f, float u, float v) {
+  const float w = __fsub_rn(__fsub_rn(1.0f, u), v);
+  const float2 t0 = __ldg(reinterpret_cast<const float2*>(a.uv) + f.x);
+  const float2 t1 = __ldg(reinterpret_cast<const float2*>(a.uv) + f.y);
+  const float2 t2 = __ldg(reinterpret_cast<const float2*>(a.uv) + f.z);
+  const float ux = __fmaf_rn(v, t2.x, __fmaf_rn(u, t1.x, __fmul_rn(w, t0.x)));
+  const float uy = __fmaf_rn(v, t2.y, __fmaf_rn(u, t1.y, __fmul_rn(w, t0.y)));
+  const float x = __fmaf_rn(ux, (float)a.tex_w, -0.5f), y = __fmaf_rn(uy, (float)a.tex_h, -0.5f);
+  const float xf = floorf(x), yf = floorf(y);
+  TexSample ts;
+  ts.fx = __fsub_rn(x, xf);
+  ts.fy = __fsub_rn(y, yf);
+  const int xi = (int)fminf(fmaxf(xf, -1.0f), (float)a.tex_w), yi = (int)fminf(fmaxf(yf, -1.0f), (float)a.tex_h);
+  ts.i0 = min(max(xi, 0), a.tex_w - 1);
+  ts.i1 = min(max(xi + 1, 0), a.tex_w - 1);
+  ts.j0 = min(max(yi, 0), a.tex_h - 1);
+  ts.j1 = min(max(yi + 1, 0), a.tex_h - 1);
+  return ts;
+}
+
+__device__ __forceinline__ float3 tex_texel(const RenderArgs& a, int i, int j) {
+  return ld3(a.tex + 3 * ((size_t)j * a.tex_w + i));
+}
+
+__device__ __forceinline__ float3 tex_albedo(const RenderArgs& a, const TexSample& ts) {
+  const float3 t00 = tex_texel(a, ts.i0, ts.j0), t10 = tex_texel(a, ts.i1, ts.j0);
+  const float3 t01 = tex_texel(a, ts.i0, ts.j1), t11 = tex_texel(a, ts.i1, ts.j1);
+  const float gx = 1.0f - ts.fx, gy = 1.0f - ts.fy;
+  return make_float3(gy * (gx * t00.x + ts.fx * t10.x) + ts.fy * (gx * t01.x + ts.fx * t11.x),
+                     gy * (gx * t00.y + ts.fx * t10.y) + ts.fy * (gx * t01.y + ts.fx * t11.y),
+                     gy * (gx * t00.z + ts.fx * t10.z) + ts.fy * (gx * t01.z + ts.fx * t11.z));
+}
+
 __device__ __forceinline__ float3 shade(const RenderArgs& a, const Hit& h) {
   int i0 = __ldg(&a.faces[3 * h.tri]), i1 = __ldg(&a.faces[3 * h.tri + 1]), i2 = __ldg(&a.faces[3 * h.tri + 2]);
   float3 n0 = ld3(a.normals + 3 * i0), n1 = ld3(a.normals + 3 * i1), n2 = ld3(a.normals + 3 * i2);
@@ -238,10 +282,15 @@ __device__ __forceinline__ float3 shade(const RenderArgs& a, const Hit& h) {
   if (ndl > 0.0f) sigma = ndl * rsqrtf(nm.x * nm.x + nm.y * nm.y + nm.z * nm.z);
   float w = 1.0f - h.u - h.v;
   float k = a.sh.ka + a.sh.kd * sigma;
-  float3 a0 = ld3(a.albedo + 3 * i0), a1 = ld3(a.albedo + 3 * i1), a2 = ld3(a.albedo + 3 * i2);
-  return make_float3((w * a0.x + h.u * a1.x + h.v * a2.x) * a.sh.lrgb.x * k,
-                     (w * a0.y + h.u * a1.y + h.v * a2.y) * a.sh.lrgb.y * k,
-                     (w * a0.z + h.u * a1.z + h.v * a2.z) * a.sh.lrgb.z * k);
+  float3 alb;
+  if (a.tex) {
+    alb = tex_albedo(a, tex_coords(a, make_int3(i0, i1, i2), h.u, h.v));
+  } else {
+    float3 a0 = ld3(a.albedo + 3 * i0), a1 = ld3(a.albedo + 3 * i1), a2 = ld3(a.albedo + 3 * i2);
+    alb = make_float3(w * a0.x + h.u * a1.x + h.v * a2.x, w * a0.y + h.u * a1.y + h.v * a2.y,
+                      w * a0.z + h.u * a1.z + h.v * a2.z);
+  }
+  return make_float3(alb.x * a.sh.lrgb.x * k, alb.y * a.sh.lrgb.y * k, alb.z * a.sh.lrgb.z * k);
 }
 
 __device__ __forceinline__ Cam load_cam(const Cam* cams, int view) {
@@ -701,12 +750,41 @@ __device__ __forceinline__ void hit_grad(const RenderArgs& a, const Hit& h, cons
   float sigma = lit ? dot3(nh, a.sh.l) : 0.0f;
   float k = a.sh.ka + a.sh.kd * sigma;
   float3 dalb = make_float3(g.x * a.sh.lrgb.x * k, g.y * a.sh.lrgb.y * k, g.z * a.sh.lrgb.z * k);
-  float gu = dalb.x * (a1.x - a0.x) + dalb.y * (a1.y - a0.y) + dalb.z * (a1.z - a0.z);
-  float gv = dalb.x * (a2.x - a0.x) + dalb.y * (a2.y - a0.y) + dalb.z * (a2.z - a0.z);
+  float gu, gv;
+  float3 alb;
+  if (a.tex) {
+    // albedo = bilinear(texture, uv(u, v)): texel gradients, and the uv chain to (u, v)
+    const TexSample ts = tex_coords(a, f, u, v);
+    alb = tex_albedo(a, ts);
+    const float3 t00 = tex_texel(a, ts.i0, ts.j0), t10 = tex_texel(a, ts.i1, ts.j0);
+    const float3 t01 = tex_texel(a, ts.i0, ts.j1), t11 = tex_texel(a, ts.i1, ts.j1);
+    const float gx = 1.0f - ts.fx, gy = 1.0f - ts.fy;
+    const float dax = (gy * (t10.x - t00.x) + ts.fy * (t11.x - t01.x)) * dalb.x +
+                      (gy * (t10.y - t00.y) + ts.fy * (t11.y - t01.y)) * dalb.y +
+                      (gy * (t10.z - t00.z) + ts.fy * (t11.z - t01.z)) * dalb.z;
+    const float day = (gx * (t01.x - t00.x) + ts.fx * (t11.x - t10.x)) * dalb.x +
+                      (gx * (t01.y - t00.y) + ts.fx * (t11.y - t10.y)) * dalb.y +
+                      (gx * (t01.z - t00.z) + ts.fx * (t11.z - t10.z)) * dalb.z;
+    const float dux = dax * (float)a.tex_w, duy = day * (float)a.tex_h;   // dL/d(uv of the hit)
+    const float2 q0 = __ldg(reinterpret_cast<const float2*>(a.uv) + f.x);
+    const float2 q1 = __ldg(reinterpret_cast<const float2*>(a.uv) + f.y);
+    const float2 q2 = __ldg(reinterpret_cast<const float2*>(a.uv) + f.z);
+    gu = dux * (q1.x - q0.x) + duy * (q1.y - q0.y);
+    gv = dux * (q2.x - q0.x) + duy * (q2.y - q0.y);
+    if (a.d_tex) {
+      const float wts[4] = {gx * gy, ts.fx * gy, gx * ts.fy, ts.fx * ts.fy};
+      const int ii[4] = {ts.i0, ts.i1, ts.i0, ts.i1}, jj[4] = {ts.j0, ts.j0, ts.j1, ts.j1};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        add3(a.d_tex, jj[q] * a.tex_w + ii[q], wts[q] * dalb.x, wts[q] * dalb.y, wts[q] * dalb.z);
+    }
+  } else {
+    gu = dalb.x * (a1.x - a0.x) + dalb.y * (a1.y - a0.y) + dalb.z * (a1.z - a0.z);
+    gv = dalb.x * (a2.x - a0.x) + dalb.y * (a2.y - a0.y) + dalb.z * (a2.z - a0.z);
+    alb = make_float3(w * a0.x + u * a1.x + v * a2.x, w * a0.y + u * a1.y + v * a2.y, w * a0.z + u * a1.z + v * a2.z);
+  }
   float3 dnm = make_float3(0.0f, 0.0f, 0.0f);
   if (lit) {
-    float3 alb = make_float3(w * a0.x + u * a1.x + v * a2.x, w * a0.y + u * a1.y + v * a2.y,
-                             w * a0.z + u * a1.z + v * a2.z);
     float dsig = a.sh.kd * (g.x * alb.x * a.sh.lrgb.x + g.y * alb.y * a.sh.lrgb.y + g.z * alb.z * a.sh.lrgb.z);
     float3 dnh = make_float3(dsig * a.sh.l.x, dsig * a.sh.l.y, dsig * a.sh.l.z);
     float pr = dot3(nh, dnh);
@@ -1517,6 +1595,11 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.node_stride = ctx->lim.max_F;
   a.cand_per_chunk = ctx->tune.cand_per_chunk;
   a.max_chunks = ctx->tune.max_chunks;
+  a.uv = m->uv;
+  a.tex = (o->texture && m->uv) ? o->texture : nullptr;
+  a.tex_w = o->tex_w;
+  a.tex_h = o->tex_h;
+  a.d_tex = a.tex ? o->d_texture : nullptr;
   if (ctx->vt) {
     a.vt = ctx->vt;
     a.it = ctx->it;

@@ -208,6 +208,7 @@ class HandModel:
     vf_offsets: np.ndarray     # [V+1]   vertex -> incident faces, CSR
     vf_faces: np.ndarray       # [3F]    ascending face ids per vertex
     albedo: np.ndarray         # [V][3]
+    uv: np.ndarray = None      # [V][2] texture coordinates (planar projection of the rest pose)
 
     @property
     def V(self):
@@ -386,7 +387,31 @@ def make_hand(seed: int = 0) -> HandModel:
         faces=np.ascontiguousarray(f, np.int32),
         edges=edges, edge_faces=ef, vf_offsets=vfo, vf_faces=vff,
         albedo=np.ascontiguousarray(alb, np.float32),
+        uv=planar_uv(v),
     )
+
+
+def planar_uv(v):
+    """Texture coordinates of the rest pose: its (x, y) projection scaled to the unit
+    square (front and back share texels; there is no seam)."""
+    v = np.asarray(v, np.float64)
+    lo, hi = v[:, :2].min(0), v[:, :2].max(0)
+    return np.ascontiguousarray((v[:, :2] - lo) / (hi - lo), np.float32)
+
+
+def texture(seed: int, size: int = 256):
+    """Albedo texture [size][size][3] from smooth noise (eight random 2-D sinusoids per
+    channel, remapped to [0.2, 0.9])."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 256]))
+    y, x = np.mgrid[0:size, 0:size] / size
+    out = np.zeros((size, size, 3))
+    for c in range(3):
+        acc = np.zeros((size, size))
+        for _ in range(8):
+            k = rng.normal(0.0, 12.0, 2)
+            acc += rng.uniform(0.5, 1.0) * np.sin(k[0] * x + k[1] * y + rng.uniform(0, 2 * math.pi))
+        out[..., c] = 0.2 + 0.7 * (acc - acc.min()) / max(acc.max() - acc.min(), 1e-12)
+    return np.ascontiguousarray(out, np.float32)
 
 
 # ----------------------------------------------------------------------------------
@@ -572,12 +597,13 @@ def subdivide_hand(hand: HandModel, levels: int = 2) -> HandModel:
     """The hand after `levels` Loop subdivisions: positions, shape blendshapes, skin
     weights and albedo all follow the same (affine, rows summing to one) linear map;
     the skeleton and joint regressor are unchanged."""
-    v, sd, w, alb, faces = hand.v_template, hand.shapedirs, hand.weights, hand.albedo, hand.faces
+    v, sd, w, alb, uv, faces = hand.v_template, hand.shapedirs, hand.weights, hand.albedo, hand.uv, hand.faces
     for _ in range(levels):
         rows, faces = loop_subdivision_matrix(faces, v.shape[0])
-        v, sd, w, alb = (_apply_rows(rows, a) for a in (v, sd, w, alb))
+        v, sd, w, alb, uv = (_apply_rows(rows, a) for a in (v, sd, w, alb, uv))
     edges, edge_faces, vf_off, vf = mesh_topology(faces, v.shape[0])
     f32 = lambda a: np.ascontiguousarray(a, np.float32)
     return HandModel(v_template=f32(v), shapedirs=f32(sd), weights=f32(w), j_template=hand.j_template,
                      j_shapedirs=hand.j_shapedirs, parents=hand.parents, faces=np.ascontiguousarray(faces, np.int32),
-                     edges=edges, edge_faces=edge_faces, vf_offsets=vf_off, vf_faces=vf, albedo=f32(alb))
+                     edges=edges, edge_faces=edge_faces, vf_offsets=vf_off, vf_faces=vf, albedo=f32(alb),
+                     uv=f32(uv))
