@@ -580,8 +580,9 @@ def run_refinement(args, dev):
 
 def run_scale(dev, iters=10):
     """The scale workload: the hand Loop-subdivided twice (12,337 vertices, 24,608
-    triangles; multi-block BVH build, float64-atomic backward sums), 16 views of
-    1024 x 1024, 64 spp, 32768 edge samples per view.  One refinement iteration
+    triangles; multi-block BVH build, float64-atomic backward sums) with a 256 x 256
+    RGB albedo texture (bilinear lookup; its gradient is accumulated every iteration),
+    16 views of 1024 x 1024, 64 spp, 32768 edge samples per view.  One refinement iteration
     (skinning, BVH update, forward, loss, backward, skinning adjoint, Adam) captured as
     a CUDA graph, replayed `iters` times; inputs (1.2 GB of images) exceed L2."""
     import torch
@@ -595,10 +596,13 @@ def run_scale(dev, iters=10):
     model = B.Model(hand, device=dev)
     x_gt = I.gt_params(cfg.seed)
     ctx = B.Context(hand.V, hand.F, hand.E, cfg.views, cfg.width, cfg.height)
-    views, _ = P.make_views(cfg, model, x_gt, device=dev, ctx=ctx)
+    tex = torch.as_tensor(I.texture(cfg.seed, 256), device=dev)
+    views, _ = P.make_views(cfg, model, x_gt, device=dev, ctx=ctx, texture=tex)
     ref = torch.empty((hand.V, 3), device=dev)
     B.hr_skin(ctx, model, torch.as_tensor(x_gt, device=dev), ref)
-    pr = P.PlainRefiner(model, views, cfg, ctx=ctx, ref_verts=ref, max_iters=iters + 8, device=dev)
+    pr = P.PlainRefiner(model, views, cfg, ctx=ctx, ref_verts=ref, max_iters=iters + 8, device=dev, texture=tex)
+    d_tex = torch.zeros_like(tex)
+    pr.r.opts.d_texture = d_tex.data_ptr()
     x0 = torch.as_tensor(I.perturb_params(x_gt, cfg.seed), device=dev)
     pr.reset(x0)
     tuning, t0, t1 = P.autotune(ctx, pr.render_pass,
@@ -631,7 +635,8 @@ def run_scale(dev, iters=10):
         raise RuntimeError(f"scale device status {B.status_string(status)}")
     err = pr.err[:iters + 2, 0].cpu().numpy() * 1e3
     ctx.close()
-    return {"workload": cfg.name, "vertices": hand.V, "triangles": hand.F, "views": cfg.views,
+    return {"workload": cfg.name, "vertices": hand.V, "triangles": hand.F, "texture": "256x256 RGB, bilinear",
+            "views": cfg.views,
             "width": cfg.width, "height": cfg.height, "spp": cfg.spp, "edge_samples_per_view": cfg.edge_samples,
             "ms_per_iter": round(ms, 3), "rays_per_iter": int(rays), "value": round(rays / (ms * 1e-3) / 1e6, 1),
             "unit": UNIT, "kernel_ms": {k: round(v, 4) for k, v in kt.items() if v >= 0}, "tuning": tuning,

@@ -117,15 +117,17 @@ class HandRenderLoss(torch.autograd.Function):
 # Synthetic multiframes
 # --------------------------------------------------------------------------------------
 
-def opts_for(cfg: I.SceneConfig, spp=None, seed=None, iter=0, iter_dev=None, flags=B.HR_BWD_REUSE_FWD):
+def opts_for(cfg: I.SceneConfig, spp=None, seed=None, iter=0, iter_dev=None, flags=B.HR_BWD_REUSE_FWD,
+             texture=None, d_texture=None):
     """Render options of a workload; the backward reuses the forward's candidate lists
     (a refinement iteration renders and differentiates the same scene)."""
     return B.render_opts(seed=cfg.seed * 7919 + 17 if seed is None else seed, iter=iter, spp=spp or cfg.spp,
                          edge_samples=cfg.edge_samples, ka=I.K_AMBIENT, kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR,
-                         light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX, iter_dev=iter_dev, flags=flags)
+                         light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX, iter_dev=iter_dev, flags=flags,
+                         texture=texture, d_texture=d_texture)
 
 
-def make_views(cfg: I.SceneConfig, model: B.Model, x_gt, device="cuda", ctx=None):
+def make_views(cfg: I.SceneConfig, model: B.Model, x_gt, device="cuda", ctx=None, texture=None):
     """Observations by this library's own renderer: the GT render at cfg.obs_spp
     samples per pixel plus N(0, sigma) noise; mask = render differs from the plate,
     dilated by cfg.mask_dilate_px (the recipe of the synthetic multiframes)."""
@@ -140,7 +142,7 @@ def make_views(cfg: I.SceneConfig, model: B.Model, x_gt, device="cuda", ctx=None
     B.hr_skin(ctx, model, p, verts)
     B.hr_build_bvh(ctx, model, verts)
     clean = torch.empty((N, H, W, 3), device=device)
-    o = opts_for(cfg, spp=cfg.obs_spp, seed=cfg.seed * 7919 + 1)
+    o = opts_for(cfg, spp=cfg.obs_spp, seed=cfg.seed * 7919 + 1, texture=texture)
     B.hr_render_fwd(ctx, model, verts, cams, H, W, bg, o, clean)
     clean_np = clean.cpu().numpy()
     obs = I.add_noise(clean_np, cfg.seed, cfg.noise_sigma)
@@ -297,11 +299,12 @@ class PlainRefiner:
     with per-group step sizes; the device counter advances the sample streams."""
 
     def __init__(self, model: B.Model, views: Views, cfg: I.SceneConfig, instance=0, seed=17, lr=1.0,
-                 lr_groups=LR_GROUPS, ref_verts=None, max_iters=1024, ctx=None, device="cuda"):
+                 lr_groups=LR_GROUPS, ref_verts=None, max_iters=1024, ctx=None, device="cuda", texture=None):
         self.counter = torch.zeros(1, dtype=torch.int32, device=device)
         opts = B.render_opts(seed=seed, instance=instance, spp=cfg.spp, edge_samples=cfg.edge_samples,
                              ka=I.K_AMBIENT, kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR, light_rgb=I.LIGHT_RGB,
-                             edge_eps_px=I.EDGE_EPS_PX, iter_dev=self.counter, flags=B.HR_BWD_REUSE_FWD)
+                             edge_eps_px=I.EDGE_EPS_PX, iter_dev=self.counter, flags=B.HR_BWD_REUSE_FWD,
+                             texture=texture)
         self.r = Refiner(model, views, opts, ctx=ctx)
         self.params = torch.zeros(I.N_PARAMS, device=device)
         self.m1 = torch.zeros_like(self.params)
