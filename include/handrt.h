@@ -239,6 +239,17 @@ int hr_render_fwd(hr_context* ctx, const hr_model* model, const float* verts, co
 int hr_loss(hr_context* ctx, const float* image, const float* observed, const uint8_t* mask, int N, int H,
             int W, float* loss, float* adjoint, hr_stream stream);
 
+/* The data term with the per-camera colour transform (Eq. 2: camera i's rendering
+ * enters the comparison as T_i R, T_i a 3x3 matrix applied to every pixel's RGB):
+ *   L = sum_p M_p sum_c |(T_i R_p)_c - O_pc| / (3 sum_p M_p),
+ *   adjoint_p = dL/dR_p = T_i^T (M_p sign(T_i R_p - O_p) / (3 sum M)),
+ *   dT[i] = dL/dT_i = sum over camera i's pixels of (M sign(...) / (3 sum M)) R_p^T.
+ * T: device float[N][9] row-major (NULL = identity, the plain hr_loss); dT: device
+ * float[N][9] (overwritten) or NULL.  Sums in a fixed order; N <= 113.  Single-
+ * instance contexts. */
+int hr_loss_ct(hr_context* ctx, const float* image, const float* observed, const uint8_t* mask, const float* T,
+               int N, int H, int W, float* loss, float* adjoint, float* dT, hr_stream stream);
+
 /* Backward of hr_render_fwd for adjoint image A = dL/dR (Section 1 and Section 3.1:
  * the ray tracer of Li et al. 2018 handles visibility discontinuities in the
  * backward pass).  d_verts (device float[V][3], overwritten) is the sum of
@@ -271,6 +282,34 @@ int hr_adam_step(float* params, const float* grad, float* m, float* v, int n, fl
 int hr_adam_step_dev(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1,
                      float beta2, float eps, const float* lr_scale, int scale_len, uint32_t* iter_dev,
                      hr_stream stream);
+
+/* G_J, the model's 3-D joint locations (Section 3, the prior term E_2): hr_skin plus
+ * the posed joints (each joint frame's origin plus the root translation), joints:
+ * device float[J][3] ([n][J][3] on a batch context).  hr_skin_bwd_joints is
+ * hr_skin_bwd with an optional upstream gradient of those joints (d_joints, same
+ * layout, or NULL) added to the kinematic chain's adjoint.  Single-instance or batch
+ * contexts. */
+int hr_skin_joints(hr_context* ctx, const hr_model* model, const float* params, float* verts, float* joints,
+                   hr_stream stream);
+int hr_skin_bwd_joints(hr_context* ctx, const hr_model* model, const float* params, const float* d_verts,
+                       const float* d_joints, float* d_params, hr_stream stream);
+
+/* The prior term E_2 per instance (Section 3): weight * sum over joints and coordinates
+ * of f_2(x, y) = 0.5 (x - y)^2 / gamma for |x - y| < gamma, |x - y| - 0.5 gamma
+ * otherwise, x the target joints, y the model's (device float[n][J][3] each); loss:
+ * device float[n]; d_joints (device float[n][J][3] or NULL) = dE_2/dy.  The paper
+ * uses gamma = 5 mm and weight 1e-3.  J <= 1024. */
+int hr_joint_prior(const float* joints, const float* target, int J, int n, float gamma, float weight, float* loss,
+                   float* d_joints, hr_stream stream);
+
+/* The two-level colour map (Section 3, "Color mapping"): out = V_low scaled up by
+ * nearest neighbour to W x H + V_high, all device float [rows][cols][3]
+ * (V_low [hl][wl][3], V_high and out [H][W][3]; W, H multiples of wl, hl).
+ * hr_colour_map_bwd: dL/dV_low (device float[hl][wl][3], overwritten) from dL/dV
+ * (the gradient of V_high is dL/dV itself); block sums in a fixed order. */
+int hr_colour_map(const float* v_low, int wl, int hl, const float* v_high, int W, int H, float* out,
+                  hr_stream stream);
+int hr_colour_map_bwd(const float* d_v, int W, int H, int wl, int hl, float* d_low, hr_stream stream);
 
 /* Mean vertex error epsilon_v (Section 4.1: mean Euclidean distance between the
  * vertices of the estimate and of the ground truth), per instance, in metres:

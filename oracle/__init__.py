@@ -350,8 +350,16 @@ def skin(hand, params, return_state=False):
     return verts
 
 
-def skin_bwd(hand, params, dverts):
-    """dL/dparams [61] for upstream dL/dverts [V][3] (reverse of `skin`)."""
+def skin_joints(hand, params):
+    """G_J (Section 3, the prior term): the posed 3-D joint locations, the origin of
+    each joint's global frame plus the root translation, [J][3]."""
+    _, st = skin(hand, params, return_state=True)
+    return np.stack(st["tG"]) + np.asarray(params, np.float64)[58:61]
+
+
+def skin_bwd(hand, params, dverts, djoints=None):
+    """dL/dparams [61] for upstream dL/dverts [V][3] and, optionally, dL/d(posed
+    joints) [J][3] (reverse of `skin` and `skin_joints`)."""
     x = np.asarray(params, np.float64)
     theta, phi = x[10:55], x[55:58]
     dV = np.asarray(dverts, np.float64)
@@ -362,6 +370,8 @@ def skin_bwd(hand, params, dverts):
     nj = Jr.shape[0]
     g = np.zeros(61)
     g[58:61] = dV.sum(0)                                        # tau
+    dJt = np.zeros((len(par), 3)) if djoints is None else np.asarray(djoints, np.float64)
+    g[58:61] += dJt.sum(0)
     dRA = np.einsum("vj,va,vb->jab", W, dV, vt)                # [J,3,3]
     dtA = np.einsum("vj,va->ja", W, dV)                        # [J,3]
     dvt = np.einsum("vj,jab,va->vb", W, RA, dV)                # [V,3]
@@ -369,7 +379,7 @@ def skin_bwd(hand, params, dverts):
     g[0:10] = np.einsum("vck,vc->k", S, dvt)
     # A_j = [RG_j | tG_j - RG_j J_j]
     dRG = [dRA[j] - np.outer(dtA[j], Jr[j]) for j in range(nj)]
-    dtG = [dtA[j].copy() for j in range(nj)]
+    dtG = [dtA[j] + dJt[j] for j in range(nj)]
     dJ = [-RG[j].T @ dtA[j] for j in range(nj)]
     dRl = [None] * nj
     for j in range(nj - 1, -1, -1):
@@ -394,3 +404,64 @@ def skin_bwd(hand, params, dverts):
 def vertex_error_mm(verts_a, verts_b):
     """epsilon_v: mean per-vertex Euclidean distance in millimetres (Section 4.1)."""
     return float(np.linalg.norm(np.asarray(verts_a, np.float64) - np.asarray(verts_b, np.float64), axis=1).mean() * 1e3)
+
+
+def _fma32(a, b, c):
+    """float32 fused multiply-add (the product of two float32 is exact in float64)."""
+    return (np.asarray(a, np.float64) * np.asarray(b, np.float64) + np.asarray(c, np.float64)).astype(np.float32)
+
+
+def loss_ct(render, observed, mask, T):
+    """Data term with per-camera 3x3 colour transforms (Eq. 2): T_i R evaluated in
+    float32 as fma(t2, r2, fma(t1, r1, t0 r0)) (the order the kernels use), d = T R - O;
+    L = sum M |d| / (3 sum M), adjoint dL/dR = T^T (M sign(d) / (3 sum M)),
+    dT_i = sum_p (M sign(d) / (3 sum M)) R_p^T."""
+    R = np.asarray(render, np.float32)
+    O = np.asarray(observed, np.float32)
+    M = (np.asarray(mask) != 0).astype(np.float64)
+    T = np.asarray(T, np.float32).reshape(-1, 3, 3)
+    N = R.shape[0]
+    cnt = M.sum()
+    scale = 1.0 / (3.0 * cnt) if cnt > 0 else 0.0
+    TR = np.empty_like(R)
+    for c in range(3):
+        t = T[:, c, :][:, None, None, :]
+        TR[..., c] = _fma32(t[..., 2], R[..., 2], _fma32(t[..., 1], R[..., 1],
+                                                          (t[..., 0].astype(np.float32) * R[..., 0]).astype(np.float32)))
+    # the exact difference of the float32 transformed value and the observation (its
+    # sign is that of the float32 difference the kernels take)
+    d = TR.astype(np.float64) - O.astype(np.float64)
+    s = np.sign(d) * M[..., None] * scale
+    L = float((M[..., None] * np.abs(d)).sum() * scale)
+    A = np.einsum("nji,nhwj->nhwi", T.astype(np.float64), s)
+    dT = np.einsum("nhwi,nhwj->nij", s, R.astype(np.float64)).reshape(N, 9)
+    return L, A, dT
+
+
+def joint_prior(joints, target, gamma, weight):
+    """E_2 (the prior term): weight * sum over joints and coordinates of the smooth L1
+    f_2(x, y) = 0.5 (x - y)^2 / gamma for |x - y| < gamma, |x - y| - 0.5 gamma otherwise,
+    between the target joints x and the model's joints y; returns (E_2, dE_2/dy)."""
+    y = np.asarray(joints, np.float64)
+    x = np.asarray(target, np.float64)
+    d = y - x
+    a = np.abs(d)
+    quad = a < gamma
+    f = np.where(quad, 0.5 * d * d / gamma, a - 0.5 * gamma)
+    g = np.where(quad, d / gamma, np.sign(d))
+    return float(weight * f.sum()), weight * g
+
+
+def colour_map(v_low, v_high):
+    """V(c) = V_low scaled up by nearest neighbour to V_high's size + V_high."""
+    lo = np.asarray(v_low, np.float64)
+    hi = np.asarray(v_high, np.float64)
+    fy, fx = hi.shape[0] // lo.shape[0], hi.shape[1] // lo.shape[1]
+    return np.repeat(np.repeat(lo, fy, axis=0), fx, axis=1) + hi
+
+
+def colour_map_bwd(d_v, low_shape):
+    """dL/dV_low: sums of dL/dV over each low texel's block."""
+    d = np.asarray(d_v, np.float64)
+    hl, wl = low_shape[0], low_shape[1]
+    return d.reshape(hl, d.shape[0] // hl, wl, d.shape[1] // wl, 3).sum(axis=(1, 3))

@@ -42,7 +42,8 @@ EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", 
            "hr_gemm_bf16", "hr_net_param_count", "hr_net_create", "hr_net_destroy", "hr_net_set_params",
            "hr_net_get_params", "hr_net_inputs", "hr_net_set_inputs_bf16", "hr_net_forward", "hr_net_backward",
            "hr_net_adam", "hr_net_status", "hr_vertex_mse", "hr_add_noise", "hr_select_best", "hr_update_bvh",
-           "hr_set_tuning", "hr_get_tuning")
+           "hr_set_tuning", "hr_get_tuning", "hr_loss_ct",
+           "hr_skin_joints", "hr_skin_bwd_joints", "hr_joint_prior", "hr_colour_map", "hr_colour_map_bwd")
 
 
 class HandrtError(RuntimeError):
@@ -103,6 +104,12 @@ def lib():
             "hr_build_bvh": [P, P, P, P],
             "hr_update_bvh": [P, P, P, P, I, P],
             "hr_set_tuning": [P, P],
+            "hr_loss_ct": [P, P, P, P, P, I, I, I, P, P, P, P],
+            "hr_skin_joints": [P, P, P, P, P, P],
+            "hr_skin_bwd_joints": [P, P, P, P, P, P, P],
+            "hr_joint_prior": [P, P, I, I, F, F, P, P, P],
+            "hr_colour_map": [P, I, I, P, I, I, P, P],
+            "hr_colour_map_bwd": [P, I, I, I, I, P, P],
             "hr_get_tuning": [P, P],
             "hr_render_fwd": [P, P, P, P, I, I, I, P, P, P, P],
             "hr_loss": [P, P, P, P, I, I, I, P, P, P],
@@ -349,6 +356,46 @@ def hr_loss(ctx, image, observed, mask, loss, adjoint, stream=None):
     assert mask.dtype == torch.uint8
     _check("hr_loss", lib().hr_loss(ctx.handle, _f32(image), _f32(observed), _ptr(mask), N, H, W, _f32(loss),
                                     _f32(adjoint), _stream(stream)))
+
+
+def hr_skin_joints(ctx, model, params, verts, joints, stream=None):
+    _check("hr_skin_joints", lib().hr_skin_joints(ctx.handle, ctypes.byref(model.struct), _f32(params), _f32(verts),
+                                                  _f32(joints), _stream(stream)))
+
+
+def hr_skin_bwd_joints(ctx, model, params, d_verts, d_joints, d_params, stream=None):
+    _check("hr_skin_bwd_joints", lib().hr_skin_bwd_joints(ctx.handle, ctypes.byref(model.struct), _f32(params),
+                                                          _f32(d_verts), None if d_joints is None else _f32(d_joints),
+                                                          _f32(d_params), _stream(stream)))
+
+
+def hr_joint_prior(joints, target, gamma, weight, loss, d_joints=None, stream=None):
+    J = joints.shape[-2]
+    n = joints.numel() // (3 * J)
+    _check("hr_joint_prior", lib().hr_joint_prior(_f32(joints), _f32(target), J, n, float(gamma), float(weight),
+                                                  _f32(loss), None if d_joints is None else _f32(d_joints),
+                                                  _stream(stream)))
+
+
+def hr_colour_map(v_low, v_high, out, stream=None):
+    hl, wl = v_low.shape[0], v_low.shape[1]
+    H, W = v_high.shape[0], v_high.shape[1]
+    _check("hr_colour_map", lib().hr_colour_map(_f32(v_low), wl, hl, _f32(v_high), W, H, _f32(out), _stream(stream)))
+
+
+def hr_colour_map_bwd(d_v, d_low, stream=None):
+    hl, wl = d_low.shape[0], d_low.shape[1]
+    H, W = d_v.shape[0], d_v.shape[1]
+    _check("hr_colour_map_bwd", lib().hr_colour_map_bwd(_f32(d_v), W, H, wl, hl, _f32(d_low), _stream(stream)))
+
+
+def hr_loss_ct(ctx, image, observed, mask, T, loss, adjoint, dT=None, stream=None):
+    """Masked L1 loss of T_i R against O per camera; adjoint = dL/dR; dT = dL/dT [N][9]."""
+    N, H, W = mask.shape
+    assert mask.dtype == torch.uint8
+    _check("hr_loss_ct", lib().hr_loss_ct(ctx.handle, _f32(image), _f32(observed), _ptr(mask),
+                                          None if T is None else _f32(T), N, H, W, _f32(loss), _f32(adjoint),
+                                          None if dT is None else _f32(dT), _stream(stream)))
 
 
 def hr_render_bwd(ctx, model, verts, cams, H, W, background, opts, adjoint, d_verts, stream=None):

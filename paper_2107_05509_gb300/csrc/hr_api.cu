@@ -38,7 +38,7 @@ void free_ctx(Context* c) {
                   c->status,  c->stats,   c->pool_bb,   c->pool_z,     c->pool_rec,      c->st_info,
                   c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it,
                   c->bvh_parent, c->bvh_valid, c->bvh_keys, c->bvh_flags, c->bvh_bounds, c->bvh_bad,
-                  c->bvh_mode, c->extra64};
+                  c->bvh_mode, c->extra64, c->ct_partials};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete[] c->hvt;
@@ -120,6 +120,7 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
   if (ok && F > 2048)
     ok = dev_alloc(&c->bvh_keys, ni * (size_t)c->bvh_pmax, a) && dev_alloc(&c->bvh_flags, ni * F, a);
   if (ok && V > 8192) ok = dev_alloc(&c->extra64, ni * 6 * V, a);
+  if (ok && n == 1) ok = dev_alloc(&c->ct_partials, views * 64 * 10, a);
   if (ok) ok = cudaMemset(c->counters, 0, ni * 4 * sizeof(unsigned)) == cudaSuccess &&
                cudaMemset(c->status, 0, sizeof(int)) == cudaSuccess &&
                cudaMemset(c->stats, 0, 3 * hr::kStatsPer * sizeof(unsigned long long)) == cudaSuccess &&
@@ -288,14 +289,14 @@ int hr_context_destroy(hr_context* ctx) {
 int hr_skin(hr_context* ctx, const hr_model* model, const float* params, float* verts, hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || c->vt || !model_ok(model, c) || !params || !verts) return HR_ERR_ARG;
-  return hr::launch_skin(c, model, params, verts, (cudaStream_t)stream);
+  return hr::launch_skin(c, model, params, verts, nullptr, (cudaStream_t)stream);
 }
 
 int hr_skin_bwd(hr_context* ctx, const hr_model* model, const float* params, const float* d_verts, float* d_params,
                 hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || c->vt || !model_ok(model, c) || !params || !d_verts || !d_params) return HR_ERR_ARG;
-  return hr::launch_skin_bwd(c, model, params, d_verts, d_params, (cudaStream_t)stream);
+  return hr::launch_skin_bwd(c, model, params, d_verts, nullptr, d_params, (cudaStream_t)stream);
 }
 
 int hr_build_bvh(hr_context* ctx, const hr_model* model, const float* verts, hr_stream stream) {
@@ -329,6 +330,16 @@ int hr_loss(hr_context* ctx, const float* image, const float* observed, const ui
   return hr::launch_loss(c, image, observed, mask, (long long)N * H * W, loss, adjoint, (cudaStream_t)stream);
 }
 
+int hr_loss_ct(hr_context* ctx, const float* image, const float* observed, const uint8_t* mask, const float* T,
+               int N, int H, int W, float* loss, float* adjoint, float* dT, hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || c->vt || !c->ct_partials || !image || !observed || !mask || !loss || !adjoint || !image_ok(c, N, H, W) ||
+      9 * N > 1024)
+    return HR_ERR_ARG;
+  return hr::launch_loss_ct(c, image, observed, mask, T, N, (long long)H * W, loss, adjoint, dT,
+                            (cudaStream_t)stream);
+}
+
 int hr_render_bwd(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams, int N, int H,
                   int W, const float* background, const hr_render_opts* opts, const float* adjoint, float* d_verts,
                   hr_stream stream) {
@@ -345,14 +356,14 @@ int hr_render_bwd(hr_context* ctx, const hr_model* model, const float* verts, co
 int hr_skin_batch(hr_context* ctx, const hr_model* model, const float* params, float* verts, hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || !c->vt || !model_ok(model, c) || !params || !verts) return HR_ERR_ARG;
-  return hr::launch_skin(c, model, params, verts, (cudaStream_t)stream);
+  return hr::launch_skin(c, model, params, verts, nullptr, (cudaStream_t)stream);
 }
 
 int hr_skin_bwd_batch(hr_context* ctx, const hr_model* model, const float* params, const float* d_verts,
                       float* d_params, hr_stream stream) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || !c->vt || !model_ok(model, c) || !params || !d_verts || !d_params) return HR_ERR_ARG;
-  return hr::launch_skin_bwd(c, model, params, d_verts, d_params, (cudaStream_t)stream);
+  return hr::launch_skin_bwd(c, model, params, d_verts, nullptr, d_params, (cudaStream_t)stream);
 }
 
 int hr_build_bvh_batch(hr_context* ctx, const hr_model* model, const float* verts, hr_stream stream) {
@@ -389,6 +400,37 @@ int hr_render_bwd_batch(hr_context* ctx, const hr_model* model, const float* ver
   if (c->F != model->F || c->V != model->V) return HR_ERR_ARG;
   return hr::launch_render_bwd(c, model, verts, reinterpret_cast<const Cam*>(cams), 0, 0, 0, background, opts,
                                adjoint, d_verts, (cudaStream_t)stream);
+}
+
+int hr_skin_joints(hr_context* ctx, const hr_model* model, const float* params, float* verts, float* joints,
+                   hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !model_ok(model, c) || !params || !verts || !joints) return HR_ERR_ARG;
+  return hr::launch_skin(c, model, params, verts, joints, (cudaStream_t)stream);
+}
+
+int hr_skin_bwd_joints(hr_context* ctx, const hr_model* model, const float* params, const float* d_verts,
+                       const float* d_joints, float* d_params, hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !model_ok(model, c) || !params || !d_verts || !d_params) return HR_ERR_ARG;
+  return hr::launch_skin_bwd(c, model, params, d_verts, d_joints, d_params, (cudaStream_t)stream);
+}
+
+int hr_joint_prior(const float* joints, const float* target, int J, int n, float gamma, float weight, float* loss,
+                   float* d_joints, hr_stream stream) {
+  if (!joints || !target || !loss || J < 1 || J > 1024 || n < 1 || !(gamma > 0.0f)) return HR_ERR_ARG;
+  return hr::launch_joint_prior(joints, target, J, n, gamma, weight, loss, d_joints, (cudaStream_t)stream);
+}
+
+int hr_colour_map(const float* v_low, int wl, int hl, const float* v_high, int W, int H, float* out,
+                  hr_stream stream) {
+  if (!v_low || !v_high || !out || wl < 1 || hl < 1 || W < wl || H < hl || W % wl || H % hl) return HR_ERR_ARG;
+  return hr::launch_colour_map(v_low, wl, hl, v_high, W, H, out, (cudaStream_t)stream);
+}
+
+int hr_colour_map_bwd(const float* d_v, int W, int H, int wl, int hl, float* d_low, hr_stream stream) {
+  if (!d_v || !d_low || wl < 1 || hl < 1 || W < wl || H < hl || W % wl || H % hl) return HR_ERR_ARG;
+  return hr::launch_colour_map_bwd(d_v, W, H, wl, hl, d_low, (cudaStream_t)stream);
 }
 
 int hr_vertex_error(const float* verts, const float* ref, int V, int n, float* out, const uint32_t* iter_dev,

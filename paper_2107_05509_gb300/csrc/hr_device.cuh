@@ -125,6 +125,7 @@ struct Context {
   // loss scratch: per instance kLossStride(loss_blocks) floats
   float* loss_partials;
   int loss_blocks;       // blocks per instance of the loss kernels
+  float* ct_partials;    // [max_views][64][10] colour-transformed loss partials
   unsigned int* counters;// [n_inst][4] last-block counters (mask count, loss, skin adjoint)
   // skin scratch
   float* skin_partials;  // [n_inst][kSkinBlocks][kSkinAcc]

@@ -7,9 +7,14 @@
 
 namespace hr {
 
-int launch_skin(Context* ctx, const hr_model* m, const float* params, float* verts, cudaStream_t s);
+int launch_skin(Context* ctx, const hr_model* m, const float* params, float* verts, float* joints, cudaStream_t s);
 int launch_skin_bwd(Context* ctx, const hr_model* m, const float* params, const float* d_verts,
-                    float* d_params, cudaStream_t s);
+                    const float* d_joints, float* d_params, cudaStream_t s);
+int launch_joint_prior(const float* joints, const float* target, int J, int n, float gamma, float weight,
+                       float* loss, float* d_joints, cudaStream_t s);
+int launch_colour_map(const float* v_low, int wl, int hl, const float* v_high, int W, int H, float* out,
+                      cudaStream_t s);
+int launch_colour_map_bwd(const float* d_v, int W, int H, int wl, int hl, float* d_low, cudaStream_t s);
 int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaStream_t s);
 int launch_update_bvh(Context* ctx, const hr_model* m, const float* verts, const uint32_t* iter_dev,
                       int rebuild_every, cudaStream_t s);
@@ -23,6 +28,8 @@ int launch_silhouettes(Context* ctx, const hr_model* m, const float* verts, cons
 int launch_trace(Context* ctx, const float* o, const float* d, int n, int* tri, float* tuv, cudaStream_t s);
 int launch_loss(Context* ctx, const float* image, const float* obs, const uint8_t* mask, long long P,
                 float* loss, float* adjoint, cudaStream_t s);
+int launch_loss_ct(Context* ctx, const float* image, const float* obs, const uint8_t* mask, const float* T, int N,
+                   long long HW, float* loss, float* adjoint, float* dT, cudaStream_t s);
 int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
                 int step, cudaStream_t s);
 int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,

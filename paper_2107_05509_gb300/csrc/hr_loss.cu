@@ -303,6 +303,131 @@ __global__ void k_select_best(const float* __restrict__ cand, const float* __res
   if (chosen && threadIdx.x == 0) chosen[i] = best;
 }
 
+// Colour-transformed loss (Eq. 2: the rendering of camera i enters the comparison as
+// T_i R): per view, blocks over the view's pixels compute d = T R - O, the adjoint
+// with respect to R, A = T^T (M sign(d) scale), and partial sums of M |d| and of
+// dL/dT = (M sign(d) scale) R^T; a final block adds the partials in a fixed order.
+constexpr int kCtBlocks = 64;
+constexpr int kCtVals = 10;   // |d| sum, dT (9)
+__global__ void __launch_bounds__(kLossThreads) k_loss_ct(const float* __restrict__ image,
+                                                          const float* __restrict__ obs,
+                                                          const uint8_t* __restrict__ mask,
+                                                          const float* __restrict__ T, long long HW,
+                                                          const float* __restrict__ scale_p,
+                                                          float* __restrict__ adjoint,
+                                                          float* __restrict__ part) {
+  __shared__ float red[kCtVals][kLossThreads / 32];
+  const int view = blockIdx.y;
+  const float sc = scale_p[0];
+  float t[9] = {1.0f, 0.0f, 0.0f, 0.0f, 1.0f, 0.0f, 0.0f, 0.0f, 1.0f};
+  if (T)
+    for (int k = 0; k < 9; ++k) t[k] = T[view * 9 + k];
+  float acc[kCtVals] = {};
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < HW; q += (long long)gridDim.x * blockDim.x) {
+    const long long p = view * HW + q;
+    const float m = mask[p] ? 1.0f : 0.0f;
+    const float r[3] = {image[3 * p], image[3 * p + 1], image[3 * p + 2]};
+    float sg[3];
+    for (int c = 0; c < 3; ++c) {
+      // the sign of d decides the adjoint: float32 with a fixed operation order
+      const float tr = __fmaf_rn(t[3 * c + 2], r[2], __fmaf_rn(t[3 * c + 1], r[1], __fmul_rn(t[3 * c], r[0])));
+      const float d = __fsub_rn(tr, obs[3 * p + c]);
+      acc[0] += m * fabsf(d);
+      sg[c] = m * sgn(d) * sc;
+    }
+    for (int c = 0; c < 3; ++c) {
+      adjoint[3 * p + c] = t[c] * sg[0] + t[3 + c] * sg[1] + t[6 + c] * sg[2];
+      for (int k = 0; k < 3; ++k) acc[1 + 3 * c + k] += sg[c] * r[k];
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < kCtVals; ++k) {
+    float x = acc[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[k][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < kCtVals) {
+    float x = 0.0f;
+    for (int w = 0; w < kLossThreads / 32; ++w) x += red[threadIdx.x][w];
+    part[((size_t)view * gridDim.x + blockIdx.x) * kCtVals + threadIdx.x] = x;
+  }
+}
+
+// loss = scale sum_views sum_blocks |d| (double, fixed order); dT[view] = its partials
+__global__ void k_loss_ct_final(const float* __restrict__ part, int N, int nb, const float* __restrict__ scale_p,
+                                float* __restrict__ loss, float* __restrict__ dT) {
+  if (threadIdx.x < 9 * N && dT) {
+    const int view = threadIdx.x / 9, k = threadIdx.x % 9;
+    float x = 0.0f;
+    for (int b = 0; b < nb; ++b) x += part[((size_t)view * nb + b) * kCtVals + 1 + k];
+    dT[view * 9 + k] = x;
+  }
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int v = 0; v < N; ++v)
+      for (int b = 0; b < nb; ++b) tot += part[((size_t)v * nb + b) * kCtVals];
+    loss[0] = (float)(tot * (double)scale_p[0]);
+  }
+}
+
+// E_2 (the prior term), per instance (block): weight * sum over joints and
+// coordinates of the smooth L1 f_2 between the target joints x and the model's joints
+// y (0.5 d^2 / gamma for |d| < gamma, |d| - gamma / 2 beyond, d = y - x), and dE_2/dy
+__global__ void k_joint_prior(const float* __restrict__ joints, const float* __restrict__ target, int J,
+                              float gamma, float weight, float* __restrict__ loss, float* __restrict__ d_joints) {
+  __shared__ double red[1024];
+  const size_t o = (size_t)blockIdx.x * 3 * J;
+  double f = 0.0;
+  for (int i = threadIdx.x; i < 3 * J; i += blockDim.x) {
+    const float d = joints[o + i] - target[o + i];
+    const float a = fabsf(d);
+    const bool quad = a < gamma;
+    f += quad ? 0.5 * (double)d * d / gamma : (double)a - 0.5 * gamma;
+    if (d_joints) d_joints[o + i] = weight * (quad ? d / gamma : (d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f)));
+  }
+  red[threadIdx.x] = f;
+  __syncthreads();
+  for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[blockIdx.x] = (float)(weight * red[0]);
+}
+
+// V(c) = V_low scaled up by nearest neighbour + V_high (the two-level colour map)
+__global__ void k_colour_map(const float* __restrict__ v_low, int wl, int hl, const float* __restrict__ v_high, int W,
+                             int H, float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)W * H * 3) return;
+  const int c = (int)(i % 3);
+  const long long p = i / 3;
+  const int x = (int)(p % W), y = (int)(p / W);
+  const int xl = x / (W / wl), yl = y / (H / hl);
+  out[i] = v_low[((size_t)yl * wl + xl) * 3 + c] + v_high[i];
+}
+
+// dL/dV_low: the sum of dL/dV over each low texel's block (one block of threads per
+// low texel and channel; strided sums added in a fixed tree order)
+__global__ void __launch_bounds__(256) k_colour_low_grad(const float* __restrict__ d_v, int W, int H, int wl, int hl,
+                                                         float* __restrict__ d_low) {
+  __shared__ float red[256];
+  const int c = blockIdx.y, xl = blockIdx.x % wl, yl = blockIdx.x / wl;
+  const int bw = W / wl, bh = H / hl;
+  float acc = 0.0f;
+  for (int k = threadIdx.x; k < bw * bh; k += blockDim.x) {
+    const int x = xl * bw + k % bw, y = yl * bh + k / bw;
+    acc += d_v[((size_t)y * W + x) * 3 + c];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d_low[((size_t)yl * wl + xl) * 3 + c] = red[0];
+}
+
 }  // namespace
 
 int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
@@ -329,6 +454,29 @@ int launch_add_noise(float* img, long long n, float sigma, uint64_t seed, cudaSt
 int launch_select_best(const float* cand, const float* losses, int K, int n, float* out, int* chosen,
                        cudaStream_t s) {
   k_select_best<<<n, 64, 0, s>>>(cand, losses, K, n, out, chosen);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_joint_prior(const float* joints, const float* target, int J, int n, float gamma, float weight,
+                       float* loss, float* d_joints, cudaStream_t s) {
+  int threads = 32;
+  while (threads < 3 * J && threads < 1024) threads <<= 1;
+  k_joint_prior<<<n, threads, 0, s>>>(joints, target, J, gamma, weight, loss, d_joints);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_colour_map(const float* v_low, int wl, int hl, const float* v_high, int W, int H, float* out,
+                      cudaStream_t s) {
+  const long long n = (long long)W * H * 3;
+  k_colour_map<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v_low, wl, hl, v_high, W, H, out);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_colour_map_bwd(const float* d_v, int W, int H, int wl, int hl, float* d_low, cudaStream_t s) {
+  k_colour_low_grad<<<dim3(wl * hl, 3), 256, 0, s>>>(d_v, W, H, wl, hl, d_low);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -361,6 +509,22 @@ int launch_loss(Context* ctx, const float* image, const float* obs, const uint8_
   HR_CHECK_LAUNCH();
   k_loss_adjoint<<<grid, kLossThreads, 0, s>>>(image, obs, mask, it, P, ctx->loss_partials, lstride, ctx->counters,
                                                adjoint, loss, vec);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_loss_ct(Context* ctx, const float* image, const float* obs, const uint8_t* mask, const float* T, int N,
+                   long long HW, float* loss, float* adjoint, float* dT, cudaStream_t s) {
+  const long long P = (long long)N * HW;
+  const long long want = (P + kLossThreads - 1) / kLossThreads;
+  const int blocks = (int)(want < kLossBlocks ? (want > 0 ? want : 1) : kLossBlocks);
+  float* scale = ctx->loss_partials + 3 * blocks;   // where k_mask_count leaves 1 / (3 sum M)
+  k_mask_count<<<dim3(blocks, 1), kLossThreads, 0, s>>>(mask, nullptr, P, ctx->loss_partials, 0, ctx->counters);
+  HR_CHECK_LAUNCH();
+  k_loss_ct<<<dim3(kCtBlocks, N), kLossThreads, 0, s>>>(image, obs, mask, T, HW, scale, adjoint, ctx->ct_partials);
+  HR_CHECK_LAUNCH();
+  k_loss_ct_final<<<1, 32 * ((9 * N + 31) / 32 > 0 ? (9 * N + 31) / 32 : 1), 0, s>>>(ctx->ct_partials, N, kCtBlocks,
+                                                                                     scale, loss, dT);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }

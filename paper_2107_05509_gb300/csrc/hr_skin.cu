@@ -164,13 +164,20 @@ __device__ __forceinline__ float3 shaped_vertex(const ModelArgs& m, const Chain&
   return make_float3(p[0], p[1], p[2]);
 }
 
-// blockIdx.y selects the instance: params [61] and verts [V][3] of instance y
+// blockIdx.y selects the instance: params [61] and verts [V][3] of instance y; block 0
+// also writes the posed joints G_J (each joint frame's origin plus the root
+// translation, [J][3]) when `joints_all` is given
 __global__ void __launch_bounds__(kSkinThreads) k_skin(ModelArgs m, const float* __restrict__ params_all,
-                                                       float* __restrict__ verts_all, int* status) {
+                                                       float* __restrict__ verts_all, float* __restrict__ joints_all,
+                                                       int* status) {
   __shared__ Chain ch;
   const float* params = params_all + (size_t)blockIdx.y * 61;
   float* verts = verts_all + (size_t)blockIdx.y * 3 * m.V;
   build_chain(m, params, ch, status);
+  if (joints_all && blockIdx.x == 0 && threadIdx.x < 3 * m.J) {
+    const int j = threadIdx.x / 3, c = threadIdx.x % 3;
+    joints_all[((size_t)blockIdx.y * m.J + j) * 3 + c] = ch.tG[j][c] + ch.tau[c];
+  }
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < m.V; v += gridDim.x * blockDim.x) {
     float3 p = shaped_vertex(m, ch, v);
     float out[3] = {ch.tau[0], ch.tau[1], ch.tau[2]};
@@ -195,9 +202,11 @@ __device__ __forceinline__ float warp_sum(float x) {
 // accumulator layout: [j*12 + 0..8] dRA_j (row-major), [j*12 + 9..11] dtA_j,
 // [16*12 + k] dbeta_k (blendshape part), [16*12 + 10 + c] dtau_c.
 // blockIdx.y selects the instance: params / dparams [61], dverts [V][3], partials
-// [kSkinBlocks][kSkinAcc] and the last-block counter at counter_all + y * cstride.
+// [kSkinBlocks][kSkinAcc] and the last-block counter at counter_all + y * cstride;
+// djoints_all (optional, [J][3] per instance) is dL/d(posed joints).
 __global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const float* __restrict__ params_all,
                                                            const float* __restrict__ dverts_all,
+                                                           const float* __restrict__ djoints_all,
                                                            float* __restrict__ partials_all, unsigned* counter_all,
                                                            int cstride, float* __restrict__ dparams_all,
                                                            int* status) {
@@ -274,12 +283,13 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const fl
   if (threadIdx.x == 0) {
     *counter = 0u;
     float dRG[kMaxJ][9], dtG[kMaxJ][3];
+    const float* djoints = djoints_all ? djoints_all + (size_t)blockIdx.y * 3 * m.J : nullptr;
     for (int j = 0; j < m.J; ++j) {
       const float* dRA = &bacc[12 * j];
       const float* dtA = &bacc[12 * j + 9];
       for (int a = 0; a < 3; ++a) {
         for (int b = 0; b < 3; ++b) dRG[j][3 * a + b] = dRA[3 * a + b] - dtA[a] * ch.J[j][b];
-        dtG[j][a] = dtA[a];
+        dtG[j][a] = dtA[a] + (djoints ? djoints[3 * j + a] : 0.0f);
         sdJ[j][a] = -(ch.RG[j][a] * dtA[0] + ch.RG[j][3 + a] * dtA[1] + ch.RG[j][6 + a] * dtA[2]);
       }
     }
@@ -325,7 +335,11 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const fl
       for (int c = 0; c < 3; ++c) s += m.j_shapedirs[(3 * j + c) * m.K + k] * sdJ[j][c];
     dparams[k] = s;
   } else if (tid >= 64 && tid < 67) {
-    dparams[58 + tid - 64] = bacc[16 * 12 + 10 + tid - 64];
+    const int c = tid - 64;
+    float dt = bacc[16 * 12 + 10 + c];
+    if (djoints_all)
+      for (int j = 0; j < m.J; ++j) dt += djoints_all[((size_t)blockIdx.y * m.J + j) * 3 + c];
+    dparams[58 + c] = dt;
   }
 }
 
@@ -345,19 +359,20 @@ ModelArgs model_args(const hr_model* m) {
 
 }  // namespace
 
-int launch_skin(Context* ctx, const hr_model* m, const float* params, float* verts, cudaStream_t s) {
+int launch_skin(Context* ctx, const hr_model* m, const float* params, float* verts, float* joints, cudaStream_t s) {
   int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
-  k_skin<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, verts, ctx->status);
+  k_skin<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, verts, joints, ctx->status);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
 
-int launch_skin_bwd(Context* ctx, const hr_model* m, const float* params, const float* d_verts, float* d_params,
-                    cudaStream_t s) {
+int launch_skin_bwd(Context* ctx, const hr_model* m, const float* params, const float* d_verts,
+                    const float* d_joints, float* d_params, cudaStream_t s) {
   int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
   if (blocks > kSkinBlocks) blocks = kSkinBlocks;
-  k_skin_bwd<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, d_verts, ctx->skin_partials,
-                                                                ctx->counters + 2, 4, d_params, ctx->status);
+  k_skin_bwd<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, d_verts, d_joints,
+                                                                ctx->skin_partials, ctx->counters + 2, 4, d_params,
+                                                                ctx->status);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -436,7 +451,8 @@ extern "C" int hr_skin_bwd_noalloc(const hr_model* m, const float* params, const
     return HR_ERR_CUDA;
   }
   int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
-  k_skin_bwd<<<blocks, kSkinThreads, 0, s>>>(model_args(m), params, d_verts, partials, counter, 0, d_params, status);
+  k_skin_bwd<<<blocks, kSkinThreads, 0, s>>>(model_args(m), params, d_verts, nullptr, partials, counter, 0, d_params,
+                                             status);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }

@@ -132,3 +132,50 @@ def test_loss_properties():
         assert abs(fd - A[idx]) < 1e-9
     # masked-out pixels carry no adjoint; epsilon_b = 255 L in 0-255 levels
     assert not A[M == 0].any()
+
+
+def test_joint_locations_and_their_adjoint():
+    """G_J: at zero parameters the joints are the rest joints; a root translation moves
+    every joint by it; the joint adjoint of skin_bwd matches central differences of the
+    joint locations (all 61 parameters, a random upstream gradient)."""
+    h = I.make_hand(0)
+    x0 = np.zeros(61)
+    assert np.allclose(oracle.skin_joints(h, x0), h.j_template.astype(np.float64))
+    xt = x0.copy()
+    xt[58:61] = (0.01, -0.02, 0.03)
+    assert np.allclose(oracle.skin_joints(h, xt) - oracle.skin_joints(h, x0), xt[58:61])
+    rng = np.random.default_rng(3)
+    x = I.perturb_params(I.gt_params(5), 5).astype(np.float64)
+    dJ = rng.normal(size=(h.j_template.shape[0], 3))
+    g = oracle.skin_bwd(h, x, np.zeros((h.V, 3)), dJ)
+    eps = 1e-6
+    fd = np.zeros(61)
+    for k in range(61):
+        xp, xm = x.copy(), x.copy()
+        xp[k] += eps
+        xm[k] -= eps
+        fd[k] = ((oracle.skin_joints(h, xp) - oracle.skin_joints(h, xm)) * dJ).sum() / (2 * eps)
+    assert np.allclose(g, fd, rtol=1e-6, atol=1e-9 * np.abs(fd).max())
+
+
+def test_joint_prior_smooth_l1():
+    """f_2: quadratic inside gamma, linear outside, continuous with a continuous
+    derivative at |x - y| = gamma; gradient = central differences."""
+    gamma, lam = 0.005, 1e-3
+    t = np.zeros((1, 3))
+    for d, expect in ((0.002, 0.5 * 0.002 ** 2 / gamma), (0.008, 0.008 - 0.5 * gamma), (-0.008, 0.008 - 0.5 * gamma)):
+        E, _ = oracle.joint_prior(np.array([[d, 0.0, 0.0]]), t, gamma, lam)
+        assert abs(E - lam * expect) <= 1e-15
+    a, _ = oracle.joint_prior(np.array([[gamma - 1e-9, 0, 0]]), t, gamma, 1.0)
+    b, _ = oracle.joint_prior(np.array([[gamma + 1e-9, 0, 0]]), t, gamma, 1.0)
+    assert abs(a - b) < 1e-8
+    rng = np.random.default_rng(4)
+    y = rng.normal(0, 0.006, (16, 3))
+    x = rng.normal(0, 0.006, (16, 3))
+    E, g = oracle.joint_prior(y, x, gamma, lam)
+    for idx in [(0, 0), (3, 1), (9, 2), (15, 0)]:
+        yp, ym = y.copy(), y.copy()
+        yp[idx] += 1e-9
+        ym[idx] -= 1e-9
+        fd = (oracle.joint_prior(yp, x, gamma, lam)[0] - oracle.joint_prior(ym, x, gamma, lam)[0]) / 2e-9
+        assert abs(fd - g[idx]) <= 1e-6 * max(abs(g[idx]), 1e-6)
