@@ -421,3 +421,154 @@ def autotune(ctx: B.Context, run, key: str, reps=3, space=TUNING_SPACE, cache=Tr
         except OSError:
             pass
     return best, start_ms, best_ms
+
+
+# --------------------------------------------------------------------------------------
+# The paper's full objective with its optimisation schedule
+# --------------------------------------------------------------------------------------
+
+class PaperRefiner:
+    """Refinement of geometry, colour map and per-camera colour transforms (Section 3:
+    E = E_1(dh, c, T) + lambda E_2(dh) with the colour-difference data term; the
+    edge-detection term D_e is not included) with the schedule of Section 3.3: a
+    warm-up in which only T and V_low move, then all of (dh, c, T).
+
+    One iteration: hr_skin_joints -> hr_joint_prior (target: the joints of the initial
+    estimate) -> hr_update_bvh -> hr_colour_map -> hr_render_fwd (texture V(c)) ->
+    hr_loss_ct (T) -> hr_render_bwd (vertex and texture gradients) -> hr_colour_map_bwd
+    -> hr_skin_bwd_joints -> hr_adam_step_dev over the whole parameter vector
+    [h (61) | T (N x 9) | V_low | V_high], with per-entry step sizes (zero for the
+    parameters a phase keeps fixed).  Both phases are captured as CUDA graphs."""
+
+    def __init__(self, model: B.Model, views: Views, cfg: I.SceneConfig, tex_size=512, low_size=8, gamma=0.005,
+                 weight=1e-3, lr_groups=LR_GROUPS, lr_T=0.01, lr_low=0.02, lr_high=0.01, ref_verts=None,
+                 max_iters=1024, ctx=None, device="cuda"):
+        hand = model.hand
+        N = views.N
+        self.model, self.views, self.cfg = model, views, cfg
+        self.ctx = ctx or B.Context(hand.V, hand.F, hand.E, N, views.W, views.H)
+        self.gamma, self.weight = gamma, weight
+        self.S, self.Sl = tex_size, low_size
+        nJ = hand.j_template.shape[0]
+        self.o_h, self.o_T = 0, 61
+        self.o_lo = self.o_T + 9 * N
+        self.o_hi = self.o_lo + 3 * low_size * low_size
+        self.n = self.o_hi + 3 * tex_size * tex_size
+        f = lambda *shape: torch.zeros(shape, device=device)
+        self.p, self.g, self.m1, self.m2 = f(self.n), f(self.n), f(self.n), f(self.n)
+        self.verts, self.d_verts = f(hand.V, 3), f(hand.V, 3)
+        self.joints, self.d_joints, self.target = f(nJ, 3), f(nJ, 3), f(nJ, 3)
+        self.tex = f(tex_size, tex_size, 3)
+        self.image, self.adjoint = f(N, views.H, views.W, 3), f(N, views.H, views.W, 3)
+        self.loss, self.prior = f(1), f(1)
+        self.counter = torch.zeros(1, dtype=torch.int32, device=device)
+        self.opts = opts_for(cfg, iter_dev=self.counter, texture=self.tex,
+                             d_texture=self.g[self.o_hi:].view(tex_size, tex_size, 3))
+        self.ref_verts = ref_verts
+        self.err = torch.full((max_iters, 1), float("nan"), device=device)
+        base = np.zeros(self.n, np.float32)
+        base[:61] = lr_scale_vector(lr_groups, "cpu").numpy()
+        base[self.o_T:self.o_lo] = lr_T
+        base[self.o_lo:self.o_hi] = lr_low
+        base[self.o_hi:] = lr_high
+        warm = base.copy()
+        warm[:61] = 0.0
+        warm[self.o_hi:] = 0.0
+        self.scale_warm = torch.as_tensor(warm, device=device)
+        self.scale_main = torch.as_tensor(base, device=device)
+        self.graphs = {}
+
+    # views of the parameter vector
+    def h(self):
+        return self.p[:61]
+
+    def T(self):
+        return self.p[self.o_T:self.o_lo].view(-1, 9)
+
+    def reset(self, h0, v_low=0.5):
+        """Start from estimate h0, identity transforms, a flat low map and no detail;
+        the prior's target is h0's joints."""
+        self.p.zero_()
+        self.p[:61].copy_(torch.as_tensor(np.asarray(h0, np.float32), device=self.p.device))
+        self.T().copy_(torch.eye(3, device=self.p.device).reshape(1, 9).expand(self.views.N, 9))
+        self.p[self.o_lo:self.o_hi].fill_(v_low)
+        self.m1.zero_()
+        self.m2.zero_()
+        self.counter.zero_()
+        self.err.fill_(float("nan"))
+        B.hr_skin_joints(self.ctx, self.model, self.h(), self.verts, self.target)
+
+    def iteration(self, scale, stream=None):
+        ctx, m, v = self.ctx, self.model, self.views
+        S, Sl = self.S, self.Sl
+        B.hr_skin_joints(ctx, m, self.h(), self.verts, self.joints, stream)
+        if self.ref_verts is not None:
+            B.hr_vertex_error(self.verts, self.ref_verts, self.err, self.counter, stream)
+        B.hr_joint_prior(self.joints, self.target, self.gamma, self.weight, self.prior, self.d_joints, stream)
+        B.hr_update_bvh(ctx, m, self.verts, self.counter, REBUILD_EVERY, stream)
+        lo = self.p[self.o_lo:self.o_hi].view(Sl, Sl, 3)
+        hi = self.p[self.o_hi:].view(S, S, 3)
+        B.hr_colour_map(lo, hi, self.tex, stream)
+        B.hr_render_fwd(ctx, m, self.verts, v.cams, v.H, v.W, v.background, self.opts, self.image, stream)
+        B.hr_loss_ct(ctx, self.image, v.observed, v.mask, self.T(), self.loss, self.adjoint,
+                     self.g[self.o_T:self.o_lo].view(-1, 9), stream)
+        self.g[self.o_hi:].zero_()   # the texture gradient accumulates
+        B.hr_render_bwd(ctx, m, self.verts, v.cams, v.H, v.W, v.background, self.opts, self.adjoint, self.d_verts,
+                        stream)
+        B.hr_colour_map_bwd(self.g[self.o_hi:].view(S, S, 3), self.g[self.o_lo:self.o_hi].view(Sl, Sl, 3), stream)
+        B.hr_skin_bwd_joints(ctx, m, self.h(), self.d_verts, self.d_joints, self.g[:61], stream)
+        B.hr_adam_step_dev(self.p, self.g, self.m1, self.m2, 1.0, 0.9, 0.999, 1e-8, self.counter, lr_scale=scale,
+                           stream=stream)
+
+    def capture(self):
+        """Graphs of a warm-up and a main iteration (state restored afterwards)."""
+        saved = [t.clone() for t in (self.p, self.m1, self.m2, self.counter)]
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        for name, sc in (("warm", self.scale_warm), ("main", self.scale_main)):
+            with torch.cuda.stream(s):
+                self.iteration(sc, s)
+            torch.cuda.current_stream().wait_stream(s)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                self.iteration(sc, s)
+            self.graphs[name] = g
+        for t, v in zip((self.p, self.m1, self.m2, self.counter), saved):
+            t.copy_(v)
+        return self.graphs
+
+    def run(self, warm=50, main=150):
+        """The schedule of Section 3.3 (50 warm-up + 150 iterations by default)."""
+        if not self.graphs:
+            self.capture()
+        for _ in range(warm):
+            self.graphs["warm"].replay()
+        for _ in range(main):
+            self.graphs["main"].replay()
+
+
+def make_paper_views(cfg: I.SceneConfig, model: B.Model, x_gt, tex_gt, T_gt, device="cuda", ctx=None):
+    """Observations for the full objective: the ground truth rendered with the colour
+    map tex_gt ([S][S][3]) at cfg.obs_spp, every pixel of camera i's image transformed
+    by its T_gt[i] ([N][3][3], near identity: the camera's colour response, which the
+    data term models as T_i R), plus noise; mask as in make_views."""
+    hand = model.hand
+    cams = torch.as_tensor(I.pack_cameras(I.make_cameras(cfg, hand.v_template.mean(0))), device=device)
+    bg_np = I.background(cfg.seed, cfg.views, cfg.height, cfg.width)
+    bg = torch.as_tensor(bg_np, device=device)
+    N, H, W = cfg.views, cfg.height, cfg.width
+    ctx = ctx or B.Context(hand.V, hand.F, hand.E, N, W, H)
+    verts = torch.empty((hand.V, 3), device=device)
+    B.hr_skin(ctx, model, torch.as_tensor(np.asarray(x_gt, np.float32), device=device), verts)
+    B.hr_build_bvh(ctx, model, verts)
+    clean = torch.empty((N, H, W, 3), device=device)
+    tex = torch.as_tensor(np.asarray(tex_gt, np.float32), device=device)
+    B.hr_render_fwd(ctx, model, verts, cams, H, W, bg, opts_for(cfg, spp=cfg.obs_spp, seed=cfg.seed * 7919 + 1,
+                                                                texture=tex), clean)
+    clean_np = clean.cpu().numpy()
+    Tt = np.asarray(T_gt, np.float64)
+    coloured = np.einsum("nij,nhwj->nhwi", Tt, clean_np).astype(np.float32)
+    obs = I.add_noise(coloured, cfg.seed, cfg.noise_sigma)
+    mask = I.coverage_mask(clean_np, bg_np, cfg.mask_dilate_px)
+    return Views(cams=cams, background=bg, observed=torch.as_tensor(obs, device=device),
+                 mask=torch.as_tensor(mask, device=device), H=H, W=W)
