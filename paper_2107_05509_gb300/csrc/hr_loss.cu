@@ -10,6 +10,8 @@
 // pointers are 16-byte aligned.  A batch reduces every instance separately (its own
 // mean over its own masked pixels): grid row blockIdx.y is instance y, whose pixels
 // are one contiguous range, with its own partials and last-block counters.
+#include <algorithm>
+
 #include "hr_internal.h"
 
 namespace hr {
@@ -195,12 +197,15 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 
 // one block: bias corrections from the device step counter, then the counter
 // advances; entry i steps by lr * lr_scale[i % scale_len] when a scale is given
+// Grid-stride over the entries.  A one-block launch also advances the counter; a
+// multi-block launch leaves that to k_counter_advance, launched after it on the same
+// stream (no block may advance it while another still reads it).
 __global__ void k_adam_dev(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
                            const float* __restrict__ lr_scale, int scale_len, uint32_t* __restrict__ iter_dev) {
   const float step = (float)(*iter_dev + 1u);
   const float c1 = 1.0f - powf(b1, step), c2 = 1.0f - powf(b2, step);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float gi = g[i];
     float mi = b1 * m[i] + (1.0f - b1) * gi;
     float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -209,9 +214,13 @@ __global__ void k_adam_dev(float* __restrict__ p, const float* __restrict__ g, f
     const float li = lr_scale ? lr * lr_scale[i % scale_len] : lr;
     p[i] -= li * (mi / c1) / (sqrtf(vi / c2) + eps);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) *iter_dev += 1u;
+  if (gridDim.x == 1) {
+    __syncthreads();
+    if (threadIdx.x == 0) *iter_dev += 1u;
+  }
 }
+
+__global__ void k_counter_advance(uint32_t* iter_dev) { *iter_dev += 1u; }
 
 // epsilon_v of instance blockIdx.x: mean over vertices of |verts - ref| (metres),
 // summed in a fixed order, into out[row][instance] with row = *iter_dev (row 0 when
@@ -432,8 +441,16 @@ __global__ void __launch_bounds__(256) k_colour_low_grad(const float* __restrict
 
 int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
                     const float* lr_scale, int scale_len, uint32_t* iter_dev, cudaStream_t s) {
-  k_adam_dev<<<1, 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, lr_scale, scale_len, iter_dev);
+  // one block up to 16 entries per thread (the pose vector of one or a few
+  // instances), else enough blocks to stream the five arrays at memory speed
+  constexpr int kThreads = 256;
+  const int blocks = n <= 16 * kThreads ? 1 : (int)std::min<long long>((n + kThreads - 1) / kThreads, 152LL * 8);
+  k_adam_dev<<<blocks, kThreads, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, lr_scale, scale_len, iter_dev);
   HR_CHECK_LAUNCH();
+  if (blocks > 1) {
+    k_counter_advance<<<1, 1, 0, s>>>(iter_dev);
+    HR_CHECK_LAUNCH();
+  }
   return HR_OK;
 }
 

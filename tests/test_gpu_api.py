@@ -45,12 +45,13 @@ def test_iter_dev_matches_host_iter(B):
     assert B.hr_get_status(ctx) == B.HR_OK
 
 
-def test_adam_step_dev_matches_host_step_and_advances(B):
+@pytest.mark.parametrize("n", [61, 786757])   # one block; many blocks and a separate counter advance
+def test_adam_step_dev_matches_host_step_and_advances(B, n):
     rng = np.random.default_rng(0)
-    p0 = rng.normal(size=61).astype(np.float32)
-    gr = rng.normal(size=61).astype(np.float32)
+    p0 = rng.normal(size=n).astype(np.float32)
+    gr = rng.normal(size=n).astype(np.float32)
     pa, pb = _t(p0), _t(p0)
-    ma, va, mb, vb = (torch.zeros(61, device="cuda") for _ in range(4))
+    ma, va, mb, vb = (torch.zeros(n, device="cuda") for _ in range(4))
     g = _t(gr)
     counter = torch.zeros(1, dtype=torch.int32, device="cuda")
     for step in range(1, 4):
