@@ -250,6 +250,39 @@ int hr_loss(hr_context* ctx, const float* image, const float* observed, const ui
 int hr_loss_ct(hr_context* ctx, const float* image, const float* observed, const uint8_t* mask, const float* T,
                int N, int H, int W, float* loss, float* adjoint, float* dT, hr_stream stream);
 
+/* The edge term D_e of the data term (Eq. 4): |Canny(o) * K - Canny(r) * K| with K the
+ * 11 x 11 Gaussian of sigma 5 (zero padding), r = T_i R the colour-transformed render
+ * of camera i (Eq. 2).  Canny's detector, per view: luma g = a . R with a = T_i^T w,
+ * w = (0.299, 0.587, 0.114); 5-tap Gaussian of sigma 1 along x then y; Sobel / 8
+ * ((1/4, 1/2, 1/4) smoothing, (-1/2, 0, 1/2) differences); m = sqrt(gx^2 + gy^2 +
+ * 1e-12); non-maximum suppression along the gradient direction quantised to 0, 45, 90
+ * or 135 degrees (a pixel survives when m >= m at both neighbours, coordinates clamped);
+ * candidates m > low, strong m > high; hysteresis keeps the candidates 8-connected
+ * through candidates to a strong pixel.  The detector's passes replicate the image
+ * border.  Canny(x) is m on the kept pixels and 0 elsewhere: the selection is
+ * piecewise constant, so the derivative flows through m with the selection fixed.
+ * Everything up to the blurred map is float32 with one rounding per multiply and per
+ * add, taps summed from the most negative offset up (the selection and the loss's
+ * signs are reproducible decisions).
+ *
+ * hr_edges writes Canny(T R) * K (device float[N][H][W]; T device float[N][9]
+ * row-major or NULL for none): the observation's map, computed once.
+ * hr_edge_loss evaluates, for edges_obs = hr_edges of the observation,
+ *   L_e = weight sum_p M_p |E_r - E_o| / sum_p M_p  (into loss, device float[1];
+ *         0 without masked pixels),
+ * ADDS dL_e/dR into adjoint (device float[N][H][W][3]) and, when dT is not NULL,
+ * dL_e/dT into dT (device float[N][9]).  Call it after hr_loss_ct, which overwrites
+ * both, to form the whole data term.  The per-pixel scratch (23 bytes per pixel of
+ * the context's maximum image stack) is allocated by the first edge call on a
+ * context, so make that call outside stream capture.  Single-instance contexts;
+ * N H W <= INT_MAX; 0 <= low <= high, finite.  A union-find that ran past its bound
+ * reports HR_ERR_LIMIT through hr_get_status. */
+int hr_edges(hr_context* ctx, const float* image, const float* T, int N, int H, int W, float low, float high,
+             float* edges, hr_stream stream);
+int hr_edge_loss(hr_context* ctx, const float* image, const float* T, const float* edges_obs, const uint8_t* mask,
+                 int N, int H, int W, float low, float high, float weight, float* loss, float* adjoint, float* dT,
+                 hr_stream stream);
+
 /* Backward of hr_render_fwd for adjoint image A = dL/dR (Section 1 and Section 3.1:
  * the ray tracer of Li et al. 2018 handles visibility discontinuities in the
  * backward pass).  d_verts (device float[V][3], overwritten) is the sum of

@@ -16,8 +16,8 @@ T_i R.  Canny's detector (Canny 1986) is taken as its textbook steps:
   NMS    the gradient direction quantised to 0, 45, 90 or 135 degrees
          (|gy| <= tan(22.5) |gx|: along x; |gy| >= tan(67.5) |gx|: along y; else the
          diagonal with gx gy > 0 (x+1, y+1)/(x-1, y-1), or the other one); a pixel
-         survives when m >= m at both neighbours along that direction (a neighbour
-         outside the image is the pixel itself)
+         survives when m >= m at both neighbours along that direction (neighbour
+         coordinates clamped to the image, each on its own)
   double threshold: candidates = survivors with m > low; strong = m > high
   hysteresis: a candidate is kept when its 8-connected component of candidates
          holds a strong pixel

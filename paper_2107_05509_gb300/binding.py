@@ -43,7 +43,8 @@ EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", 
            "hr_net_get_params", "hr_net_inputs", "hr_net_set_inputs_bf16", "hr_net_forward", "hr_net_backward",
            "hr_net_adam", "hr_net_status", "hr_vertex_mse", "hr_add_noise", "hr_select_best", "hr_update_bvh",
            "hr_set_tuning", "hr_get_tuning", "hr_loss_ct",
-           "hr_skin_joints", "hr_skin_bwd_joints", "hr_joint_prior", "hr_colour_map", "hr_colour_map_bwd")
+           "hr_skin_joints", "hr_skin_bwd_joints", "hr_joint_prior", "hr_colour_map", "hr_colour_map_bwd",
+           "hr_edges", "hr_edge_loss")
 
 
 class HandrtError(RuntimeError):
@@ -110,6 +111,8 @@ def lib():
             "hr_joint_prior": [P, P, I, I, F, F, P, P, P],
             "hr_colour_map": [P, I, I, P, I, I, P, P],
             "hr_colour_map_bwd": [P, I, I, I, I, P, P],
+            "hr_edges": [P, P, P, I, I, I, F, F, P, P],
+            "hr_edge_loss": [P, P, P, P, P, I, I, I, F, F, F, P, P, P, P],
             "hr_get_tuning": [P, P],
             "hr_render_fwd": [P, P, P, P, I, I, I, P, P, P, P],
             "hr_loss": [P, P, P, P, I, I, I, P, P, P],
@@ -396,6 +399,31 @@ def hr_loss_ct(ctx, image, observed, mask, T, loss, adjoint, dT=None, stream=Non
     _check("hr_loss_ct", lib().hr_loss_ct(ctx.handle, _f32(image), _f32(observed), _ptr(mask),
                                           None if T is None else _f32(T), N, H, W, _f32(loss), _f32(adjoint),
                                           None if dT is None else _f32(dT), _stream(stream)))
+
+
+# thresholds of the edge detector on the /8-normalised gradient magnitude (a step of
+# contrast c peaks near 0.32 c)
+EDGE_LOW, EDGE_HIGH = 0.05, 0.1
+
+
+def hr_edges(ctx, image, edges, T=None, low=EDGE_LOW, high=EDGE_HIGH, stream=None):
+    """Canny(T R) * K per view (the edge term's blurred edge map): image [N][H][W][3],
+    edges [N][H][W], T [N][9] or None."""
+    N, H, W = edges.shape
+    _check("hr_edges", lib().hr_edges(ctx.handle, _f32(image), None if T is None else _f32(T), N, H, W, float(low),
+                                      float(high), _f32(edges), _stream(stream)))
+
+
+def hr_edge_loss(ctx, image, edges_obs, mask, loss, adjoint, T=None, dT=None, weight=1.0, low=EDGE_LOW,
+                 high=EDGE_HIGH, stream=None):
+    """L_e = weight sum M |E_r - E_o| / sum M into loss; ADDS dL_e/dR into adjoint and
+    dL_e/dT into dT."""
+    N, H, W = mask.shape
+    assert mask.dtype == torch.uint8
+    _check("hr_edge_loss", lib().hr_edge_loss(ctx.handle, _f32(image), None if T is None else _f32(T),
+                                              _f32(edges_obs), _ptr(mask), N, H, W, float(low), float(high),
+                                              float(weight), _f32(loss), _f32(adjoint),
+                                              None if dT is None else _f32(dT), _stream(stream)))
 
 
 def hr_render_bwd(ctx, model, verts, cams, H, W, background, opts, adjoint, d_verts, stream=None):

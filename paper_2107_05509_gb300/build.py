@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhandrt.so")
-SOURCES = ["hr_api.cu", "hr_bvh.cu", "hr_render.cu", "hr_skin.cu", "hr_loss.cu", "hr_gemm.cu", "hr_net.cu"]
+SOURCES = ["hr_api.cu", "hr_bvh.cu", "hr_render.cu", "hr_skin.cu", "hr_loss.cu", "hr_gemm.cu", "hr_net.cu", "hr_edge.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

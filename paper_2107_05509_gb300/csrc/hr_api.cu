@@ -3,6 +3,8 @@
 // throws; device-side errors go to the context's status word.
 #include <cstdlib>
 #include <algorithm>
+#include <climits>
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -31,6 +33,7 @@ bool dev_alloc(T** p, size_t count, Alloc& list) {
 }
 
 void free_ctx(Context* c) {
+  hr::free_edge_buffers(c);
   for (int i = 0; i < 2 * hr::kTimeSlots; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   void* ptrs[] = {c->nodes,   c->tris,    c->normals,   c->normal_len, c->partials,      c->dN,
@@ -338,6 +341,33 @@ int hr_loss_ct(hr_context* ctx, const float* image, const float* observed, const
     return HR_ERR_ARG;
   return hr::launch_loss_ct(c, image, observed, mask, T, N, (long long)H * W, loss, adjoint, dT,
                             (cudaStream_t)stream);
+}
+
+static bool edge_args_ok(const Context* c, int N, int H, int W, float low, float high) {
+  return c && !c->vt && image_ok(c, N, H, W) && (long long)N * H * W <= INT_MAX && std::isfinite(low) &&
+         std::isfinite(high) && low >= 0.0f && high >= low;
+}
+
+int hr_edges(hr_context* ctx, const float* image, const float* T, int N, int H, int W, float low, float high,
+             float* edges, hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!edge_args_ok(c, N, H, W, low, high) || !image || !edges) return HR_ERR_ARG;
+  const int rc = hr::edge_buffers(c);
+  if (rc != HR_OK) return rc;
+  return hr::launch_edges(c, image, T, N, H, W, low, high, edges, (cudaStream_t)stream);
+}
+
+int hr_edge_loss(hr_context* ctx, const float* image, const float* T, const float* edges_obs, const uint8_t* mask,
+                 int N, int H, int W, float low, float high, float weight, float* loss, float* adjoint, float* dT,
+                 hr_stream stream) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!edge_args_ok(c, N, H, W, low, high) || !image || !edges_obs || !mask || !loss || !adjoint ||
+      !std::isfinite(weight))
+    return HR_ERR_ARG;
+  const int rc = hr::edge_buffers(c);
+  if (rc != HR_OK) return rc;
+  return hr::launch_edge_loss(c, image, T, edges_obs, mask, N, H, W, low, high, weight, loss, adjoint, dT,
+                              (cudaStream_t)stream);
 }
 
 int hr_render_bwd(hr_context* ctx, const hr_model* model, const float* verts, const hr_camera* cams, int N, int H,

@@ -129,6 +129,16 @@ struct Context {
   unsigned int* counters;// [n_inst][4] last-block counters (mask count, loss, skin adjoint)
   // skin scratch
   float* skin_partials;  // [n_inst][kSkinBlocks][kSkinAcc]
+  // edge-term scratch (single-instance contexts; allocated by the first edge call),
+  // per pixel of max_views x max_height x max_width
+  float2* edge_gxy;      // Sobel gradient of the last detector run
+  float2* edge_gbar;     // adjoint of the gradient
+  int* edge_parent;      // union-find parents of the candidates (-1 elsewhere)
+  uint8_t* edge_cls;     // bit 0 candidate, bit 1 strong
+  uint8_t* edge_flag;    // a component root holding a strong pixel
+  int8_t* edge_gs;       // M sign(E_hat_r - E_hat_o)
+  float4* edge_part;     // per-tile partial sums
+  float* edge_scale;     // weight / sum M of the last edge loss
   // kernel timing (HR_TIMING): events around the render kernels of the last call
   cudaEvent_t ev[32];          // >= 2 * kTimeSlots
   int ev_ready;

@@ -30,6 +30,14 @@ int launch_loss(Context* ctx, const float* image, const float* obs, const uint8_
                 float* loss, float* adjoint, cudaStream_t s);
 int launch_loss_ct(Context* ctx, const float* image, const float* obs, const uint8_t* mask, const float* T, int N,
                    long long HW, float* loss, float* adjoint, float* dT, cudaStream_t s);
+// the edge term D_e (hr_edge.cu); edge_buffers allocates the context's scratch once
+int edge_buffers(Context* c);
+void free_edge_buffers(Context* c);
+int launch_edges(Context* c, const float* image, const float* T, int N, int H, int W, float low, float high,
+                 float* edges, cudaStream_t s);
+int launch_edge_loss(Context* c, const float* image, const float* T, const float* edges_obs, const uint8_t* mask,
+                     int N, int H, int W, float low, float high, float weight, float* loss, float* adjoint,
+                     float* dT, cudaStream_t s);
 int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
                 int step, cudaStream_t s);
 int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,

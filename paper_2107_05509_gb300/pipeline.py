@@ -429,20 +429,21 @@ def autotune(ctx: B.Context, run, key: str, reps=3, space=TUNING_SPACE, cache=Tr
 
 class PaperRefiner:
     """Refinement of geometry, colour map and per-camera colour transforms (Section 3:
-    E = E_1(dh, c, T) + lambda E_2(dh) with the colour-difference data term; the
-    edge-detection term D_e is not included) with the schedule of Section 3.3: a
-    warm-up in which only T and V_low move, then all of (dh, c, T).
+    E = E_1(dh, c, T) + lambda E_2(dh), the data term f_1 = D_c + edge_weight D_e of
+    Eq. 4) with the schedule of Section 3.3: a warm-up in which only T and V_low move,
+    then all of (dh, c, T).
 
     One iteration: hr_skin_joints -> hr_joint_prior (target: the joints of the initial
     estimate) -> hr_update_bvh -> hr_colour_map -> hr_render_fwd (texture V(c)) ->
-    hr_loss_ct (T) -> hr_render_bwd (vertex and texture gradients) -> hr_colour_map_bwd
-    -> hr_skin_bwd_joints -> hr_adam_step_dev over the whole parameter vector
+    hr_loss_ct (D_c with T) -> hr_edge_loss (D_e, adding to the same adjoint and dT) ->
+    hr_render_bwd (vertex and texture gradients) -> hr_colour_map_bwd ->
+    hr_skin_bwd_joints -> hr_adam_step_dev over the whole parameter vector
     [h (61) | T (N x 9) | V_low | V_high], with per-entry step sizes (zero for the
     parameters a phase keeps fixed).  Both phases are captured as CUDA graphs."""
 
     def __init__(self, model: B.Model, views: Views, cfg: I.SceneConfig, tex_size=512, low_size=8, gamma=0.005,
                  weight=1e-3, lr_groups=LR_GROUPS, lr_T=0.01, lr_low=0.02, lr_high=0.01, ref_verts=None,
-                 max_iters=1024, ctx=None, device="cuda"):
+                 max_iters=1024, ctx=None, device="cuda", edge_weight=1.0):
         hand = model.hand
         N = views.N
         self.model, self.views, self.cfg = model, views, cfg
@@ -460,7 +461,13 @@ class PaperRefiner:
         self.joints, self.d_joints, self.target = f(nJ, 3), f(nJ, 3), f(nJ, 3)
         self.tex = f(tex_size, tex_size, 3)
         self.image, self.adjoint = f(N, views.H, views.W, 3), f(N, views.H, views.W, 3)
-        self.loss, self.prior = f(1), f(1)
+        self.loss, self.prior, self.edge_loss = f(1), f(1), f(1)
+        self.edge_weight = float(edge_weight)
+        self.edges_obs = f(N, views.H, views.W)
+        if self.edge_weight:
+            # the observation's blurred edge map, once (this first edge call also
+            # allocates the context's edge scratch, outside any graph capture)
+            B.hr_edges(self.ctx, views.observed, self.edges_obs)
         self.counter = torch.zeros(1, dtype=torch.int32, device=device)
         self.opts = opts_for(cfg, iter_dev=self.counter, texture=self.tex,
                              d_texture=self.g[self.o_hi:].view(tex_size, tex_size, 3))
@@ -512,6 +519,9 @@ class PaperRefiner:
         B.hr_render_fwd(ctx, m, self.verts, v.cams, v.H, v.W, v.background, self.opts, self.image, stream)
         B.hr_loss_ct(ctx, self.image, v.observed, v.mask, self.T(), self.loss, self.adjoint,
                      self.g[self.o_T:self.o_lo].view(-1, 9), stream)
+        if self.edge_weight:
+            B.hr_edge_loss(ctx, self.image, self.edges_obs, v.mask, self.edge_loss, self.adjoint, T=self.T(),
+                           dT=self.g[self.o_T:self.o_lo].view(-1, 9), weight=self.edge_weight, stream=stream)
         self.g[self.o_hi:].zero_()   # the texture gradient accumulates
         B.hr_render_bwd(ctx, m, self.verts, v.cams, v.H, v.W, v.background, self.opts, self.adjoint, self.d_verts,
                         stream)

@@ -1,5 +1,6 @@
-"""The paper's whole objective on the GPU (Section 3: the data term with per-camera
-colour transforms T_i and the two-level colour map, plus the joint prior E_2) under
+"""The paper's whole objective on the GPU (Section 3: the data term, colour
+differences and blurred Canny edge maps, with per-camera colour transforms T_i and
+the two-level colour map, plus the joint prior E_2) under
 its schedule (Section 3.3: a warm-up that moves only T and V_low, then everything).
 
 Observations: the ground-truth pose rendered with a smooth-noise colour map, every
@@ -61,6 +62,7 @@ def test_warmup_then_full_refinement():
     assert err[-1] < 0.6 * err[0], (err[0], err[49], err[-1])
     assert np.allclose(err[:50], err[0])   # geometry fixed during the warm-up
     assert int(pr.counter.item()) == 200
+    assert np.isfinite(float(pr.edge_loss.item())) and float(pr.edge_loss.item()) > 0
     assert B.hr_get_status(ctx) == B.HR_OK
     print(f"T err {T0:.4f} -> {T1:.4f}; loss {loss_first:.5f} -> {loss_warm:.5f} -> {loss_main:.5f}; "
           f"eps_v {err[0]:.3f} -> {err[-1]:.3f} mm")
