@@ -18,10 +18,13 @@
 // and the sign of E_hat_r - E_hat_o are decisions.  Kernels:
 //   k_canny      32 x 8 output tiles: luma, smoothing, Sobel, magnitude and
 //                suppression in shared memory (4-pixel halo); writes (gx, gy), the
-//                candidate/strong bits and the union-find parents
-//   k_cc_union   every candidate joins its W, NW, N, NE candidate neighbours
-//                (lock-free union by atomicMin on roots; parents only decrease)
-//   k_cc_flag    strong pixels mark their component's root
+//                candidate/strong bits, and union-find parents after joining the
+//                tile's candidates in shared memory
+//   k_cc_border  candidates on tile borders join their W, NW, N, NE candidate
+//                neighbours in other tiles (lock-free union by atomicMin on roots;
+//                parents only decrease)
+//   k_cc_flag    every candidate points at its root; strong pixels mark the root
+//                (kept = candidate whose root is marked: one hop afterwards)
 //   k_edge_blur  tiles with a 5-pixel halo: E from (gx, gy) on kept pixels, K along x
 //                then y; writes E_hat, or the loss's sign map and block partials
 //   k_edge_final block partials in a fixed order: loss and weight / sum M
@@ -124,8 +127,37 @@ __device__ void cc_unite(int* parent, int a, int b, int* status) {
   atomicOr(status, kStatusLimit);
 }
 
-__device__ __forceinline__ bool kept_pixel(const uint8_t* cls, const int* parent, const uint8_t* flag, int p) {
-  return (cls[p] & 1) && flag[cc_find(parent, p)];
+// a kept pixel: a candidate whose root holds a strong pixel (parents flattened)
+__device__ __forceinline__ bool kept(const uint8_t* cls, const int* parent, const uint8_t* flag, int p) {
+  return (cls[p] & 1) && flag[parent[p]];
+}
+
+// the same on a tile's labels in shared memory
+__device__ __forceinline__ int find_local(const int* lab, int x) {
+  const volatile int* v = lab;
+  int p = v[x];
+  while (p != x) {
+    x = p;
+    p = v[x];
+  }
+  return x;
+}
+
+__device__ void unite_local(int* lab, int a, int b, int* status) {
+  for (int it = 0; it < kUnionIters; ++it) {
+    a = find_local(lab, a);
+    b = find_local(lab, b);
+    if (a == b) return;
+    if (a > b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    const int old = atomicMin(lab + b, a);
+    if (old == b) return;
+    b = old;
+  }
+  atomicOr(status, kStatusLimit);
 }
 
 // ---- the detector on one 32 x 8 tile.  Shared-memory stages and the global
@@ -137,128 +169,195 @@ __device__ __forceinline__ bool kept_pixel(const uint8_t* cls, const int* parent
 //   v  (S, y)   x0-2 .. x0+33, y0-1 .. y0+8      gx = D_x v
 //   u  (S, x)   x0-1 .. x0+32, y0-2 .. y0+9      gy = D_y u
 //   gx, gy, m   x0-1 .. x0+32, y0-1 .. y0+8
-__global__ void __launch_bounds__(kEThreads) k_canny(const float* __restrict__ image, const float* __restrict__ T,
-                                                     int H, int W, EdgeW w, float2* __restrict__ gxy,
-                                                     uint8_t* __restrict__ cls, uint8_t* __restrict__ flag,
-                                                     int* __restrict__ parent) {
+struct CannySmem {
+  float sl[kTY + 8][kTX + 8];
+  float sh[kTY + 8][kTX + 4];
+  float ss[kTY + 4][kTX + 4];
+  float sv[kTY + 2][kTX + 4];
+  float su[kTY + 4][kTX + 2];
+  float sgx[kTY + 2][kTX + 2], sgy[kTY + 2][kTX + 2], sm[kTY + 2][kTX + 2];
+  int lab[kEThreads];
+};
+
+// INNER: the tile's 4-pixel halo lies inside the image, so no coordinate needs a
+// clamp or a bounds check (the same arithmetic as the general path, fewer
+// instructions)
+template <bool INNER>
+__device__ __forceinline__ void canny_tile(CannySmem& S, const float* __restrict__ img, float3 a, int view, int x0,
+                                           int y0, int H, int W, const EdgeW& w, float2* __restrict__ gxy,
+                                           uint8_t* __restrict__ cls, uint8_t* __restrict__ flag,
+                                           int* __restrict__ parent, int* status) {
   constexpr int LX = kTX + 8, LY = kTY + 8;
   constexpr int HX = kTX + 4, HY = kTY + 8;
   constexpr int SX = kTX + 4, SY = kTY + 4;
   constexpr int VX = kTX + 4, VY = kTY + 2;
   constexpr int UX = kTX + 2, UY = kTY + 4;
   constexpr int MX = kTX + 2, MY = kTY + 2;
-  __shared__ float sl[LY][LX], sh[HY][HX], ss[SY][SX], sv[VY][VX], su[UY][UX];
-  __shared__ float sgx[MY][MX], sgy[MY][MX], sm[MY][MX];
-  const int view = blockIdx.z, x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, tid = threadIdx.x;
-  const float3 a = luma_weights(T, view, w);
-  const float* img = image + (size_t)view * H * W * 3;
+  const int tid = threadIdx.x;
+  auto cx = [&](int x) { return INNER ? x : clampi(x, 0, W - 1); };
+  auto cy = [&](int y) { return INNER ? y : clampi(y, 0, H - 1); };
+  auto outside = [&](int x, int y) { return !INNER && (x < 0 || x >= W || y < 0 || y >= H); };
   for (int i = tid; i < LX * LY; i += kEThreads) {
     const int ry = i / LX, rx = i % LX, x = x0 - 4 + rx, y = y0 - 4 + ry;
-    if (x < 0 || x >= W || y < 0 || y >= H) continue;
+    if (outside(x, y)) continue;
     const float* px = img + ((size_t)y * W + x) * 3;
-    sl[ry][rx] = __fadd_rn(__fadd_rn(__fmul_rn(a.x, px[0]), __fmul_rn(a.y, px[1])), __fmul_rn(a.z, px[2]));
+    S.sl[ry][rx] = __fadd_rn(__fadd_rn(__fmul_rn(a.x, px[0]), __fmul_rn(a.y, px[1])), __fmul_rn(a.z, px[2]));
   }
   __syncthreads();
   for (int i = tid; i < HX * HY; i += kEThreads) {
     const int ry = i / HX, rx = i % HX, x = x0 - 2 + rx, y = y0 - 4 + ry;
-    if (x < 0 || x >= W || y < 0 || y >= H) continue;
+    if (outside(x, y)) continue;
     float acc = 0.0f;
 #pragma unroll
     for (int t = 0; t < 5; ++t) {
-      const float term = __fmul_rn(w.g5[t], sl[ry][clampi(x + t - 2, 0, W - 1) - (x0 - 4)]);
+      const float term = __fmul_rn(w.g5[t], S.sl[ry][cx(x + t - 2) - (x0 - 4)]);
       acc = t ? __fadd_rn(acc, term) : term;
     }
-    sh[ry][rx] = acc;
+    S.sh[ry][rx] = acc;
   }
   __syncthreads();
   for (int i = tid; i < SX * SY; i += kEThreads) {
     const int ry = i / SX, rx = i % SX, x = x0 - 2 + rx, y = y0 - 2 + ry;
-    if (x < 0 || x >= W || y < 0 || y >= H) continue;
+    if (outside(x, y)) continue;
     float acc = 0.0f;
 #pragma unroll
     for (int t = 0; t < 5; ++t) {
-      const float term = __fmul_rn(w.g5[t], sh[clampi(y + t - 2, 0, H - 1) - (y0 - 4)][rx]);
+      const float term = __fmul_rn(w.g5[t], S.sh[cy(y + t - 2) - (y0 - 4)][rx]);
       acc = t ? __fadd_rn(acc, term) : term;
     }
-    ss[ry][rx] = acc;
+    S.ss[ry][rx] = acc;
   }
   __syncthreads();
   for (int i = tid; i < VX * VY + UX * UY; i += kEThreads) {
     if (i < VX * VY) {
       const int ry = i / VX, rx = i % VX, x = x0 - 2 + rx, y = y0 - 1 + ry;
-      if (x < 0 || x >= W || y < 0 || y >= H) continue;
+      if (outside(x, y)) continue;
       float acc = 0.0f;
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
-        const float term = __fmul_rn(kSmooth[t], ss[clampi(y + t - 1, 0, H - 1) - (y0 - 2)][rx]);
+        const float term = __fmul_rn(kSmooth[t], S.ss[cy(y + t - 1) - (y0 - 2)][rx]);
         acc = t ? __fadd_rn(acc, term) : term;
       }
-      sv[ry][rx] = acc;
+      S.sv[ry][rx] = acc;
     } else {
       const int j = i - VX * VY, ry = j / UX, rx = j % UX, x = x0 - 1 + rx, y = y0 - 2 + ry;
-      if (x < 0 || x >= W || y < 0 || y >= H) continue;
+      if (outside(x, y)) continue;
       float acc = 0.0f;
 #pragma unroll
       for (int t = 0; t < 3; ++t) {
-        const float term = __fmul_rn(kSmooth[t], ss[ry][clampi(x + t - 1, 0, W - 1) - (x0 - 2)]);
+        const float term = __fmul_rn(kSmooth[t], S.ss[ry][cx(x + t - 1) - (x0 - 2)]);
         acc = t ? __fadd_rn(acc, term) : term;
       }
-      su[ry][rx] = acc;
+      S.su[ry][rx] = acc;
     }
   }
   __syncthreads();
   for (int i = tid; i < MX * MY; i += kEThreads) {
     const int ry = i / MX, rx = i % MX, x = x0 - 1 + rx, y = y0 - 1 + ry;
-    if (x < 0 || x >= W || y < 0 || y >= H) continue;
+    if (outside(x, y)) continue;
     float gx = 0.0f, gy = 0.0f;
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
-      const float tx = __fmul_rn(kDeriv[t], sv[ry][clampi(x + t - 1, 0, W - 1) - (x0 - 2)]);
-      const float ty = __fmul_rn(kDeriv[t], su[clampi(y + t - 1, 0, H - 1) - (y0 - 2)][rx]);
+      const float tx = __fmul_rn(kDeriv[t], S.sv[ry][cx(x + t - 1) - (x0 - 2)]);
+      const float ty = __fmul_rn(kDeriv[t], S.su[cy(y + t - 1) - (y0 - 2)][rx]);
       gx = t ? __fadd_rn(gx, tx) : tx;
       gy = t ? __fadd_rn(gy, ty) : ty;
     }
-    sgx[ry][rx] = gx;
-    sgy[ry][rx] = gy;
-    sm[ry][rx] = magnitude(gx, gy);
+    S.sgx[ry][rx] = gx;
+    S.sgy[ry][rx] = gy;
+    S.sm[ry][rx] = magnitude(gx, gy);
   }
   __syncthreads();
   const int tx = tid % kTX, ty = tid / kTX, x = x0 + tx, y = y0 + ty;
-  if (x >= W || y >= H) return;
-  const float gx = sgx[ty + 1][tx + 1], gy = sgy[ty + 1][tx + 1], m = sm[ty + 1][tx + 1];
-  const float ax = fabsf(gx), ay = fabsf(gy);
-  const bool along_x = ay <= __fmul_rn(w.t1, ax);
-  const bool along_y = !along_x && ay >= __fmul_rn(w.t2, ax);
-  const int dx = along_y ? 0 : 1;
-  const int dy = along_x ? 0 : (along_y ? 1 : (((gx > 0.0f) == (gy > 0.0f)) ? 1 : -1));
-  const float m1 = sm[clampi(y + dy, 0, H - 1) - (y0 - 1)][clampi(x + dx, 0, W - 1) - (x0 - 1)];
-  const float m2 = sm[clampi(y - dy, 0, H - 1) - (y0 - 1)][clampi(x - dx, 0, W - 1) - (x0 - 1)];
-  const bool cand = m >= m1 && m >= m2 && m > w.low;
-  const bool strong = cand && m > w.high;
-  const int p = (view * H + y) * W + x;
-  gxy[p] = make_float2(gx, gy);
-  cls[p] = (uint8_t)((cand ? 1 : 0) | (strong ? 2 : 0));
-  flag[p] = 0;
-  parent[p] = cand ? p : -1;
-}
-
-__global__ void k_cc_union(const uint8_t* __restrict__ cls, int* parent, int H, int W, int P, int* status) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    if (!(cls[p] & 1)) continue;
-    const int x = p % W, y = (p / W) % H;
-    if (x > 0 && (cls[p - 1] & 1)) cc_unite(parent, p, p - 1, status);
-    if (y > 0) {
-      const int q = p - W;
-      if (x > 0 && (cls[q - 1] & 1)) cc_unite(parent, p, q - 1, status);
-      if (cls[q] & 1) cc_unite(parent, p, q, status);
-      if (x + 1 < W && (cls[q + 1] & 1)) cc_unite(parent, p, q + 1, status);
+  const bool in = INNER || (x < W && y < H);
+  bool cand = false;
+  if (in) {
+    const float gx = S.sgx[ty + 1][tx + 1], gy = S.sgy[ty + 1][tx + 1], m = S.sm[ty + 1][tx + 1];
+    const float ax = fabsf(gx), ay = fabsf(gy);
+    const bool along_x = ay <= __fmul_rn(w.t1, ax);
+    const bool along_y = !along_x && ay >= __fmul_rn(w.t2, ax);
+    const int dx = along_y ? 0 : 1;
+    const int dy = along_x ? 0 : (along_y ? 1 : (((gx > 0.0f) == (gy > 0.0f)) ? 1 : -1));
+    const float m1 = S.sm[cy(y + dy) - (y0 - 1)][cx(x + dx) - (x0 - 1)];
+    const float m2 = S.sm[cy(y - dy) - (y0 - 1)][cx(x - dx) - (x0 - 1)];
+    cand = m >= m1 && m >= m2 && m > w.low;
+    const bool strong = cand && m > w.high;
+    const int p = (view * H + y) * W + x;
+    gxy[p] = make_float2(gx, gy);
+    cls[p] = (uint8_t)((cand ? 1 : 0) | (strong ? 2 : 0));
+    flag[p] = 0;
+  }
+  // the tile's candidates joined in shared memory (local index l = ty 32 + tx; a
+  // component's root is its smallest index, so a pixel's global parent, the root's
+  // global index, never exceeds its own)
+  int* lab = S.lab;
+  lab[tid] = cand ? tid : -1;
+  __syncthreads();
+  if (cand) {
+    if (tx > 0 && lab[tid - 1] >= 0) unite_local(lab, tid, tid - 1, status);
+    if (ty > 0) {
+      if (tx > 0 && lab[tid - kTX - 1] >= 0) unite_local(lab, tid, tid - kTX - 1, status);
+      if (lab[tid - kTX] >= 0) unite_local(lab, tid, tid - kTX, status);
+      if (tx + 1 < kTX && lab[tid - kTX + 1] >= 0) unite_local(lab, tid, tid - kTX + 1, status);
     }
+  }
+  __syncthreads();
+  if (in) {
+    int root = -1;
+    if (cand) {
+      const int r = find_local(lab, tid);
+      root = (view * H + y0 + r / kTX) * W + x0 + r % kTX;
+    }
+    parent[(view * H + y) * W + x] = root;
   }
 }
 
-__global__ void k_cc_flag(const uint8_t* __restrict__ cls, const int* parent, uint8_t* flag, int P) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-    if (cls[p] & 2) flag[cc_find(parent, p)] = 1;
+__global__ void __launch_bounds__(kEThreads) k_canny(const float* __restrict__ image, const float* __restrict__ T,
+                                                     int H, int W, EdgeW w, float2* __restrict__ gxy,
+                                                     uint8_t* __restrict__ cls, uint8_t* __restrict__ flag,
+                                                     int* __restrict__ parent, int* status) {
+  __shared__ CannySmem S;
+  const int view = blockIdx.z, x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const float3 a = luma_weights(T, view, w);
+  const float* img = image + (size_t)view * H * W * 3;
+  if (x0 >= 4 && x0 + kTX + 4 <= W && y0 >= 4 && y0 + kTY + 4 <= H)
+    canny_tile<true>(S, img, a, view, x0, y0, H, W, w, gxy, cls, flag, parent, status);
+  else
+    canny_tile<false>(S, img, a, view, x0, y0, H, W, w, gxy, cls, flag, parent, status);
+}
+
+// candidates on a tile's border join their candidate neighbours in other tiles (the
+// W, NW, N, NE neighbours that lie outside the tile), on the global forest
+__global__ void __launch_bounds__(kEThreads) k_cc_border(const uint8_t* __restrict__ cls, int* parent, int H, int W,
+                                                         int* status) {
+  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+  if (ty != 0 && tx != 0 && tx != kTX - 1) return;
+  const int view = blockIdx.z, x = blockIdx.x * kTX + tx, y = blockIdx.y * kTY + ty;
+  if (x >= W || y >= H) return;
+  const int p = (view * H + y) * W + x;
+  if (!(cls[p] & 1)) return;
+  // neighbour (x + ox, y + oy) for the four earlier neighbours, when outside the tile
+  const int ox[4] = {-1, -1, 0, 1}, oy[4] = {0, -1, -1, -1};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int nx = x + ox[k], ny = y + oy[k], ntx = tx + ox[k], nty = ty + oy[k];
+    if (nx < 0 || nx >= W || ny < 0) continue;
+    if (ntx >= 0 && ntx < kTX && nty >= 0) continue;   // inside the tile: joined already
+    const int q = (view * H + ny) * W + nx;
+    if (cls[q] & 1) cc_unite(parent, p, q, status);
+  }
+}
+
+// every candidate points at its root (flattening; a concurrent find reads either an
+// ancestor or the root), and strong pixels mark their root
+__global__ void k_cc_flag(const uint8_t* __restrict__ cls, int* parent, uint8_t* flag, int P) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const uint8_t c = cls[p];
+    if (!(c & 1)) continue;
+    const int r = cc_find(parent, p);
+    parent[p] = r;
+    if (c & 2) flag[r] = 1;
+  }
 }
 
 // fixed-order block sum (warp shuffles, then the warps in order); thread 0 holds the
@@ -286,7 +385,8 @@ __device__ __forceinline__ void block_sum(float (&v)[NV], float (*red)[kEThreads
 // E_hat = K_y K_x E on a tile (E from (gx, gy) on kept pixels, zero outside the image).
 // Without `obs`: writes E_hat to `out`.  With `obs` (the observation's E_hat) and
 // `mask`: sign map gs = M sign(E_hat - obs) and per-tile (sum M |d|, sum M).
-__global__ void __launch_bounds__(kEThreads) k_edge_blur(const uint8_t* __restrict__ cls, const int* parent,
+__global__ void __launch_bounds__(kEThreads) k_edge_blur(const uint8_t* __restrict__ cls,
+                                                         const int* __restrict__ parent,
                                                          const uint8_t* __restrict__ flag,
                                                          const float2* __restrict__ gxy, int H, int W, EdgeW w,
                                                          float* __restrict__ out, const float* __restrict__ obs,
@@ -301,7 +401,7 @@ __global__ void __launch_bounds__(kEThreads) k_edge_blur(const uint8_t* __restri
     float e = 0.0f;
     if (x >= 0 && x < W && y >= 0 && y < H) {
       const int p = (view * H + y) * W + x;
-      if (kept_pixel(cls, parent, flag, p)) {
+      if (kept(cls, parent, flag, p)) {
         const float2 g = gxy[p];
         e = magnitude(g.x, g.y);
       }
@@ -378,7 +478,8 @@ __global__ void __launch_bounds__(kFinalThreads) k_edge_final(const float2* __re
 // mbar = kept ? scale (K_x^T K_y^T gs) : 0 (K is symmetric and zero-padded, so each
 // transpose is the same tap sum), then (gbar_x, gbar_y) = mbar (gx, gy) / m
 __global__ void __launch_bounds__(kEThreads) k_edge_bwd1(const int8_t* __restrict__ gs,
-                                                         const uint8_t* __restrict__ cls, const int* parent,
+                                                         const uint8_t* __restrict__ cls,
+                                                         const int* __restrict__ parent,
                                                          const uint8_t* __restrict__ flag,
                                                          const float2* __restrict__ gxy, int H, int W, EdgeW w,
                                                          const float* __restrict__ scale,
@@ -403,7 +504,7 @@ __global__ void __launch_bounds__(kEThreads) k_edge_bwd1(const int8_t* __restric
   if (x >= W || y >= H) return;
   const int p = (view * H + y) * W + x;
   float2 out = make_float2(0.0f, 0.0f);
-  if (kept_pixel(cls, parent, flag, p)) {
+  if (kept(cls, parent, flag, p)) {
     float acc = 0.0f;
 #pragma unroll
     for (int t = 0; t < 11; ++t) acc += w.k11[t] * sb[ty][tx + t];
@@ -416,21 +517,31 @@ __global__ void __launch_bounds__(kEThreads) k_edge_bwd1(const int8_t* __restric
 
 // The adjoint of a replicated-border tap pass y[i] = sum_t w_t x[clamp(i + t - R)]
 // at output j (0 <= j < n): x_bar[j] = sum over the reads that landed on j.  The
-// input element of coordinate i along the pass is y[(i - origin) * stride].
-template <int R>
+// input element of coordinate i along the pass is y[(i - origin) * stride].  INNER:
+// j - R .. j + R lie inside (1 .. n - 2), so neither bounds nor folds apply.
+template <int R, bool INNER>
 __device__ __forceinline__ float tap_T(const float* w, int j, int n, const float* y, int origin, int stride) {
   float acc = 0.0f;
 #pragma unroll
   for (int t = 0; t <= 2 * R; ++t) {
     const int i = j + R - t;
-    if (i >= 0 && i < n) acc += w[t] * y[(i - origin) * stride];
+    if (INNER || (i >= 0 && i < n)) acc += w[t] * y[(i - origin) * stride];
   }
-  if (j == 0)   // reads below the border were clamped onto coordinate 0
-    for (int i = 0; i < R && i < n; ++i)
-      for (int t = 0; t < R - i; ++t) acc += w[t] * y[(i - origin) * stride];
-  if (j == n - 1)   // and reads beyond it onto n - 1
-    for (int i = max(n - R, 0); i < n; ++i)
-      for (int t = n - 1 - i + R + 1; t <= 2 * R; ++t) acc += w[t] * y[(i - origin) * stride];
+  if (INNER) return acc;
+  if (j == 0) {   // reads below the border were clamped onto coordinate 0
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+      if (i < n)
+#pragma unroll
+        for (int t = 0; t < R - i; ++t) acc += w[t] * y[(i - origin) * stride];
+  }
+  if (j == n - 1) {   // and reads beyond it onto n - 1 (i = n - 1 - q)
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+      if (n - 1 - q >= 0)
+#pragma unroll
+        for (int t = R + q + 1; t <= 2 * R; ++t) acc += w[t] * y[(n - 1 - q - origin) * stride];
+  }
   return acc;
 }
 
@@ -442,55 +553,64 @@ __device__ __forceinline__ float tap_T(const float* w, int j, int n, const float
 //   sb = S_y^T vb + S_x^T ub          x0-2 .. x0+33, y0-2 .. y0+9
 //   hb = G5_y^T sb                    x0-2 .. x0+33, y0 .. y0+7
 //   gb = G5_x^T hb                    the tile
-__global__ void __launch_bounds__(kEThreads) k_edge_bwd2(const float2* __restrict__ gbar,
-                                                         const float* __restrict__ image,
-                                                         const float* __restrict__ T, int H, int W, EdgeW w,
-                                                         float* __restrict__ adjoint, float4* __restrict__ part) {
+struct Bwd2Smem {
+  float sbx[kTY + 6][kTX + 6], sby[kTY + 6][kTX + 6];
+  float sv[kTY + 6][kTX + 4];
+  float su[kTY + 4][kTX + 6];
+  float ssb[kTY + 4][kTX + 4];
+  float shb[kTY][kTX + 4];
+  float red[3][kEThreads / 32];
+};
+
+template <bool INNER>
+__device__ __forceinline__ void bwd2_tile(Bwd2Smem& S, const float2* __restrict__ gbar,
+                                          const float* __restrict__ image, float3 a, int view, int x0, int y0, int H,
+                                          int W, const EdgeW& w, float* __restrict__ adjoint,
+                                          float4* __restrict__ part) {
   constexpr int BX = kTX + 6, BY = kTY + 6;
   constexpr int VX = kTX + 4, VY = kTY + 6;
   constexpr int UX = kTX + 6, UY = kTY + 4;
   constexpr int SX = kTX + 4, SY = kTY + 4;
   constexpr int HX = kTX + 4;
-  __shared__ float sbx[BY][BX], sby[BY][BX], sv[VY][VX], su[UY][UX], ssb[SY][SX], shb[kTY][HX];
-  __shared__ float red[3][kEThreads / 32];
-  const int view = blockIdx.z, x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, tid = threadIdx.x;
+  const int tid = threadIdx.x;
+  auto outside = [&](int x, int y) { return !INNER && (x < 0 || x >= W || y < 0 || y >= H); };
   for (int i = tid; i < BX * BY; i += kEThreads) {
     const int ry = i / BX, rx = i % BX, x = x0 - 3 + rx, y = y0 - 3 + ry;
     float2 g = make_float2(0.0f, 0.0f);
-    if (x >= 0 && x < W && y >= 0 && y < H) g = gbar[(view * H + y) * W + x];
-    sbx[ry][rx] = g.x;
-    sby[ry][rx] = g.y;
+    if (!outside(x, y)) g = gbar[(view * H + y) * W + x];
+    S.sbx[ry][rx] = g.x;
+    S.sby[ry][rx] = g.y;
   }
   __syncthreads();
   for (int i = tid; i < VX * VY + UX * UY; i += kEThreads) {
     if (i < VX * VY) {
       const int ry = i / VX, rx = i % VX, x = x0 - 2 + rx, y = y0 - 3 + ry;
-      if (x < 0 || x >= W || y < 0 || y >= H) continue;
-      sv[ry][rx] = tap_T<1>(kDeriv, x, W, &sbx[ry][0], x0 - 3, 1);
+      if (outside(x, y)) continue;
+      S.sv[ry][rx] = tap_T<1, INNER>(kDeriv, x, W, &S.sbx[ry][0], x0 - 3, 1);
     } else {
       const int j = i - VX * VY, ry = j / UX, rx = j % UX, x = x0 - 3 + rx, y = y0 - 2 + ry;
-      if (x < 0 || x >= W || y < 0 || y >= H) continue;
-      su[ry][rx] = tap_T<1>(kDeriv, y, H, &sby[0][rx], y0 - 3, BX);
+      if (outside(x, y)) continue;
+      S.su[ry][rx] = tap_T<1, INNER>(kDeriv, y, H, &S.sby[0][rx], y0 - 3, BX);
     }
   }
   __syncthreads();
   for (int i = tid; i < SX * SY; i += kEThreads) {
     const int ry = i / SX, rx = i % SX, x = x0 - 2 + rx, y = y0 - 2 + ry;
-    if (x < 0 || x >= W || y < 0 || y >= H) continue;
-    ssb[ry][rx] = tap_T<1>(kSmooth, y, H, &sv[0][rx], y0 - 3, VX) + tap_T<1>(kSmooth, x, W, &su[ry][0], x0 - 3, 1);
+    if (outside(x, y)) continue;
+    S.ssb[ry][rx] = tap_T<1, INNER>(kSmooth, y, H, &S.sv[0][rx], y0 - 3, VX) +
+                    tap_T<1, INNER>(kSmooth, x, W, &S.su[ry][0], x0 - 3, 1);
   }
   __syncthreads();
   for (int i = tid; i < HX * kTY; i += kEThreads) {
     const int ry = i / HX, rx = i % HX, x = x0 - 2 + rx, y = y0 + ry;
-    if (x < 0 || x >= W || y >= H) continue;
-    shb[ry][rx] = tap_T<2>(w.g5, y, H, &ssb[0][rx], y0 - 2, SX);
+    if (outside(x, y)) continue;
+    S.shb[ry][rx] = tap_T<2, INNER>(w.g5, y, H, &S.ssb[0][rx], y0 - 2, SX);
   }
   __syncthreads();
   const int tx = tid % kTX, ty = tid / kTX, x = x0 + tx, y = y0 + ty;
   float v[3] = {0.0f, 0.0f, 0.0f};
-  if (x < W && y < H) {
-    const float g = tap_T<2>(w.g5, x, W, &shb[ty][0], x0 - 2, 1);
-    const float3 a = luma_weights(T, view, w);
+  if (INNER || (x < W && y < H)) {
+    const float g = tap_T<2, INNER>(w.g5, x, W, &S.shb[ty][0], x0 - 2, 1);
     const size_t p = (size_t)(view * H + y) * W + x;
     const float* r = image + 3 * p;
     float* ad = adjoint + 3 * p;
@@ -501,36 +621,66 @@ __global__ void __launch_bounds__(kEThreads) k_edge_bwd2(const float2* __restric
     v[1] = g * r[1];
     v[2] = g * r[2];
   }
-  block_sum<3>(v, red);
+  block_sum<3>(v, S.red);
   if (tid == 0)
     part[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = make_float4(v[0], v[1], v[2], 0.0f);
 }
 
-// dT[view][r][c] += w_r sum over the view's tiles of sum gbar R_c (fixed order)
-__global__ void k_edge_dT(const float4* __restrict__ part, int N, int tiles, EdgeW w, float* __restrict__ dT) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 9 * N) return;
-  const int view = i / 9, r = (i % 9) / 3, c = i % 3;
-  double s = 0.0;
-  for (int t = 0; t < tiles; ++t) {
+__global__ void __launch_bounds__(kEThreads) k_edge_bwd2(const float2* __restrict__ gbar,
+                                                         const float* __restrict__ image,
+                                                         const float* __restrict__ T, int H, int W, EdgeW w,
+                                                         float* __restrict__ adjoint, float4* __restrict__ part) {
+  __shared__ Bwd2Smem S;
+  const int view = blockIdx.z, x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const float3 a = luma_weights(T, view, w);
+  if (x0 >= 3 && x0 + kTX + 3 <= W && y0 >= 3 && y0 + kTY + 3 <= H)
+    bwd2_tile<true>(S, gbar, image, a, view, x0, y0, H, W, w, adjoint, part);
+  else
+    bwd2_tile<false>(S, gbar, image, a, view, x0, y0, H, W, w, adjoint, part);
+}
+
+// dT[view][r][c] += w_r sum over the view's tiles of sum gbar R_c: one block per view,
+// each thread a fixed stride of tiles in double, then a fixed-order tree
+__global__ void __launch_bounds__(kFinalThreads) k_edge_dT(const float4* __restrict__ part, int tiles, EdgeW w,
+                                                           float* __restrict__ dT) {
+  __shared__ double red[3][kFinalThreads];
+  const int view = blockIdx.x;
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int t = threadIdx.x; t < tiles; t += kFinalThreads) {
     const float4 v = part[(size_t)view * tiles + t];
-    s += c == 0 ? v.x : (c == 1 ? v.y : v.z);
+    a += v.x;
+    b += v.y;
+    c += v.z;
   }
-  dT[i] += (float)(w.gray[r] * s);
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  red[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int s = kFinalThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 9) {
+    const int r = threadIdx.x / 3, col = threadIdx.x % 3;
+    dT[view * 9 + threadIdx.x] += (float)(w.gray[r] * red[col][0]);
+  }
 }
 
 int grid_blocks(long long P, int threads) {
   return (int)std::min<long long>((P + threads - 1) / threads, 152LL * 16);
 }
 
-// the detector and the hysteresis for N views (k_canny, k_cc_union, k_cc_flag)
+// the detector and the hysteresis for N views: k_canny (with the tiles' own unions),
+// k_cc_border, k_cc_flag
 int run_detector(Context* c, const float* image, const float* T, int N, int H, int W, const EdgeW& w,
                  cudaStream_t s) {
   const dim3 grid((W + kTX - 1) / kTX, (H + kTY - 1) / kTY, N);
   const int P = N * H * W;
-  k_canny<<<grid, kEThreads, 0, s>>>(image, T, H, W, w, c->edge_gxy, c->edge_cls, c->edge_flag, c->edge_parent);
+  k_canny<<<grid, kEThreads, 0, s>>>(image, T, H, W, w, c->edge_gxy, c->edge_cls, c->edge_flag, c->edge_parent,
+                                     c->status);
   HR_CHECK_LAUNCH();
-  k_cc_union<<<grid_blocks(P, 256), 256, 0, s>>>(c->edge_cls, c->edge_parent, H, W, P, c->status);
+  k_cc_border<<<grid, kEThreads, 0, s>>>(c->edge_cls, c->edge_parent, H, W, c->status);
   HR_CHECK_LAUNCH();
   k_cc_flag<<<grid_blocks(P, 256), 256, 0, s>>>(c->edge_cls, c->edge_parent, c->edge_flag, P);
   HR_CHECK_LAUNCH();
@@ -604,7 +754,7 @@ int launch_edge_loss(Context* c, const float* image, const float* T, const float
   k_edge_bwd2<<<grid, kEThreads, 0, s>>>(c->edge_gbar, image, T, H, W, w, adjoint, c->edge_part);
   HR_CHECK_LAUNCH();
   if (dT) {
-    k_edge_dT<<<(9 * N + 127) / 128, 128, 0, s>>>(c->edge_part, N, tiles, w, dT);
+    k_edge_dT<<<N, kFinalThreads, 0, s>>>(c->edge_part, tiles, w, dT);
     HR_CHECK_LAUNCH();
   }
   return HR_OK;
