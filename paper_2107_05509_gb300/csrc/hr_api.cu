@@ -36,12 +36,15 @@ void free_ctx(Context* c) {
   hr::free_edge_buffers(c);
   for (int i = 0; i < 2 * hr::kTimeSlots; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   void* ptrs[] = {c->nodes,   c->tris,    c->normals,   c->normal_len, c->partials,      c->dN,
                   c->dm,      c->sil,     c->sil_count, c->loss_partials, c->counters,   c->skin_partials,
                   c->status,  c->stats,   c->pool_bb,   c->pool_z,     c->pool_rec,      c->st_info,
                   c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it,
                   c->bvh_parent, c->bvh_valid, c->bvh_keys, c->bvh_flags, c->bvh_bounds, c->bvh_bad,
-                  c->bvh_mode, c->extra64, c->ct_partials};
+                  c->bvh_mode, c->extra64, c->ct_partials, c->dedge};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete[] c->hvt;
@@ -106,6 +109,7 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
   bool ok = dev_alloc(&c->nodes, ni * F, a) && dev_alloc(&c->tris, ni * 3 * F, a) &&
             dev_alloc(&c->normals, ni * 3 * V, a) && dev_alloc(&c->normal_len, ni * V, a) &&
             dev_alloc(&c->partials, partial_blocks * 6 * V, a) && dev_alloc(&c->dN, ni * 3 * V, a) &&
+            dev_alloc(&c->dedge, ni * 3 * V, a) &&
             dev_alloc(&c->dm, ni * 3 * V, a) && dev_alloc(&c->sil, nviews * lim->max_E, a) &&
             dev_alloc(&c->sil_count, nviews, a) &&
             dev_alloc(&c->loss_partials, ni * hr::kLossStride(c->loss_blocks), a) &&
@@ -130,6 +134,10 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
                cudaMemset(c->nodes, 0, ni * F * sizeof(hr::Node)) == cudaSuccess &&
                cudaMemset(c->bvh_valid, 0, ni * sizeof(int)) == cudaSuccess;
   for (int i = 0; ok && i < 2 * hr::kTimeSlots; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
+  if (ok)
+    ok = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
   // kernel attributes are set here, once, so that the per-iteration calls are only
   // launches and asynchronous memsets
   if (ok)

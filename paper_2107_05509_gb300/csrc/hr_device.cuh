@@ -119,6 +119,9 @@ struct Context {
   // backward scratch
   float* partials;       // [render_blocks][max_V][6] (single-instance contexts)
   float* dN;             // [n_inst][max_V][3]
+  float* dedge;          // [n_inst][max_V][3] the edge-sampling term's vertex sums
+  cudaStream_t side;     // the edge-sampling term runs here, beside the interior term
+  cudaEvent_t ev_fork, ev_join;
   float* dm;             // [n_inst][max_V][3]
   int* sil;              // [views][max_E]
   int* sil_count;        // [views]

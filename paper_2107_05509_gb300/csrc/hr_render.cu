@@ -1496,15 +1496,18 @@ __global__ void k_normal_dm(const float* __restrict__ normals_all, const float* 
 
 // d_verts[v] += sum over incident faces of d(e1 x e2)/dv . dc_f, dc_f = sum of dm
 // over f; blockIdx.y selects the instance
+// d_verts += the normals' vertex adjoint, and the edge term's sums when dedge is given
 __global__ void k_normal_gather(const float* __restrict__ verts_all, const int* __restrict__ faces,
                                 const int* __restrict__ vf_off, const int* __restrict__ vf_faces,
-                                const float* __restrict__ dm_all, int V, float* __restrict__ d_verts_all) {
+                                const float* __restrict__ dm_all, int V, const float* __restrict__ dedge_all,
+                                float* __restrict__ d_verts_all) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
   const size_t o = (size_t)blockIdx.y * 3 * V;
   const float *verts = verts_all + o, *dm = dm_all + o;
   float* d_verts = d_verts_all + o;
   float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+  if (dedge_all) acc = ld3(dedge_all + o + 3 * v);
   for (int k = vf_off[v]; k < vf_off[v + 1]; ++k) {
     int f = vf_faces[k];
     int i0 = faces[3 * f], i1 = faces[3 * f + 1], i2 = faces[3 * f + 2];
@@ -1526,6 +1529,12 @@ __global__ void k_normal_gather(const float* __restrict__ verts_all, const int* 
   d_verts[3 * v] += acc.x;
   d_verts[3 * v + 1] += acc.y;
   d_verts[3 * v + 2] += acc.z;
+}
+
+// d_verts += dedge (the edge term's sums, when the normals' adjoint is off)
+__global__ void k_add_edges(const float* __restrict__ dedge, long long n, float* __restrict__ d_verts) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d_verts[i] += dedge[i];
 }
 
 __global__ void k_trace(const Node* __restrict__ nodes, const float4* __restrict__ tris, const float* __restrict__ o,
@@ -1743,6 +1752,17 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdGather);
   }
+  // The edge-sampling term (silhouettes, edge samples into ctx->dedge) needs only the
+  // candidate lists made above; it runs on the context's side stream beside the
+  // interior shader and joins before the normals' adjoint adds it to d_verts.  With
+  // kernel timing on, everything stays on the caller's stream.
+  const bool fork = edges && !tm.on;
+  cudaStream_t es = fork ? ctx->side : s;
+  if (edges) {
+    if (fork && (cudaEventRecord(ctx->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(es, ctx->ev_fork, 0) != cudaSuccess))
+      return HR_ERR_CUDA;
+    if (cudaMemsetAsync(ctx->dedge, 0, sizeof(float) * 3 * V * ni, es) != cudaSuccess) return HR_ERR_CUDA;
+  }
   if (interior) {
     // shared-memory sums up to the opt-in of configure_render_kernels (V <= 8192),
     // global float64 atomics beyond
@@ -1776,26 +1796,33 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
   }
   if (edges) {
     tm.begin(kTimeBwdSil);
-    int rc = launch_silhouettes(ctx, m, verts, cams, nv, ctx->sil, ctx->lim.max_E, ctx->sil_count, s);
+    int rc = launch_silhouettes(ctx, m, verts, cams, nv, ctx->sil, ctx->lim.max_E, ctx->sil_count, es);
     if (rc != HR_OK) return rc;
     tm.end(kTimeBwdSil);
     const long long n = (long long)nv * Ne * 32;   // one warp per edge sample
     auto kern = st ? k_edge_samples<true> : k_edge_samples<false>;
     tm.begin(kTimeBwdEdges);
-    kern<<<(unsigned)((n + kRenderThreads - 1) / kRenderThreads), kRenderThreads, 0, s>>>(
-        a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count, Ne, o->edge_eps_px, d_verts,
+    kern<<<(unsigned)((n + kRenderThreads - 1) / kRenderThreads), kRenderThreads, 0, es>>>(
+        a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count, Ne, o->edge_eps_px, ctx->dedge,
         ctx->stats + 2 * kStatsPer);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdEdges);
+    if (fork && (cudaEventRecord(ctx->ev_join, es) != cudaSuccess || cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess))
+      return HR_ERR_CUDA;
   }
   if (normals) {
     tm.begin(kTimeBwdNormals);
     const dim3 g((V + 255) / 256, ni);
     k_normal_dm<<<g, 256, 0, s>>>(ctx->normals, ctx->normal_len, ctx->dN, V, ctx->dm);
     HR_CHECK_LAUNCH();
-    k_normal_gather<<<g, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, ctx->dm, V, d_verts);
+    k_normal_gather<<<g, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, ctx->dm, V,
+                                      edges ? ctx->dedge : nullptr, d_verts);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdNormals);
+  } else if (edges) {
+    const long long n3 = 3LL * V * ni;
+    k_add_edges<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(ctx->dedge, n3, d_verts);
+    HR_CHECK_LAUNCH();
   }
   if (tm.on) ctx->ev_ready |= 2 | (interior ? 4 : 0) | (edges ? 8 : 0) | (normals ? 16 : 0);
   return HR_OK;
