@@ -381,6 +381,7 @@ def run_handrt(args):
         line["tensor"] = run_tensor(dev)
         line["scale"] = run_scale(dev)
         line["paper_objective"] = run_paper_objective(dev)
+        line["edge_term"] = run_edge_term(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, budget_s=args.cpu_seconds)
     if dist:
@@ -704,6 +705,58 @@ def run_paper_objective(dev):
                            "prior": round(float(pr.prior.item()), 8)}}
 
 
+def run_edge_term(dev, reps=20):
+    """The edge term alone at the paper workload's size (8 views of 512 x 384):
+    `hr_edges` (Canny + K of one image stack) and `hr_edge_loss` (the same plus the
+    masked loss and the adjoint into the image and the colour transforms), event-timed
+    over `reps` calls after 3 warm-up calls.  Images: the background plates with one
+    bright disc per view (a silhouette's stand-in), transforms I + N(0, 0.04)."""
+    import torch
+
+    from paper_2107_05509_gb300 import binding as B
+    from paper_2107_05509_gb300 import inputs as I
+
+    N, H, W, seed = 8, 384, 512, 32
+    R = I.background(seed, N, H, W).astype(np.float32)
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:H, 0:W]
+    for n in range(N):
+        cx, cy, r = W * rng.uniform(0.4, 0.6), H * rng.uniform(0.4, 0.6), min(H, W) * rng.uniform(0.15, 0.3)
+        R[n][(x - cx) ** 2 + (y - cy) ** 2 < r * r] = rng.uniform(0.6, 0.95, 3).astype(np.float32)
+    obs = I.add_noise(R, seed, 0.01)
+    mask = np.zeros((N, H, W), np.uint8)
+    mask[:, H // 8:H - H // 8, W // 10:W - W // 10] = 1
+    T = (np.eye(3)[None] + rng.normal(0, 0.04, (N, 3, 3))).astype(np.float32).reshape(N, 9)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device=dev)
+    ctx = B.Context(8, 8, 8, N, W, H)
+    Rt, Ot, Mt, Tt = t(R), t(obs), t(mask), t(T)
+    eo = torch.empty((N, H, W), device=dev)
+    B.hr_edges(ctx, Ot, eo)
+    adj = torch.zeros((N, H, W, 3), device=dev)
+    dT = torch.zeros((N, 9), device=dev)
+    loss = torch.empty(1, device=dev)
+    er = torch.empty((N, H, W), device=dev)
+    calls = {"edge_loss": lambda: B.hr_edge_loss(ctx, Rt, eo, Mt, loss, adj, T=Tt, dT=dT),
+             "edges": lambda: B.hr_edges(ctx, Rt, er, T=Tt)}
+    out = {"workload": "8 x 512x384, plates with one disc per view", "ms": {}}
+    for name, fn in calls.items():
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        out["ms"][name] = round(float(np.median([a.elapsed_time(b) for a, b in ev])), 4)
+    status = B.hr_get_status(ctx)
+    if status != B.HR_OK:
+        raise RuntimeError(f"edge-term device status {B.status_string(status)}")
+    ctx.close()
+    return out
+
+
 def run_tensor(dev, steps=20):
     """The bf16 tensor-core GEMM (tcgen05) on the proposal network's largest shapes and
     on a square product, and one training step of the network (B = 128 instances x 8
@@ -854,6 +907,7 @@ def main():
     ap.add_argument("--refine-iters", type=int, default=150)
     ap.add_argument("--gemm-only", action="store_true", help="only the tensor-core GEMM timings (for profiling)")
     ap.add_argument("--objective-only", action="store_true", help="only the full-objective schedule")
+    ap.add_argument("--edges-only", action="store_true", help="only the edge-term timings (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "handrt":
         args.warmup = 3
@@ -861,6 +915,11 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps(run_tensor(torch.device("cuda", 0))), flush=True)
+        return
+    if args.edges_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_edge_term(torch.device("cuda", 0))), flush=True)
         return
     if args.objective_only:
         import torch
