@@ -825,6 +825,39 @@ __device__ __forceinline__ void flush_tri(int3 f, const HitGrad& acc, T* dV, T* 
   add3(dN, f.z, acc.dn[6], acc.dn[7], acc.dn[8]);
 }
 
+// End-of-item flush by the whole warp: lanes whose run is on a triangle no other
+// lane holds add their sums directly; lanes sharing a triangle (the usual case in a
+// coherent 8x4 sub-tile) are summed by a warp butterfly first and one lane adds the
+// group's sums, so the shared-memory atomics do not collide on the same addresses.
+template <class T>
+__device__ __forceinline__ void flush_tri_warp(int cur, int3 cf, const HitGrad& acc, T* dV, T* dN) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned grp = __match_any_sync(full, cur);
+  const bool shared = __popc(grp) > 1;
+  if (cur >= 0 && !shared) flush_tri(cf, acc, dV, dN);
+  unsigned pending = __ballot_sync(full, cur >= 0 && shared && lane == __ffs(grp) - 1);
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    pending &= pending - 1;
+    const int key = __shfl_sync(full, cur, leader);
+    const bool in = cur == key;
+    HitGrad sum;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      float x = in ? acc.dv[c] : 0.0f, y = in ? acc.dn[c] : 0.0f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(full, x, o);
+        y += __shfl_xor_sync(full, y, o);
+      }
+      sum.dv[c] = x;
+      sum.dn[c] = y;
+    }
+    if (lane == leader) flush_tri(cf, sum, dV, dN);
+  }
+}
+
 // Gradient of samples [s0, s1) of this lane's pixel (upstream g, `live` lanes only;
 // all lanes call it), traced S at a time and differentiated in sample order; added to
 // dV [V][3] / dN [V][3] per run of hits on one triangle.
@@ -891,7 +924,7 @@ __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile&
       }
     }
   }
-  if (cur >= 0) flush_tri(cf, acc, dV, dN);
+  flush_tri_warp(cur, cf, acc, dV, dN);
 }
 
 // this lane's upstream gradient dL/df / spp; `live` = non-zero adjoint
