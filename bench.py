@@ -55,8 +55,8 @@ KERNEL_NAMES = {"fwd_gather": "k_gather<fwd>", "fwd_shade": "k_shade_fwd", "bwd_
                 "bwd_shade": "k_shade_bwd", "edge_samples": "k_edge_samples"}
 # DRAM bytes (read + write) per launch from the ncu capture summarised under profiles/
 # (None once the kernel has changed since that capture)
-NCU_TRAFFIC = {"k_shade_bwd": 3755264, "k_shade_fwd": 2433536, "k_gather<fwd>": 17760512,
-               "k_items_bwd": 19331584, "k_edge_samples": 2976512}
+NCU_TRAFFIC = {"k_shade_bwd": 3766784, "k_shade_fwd": 2436864, "k_gather<fwd>": 17761280,
+               "k_items_bwd": 19334912, "k_edge_samples": 2983680}
 # kernels of one step: skin 1, BVH + normals 2, forward 3, loss 2, backward 7, skin adjoint 1, Adam 1
 LAUNCHES_PER_STEP = 17
 # a batched iteration: the same kernels (one launch each over all instances) plus the
