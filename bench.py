@@ -57,11 +57,13 @@ KERNEL_NAMES = {"fwd_gather": "k_gather<fwd>", "fwd_shade": "k_shade_fwd", "bwd_
 # (None once the kernel has changed since that capture)
 NCU_TRAFFIC = {"k_shade_bwd": 3766784, "k_shade_fwd": 2436864, "k_gather<fwd>": 17761280,
                "k_items_bwd": 19334912, "k_edge_samples": 2983680}
-# kernels of one step: skin 1, BVH + normals 2, forward 3, loss 2, backward 7, skin adjoint 1, Adam 1
-LAUNCHES_PER_STEP = 17
+# kernels of one step: skin 1, BVH + normals 2, forward 4 (gather, shade, overflow,
+# combine), loss 2, backward 8 (items, shade, overflow, reduce, silhouettes, edge
+# samples, normal adjoint 2), skin adjoint 1, Adam 1
+LAUNCHES_PER_STEP = 19
 # a batched iteration: the same kernels (one launch each over all instances) plus the
 # vertex-error kernel
-LAUNCHES_BATCH_ITER = 18
+LAUNCHES_BATCH_ITER = 20
 
 
 def env_rank():

@@ -44,7 +44,7 @@ void free_ctx(Context* c) {
                   c->status,  c->stats,   c->pool_bb,   c->pool_z,     c->pool_rec,      c->st_info,
                   c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it,
                   c->bvh_parent, c->bvh_valid, c->bvh_keys, c->bvh_flags, c->bvh_bounds, c->bvh_bad,
-                  c->bvh_mode, c->extra64, c->ct_partials, c->dedge};
+                  c->bvh_mode, c->extra64, c->ct_partials, c->dedge, c->ovf_list};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete[] c->hvt;
@@ -118,7 +118,8 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
             dev_alloc(&c->pool_bb, c->pool_cap, a) && dev_alloc(&c->pool_z, c->pool_cap, a) &&
             dev_alloc(&c->pool_rec, c->pool_cap, a) && dev_alloc(&c->st_info, subtiles, a) &&
             dev_alloc(&c->items, c->item_cap, a) && dev_alloc(&c->item_part, (size_t)c->item_cap * 32, a) &&
-            dev_alloc(&c->extra, ni * 6 * V, a) && dev_alloc(&c->work_ctr, 2 + 2 * ni, a) &&
+            dev_alloc(&c->extra, ni * 6 * V, a) && dev_alloc(&c->work_ctr, 3 + 2 * ni, a) &&
+            dev_alloc(&c->ovf_list, subtiles, a) &&
             dev_alloc(&c->bvh_parent, ni * 2 * F, a) && dev_alloc(&c->bvh_valid, ni, a) &&
             dev_alloc(&c->bvh_bounds, ni * 6, a) && dev_alloc(&c->bvh_bad, ni, a) && dev_alloc(&c->bvh_mode, ni, a);
   // keys of the multi-block build, for meshes beyond one block's shared memory

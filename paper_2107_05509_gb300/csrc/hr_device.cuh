@@ -115,7 +115,8 @@ struct Context {
   int item_cap;
   float* extra;          // [n_inst][max_V][6]
   double* extra64;       // [n_inst][max_V][6] backward sums when max_V > 8192
-  unsigned* work_ctr;    // [2 + 2 n_inst]
+  unsigned* work_ctr;    // [3 + 2 n_inst]
+  int* ovf_list;         // [sub-tiles] sub-tiles whose items overflowed their region
   // backward scratch
   float* partials;       // [render_blocks][max_V][6] (single-instance contexts)
   float* dN;             // [n_inst][max_V][3]

@@ -200,8 +200,10 @@ struct Work {
                    // atomics: long runs of cancelling contributions)
   float* extra;    // [n_inst][6V] backward sums: shading blocks of a batch, and work
                    // done outside the shading blocks
-  unsigned* ctr;   // [2 + 2 n_inst] sub-tile counter, pool fill, then per instance
-                   // item fill and item counter
+  unsigned* ctr;   // [3 + 2 n_inst] sub-tile counter, pool fill, per instance item
+                   // fill and item counter, then the overflow count
+  int* ovf;        // [sub-tiles] sub-tiles whose items did not fit their instance's
+                   // region (k_overflow does them whole)
 };
 
 struct RenderArgs {
@@ -1047,20 +1049,11 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
     if (first + C <= icap) {
       for (int c = lane; c < C; c += 32) a.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
     } else {
-      // item region full: blank the reserved slots that exist, and this warp does
-      // the whole sub-tile itself
+      // item region full: blank the reserved slots that exist and hand the whole
+      // sub-tile to k_overflow
       for (int c = lane; c < C; c += 32)
         if (first + c < icap) a.wk.items[ibase + first + c] = make_int4(-1, 0, 0, 0);
-      __threadfence_block();
-      if (BWD) {
-        float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
-        grad_samples<STATS, kRaysPerLane>(a, t, cam, off, K, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
-      } else {
-        float3 acc = make_float3(0.0f, 0.0f, 0.0f);
-        int misses = 0;
-        shade_samples<STATS, kRaysPerLane>(a, t, cam, off, K, 0, t.spp, acc, misses, cnt);
-        write_pixel(a, t, acc, misses, image);
-      }
+      if (lane == 0) a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
     }
     __syncwarp();
   }
@@ -1101,10 +1094,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, c
     } else {
       for (int c = lane; c < C; c += 32)
         if (first + c < icap) a.wk.items[ibase + first + c] = make_int4(-1, 0, 0, 0);
-      __threadfence_block();
-      const Cam cam = load_cam(a.cams, t.view);
-      float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
-      grad_samples<STATS, kRaysPerLane>(a, t, cam, pk.x, pk.y, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
+      if (lane == 0) a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
     }
     __syncwarp();
   }
@@ -1172,6 +1162,42 @@ __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in
 }
 
 // one warp per sub-tile with items: its item sums in item order, then the pixel
+// Sub-tiles whose work items did not fit their instance's region (rare: the region is
+// sized for the workload): one warp does a whole sub-tile, all its samples, against
+// the candidate list the gather left for it -- the forward writes its pixels, the
+// backward adds its gradient to the instance's extra sums.  Kept out of the gather so
+// that the gather's registers are sized for its own work.
+template <bool BWD, bool STATS>
+__global__ void __launch_bounds__(kRenderThreads) k_overflow(RenderArgs a_in, const float* __restrict__ adjoint,
+                                                            float* __restrict__ image, unsigned long long* stats) {
+  const RenderArgs a0 = with_iter(a_in);
+  const int total = subtile_count(a0);
+  const int n = (int)min(*reinterpret_cast<volatile unsigned*>(&a0.wk.ctr[2 + 2 * a0.n_inst]), (unsigned)total);
+  Counts cnt;
+  for (int i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < n; i += gridDim.x * kWarps) {
+    const int st = a0.wk.ovf[i];
+    if (!in_range(a0.status, st, 0, total)) continue;
+    const SubTile t = subtile(a0, st);
+    if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
+    const RenderArgs a = for_inst(a0, t.inst);
+    int2 pk = a.wk.st[st];
+    if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
+    const Cam cam = load_cam(a.cams, t.view);
+    if (BWD) {
+      bool live;
+      const float3 g = lane_adjoint(a, t, adjoint, live);
+      float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
+      grad_samples<STATS, kRaysPerLane>(a, t, cam, pk.x, pk.y, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
+    } else {
+      float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+      int misses = 0;
+      shade_samples<STATS, kRaysPerLane>(a, t, cam, pk.x, pk.y, 0, t.spp, acc, misses, cnt);
+      write_pixel(a, t, acc, misses, image);
+    }
+  }
+  flush_counts<STATS>(cnt, stats);
+}
+
 __global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, float* __restrict__ image) {
   const int lane = threadIdx.x & 31;
   const int nw = gridDim.x * kWarps;
@@ -1634,6 +1660,7 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.wk.extra = ctx->extra;
   a.wk.extra64 = ctx->extra64;
   a.wk.ctr = ctx->work_ctr;
+  a.wk.ovf = ctx->ovf_list;
   a.node_stride = ctx->lim.max_F;
   a.cand_per_chunk = ctx->tune.cand_per_chunk;
   a.max_chunks = ctx->tune.max_chunks;
@@ -1704,7 +1731,7 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   RenderArgs a = make_args(ctx, m, verts, cams, N, H, W, bg, o);
   const bool st = o->flags & HR_STATS;
   Timer tm{ctx, s, (o->flags & HR_TIMING) != 0};
-  if (cudaMemsetAsync(ctx->work_ctr, 0, (2 + 2 * a.n_inst) * sizeof(unsigned), s) != cudaSuccess)
+  if (cudaMemsetAsync(ctx->work_ctr, 0, (3 + 2 * a.n_inst) * sizeof(unsigned), s) != cudaSuccess)
     return HR_ERR_CUDA;
   const int blocks = ctx->num_sms * ctx->tune.blocks_per_sm;
   tm.begin(kTimeFwdGather);
@@ -1721,6 +1748,11 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
                    : (S == 1 ? k_shade_fwd<false, 1> : (S == 2 ? k_shade_fwd<false, 2> : k_shade_fwd<false, 4>));
     kern<<<blocks, kRenderThreads, 0, s>>>(a, st ? ctx->stats : nullptr);
   }
+  HR_CHECK_LAUNCH();
+  if (st)
+    k_overflow<false, true><<<ctx->num_sms, kRenderThreads, 0, s>>>(a, nullptr, image, ctx->stats);
+  else
+    k_overflow<false, false><<<ctx->num_sms, kRenderThreads, 0, s>>>(a, nullptr, image, nullptr);
   HR_CHECK_LAUNCH();
   tm.end(kTimeFwdShade);
   tm.begin(kTimeFwdCombine);
@@ -1762,7 +1794,7 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
   if (interior || edges) {
     // candidates of the sub-tiles with a non-zero adjoint: the interior shader's work
     // items, and the edge rays' candidate lists
-    if (cudaMemsetAsync(ctx->work_ctr, 0, (2 + 2 * ni) * sizeof(unsigned), s) != cudaSuccess ||
+    if (cudaMemsetAsync(ctx->work_ctr, 0, (3 + 2 * ni) * sizeof(unsigned), s) != cudaSuccess ||
         cudaMemsetAsync(ctx->extra, 0, sizeof(float) * 6 * V * ni, s) != cudaSuccess)
       return HR_ERR_CUDA;
     // the forward's candidate lists still describe this scene when it used the same
@@ -1816,6 +1848,11 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     const int blocks = ctx->num_sms * ctx->tune.bwd_blocks_per_sm;
     tm.begin(kTimeBwdShade);
     kern<<<blocks, kRenderThreads, smem, s>>>(a, adjoint, ctx->partials, st ? ctx->stats + kStatsPer : nullptr);
+    HR_CHECK_LAUNCH();
+    if (st)
+      k_overflow<true, true><<<ctx->num_sms, kRenderThreads, 0, s>>>(a, adjoint, nullptr, ctx->stats + kStatsPer);
+    else
+      k_overflow<true, false><<<ctx->num_sms, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdShade);
     tm.begin(kTimeBwdReduce);

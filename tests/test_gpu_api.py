@@ -215,3 +215,79 @@ def test_tunings_keep_results(B):
         with pytest.raises(B.HandrtError):
             ctx.set_tuning(**bad)
     assert B.hr_get_status(ctx) == B.HR_OK
+
+
+def test_item_region_overflow_matches_oracle(B):
+    """Sub-tiles whose work items do not fit the item region are handed whole to the
+    overflow kernel; forward pixels and the backward gradient stay the oracle's.  A
+    zoomed 2 x 64x48 scene at 16 spp with one candidate per work item asks for more
+    items than the region holds (2 x sub-tiles + 1024): counted here from below by the
+    distinct triangles covering each sub-tile's pixel centres."""
+    import oracle
+    from paper_2107_05509_gb300 import inputs as I
+    from tests.gpu_common import grad_ok, pixel_ok
+    h = hand()
+    cfg = I.SceneConfig("overflow", views=2, width=64, height=48, spp=16, edge_samples=256, elevation_deg=20.0,
+                        azimuths_deg=(30.0, 210.0), seed=41)
+    cams = I.pack_cameras(I.make_cameras(cfg, h.v_template.mean(0)))
+    for c in cams:
+        c[0:2] *= 3.0
+    N, H, W = cfg.views, cfg.height, cfg.width
+    x = I.perturb_params(I.gt_params(cfg.seed), cfg.seed).astype(np.float32)
+    verts = oracle.skin(h, x).astype(np.float32)
+    normals = oracle.vertex_normals(verts, h.faces, h.vf_offsets, h.vf_faces)
+    bg = I.background(cfg.seed, N, H, W)
+    # lower bound on the items requested: a triangle covering a pixel centre of a
+    # sub-tile meets its frustum, so it is among the sub-tile's candidates
+    need = 0
+    ys, xs = np.mgrid[0:H, 0:W] + 0.5
+    for v in range(N):
+        fx, fy, cx, cy = cams[v][:4]
+        R, t = cams[v][4:13].reshape(3, 3).astype(np.float64), cams[v][13:16].astype(np.float64)
+        P = verts.astype(np.float64) @ R.T + t
+        sx, sy = fx * P[:, 0] / P[:, 2] + cx, fy * P[:, 1] / P[:, 2] + cy
+        cover = [set() for _ in range((W // 8) * (H // 4))]
+        for f, (i0, i1, i2) in enumerate(h.faces):
+            ax, ay, bx, by, qx, qy = sx[i0], sy[i0], sx[i1], sy[i1], sx[i2], sy[i2]
+            x0, x1 = int(max(0, np.floor(min(ax, bx, qx)))), int(min(W - 1, np.ceil(max(ax, bx, qx))))
+            y0, y1 = int(max(0, np.floor(min(ay, by, qy)))), int(min(H - 1, np.ceil(max(ay, by, qy))))
+            if x0 > x1 or y0 > y1 or min(P[i0, 2], P[i1, 2], P[i2, 2]) <= 0:
+                continue
+            px, py = xs[y0:y1 + 1, x0:x1 + 1], ys[y0:y1 + 1, x0:x1 + 1]
+            e0 = (bx - ax) * (py - ay) - (by - ay) * (px - ax)
+            e1 = (qx - bx) * (py - by) - (qy - by) * (px - bx)
+            e2 = (ax - qx) * (py - qy) - (ay - qy) * (px - qx)
+            inside = ((e0 > 0) & (e1 > 0) & (e2 > 0)) | ((e0 < 0) & (e1 < 0) & (e2 < 0))
+            for yy, xx in zip(*np.nonzero(inside)):
+                cover[((y0 + yy) // 4) * (W // 8) + (x0 + xx) // 8].add(f)
+        need += sum(min(len(c), 16) for c in cover)
+    subtiles = N * ((W + 7) // 8) * ((H + 3) // 4)
+    assert need > 2 * subtiles + 1024, (need, subtiles)
+    o = oracle.make_opts(seed=77, spp=cfg.spp, edge_samples=cfg.edge_samples, ka=I.K_AMBIENT, kd=I.K_DIFFUSE,
+                         light_dir=I.LIGHT_DIR, light_rgb=I.LIGHT_RGB, edge_eps=I.EDGE_EPS_PX)
+    ref = oracle.render_fwd(verts, h.faces, normals, h.albedo, cams, H, W, bg, o)
+    obs = I.add_noise(bg, cfg.seed, 0.05)
+    mask = np.ones((N, H, W), np.uint8)
+    _, A = oracle.loss(ref.astype(np.float32), obs, mask)
+    A = A.astype(np.float32)
+    g_ref, _ = oracle.render_bwd(h, verts, cams, H, W, bg, o, A, normals=normals)
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, N, W, H)
+    ctx.set_tuning(rays_per_lane=4, cand_per_chunk=1, max_chunks=16, blocks_per_sm=8, bwd_blocks_per_sm=4)
+    vt, ct, bt = _t(verts), _t(cams), _t(bg)
+    img = torch.empty((N, H, W, 3), device="cuda")
+    dv = torch.empty((h.V, 3), device="cuda")
+    go = B.render_opts(seed=77, spp=cfg.spp, edge_samples=cfg.edge_samples, ka=I.K_AMBIENT, kd=I.K_DIFFUSE,
+                       light_dir=I.LIGHT_DIR, light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX)
+    B.hr_build_bvh(ctx, model, vt)
+    B.hr_render_fwd(ctx, model, vt, ct, H, W, bt, go, img)
+    g = img.cpu().numpy()
+    ok = pixel_ok(g, ref)
+    assert ok.all(), (np.argwhere(~ok)[:5], np.abs(g - ref).max())
+    for flags in (0, B.HR_BWD_REUSE_FWD):   # a gather of its own, and the forward's lists
+        go.flags = flags
+        B.hr_render_bwd(ctx, model, vt, ct, H, W, bt, go, _t(A), dv)
+        gd = dv.cpu().numpy()
+        ok = grad_ok(gd, g_ref)
+        assert ok.all(), (flags, np.argwhere(~ok)[:5], gd[~ok][:5], g_ref[~ok][:5])
+    assert B.hr_get_status(ctx) == B.HR_OK
