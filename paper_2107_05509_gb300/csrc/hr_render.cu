@@ -665,7 +665,7 @@ __device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, 
 // Radiance sums of samples [s0, s1) of this lane's pixel (all lanes call it), traced
 // S at a time (the tuning's rays per lane); the radiance is added in sample order.
 constexpr int kRaysPerLane = 4;   // for the gather kernels' fall-back paths
-template <bool STATS, int S>
+template <bool STATS, int S, bool TRACE = true>
 __device__ __forceinline__ void shade_samples(const RenderArgs& a, const SubTile& t, const Cam& cam, int off, int K,
                                               int s0, int s1, float3& acc, int& misses, Counts& cnt) {
   const int lane = threadIdx.x & 31;
@@ -699,7 +699,9 @@ __device__ __forceinline__ void shade_samples(const RenderArgs& a, const SubTile
 #pragma unroll
       for (int j = 0; j < S; ++j) {
         h[j] = Hit{-1, INFINITY, 0.0f, 0.0f};
-        if (live[j]) h[j] = trace<STATS>(a.nodes, a.tris, o, d[j], a.status, cnt, a.max_visits);
+        // K < 0: no usable candidate list, per-ray traversal (only the overflow kernel
+        // meets such sub-tiles; the shaders are built without it)
+        if (TRACE && live[j]) h[j] = trace<STATS>(a.nodes, a.tris, o, d[j], a.status, cnt, a.max_visits);
       }
     }
 #pragma unroll
@@ -863,7 +865,7 @@ __device__ __forceinline__ void flush_tri_warp(int cur, int3 cf, const HitGrad& 
 // Gradient of samples [s0, s1) of this lane's pixel (upstream g, `live` lanes only;
 // all lanes call it), traced S at a time and differentiated in sample order; added to
 // dV [V][3] / dN [V][3] per run of hits on one triangle.
-template <bool STATS, int S, class T>
+template <bool STATS, int S, class T, bool TRACE = true>
 __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile& t, const Cam& cam, int off, int K,
                                              int s0, int s1, bool live, float3 g, T* dV, T* dN, Counts& cnt) {
   const int lane = threadIdx.x & 31;
@@ -901,7 +903,7 @@ __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile&
 #pragma unroll
       for (int j = 0; j < S; ++j) {
         h[j] = Hit{-1, INFINITY, 0.0f, 0.0f};
-        if (lv[j]) h[j] = trace<STATS>(a.nodes, a.tris, o, d[j], a.status, cnt, a.max_visits);
+        if (TRACE && lv[j]) h[j] = trace<STATS>(a.nodes, a.tris, o, d[j], a.status, cnt, a.max_visits);
       }
     }
 #pragma unroll
@@ -1040,6 +1042,16 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
         K = -1;   // pool full: per-ray traversal for this sub-tile
       }
     }
+    if (K < 0) {
+      // no usable candidate list (too many candidates, or the pool is full): the
+      // overflow kernel traces this sub-tile's rays one by one
+      if (lane == 0) {
+        a.wk.st[st] = make_int2(off, K);
+        a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
+      }
+      __syncwarp();
+      continue;
+    }
     const int C = chunks_for(a, K, t.spp);
     const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
     int first = 0;
@@ -1084,6 +1096,10 @@ __global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, c
       continue;
     }
     if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
+    if (pk.y < 0) {   // no usable candidate list: the overflow kernel traces its rays
+      if (lane == 0) a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
+      continue;
+    }
     const int C = chunks_for(a, pk.y, t.spp);
     const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
     int first = 0;
@@ -1154,7 +1170,7 @@ __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in
       item_samples(item.y, item.z, t.spp, s0, s1);
       float3 acc = make_float3(0.0f, 0.0f, 0.0f);
       int misses = 0;
-      shade_samples<STATS, S>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
+      shade_samples<STATS, S, false>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
       a.wk.part[(size_t)(ibase + it) * 32 + lane] = make_float4(acc.x, acc.y, acc.z, (float)misses);
     }
   }
@@ -1162,11 +1178,12 @@ __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in
 }
 
 // one warp per sub-tile with items: its item sums in item order, then the pixel
-// Sub-tiles whose work items did not fit their instance's region (rare: the region is
-// sized for the workload): one warp does a whole sub-tile, all its samples, against
-// the candidate list the gather left for it -- the forward writes its pixels, the
-// backward adds its gradient to the instance's extra sums.  Kept out of the gather so
-// that the gather's registers are sized for its own work.
+// Sub-tiles whose work items did not fit their instance's region, or that have no
+// usable candidate list (more than the gather's list holds, or the pool full): rare
+// on the workloads here.  One warp does a whole sub-tile, all its samples, against
+// its candidate list or, without one, by per-ray BVH traversal -- the forward writes
+// its pixels, the backward adds its gradient to the instance's extra sums.  Kept out
+// of the gather and the shaders so that their registers are sized for their own work.
 template <bool BWD, bool STATS>
 __global__ void __launch_bounds__(kRenderThreads) k_overflow(RenderArgs a_in, const float* __restrict__ adjoint,
                                                             float* __restrict__ image, unsigned long long* stats) {
@@ -1189,10 +1206,23 @@ __global__ void __launch_bounds__(kRenderThreads) k_overflow(RenderArgs a_in, co
       float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
       grad_samples<STATS, kRaysPerLane>(a, t, cam, pk.x, pk.y, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
     } else {
-      float3 acc = make_float3(0.0f, 0.0f, 0.0f);
-      int misses = 0;
-      shade_samples<STATS, kRaysPerLane>(a, t, cam, pk.x, pk.y, 0, t.spp, acc, misses, cnt);
-      write_pixel(a, t, acc, misses, image);
+      // the same chunks and the same order of sums as work items and k_combine_fwd
+      // would use, so a pixel's value does not depend on which path rendered it
+      const int C = chunks_for(a, pk.y, t.spp);
+      float3 tot = make_float3(0.0f, 0.0f, 0.0f);
+      float tmiss = 0.0f;
+      for (int c = 0; c < C; ++c) {
+        int s0, s1;
+        item_samples(c, C, t.spp, s0, s1);
+        float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+        int misses = 0;
+        shade_samples<STATS, kRaysPerLane>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
+        tot.x += acc.x;
+        tot.y += acc.y;
+        tot.z += acc.z;
+        tmiss += (float)misses;
+      }
+      write_pixel(a, t, tot, (int)tmiss, image);
     }
   }
   flush_counts<STATS>(cnt, stats);
@@ -1268,7 +1298,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
       const Cam cam = load_cam(a.cams, t.view);
       int s0, s1;
       item_samples(item.y, item.z, t.spp, s0, s1);
-      grad_samples<STATS, S>(a, t, cam, pk.x, pk.y, s0, s1, live, g, sdV, sdN, cnt);
+      grad_samples<STATS, S, AccT, false>(a, t, cam, pk.x, pk.y, s0, s1, live, g, sdV, sdN, cnt);
       did = 1;
     }
     if (ACC == kAccFlush) {
