@@ -161,19 +161,24 @@ typedef struct hr_context hr_context;
 
 /* Launch shapes of the render kernels (hr_set_tuning; see pipeline.autotune for the
  * project's autotuner, which times candidates on a workload and caches the best):
- *   rays_per_lane      samples each lane traces together against a candidate (1, 2, 4)
+ *   rays_per_lane      samples each lane of the forward shader traces together
+ *                      against a candidate (1, 2, 4)
  *   cand_per_chunk     candidates per work item when splitting a sub-tile (>= 1)
  *   max_chunks         work items per sub-tile at most (1 .. 16)
  *   blocks_per_sm      persistent blocks per SM of the gather / forward kernels (1 .. 8)
  *   bwd_blocks_per_sm  persistent blocks per SM of the backward shader (1 .. 8)
+ *   bwd_rays_per_lane  rays_per_lane of the backward shader (1, 2, 4)
+ *   bwd_cand_per_chunk cand_per_chunk of the backward's work items (>= 1)
  * Every setting gives the same results (the backward up to float32 summation order);
- * only the speed changes.  Defaults: 4, 16, 16, 8, 4. */
+ * only the speed changes.  Defaults: 2, 8, 16, 8, 4, 4, 16. */
 typedef struct hr_tuning {
     int32_t rays_per_lane;
     int32_t cand_per_chunk;
     int32_t max_chunks;
     int32_t blocks_per_sm;
     int32_t bwd_blocks_per_sm;
+    int32_t bwd_rays_per_lane;
+    int32_t bwd_cand_per_chunk;
 } hr_tuning;
 
 /* Create a context on the current CUDA device: device scratch for the given

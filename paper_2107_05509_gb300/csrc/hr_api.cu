@@ -89,7 +89,7 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
   std::memset(c, 0, sizeof(Context));
   c->lim = *lim;
   c->n_inst = n;
-  c->tune = hr_tuning{4, 16, 16, 8, 4};
+  c->tune = hr_tuning{2, 8, 16, 8, 4, 4, 16};
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     delete c;
     return HR_ERR_CUDA;
@@ -275,7 +275,9 @@ int hr_batch_layout(hr_context* ctx, int32_t* view_offsets, int64_t* pixel_offse
 int hr_set_tuning(hr_context* ctx, const hr_tuning* t) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || !t) return HR_ERR_ARG;
-  if ((t->rays_per_lane != 1 && t->rays_per_lane != 2 && t->rays_per_lane != 4) || t->cand_per_chunk < 1 ||
+  const auto rays_ok = [](int r) { return r == 1 || r == 2 || r == 4; };
+  if (!rays_ok(t->rays_per_lane) || !rays_ok(t->bwd_rays_per_lane) || t->cand_per_chunk < 1 ||
+      t->bwd_cand_per_chunk < 1 ||
       t->max_chunks < 1 || t->max_chunks > 16 || t->blocks_per_sm < 1 || t->blocks_per_sm > 8 ||
       t->bwd_blocks_per_sm < 1 || t->bwd_blocks_per_sm > 8)
     return HR_ERR_ARG;

@@ -1813,6 +1813,7 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
                       const float* bg, const hr_render_opts* o, const float* adjoint, float* d_verts,
                       cudaStream_t s) {
   RenderArgs a = make_args(ctx, m, verts, cams, N, H, W, bg, o);
+  a.cand_per_chunk = ctx->tune.bwd_cand_per_chunk;   // the backward's own work-item split
   const int V = m->V, ni = a.n_inst, nv = a.nviews;
   const bool batch = ctx->vt != nullptr;
   const int Ne = batch ? ctx->max_ne : o->edge_samples;
@@ -1867,7 +1868,7 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
       return ctx->extra64 ? HR_ERR_CUDA : HR_ERR_UNSUPPORTED;
     const size_t smem = global_acc ? 0 : render_bwd_smem(V);
     const int acc = global_acc ? kAccGlobal : (batch ? kAccFlush : kAccPartials);
-    const int S = ctx->tune.rays_per_lane;
+    const int S = ctx->tune.bwd_rays_per_lane;
 #define HR_BWD_KERNEL(A_) \
   (st ? (S == 1 ? k_shade_bwd<true, A_, 1> : (S == 2 ? k_shade_bwd<true, A_, 2> : k_shade_bwd<true, A_, 4>)) \
       : (S == 1 ? k_shade_bwd<false, A_, 1> : (S == 2 ? k_shade_bwd<false, A_, 2> : k_shade_bwd<false, A_, 4>)))

@@ -349,6 +349,8 @@ TUNING_SPACE = {
     "max_chunks": (8, 16),
     "blocks_per_sm": (4, 6, 8),
     "bwd_blocks_per_sm": (2, 3, 4, 6),
+    "bwd_rays_per_lane": (1, 2, 4),
+    "bwd_cand_per_chunk": (8, 16, 32),
 }
 
 

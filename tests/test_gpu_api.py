@@ -201,9 +201,12 @@ def test_tunings_keep_results(B):
     img = torch.empty((sc.N, sc.H, sc.W, 3), device="cuda")
     dv = torch.empty((h.V, 3), device="cuda")
     B.hr_build_bvh(ctx, model, vt)
-    for t in ({"rays_per_lane": 1, "cand_per_chunk": 8, "max_chunks": 16, "blocks_per_sm": 4, "bwd_blocks_per_sm": 2},
-              {"rays_per_lane": 2, "cand_per_chunk": 32, "max_chunks": 8, "blocks_per_sm": 8, "bwd_blocks_per_sm": 6},
-              {"rays_per_lane": 4, "cand_per_chunk": 1, "max_chunks": 1, "blocks_per_sm": 1, "bwd_blocks_per_sm": 1}):
+    for t in ({"rays_per_lane": 1, "cand_per_chunk": 8, "max_chunks": 16, "blocks_per_sm": 4, "bwd_blocks_per_sm": 2,
+               "bwd_rays_per_lane": 2, "bwd_cand_per_chunk": 16},
+              {"rays_per_lane": 2, "cand_per_chunk": 32, "max_chunks": 8, "blocks_per_sm": 8, "bwd_blocks_per_sm": 6,
+               "bwd_rays_per_lane": 4, "bwd_cand_per_chunk": 8},
+              {"rays_per_lane": 4, "cand_per_chunk": 1, "max_chunks": 1, "blocks_per_sm": 1, "bwd_blocks_per_sm": 1,
+               "bwd_rays_per_lane": 1, "bwd_cand_per_chunk": 1}):
         ctx.set_tuning(**t)
         assert ctx.get_tuning() == t
         B.hr_render_fwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o), img)
@@ -211,7 +214,7 @@ def test_tunings_keep_results(B):
         B.hr_render_bwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o, B.HR_BWD_REUSE_FWD), _t(A), dv)
         assert grad_ok(dv.cpu().numpy(), g_ref).all(), t
     for bad in ({"rays_per_lane": 3}, {"max_chunks": 17}, {"blocks_per_sm": 0}, {"bwd_blocks_per_sm": 9},
-                {"cand_per_chunk": 0}):
+                {"cand_per_chunk": 0}, {"bwd_rays_per_lane": 3}, {"bwd_cand_per_chunk": 0}):
         with pytest.raises(B.HandrtError):
             ctx.set_tuning(**bad)
     assert B.hr_get_status(ctx) == B.HR_OK
@@ -273,7 +276,8 @@ def test_item_region_overflow_matches_oracle(B):
     g_ref, _ = oracle.render_bwd(h, verts, cams, H, W, bg, o, A, normals=normals)
     model = B.Model(h)
     ctx = B.Context(h.V, h.F, h.E, N, W, H)
-    ctx.set_tuning(rays_per_lane=4, cand_per_chunk=1, max_chunks=16, blocks_per_sm=8, bwd_blocks_per_sm=4)
+    ctx.set_tuning(rays_per_lane=4, cand_per_chunk=1, max_chunks=16, blocks_per_sm=8, bwd_blocks_per_sm=4,
+                   bwd_rays_per_lane=4, bwd_cand_per_chunk=1)
     vt, ct, bt = _t(verts), _t(cams), _t(bg)
     img = torch.empty((N, H, W, 3), device="cuda")
     dv = torch.empty((h.V, 3), device="cuda")
