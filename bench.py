@@ -910,6 +910,7 @@ def main():
     ap.add_argument("--gemm-only", action="store_true", help="only the tensor-core GEMM timings (for profiling)")
     ap.add_argument("--objective-only", action="store_true", help="only the full-objective schedule")
     ap.add_argument("--edges-only", action="store_true", help="only the edge-term timings (for profiling)")
+    ap.add_argument("--scale-only", action="store_true", help="only the scale workload (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "handrt":
         args.warmup = 3
@@ -917,6 +918,11 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps(run_tensor(torch.device("cuda", 0))), flush=True)
+        return
+    if args.scale_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_scale(torch.device("cuda", 0))), flush=True)
         return
     if args.edges_only:
         import torch

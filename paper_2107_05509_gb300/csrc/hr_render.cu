@@ -1042,16 +1042,6 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
         K = -1;   // pool full: per-ray traversal for this sub-tile
       }
     }
-    if (K < 0) {
-      // no usable candidate list (too many candidates, or the pool is full): the
-      // overflow kernel traces this sub-tile's rays one by one
-      if (lane == 0) {
-        a.wk.st[st] = make_int2(off, K);
-        a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
-      }
-      __syncwarp();
-      continue;
-    }
     const int C = chunks_for(a, K, t.spp);
     const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
     int first = 0;
@@ -1096,10 +1086,6 @@ __global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, c
       continue;
     }
     if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
-    if (pk.y < 0) {   // no usable candidate list: the overflow kernel traces its rays
-      if (lane == 0) a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
-      continue;
-    }
     const int C = chunks_for(a, pk.y, t.spp);
     const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
     int first = 0;
@@ -1165,6 +1151,7 @@ __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in
       SubTile t;
       int2 pk;
       if (!load_item(a, ibase + it, item, t, pk) || t.inst != inst) continue;
+      if (pk.y < 0) continue;   // no candidate list: k_overflow traces this item
       const Cam cam = load_cam(a.cams, t.view);
       int s0, s1;
       item_samples(item.y, item.z, t.spp, s0, s1);
@@ -1178,14 +1165,15 @@ __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in
 }
 
 // one warp per sub-tile with items: its item sums in item order, then the pixel
-// Sub-tiles whose work items did not fit their instance's region, or that have no
-// usable candidate list (more than the gather's list holds, or the pool full): rare
-// on the workloads here.  One warp does a whole sub-tile, all its samples, against
-// its candidate list or, without one, by per-ray BVH traversal -- the forward writes
-// its pixels, the backward adds its gradient to the instance's extra sums.  Kept out
-// of the gather and the shaders so that their registers are sized for their own work.
+// The rare paths, kept out of the gather and the shaders so that their registers are
+// sized for their own work: (1) sub-tiles whose work items did not fit their
+// instance's region -- one warp does a whole sub-tile, all its samples, in the chunks
+// the items would have had (the forward writes its pixels, the backward adds to the
+// instance's extra sums); (2) work items of sub-tiles without a usable candidate list
+// (more candidates than the gather's list holds, or the pool full), traced ray by ray.
 template <bool BWD, bool STATS>
-__global__ void __launch_bounds__(kRenderThreads) k_overflow(RenderArgs a_in, const float* __restrict__ adjoint,
+__global__ void __launch_bounds__(kRenderThreads, BWD ? kBwdMinBlocks : 8) k_overflow(RenderArgs a_in,
+                                                                                     const float* __restrict__ adjoint,
                                                             float* __restrict__ image, unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
   const int total = subtile_count(a0);
@@ -1204,7 +1192,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_overflow(RenderArgs a_in, co
       bool live;
       const float3 g = lane_adjoint(a, t, adjoint, live);
       float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
-      grad_samples<STATS, kRaysPerLane>(a, t, cam, pk.x, pk.y, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
+      grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
     } else {
       // the same chunks and the same order of sums as work items and k_combine_fwd
       // would use, so a pixel's value does not depend on which path rendered it
@@ -1216,13 +1204,40 @@ __global__ void __launch_bounds__(kRenderThreads) k_overflow(RenderArgs a_in, co
         item_samples(c, C, t.spp, s0, s1);
         float3 acc = make_float3(0.0f, 0.0f, 0.0f);
         int misses = 0;
-        shade_samples<STATS, kRaysPerLane>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
+        shade_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
         tot.x += acc.x;
         tot.y += acc.y;
         tot.z += acc.z;
         tmiss += (float)misses;
       }
       write_pixel(a, t, tot, (int)tmiss, image);
+    }
+  }
+  // work items of sub-tiles without a candidate list (the shaders skip them): traced
+  // ray by ray, the forward writing the item's partial sums for k_combine_fwd, the
+  // backward adding to the instance's extra sums
+  for (int inst = 0; inst < a0.n_inst; ++inst) {
+    const int ni = item_count(a0, inst), ibase = inst_ibase(a0, inst);
+    const RenderArgs a = for_inst(a0, inst);
+    for (int it = blockIdx.x * kWarps + (threadIdx.x >> 5); it < ni; it += gridDim.x * kWarps) {
+      int4 item;
+      SubTile t;
+      int2 pk;
+      if (!load_item(a, ibase + it, item, t, pk) || t.inst != inst || pk.y >= 0) continue;
+      const Cam cam = load_cam(a.cams, t.view);
+      int s0, s1;
+      item_samples(item.y, item.z, t.spp, s0, s1);
+      if (BWD) {
+        bool live;
+        const float3 g = lane_adjoint(a, t, adjoint, live);
+        float* ex = a.wk.extra + (size_t)inst * 6 * a.V;
+        grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, live, g, ex, ex + 3 * a.V, cnt);
+      } else {
+        float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+        int misses = 0;
+        shade_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
+        a.wk.part[(size_t)(ibase + it) * 32 + (threadIdx.x & 31)] = make_float4(acc.x, acc.y, acc.z, (float)misses);
+      }
     }
   }
   flush_counts<STATS>(cnt, stats);
@@ -1293,6 +1308,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
       SubTile t;
       int2 pk;
       if (!load_item(a, ibase + it, item, t, pk) || t.inst != inst) continue;
+      if (pk.y < 0) continue;   // no candidate list: k_overflow traces this item
       bool live;
       const float3 g = lane_adjoint(a, t, adjoint, live);
       const Cam cam = load_cam(a.cams, t.view);
@@ -1780,9 +1796,9 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   }
   HR_CHECK_LAUNCH();
   if (st)
-    k_overflow<false, true><<<ctx->num_sms, kRenderThreads, 0, s>>>(a, nullptr, image, ctx->stats);
+    k_overflow<false, true><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, ctx->stats);
   else
-    k_overflow<false, false><<<ctx->num_sms, kRenderThreads, 0, s>>>(a, nullptr, image, nullptr);
+    k_overflow<false, false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, nullptr);
   HR_CHECK_LAUNCH();
   tm.end(kTimeFwdShade);
   tm.begin(kTimeFwdCombine);
@@ -1881,9 +1897,9 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     kern<<<blocks, kRenderThreads, smem, s>>>(a, adjoint, ctx->partials, st ? ctx->stats + kStatsPer : nullptr);
     HR_CHECK_LAUNCH();
     if (st)
-      k_overflow<true, true><<<ctx->num_sms, kRenderThreads, 0, s>>>(a, adjoint, nullptr, ctx->stats + kStatsPer);
+      k_overflow<true, true><<<blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, ctx->stats + kStatsPer);
     else
-      k_overflow<true, false><<<ctx->num_sms, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
+      k_overflow<true, false><<<blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdShade);
     tm.begin(kTimeBwdReduce);
