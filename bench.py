@@ -70,6 +70,27 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def rank_instance(seed, rank):
+    """Weak scaling: rank r refines its own hand instance, seeded seed + r, with Philox
+    instance field r (independent sample streams); no data crosses ranks."""
+    return seed + rank, rank
+
+
+def reduce_max(values, dist, device):
+    """The slowest rank's value of each entry (a MAX all-reduce when ranks exist)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_value(units_per_rank_step, world, ms_per_step):
+    """Whole-job throughput in millions of units per second: the units all ranks
+    processed in a step over the slowest rank's step time."""
+    return units_per_rank_step * world / (ms_per_step * 1e-3) / 1e6
+
+
 def peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -145,13 +166,13 @@ def run_handrt(args):
     cfg = I.PAPER
     hand = I.make_hand(0)
     model = B.Model(hand, device=dev)
-    inst_seed = cfg.seed + rank
+    inst_seed, inst_field = rank_instance(cfg.seed, rank)
     x_gt = I.gt_params(inst_seed)
     N, H, W = cfg.views, cfg.height, cfg.width
     ctx = B.Context(hand.V, hand.F, hand.E, N, W, H)
     views, _ = P.make_views(cfg, model, x_gt, device=dev, ctx=ctx)
     opts = P.opts_for(cfg)
-    opts.instance = rank
+    opts.instance = inst_field
     ref = P.Refiner(model, views, opts, ctx=ctx)
     x0 = torch.as_tensor(I.perturb_params(x_gt, inst_seed), device=dev)
     params = x0.clone()
@@ -315,16 +336,14 @@ def run_handrt(args):
     opts.iter = 0
 
     if dist:
-        t = torch.tensor([tot_ms, e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms, e2e_ms = float(t[0]), float(t[1])
+        tot_ms, e2e_ms = reduce_max([tot_ms, e2e_ms], dist, dev)
         ms_per_step = tot_ms / args.steps
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return None
 
-    value = rays_step * world / (ms_per_step * 1e-3) / 1e6
+    value = job_value(rays_step, world, ms_per_step)
     stage_ms = dict(zip(stages, st.mean(0).round(4).tolist()))
     pk, pk_kind = peaks()
     clocks = clk.summary()
@@ -372,7 +391,7 @@ def run_handrt(args):
                                                             "tuned": round(tune_best_ms, 4)},
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"{world} independent instance(s), one per GPU"},
-        "e2e": {"value": round(rays_step * world / (e2e_ms * 1e-3) / 1e6, 3), "unit": UNIT,
+        "e2e": {"value": round(job_value(rays_step, world, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "roofline": roof,
