@@ -144,6 +144,15 @@ typedef struct hr_render_opts {
                                   the same vertex and camera pointers, sizes and spp and
                                   no hr_build_bvh came after it; the caller guarantees
                                   that the contents of both arrays are unchanged      */
+#define HR_DETERMINISTIC 64u   /* hr_render_bwd: d_verts bit-identical on every call
+                                  with the same inputs -- each vertex-gradient
+                                  contribution is rounded to a multiple of 2^-40 and
+                                  summed as a 64-bit integer (exact, so the order of
+                                  the atomics does not matter); the interior shader
+                                  traces one sample per lane (whichever kernel traces
+                                  a sample does the same arithmetic) and the edge term
+                                  runs on the caller's stream.  d_texture sums stay
+                                  in float atomics (order-dependent rounding)         */
 
 /* Sizes a context is created for; all scratch is allocated once, up front. */
 typedef struct hr_limits {

@@ -31,6 +31,7 @@ HR_BWD_NO_NORMALS = 4
 HR_STATS = 8
 HR_TIMING = 16
 HR_BWD_REUSE_FWD = 32
+HR_DETERMINISTIC = 64
 KERNEL_TIMES = ("fwd_gather", "fwd_shade", "fwd_combine", "bwd_gather", "bwd_shade", "bwd_reduce", "silhouettes",
                 "edge_samples", "normal_adjoint")
 

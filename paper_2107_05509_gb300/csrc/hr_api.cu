@@ -44,7 +44,7 @@ void free_ctx(Context* c) {
                   c->status,  c->stats,   c->pool_bb,   c->pool_z,     c->pool_rec,      c->st_info,
                   c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it,
                   c->bvh_parent, c->bvh_valid, c->bvh_keys, c->bvh_flags, c->bvh_bounds, c->bvh_bad,
-                  c->bvh_mode, c->extra64, c->ct_partials, c->dedge, c->ovf_list};
+                  c->bvh_mode, c->extra64, c->ct_partials, c->dedge, c->ovf_list, c->acc_fx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete[] c->hvt;
@@ -109,7 +109,7 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
   bool ok = dev_alloc(&c->nodes, ni * F, a) && dev_alloc(&c->tris, ni * 3 * F, a) &&
             dev_alloc(&c->normals, ni * 3 * V, a) && dev_alloc(&c->normal_len, ni * V, a) &&
             dev_alloc(&c->partials, partial_blocks * 6 * V, a) && dev_alloc(&c->dN, ni * 3 * V, a) &&
-            dev_alloc(&c->dedge, ni * 3 * V, a) &&
+            dev_alloc(&c->dedge, ni * 3 * V, a) && dev_alloc(&c->acc_fx, ni * 6 * V, a) &&
             dev_alloc(&c->dm, ni * 3 * V, a) && dev_alloc(&c->sil, nviews * lim->max_E, a) &&
             dev_alloc(&c->sil_count, nviews, a) &&
             dev_alloc(&c->loss_partials, ni * hr::kLossStride(c->loss_blocks), a) &&

@@ -121,6 +121,7 @@ struct Context {
   float* partials;       // [render_blocks][max_V][6] (single-instance contexts)
   float* dN;             // [n_inst][max_V][3]
   float* dedge;          // [n_inst][max_V][3] the edge-sampling term's vertex sums
+  unsigned long long* acc_fx;   // [n_inst][max_V][6] fixed-point backward sums (HR_DETERMINISTIC)
   cudaStream_t side;     // the edge-sampling term runs here, beside the interior term
   cudaEvent_t ev_fork, ev_join;
   float* dm;             // [n_inst][max_V][3]

@@ -192,7 +192,8 @@ struct Work {
   float* z;        // [pool] nearest camera depth (sorted within a sub-tile)
   int* rec;        // [pool] triangle record
   int pool_cap;
-  int2* st;        // [sub-tiles] (pool offset, K): K = 0 no ray can hit, K < 0 per-ray traversal
+  int2* st;        // [sub-tiles] (pool offset, K): K = 0 no ray can hit, K < 0 per-ray
+                   // traversal (-1: too many candidates; -(n + 1): n found no pool room)
   int4* items;     // [items] (sub-tile, chunk, chunks, first item of the sub-tile)
   int item_cap;
   float4* part;    // [items][32] forward per-item sums (r, g, b, misses)
@@ -204,6 +205,8 @@ struct Work {
                    // fill and item counter, then the overflow count
   int* ovf;        // [sub-tiles] sub-tiles whose items did not fit their instance's
                    // region (k_overflow does them whole)
+  unsigned long long* fx;   // [n_inst][6V] fixed-point backward sums (HR_DETERMINISTIC)
+  bool det;                 // HR_DETERMINISTIC: every vertex-gradient sum goes to fx
 };
 
 struct RenderArgs {
@@ -344,6 +347,23 @@ __device__ __forceinline__ void add3(T* dst, int i, float x, float y, float z) {
   atomicAdd(&dst[3 * i], x);
   atomicAdd(&dst[3 * i + 1], y);
   atomicAdd(&dst[3 * i + 2], z);
+}
+
+// Fixed-point sums (HR_DETERMINISTIC): a contribution x is added as the 64-bit integer
+// round(x 2^40) (two's complement in an unsigned word); integer addition is exact and
+// associative, so the sums do not depend on the order of the atomics.
+constexpr double kFixScale = 1099511627776.0;   // 2^40
+__device__ __forceinline__ void add_fixed(unsigned long long* p, float x) {
+  atomicAdd(p, (unsigned long long)__double2ll_rn((double)x * kFixScale));
+}
+template <>
+__device__ __forceinline__ void add3<unsigned long long>(unsigned long long* dst, int i, float x, float y, float z) {
+  add_fixed(&dst[3 * i], x);
+  add_fixed(&dst[3 * i + 1], y);
+  add_fixed(&dst[3 * i + 2], z);
+}
+__device__ __forceinline__ float from_fixed(unsigned long long v) {
+  return (float)((double)(long long)v * (1.0 / kFixScale));
 }
 
 // ---------------------------------------------------------------------------------
@@ -538,8 +558,12 @@ __device__ int frustum_leaves(const RenderArgs& a, const Cam& cam, int x0, int y
 
 // work items of a sub-tile with K candidates (K < 0: per-ray traversal): one per
 // `cand_per_chunk` candidates, at most max_chunks and spp
+// (K = -1: more candidates than the gather's list holds; K < -1: -(K + 1) candidates
+// that found no room in the pool.)  The split depends on the geometry only, never on
+// which sub-tiles the pool served first, so sums over a sub-tile's items are
+// reproducible.
 __device__ __forceinline__ int chunks_for(const RenderArgs& a, int K, int spp) {
-  int c = K < 0 ? a.max_chunks : K / a.cand_per_chunk;
+  int c = K == -1 ? a.max_chunks : (K < 0 ? -K - 1 : K) / a.cand_per_chunk;
   return max(1, min(min(c, a.max_chunks), spp));
 }
 
@@ -921,10 +945,12 @@ __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile&
       }
       HitGrad hg;
       hit_grad(a, h[j], cf, d[j], g, hg);
+      // rounded adds: no contraction with the products inside hit_grad, so a run's sum
+      // is the same in every kernel that traces it
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        acc.dv[c] += hg.dv[c];
-        acc.dn[c] += hg.dn[c];
+        acc.dv[c] = __fadd_rn(acc.dv[c], hg.dv[c]);
+        acc.dn[c] = __fadd_rn(acc.dn[c], hg.dn[c]);
       }
     }
   }
@@ -1039,7 +1065,9 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
           a.wk.rec[off + c] = k;
         }
       } else {
-        K = -1;   // pool full: per-ray traversal for this sub-tile
+        // pool full: per-ray traversal for this sub-tile, with K's count kept as
+        // -(K + 1) so that its work items are split as they would be with the list
+        K = -(K + 1);
       }
     }
     const int C = chunks_for(a, K, t.spp);
@@ -1189,10 +1217,22 @@ __global__ void __launch_bounds__(kRenderThreads, BWD ? kBwdMinBlocks : 8) k_ove
     if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
     const Cam cam = load_cam(a.cams, t.view);
     if (BWD) {
+      // in the items' chunks too: each chunk's runs are added exactly as its work item
+      // would add them, so fixed-point sums do not depend on which sub-tiles overflowed
       bool live;
       const float3 g = lane_adjoint(a, t, adjoint, live);
-      float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
-      grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, 0, t.spp, live, g, ex, ex + 3 * a.V, cnt);
+      const int C = chunks_for(a, pk.y, t.spp);
+      for (int c = 0; c < C; ++c) {
+        int s0, s1;
+        item_samples(c, C, t.spp, s0, s1);
+        if (a.wk.det) {
+          unsigned long long* ex = a.wk.fx + (size_t)t.inst * 6 * a.V;
+          grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, live, g, ex, ex + 3 * a.V, cnt);
+        } else {
+          float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
+          grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, live, g, ex, ex + 3 * a.V, cnt);
+        }
+      }
     } else {
       // the same chunks and the same order of sums as work items and k_combine_fwd
       // would use, so a pixel's value does not depend on which path rendered it
@@ -1230,8 +1270,13 @@ __global__ void __launch_bounds__(kRenderThreads, BWD ? kBwdMinBlocks : 8) k_ove
       if (BWD) {
         bool live;
         const float3 g = lane_adjoint(a, t, adjoint, live);
-        float* ex = a.wk.extra + (size_t)inst * 6 * a.V;
-        grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, live, g, ex, ex + 3 * a.V, cnt);
+        if (a.wk.det) {
+          unsigned long long* ex = a.wk.fx + (size_t)inst * 6 * a.V;
+          grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, live, g, ex, ex + 3 * a.V, cnt);
+        } else {
+          float* ex = a.wk.extra + (size_t)inst * 6 * a.V;
+          grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, live, g, ex, ex + 3 * a.V, cnt);
+        }
       } else {
         float3 acc = make_float3(0.0f, 0.0f, 0.0f);
         int misses = 0;
@@ -1277,7 +1322,9 @@ __global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, fl
 //                 into that instance's extra [6V] (global atomics) and clears them
 //   kAccGlobal    meshes whose [V][6] sums exceed shared memory: every run of hits on
 //                 one triangle is added straight into the instance's extra [6V]
-constexpr int kAccPartials = 0, kAccFlush = 1, kAccGlobal = 2;
+//   kAccFixed     HR_DETERMINISTIC: every run goes straight into the instance's
+//                 fixed-point sums fx [6V] (order-free integer atomics)
+constexpr int kAccPartials = 0, kAccFlush = 1, kAccGlobal = 2, kAccFixed = 3;
 template <bool STATS, int ACC, int S>
 __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(RenderArgs a_in,
                                                                              const float* __restrict__ adjoint,
@@ -1285,7 +1332,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
                                                                              unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
   extern __shared__ float sacc[];
-  if (ACC != kAccGlobal) {
+  if (ACC == kAccPartials || ACC == kAccFlush) {
     for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) sacc[i] = 0.0f;
     __syncthreads();
   }
@@ -1293,10 +1340,14 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
   for (int inst = 0; inst < a0.n_inst; ++inst) {
     const int n = item_count(a0, inst), ibase = inst_ibase(a0, inst);
     const RenderArgs a = for_inst(a0, inst);
-    typedef typename std::conditional<ACC == kAccGlobal, double, float>::type AccT;
+    typedef typename std::conditional<
+        ACC == kAccGlobal, double, typename std::conditional<ACC == kAccFixed, unsigned long long, float>::type>::type
+        AccT;
     AccT* sdV;
     if constexpr (ACC == kAccGlobal)
       sdV = a0.wk.extra64 + (size_t)inst * 6 * a0.V;
+    else if constexpr (ACC == kAccFixed)
+      sdV = a0.wk.fx + (size_t)inst * 6 * a0.V;
     else
       sdV = sacc;
     AccT* sdN = sdV + 3 * a0.V;
@@ -1345,7 +1396,8 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
 constexpr int kRedEntries = 32, kRedGroups = 16;
 __global__ void __launch_bounds__(kRedEntries * kRedGroups) k_reduce_partials(
     const float* __restrict__ partials, const float* __restrict__ extra_all, const double* __restrict__ extra64_all,
-    int nblocks, int V, float* __restrict__ d_verts_all, float* __restrict__ dN_all) {
+    const unsigned long long* __restrict__ fx_all, int nblocks, int V, float* __restrict__ d_verts_all,
+    float* __restrict__ dN_all) {
   __shared__ float red[kRedGroups][kRedEntries];
   const int j = threadIdx.x % kRedEntries, g = threadIdx.x / kRedEntries;
   const int i = blockIdx.x * kRedEntries + j;
@@ -1362,6 +1414,7 @@ __global__ void __launch_bounds__(kRedEntries * kRedGroups) k_reduce_partials(
   float* dN = dN_all + (size_t)blockIdx.y * 3 * V;
   float tot = extra[i];
   if (extra64_all) tot = (float)(extra64_all[(size_t)blockIdx.y * 6 * V + i] + (double)tot);
+  if (fx_all) tot += from_fixed(fx_all[(size_t)blockIdx.y * 6 * V + i]);
   for (int q = 0; q < kRedGroups; ++q) tot += red[q][j];
   if (i < 3 * V) d_verts[i] = tot;
   else dN[i - 3 * V] = tot;
@@ -1498,12 +1551,16 @@ __device__ __forceinline__ float3 radiance_warp(const RenderArgs& a, const Cam& 
 // i % Ne_max of global view i / Ne_max (views with fewer samples skip the rest).  The
 // lanes compute the sample's set-up redundantly (same values, broadcast loads), search
 // the candidates of both offset rays together, and lanes 0-5 add the six results.
-template <bool STATS>
+__device__ __forceinline__ void add1(float* p, float x) { atomicAdd(p, x); }
+__device__ __forceinline__ void add1(unsigned long long* p, float x) { add_fixed(p, x); }
+
+// T: float sums (dedge [n_inst][3V]) or fixed-point sums (fx [n_inst][6V], dV part)
+template <bool STATS, class T>
 __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoint,
                                                                  const int* __restrict__ edges,
                                                                  const int* __restrict__ lists, int stride,
                                                                  const int* __restrict__ counts, int Ne_max, float eps,
-                                                                 float* __restrict__ d_verts_all,
+                                                                 T* __restrict__ d_verts_all, long long inst_stride,
                                                                  unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
   const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1517,7 +1574,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in
   if (k >= Ne) return;
   if (!in_range(a0.status, vw.inst, 0, a0.n_inst)) return;
   const RenderArgs a = for_inst(a0, vw.inst);
-  float* d_verts = d_verts_all + (size_t)vw.inst * 3 * a.V;
+  T* d_verts = d_verts_all + (size_t)vw.inst * inst_stride;
   int nsil = counts[view];
   if (nsil == 0) return;
   uint4 r = philox4x32_10(make_uint4((uint32_t)k, vw.ctr1, 0u, a.iter4 | 1u), a.key);
@@ -1575,7 +1632,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in
   float iz = 1.0f / Z;
   float gx = g2x * cam.fx * iz, gy = g2y * cam.fy * iz;
   float gz = -(gx * X + gy * Y) * iz;
-  atomicAdd(&d_verts[3 * (q == 0 ? ia : ib) + comp], cam.R[comp] * gx + cam.R[3 + comp] * gy + cam.R[6 + comp] * gz);
+  add1(&d_verts[3 * (q == 0 ? ia : ib) + comp], cam.R[comp] * gx + cam.R[3 + comp] * gy + cam.R[6 + comp] * gz);
 }
 
 // dm_v = (I - n n^T) dN_v / |m_v|; blockIdx.y selects the instance
@@ -1707,6 +1764,8 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.wk.extra64 = ctx->extra64;
   a.wk.ctr = ctx->work_ctr;
   a.wk.ovf = ctx->ovf_list;
+  a.wk.fx = ctx->acc_fx;
+  a.wk.det = (o->flags & HR_DETERMINISTIC) != 0;
   a.node_stride = ctx->lim.max_F;
   a.cand_per_chunk = ctx->tune.cand_per_chunk;
   a.max_chunks = ctx->tune.max_chunks;
@@ -1867,29 +1926,42 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
   // The edge-sampling term (silhouettes, edge samples into ctx->dedge) needs only the
   // candidate lists made above; it runs on the context's side stream beside the
   // interior shader and joins before the normals' adjoint adds it to d_verts.  With
-  // kernel timing on, everything stays on the caller's stream.
-  const bool fork = edges && !tm.on;
+  // kernel timing on, everything stays on the caller's stream.  HR_DETERMINISTIC:
+  // everything stays on the caller's stream, both terms add their vertex sums to the
+  // fixed-point array, and one reduction after both turns it into d_verts and dN.
+  const bool det = (o->flags & HR_DETERMINISTIC) != 0;
+  const bool fork = edges && !tm.on && !det;
   cudaStream_t es = fork ? ctx->side : s;
+  if (det && cudaMemsetAsync(ctx->acc_fx, 0, sizeof(unsigned long long) * 6 * V * ni, s) != cudaSuccess)
+    return HR_ERR_CUDA;
   if (edges) {
     if (fork && (cudaEventRecord(ctx->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(es, ctx->ev_fork, 0) != cudaSuccess))
       return HR_ERR_CUDA;
-    if (cudaMemsetAsync(ctx->dedge, 0, sizeof(float) * 3 * V * ni, es) != cudaSuccess) return HR_ERR_CUDA;
+    if (!det && cudaMemsetAsync(ctx->dedge, 0, sizeof(float) * 3 * V * ni, es) != cudaSuccess) return HR_ERR_CUDA;
   }
+  const auto reduce = [&](int acc, int nblocks) {
+    k_reduce_partials<<<dim3((6 * V + kRedEntries - 1) / kRedEntries, ni), kRedEntries * kRedGroups, 0, s>>>(
+        ctx->partials, ctx->extra, acc == kAccGlobal ? ctx->extra64 : nullptr, det ? ctx->acc_fx : nullptr,
+        acc == kAccPartials ? nblocks : 0, V, d_verts, ctx->dN);
+  };
   if (interior) {
     // shared-memory sums up to the opt-in of configure_render_kernels (V <= 8192),
-    // global float64 atomics beyond
+    // global float64 atomics beyond; fixed-point global sums when deterministic
     const bool global_acc = render_bwd_smem(V) > render_bwd_smem(8192);
-    if (global_acc && (!ctx->extra64 ||
-                       cudaMemsetAsync(ctx->extra64, 0, sizeof(double) * 6 * V * ni, s) != cudaSuccess))
+    if (!det && global_acc &&
+        (!ctx->extra64 || cudaMemsetAsync(ctx->extra64, 0, sizeof(double) * 6 * V * ni, s) != cudaSuccess))
       return ctx->extra64 ? HR_ERR_CUDA : HR_ERR_UNSUPPORTED;
-    const size_t smem = global_acc ? 0 : render_bwd_smem(V);
-    const int acc = global_acc ? kAccGlobal : (batch ? kAccFlush : kAccPartials);
-    const int S = ctx->tune.bwd_rays_per_lane;
+    const int acc = det ? kAccFixed : (global_acc ? kAccGlobal : (batch ? kAccFlush : kAccPartials));
+    const size_t smem = (acc == kAccPartials || acc == kAccFlush) ? render_bwd_smem(V) : 0;
+    // deterministic: one ray per lane, the arithmetic of the overflow kernel, which may
+    // trace any sub-tile whose candidates found no room in the pool
+    const int S = det ? 1 : ctx->tune.bwd_rays_per_lane;
 #define HR_BWD_KERNEL(A_) \
   (st ? (S == 1 ? k_shade_bwd<true, A_, 1> : (S == 2 ? k_shade_bwd<true, A_, 2> : k_shade_bwd<true, A_, 4>)) \
       : (S == 1 ? k_shade_bwd<false, A_, 1> : (S == 2 ? k_shade_bwd<false, A_, 2> : k_shade_bwd<false, A_, 4>)))
-    auto kern = acc == kAccGlobal ? HR_BWD_KERNEL(kAccGlobal)
-                                  : (acc == kAccFlush ? HR_BWD_KERNEL(kAccFlush) : HR_BWD_KERNEL(kAccPartials));
+    auto kern = acc == kAccFixed    ? HR_BWD_KERNEL(kAccFixed)
+                : acc == kAccGlobal ? HR_BWD_KERNEL(kAccGlobal)
+                                    : (acc == kAccFlush ? HR_BWD_KERNEL(kAccFlush) : HR_BWD_KERNEL(kAccPartials));
 #undef HR_BWD_KERNEL
     // the block partials are sized for kBlocksPerSm blocks per SM
     const int blocks = ctx->num_sms * ctx->tune.bwd_blocks_per_sm;
@@ -1902,13 +1974,13 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
       k_overflow<true, false><<<blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdShade);
-    tm.begin(kTimeBwdReduce);
-    k_reduce_partials<<<dim3((6 * V + kRedEntries - 1) / kRedEntries, ni), kRedEntries * kRedGroups, 0, s>>>(
-        ctx->partials, ctx->extra, acc == kAccGlobal ? ctx->extra64 : nullptr, acc == kAccPartials ? blocks : 0, V,
-        d_verts, ctx->dN);
-    HR_CHECK_LAUNCH();
-    tm.end(kTimeBwdReduce);
-  } else {
+    if (!det) {
+      tm.begin(kTimeBwdReduce);
+      reduce(acc, blocks);
+      HR_CHECK_LAUNCH();
+      tm.end(kTimeBwdReduce);
+    }
+  } else if (!det) {
     if (cudaMemsetAsync(d_verts, 0, sizeof(float) * 3 * V * ni, s) != cudaSuccess) return HR_ERR_CUDA;
   }
   if (edges) {
@@ -1917,15 +1989,27 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     if (rc != HR_OK) return rc;
     tm.end(kTimeBwdSil);
     const long long n = (long long)nv * Ne * 32;   // one warp per edge sample
-    auto kern = st ? k_edge_samples<true> : k_edge_samples<false>;
+    const unsigned grid = (unsigned)((n + kRenderThreads - 1) / kRenderThreads);
     tm.begin(kTimeBwdEdges);
-    kern<<<(unsigned)((n + kRenderThreads - 1) / kRenderThreads), kRenderThreads, 0, es>>>(
-        a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count, Ne, o->edge_eps_px, ctx->dedge,
-        ctx->stats + 2 * kStatsPer);
+    if (det) {
+      auto kern = st ? k_edge_samples<true, unsigned long long> : k_edge_samples<false, unsigned long long>;
+      kern<<<grid, kRenderThreads, 0, es>>>(a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count, Ne,
+                                            o->edge_eps_px, ctx->acc_fx, 6LL * V, ctx->stats + 2 * kStatsPer);
+    } else {
+      auto kern = st ? k_edge_samples<true, float> : k_edge_samples<false, float>;
+      kern<<<grid, kRenderThreads, 0, es>>>(a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count, Ne,
+                                            o->edge_eps_px, ctx->dedge, 3LL * V, ctx->stats + 2 * kStatsPer);
+    }
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdEdges);
     if (fork && (cudaEventRecord(ctx->ev_join, es) != cudaSuccess || cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess))
       return HR_ERR_CUDA;
+  }
+  if (det) {
+    tm.begin(kTimeBwdReduce);
+    reduce(kAccFixed, 0);
+    HR_CHECK_LAUNCH();
+    tm.end(kTimeBwdReduce);
   }
   if (normals) {
     tm.begin(kTimeBwdNormals);
@@ -1933,10 +2017,10 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     k_normal_dm<<<g, 256, 0, s>>>(ctx->normals, ctx->normal_len, ctx->dN, V, ctx->dm);
     HR_CHECK_LAUNCH();
     k_normal_gather<<<g, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, ctx->dm, V,
-                                      edges ? ctx->dedge : nullptr, d_verts);
+                                      edges && !det ? ctx->dedge : nullptr, d_verts);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdNormals);
-  } else if (edges) {
+  } else if (edges && !det) {
     const long long n3 = 3LL * V * ni;
     k_add_edges<<<(unsigned)((n3 + 255) / 256), 256, 0, s>>>(ctx->dedge, n3, d_verts);
     HR_CHECK_LAUNCH();

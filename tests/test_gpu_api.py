@@ -295,3 +295,36 @@ def test_item_region_overflow_matches_oracle(B):
         ok = grad_ok(gd, g_ref)
         assert ok.all(), (flags, np.argwhere(~ok)[:5], gd[~ok][:5], g_ref[~ok][:5])
     assert B.hr_get_status(ctx) == B.HR_OK
+
+
+def test_deterministic_backward_repeats_bit_for_bit(B):
+    """HR_DETERMINISTIC: the vertex gradient of repeated backward calls with the same
+    inputs is identical bit for bit (fixed-point sums), with a traversal of its own and
+    with the forward's candidate lists, and it is still the oracle's gradient."""
+    import oracle
+    from tests.gpu_common import grad_ok
+    sc = scene("ragged")
+    h = hand()
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, sc.N, sc.W, sc.H)
+    vt, cams, bg = _t(sc.verts), _t(sc.cams), _t(sc.bg)
+    o = sc.opts()
+    ref = oracle.render_fwd(sc.verts, h.faces, sc.normals, h.albedo, sc.cams, sc.H, sc.W, sc.bg, o)
+    _, A = oracle.loss(ref.astype(np.float32), sc.observed, sc.mask)
+    A = A.astype(np.float32)
+    g_ref, _ = oracle.render_bwd(h, sc.verts, sc.cams, sc.H, sc.W, sc.bg, o, A, normals=sc.normals)
+    img = torch.empty((sc.N, sc.H, sc.W, 3), device="cuda")
+    B.hr_build_bvh(ctx, model, vt)
+    B.hr_render_fwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o), img)
+    At = _t(A)
+    for flags in (B.HR_DETERMINISTIC, B.HR_DETERMINISTIC | B.HR_BWD_REUSE_FWD):
+        outs = []
+        for _ in range(3):
+            dv = torch.empty((h.V, 3), device="cuda")
+            B.hr_render_bwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o, flags), At, dv)
+            outs.append(dv)
+        assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2]), flags
+        g = outs[0].cpu().numpy()
+        ok = grad_ok(g, g_ref)
+        assert ok.all(), (flags, np.argwhere(~ok)[:5], g[~ok][:5], g_ref[~ok][:5])
+    assert B.hr_get_status(ctx) == B.HR_OK

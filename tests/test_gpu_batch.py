@@ -134,8 +134,9 @@ def test_batch_forward_loss_backward(setup):
     A_all = _t(_cat(A_refs, (3,)))
     refs = [oracle.render_bwd(h, i.verts, i.cams, i.H, i.W, i.bg, i.opts, A_refs[k], normals=i.normals)[0]
             for k, i in enumerate(insts)]
-    # a traversal of its own, and the forward's candidate lists (HR_BWD_REUSE_FWD)
-    for flags in (0, B.HR_BWD_REUSE_FWD):
+    # a traversal of its own, the forward's candidate lists (HR_BWD_REUSE_FWD), and
+    # fixed-point sums (HR_DETERMINISTIC: a repeated call is bit-identical)
+    for flags in (0, B.HR_BWD_REUSE_FWD, B.HR_DETERMINISTIC):
         B.hr_render_bwd_batch(bt, model, verts, cams, bg, _gopts(B, insts[0].opts, flags), A_all, dv)
         gd = dv.cpu().numpy()
         for k, i in enumerate(insts):
@@ -143,6 +144,10 @@ def test_batch_forward_loss_backward(setup):
             assert np.abs(ref).max() > 0
             ok = grad_ok(gd[k], ref)
             assert ok.all(), (flags, k, np.argwhere(~ok)[:5], gd[k][~ok][:5], ref[~ok][:5])
+        if flags == B.HR_DETERMINISTIC:
+            again = torch.empty_like(dv)
+            B.hr_render_bwd_batch(bt, model, verts, cams, bg, _gopts(B, insts[0].opts, flags), A_all, again)
+            assert torch.equal(again, dv)
     assert B.hr_get_status(bt) == B.HR_OK
 
 

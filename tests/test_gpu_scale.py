@@ -105,9 +105,13 @@ def test_scale_render_forward_backward(setup):
     A[:, ::6] = rng.choice([-1.0, 1.0], size=A[:, ::6].shape).astype(np.float32) * 1e-5
     ref, _ = oracle.render_bwd(h, verts, cams, H, W, bg, o, A, normals=normals)
     dv = torch.empty((h.V, 3), device="cuda")
-    for flags in (0, B.HR_BWD_REUSE_FWD):
+    for flags in (0, B.HR_BWD_REUSE_FWD, B.HR_DETERMINISTIC):
         B.hr_render_bwd(ctx, model, vt, ct, H, W, bt, _go(B, o, flags), _t(A), dv)
         gg = dv.cpu().numpy()
         ok = grad_ok(gg, ref)
         assert ok.all(), (flags, np.argwhere(~ok)[:5], gg[~ok][:5], ref[~ok][:5])
+    # fixed-point sums: a repeated deterministic call is bit-identical
+    again = torch.empty_like(dv)
+    B.hr_render_bwd(ctx, model, vt, ct, H, W, bt, _go(B, o, B.HR_DETERMINISTIC), _t(A), again)
+    assert torch.equal(again, dv)
     assert B.hr_get_status(ctx) == B.HR_OK
