@@ -246,3 +246,35 @@ def test_paper_size_sampled_rows_match_oracle(B, model):
     ok = grad_ok(gg, ref)
     assert ok.all(), (np.argwhere(~ok)[:5], gg[~ok][:5], ref[~ok][:5])
     assert B.hr_get_status(ctx) == B.HR_OK
+
+
+def test_lbvh_closest_hits_on_a_million_rays(B, model):
+    """The LBVH's closest hit (triangle, t, u, v) equals the brute-force closest hit
+    over all triangles for 10^6 random rays: from the cameras toward points near the
+    surface (grazing and interior hits), and from points around the hand in uniform
+    random directions (many misses, rays starting inside the hull)."""
+    sc = scene("tiny")
+    h = hand()
+    ctx = _ctx(B, sc)
+    B.hr_build_bvh(ctx, model, _t(sc.verts))
+    rng = np.random.default_rng(12)
+    n1 = 600_000
+    cam = sc.cams[rng.integers(0, sc.N, n1)]
+    o1 = cam[:, 16:19]
+    tgt = sc.verts[rng.integers(0, h.V, n1)] + rng.normal(0, 0.006, (n1, 3)).astype(np.float32)
+    n2 = 400_000
+    centre = sc.verts.mean(0)
+    o2 = centre + rng.normal(0, 0.05, (n2, 3))
+    d2 = rng.normal(size=(n2, 3))
+    o = np.concatenate([o1, o2]).astype(np.float32)
+    d = np.concatenate([tgt - o1, d2]).astype(np.float32)
+    tri = torch.empty(len(o), dtype=torch.int32, device="cuda")
+    tuv = torch.empty((len(o), 3), device="cuda")
+    B.hr_trace(ctx, _t(o), _t(d), tri, tuv)
+    rtri, rtuv = oracle.closest_hits(o, d, sc.verts, h.faces)
+    gtri = tri.cpu().numpy()
+    assert 0.2 < (rtri >= 0).mean() < 0.95
+    assert np.array_equal(gtri, rtri)
+    hit = rtri >= 0
+    assert np.array_equal(tuv.cpu().numpy()[hit], rtuv[hit])
+    assert B.hr_get_status(ctx) == B.HR_OK
