@@ -56,7 +56,7 @@ constexpr int kBwdMinBlocks = 4;      // launch bound of the backward shader (12
 constexpr int kBlocksPerSm = 8;       // largest persistent grid; backward partials are sized for it
 constexpr int kSubW = 8, kSubH = 4;   // sub-tile; lane = pixel
 constexpr int kLeafCap = 512;         // candidates per sub-tile
-constexpr int kFrontCap = 64;         // breadth-first frontier per level
+constexpr int kFrontCap = 256;        // breadth-first frontier per level (dense meshes need the width)
 constexpr int kMaxChunks = 16;        // work items per sub-tile (largest setting)
 
 // Self-check of an index read from device memory (BVH children, candidate records,
