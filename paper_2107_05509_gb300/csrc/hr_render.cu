@@ -57,7 +57,6 @@ constexpr int kBlocksPerSm = 8;       // largest persistent grid; backward parti
 constexpr int kSubW = 8, kSubH = 4;   // sub-tile; lane = pixel
 constexpr int kLeafCap = 512;         // candidates per sub-tile
 constexpr int kFrontCap = 256;        // breadth-first frontier per level (dense meshes need the width)
-constexpr int kMaxChunks = 16;        // work items per sub-tile (largest setting)
 
 // Self-check of an index read from device memory (BVH children, candidate records,
 // pool offsets, work items): out of range sets a status bit and the caller skips
@@ -688,7 +687,6 @@ __device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, 
 
 // Radiance sums of samples [s0, s1) of this lane's pixel (all lanes call it), traced
 // S at a time (the tuning's rays per lane); the radiance is added in sample order.
-constexpr int kRaysPerLane = 4;   // for the gather kernels' fall-back paths
 template <bool STATS, int S, bool TRACE = true>
 __device__ __forceinline__ void shade_samples(const RenderArgs& a, const SubTile& t, const Cam& cam, int off, int K,
                                               int s0, int s1, float3& acc, int& misses, Counts& cnt) {
