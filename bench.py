@@ -17,8 +17,8 @@ library's HR_STATS pass.  The count is a property of the workload, not of how th
 renderer finds each sample's closest hit (a sub-tile whose frustum misses the scene
 resolves its samples without tracing them one by one; the counters report both).
 Device-timed with CUDA events, inputs resident in HBM, L2 flushed between steps.  e2e: the same rays per step over the wall time of the public
-Python API with the step's inputs copied from pinned host memory and the loss and
-gradient read back every step.
+Python API's captured step (Refiner.capture_step) with the step's inputs and sample
+counter copied from pinned host memory and the loss and gradient read back every step.
 
 --impl reference times the CPU oracle (brute force, all host cores) on a bounded
 sample of the same workload.  Under torchrun every rank refines its own hand instance
@@ -305,21 +305,33 @@ def run_handrt(args):
     h_loss, h_grad = torch.empty(1).pin_memory(), torch.empty(61).pin_memory()
     e2e_views = P.Views(cams=torch.empty_like(views.cams), background=torch.empty_like(views.background),
                         observed=torch.empty_like(views.observed), mask=torch.empty_like(views.mask), H=H, W=W)
-    e2e_ref = P.Refiner(model, e2e_views, opts, ctx=ctx)
+    # the public API's captured step (Refiner.capture_step): every step copies its
+    # inputs and the sample-stream counter from pinned host memory, replays the graph
+    # and reads the loss and the gradient back
+    e_iter = torch.zeros(1, dtype=torch.int32, device=dev)
+    # one pinned word per step: an asynchronous copy reads its host word when it runs
+    h_iters = torch.arange(args.warmup + args.steps + 1, dtype=torch.int32).pin_memory()
+    e2e_opts = P.opts_for(cfg, iter_dev=e_iter)
+    e2e_opts.instance = inst_field
+    e2e_ref = P.Refiner(model, e2e_views, e2e_opts, ctx=ctx)
     e_params = torch.empty(61, device=dev)
-    h2d = sum(t.numel() * t.element_size() for t in (h_obs, h_mask, h_bg, h_cams, h_x))
+    for dst, src in ((e2e_views.observed, h_obs), (e2e_views.mask, h_mask), (e2e_views.background, h_bg),
+                     (e2e_views.cams, h_cams), (e_params, h_x)):
+        dst.copy_(src)
+    e2e_graph = e2e_ref.capture_step(e_params)
+    h2d = sum(t.numel() * t.element_size() for t in (h_obs, h_mask, h_bg, h_cams, h_x)) + 4
     d2h = h_loss.numel() * 4 + h_grad.numel() * 4
 
     def e2e_step(i):
-        opts.iter = i
+        e_iter.copy_(h_iters[i:i + 1], non_blocking=True)
         e2e_views.observed.copy_(h_obs, non_blocking=True)
         e2e_views.mask.copy_(h_mask, non_blocking=True)
         e2e_views.background.copy_(h_bg, non_blocking=True)
         e2e_views.cams.copy_(h_cams, non_blocking=True)
         e_params.copy_(h_x, non_blocking=True)
-        loss, grad = e2e_ref.step(e_params)
-        h_loss.copy_(loss, non_blocking=True)
-        h_grad.copy_(grad, non_blocking=True)
+        e2e_graph.replay()
+        h_loss.copy_(e2e_ref.loss, non_blocking=True)
+        h_grad.copy_(e2e_ref.d_params, non_blocking=True)
 
     for w in range(args.warmup):
         e2e_step(w)

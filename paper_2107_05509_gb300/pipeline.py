@@ -79,6 +79,23 @@ class Refiner:
         loss = self.forward(params, stream)
         return loss, self.backward(params, stream)
 
+    def capture_step(self, params):
+        """step(params) recorded once as a CUDA graph and returned: each replay re-reads
+        `params`, the views' tensors and, through opts.iter_dev when it is set, the
+        device iteration counter, so a caller refreshes those tensors in place (host
+        copies, a counter) and replays; loss, image, adjoint and d_params are written
+        as by step().  The first launches run eagerly on a side stream (kernel loading
+        is not capturable)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step(params, s)
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.step(params, s)
+        return g
+
     def adam(self, params, iters, lr=0.01, betas=(0.9, 0.999), eps=1e-8, callback=None, stream=None):
         """Plain refinement: `iters` Adam steps on params (device float[61], updated
         in place).  The sample seed advances with the iteration."""
