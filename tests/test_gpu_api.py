@@ -328,3 +328,31 @@ def test_deterministic_backward_repeats_bit_for_bit(B):
         ok = grad_ok(g, g_ref)
         assert ok.all(), (flags, np.argwhere(~ok)[:5], g[~ok][:5], g_ref[~ok][:5])
     assert B.hr_get_status(ctx) == B.HR_OK
+
+
+def test_capture_step_replays_the_eager_step(B):
+    """Refiner.capture_step: replaying the recorded step gives the eager step's loss
+    (bit for bit) and gradient; a new value of the device counter draws new samples."""
+    from paper_2107_05509_gb300 import pipeline as P
+    sc = scene("tiny")
+    h = hand()
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, sc.N, sc.W, sc.H)
+    views = P.Views(cams=_t(sc.cams), background=_t(sc.bg), observed=_t(sc.observed), mask=_t(sc.mask),
+                    H=sc.H, W=sc.W)
+    counter = torch.full((1,), 5, dtype=torch.int32, device="cuda")
+    ref = P.Refiner(model, views, P.opts_for(sc.cfg, iter_dev=counter), ctx=ctx)
+    x = _t(sc.x0.astype(np.float32))
+    loss_e, grad_e = ref.step(x)
+    loss_e, grad_e = loss_e.clone(), grad_e.clone()
+    g = ref.capture_step(x)
+    ref.loss.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(ref.loss, loss_e)
+    assert torch.allclose(ref.d_params, grad_e, rtol=1e-5, atol=1e-7 * float(grad_e.abs().max()))
+    counter.fill_(6)
+    g.replay()
+    torch.cuda.synchronize()
+    assert not torch.equal(ref.loss, loss_e)
+    assert B.hr_get_status(ctx) == B.HR_OK
