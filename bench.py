@@ -16,9 +16,11 @@ edges: the two rays of each edge sample that lands on such a pixel -- counted by
 library's HR_STATS pass.  The count is a property of the workload, not of how the
 renderer finds each sample's closest hit (a sub-tile whose frustum misses the scene
 resolves its samples without tracing them one by one; the counters report both).
-Device-timed with CUDA events, inputs resident in HBM, L2 flushed between steps.  e2e: the same rays per step over the wall time of the public
-Python API's captured step (Refiner.capture_step) with the step's inputs and sample
-counter copied from pinned host memory and the loss and gradient read back every step.
+Device-timed with CUDA events, inputs resident in HBM, L2 flushed between steps.  e2e:
+the same rays per step through the public Python API (StreamedRefiner: the captured
+step, Refiner.capture_step, on two input slots), every step's inputs and sample counter
+copied from pinned host memory and its loss and gradient read back, the copy of step
+k + 1 overlapping step k; serial_ms_per_step is the same without the overlap.
 
 --impl reference times the CPU oracle (brute force, all host cores) on a bounded
 sample of the same workload.  Under torchrun every rank refines its own hand instance
@@ -307,7 +309,7 @@ def run_handrt(args):
                         observed=torch.empty_like(views.observed), mask=torch.empty_like(views.mask), H=H, W=W)
     # the public API's captured step (Refiner.capture_step): every step copies its
     # inputs and the sample-stream counter from pinned host memory, replays the graph
-    # and reads the loss and the gradient back
+    # and reads the loss and the gradient back, one after another on one stream
     e_iter = torch.zeros(1, dtype=torch.int32, device=dev)
     # one pinned word per step: an asynchronous copy reads its host word when it runs
     h_iters = torch.arange(args.warmup + args.steps + 1, dtype=torch.int32).pin_memory()
@@ -322,7 +324,7 @@ def run_handrt(args):
     h2d = sum(t.numel() * t.element_size() for t in (h_obs, h_mask, h_bg, h_cams, h_x)) + 4
     d2h = h_loss.numel() * 4 + h_grad.numel() * 4
 
-    def e2e_step(i):
+    def serial_step(i):
         e_iter.copy_(h_iters[i:i + 1], non_blocking=True)
         e2e_views.observed.copy_(h_obs, non_blocking=True)
         e2e_views.mask.copy_(h_mask, non_blocking=True)
@@ -333,22 +335,40 @@ def run_handrt(args):
         h_loss.copy_(e2e_ref.loss, non_blocking=True)
         h_grad.copy_(e2e_ref.d_params, non_blocking=True)
 
-    for w in range(args.warmup):
-        e2e_step(w)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    e0.record(stream)
-    for k in range(args.steps):
-        e2e_step(k)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
+    # the streamed public API (StreamedRefiner): the same copies, graph and read-back,
+    # the copy of step k + 1 overlapping step k (two input slots)
+    streamer = P.StreamedRefiner(model, e2e_views, e2e_opts, ctx=ctx, params=e_params)
+    frames = [P.HostFrame(observed=h_obs, mask=h_mask, background=h_bg, cams=h_cams, params=h_x,
+                          iter=h_iters[i:i + 1]) for i in range(args.warmup + args.steps)]
+    h_losses = torch.empty(args.warmup + args.steps).pin_memory()
+    h_grads = torch.empty(args.warmup + args.steps, 61).pin_memory()
+
+    def streamed_step(i):
+        streamer.submit(frames[i], h_losses[i:i + 1], h_grads[i], stream)
+
+    def time_e2e(step_fn, tail):
+        for w in range(args.warmup):
+            step_fn(w)
+        tail()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        e0.record(stream)
+        streamer.order_after(stream)
+        for k in range(args.steps):
+            step_fn(args.warmup + k)
+        tail()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    serial_ms = time_e2e(serial_step, lambda: None)
+    e2e_ms = time_e2e(streamed_step, lambda: streamer.join(stream))
     opts.iter = 0
 
     if dist:
-        tot_ms, e2e_ms = reduce_max([tot_ms, e2e_ms], dist, dev)
+        tot_ms, e2e_ms, serial_ms = reduce_max([tot_ms, e2e_ms, serial_ms], dist, dev)
         ms_per_step = tot_ms / args.steps
     if rank != 0:
         if dist:
@@ -404,7 +424,9 @@ def run_handrt(args):
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"{world} independent instance(s), one per GPU"},
         "e2e": {"value": round(job_value(rays_step, world, e2e_ms), 3), "unit": UNIT,
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4),
+                "api": "StreamedRefiner (copy of step k+1 overlaps step k)",
+                "serial_ms_per_step": round(serial_ms, 4)},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "roofline": roof,
         "clocks": clocks,

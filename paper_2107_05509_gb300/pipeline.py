@@ -112,6 +112,106 @@ class Refiner:
         return params
 
 
+@dataclasses.dataclass
+class HostFrame:
+    """One step's inputs in pinned host memory: a multiframe (the shapes and dtypes of
+    Views' tensors), the 61 parameters and the sample-stream counter (int32[1])."""
+    observed: torch.Tensor
+    mask: torch.Tensor
+    background: torch.Tensor
+    cams: torch.Tensor
+    params: torch.Tensor
+    iter: torch.Tensor
+
+
+@dataclasses.dataclass
+class _Slot:
+    ref: Refiner
+    params: torch.Tensor
+    counter: torch.Tensor
+    graph: torch.cuda.CUDAGraph
+    free: torch.cuda.Event   # the last step on this slot has been read back
+
+
+class StreamedRefiner:
+    """Refiner.step over a sequence of host-resident frames, each step's inputs copied
+    to the device while the step before runs.
+
+    Two device copies of the inputs alternate, each with its own Refiner (one shared
+    context) and its own captured step.  For step k a copy stream fills slot k % 2
+    from pinned host memory once the step that last used the slot has been read
+    back; the caller's stream waits for that copy and replays the slot's graph; a
+    read-back stream copies the loss and the parameter gradient to pinned host
+    memory.  The copy of step k + 1 thus overlaps the render of step k, and the
+    steps themselves run one after another on the caller's stream (they share the
+    context's scratch)."""
+
+    def __init__(self, model: B.Model, views: Views, opts: B.hr_render_opts, ctx: B.Context | None = None,
+                 params: torch.Tensor | None = None):
+        """views: a device multiframe whose shapes and dtypes every frame has; its
+        contents, and params (device float[61], zeros if None), seed the capture.
+        opts: the render options (each slot takes a copy whose iter_dev points at the
+        slot's own counter)."""
+        dev = views.cams.device
+        self.copy_stream = torch.cuda.Stream(device=dev)
+        self.read_stream = torch.cuda.Stream(device=dev)
+        self.slots = []
+        for _ in range(2):
+            counter = torch.zeros(1, dtype=torch.int32, device=dev)
+            o = B.hr_render_opts.from_buffer_copy(opts)
+            o.iter_dev = counter.data_ptr()
+            v = Views(cams=views.cams.clone(), background=views.background.clone(), observed=views.observed.clone(),
+                      mask=views.mask.clone(), H=views.H, W=views.W)
+            ref = Refiner(model, v, o, ctx=ctx)
+            ctx = ref.ctx
+            p = params.clone() if params is not None else torch.zeros(61, device=dev)
+            graph = ref.capture_step(p)
+            slot = _Slot(ref, p, counter, graph, torch.cuda.Event())
+            slot.free.record(torch.cuda.current_stream(dev))
+            self.slots.append(slot)
+        self.ctx = ctx
+        self.k = 0
+
+    def order_after(self, stream=None):
+        """Start the next copies only after the work already queued on `stream`."""
+        s = stream or torch.cuda.current_stream()
+        self.copy_stream.wait_stream(s)
+
+    def submit(self, frame: HostFrame, h_loss: torch.Tensor, h_grad: torch.Tensor, stream=None):
+        """Queue one step on `frame`; its loss (float[1]) and d_params (float[61]) land
+        in the pinned tensors h_loss and h_grad.  Returns (copied, done): events after
+        which the frame's host memory may be reused and the outputs are valid."""
+        s = stream or torch.cuda.current_stream()
+        slot = self.slots[self.k % 2]
+        self.k += 1
+        v = slot.ref.views
+        cs = self.copy_stream
+        cs.wait_event(slot.free)
+        with torch.cuda.stream(cs):
+            for dst, src in ((v.observed, frame.observed), (v.mask, frame.mask), (v.background, frame.background),
+                             (v.cams, frame.cams), (slot.params, frame.params), (slot.counter, frame.iter)):
+                dst.copy_(src, non_blocking=True)
+        copied = torch.cuda.Event()
+        copied.record(cs)
+        s.wait_event(copied)
+        with torch.cuda.stream(s):
+            slot.graph.replay()
+        rs = self.read_stream
+        rs.wait_stream(s)
+        with torch.cuda.stream(rs):
+            h_loss.copy_(slot.ref.loss, non_blocking=True)
+            h_grad.copy_(slot.ref.d_params, non_blocking=True)
+        slot.free = torch.cuda.Event()
+        slot.free.record(rs)
+        return copied, slot.free
+
+    def join(self, stream=None):
+        """Make `stream` wait for every queued copy and read-back."""
+        s = stream or torch.cuda.current_stream()
+        s.wait_stream(self.copy_stream)
+        s.wait_stream(self.read_stream)
+
+
 class HandRenderLoss(torch.autograd.Function):
     """loss = E_1(params); backward re-traces the samples (no stored hit records)."""
 

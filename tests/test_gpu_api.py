@@ -356,3 +356,46 @@ def test_capture_step_replays_the_eager_step(B):
     torch.cuda.synchronize()
     assert not torch.equal(ref.loss, loss_e)
     assert B.hr_get_status(ctx) == B.HR_OK
+
+
+def test_streamed_refiner_matches_eager_steps(B):
+    """StreamedRefiner: every submitted frame (its own parameters and counter, copied
+    from pinned host memory while the step before runs) gives the loss of an eager
+    step on the same inputs, bit for bit, and its gradient."""
+    from paper_2107_05509_gb300 import pipeline as P
+    sc = scene("tiny")
+    h = hand()
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, sc.N, sc.W, sc.H)
+    views = P.Views(cams=_t(sc.cams), background=_t(sc.bg), observed=_t(sc.observed), mask=_t(sc.mask),
+                    H=sc.H, W=sc.W)
+    x0 = sc.x0.astype(np.float32)
+    xs = [x0, x0 + np.float32(0.01), x0, x0 - np.float32(0.01), x0]
+    counters = [5, 6, 7, 8, 9]
+    counter = torch.zeros(1, dtype=torch.int32, device="cuda")
+    opts = P.opts_for(sc.cfg, iter_dev=counter)
+    ref = P.Refiner(model, views, opts, ctx=ctx)
+    want = []
+    for x, c in zip(xs, counters):
+        counter.fill_(c)
+        loss, grad = ref.step(_t(x))
+        want.append((loss.clone(), grad.clone()))
+    pin = lambda t: t.cpu().pin_memory()
+    frames = [P.HostFrame(observed=pin(views.observed), mask=pin(views.mask), background=pin(views.background),
+                          cams=pin(views.cams), params=torch.from_numpy(x).pin_memory(),
+                          iter=torch.tensor([c], dtype=torch.int32).pin_memory()) for x, c in zip(xs, counters)]
+    streamer = P.StreamedRefiner(model, views, opts, ctx=ctx, params=_t(x0))
+    h_loss = torch.zeros(len(frames)).pin_memory()
+    h_grad = torch.zeros(len(frames), 61).pin_memory()
+    s = torch.cuda.current_stream()
+    streamer.order_after(s)
+    for i, f in enumerate(frames):
+        streamer.submit(f, h_loss[i:i + 1], h_grad[i], s)
+    streamer.join(s)
+    torch.cuda.synchronize()
+    for i, (loss, grad) in enumerate(want):
+        assert float(h_loss[i]) == float(loss.cpu()[0]), i
+        g = grad.cpu()
+        assert torch.allclose(h_grad[i], g, rtol=1e-5, atol=1e-7 * float(g.abs().max())), i
+    assert float(h_loss[0]) != float(h_loss[1])
+    assert B.hr_get_status(ctx) == B.HR_OK
