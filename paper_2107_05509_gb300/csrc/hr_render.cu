@@ -928,21 +928,35 @@ __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile&
         if (TRACE && lv[j]) h[j] = trace<STATS>(a.nodes, a.tris, o, d[j], a.status, cnt, a.max_visits);
       }
     }
-#pragma unroll
+    // one copy of the differentiation for the S rays (the trace above is unrolled for
+    // its independent loads; unrolling this too multiplies the kernel's largest body
+    // S times and the warps then wait on instruction fetch): ray j is picked by
+    // selects, which keeps h and d in registers
+#pragma unroll 1
     for (int j = 0; j < S; ++j) {
-      if (!lv[j] || h[j].tri < 0) continue;
+      bool lj = lv[0];
+      Hit hj = h[0];
+      float3 dj = d[0];
+#pragma unroll
+      for (int q = 1; q < S; ++q)
+        if (j == q) {
+          lj = lv[q];
+          hj = h[q];
+          dj = d[q];
+        }
+      if (!lj || hj.tri < 0) continue;
       if (STATS) ++cnt.hits;
-      if (h[j].tri != cur) {
+      if (hj.tri != cur) {
         if (cur >= 0) {
           flush_tri(cf, acc, dV, dN);
 #pragma unroll
           for (int c = 0; c < 9; ++c) acc.dv[c] = acc.dn[c] = 0.0f;
         }
-        cur = h[j].tri;
+        cur = hj.tri;
         cf = make_int3(__ldg(&a.faces[3 * cur]), __ldg(&a.faces[3 * cur + 1]), __ldg(&a.faces[3 * cur + 2]));
       }
       HitGrad hg;
-      hit_grad(a, h[j], cf, d[j], g, hg);
+      hit_grad(a, hj, cf, dj, g, hg);
       // rounded adds: no contraction with the products inside hit_grad, so a run's sum
       // is the same in every kernel that traces it
 #pragma unroll
