@@ -2,14 +2,16 @@
 // vertices) as linear blend skinning, and its adjoint.
 //
 //   k_skin      every block first builds the J joint transforms in shared memory
-//               (one thread walks the kinematic chain: Rodrigues per joint, parents
-//               before children), then each thread blends one vertex.
+//               (Rodrigues per joint in parallel, then the kinematic tree composed
+//               level by level, parents before children), then each thread blends
+//               one vertex.
 //   k_skin_bwd  per vertex the gradients w.r.t. the blended transforms A_j, the
-//               shape coefficients (through the blendshapes) and the translation;
-//               warp sums accumulate per warp in shared memory (no atomics), blocks
+//               shape coefficients (through the blendshapes) and the translation:
+//               the block stages its vertices' terms in shared memory and one
+//               thread per output sums them in vertex order (no atomics), blocks
 //               write one partial each, and the last block to finish sums the
-//               partials in block order and runs the chain backward in one thread.
-//               Fully deterministic.
+//               partials in block order and runs the chain backward level by level
+//               (children before parents).  Fully deterministic.
 #include <mutex>
 
 #include "hr_internal.h"
@@ -29,6 +31,9 @@ struct Chain {
   float J[kMaxJ][3];    // shaped joints
   float beta[kMaxK];
   float tau[3];
+  int par[kMaxJ];       // checked parent of each joint (-1 for the root)
+  int depth[kMaxJ];     // level of each joint in the kinematic tree (root 0)
+  int levels;           // 1 + the deepest level
 };
 
 __device__ void rod_coeffs(float t, float& A, float& B, float& C, float& D) {
@@ -104,19 +109,46 @@ struct ModelArgs {
   int V, J, K;
 };
 
+// joint j's parent as the chain uses it: parents must precede children and only joint
+// 0 is a root; a parent that breaks this is taken as joint 0 (as -1 for joint 0) and
+// reported (report = true) in the status word
+__device__ __forceinline__ int chain_parent(const ModelArgs& m, int j, int* status, bool report) {
+  int p = m.parents[j];
+  if (p >= j || p < -1 || (j == 0) != (p < 0)) {
+    if (report) set_status(status, kStatusBadModel);
+    p = j == 0 ? -1 : 0;
+  }
+  return p;
+}
+
 // the forward kinematic chain into shared memory, called by every thread of the
-// block: per-joint work (shaped joint, local rotation) in parallel, then one thread
-// composes parents before children
+// block: per-joint work (shaped joint, local rotation) in parallel, then the
+// composition level by level of the kinematic tree (thread j composes joint j once
+// its parent, one level up, is done; one barrier per level, the same arithmetic per
+// joint as a parents-first walk)
 __device__ void build_chain(const ModelArgs& m, const float* __restrict__ params, Chain& ch, int* status) {
   const int tid = threadIdx.x;
   if (tid < 61 && !isfinite(params[tid])) set_status(status, kStatusNonfinite);
   if (tid < m.K) ch.beta[tid] = params[tid];
   if (tid < 3) ch.tau[tid] = params[58 + tid];
+  if (tid < m.J) {   // depth of joint j (a chain of checked parents ends within j steps)
+    const int p = chain_parent(m, tid, status, true);
+    int d = 0;
+    for (int q = p; q >= 0; q = chain_parent(m, q, status, false)) ++d;
+    ch.par[tid] = p;
+    ch.depth[tid] = d;
+  }
   __syncthreads();
   if (tid < 3 * m.J) {
     const int j = tid / 3, c = tid % 3;
-    float acc = m.j_template[3 * j + c];
-    for (int k = 0; k < m.K; ++k) acc += m.j_shapedirs[(3 * j + c) * m.K + k] * ch.beta[k];
+    const float* row = m.j_shapedirs + (3 * j + c) * m.K;
+    float Sj[kMaxK];
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) Sj[k] = k < m.K ? __ldg(row + k) : 0.0f;
+    float acc = __ldg(m.j_template + 3 * j + c);
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k)
+      if (k < m.K) acc += Sj[k] * ch.beta[k];
     ch.J[j][c] = acc;
   }
   if (tid >= 64 && tid < 64 + m.J) {
@@ -125,14 +157,16 @@ __device__ void build_chain(const ModelArgs& m, const float* __restrict__ params
     float rr[3] = {r[0], r[1], r[2]};
     rodrigues(rr, ch.Rl[j]);
   }
-  __syncthreads();
   if (tid == 0) {
-    for (int j = 0; j < m.J; ++j) {
-      int p = m.parents[j];
-      if (p >= j || p < -1 || (j == 0) != (p < 0)) {   // parents must precede children; only joint 0 is a root
-        set_status(status, kStatusBadModel);
-        p = j == 0 ? -1 : 0;
-      }
+    int d = 0;
+    for (int j = 0; j < m.J; ++j) d = max(d, ch.depth[j]);
+    ch.levels = d + 1;
+  }
+  __syncthreads();
+  const int levels = ch.levels;
+  for (int L = 0; L < levels; ++L) {
+    if (tid < m.J && ch.depth[tid] == L) {
+      const int j = tid, p = ch.par[j];
       if (p < 0) {
         for (int i = 0; i < 9; ++i) ch.RG[j][i] = ch.Rl[j][i];
         for (int c = 0; c < 3; ++c) ch.tG[j][c] = ch.J[j][c];
@@ -149,16 +183,34 @@ __device__ void build_chain(const ModelArgs& m, const float* __restrict__ params
         ch.tA[j][a] = ch.tG[j][a] - (ch.RG[j][3 * a] * ch.J[j][0] + ch.RG[j][3 * a + 1] * ch.J[j][1] +
                                      ch.RG[j][3 * a + 2] * ch.J[j][2]);
     }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
-__device__ __forceinline__ float3 shaped_vertex(const ModelArgs& m, const Chain& ch, int v) {
+// vertex v's rows of the blendshape basis, S[c][k] = shapedirs[3v + c][k] (zero for
+// k >= K) and its skinning weights wv[j] (zero for j >= J): loaded up front so that
+// the loads are in flight together (loops over the run-time K and J issue them one
+// round trip at a time)
+__device__ __forceinline__ void load_vertex_rows(const ModelArgs& m, int v, float (&S)[3][kMaxK], float (&wv)[kMaxJ]) {
+  const float* row = m.shapedirs + (size_t)3 * v * m.K;
+  const float* w = m.weights + (size_t)v * m.J;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) S[c][k] = k < m.K ? __ldg(row + c * m.K + k) : 0.0f;
+#pragma unroll
+  for (int j = 0; j < kMaxJ; ++j) wv[j] = j < m.J ? __ldg(w + j) : 0.0f;
+}
+
+// the shaped vertex: template + sum_k S[c][k] beta_k, summed in k order
+__device__ __forceinline__ float3 shaped_vertex(const ModelArgs& m, const Chain& ch, int v, const float (&S)[3][kMaxK]) {
   float p[3];
+#pragma unroll
   for (int c = 0; c < 3; ++c) {
-    float acc = m.v_template[3 * v + c];
-    const float* S = m.shapedirs + (size_t)(3 * v + c) * m.K;
-    for (int k = 0; k < m.K; ++k) acc += S[k] * ch.beta[k];
+    float acc = __ldg(m.v_template + 3 * v + c);
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k)
+      if (k < m.K) acc += S[c][k] * ch.beta[k];
     p[c] = acc;
   }
   return make_float3(p[0], p[1], p[2]);
@@ -179,12 +231,14 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin(ModelArgs m, const float*
     joints_all[((size_t)blockIdx.y * m.J + j) * 3 + c] = ch.tG[j][c] + ch.tau[c];
   }
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < m.V; v += gridDim.x * blockDim.x) {
-    float3 p = shaped_vertex(m, ch, v);
+    float S[3][kMaxK], wv[kMaxJ];
+    load_vertex_rows(m, v, S, wv);
+    float3 p = shaped_vertex(m, ch, v, S);
     float out[3] = {ch.tau[0], ch.tau[1], ch.tau[2]};
-    const float* w = m.weights + (size_t)v * m.J;
-    for (int j = 0; j < m.J; ++j) {
-      float wj = w[j];
-      if (wj == 0.0f) continue;
+#pragma unroll
+    for (int j = 0; j < kMaxJ; ++j) {
+      const float wj = wv[j];
+      if (j >= m.J || wj == 0.0f) continue;
       for (int a = 0; a < 3; ++a)
         out[a] += wj * (ch.RA[j][3 * a] * p.x + ch.RA[j][3 * a + 1] * p.y + ch.RA[j][3 * a + 2] * p.z + ch.tA[j][a]);
     }
@@ -192,11 +246,6 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin(ModelArgs m, const float*
     verts[3 * v + 1] = out[1];
     verts[3 * v + 2] = out[2];
   }
-}
-
-__device__ __forceinline__ float warp_sum(float x) {
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-  return x;
 }
 
 // accumulator layout: [j*12 + 0..8] dRA_j (row-major), [j*12 + 9..11] dtA_j,
@@ -216,54 +265,70 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const fl
   float* partials = partials_all + (size_t)blockIdx.y * kSkinBlocks * kSkinAcc;
   unsigned* counter = counter_all + (size_t)blockIdx.y * cstride;
   float* dparams = dparams_all + (size_t)blockIdx.y * 61;
-  __shared__ float wacc[kSkinThreads / 32][kSkinAcc];
+  // per-vertex terms of the block's current vertices (rows padded against bank
+  // conflicts): g_a p_b and g_a, the skinning weights, and dL/d(shaped vertex)
+  __shared__ float sgp[kSkinThreads][13];
+  __shared__ float sw[kSkinThreads][kMaxJ + 1];
+  __shared__ float sy[kSkinThreads][kMaxK + 1];
   __shared__ float bacc[kSkinAcc];
   __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = lane; i < kSkinAcc; i += 32) wacc[warp][i] = 0.0f;
   build_chain(m, params, ch, status);
+  // thread i < kSkinAcc owns output i: it sums the block's vertices in vertex order
+  // (dRA_j[a][b] = sum_v w_vj g_va p_vb, dtA_j[a] = sum_v w_vj g_va, dbeta_k through
+  // the blendshapes, dtau = sum_v g_v)
+  float tot = 0.0f;
   const int nv_iter = (m.V + gridDim.x * blockDim.x - 1) / (gridDim.x * blockDim.x);
   for (int it = 0; it < nv_iter; ++it) {
-    int v = (it * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
-    bool ok = v < m.V;
-    float3 g = ok ? ld3(dverts + 3 * v) : make_float3(0.0f, 0.0f, 0.0f);
-    float3 p = ok ? shaped_vertex(m, ch, v) : make_float3(0.0f, 0.0f, 0.0f);
-    const float* w = m.weights + (size_t)(ok ? v : 0) * m.J;
+    const int v0 = (it * gridDim.x + blockIdx.x) * blockDim.x;
+    const int v = v0 + threadIdx.x;
+    const bool ok = v < m.V;
+    float S[3][kMaxK], wv[kMaxJ];
+    load_vertex_rows(m, ok ? v : 0, S, wv);
+    const float3 g = ok ? ld3(dverts + 3 * v) : make_float3(0.0f, 0.0f, 0.0f);
+    const float3 p = ok ? shaped_vertex(m, ch, v, S) : make_float3(0.0f, 0.0f, 0.0f);
+    // dL/d(shaped vertex) through the blend, then its blendshape terms
     float dvt[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
     for (int j = 0; j < kMaxJ; ++j) {
-      float wj = (ok && j < m.J) ? w[j] : 0.0f;
-      float gw[3] = {wj * g.x, wj * g.y, wj * g.z};
-      float pv[3] = {p.x, p.y, p.z};
-      for (int a = 0; a < 3; ++a) {
-        for (int b = 0; b < 3; ++b) {
-          float s = warp_sum(gw[a] * pv[b]);
-          if (lane == 0) wacc[warp][12 * j + 3 * a + b] += s;
-        }
-        float s = warp_sum(gw[a]);
-        if (lane == 0) wacc[warp][12 * j + 9 + a] += s;
-      }
-      if (j < m.J)
-        for (int b = 0; b < 3; ++b) dvt[b] += ch.RA[j][b] * gw[0] + ch.RA[j][3 + b] * gw[1] + ch.RA[j][6 + b] * gw[2];
+      const float wj = ok ? wv[j] : 0.0f;
+      sw[threadIdx.x][j] = wj;
+      if (j >= m.J) continue;
+      const float gw[3] = {wj * g.x, wj * g.y, wj * g.z};
+      for (int b = 0; b < 3; ++b) dvt[b] += ch.RA[j][b] * gw[0] + ch.RA[j][3 + b] * gw[1] + ch.RA[j][6 + b] * gw[2];
     }
+#pragma unroll
     for (int k = 0; k < kMaxK; ++k) {
-      float s = 0.0f;
-      if (ok && k < m.K)
-        for (int c = 0; c < 3; ++c) s += m.shapedirs[(size_t)(3 * v + c) * m.K + k] * dvt[c];
-      s = warp_sum(s);
-      if (lane == 0) wacc[warp][16 * 12 + k] += s;
+      float y = 0.0f;
+      if (ok)
+        for (int c = 0; c < 3; ++c) y += S[c][k] * dvt[c];
+      sy[threadIdx.x][k] = y;
     }
-    float gt[3] = {g.x, g.y, g.z};
-    for (int c = 0; c < 3; ++c) {
-      float s = warp_sum(gt[c]);
-      if (lane == 0) wacc[warp][16 * 12 + 10 + c] += s;
+    const float gv[3] = {g.x, g.y, g.z}, pv[3] = {p.x, p.y, p.z};
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) sgp[threadIdx.x][3 * a + b] = gv[a] * pv[b];
+      sgp[threadIdx.x][9 + a] = gv[a];
     }
+    __syncthreads();
+    const int nv = max(0, min((int)blockDim.x, m.V - v0));
+    const int i = threadIdx.x;
+    if (i < 16 * 12) {
+      const int j = i / 12, c = i % 12;
+      if (j < m.J)
+#pragma unroll 4
+        for (int u = 0; u < nv; ++u) tot += sw[u][j] * sgp[u][c];
+    } else if (i < 16 * 12 + kMaxK) {
+      const int k = i - 16 * 12;
+      if (k < m.K)
+#pragma unroll 4
+        for (int u = 0; u < nv; ++u) tot += sy[u][k];
+    } else if (i < kSkinAcc) {
+      const int c = i - 16 * 12 - 10;
+#pragma unroll 4
+      for (int u = 0; u < nv; ++u) tot += sgp[u][9 + c];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kSkinAcc; i += blockDim.x) {
-    float s = 0.0f;
-    for (int q = 0; q < kSkinThreads / 32; ++q) s += wacc[q][i];
-    partials[(size_t)blockIdx.x * kSkinAcc + i] = s;
-  }
+  if (threadIdx.x < kSkinAcc) partials[(size_t)blockIdx.x * kSkinAcc + threadIdx.x] = tot;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
@@ -276,48 +341,95 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const fl
     bacc[i] = s;
   }
   __syncthreads();
-  // chain backward: one thread walks children before parents; the per-joint
-  // Rodrigues gradients and the shape gradient then run in parallel
+  // chain backward, level by level from the deepest: the thread of joint p takes its
+  // children in descending order (each child's own children were done one level
+  // deeper), so every sum gets its terms in the order of a children-before-parents
+  // walk; the per-joint Rodrigues gradients and the shape gradient then run in
+  // parallel
   __shared__ float sdRl[kMaxJ][9];
   __shared__ float sdJ[kMaxJ][3];
-  if (threadIdx.x == 0) {
-    *counter = 0u;
-    float dRG[kMaxJ][9], dtG[kMaxJ][3];
-    const float* djoints = djoints_all ? djoints_all + (size_t)blockIdx.y * 3 * m.J : nullptr;
-    for (int j = 0; j < m.J; ++j) {
-      const float* dRA = &bacc[12 * j];
-      const float* dtA = &bacc[12 * j + 9];
+  __shared__ float sdRG[kMaxJ][9];
+  __shared__ float sdtG[kMaxJ][3];
+  const float* djoints = djoints_all ? djoints_all + (size_t)blockIdx.y * 3 * m.J : nullptr;
+  if (threadIdx.x == 0) *counter = 0u;
+  if (threadIdx.x < m.J) {
+    const int j = threadIdx.x;
+    const float* dRA = &bacc[12 * j];
+    const float* dtA = &bacc[12 * j + 9];
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) sdRG[j][3 * a + b] = dRA[3 * a + b] - dtA[a] * ch.J[j][b];
+      sdtG[j][a] = dtA[a] + (djoints ? djoints[3 * j + a] : 0.0f);
+      sdJ[j][a] = -(ch.RG[j][a] * dtA[0] + ch.RG[j][3 + a] * dtA[1] + ch.RG[j][6 + a] * dtA[2]);
+    }
+  }
+  __syncthreads();
+  for (int L = ch.levels - 2; L >= 0; --L) {
+    if (threadIdx.x < m.J && ch.depth[threadIdx.x] == L) {
+      // joint p's sums stay in registers over its children (through shared memory
+      // every access would wait on the one before)
+      const int p = threadIdx.x;
+      float Rp[9], gRp[9], gtp[3], gJp[3], Jp[3];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        Rp[i] = ch.RG[p][i];
+        gRp[i] = sdRG[p][i];
+      }
+#pragma unroll
       for (int a = 0; a < 3; ++a) {
-        for (int b = 0; b < 3; ++b) dRG[j][3 * a + b] = dRA[3 * a + b] - dtA[a] * ch.J[j][b];
-        dtG[j][a] = dtA[a] + (djoints ? djoints[3 * j + a] : 0.0f);
-        sdJ[j][a] = -(ch.RG[j][a] * dtA[0] + ch.RG[j][3 + a] * dtA[1] + ch.RG[j][6 + a] * dtA[2]);
+        gtp[a] = sdtG[p][a];
+        gJp[a] = sdJ[p][a];
+        Jp[a] = ch.J[p][a];
+      }
+      for (int j = m.J - 1; j > p; --j) {
+        if (ch.par[j] != p) continue;
+        float gRj[9], Rlj[9], gtj[3], Jj[3], gJj[3];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          gRj[i] = sdRG[j][i];
+          Rlj[i] = ch.Rl[j][i];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          gtj[a] = sdtG[j][a];
+          Jj[a] = ch.J[j][a];
+          gJj[a] = sdJ[j][a];
+        }
+        // dRl_j = Rp^T dRG_j
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) sdRl[j][3 * a + b] = Rp[a] * gRj[b] + Rp[3 + a] * gRj[3 + b] + Rp[6 + a] * gRj[6 + b];
+        // dRG_p += dRG_j Rl_j^T + dtG_j (J_j - J_p)^T
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+            gRp[3 * a + b] += gRj[3 * a] * Rlj[3 * b] + gRj[3 * a + 1] * Rlj[3 * b + 1] + gRj[3 * a + 2] * Rlj[3 * b + 2] +
+                              gtj[a] * (Jj[b] - Jp[b]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float rt = Rp[a] * gtj[0] + Rp[3 + a] * gtj[1] + Rp[6 + a] * gtj[2];
+          gtp[a] += gtj[a];
+          gJj[a] += rt;
+          gJp[a] -= rt;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sdJ[j][a] = gJj[a];
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) sdRG[p][i] = gRp[i];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        sdtG[p][a] = gtp[a];
+        sdJ[p][a] = gJp[a];
       }
     }
-    for (int j = m.J - 1; j >= 0; --j) {
-      int p = m.parents[j];
-      if (p >= j || p < -1 || (j == 0) != (p < 0)) p = j == 0 ? -1 : 0;   // reported by build_chain
-      if (p < 0) {
-        for (int i = 0; i < 9; ++i) sdRl[j][i] = dRG[j][i];
-        for (int a = 0; a < 3; ++a) sdJ[j][a] += dtG[j][a];
-        continue;
-      }
-      const float* Rp = ch.RG[p];
-      // dRl_j = Rp^T dRG_j
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-          sdRl[j][3 * a + b] = Rp[a] * dRG[j][b] + Rp[3 + a] * dRG[j][3 + b] + Rp[6 + a] * dRG[j][6 + b];
-      // dRG_p += dRG_j Rl_j^T + dtG_j (J_j - J_p)^T
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b)
-          dRG[p][3 * a + b] += dRG[j][3 * a] * ch.Rl[j][3 * b] + dRG[j][3 * a + 1] * ch.Rl[j][3 * b + 1] +
-                               dRG[j][3 * a + 2] * ch.Rl[j][3 * b + 2] + dtG[j][a] * (ch.J[j][b] - ch.J[p][b]);
-      for (int a = 0; a < 3; ++a) {
-        float rt = Rp[a] * dtG[j][0] + Rp[3 + a] * dtG[j][1] + Rp[6 + a] * dtG[j][2];
-        dtG[p][a] += dtG[j][a];
-        sdJ[j][a] += rt;
-        sdJ[p][a] -= rt;
-      }
-    }
+    __syncthreads();
+  }
+  if (threadIdx.x < m.J && ch.par[threadIdx.x] < 0) {   // the root
+    const int j = threadIdx.x;
+    for (int i = 0; i < 9; ++i) sdRl[j][i] = sdRG[j][i];
+    for (int a = 0; a < 3; ++a) sdJ[j][a] += sdtG[j][a];
   }
   __syncthreads();
   const int tid = threadIdx.x;
@@ -330,9 +442,14 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const fl
     for (int c = 0; c < 3; ++c) dst[c] = out[c];
   } else if (tid >= 32 && tid < 32 + m.K) {
     const int k = tid - 32;
+    float Sj[3 * kMaxJ];
+#pragma unroll
+    for (int q = 0; q < 3 * kMaxJ; ++q) Sj[q] = q < 3 * m.J ? __ldg(m.j_shapedirs + q * m.K + k) : 0.0f;
     float s = bacc[16 * 12 + k];
-    for (int j = 0; j < m.J; ++j)
-      for (int c = 0; c < 3; ++c) s += m.j_shapedirs[(3 * j + c) * m.K + k] * sdJ[j][c];
+#pragma unroll
+    for (int j = 0; j < kMaxJ; ++j)
+      if (j < m.J)
+        for (int c = 0; c < 3; ++c) s += Sj[3 * j + c] * sdJ[j][c];
     dparams[k] = s;
   } else if (tid >= 64 && tid < 67) {
     const int c = tid - 64;
