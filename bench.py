@@ -57,7 +57,7 @@ KERNEL_NAMES = {"fwd_gather": "k_gather<fwd>", "fwd_shade": "k_shade_fwd", "bwd_
                 "bwd_shade": "k_shade_bwd", "edge_samples": "k_edge_samples"}
 # DRAM bytes (read + write) per launch from the ncu capture summarised under profiles/
 # (None once the kernel has changed since that capture)
-NCU_TRAFFIC = {"k_shade_bwd": 3762176, "k_shade_fwd": 2507264, "k_gather<fwd>": 17721344,
+NCU_TRAFFIC = {"k_shade_bwd": 3819264, "k_shade_fwd": 2507264, "k_gather<fwd>": 17721344,
                "k_items_bwd": 19277312, "k_edge_samples": 2993152}
 # kernels of one step: skin 1, BVH + normals 2, forward 4 (gather, shade, overflow,
 # combine), loss 2, backward 8 (items, shade, overflow, reduce, silhouettes, edge
