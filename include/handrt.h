@@ -84,6 +84,17 @@ typedef struct hr_model {
                                   used when the render options give a texture        */
 } hr_model;
 
+/* Check a model's index tables once, after filling the struct (synchronous: copies
+ * the tables from the device; not for the refinement loop).  Returns HR_ERR_ARG for
+ * a parent table that is not in tree order (parents[0] = -1 and 0 <= parents[j] < j
+ * for j > 0: the skinning kernels compose and differentiate the kinematic chain of
+ * Section 3 level by level from the root), face, edge or incident-face indices out
+ * of range, or vertex->face offsets that are not a CSR table; HR_ERR_UNSUPPORTED for
+ * more than 16 joints or 10 shape components; HR_ERR_CUDA if a copy fails.  The
+ * other calls only check sizes and pointers on the host; their kernels report index
+ * errors they meet through the status word. */
+int hr_model_check(const hr_model* model);
+
 /* Allocation-free variant of hr_skin_bwd (the paper has no counterpart: it is an
  * interface for callers that cannot let a library allocate device memory, such as
  * host applications that hand out all device memory from their own pool, processes
@@ -92,8 +103,11 @@ typedef struct hr_model {
  * hr_skin_bwd, without a context: the reduction scratch is a static device array
  * of about 52 KB inside this library, which every GPU that loads the library keeps
  * until the process exits.  No device memory is allocated or freed by the call.
- *   - The first call on a device looks up that array's device address with the
- *     device current; make that first call before capturing the stream.
+ *   - The array's device address is looked up, on the current device, by every
+ *     call whose stream is not being captured (so a device reset does not leave a
+ *     stale address); other calls use the device's last looked-up address.  Make
+ *     the first call on a device, and the first call after a device reset, before
+ *     any stream capture.
  *   - model->V <= 16384, model->J <= 16, model->K <= 10, else HR_ERR_UNSUPPORTED.
  *   - All calls share the one array: calls that may overlap on the GPU (different
  *     streams, or different host threads on one device) race and must be ordered

@@ -406,6 +406,31 @@ def vertex_error_mm(verts_a, verts_b):
     return float(np.linalg.norm(np.asarray(verts_a, np.float64) - np.asarray(verts_b, np.float64), axis=1).mean() * 1e3)
 
 
+def adam_step(params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, lr_scale=None):
+    """One Adam step (Section 3.3 optimises with Adam; Kingma and Ba's update, in
+    float64):
+        m <- beta1 m + (1 - beta1) g
+        v <- beta2 v + (1 - beta2) g^2
+        p <- p - lr_i (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps)
+    with step >= 1 counting the steps taken so far, this one included.  Entry i uses
+    lr_i = lr * lr_scale[i % len(lr_scale)] when a scale vector is given (parameters
+    of different units each get their own step), else lr.  Returns new arrays
+    (params, m, v); the inputs are not modified."""
+    if step < 1:
+        raise ValueError("Adam's step count starts at 1")
+    p = np.asarray(params, np.float64)
+    g = np.asarray(grad, np.float64)
+    m1 = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    m2 = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    m_hat = m1 / (1.0 - beta1 ** step)
+    v_hat = m2 / (1.0 - beta2 ** step)
+    lr_i = np.full(p.shape, float(lr))
+    if lr_scale is not None:
+        s = np.asarray(lr_scale, np.float64).reshape(-1)
+        lr_i = lr * s[np.arange(p.size) % s.size].reshape(p.shape)
+    return p - lr_i * m_hat / (np.sqrt(v_hat) + eps), m1, m2
+
+
 def _fma32(a, b, c):
     """float32 fused multiply-add (the product of two float32 is exact in float64)."""
     return (np.asarray(a, np.float64) * np.asarray(b, np.float64) + np.asarray(c, np.float64)).astype(np.float32)

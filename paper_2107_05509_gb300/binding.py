@@ -45,7 +45,7 @@ EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", 
            "hr_net_adam", "hr_net_status", "hr_vertex_mse", "hr_add_noise", "hr_select_best", "hr_update_bvh",
            "hr_set_tuning", "hr_get_tuning", "hr_loss_ct",
            "hr_skin_joints", "hr_skin_bwd_joints", "hr_joint_prior", "hr_colour_map", "hr_colour_map_bwd",
-           "hr_edges", "hr_edge_loss")
+           "hr_edges", "hr_edge_loss", "hr_model_check")
 
 
 class HandrtError(RuntimeError):
@@ -103,6 +103,7 @@ def lib():
             "hr_skin": [P, P, P, P, P],
             "hr_skin_bwd": [P, P, P, P, P, P],
             "hr_skin_bwd_noalloc": [P, P, P, P, P],
+            "hr_model_check": [P],
             "hr_build_bvh": [P, P, P, P],
             "hr_update_bvh": [P, P, P, P, I, P],
             "hr_set_tuning": [P, P],
@@ -280,6 +281,12 @@ class Model:
         for k, v in self.t.items():
             setattr(m, k, v.data_ptr())
         self.struct = m
+        self.check()
+
+    def check(self):
+        """hr_model_check: the parent table in tree order and every index in range
+        (synchronous; raises HandrtError)."""
+        _check("hr_model_check", lib().hr_model_check(ctypes.byref(self.struct)))
 
     @property
     def V(self):

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "hr_internal.h"
 
@@ -297,6 +298,50 @@ int hr_context_destroy(hr_context* ctx) {
   Context* c = reinterpret_cast<Context*>(ctx);
   cudaDeviceSynchronize();
   free_ctx(c);
+  return HR_OK;
+}
+
+// host copy of n int32 from device memory (synchronous)
+static bool copy_ints(std::vector<int32_t>& dst, const int32_t* src, size_t n) {
+  dst.resize(n);
+  if (n == 0) return true;
+  if (cudaMemcpy(dst.data(), src, n * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+int hr_model_check(const hr_model* m) {
+  if (!m || m->V <= 0 || m->F <= 0 || m->E <= 0 || m->J <= 0 || m->K < 0) return HR_ERR_ARG;
+  if (m->J > hr::kMaxJ || m->K > hr::kMaxK) return HR_ERR_UNSUPPORTED;
+  if (!m->v_template || !m->shapedirs || !m->weights || !m->j_template || !m->j_shapedirs || !m->parents ||
+      !m->faces || !m->edges || !m->edge_faces || !m->vf_offsets || !m->vf_faces || !m->albedo)
+    return HR_ERR_ARG;
+  const int V = m->V, F = m->F, E = m->E, J = m->J;
+  std::vector<int32_t> a;
+  // the kinematic tree: the root first, every parent before its children
+  if (!copy_ints(a, m->parents, J)) return HR_ERR_CUDA;
+  if (a[0] != -1) return HR_ERR_ARG;
+  for (int j = 1; j < J; ++j)
+    if (a[j] < 0 || a[j] >= j) return HR_ERR_ARG;
+  if (!copy_ints(a, m->faces, 3 * (size_t)F)) return HR_ERR_CUDA;
+  for (int32_t x : a)
+    if (x < 0 || x >= V) return HR_ERR_ARG;
+  if (!copy_ints(a, m->edges, 2 * (size_t)E)) return HR_ERR_CUDA;
+  for (int32_t x : a)
+    if (x < 0 || x >= V) return HR_ERR_ARG;
+  if (!copy_ints(a, m->edge_faces, 2 * (size_t)E)) return HR_ERR_CUDA;
+  for (int e = 0; e < E; ++e)
+    if (a[2 * e] < 0 || a[2 * e] >= F || a[2 * e + 1] < -1 || a[2 * e + 1] >= F) return HR_ERR_ARG;
+  if (!copy_ints(a, m->vf_offsets, (size_t)V + 1)) return HR_ERR_CUDA;
+  if (a[0] != 0 || a[V] > 3 * F) return HR_ERR_ARG;
+  for (int v = 0; v < V; ++v)
+    if (a[v + 1] < a[v]) return HR_ERR_ARG;
+  const int n_inc = a[V];
+  if (!copy_ints(a, m->vf_faces, (size_t)n_inc)) return HR_ERR_CUDA;
+  for (int32_t x : a)
+    if (x < 0 || x >= F) return HR_ERR_ARG;
   return HR_OK;
 }
 

@@ -521,17 +521,26 @@ constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
-// device address of the scratch array on the current device (looked up once per
-// device; the host-side symbol is only a stand-in and must never reach a kernel)
-int noalloc_scratch(void** out) {
+// device address of the scratch array on the current device (the host-side symbol
+// is only a stand-in and must never reach a kernel).  Looked up again on every call
+// whose stream is not being captured, so a device reset (which reloads the module,
+// possibly elsewhere) cannot leave a stale address; a call on a capturing stream
+// takes the address of the device's last uncaptured call, or looks it up when there
+// was none.
+int noalloc_scratch(cudaStream_t s, void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return HR_ERR_CUDA;
   }
   if (dev < 0 || dev >= kNoAllocMaxDevices) return HR_ERR_UNSUPPORTED;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return HR_ERR_CUDA;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
+  if (!g_noalloc_addr[dev] || cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_skin_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -554,14 +563,14 @@ extern "C" int hr_skin_bwd_noalloc(const hr_model* m, const float* params, const
       !m->j_shapedirs || !m->parents)
     return HR_ERR_ARG;
   if (m->V > kNoAllocMaxV || m->J > kMaxJ || m->K > kMaxK) return HR_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
   void* base = nullptr;
-  int rc = noalloc_scratch(&base);
+  int rc = noalloc_scratch(s, &base);
   if (rc != HR_OK) return rc;
   unsigned char* b = static_cast<unsigned char*>(base);
   float* partials = reinterpret_cast<float*>(b);
   unsigned* counter = reinterpret_cast<unsigned*>(b + kNoAllocPartialBytes);
   int* status = reinterpret_cast<int*>(b + kNoAllocPartialBytes + 128);
-  cudaStream_t s = (cudaStream_t)stream;
   // the last-block counter must start at zero; the rest is overwritten by the call
   if (cudaMemsetAsync(counter, 0, sizeof(unsigned), s) != cudaSuccess) {
     cudaGetLastError();

@@ -57,9 +57,13 @@ class Refiner:
         self.loss = torch.zeros(1, device=dev)
         self.d_verts = torch.empty((hand.V, 3), device=dev)
         self.d_params = torch.empty(61, device=dev)
+        # counts forward() calls: backward() differentiates the state the latest
+        # forward left (vertices, BVH, candidate lists, adjoint image)
+        self.generation = 0
 
     def forward(self, params, stream=None, skin=True, build=True):
         ctx, m, v = self.ctx, self.model, self.views
+        self.generation += 1
         if skin:
             B.hr_skin(ctx, m, params, self.verts, stream)
         if build:
@@ -212,22 +216,43 @@ class StreamedRefiner:
         s.wait_stream(self.read_stream)
 
 
+class StaleRenderError(RuntimeError):
+    """backward of a HandRenderLoss after its Refiner rendered again."""
+
+
 class HandRenderLoss(torch.autograd.Function):
-    """loss = E_1(params); backward re-traces the samples (no stored hit records)."""
+    """loss = E_1(params) (Eq. 3 with the D_c term of Eq. 4) as a scalar tensor;
+    backward re-traces the forward's samples (hr_render_bwd, no stored hit records)
+    and applies the skinning adjoint, scaled by the incoming gradient.
+
+    The Refiner's buffers (vertices, BVH, candidate lists, adjoint image) hold the
+    state of its latest forward and are what the backward differentiates, so each
+    loss must be back-propagated before the same Refiner renders again: a backward
+    after another forward raises StaleRenderError instead of returning the other
+    forward's gradient.  Use one Refiner per loss term that must stay alive (for
+    example two terms summed before one backward).  params: device float32[61]."""
 
     @staticmethod
     def forward(ctx, params, refiner: Refiner):
+        if params.dtype != torch.float32 or params.numel() != 61 or not params.is_cuda:
+            raise ValueError("params must be a CUDA float32 tensor of 61 entries")
         p = params.detach().contiguous()
         loss = refiner.forward(p).clone()
         ctx.refiner = refiner
+        ctx.generation = refiner.generation
         ctx.save_for_backward(p)
         return loss.reshape(())
 
     @staticmethod
     def backward(ctx, grad_out):
         (p,) = ctx.saved_tensors
-        g = ctx.refiner.backward(p)
-        return g * grad_out, None
+        r = ctx.refiner
+        if r.generation != ctx.generation:
+            raise StaleRenderError(
+                f"the Refiner rendered {r.generation - ctx.generation} more time(s) after this loss was computed; "
+                "back-propagate each HandRenderLoss before the next forward on the same Refiner")
+        g = r.backward(p)
+        return (g * grad_out).reshape(p.shape), None
 
 
 # --------------------------------------------------------------------------------------

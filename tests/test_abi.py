@@ -46,6 +46,7 @@ def test_status_strings_and_host_argument_checks(libpath):
     assert L.hr_render_fwd(None, None, None, None, 1, 1, 1, None, None, None, None) == -1
     assert L.hr_loss(None, None, None, None, 1, 1, 1, None, None, None) == -1
     assert L.hr_get_status(None, None) == -1
+    assert L.hr_model_check(None) == -1
     fn = L.hr_adam_step
     fn.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] + [ctypes.c_float] * 4 + [ctypes.c_int, ctypes.c_void_p]
     assert fn(None, None, None, None, 61, 0.01, 0.9, 0.999, 1e-8, 1, None) == -1

@@ -119,6 +119,34 @@ def test_bad_face_index_reported_not_faulted(B):
     assert B.hr_get_status(ctx) == B.HR_OK
 
 
+def test_model_check_rejects_out_of_order_parents_and_bad_indices(B):
+    """hr_model_check: the skinning kernels walk the kinematic chain from the root,
+    so a parent table not in tree order is an argument error on the host, as are
+    indices out of range; the model as generated passes."""
+    h = hand()
+    model = B.Model(h)                  # checked on creation
+    assert B.lib().hr_model_check(ctypes.byref(model.struct)) == B.HR_OK
+    good = model.t["parents"]
+    for bad_parents in ([-1, 2, 0] + list(h.parents[3:]),      # joint 1's parent comes after it
+                        [0] + list(h.parents[1:]),              # the root has a parent
+                        list(h.parents[:5]) + [5] + list(h.parents[6:])):   # a joint is its own parent
+        p = torch.as_tensor(np.asarray(bad_parents, np.int32), device="cuda")
+        model.struct.parents = p.data_ptr()
+        assert B.lib().hr_model_check(ctypes.byref(model.struct)) == B.HR_ERR_ARG
+    model.struct.parents = good.data_ptr()
+    bad = model.t["faces"].clone()
+    bad[7, 2] = -1
+    model.struct.faces = bad.data_ptr()
+    assert B.lib().hr_model_check(ctypes.byref(model.struct)) == B.HR_ERR_ARG
+    model.struct.faces = model.t["faces"].data_ptr()
+    bad = model.t["edge_faces"].clone()
+    bad[3, 0] = h.F
+    model.struct.edge_faces = bad.data_ptr()
+    assert B.lib().hr_model_check(ctypes.byref(model.struct)) == B.HR_ERR_ARG
+    model.struct.edge_faces = model.t["edge_faces"].data_ptr()
+    assert B.lib().hr_model_check(ctypes.byref(model.struct)) == B.HR_OK
+
+
 def test_host_argument_errors(B):
     h = hand()
     model = B.Model(h)

@@ -13,7 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
-from tests.gpu_common import grad_ok, hand, require_gpu, torch
+from tests.gpu_common import hand, require_gpu, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +39,8 @@ def test_noalloc_skin_bwd_matches_context_entry_point_twice():
         torch.cuda.synchronize()
         r, o = ref.cpu().numpy(), out.cpu().numpy()
         assert np.isfinite(o).all(), trial
-        assert grad_ok(o, r).all(), (trial, o, r)
+        # the same kernel, block count and fixed-order reduction: bit-identical
+        assert np.array_equal(o, r), (trial, o, r)
     assert B.hr_get_status(ctx) == B.HR_OK
     ctx.close()
 
