@@ -119,7 +119,7 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
             dev_alloc(&c->pool_bb, c->pool_cap, a) && dev_alloc(&c->pool_z, c->pool_cap, a) &&
             dev_alloc(&c->pool_rec, c->pool_cap, a) && dev_alloc(&c->st_info, subtiles, a) &&
             dev_alloc(&c->items, c->item_cap, a) && dev_alloc(&c->item_part, (size_t)c->item_cap * 32, a) &&
-            dev_alloc(&c->extra, ni * 6 * V, a) && dev_alloc(&c->work_ctr, 3 + 2 * ni, a) &&
+            dev_alloc(&c->extra, ni * 6 * V, a) && dev_alloc(&c->work_ctr, hr::ctr_words(ni), a) &&
             dev_alloc(&c->ovf_list, subtiles, a) &&
             dev_alloc(&c->bvh_parent, ni * 2 * F, a) && dev_alloc(&c->bvh_valid, ni, a) &&
             dev_alloc(&c->bvh_bounds, ni * 6, a) && dev_alloc(&c->bvh_bad, ni, a) && dev_alloc(&c->bvh_mode, ni, a);

@@ -152,6 +152,10 @@ struct Context {
   unsigned long long* stats;  // [3][kStatsPer]
 };
 
+// work counters of the render kernels for n instances: 3 + 3n words, then (from an
+// even word) one 64-bit item-allocation word per instance
+__host__ __device__ constexpr int ctr_alloc_base(int n) { return (3 + 3 * n + 1) & ~1; }
+__host__ __device__ constexpr int ctr_words(int n) { return ctr_alloc_base(n) + 2 * n; }
 constexpr int kLossBlocks = 1024;        // loss blocks of a single-instance context
 constexpr int kLossBlocksBatch = 128;    // per instance in a batch
 // per-instance loss scratch: block counts (u64), block sums, 1 / (3 sum M), padding

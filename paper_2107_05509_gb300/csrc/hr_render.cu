@@ -200,8 +200,9 @@ struct Work {
                    // atomics: long runs of cancelling contributions)
   float* extra;    // [n_inst][6V] backward sums: shading blocks of a batch, and work
                    // done outside the shading blocks
-  unsigned* ctr;   // [3 + 2 n_inst] sub-tile counter, pool fill, per instance item
-                   // fill and item counter, then the overflow count
+  unsigned* ctr;   // [ctr_words(n_inst)] sub-tile counter, pool fill, per instance
+                   // front items and taken items, the overflow count, per instance back
+                   // items, then per instance a 64-bit allocation word
   int* ovf;        // [sub-tiles] sub-tiles whose items did not fit their instance's
                    // region (k_overflow does them whole)
   unsigned long long* fx;   // [n_inst][6V] fixed-point backward sums (HR_DETERMINISTIC)
@@ -566,6 +567,44 @@ __device__ __forceinline__ int chunks_for(const RenderArgs& a, int K, int spp) {
   return max(1, min(min(c, a.max_chunks), spp));
 }
 
+// Work-item order.  A warp's item costs about (samples per lane) x (kSampleCost + K)
+// candidate tests: a sample's own work (jitter, direction, shading or
+// differentiation) weighs about kSampleCost tests (measured on the paper-shaped
+// workload).  Items are taken from one counter, so the launch ends when the last
+// item taken finishes; heavy items taken last leave most warps idle for the length
+// of one heavy item.  Items whose cost exceeds twice the split's target
+// (cand_per_chunk x spp) are therefore allocated from the front of the instance's
+// item region and the others from its back, and the shaders take the front first.
+// Per instance the counters are: front items (ctr[2 + 2i]), taken items
+// (ctr[3 + 2i]), back items (ctr[3 + 2n + i]), and a 64-bit allocation word
+// (front | back << 32) that decides, in one atomic, whether a group still fits.
+constexpr int kSampleCost = 16;
+__device__ __forceinline__ bool heavy_item(const RenderArgs& a, int K, int C, int spp) {
+  const int k = K == -1 ? kLeafCap : (K < 0 ? -K - 1 : K);
+  const int ns = (spp + C - 1) / C;
+  return (long long)ns * (k + kSampleCost) > 2LL * a.cand_per_chunk * spp;
+}
+__device__ __forceinline__ unsigned* back_count(const RenderArgs& a, int inst) {
+  return a.wk.ctr + 3 + 2 * a.n_inst + inst;
+}
+__device__ __forceinline__ unsigned long long* alloc_word(const RenderArgs& a, int inst) {
+  return reinterpret_cast<unsigned long long*>(a.wk.ctr + ctr_alloc_base(a.n_inst)) + inst;
+}
+// reserve C consecutive slots of instance inst's region (lane 0 calls); -1 when the
+// region has no room for them
+__device__ __forceinline__ int alloc_items(const RenderArgs& a, int inst, int C, bool heavy, int icap) {
+  const unsigned long long v =
+      atomicAdd(alloc_word(a, inst), heavy ? (unsigned long long)C : ((unsigned long long)C << 32));
+  const long long front = (long long)(v & 0xffffffffull), back = (long long)(v >> 32);
+  if (front + back + C > icap) return -1;
+  if (heavy) {
+    atomicAdd(&a.wk.ctr[2 + 2 * inst], (unsigned)C);
+    return (int)front;
+  }
+  atomicAdd(back_count(a, inst), (unsigned)C);
+  return (int)(icap - back - C);
+}
+
 // closest hit of the primary ray through (sx, sy) among the K pool candidates at
 // `off`; `live` lanes take part, the others only vote
 template <bool STATS>
@@ -590,53 +629,82 @@ __device__ __forceinline__ Hit closest_candidate(const RenderArgs& a, int off, i
 }
 
 // closest hits of a lane's S rays (same origin) among the K pool candidates at `off`:
-// the candidate's depth, screen box and triangle record are loaded once for all S
-// rays; `live[j]` rays take part, the others only vote.  Each ray gets exactly the hit
-// the one-ray search gives it.
+// the warp loads the candidates 32 at a time, one per lane (depth, screen box and
+// triangle record in three coalesced loads), and hands each in turn to every lane by
+// shuffles, so the scan waits on no memory load per candidate; the triangle's
+// vertices are loaded only for a candidate whose box holds one of the lane's rays,
+// once for all S rays.  `live[j]` rays take part, the others only vote.  Each ray
+// gets exactly the hit the one-ray search gives it.
 template <bool STATS, int S>
 __device__ __forceinline__ void closest_candidates(const RenderArgs& a, int off, int K, const bool (&live)[S],
                                                    const float (&sx)[S], const float (&sy)[S], float3 o,
                                                    const float3 (&d)[S], Hit (&h)[S], Counts& cnt) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < S; ++j) h[j] = Hit{-1, INFINITY, 0.0f, 0.0f};
-  for (int c = 0; c < K; ++c) {
-    if (!in_range(a.status, off + c, 0, a.wk.pool_cap)) break;
-    const float zm = __ldg(&a.wk.z[off + c]);
-    const float zlim = zm - (1e-4f * fabsf(zm) + 1e-6f);
-    bool want[S];
-    bool any = false;
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-      want[j] = live[j] && !(h[j].t < zlim);
-      any = any || want[j];
+  bool stop = false;
+  for (int c0 = 0; c0 < K && !stop; c0 += 32) {
+    // this block of candidates, one per lane; a pool index out of range ends the scan
+    const int cl = c0 + lane;
+    const bool have = cl < K;
+    const bool ok = have && in_range(a.status, off + cl, 0, a.wk.pool_cap);
+    float zl = 0.0f;
+    float4 bl = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    int kl = 0;
+    if (ok) {
+      zl = __ldg(&a.wk.z[off + cl]);
+      bl = __ldg(&a.wk.bb[off + cl]);
+      kl = __ldg(&a.wk.rec[off + cl]);
     }
-    if (!__any_sync(0xffffffffu, any)) break;
-    if (!any) continue;
-    const float4 bb = __ldg(&a.wk.bb[off + c]);
-    bool inside = false;
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-      if (STATS && want[j]) ++cnt.cands;
-      want[j] = want[j] && sx[j] >= bb.x && sx[j] <= bb.z && sy[j] >= bb.y && sy[j] <= bb.w;
-      inside = inside || want[j];
+    const unsigned bad = __ballot_sync(full, have && !ok);
+    int n = min(32, K - c0);
+    if (bad) {
+      n = min(n, __ffs(bad) - 1);
+      stop = true;
     }
-    if (!inside) continue;
-    const int k = __ldg(&a.wk.rec[off + c]);
-    if (!in_range(a.status, k, 0, a.max_visits - 1)) continue;
-    const float4 ta = __ldg(&a.tris[3 * k]), tb = __ldg(&a.tris[3 * k + 1]), tc = __ldg(&a.tris[3 * k + 2]);
-    const float3 v0 = make_float3(ta.x, ta.y, ta.z), e1 = make_float3(ta.w, tb.x, tb.y),
-                 e2 = make_float3(tb.z, tb.w, tc.x);
-    const int id = __float_as_int(tc.y);
+    for (int i = 0; i < n; ++i) {
+      const float zm = __shfl_sync(full, zl, i);
+      const float bx0 = __shfl_sync(full, bl.x, i), by0 = __shfl_sync(full, bl.y, i);
+      const float bx1 = __shfl_sync(full, bl.z, i), by1 = __shfl_sync(full, bl.w, i);
+      const int k = __shfl_sync(full, kl, i);
+      const float zlim = zm - (1e-4f * fabsf(zm) + 1e-6f);
+      bool want[S];
+      bool any = false;
 #pragma unroll
-    for (int j = 0; j < S; ++j) {
-      if (!want[j]) continue;
-      if (STATS) ++cnt.tris;
-      float t, u, v;
-      if (mt_hit(o, d[j], v0, e1, e2, t, u, v) && (t < h[j].t || (t == h[j].t && id < h[j].tri))) {
-        h[j].tri = id;
-        h[j].t = t;
-        h[j].u = u;
-        h[j].v = v;
+      for (int j = 0; j < S; ++j) {
+        want[j] = live[j] && !(h[j].t < zlim);
+        any = any || want[j];
+      }
+      if (!__any_sync(full, any)) {
+        stop = true;
+        break;
+      }
+      if (!any) continue;
+      bool inside = false;
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        if (STATS && want[j]) ++cnt.cands;
+        want[j] = want[j] && sx[j] >= bx0 && sx[j] <= bx1 && sy[j] >= by0 && sy[j] <= by1;
+        inside = inside || want[j];
+      }
+      if (!inside) continue;
+      if (!in_range(a.status, k, 0, a.max_visits - 1)) continue;
+      const float4 ta = __ldg(&a.tris[3 * k]), tb = __ldg(&a.tris[3 * k + 1]), tc = __ldg(&a.tris[3 * k + 2]);
+      const float3 v0 = make_float3(ta.x, ta.y, ta.z), e1 = make_float3(ta.w, tb.x, tb.y),
+                   e2 = make_float3(tb.z, tb.w, tc.x);
+      const int id = __float_as_int(tc.y);
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        if (!want[j]) continue;
+        if (STATS) ++cnt.tris;
+        float t, u, v;
+        if (mt_hit(o, d[j], v0, e1, e2, t, u, v) && (t < h[j].t || (t == h[j].t && id < h[j].tri))) {
+          h[j].tri = id;
+          h[j].t = t;
+          h[j].u = u;
+          h[j].v = v;
+        }
       }
     }
   }
@@ -1085,17 +1153,14 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
     const int C = chunks_for(a, K, t.spp);
     const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
     int first = 0;
-    if (lane == 0) first = (int)atomicAdd(&a.wk.ctr[2 + 2 * t.inst], (unsigned)C);
+    if (lane == 0) first = alloc_items(a, t.inst, C, heavy_item(a, K, C, t.spp), icap);
     first = __shfl_sync(0xffffffffu, first, 0);
     if (lane == 0) a.wk.st[st] = make_int2(off, K);
-    if (first + C <= icap) {
+    if (first >= 0) {
       for (int c = lane; c < C; c += 32) a.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
-    } else {
-      // item region full: blank the reserved slots that exist and hand the whole
-      // sub-tile to k_overflow
-      for (int c = lane; c < C; c += 32)
-        if (first + c < icap) a.wk.items[ibase + first + c] = make_int4(-1, 0, 0, 0);
-      if (lane == 0) a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
+    } else if (lane == 0) {
+      // item region full: the whole sub-tile goes to k_overflow
+      a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
     }
     __syncwarp();
   }
@@ -1129,23 +1194,30 @@ __global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, c
     const int C = chunks_for(a, pk.y, t.spp);
     const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
     int first = 0;
-    if (lane == 0) first = (int)atomicAdd(&a.wk.ctr[2 + 2 * t.inst], (unsigned)C);
+    if (lane == 0) first = alloc_items(a, t.inst, C, heavy_item(a, pk.y, C, t.spp), icap);
     first = __shfl_sync(0xffffffffu, first, 0);
-    if (first + C <= icap) {
+    if (first >= 0) {
       for (int c = lane; c < C; c += 32) a.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
-    } else {
-      for (int c = lane; c < C; c += 32)
-        if (first + c < icap) a.wk.items[ibase + first + c] = make_int4(-1, 0, 0, 0);
-      if (lane == 0) a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
+    } else if (lane == 0) {
+      a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
     }
     __syncwarp();
   }
   flush_counts<STATS>(cnt, stats);
 }
 
-// items of an instance's region that the gather filled
-__device__ __forceinline__ int item_count(const RenderArgs& a, int inst) {
+// items of an instance's region that the gather filled (front and back)
+__device__ __forceinline__ int front_count(const RenderArgs& a, int inst) {
   return (int)min(*reinterpret_cast<volatile unsigned*>(&a.wk.ctr[2 + 2 * inst]), (unsigned)inst_icap(a, inst));
+}
+__device__ __forceinline__ int item_count(const RenderArgs& a, int inst) {
+  const unsigned b = *reinterpret_cast<volatile unsigned*>(back_count(a, inst));
+  return (int)min((unsigned)front_count(a, inst) + b, (unsigned)inst_icap(a, inst));
+}
+// region slot of the instance's i-th item (0 <= i < item_count): the front items,
+// heavy, first; then the back items from the region's end
+__device__ __forceinline__ int item_slot(const RenderArgs& a, int inst, int i, int nfront) {
+  return i < nfront ? i : inst_icap(a, inst) - 1 - (i - nfront);
 }
 
 __device__ __forceinline__ void item_samples(int c, int C, int spp, int& s0, int& s1) {
@@ -1182,15 +1254,16 @@ __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in
   const int lane = threadIdx.x & 31;
   Counts cnt;
   for (int inst = 0; inst < a0.n_inst; ++inst) {
-    const int n = item_count(a0, inst), ibase = inst_ibase(a0, inst);
+    const int n = item_count(a0, inst), nf = front_count(a0, inst), ibase = inst_ibase(a0, inst);
     const RenderArgs a = for_inst(a0, inst);
     for (;;) {
       const int it = next_item(a, inst, n);
       if (it < 0) break;
+      const int slot = ibase + item_slot(a, inst, it, nf);
       int4 item;
       SubTile t;
       int2 pk;
-      if (!load_item(a, ibase + it, item, t, pk) || t.inst != inst) continue;
+      if (!load_item(a, slot, item, t, pk) || t.inst != inst) continue;
       if (pk.y < 0) continue;   // no candidate list: k_overflow traces this item
       const Cam cam = load_cam(a.cams, t.view);
       int s0, s1;
@@ -1198,7 +1271,7 @@ __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in
       float3 acc = make_float3(0.0f, 0.0f, 0.0f);
       int misses = 0;
       shade_samples<STATS, S, false>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
-      a.wk.part[(size_t)(ibase + it) * 32 + lane] = make_float4(acc.x, acc.y, acc.z, (float)misses);
+      a.wk.part[(size_t)slot * 32 + lane] = make_float4(acc.x, acc.y, acc.z, (float)misses);
     }
   }
   flush_counts<STATS>(cnt, stats);
@@ -1269,13 +1342,14 @@ __global__ void __launch_bounds__(kRenderThreads, BWD ? kBwdMinBlocks : 8) k_ove
   // ray by ray, the forward writing the item's partial sums for k_combine_fwd, the
   // backward adding to the instance's extra sums
   for (int inst = 0; inst < a0.n_inst; ++inst) {
-    const int ni = item_count(a0, inst), ibase = inst_ibase(a0, inst);
+    const int ni = item_count(a0, inst), nf = front_count(a0, inst), ibase = inst_ibase(a0, inst);
     const RenderArgs a = for_inst(a0, inst);
     for (int it = blockIdx.x * kWarps + (threadIdx.x >> 5); it < ni; it += gridDim.x * kWarps) {
+      const int slot = ibase + item_slot(a, inst, it, nf);
       int4 item;
       SubTile t;
       int2 pk;
-      if (!load_item(a, ibase + it, item, t, pk) || t.inst != inst || pk.y >= 0) continue;
+      if (!load_item(a, slot, item, t, pk) || t.inst != inst || pk.y >= 0) continue;
       const Cam cam = load_cam(a.cams, t.view);
       int s0, s1;
       item_samples(item.y, item.z, t.spp, s0, s1);
@@ -1293,7 +1367,7 @@ __global__ void __launch_bounds__(kRenderThreads, BWD ? kBwdMinBlocks : 8) k_ove
         float3 acc = make_float3(0.0f, 0.0f, 0.0f);
         int misses = 0;
         shade_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
-        a.wk.part[(size_t)(ibase + it) * 32 + (threadIdx.x & 31)] = make_float4(acc.x, acc.y, acc.z, (float)misses);
+        a.wk.part[(size_t)slot * 32 + (threadIdx.x & 31)] = make_float4(acc.x, acc.y, acc.z, (float)misses);
       }
     }
   }
@@ -1304,9 +1378,9 @@ __global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, fl
   const int lane = threadIdx.x & 31;
   const int nw = gridDim.x * kWarps;
   for (int inst = 0; inst < a.n_inst; ++inst) {
-    const int n = item_count(a, inst), ibase = inst_ibase(a, inst);
+    const int n = item_count(a, inst), nf = front_count(a, inst), ibase = inst_ibase(a, inst);
     for (int it = blockIdx.x * kWarps + (threadIdx.x >> 5); it < n; it += nw) {
-      const int4 item = a.wk.items[ibase + it];
+      const int4 item = a.wk.items[ibase + item_slot(a, inst, it, nf)];
       if (item.x < 0 || item.y != 0) continue;
       if (!in_range(a.status, item.x, 0, subtile_count(a)) ||
           !in_range(a.status, (long long)item.w + item.z - 1, ibase, ibase + inst_icap(a, inst)))
@@ -1326,12 +1400,16 @@ __global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, fl
 }
 
 // interior term: warps take work items.  ACC selects where the gradient collects:
-//   kAccPartials  the block accumulates dV/dN in shared memory (sdV [V][3], sdN [V][3])
-//                 and writes one partial per block, summed in block order by
-//                 k_reduce_partials (single instance)
-//   kAccFlush     shared memory as above; the block works through the instances in
-//                 order and, when every warp is done with one, adds its non-zero sums
-//                 into that instance's extra [6V] (global atomics) and clears them
+//   kAccPartials  the block accumulates dV/dN into its own partial [6V] in global
+//                 memory (L2-resident), with atomic adds whose result is not read:
+//                 they retire in L2 without holding up the warp, where float adds to
+//                 shared memory cost a read and a compare-and-swap loop each.  The
+//                 partials are summed in block order by k_reduce_partials (single
+//                 instance)
+//   kAccFlush     the block accumulates dV/dN in shared memory (sdV [V][3], sdN
+//                 [V][3]), works through the instances in order and, when every warp
+//                 is done with one, adds its non-zero sums into that instance's extra
+//                 [6V] (global atomics) and clears them
 //   kAccGlobal    meshes whose [V][6] sums exceed shared memory: every run of hits on
 //                 one triangle is added straight into the instance's extra [6V]
 //   kAccFixed     HR_DETERMINISTIC: every run goes straight into the instance's
@@ -1344,13 +1422,14 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
                                                                              unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
   extern __shared__ float sacc[];
+  float* part = ACC == kAccPartials ? partials + (size_t)blockIdx.x * 6 * a0.V : sacc;
   if (ACC == kAccPartials || ACC == kAccFlush) {
-    for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) sacc[i] = 0.0f;
+    for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) part[i] = 0.0f;
     __syncthreads();
   }
   Counts cnt;
   for (int inst = 0; inst < a0.n_inst; ++inst) {
-    const int n = item_count(a0, inst), ibase = inst_ibase(a0, inst);
+    const int n = item_count(a0, inst), nf = front_count(a0, inst), ibase = inst_ibase(a0, inst);
     const RenderArgs a = for_inst(a0, inst);
     typedef typename std::conditional<
         ACC == kAccGlobal, double, typename std::conditional<ACC == kAccFixed, unsigned long long, float>::type>::type
@@ -1361,7 +1440,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
     else if constexpr (ACC == kAccFixed)
       sdV = a0.wk.fx + (size_t)inst * 6 * a0.V;
     else
-      sdV = sacc;
+      sdV = part;
     AccT* sdN = sdV + 3 * a0.V;
     int did = 0;
     for (;;) {
@@ -1370,7 +1449,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
       int4 item;
       SubTile t;
       int2 pk;
-      if (!load_item(a, ibase + it, item, t, pk) || t.inst != inst) continue;
+      if (!load_item(a, ibase + item_slot(a, inst, it, nf), item, t, pk) || t.inst != inst) continue;
       if (pk.y < 0) continue;   // no candidate list: k_overflow traces this item
       bool live;
       const float3 g = lane_adjoint(a, t, adjoint, live);
@@ -1395,10 +1474,6 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
     }
   }
   flush_counts<STATS>(cnt, stats);
-  if (ACC != kAccPartials) return;
-  __syncthreads();
-  float* out = partials + (size_t)blockIdx.x * 6 * a0.V;
-  for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) out[i] = sacc[i];
 }
 
 // d_verts[i] = extra[i] + sum_b partials[b][i] (i < 3V), dN[i-3V] likewise.  A block
@@ -1848,7 +1923,7 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   RenderArgs a = make_args(ctx, m, verts, cams, N, H, W, bg, o);
   const bool st = o->flags & HR_STATS;
   Timer tm{ctx, s, (o->flags & HR_TIMING) != 0};
-  if (cudaMemsetAsync(ctx->work_ctr, 0, (3 + 2 * a.n_inst) * sizeof(unsigned), s) != cudaSuccess)
+  if (cudaMemsetAsync(ctx->work_ctr, 0, ctr_words(a.n_inst) * sizeof(unsigned), s) != cudaSuccess)
     return HR_ERR_CUDA;
   const int blocks = ctx->num_sms * ctx->tune.blocks_per_sm;
   tm.begin(kTimeFwdGather);
@@ -1912,7 +1987,7 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
   if (interior || edges) {
     // candidates of the sub-tiles with a non-zero adjoint: the interior shader's work
     // items, and the edge rays' candidate lists
-    if (cudaMemsetAsync(ctx->work_ctr, 0, (3 + 2 * ni) * sizeof(unsigned), s) != cudaSuccess ||
+    if (cudaMemsetAsync(ctx->work_ctr, 0, ctr_words(ni) * sizeof(unsigned), s) != cudaSuccess ||
         cudaMemsetAsync(ctx->extra, 0, sizeof(float) * 6 * V * ni, s) != cudaSuccess)
       return HR_ERR_CUDA;
     // the forward's candidate lists still describe this scene when it used the same
@@ -1964,7 +2039,7 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
         (!ctx->extra64 || cudaMemsetAsync(ctx->extra64, 0, sizeof(double) * 6 * V * ni, s) != cudaSuccess))
       return ctx->extra64 ? HR_ERR_CUDA : HR_ERR_UNSUPPORTED;
     const int acc = det ? kAccFixed : (global_acc ? kAccGlobal : (batch ? kAccFlush : kAccPartials));
-    const size_t smem = (acc == kAccPartials || acc == kAccFlush) ? render_bwd_smem(V) : 0;
+    const size_t smem = acc == kAccFlush ? render_bwd_smem(V) : 0;
     // deterministic: one ray per lane, the arithmetic of the overflow kernel, which may
     // trace any sub-tile whose candidates found no room in the pool
     const int S = det ? 1 : ctx->tune.bwd_rays_per_lane;
