@@ -104,8 +104,8 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
   c->pool_cap = (int)std::min<size_t>((size_t)1 << 28, 16 * subtiles + 4096);
   c->item_cap = (int)items;
   c->loss_blocks = loss_blocks;
-  // block partials: single-instance backward with shared-memory sums (V <= 8192)
-  const size_t partial_blocks = (n == 1 && V <= 8192) ? (size_t)c->render_blocks : 1;
+  // block partials of the single-instance backward (V <= kPartialMaxV)
+  const size_t partial_blocks = (n == 1 && V <= (size_t)hr::kPartialMaxV) ? (size_t)c->render_blocks : 1;
   const size_t nviews = views;
   bool ok = dev_alloc(&c->nodes, ni * F, a) && dev_alloc(&c->tris, ni * 3 * F, a) &&
             dev_alloc(&c->normals, ni * 3 * V, a) && dev_alloc(&c->normal_len, ni * V, a) &&
@@ -143,7 +143,7 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
   // kernel attributes are set here, once, so that the per-iteration calls are only
   // launches and asynchronous memsets
   if (ok)
-    ok = hr::configure_bvh_kernels() == HR_OK && hr::configure_render_kernels(lim->max_V) == HR_OK &&
+    ok = hr::configure_bvh_kernels() == HR_OK &&
          hr::configure_gemm_kernels() == HR_OK;
   if (!ok) {
     cudaGetLastError();

@@ -156,6 +156,9 @@ struct Context {
 // even word) one 64-bit item-allocation word per instance
 __host__ __device__ constexpr int ctr_alloc_base(int n) { return (3 + 3 * n + 1) & ~1; }
 __host__ __device__ constexpr int ctr_words(int n) { return ctr_alloc_base(n) + 2 * n; }
+// meshes up to this many vertices take float backward sums (per block of the shader
+// in a single-instance context); larger ones float64 sums
+constexpr int kPartialMaxV = 8192;
 constexpr int kLossBlocks = 1024;        // loss blocks of a single-instance context
 constexpr int kLossBlocksBatch = 128;    // per instance in a batch
 // per-instance loss scratch: block counts (u64), block sums, 1 / (3 sum M), padding

@@ -57,11 +57,9 @@ int configure_gemm_kernels();
 
 // per-device properties of the render kernels (persistent grid)
 int render_grid(int device, int* blocks, int* threads, int* num_sms);
-size_t render_bwd_smem(int V);
 int subtiles_for(int views, int W, int H);
 int subtile_columns(int W);
 // one-time kernel attributes (shared-memory opt-in) on the current device
 int configure_bvh_kernels();
-int configure_render_kernels(int max_V);
 
 }  // namespace hr

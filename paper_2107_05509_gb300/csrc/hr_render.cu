@@ -605,29 +605,6 @@ __device__ __forceinline__ int alloc_items(const RenderArgs& a, int inst, int C,
   return (int)(icap - back - C);
 }
 
-// closest hit of the primary ray through (sx, sy) among the K pool candidates at
-// `off`; `live` lanes take part, the others only vote
-template <bool STATS>
-__device__ __forceinline__ Hit closest_candidate(const RenderArgs& a, int off, int K, bool live, float sx, float sy,
-                                                 float3 o, float3 d, Counts& cnt) {
-  Hit h{-1, INFINITY, 0.0f, 0.0f};
-  for (int c = 0; c < K; ++c) {
-    if (!in_range(a.status, off + c, 0, a.wk.pool_cap)) break;
-    const float zm = __ldg(&a.wk.z[off + c]);
-    // no remaining candidate can be nearer than this lane's hit (t >= its depth)
-    const bool done = !live || h.t < zm - (1e-4f * fabsf(zm) + 1e-6f);
-    if (__all_sync(0xffffffffu, done)) break;
-    if (done) continue;
-    const float4 bb = __ldg(&a.wk.bb[off + c]);
-    if (STATS) ++cnt.cands;
-    if (sx >= bb.x && sx <= bb.z && sy >= bb.y && sy <= bb.w) {
-      const int k = __ldg(&a.wk.rec[off + c]);
-      if (in_range(a.status, k, 0, a.max_visits - 1)) isect<STATS>(a.tris, k, o, d, h, cnt);
-    }
-  }
-  return h;
-}
-
 // closest hits of a lane's S rays (same origin) among the K pool candidates at `off`:
 // the warp loads the candidates 32 at a time, one per lane (depth, screen box and
 // triangle record in three coalesced loads), and hands each in turn to every lane by
@@ -708,49 +685,6 @@ __device__ __forceinline__ void closest_candidates(const RenderArgs& a, int off,
       }
     }
   }
-}
-
-// closest hit among the pool candidates at `off` for one ray on its own (no warp
-// votes): candidates are sorted by nearest depth, so the first one farther than the
-// hit so far ends the search
-template <bool STATS>
-__device__ __forceinline__ Hit closest_candidate_1(const RenderArgs& a, int off, int K, float sx, float sy, float3 o,
-                                                   float3 d, Counts& cnt) {
-  Hit h{-1, INFINITY, 0.0f, 0.0f};
-  for (int c = 0; c < K; ++c) {
-    if (!in_range(a.status, off + c, 0, a.wk.pool_cap)) break;
-    const float zm = __ldg(&a.wk.z[off + c]);
-    if (h.t < zm - (1e-4f * fabsf(zm) + 1e-6f)) break;
-    const float4 bb = __ldg(&a.wk.bb[off + c]);
-    if (STATS) ++cnt.cands;
-    if (sx >= bb.x && sx <= bb.z && sy >= bb.y && sy <= bb.w) {
-      const int k = __ldg(&a.wk.rec[off + c]);
-      if (in_range(a.status, k, 0, a.max_visits - 1)) isect<STATS>(a.tris, k, o, d, h, cnt);
-    }
-  }
-  return h;
-}
-
-// radiance through screen point (sx, sy) of a sub-tile whose candidates are (off, K)
-// (K < 0: per-ray traversal); a miss returns background pixel (bx, by) of the view
-// whose first pixel is pix0 and width W.  `a` holds the instance's scene pointers.
-template <bool STATS>
-__device__ __forceinline__ float3 radiance(const RenderArgs& a, const Cam& cam, long long pix0, int W, float sx,
-                                           float sy, int bx, int by, int off, int K, Counts& cnt) {
-  float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
-  float3 d = primary_dir(cam, sx, sy);
-  if (STATS) {
-    ++cnt.samples;
-    ++cnt.rays;
-  }
-  Hit h{-1, INFINITY, 0.0f, 0.0f};
-  if (K > 0)
-    h = closest_candidate_1<STATS>(a, off, K, sx, sy, o, d, cnt);
-  else if (K < 0)
-    h = trace<STATS>(a.nodes, a.tris, o, d, a.status, cnt, a.max_visits);
-  if (STATS) cnt.hits += h.tri >= 0;
-  if (h.tri >= 0) return shade(a, h);
-  return ld3(a.bg + 3 * (pix0 + (size_t)by * W + bx));
 }
 
 // Radiance sums of samples [s0, s1) of this lane's pixel (all lanes call it), traced
@@ -1399,31 +1333,27 @@ __global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, fl
   }
 }
 
-// interior term: warps take work items.  ACC selects where the gradient collects:
-//   kAccPartials  the block accumulates dV/dN into its own partial [6V] in global
-//                 memory (L2-resident), with atomic adds whose result is not read:
-//                 they retire in L2 without holding up the warp, where float adds to
-//                 shared memory cost a read and a compare-and-swap loop each.  The
-//                 partials are summed in block order by k_reduce_partials (single
-//                 instance)
-//   kAccFlush     the block accumulates dV/dN in shared memory (sdV [V][3], sdN
-//                 [V][3]), works through the instances in order and, when every warp
-//                 is done with one, adds its non-zero sums into that instance's extra
-//                 [6V] (global atomics) and clears them
-//   kAccGlobal    meshes whose [V][6] sums exceed shared memory: every run of hits on
-//                 one triangle is added straight into the instance's extra [6V]
-//   kAccFixed     HR_DETERMINISTIC: every run goes straight into the instance's
-//                 fixed-point sums fx [6V] (order-free integer atomics)
-constexpr int kAccPartials = 0, kAccFlush = 1, kAccGlobal = 2, kAccFixed = 3;
+// interior term: warps take work items.  ACC selects where the gradient collects;
+// every mode adds with atomic adds whose result is not read, which retire in L2
+// without holding up the warp (float adds to shared memory cost a read and a
+// compare-and-swap loop each, and made the sums a quarter of this kernel's time):
+//   kAccPartials  each block into its own partial [6V] (L2-resident), summed in block
+//                 order by k_reduce_partials (single instance)
+//   kAccDirect    every run of hits on one triangle straight into its instance's
+//                 extra [6V] (batches)
+//   kAccGlobal    meshes beyond kPartialMaxV vertices: into the instance's float64
+//                 extra64 [6V] (long runs of cancelling contributions)
+//   kAccFixed     HR_DETERMINISTIC: into the instance's fixed-point sums fx [6V]
+//                 (order-free integer atomics)
+constexpr int kAccPartials = 0, kAccDirect = 1, kAccGlobal = 2, kAccFixed = 3;
 template <bool STATS, int ACC, int S>
 __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(RenderArgs a_in,
                                                                              const float* __restrict__ adjoint,
                                                                              float* __restrict__ partials,
                                                                              unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
-  extern __shared__ float sacc[];
-  float* part = ACC == kAccPartials ? partials + (size_t)blockIdx.x * 6 * a0.V : sacc;
-  if (ACC == kAccPartials || ACC == kAccFlush) {
+  float* part = partials + (size_t)blockIdx.x * 6 * a0.V;
+  if (ACC == kAccPartials) {
     for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) part[i] = 0.0f;
     __syncthreads();
   }
@@ -1439,10 +1369,11 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
       sdV = a0.wk.extra64 + (size_t)inst * 6 * a0.V;
     else if constexpr (ACC == kAccFixed)
       sdV = a0.wk.fx + (size_t)inst * 6 * a0.V;
+    else if constexpr (ACC == kAccDirect)
+      sdV = a0.wk.extra + (size_t)inst * 6 * a0.V;
     else
       sdV = part;
     AccT* sdN = sdV + 3 * a0.V;
-    int did = 0;
     for (;;) {
       const int it = next_item(a, inst, n);
       if (it < 0) break;
@@ -1457,20 +1388,6 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
       int s0, s1;
       item_samples(item.y, item.z, t.spp, s0, s1);
       grad_samples<STATS, S, AccT, false>(a, t, cam, pk.x, pk.y, s0, s1, live, g, sdV, sdN, cnt);
-      did = 1;
-    }
-    if (ACC == kAccFlush) {
-      if (__syncthreads_or(did)) {
-        float* dst = a0.wk.extra + (size_t)inst * 6 * a0.V;
-        for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) {
-          const float v = sacc[i];
-          if (v != 0.0f) {
-            atomicAdd(dst + i, v);
-            sacc[i] = 0.0f;
-          }
-        }
-        __syncthreads();
-      }
     }
   }
   flush_counts<STATS>(cnt, stats);
@@ -1561,165 +1478,221 @@ __global__ void k_silhouettes(const float* __restrict__ verts_all, const int* __
   if (threadIdx.x == 0) counts[view] = base;
 }
 
-// closest hit among the pool candidates at `off` for one ray, searched by the whole
-// warp: lane l tests candidate base + l of each group of 32 (depth-sorted), the warp
-// keeps the nearest (t, then the lower triangle id), and stops at the first group
-// whose nearest depth is beyond the hit found so far -- the same hit as testing the
-// candidates one by one in depth order.  Every lane returns the same hit.
-template <bool STATS>
-__device__ __forceinline__ Hit closest_candidate_warp(const RenderArgs& a, int off, int K, float sx, float sy,
-                                                      float3 o, float3 d, Counts& cnt) {
-  const int lane = threadIdx.x & 31;
-  Hit h{-1, INFINITY, 0.0f, 0.0f};
-  for (int base = 0; base < K; base += 32) {
-    if (!in_range(a.status, off + base, 0, a.wk.pool_cap)) break;
-    const float z0 = __ldg(&a.wk.z[off + base]);
-    if (h.t < z0 - (1e-4f * fabsf(z0) + 1e-6f)) break;   // uniform: h is the warp's hit
-    Hit m{-1, INFINITY, 0.0f, 0.0f};
-    const int c = base + lane;
-    if (c < K && in_range(a.status, off + c, 0, a.wk.pool_cap)) {
-      const float zm = __ldg(&a.wk.z[off + c]);
-      if (!(h.t < zm - (1e-4f * fabsf(zm) + 1e-6f))) {
-        const float4 bb = __ldg(&a.wk.bb[off + c]);
-        if (STATS) ++cnt.cands;
-        if (sx >= bb.x && sx <= bb.z && sy >= bb.y && sy <= bb.w) {
-          const int k = __ldg(&a.wk.rec[off + c]);
-          if (in_range(a.status, k, 0, a.max_visits - 1)) isect<STATS>(a.tris, k, o, d, m, cnt);
-        }
-      }
-    }
-    // warp minimum of (t, id)
+// nearer of two hits: smaller t, then the lower triangle id (a miss loses)
+__device__ __forceinline__ bool nearer(const Hit& m, const Hit& h) {
+  return m.tri >= 0 && (h.tri < 0 || m.t < h.t || (m.t == h.t && m.tri < h.tri));
+}
+
+// the nearest hit of a group of L lanes (all 32 lanes call; the result is the same in
+// every lane of a group)
+template <int L>
+__device__ __forceinline__ Hit group_min(Hit m) {
 #pragma unroll
-    for (int sh = 16; sh > 0; sh >>= 1) {
-      const float t2 = __shfl_xor_sync(0xffffffffu, m.t, sh);
-      const int i2 = __shfl_xor_sync(0xffffffffu, m.tri, sh);
-      const float u2 = __shfl_xor_sync(0xffffffffu, m.u, sh);
-      const float v2 = __shfl_xor_sync(0xffffffffu, m.v, sh);
-      if (i2 >= 0 && (m.tri < 0 || t2 < m.t || (t2 == m.t && i2 < m.tri))) {
-        m.t = t2;
-        m.tri = i2;
-        m.u = u2;
-        m.v = v2;
-      }
-    }
-    if (m.tri >= 0 && (m.t < h.t || (m.t == h.t && m.tri < h.tri))) h = m;
+  for (int sh = L / 2; sh > 0; sh >>= 1) {
+    Hit o;
+    o.t = __shfl_xor_sync(0xffffffffu, m.t, sh, L);
+    o.tri = __shfl_xor_sync(0xffffffffu, m.tri, sh, L);
+    o.u = __shfl_xor_sync(0xffffffffu, m.u, sh, L);
+    o.v = __shfl_xor_sync(0xffffffffu, m.v, sh, L);
+    if (nearer(o, m)) m = o;
   }
-  return h;
+  return m;
 }
 
-// radiance through (sx, sy) for the whole warp (every lane returns the same value)
-template <bool STATS>
-__device__ __forceinline__ float3 radiance_warp(const RenderArgs& a, const Cam& cam, long long pix0, int W, float sx,
-                                                float sy, int bx, int by, int off, int K, Counts& cnt) {
-  const float3 o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
-  const float3 d = primary_dir(cam, sx, sy);
-  const int lane = threadIdx.x & 31;
-  if (STATS && lane == 0) {
-    ++cnt.samples;
-    ++cnt.rays;
-  }
-  Hit h{-1, INFINITY, 0.0f, 0.0f};
-  if (K > 0) {
-    h = closest_candidate_warp<STATS>(a, off, K, sx, sy, o, d, cnt);
-  } else if (K < 0) {
-    Counts c0;
-    if (lane == 0) h = trace<STATS>(a.nodes, a.tris, o, d, a.status, STATS ? cnt : c0, a.max_visits);
-    h.tri = __shfl_sync(0xffffffffu, h.tri, 0);
-    h.t = __shfl_sync(0xffffffffu, h.t, 0);
-    h.u = __shfl_sync(0xffffffffu, h.u, 0);
-    h.v = __shfl_sync(0xffffffffu, h.v, 0);
-  }
-  if (STATS && lane == 0) cnt.hits += h.tri >= 0;
-  if (h.tri >= 0) return shade(a, h);
-  return ld3(a.bg + 3 * (pix0 + (size_t)by * W + bx));
-}
-
-// boundary term (edge sampling); one warp per (view, sample): warp i is sample
-// i % Ne_max of global view i / Ne_max (views with fewer samples skip the rest).  The
-// lanes compute the sample's set-up redundantly (same values, broadcast loads), search
-// the candidates of both offset rays together, and lanes 0-5 add the six results.
+// boundary term (edge sampling).  A warp takes 32 / L samples, L lanes each: sample i
+// of the launch is i % Ne_max of global view i / Ne_max (views with fewer samples skip
+// the rest).  The lanes of a group compute the sample's set-up redundantly (same
+// values, broadcast loads), then search the depth-sorted candidates of the sub-tile
+// under the sample L at a time, lane q of the group testing candidate base + q against
+// both offset rays (f+ and f-) and the group keeping the nearest hit of each (t, then
+// the lower triangle id).  A ray stops at the first group of candidates whose nearest
+// depth lies beyond its hit: the hits are those of testing the candidates one by one
+// in depth order.  Lanes 0-5 of the group add the six results.
 __device__ __forceinline__ void add1(float* p, float x) { atomicAdd(p, x); }
 __device__ __forceinline__ void add1(unsigned long long* p, float x) { add_fixed(p, x); }
 
 // T: float sums (dedge [n_inst][3V]) or fixed-point sums (fx [n_inst][6V], dV part)
-template <bool STATS, class T>
+constexpr int kEdgeLanes = 8;
+template <bool STATS, class T, int L>
 __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoint,
                                                                  const int* __restrict__ edges,
                                                                  const int* __restrict__ lists, int stride,
                                                                  const int* __restrict__ counts, int Ne_max, float eps,
                                                                  T* __restrict__ d_verts_all, long long inst_stride,
                                                                  unsigned long long* stats) {
+  static_assert(L == 8 || L == 16 || L == 32, "lanes per edge sample");
+  const unsigned full = 0xffffffffu;
   const RenderArgs a0 = with_iter(a_in);
-  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= (long long)a0.nviews * Ne_max) return;   // whole warps leave together
-  const int view = (int)(i / Ne_max), k = (int)(i - (long long)view * Ne_max);
-  SubTile vw;
-  int st0, nsx;
-  view_info(a0, view, vw, st0, nsx);
-  const int Ne = a0.vt ? __ldg(&a0.vt[view].ne) : Ne_max;
-  if (k >= Ne) return;
-  if (!in_range(a0.status, vw.inst, 0, a0.n_inst)) return;
-  const RenderArgs a = for_inst(a0, vw.inst);
-  T* d_verts = d_verts_all + (size_t)vw.inst * inst_stride;
-  int nsil = counts[view];
-  if (nsil == 0) return;
-  uint4 r = philox4x32_10(make_uint4((uint32_t)k, vw.ctr1, 0u, a.iter4 | 1u), a.key);
-  int si = (int)__umulhi(r.x, (uint32_t)nsil);
-  float t = u24(r.y);
-  int e = lists[(size_t)view * stride + si];
-  int ia = edges[2 * e], ib = edges[2 * e + 1];
-  Cam cam = load_cam(a.cams, view);
-  float3 va = ld3(a.verts + 3 * ia), vb = ld3(a.verts + 3 * ib);
-  float ax, ay, bx, by;
-  if (!project(cam, va, ax, ay) || !project(cam, vb, bx, by)) return;
-  float x = __fmaf_rn(t, __fsub_rn(bx, ax), ax), y = __fmaf_rn(t, __fsub_rn(by, ay), ay);
-  float nx = __fsub_rn(ay, by), ny = __fsub_rn(bx, ax);
-  float len = __fsqrt_rn(__fmaf_rn(nx, nx, __fmul_rn(ny, ny)));
-  if (!(len > 0.0f)) return;
-  float nhx = __fdiv_rn(nx, len), nhy = __fdiv_rn(ny, len);
-  float fxp = floorf(x), fyp = floorf(y);
-  const int W = vw.W, H = vw.H;
-  if (fxp < 0.0f || fyp < 0.0f || fxp >= (float)W || fyp >= (float)H) return;
-  int px = (int)fxp, py = (int)fyp;
-  float3 A = ld3(adjoint + 3 * (vw.pix0 + (size_t)py * W + px));
-  if (A.x == 0.0f && A.y == 0.0f && A.z == 0.0f) return;
-  float xp = __fmaf_rn(eps, nhx, x), yp = __fmaf_rn(eps, nhy, y);
-  float xm = __fmaf_rn(-eps, nhx, x), ym = __fmaf_rn(-eps, nhy, y);
-  int bxp = (int)fminf(fmaxf(floorf(xp), 0.0f), (float)(W - 1));
-  int byp = (int)fminf(fmaxf(floorf(yp), 0.0f), (float)(H - 1));
-  int bxm = (int)fminf(fmaxf(floorf(xm), 0.0f), (float)(W - 1));
-  int bym = (int)fminf(fmaxf(floorf(ym), 0.0f), (float)(H - 1));
-  // the candidates of the sub-tile holding the centre pixel serve both offset rays:
-  // its frustum is padded by half a pixel and the offsets are far smaller
-  const int st = st0 + (py / kSubH) * nsx + (px / kSubW);
-  int2 pk = a.wk.st[st];
-  if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
+  const int lane = threadIdx.x & 31, q = lane % L;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long i = warp * (32 / L) + lane / L;
+  if (warp * (32 / L) >= (long long)a0.nviews * Ne_max) return;   // whole warps leave together
   Counts cnt;
-  float3 fp = radiance_warp<STATS>(a, cam, vw.pix0, W, xp, yp, bxp, byp, pk.x, pk.y, cnt);
-  float3 fm = radiance_warp<STATS>(a, cam, vw.pix0, W, xm, ym, bxm, bym, pk.x, pk.y, cnt);
-  if (STATS) {
-    unsigned v[kStatsPer] = {cnt.samples, cnt.rays, cnt.nodes, cnt.tris, cnt.hits, cnt.cands};
-    for (int q = 0; q < kStatsPer; ++q) {
-      unsigned long long xq = v[q];
-      for (int o2 = 16; o2 > 0; o2 >>= 1) xq += __shfl_down_sync(0xffffffffu, xq, o2);
-      if (lane == 0 && xq) atomicAdd(stats + q, xq);
+  // ---- set-up (group-uniform); `active` groups go on to the search -------------
+  bool active = i < (long long)a0.nviews * Ne_max;
+  const int view = active ? (int)(i / Ne_max) : 0, k = active ? (int)(i - (long long)view * Ne_max) : 0;
+  SubTile vw;
+  int st0 = 0, nsx = 1;
+  RenderArgs a = a0;
+  T* d_verts = d_verts_all;
+  int nsil = 0, ia = 0, ib = 0, K = 0, off = 0, W = 1;
+  float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f, x = 0.f, y = 0.f, xp = 0.f, yp = 0.f, xm = 0.f, ym = 0.f;
+  int bxp = 0, byp = 0, bxm = 0, bym = 0;
+  float3 A = make_float3(0.f, 0.f, 0.f), va = A, vb = A, dp = A, dm = A, o = A;
+  Cam cam;
+  if (active) {
+    view_info(a0, view, vw, st0, nsx);
+    const int Ne = a0.vt ? __ldg(&a0.vt[view].ne) : Ne_max;
+    active = k < Ne && in_range(a0.status, vw.inst, 0, a0.n_inst);
+    if (active) {
+      a = for_inst(a0, vw.inst);
+      d_verts = d_verts_all + (size_t)vw.inst * inst_stride;
+      nsil = counts[view];
+      active = nsil > 0;
+    }
+    if (active) {
+      const uint4 r = philox4x32_10(make_uint4((uint32_t)k, vw.ctr1, 0u, a.iter4 | 1u), a.key);
+      const int si = (int)__umulhi(r.x, (uint32_t)nsil);
+      const float t = u24(r.y);
+      const int e = lists[(size_t)view * stride + si];
+      ia = edges[2 * e];
+      ib = edges[2 * e + 1];
+      cam = load_cam(a.cams, view);
+      va = ld3(a.verts + 3 * ia);
+      vb = ld3(a.verts + 3 * ib);
+      active = project(cam, va, ax, ay) && project(cam, vb, bx, by);
+      if (active) {
+        x = __fmaf_rn(t, __fsub_rn(bx, ax), ax);
+        y = __fmaf_rn(t, __fsub_rn(by, ay), ay);
+        const float nx = __fsub_rn(ay, by), ny = __fsub_rn(bx, ax);
+        const float len = __fsqrt_rn(__fmaf_rn(nx, nx, __fmul_rn(ny, ny)));
+        active = len > 0.0f;
+        if (active) {
+          const float nhx = __fdiv_rn(nx, len), nhy = __fdiv_rn(ny, len);
+          const float fxp = floorf(x), fyp = floorf(y);
+          W = vw.W;
+          const int H = vw.H;
+          active = !(fxp < 0.0f || fyp < 0.0f || fxp >= (float)W || fyp >= (float)H);
+          if (active) {
+            const int px = (int)fxp, py = (int)fyp;
+            A = ld3(adjoint + 3 * (vw.pix0 + (size_t)py * W + px));
+            active = A.x != 0.0f || A.y != 0.0f || A.z != 0.0f;
+            if (active) {
+              xp = __fmaf_rn(eps, nhx, x);
+              yp = __fmaf_rn(eps, nhy, y);
+              xm = __fmaf_rn(-eps, nhx, x);
+              ym = __fmaf_rn(-eps, nhy, y);
+              bxp = (int)fminf(fmaxf(floorf(xp), 0.0f), (float)(W - 1));
+              byp = (int)fminf(fmaxf(floorf(yp), 0.0f), (float)(H - 1));
+              bxm = (int)fminf(fmaxf(floorf(xm), 0.0f), (float)(W - 1));
+              bym = (int)fminf(fmaxf(floorf(ym), 0.0f), (float)(H - 1));
+              // the candidates of the sub-tile holding the centre pixel serve both
+              // offset rays: its frustum is padded by half a pixel and the offsets are
+              // far smaller
+              const int st = st0 + (py / kSubH) * nsx + (px / kSubW);
+              int2 pk = a.wk.st[st];
+              if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
+              off = pk.x;
+              K = pk.y;
+              o = make_float3(cam.c[0], cam.c[1], cam.c[2]);
+              dp = primary_dir(cam, xp, yp);
+              dm = primary_dir(cam, xm, ym);
+              if (STATS && q == 0) {
+                cnt.samples += 2;
+                cnt.rays += 2;
+              }
+            }
+          }
+        }
+      }
     }
   }
-  float wgt = (A.x * (fp.x - fm.x) + A.y * (fp.y - fm.y) + A.z * (fp.z - fm.z)) * ((float)nsil / (float)Ne);
-  if (wgt == 0.0f || lane >= 6) return;
-  float dax = wgt * (by - y), day = wgt * (x - bx), dbx = wgt * (y - ay), dby = wgt * (ax - x);
-  // projection Jacobian of endpoint q = lane / 3, coordinate lane % 3: J^T g = R^T (gx, gy, gz)
-  const int q = lane / 3, comp = lane % 3;
-  const float3 p = q == 0 ? va : vb;
-  const float g2x = q == 0 ? dax : dbx, g2y = q == 0 ? day : dby;
-  float X = cam.R[0] * p.x + cam.R[1] * p.y + cam.R[2] * p.z + cam.t[0];
-  float Y = cam.R[3] * p.x + cam.R[4] * p.y + cam.R[5] * p.z + cam.t[1];
-  float Z = cam.R[6] * p.x + cam.R[7] * p.y + cam.R[8] * p.z + cam.t[2];
-  float iz = 1.0f / Z;
-  float gx = g2x * cam.fx * iz, gy = g2y * cam.fy * iz;
-  float gz = -(gx * X + gy * Y) * iz;
-  add1(&d_verts[3 * (q == 0 ? ia : ib) + comp], cam.R[comp] * gx + cam.R[3 + comp] * gy + cam.R[6 + comp] * gz);
+  Hit hp{-1, INFINITY, 0.0f, 0.0f}, hm{-1, INFINITY, 0.0f, 0.0f};
+  // ---- no candidate list: lanes 0 and 1 of the group traverse the BVH -----------
+  if (__any_sync(full, active && K < 0)) {
+    Hit h{-1, INFINITY, 0.0f, 0.0f};
+    if (active && K < 0 && q < 2) h = trace<STATS>(a.nodes, a.tris, o, q == 0 ? dp : dm, a.status, cnt, a.max_visits);
+    const int g0 = lane - q;
+    Hit r0, r1;
+    r0.tri = __shfl_sync(full, h.tri, g0);
+    r0.t = __shfl_sync(full, h.t, g0);
+    r0.u = __shfl_sync(full, h.u, g0);
+    r0.v = __shfl_sync(full, h.v, g0);
+    r1.tri = __shfl_sync(full, h.tri, g0 + 1);
+    r1.t = __shfl_sync(full, h.t, g0 + 1);
+    r1.u = __shfl_sync(full, h.u, g0 + 1);
+    r1.v = __shfl_sync(full, h.v, g0 + 1);
+    if (active && K < 0) {
+      hp = r0;
+      hm = r1;
+    }
+  }
+  // ---- candidate search, both rays together, L candidates per step ---------------
+  bool donep = !(active && K > 0), donem = donep;
+  for (int base = 0;; base += L) {
+    const bool go = !(donep && donem) && base < K;
+    if (!__any_sync(full, go)) break;
+    Hit mp{-1, INFINITY, 0.0f, 0.0f}, mm{-1, INFINITY, 0.0f, 0.0f};
+    if (go) {
+      // group-uniform: no candidate from here on can be nearer than a ray's hit
+      const float z0 = __ldg(&a.wk.z[off + base]);
+      const float zl0 = z0 - (1e-4f * fabsf(z0) + 1e-6f);
+      donep = donep || hp.t < zl0;
+      donem = donem || hm.t < zl0;
+      const int c = base + q;
+      if (!(donep && donem) && c < K && in_range(a.status, off + c, 0, a.wk.pool_cap)) {
+        const float zm = __ldg(&a.wk.z[off + c]);
+        const float zl = zm - (1e-4f * fabsf(zm) + 1e-6f);
+        bool tp = !donep && !(hp.t < zl), tm = !donem && !(hm.t < zl);
+        if (tp || tm) {
+          const float4 bb = __ldg(&a.wk.bb[off + c]);
+          if (STATS) cnt.cands += (unsigned)tp + (unsigned)tm;
+          tp = tp && xp >= bb.x && xp <= bb.z && yp >= bb.y && yp <= bb.w;
+          tm = tm && xm >= bb.x && xm <= bb.z && ym >= bb.y && ym <= bb.w;
+          if (tp || tm) {
+            const int kr = __ldg(&a.wk.rec[off + c]);
+            if (in_range(a.status, kr, 0, a.max_visits - 1)) {
+              if (tp) isect<STATS>(a.tris, kr, o, dp, mp, cnt);
+              if (tm) isect<STATS>(a.tris, kr, o, dm, mm, cnt);
+            }
+          }
+        }
+      }
+    }
+    mp = group_min<L>(mp);
+    mm = group_min<L>(mm);
+    if (go) {
+      if (nearer(mp, hp)) hp = mp;
+      if (nearer(mm, hm)) hm = mm;
+    }
+  }
+  if (STATS) {
+    if (q == 0) cnt.hits += (unsigned)(active && hp.tri >= 0) + (unsigned)(active && hm.tri >= 0);
+    unsigned v[kStatsPer] = {cnt.samples, cnt.rays, cnt.nodes, cnt.tris, cnt.hits, cnt.cands};
+    for (int s2 = 0; s2 < kStatsPer; ++s2) {
+      unsigned long long xq = v[s2];
+      for (int o2 = 16; o2 > 0; o2 >>= 1) xq += __shfl_down_sync(full, xq, o2);
+      if (lane == 0 && xq) atomicAdd(stats + s2, xq);
+    }
+  }
+  if (!active || q >= 6) return;
+  const float3 fp = hp.tri >= 0 ? shade(a, hp) : ld3(a.bg + 3 * (vw.pix0 + (size_t)byp * W + bxp));
+  const float3 fm = hm.tri >= 0 ? shade(a, hm) : ld3(a.bg + 3 * (vw.pix0 + (size_t)bym * W + bxm));
+  const int Ne = a0.vt ? __ldg(&a0.vt[view].ne) : Ne_max;
+  const float wgt = (A.x * (fp.x - fm.x) + A.y * (fp.y - fm.y) + A.z * (fp.z - fm.z)) * ((float)nsil / (float)Ne);
+  if (wgt == 0.0f) return;
+  const float dax = wgt * (by - y), day = wgt * (x - bx), dbx = wgt * (y - ay), dby = wgt * (ax - x);
+  // projection Jacobian of endpoint e = q / 3, coordinate q % 3: J^T g = R^T (gx, gy, gz)
+  const int ep = q / 3, comp = q % 3;
+  const float3 p = ep == 0 ? va : vb;
+  const float g2x = ep == 0 ? dax : dbx, g2y = ep == 0 ? day : dby;
+  const float X = cam.R[0] * p.x + cam.R[1] * p.y + cam.R[2] * p.z + cam.t[0];
+  const float Y = cam.R[3] * p.x + cam.R[4] * p.y + cam.R[5] * p.z + cam.t[1];
+  const float Z = cam.R[6] * p.x + cam.R[7] * p.y + cam.R[8] * p.z + cam.t[2];
+  const float iz = 1.0f / Z;
+  const float gx = g2x * cam.fx * iz, gy = g2y * cam.fy * iz;
+  const float gz = -(gx * X + gy * Y) * iz;
+  add1(&d_verts[3 * (ep == 0 ? ia : ib) + comp], cam.R[comp] * gx + cam.R[3 + comp] * gy + cam.R[6 + comp] * gz);
 }
 
 // dm_v = (I - n n^T) dN_v / |m_v|; blockIdx.y selects the instance
@@ -1888,33 +1861,6 @@ int render_grid(int device, int* blocks, int* threads, int* num_sms) {
   return HR_OK;
 }
 
-size_t render_bwd_smem(int V) { return (size_t)6 * V * sizeof(float); }
-
-template <bool STATS, int ACC, int S>
-bool set_bwd_smem(int smem) {
-  return cudaFuncSetAttribute(k_shade_bwd<STATS, ACC, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-         cudaSuccess;
-}
-
-template <bool STATS, int ACC>
-bool set_bwd_smem_all(int smem) {
-  return set_bwd_smem<STATS, ACC, 1>(smem) && set_bwd_smem<STATS, ACC, 2>(smem) &&
-         set_bwd_smem<STATS, ACC, 4>(smem);
-}
-
-int configure_render_kernels(int max_V) {
-  // the largest any context may use (max_V <= 8192), so that creating a smaller
-  // context never lowers the opt-in of a larger one
-  (void)max_V;
-  const int smem = (int)render_bwd_smem(8192);
-  if (!set_bwd_smem_all<true, kAccPartials>(smem) || !set_bwd_smem_all<false, kAccPartials>(smem) ||
-      !set_bwd_smem_all<true, kAccFlush>(smem) || !set_bwd_smem_all<false, kAccFlush>(smem)) {
-    cudaGetLastError();
-    return HR_ERR_CUDA;
-  }
-  return HR_OK;
-}
-
 int subtiles_for(int views, int W, int H) { return views * ((W + kSubW - 1) / kSubW) * ((H + kSubH - 1) / kSubH); }
 int subtile_columns(int W) { return (W + kSubW - 1) / kSubW; }
 
@@ -2032,14 +1978,13 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
         acc == kAccPartials ? nblocks : 0, V, d_verts, ctx->dN);
   };
   if (interior) {
-    // shared-memory sums up to the opt-in of configure_render_kernels (V <= 8192),
-    // global float64 atomics beyond; fixed-point global sums when deterministic
-    const bool global_acc = render_bwd_smem(V) > render_bwd_smem(8192);
+    // float sums up to kPartialMaxV vertices (per block, or per instance in a batch),
+    // float64 beyond; fixed-point sums when deterministic
+    const bool global_acc = V > kPartialMaxV;
     if (!det && global_acc &&
         (!ctx->extra64 || cudaMemsetAsync(ctx->extra64, 0, sizeof(double) * 6 * V * ni, s) != cudaSuccess))
       return ctx->extra64 ? HR_ERR_CUDA : HR_ERR_UNSUPPORTED;
-    const int acc = det ? kAccFixed : (global_acc ? kAccGlobal : (batch ? kAccFlush : kAccPartials));
-    const size_t smem = acc == kAccFlush ? render_bwd_smem(V) : 0;
+    const int acc = det ? kAccFixed : (global_acc ? kAccGlobal : (batch ? kAccDirect : kAccPartials));
     // deterministic: one ray per lane, the arithmetic of the overflow kernel, which may
     // trace any sub-tile whose candidates found no room in the pool
     const int S = det ? 1 : ctx->tune.bwd_rays_per_lane;
@@ -2048,12 +1993,12 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
       : (S == 1 ? k_shade_bwd<false, A_, 1> : (S == 2 ? k_shade_bwd<false, A_, 2> : k_shade_bwd<false, A_, 4>)))
     auto kern = acc == kAccFixed    ? HR_BWD_KERNEL(kAccFixed)
                 : acc == kAccGlobal ? HR_BWD_KERNEL(kAccGlobal)
-                                    : (acc == kAccFlush ? HR_BWD_KERNEL(kAccFlush) : HR_BWD_KERNEL(kAccPartials));
+                                    : (acc == kAccDirect ? HR_BWD_KERNEL(kAccDirect) : HR_BWD_KERNEL(kAccPartials));
 #undef HR_BWD_KERNEL
     // the block partials are sized for kBlocksPerSm blocks per SM
     const int blocks = ctx->num_sms * ctx->tune.bwd_blocks_per_sm;
     tm.begin(kTimeBwdShade);
-    kern<<<blocks, kRenderThreads, smem, s>>>(a, adjoint, ctx->partials, st ? ctx->stats + kStatsPer : nullptr);
+    kern<<<blocks, kRenderThreads, 0, s>>>(a, adjoint, ctx->partials, st ? ctx->stats + kStatsPer : nullptr);
     HR_CHECK_LAUNCH();
     if (st)
       k_overflow<true, true><<<blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, ctx->stats + kStatsPer);
@@ -2075,15 +2020,17 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     int rc = launch_silhouettes(ctx, m, verts, cams, nv, ctx->sil, ctx->lim.max_E, ctx->sil_count, es);
     if (rc != HR_OK) return rc;
     tm.end(kTimeBwdSil);
-    const long long n = (long long)nv * Ne * 32;   // one warp per edge sample
+    // kEdgeLanes lanes per edge sample
+    const long long n = ((long long)nv * Ne + 32 / kEdgeLanes - 1) / (32 / kEdgeLanes) * 32;
     const unsigned grid = (unsigned)((n + kRenderThreads - 1) / kRenderThreads);
     tm.begin(kTimeBwdEdges);
     if (det) {
-      auto kern = st ? k_edge_samples<true, unsigned long long> : k_edge_samples<false, unsigned long long>;
+      auto kern = st ? k_edge_samples<true, unsigned long long, kEdgeLanes>
+                    : k_edge_samples<false, unsigned long long, kEdgeLanes>;
       kern<<<grid, kRenderThreads, 0, es>>>(a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count, Ne,
                                             o->edge_eps_px, ctx->acc_fx, 6LL * V, ctx->stats + 2 * kStatsPer);
     } else {
-      auto kern = st ? k_edge_samples<true, float> : k_edge_samples<false, float>;
+      auto kern = st ? k_edge_samples<true, float, kEdgeLanes> : k_edge_samples<false, float, kEdgeLanes>;
       kern<<<grid, kRenderThreads, 0, es>>>(a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count, Ne,
                                             o->edge_eps_px, ctx->dedge, 3LL * V, ctx->stats + 2 * kStatsPer);
     }
