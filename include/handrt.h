@@ -192,8 +192,10 @@ typedef struct hr_context hr_context;
  *   bwd_blocks_per_sm  persistent blocks per SM of the backward shader (1 .. 8)
  *   bwd_rays_per_lane  rays_per_lane of the backward shader (1, 2, 4)
  *   bwd_cand_per_chunk cand_per_chunk of the backward's work items (>= 1)
+ *   edge_lanes         lanes per silhouette-edge sample in the edge-sampling kernel
+ *                      (2, 4, 8, 16, 32: a warp takes 32 / edge_lanes samples)
  * Every setting gives the same results (the backward up to float32 summation order);
- * only the speed changes.  Defaults: 2, 8, 16, 8, 4, 4, 16. */
+ * only the speed changes.  Defaults: 2, 8, 16, 8, 4, 4, 16, 4. */
 typedef struct hr_tuning {
     int32_t rays_per_lane;
     int32_t cand_per_chunk;
@@ -202,6 +204,7 @@ typedef struct hr_tuning {
     int32_t bwd_blocks_per_sm;
     int32_t bwd_rays_per_lane;
     int32_t bwd_cand_per_chunk;
+    int32_t edge_lanes;
 } hr_tuning;
 
 /* Create a context on the current CUDA device: device scratch for the given

@@ -77,7 +77,8 @@ class hr_instance_desc(ctypes.Structure):
 
 class hr_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("rays_per_lane", "cand_per_chunk", "max_chunks", "blocks_per_sm",
-                                              "bwd_blocks_per_sm", "bwd_rays_per_lane", "bwd_cand_per_chunk")]
+                                              "bwd_blocks_per_sm", "bwd_rays_per_lane", "bwd_cand_per_chunk",
+                                              "edge_lanes")]
 
 
 class hr_limits(ctypes.Structure):

@@ -90,7 +90,7 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
   std::memset(c, 0, sizeof(Context));
   c->lim = *lim;
   c->n_inst = n;
-  c->tune = hr_tuning{2, 8, 16, 8, 4, 4, 16};
+  c->tune = hr_tuning{2, 8, 16, 8, 4, 4, 16, 4};
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     delete c;
     return HR_ERR_CUDA;
@@ -280,7 +280,9 @@ int hr_set_tuning(hr_context* ctx, const hr_tuning* t) {
   if (!rays_ok(t->rays_per_lane) || !rays_ok(t->bwd_rays_per_lane) || t->cand_per_chunk < 1 ||
       t->bwd_cand_per_chunk < 1 ||
       t->max_chunks < 1 || t->max_chunks > 16 || t->blocks_per_sm < 1 || t->blocks_per_sm > 8 ||
-      t->bwd_blocks_per_sm < 1 || t->bwd_blocks_per_sm > 8)
+      t->bwd_blocks_per_sm < 1 || t->bwd_blocks_per_sm > 8 ||
+      !(t->edge_lanes == 2 || t->edge_lanes == 4 || t->edge_lanes == 8 || t->edge_lanes == 16 ||
+        t->edge_lanes == 32))
     return HR_ERR_ARG;
   c->tune = *t;
   return HR_OK;

@@ -1507,12 +1507,13 @@ __device__ __forceinline__ Hit group_min(Hit m) {
 // both offset rays (f+ and f-) and the group keeping the nearest hit of each (t, then
 // the lower triangle id).  A ray stops at the first group of candidates whose nearest
 // depth lies beyond its hit: the hits are those of testing the candidates one by one
-// in depth order.  Lanes 0-5 of the group add the six results.
+// in depth order.  The group's lanes add the six results (two endpoints x three
+// coordinates).
 __device__ __forceinline__ void add1(float* p, float x) { atomicAdd(p, x); }
 __device__ __forceinline__ void add1(unsigned long long* p, float x) { add_fixed(p, x); }
 
-// T: float sums (dedge [n_inst][3V]) or fixed-point sums (fx [n_inst][6V], dV part)
-constexpr int kEdgeLanes = 8;
+// T: float sums (dedge [n_inst][3V]) or fixed-point sums (fx [n_inst][6V], dV part);
+// L: lanes per sample (the tuning's edge_lanes)
 template <bool STATS, class T, int L>
 __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in, const float* __restrict__ adjoint,
                                                                  const int* __restrict__ edges,
@@ -1520,7 +1521,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in
                                                                  const int* __restrict__ counts, int Ne_max, float eps,
                                                                  T* __restrict__ d_verts_all, long long inst_stride,
                                                                  unsigned long long* stats) {
-  static_assert(L == 8 || L == 16 || L == 32, "lanes per edge sample");
+  static_assert(L == 2 || L == 4 || L == 8 || L == 16 || L == 32, "lanes per edge sample");
   const unsigned full = 0xffffffffu;
   const RenderArgs a0 = with_iter(a_in);
   const int lane = threadIdx.x & 31, q = lane % L;
@@ -1682,17 +1683,20 @@ __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in
   const float wgt = (A.x * (fp.x - fm.x) + A.y * (fp.y - fm.y) + A.z * (fp.z - fm.z)) * ((float)nsil / (float)Ne);
   if (wgt == 0.0f) return;
   const float dax = wgt * (by - y), day = wgt * (x - bx), dbx = wgt * (y - ay), dby = wgt * (ax - x);
-  // projection Jacobian of endpoint e = q / 3, coordinate q % 3: J^T g = R^T (gx, gy, gz)
-  const int ep = q / 3, comp = q % 3;
-  const float3 p = ep == 0 ? va : vb;
-  const float g2x = ep == 0 ? dax : dbx, g2y = ep == 0 ? day : dby;
-  const float X = cam.R[0] * p.x + cam.R[1] * p.y + cam.R[2] * p.z + cam.t[0];
-  const float Y = cam.R[3] * p.x + cam.R[4] * p.y + cam.R[5] * p.z + cam.t[1];
-  const float Z = cam.R[6] * p.x + cam.R[7] * p.y + cam.R[8] * p.z + cam.t[2];
-  const float iz = 1.0f / Z;
-  const float gx = g2x * cam.fx * iz, gy = g2y * cam.fy * iz;
-  const float gz = -(gx * X + gy * Y) * iz;
-  add1(&d_verts[3 * (ep == 0 ? ia : ib) + comp], cam.R[comp] * gx + cam.R[3 + comp] * gy + cam.R[6 + comp] * gz);
+  // the six results (endpoint ep = j / 3, coordinate j % 3), lanes q, q + L, ... of the
+  // group: the projection Jacobian's transpose, J^T g = R^T (gx, gy, gz)
+  for (int j = q; j < 6; j += L) {
+    const int ep = j / 3, comp = j % 3;
+    const float3 p = ep == 0 ? va : vb;
+    const float g2x = ep == 0 ? dax : dbx, g2y = ep == 0 ? day : dby;
+    const float X = cam.R[0] * p.x + cam.R[1] * p.y + cam.R[2] * p.z + cam.t[0];
+    const float Y = cam.R[3] * p.x + cam.R[4] * p.y + cam.R[5] * p.z + cam.t[1];
+    const float Z = cam.R[6] * p.x + cam.R[7] * p.y + cam.R[8] * p.z + cam.t[2];
+    const float iz = 1.0f / Z;
+    const float gx = g2x * cam.fx * iz, gy = g2y * cam.fy * iz;
+    const float gz = -(gx * X + gy * Y) * iz;
+    add1(&d_verts[3 * (ep == 0 ? ia : ib) + comp], cam.R[comp] * gx + cam.R[3 + comp] * gy + cam.R[6 + comp] * gz);
+  }
 }
 
 // dm_v = (I - n n^T) dN_v / |m_v|; blockIdx.y selects the instance
@@ -2020,20 +2024,28 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     int rc = launch_silhouettes(ctx, m, verts, cams, nv, ctx->sil, ctx->lim.max_E, ctx->sil_count, es);
     if (rc != HR_OK) return rc;
     tm.end(kTimeBwdSil);
-    // kEdgeLanes lanes per edge sample
-    const long long n = ((long long)nv * Ne + 32 / kEdgeLanes - 1) / (32 / kEdgeLanes) * 32;
+    // edge_lanes lanes per edge sample
+    const int L = ctx->tune.edge_lanes;
+    const long long n = ((long long)nv * Ne + 32 / L - 1) / (32 / L) * 32;
     const unsigned grid = (unsigned)((n + kRenderThreads - 1) / kRenderThreads);
     tm.begin(kTimeBwdEdges);
+#define HR_EDGE_KERNEL(T_)                                                                            \
+  (st ? (L == 2 ? k_edge_samples<true, T_, 2> : L == 4 ? k_edge_samples<true, T_, 4>                  \
+         : L == 8 ? k_edge_samples<true, T_, 8> : L == 16 ? k_edge_samples<true, T_, 16>              \
+                                                        : k_edge_samples<true, T_, 32>)               \
+      : (L == 2 ? k_edge_samples<false, T_, 2> : L == 4 ? k_edge_samples<false, T_, 4>                \
+         : L == 8 ? k_edge_samples<false, T_, 8> : L == 16 ? k_edge_samples<false, T_, 16>            \
+                                                         : k_edge_samples<false, T_, 32>))
     if (det) {
-      auto kern = st ? k_edge_samples<true, unsigned long long, kEdgeLanes>
-                    : k_edge_samples<false, unsigned long long, kEdgeLanes>;
+      auto kern = HR_EDGE_KERNEL(unsigned long long);
       kern<<<grid, kRenderThreads, 0, es>>>(a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count, Ne,
                                             o->edge_eps_px, ctx->acc_fx, 6LL * V, ctx->stats + 2 * kStatsPer);
     } else {
-      auto kern = st ? k_edge_samples<true, float, kEdgeLanes> : k_edge_samples<false, float, kEdgeLanes>;
+      auto kern = HR_EDGE_KERNEL(float);
       kern<<<grid, kRenderThreads, 0, es>>>(a, adjoint, m->edges, ctx->sil, ctx->lim.max_E, ctx->sil_count, Ne,
                                             o->edge_eps_px, ctx->dedge, 3LL * V, ctx->stats + 2 * kStatsPer);
     }
+#undef HR_EDGE_KERNEL
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdEdges);
     if (fork && (cudaEventRecord(ctx->ev_join, es) != cudaSuccess || cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess))

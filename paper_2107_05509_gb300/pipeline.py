@@ -493,6 +493,7 @@ TUNING_SPACE = {
     "bwd_blocks_per_sm": (2, 3, 4, 6),
     "bwd_rays_per_lane": (1, 2, 4),
     "bwd_cand_per_chunk": (8, 16, 32),
+    "edge_lanes": (2, 4, 8),
 }
 
 

@@ -230,11 +230,11 @@ def test_tunings_keep_results(B):
     dv = torch.empty((h.V, 3), device="cuda")
     B.hr_build_bvh(ctx, model, vt)
     for t in ({"rays_per_lane": 1, "cand_per_chunk": 8, "max_chunks": 16, "blocks_per_sm": 4, "bwd_blocks_per_sm": 2,
-               "bwd_rays_per_lane": 2, "bwd_cand_per_chunk": 16},
+               "bwd_rays_per_lane": 2, "bwd_cand_per_chunk": 16, "edge_lanes": 2},
               {"rays_per_lane": 2, "cand_per_chunk": 32, "max_chunks": 8, "blocks_per_sm": 8, "bwd_blocks_per_sm": 6,
-               "bwd_rays_per_lane": 4, "bwd_cand_per_chunk": 8},
+               "bwd_rays_per_lane": 4, "bwd_cand_per_chunk": 8, "edge_lanes": 8},
               {"rays_per_lane": 4, "cand_per_chunk": 1, "max_chunks": 1, "blocks_per_sm": 1, "bwd_blocks_per_sm": 1,
-               "bwd_rays_per_lane": 1, "bwd_cand_per_chunk": 1}):
+               "bwd_rays_per_lane": 1, "bwd_cand_per_chunk": 1, "edge_lanes": 32}):
         ctx.set_tuning(**t)
         assert ctx.get_tuning() == t
         B.hr_render_fwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o), img)
@@ -242,7 +242,8 @@ def test_tunings_keep_results(B):
         B.hr_render_bwd(ctx, model, vt, cams, sc.H, sc.W, bg, sc.gpu_opts(o, B.HR_BWD_REUSE_FWD), _t(A), dv)
         assert grad_ok(dv.cpu().numpy(), g_ref).all(), t
     for bad in ({"rays_per_lane": 3}, {"max_chunks": 17}, {"blocks_per_sm": 0}, {"bwd_blocks_per_sm": 9},
-                {"cand_per_chunk": 0}, {"bwd_rays_per_lane": 3}, {"bwd_cand_per_chunk": 0}):
+                {"cand_per_chunk": 0}, {"bwd_rays_per_lane": 3}, {"bwd_cand_per_chunk": 0}, {"edge_lanes": 3},
+                {"edge_lanes": 64}):
         with pytest.raises(B.HandrtError):
             ctx.set_tuning(**bad)
     assert B.hr_get_status(ctx) == B.HR_OK
