@@ -473,6 +473,9 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
     ref = torch.empty((n, hand.V, 3), device=dev)
     B.hr_skin_batch(bt, model, torch.as_tensor(np.stack(x_gt), device=dev), ref)
     R = P.BatchRefiner(model, bt, views, ref_verts=ref, max_iters=iters + 8, device=dev)
+    # the same batch with converged instances retired on the device (the per-instance
+    # criterion: an instance leaves the batch once its epsilon_v is <= 1 mm)
+    Rr = P.BatchRefiner(model, bt, views, ref_verts=ref, max_iters=iters + 8, device=dev, retire="converged")
 
     # work counters of one batched iteration
     R.reset(x0)
@@ -495,13 +498,16 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
 
     R.reset(x0)
     tune(bt, R.render_pass, [(c.views, c.width, c.height, c.spp, c.edge_samples) for c in cfgs])
+    Rr.reset(x0)
+    g_r = Rr.capture()
     R.reset(x0)
     g = R.capture()
     for _ in range(3):
         g.replay()
 
-    def run_batch(pre=None):
-        R.reset(x0)
+    def run_batch(pre=None, refiner=None, graph=None):
+        refiner, graph = refiner or R, graph or g
+        refiner.reset(x0)
         torch.cuda.synchronize()
         pre_ms = 0.0
         if pre is not None:
@@ -514,18 +520,19 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 1)]
         ev[0].record()
         for k in range(iters):
-            g.replay()
+            graph.replay()
             ev[k + 1].record()
         torch.cuda.synchronize()
         dt = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(iters)])
-        err = R.err[:iters].cpu().numpy() * 1e3
+        err = refiner.err[:iters].cpu().numpy() * 1e3
         status = B.hr_get_status(bt)
         if status != B.HR_OK:
             raise RuntimeError(f"batch device status {B.status_string(status)}")
         return err, dt, pre_ms
 
     err_b, dt_b, _ = run_batch()
-    res_learned = None
+    err_r, dt_r, _ = run_batch(refiner=Rr, graph=g_r)
+    res_learned = res_learned_r = None
     if learned is not None:
         from paper_2107_05509_gb300 import proposal as PR
         prop = PR.Proposer(R, learned, steps=proposal_steps)
@@ -535,6 +542,9 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
         if prop.net.status() != B.HR_OK:
             raise RuntimeError("proposal network status")
         res_learned = (err_l, dt_l, pre_ms, chosen)
+        prop.r = Rr                      # the same network and candidates for the retiring batch
+        err_lr, dt_lr, pre_ms_r = run_batch(prop.run, refiner=Rr, graph=g_r)
+        res_learned_r = (err_lr, dt_lr, pre_ms_r)
 
     # plain per-instance refinement, instance after instance
     err_p = np.full((iters, n), np.nan)
@@ -591,6 +601,12 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
     sb["tuning"] = bt.get_tuning()
     res = {"instances": n, "views": int(bt.total_views), "pixels": int(bt.total_pixels), "iterations": iters,
            "plain_sequential": sp, "batched": sb}
+    # with retirement the batch stops at the last instance's first iteration at or below
+    # 1 mm (its iterations get cheaper as instances leave)
+    sr = summary(err_r, dt_r, False)
+    sr["ms_per_iter_first"] = round(float(dt_r[0]), 3)
+    sr["ms_per_iter_last"] = round(float(dt_r[-1]), 3)
+    res["batched_retiring"] = sr
     if res_learned is not None:
         err_l, dt_l, pre_ms, chosen = res_learned
         sl = summary(err_l, dt_l, False, pre_ms)
@@ -598,10 +614,15 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
         sl["proposal_ms"] = round(pre_ms, 3)
         sl["instances_taking_a_proposal"] = int((chosen > 0).sum())
         res["batched_learned"] = sl
-    for name in ("batched", "batched_learned"):
+        err_lr, dt_lr, pre_ms_r = res_learned_r
+        res["batched_learned_retiring"] = summary(err_lr, dt_lr, False, pre_ms_r)
+    for name in ("batched", "batched_learned", "batched_retiring", "batched_learned_retiring"):
         if name in res and res[name]["time_to_mean_1mm_ms"] and sp["time_to_mean_1mm_ms"]:
             res[f"speedup_time_to_mean_1mm_{name}_vs_plain"] = round(
                 sp["time_to_mean_1mm_ms"] / res[name]["time_to_mean_1mm_ms"], 3)
+        if name in res and res[name]["time_to_each_1mm_ms"] and sp["time_to_each_1mm_ms"]:
+            res[f"speedup_time_to_each_1mm_{name}_vs_plain"] = round(
+                sp["time_to_each_1mm_ms"] / res[name]["time_to_each_1mm_ms"], 3)
     return res
 
 
@@ -964,6 +985,7 @@ def main():
     ap.add_argument("--objective-only", action="store_true", help="only the full-objective schedule")
     ap.add_argument("--edges-only", action="store_true", help="only the edge-term timings (for profiling)")
     ap.add_argument("--scale-only", action="store_true", help="only the scale workload (for profiling)")
+    ap.add_argument("--refine-only", action="store_true", help="only the time-to-1 mm refinement comparison")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "handrt":
         args.warmup = 3
@@ -981,6 +1003,11 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps(run_edge_term(torch.device("cuda", 0))), flush=True)
+        return
+    if args.refine_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_refinement(args, torch.device("cuda", 0))), flush=True)
         return
     if args.objective_only:
         import torch

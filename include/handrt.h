@@ -445,6 +445,29 @@ int hr_render_bwd_batch(hr_context* ctx, const hr_model* model, const float* ver
                         const float* background, const hr_render_opts* opts, const float* adjoint, float* d_verts,
                         hr_stream stream);
 
+/* Retiring converged instances of a batch (Section 3.3 refines each multiframe until
+ * its estimate stops improving; in a batch an instance that has converged would
+ * otherwise keep costing a full share of every launch).  hr_batch_set_active gives
+ * the batch context a device int32[n] mask (NULL: every instance active), read by
+ * every batch call at each launch (so a captured iteration sees later changes):
+ * instances with 0 are skipped by hr_skin_batch, hr_skin_bwd_batch, hr_update_bvh /
+ * hr_build_bvh_batch (single-block builds), hr_render_fwd_batch, hr_loss_batch and
+ * hr_render_bwd_batch, and their outputs keep their previous values.  The two calls
+ * below clear mask entries on the device; with lr_scale (the per-entry step sizes of
+ * hr_adam_step_dev, device float[n][per_instance]) they also zero the retired
+ * instance's steps, so that Adam leaves its parameters where they are.
+ *   hr_retire_converged: instance i retires when err[*iter_dev][i] <= threshold (err
+ *     as written by hr_vertex_error, rows rows; a criterion with ground truth, the
+ *     benchmark's 1 mm).
+ *   hr_retire_plateau: instance i retires once loss[i] (hr_loss_batch) has not fallen
+ *     below (1 - rel_tol) best[i] for `patience` calls in a row; best (device
+ *     float[n], start at +inf) and stall (device int32[n], start at 0) are its state. */
+int hr_batch_set_active(hr_context* ctx, const int32_t* active);
+int hr_retire_converged(const float* err, const uint32_t* iter_dev, int rows, int n, float threshold,
+                        int32_t* active, float* lr_scale, int per_instance, hr_stream stream);
+int hr_retire_plateau(const float* loss, int n, float rel_tol, int patience, float* best, int32_t* stall,
+                      int32_t* active, float* lr_scale, int per_instance, hr_stream stream);
+
 /* BF16 matrix product on the tensor cores (tcgen05, float32 accumulation), the
  * building block of the learned proposal network:
  *   C[M][N] = act(A[M][K] B[N][K]^T + bias[N]),  act = ReLU when relu != 0.

@@ -45,7 +45,8 @@ EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", 
            "hr_net_adam", "hr_net_status", "hr_vertex_mse", "hr_add_noise", "hr_select_best", "hr_update_bvh",
            "hr_set_tuning", "hr_get_tuning", "hr_loss_ct",
            "hr_skin_joints", "hr_skin_bwd_joints", "hr_joint_prior", "hr_colour_map", "hr_colour_map_bwd",
-           "hr_edges", "hr_edge_loss", "hr_model_check")
+           "hr_edges", "hr_edge_loss", "hr_model_check",
+           "hr_batch_set_active", "hr_retire_converged", "hr_retire_plateau")
 
 
 class HandrtError(RuntimeError):
@@ -105,6 +106,9 @@ def lib():
             "hr_skin_bwd": [P, P, P, P, P, P],
             "hr_skin_bwd_noalloc": [P, P, P, P, P],
             "hr_model_check": [P],
+            "hr_batch_set_active": [P, P],
+            "hr_retire_converged": [P, P, I, I, F, P, P, I, P],
+            "hr_retire_plateau": [P, I, F, I, P, P, P, P, I, P],
             "hr_build_bvh": [P, P, P, P],
             "hr_update_bvh": [P, P, P, P, I, P],
             "hr_set_tuning": [P, P],
@@ -531,6 +535,30 @@ class Net:
 
     def status(self, stream=None):
         return int(lib().hr_net_status(self.handle, _stream(stream)))
+
+
+def hr_batch_set_active(ctx, active):
+    """active: device int32 tensor [n] (kept alive by the caller) or None."""
+    assert active is None or (active.dtype == torch.int32 and active.is_cuda)
+    _check("hr_batch_set_active", lib().hr_batch_set_active(ctx.handle, None if active is None else _ptr(active)))
+
+
+def hr_retire_converged(err, iter_dev, threshold, active, lr_scale=None, stream=None):
+    """err: device float [rows][n] (hr_vertex_error's table); lr_scale: device float
+    [n][per] per-entry Adam steps, zeroed for retired instances."""
+    rows, n = err.shape
+    per = 0 if lr_scale is None else lr_scale.numel() // n
+    _check("hr_retire_converged", lib().hr_retire_converged(
+        _f32(err), None if iter_dev is None else _ptr(iter_dev), rows, n, float(threshold), _ptr(active),
+        None if lr_scale is None else _f32(lr_scale), per, _stream(stream)))
+
+
+def hr_retire_plateau(loss, rel_tol, patience, best, stall, active, lr_scale=None, stream=None):
+    n = loss.numel()
+    per = 0 if lr_scale is None else lr_scale.numel() // n
+    _check("hr_retire_plateau", lib().hr_retire_plateau(
+        _f32(loss), n, float(rel_tol), int(patience), _f32(best), _ptr(stall), _ptr(active),
+        None if lr_scale is None else _f32(lr_scale), per, _stream(stream)))
 
 
 def hr_vertex_mse(verts, ref, loss, d_verts=None, stream=None):

@@ -261,6 +261,30 @@ int hr_batch_create(const hr_limits* lim, const hr_instance_desc* desc, int n, h
   return HR_OK;
 }
 
+int hr_batch_set_active(hr_context* ctx, const int32_t* active) {
+  Context* c = reinterpret_cast<Context*>(ctx);
+  if (!c || !c->vt) return HR_ERR_ARG;
+  c->active = active;
+  return HR_OK;
+}
+
+int hr_retire_converged(const float* err, const uint32_t* iter_dev, int rows, int n, float threshold,
+                        int32_t* active, float* lr_scale, int per_instance, hr_stream stream) {
+  if (!err || !active || rows < 1 || n < 1 || !std::isfinite(threshold) || (lr_scale && per_instance < 1))
+    return HR_ERR_ARG;
+  return hr::launch_retire_converged(err, iter_dev, rows, n, threshold, active, lr_scale, per_instance,
+                                     (cudaStream_t)stream);
+}
+
+int hr_retire_plateau(const float* loss, int n, float rel_tol, int patience, float* best, int32_t* stall,
+                      int32_t* active, float* lr_scale, int per_instance, hr_stream stream) {
+  if (!loss || !best || !stall || !active || n < 1 || !(rel_tol >= 0.0f && rel_tol < 1.0f) || patience < 1 ||
+      (lr_scale && per_instance < 1))
+    return HR_ERR_ARG;
+  return hr::launch_retire_plateau(loss, n, rel_tol, patience, best, stall, active, lr_scale, per_instance,
+                                   (cudaStream_t)stream);
+}
+
 int hr_batch_layout(hr_context* ctx, int32_t* view_offsets, int64_t* pixel_offsets) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || !c->vt || !view_offsets || !pixel_offsets) return HR_ERR_ARG;

@@ -90,8 +90,9 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
                                                              float4* __restrict__ tris_all,
                                                              int* __restrict__ parent_all, int* __restrict__ valid,
                                                              const uint32_t* iter_dev, int rebuild_every,
-                                                             int* status) {
+                                                             int* status, const int* __restrict__ active) {
   extern __shared__ unsigned long long smem_keys[];
+  if (active && !active[blockIdx.x]) return;   // a retired instance of a batch
   unsigned long long* keys = smem_keys;
   int* parent = reinterpret_cast<int*>(keys + P);
   int* flags = parent + 2 * F;
@@ -314,9 +315,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
 // Batched: blockIdx.y selects the instance ([V][3] vertices and normals, [V] lengths).
 __global__ void k_vertex_normals(const float* __restrict__ verts_all, const int* __restrict__ faces,
                                  const int* __restrict__ vf_off, const int* __restrict__ vf_faces, int V, int F,
-                                 float* __restrict__ normals_all, float* __restrict__ normal_len_all, int* status) {
+                                 float* __restrict__ normals_all, float* __restrict__ normal_len_all, int* status,
+                                 const int* __restrict__ active) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V) return;
+  if (v >= V || (active && !active[blockIdx.y])) return;
   const float* verts = verts_all + (size_t)blockIdx.y * 3 * V;
   float* normals = normals_all + (size_t)blockIdx.y * 3 * V;
   float* normal_len = normal_len_all + (size_t)blockIdx.y * V;
@@ -659,7 +661,7 @@ int launch_build_bvh_grid(Context* ctx, const hr_model* m, const float* verts, c
                                                     ctx->bvh_bad, ctx->bvh_mode, ctx->status);
   HR_CHECK_LAUNCH();
   k_vertex_normals<<<dim3((V + 255) / 256, ni), 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, V, F,
-                                                             ctx->normals, ctx->normal_len, ctx->status);
+                                                             ctx->normals, ctx->normal_len, ctx->status, ctx->active);
   HR_CHECK_LAUNCH();
   ctx->V = V;
   ctx->F = F;
@@ -689,11 +691,11 @@ int launch_update_bvh(Context* ctx, const hr_model* m, const float* verts, const
   }
   k_build_bvh<<<ctx->n_inst, kBuildThreads, smem, s>>>(verts, m->faces, F, V, P, ctx->lim.max_F, snodes,
                                                        ctx->nodes, ctx->tris, ctx->bvh_parent, ctx->bvh_valid,
-                                                       iter_dev, rebuild_every, ctx->status);
+                                                       iter_dev, rebuild_every, ctx->status, ctx->active);
   HR_CHECK_LAUNCH();
   k_vertex_normals<<<dim3((V + 255) / 256, ctx->n_inst), 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces,
                                                                       V, F, ctx->normals, ctx->normal_len,
-                                                                      ctx->status);
+                                                                      ctx->status, ctx->active);
   HR_CHECK_LAUNCH();
   ctx->V = V;
   ctx->F = F;

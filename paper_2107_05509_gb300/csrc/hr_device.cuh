@@ -72,6 +72,8 @@ struct Context {
   int max_ne;            // largest edge-sample count of a view
   bool loss_vec;         // every instance's first pixel is a multiple of 4
   ViewRec* vt;           // device [nviews]
+  const int* active;     // device [n_inst] of a batch: instances with 0 are skipped, or
+                         // NULL (every instance); hr_batch_set_active
   InstRec* it;           // device [n_inst]
   ViewRec* hvt;          // host copies
   InstRec* hit;

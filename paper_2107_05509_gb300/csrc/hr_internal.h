@@ -42,6 +42,10 @@ int launch_adam(float* p, const float* g, float* m, float* v, int n, float lr, f
                 int step, cudaStream_t s);
 int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2, float eps,
                     const float* lr_scale, int scale_len, uint32_t* iter_dev, cudaStream_t s);
+int launch_retire_converged(const float* err, const uint32_t* iter_dev, int rows, int n, float thr, int* active,
+                            float* lr_scale, int per, cudaStream_t s);
+int launch_retire_plateau(const float* loss, int n, float rel_tol, int patience, float* best, int* stall, int* active,
+                          float* lr_scale, int per, cudaStream_t s);
 int launch_vertex_mse(const float* a, const float* b, int V, int n, float* loss, float* grad, cudaStream_t s);
 int launch_add_noise(float* img, long long n, float sigma, uint64_t seed, cudaStream_t s);
 int launch_select_best(const float* cand, const float* losses, int K, int n, float* out, int* chosen,

@@ -58,9 +58,10 @@ __device__ __forceinline__ void inst_range(const InstRec* it, long long P, long 
 __global__ void __launch_bounds__(kLossThreads) k_mask_count(const uint8_t* __restrict__ mask_all,
                                                              const InstRec* __restrict__ it, long long P,
                                                              float* __restrict__ scratch_all, int lstride,
-                                                             unsigned* counters_all) {
+                                                             unsigned* counters_all, const int* __restrict__ active) {
   __shared__ unsigned long long red[32];
   __shared__ bool last;
+  if (active && !active[blockIdx.y]) return;   // a retired instance of a batch
   long long p0, n;
   inst_range(it, P, p0, n);
   const uint8_t* mask = mask_all + p0;
@@ -100,9 +101,11 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_adjoint(const float* __re
                                                                float* __restrict__ scratch_all, int lstride,
                                                                unsigned* counters_all,
                                                                float* __restrict__ adjoint_all,
-                                                               float* __restrict__ loss_all, bool vec) {
+                                                               float* __restrict__ loss_all, bool vec,
+                                                               const int* __restrict__ active) {
   __shared__ float red[32];
   __shared__ bool last;
+  if (active && !active[blockIdx.y]) return;   // a retired instance of a batch
   long long p0;
   inst_range(it, P, p0, P);
   const float* image = image_all + 3 * p0;
@@ -221,6 +224,41 @@ __global__ void k_adam_dev(float* __restrict__ p, const float* __restrict__ g, f
 }
 
 __global__ void k_counter_advance(uint32_t* iter_dev) { *iter_dev += 1u; }
+
+// retire an instance of a batch: it is skipped from now on, and the Adam step sizes
+// of its `per` parameters are zeroed so that its estimate stays where it is
+__device__ __forceinline__ void retire(int i, int* active, float* lr_scale, int per) {
+  active[i] = 0;
+  if (lr_scale)
+    for (int j = 0; j < per; ++j) lr_scale[(size_t)i * per + j] = 0.0f;
+}
+
+// instances whose error in the current row (err[*iter_dev][i]) is at most `thr`
+__global__ void k_retire_converged(const float* __restrict__ err, const uint32_t* iter_dev, int rows, int n,
+                                   float thr, int* __restrict__ active, float* __restrict__ lr_scale, int per) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !active[i]) return;
+  const unsigned row = iter_dev ? *iter_dev : 0u;
+  if (row >= (unsigned)rows) return;
+  const float e = err[(size_t)row * n + i];
+  if (e <= thr) retire(i, active, lr_scale, per);
+}
+
+// instances whose loss has not fallen below (1 - rel_tol) x its best for `patience`
+// calls in a row
+__global__ void k_retire_plateau(const float* __restrict__ loss, int n, float rel_tol, int patience,
+                                 float* __restrict__ best, int* __restrict__ stall, int* __restrict__ active,
+                                 float* __restrict__ lr_scale, int per) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !active[i]) return;
+  const float l = loss[i];
+  if (l < best[i] * (1.0f - rel_tol)) {
+    best[i] = l;
+    stall[i] = 0;
+  } else if (++stall[i] >= patience) {
+    retire(i, active, lr_scale, per);
+  }
+}
 
 // epsilon_v of instance blockIdx.x: mean over vertices of |verts - ref| (metres),
 // summed in a fixed order, into out[row][instance] with row = *iter_dev (row 0 when
@@ -454,6 +492,20 @@ int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float l
   return HR_OK;
 }
 
+int launch_retire_converged(const float* err, const uint32_t* iter_dev, int rows, int n, float thr, int* active,
+                            float* lr_scale, int per, cudaStream_t s) {
+  k_retire_converged<<<(n + 127) / 128, 128, 0, s>>>(err, iter_dev, rows, n, thr, active, lr_scale, per);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_retire_plateau(const float* loss, int n, float rel_tol, int patience, float* best, int* stall, int* active,
+                          float* lr_scale, int per, cudaStream_t s) {
+  k_retire_plateau<<<(n + 127) / 128, 128, 0, s>>>(loss, n, rel_tol, patience, best, stall, active, lr_scale, per);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
 int launch_vertex_mse(const float* a, const float* b, int V, int n, float* loss, float* grad, cudaStream_t s) {
   k_vertex_mse<<<n, kErrThreads, 0, s>>>(a, b, V, loss, grad);
   HR_CHECK_LAUNCH();
@@ -522,10 +574,11 @@ int launch_loss(Context* ctx, const float* image, const float* obs, const uint8_
   const int lstride = kLossStride(ctx->loss_blocks);
   const dim3 grid(blocks, ctx->vt ? ctx->n_inst : 1);
   const InstRec* it = ctx->vt ? ctx->it : nullptr;
-  k_mask_count<<<grid, kLossThreads, 0, s>>>(mask, it, P, ctx->loss_partials, lstride, ctx->counters);
+  k_mask_count<<<grid, kLossThreads, 0, s>>>(mask, it, P, ctx->loss_partials, lstride, ctx->counters,
+                                             ctx->vt ? ctx->active : nullptr);
   HR_CHECK_LAUNCH();
   k_loss_adjoint<<<grid, kLossThreads, 0, s>>>(image, obs, mask, it, P, ctx->loss_partials, lstride, ctx->counters,
-                                               adjoint, loss, vec);
+                                               adjoint, loss, vec, ctx->vt ? ctx->active : nullptr);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -536,7 +589,8 @@ int launch_loss_ct(Context* ctx, const float* image, const float* obs, const uin
   const long long want = (P + kLossThreads - 1) / kLossThreads;
   const int blocks = (int)(want < kLossBlocks ? (want > 0 ? want : 1) : kLossBlocks);
   float* scale = ctx->loss_partials + 3 * blocks;   // where k_mask_count leaves 1 / (3 sum M)
-  k_mask_count<<<dim3(blocks, 1), kLossThreads, 0, s>>>(mask, nullptr, P, ctx->loss_partials, 0, ctx->counters);
+  k_mask_count<<<dim3(blocks, 1), kLossThreads, 0, s>>>(mask, nullptr, P, ctx->loss_partials, 0, ctx->counters,
+                                                        nullptr);
   HR_CHECK_LAUNCH();
   k_loss_ct<<<dim3(kCtBlocks, N), kLossThreads, 0, s>>>(image, obs, mask, T, HW, scale, adjoint, ctx->ct_partials);
   HR_CHECK_LAUNCH();

@@ -221,6 +221,7 @@ struct RenderArgs {
   int N, H, W, spp, V;     // uniform layout (single instance)
   const ViewRec* vt;       // batch view table, nullptr = uniform layout
   const InstRec* it;       // batch instance table
+  const int* active;       // batch: instances with 0 are skipped (retired), or null
   int n_inst, nviews, total_st;
   int node_stride;
   int cand_per_chunk, max_chunks;   // work-item split (tuning)
@@ -320,6 +321,11 @@ __device__ __forceinline__ RenderArgs for_inst(RenderArgs a, int inst) {
   a.verts += (size_t)inst * 3 * a.V;
   a.normals += (size_t)inst * 3 * a.V;
   return a;
+}
+
+// a batch instance still being refined (hr_batch_set_active)
+__device__ __forceinline__ bool inst_active(const RenderArgs& a, int inst) {
+  return !a.active || __ldg(&a.active[inst]) != 0;
 }
 
 // work-item region of an instance
@@ -1005,6 +1011,10 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
     if (st >= total) break;
     const SubTile t = subtile(a0, st);
     if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
+    if (!inst_active(a0, t.inst)) {   // a retired instance: nothing to render
+      if (lane == 0) a0.wk.st[st] = make_int2(0, 0);
+      continue;
+    }
     const RenderArgs a = for_inst(a0, t.inst);
     bool live = true;
     float3 g = make_float3(0.0f, 0.0f, 0.0f);
@@ -1115,7 +1125,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, c
   for (int st = blockIdx.x * kWarps + (threadIdx.x >> 5); st < total; st += nw) {
     int2 pk = a0.wk.st[st];
     const SubTile t = subtile(a0, st);
-    if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
+    if (!in_range(a0.status, t.inst, 0, a0.n_inst) || !inst_active(a0, t.inst)) continue;
     const RenderArgs a = for_inst(a0, t.inst);
     bool live;
     const float3 g = lane_adjoint(a, t, adjoint, live);
@@ -1429,10 +1439,12 @@ __global__ void __launch_bounds__(kRedEntries * kRedGroups) k_reduce_partials(
 __global__ void k_silhouettes(const float* __restrict__ verts_all, const int* __restrict__ faces,
                               const int* __restrict__ edges, const int* __restrict__ edge_faces, int E,
                               const Cam* __restrict__ cams, const ViewRec* __restrict__ vt, int V,
-                              int* __restrict__ lists, int stride, int* __restrict__ counts) {
+                              int* __restrict__ lists, int stride, int* __restrict__ counts,
+                              const int* __restrict__ active) {
   __shared__ int warp_tot[32];
   __shared__ int base;
   const int view = blockIdx.x;
+  if (vt && active && !active[__ldg(&vt[view].inst)]) return;   // a retired instance
   const float* verts = verts_all + (vt ? (size_t)__ldg(&vt[view].inst) * 3 * V : 0);
   Cam cam = load_cam(cams, view);
   float3 c = make_float3(cam.c[0], cam.c[1], cam.c[2]);
@@ -1544,7 +1556,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in
   if (active) {
     view_info(a0, view, vw, st0, nsx);
     const int Ne = a0.vt ? __ldg(&a0.vt[view].ne) : Ne_max;
-    active = k < Ne && in_range(a0.status, vw.inst, 0, a0.n_inst);
+    active = k < Ne && in_range(a0.status, vw.inst, 0, a0.n_inst) && inst_active(a0, vw.inst);
     if (active) {
       a = for_inst(a0, vw.inst);
       d_verts = d_verts_all + (size_t)vw.inst * inst_stride;
@@ -1701,9 +1713,10 @@ __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in
 
 // dm_v = (I - n n^T) dN_v / |m_v|; blockIdx.y selects the instance
 __global__ void k_normal_dm(const float* __restrict__ normals_all, const float* __restrict__ normal_len_all,
-                            const float* __restrict__ dN_all, int V, float* __restrict__ dm_all) {
+                            const float* __restrict__ dN_all, int V, float* __restrict__ dm_all,
+                            const int* __restrict__ active) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V) return;
+  if (v >= V || (active && !active[blockIdx.y])) return;
   const size_t o = (size_t)blockIdx.y * V;
   const float *normals = normals_all + 3 * o, *normal_len = normal_len_all + o, *dN = dN_all + 3 * o;
   float* dm = dm_all + 3 * o;
@@ -1726,9 +1739,9 @@ __global__ void k_normal_dm(const float* __restrict__ normals_all, const float* 
 __global__ void k_normal_gather(const float* __restrict__ verts_all, const int* __restrict__ faces,
                                 const int* __restrict__ vf_off, const int* __restrict__ vf_faces,
                                 const float* __restrict__ dm_all, int V, const float* __restrict__ dedge_all,
-                                float* __restrict__ d_verts_all) {
+                                float* __restrict__ d_verts_all, const int* __restrict__ active) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V) return;
+  if (v >= V || (active && !active[blockIdx.y])) return;
   const size_t o = (size_t)blockIdx.y * 3 * V;
   const float *verts = verts_all + o, *dm = dm_all + o;
   float* d_verts = d_verts_all + o;
@@ -1838,6 +1851,7 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.tex_w = o->tex_w;
   a.tex_h = o->tex_h;
   a.d_tex = a.tex ? o->d_texture : nullptr;
+  a.active = ctx->vt ? ctx->active : nullptr;
   if (ctx->vt) {
     a.vt = ctx->vt;
     a.it = ctx->it;
@@ -1916,7 +1930,7 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
 int launch_silhouettes(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int* lists,
                        int list_stride, int* counts, cudaStream_t s) {
   k_silhouettes<<<N, 512, 0, s>>>(verts, m->faces, m->edges, m->edge_faces, m->E, cams, ctx->vt, m->V, lists,
-                                  list_stride, counts);
+                                  list_stride, counts, ctx->vt ? ctx->active : nullptr);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -2060,10 +2074,11 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
   if (normals) {
     tm.begin(kTimeBwdNormals);
     const dim3 g((V + 255) / 256, ni);
-    k_normal_dm<<<g, 256, 0, s>>>(ctx->normals, ctx->normal_len, ctx->dN, V, ctx->dm);
+    const int* act = batch ? ctx->active : nullptr;
+    k_normal_dm<<<g, 256, 0, s>>>(ctx->normals, ctx->normal_len, ctx->dN, V, ctx->dm, act);
     HR_CHECK_LAUNCH();
     k_normal_gather<<<g, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, ctx->dm, V,
-                                      edges && !det ? ctx->dedge : nullptr, d_verts);
+                                      edges && !det ? ctx->dedge : nullptr, d_verts, act);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdNormals);
   } else if (edges && !det) {

@@ -221,8 +221,9 @@ __device__ __forceinline__ float3 shaped_vertex(const ModelArgs& m, const Chain&
 // translation, [J][3]) when `joints_all` is given
 __global__ void __launch_bounds__(kSkinThreads) k_skin(ModelArgs m, const float* __restrict__ params_all,
                                                        float* __restrict__ verts_all, float* __restrict__ joints_all,
-                                                       int* status) {
+                                                       int* status, const int* __restrict__ active) {
   __shared__ Chain ch;
+  if (active && !active[blockIdx.y]) return;   // a retired instance of a batch
   const float* params = params_all + (size_t)blockIdx.y * 61;
   float* verts = verts_all + (size_t)blockIdx.y * 3 * m.V;
   build_chain(m, params, ch, status);
@@ -258,8 +259,9 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const fl
                                                            const float* __restrict__ djoints_all,
                                                            float* __restrict__ partials_all, unsigned* counter_all,
                                                            int cstride, float* __restrict__ dparams_all,
-                                                           int* status) {
+                                                           int* status, const int* __restrict__ active) {
   __shared__ Chain ch;
+  if (active && !active[blockIdx.y]) return;   // a retired instance of a batch
   const float* params = params_all + (size_t)blockIdx.y * 61;
   const float* dverts = dverts_all + (size_t)blockIdx.y * 3 * m.V;
   float* partials = partials_all + (size_t)blockIdx.y * kSkinBlocks * kSkinAcc;
@@ -478,7 +480,8 @@ ModelArgs model_args(const hr_model* m) {
 
 int launch_skin(Context* ctx, const hr_model* m, const float* params, float* verts, float* joints, cudaStream_t s) {
   int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
-  k_skin<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, verts, joints, ctx->status);
+  k_skin<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, verts, joints, ctx->status,
+                                                            ctx->active);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -489,7 +492,7 @@ int launch_skin_bwd(Context* ctx, const hr_model* m, const float* params, const 
   if (blocks > kSkinBlocks) blocks = kSkinBlocks;
   k_skin_bwd<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, d_verts, d_joints,
                                                                 ctx->skin_partials, ctx->counters + 2, 4, d_params,
-                                                                ctx->status);
+                                                                ctx->status, ctx->active);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -578,7 +581,7 @@ extern "C" int hr_skin_bwd_noalloc(const hr_model* m, const float* params, const
   }
   int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
   k_skin_bwd<<<blocks, kSkinThreads, 0, s>>>(model_args(m), params, d_verts, nullptr, partials, counter, 0, d_params,
-                                             status);
+                                             status, nullptr);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }

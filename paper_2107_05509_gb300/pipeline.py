@@ -359,12 +359,25 @@ class BatchRefiner:
     hr_skin_batch -> hr_update_bvh -> hr_render_fwd_batch -> hr_loss_batch ->
     hr_render_bwd_batch -> hr_skin_bwd_batch -> hr_adam_step_dev, plus (with ground
     truth vertices) hr_vertex_error into the error table: a fixed sequence of launches
-    over all instances that capture() records once as a CUDA graph."""
+    over all instances that capture() records once as a CUDA graph.
+
+    retire: None (every instance refined every iteration), "converged" (an instance
+    leaves the batch once its vertex error is <= retire_mm; needs ref_verts: the
+    benchmark's per-instance criterion) or "plateau" (an instance leaves once its loss
+    has not fallen by rel_tol for `patience` iterations).  A retired instance is
+    skipped by every batch kernel and its Adam steps are zeroed, on the device, so the
+    captured iteration gets cheaper as instances converge."""
 
     def __init__(self, model: B.Model, batch: B.Batch, views: BatchViews, seed=17, lr=1.0, lr_groups=LR_GROUPS,
-                 ref_verts=None, max_iters=1024, device="cuda"):
+                 ref_verts=None, max_iters=1024, device="cuda", retire=None, retire_mm=1.0, rel_tol=1e-3,
+                 patience=10):
         self.model, self.batch, self.views = model, batch, views
         n, V, P = batch.n, model.V, batch.total_pixels
+        if retire not in (None, "converged", "plateau"):
+            raise ValueError(f"retire: {retire}")
+        if retire == "converged" and ref_verts is None:
+            raise ValueError("retire='converged' needs the ground-truth vertices")
+        self.retire, self.retire_m, self.rel_tol, self.patience = retire, retire_mm * 1e-3, rel_tol, patience
         self.counter = torch.zeros(1, dtype=torch.int32, device=device)
         self.opts = B.render_opts(seed=seed, ka=I.K_AMBIENT, kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR,
                                   light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX, iter_dev=self.counter,
@@ -379,7 +392,15 @@ class BatchRefiner:
         self.m1 = torch.zeros_like(self.params)
         self.m2 = torch.zeros_like(self.params)
         self.lr = float(lr)
-        self.lr_scale = lr_scale_vector(lr_groups, device)
+        # per-entry steps [n][61] (the groups' steps repeated): retiring an instance
+        # zeroes its row
+        self.lr_scale0 = lr_scale_vector(lr_groups, device).repeat(n)
+        self.lr_scale = self.lr_scale0.clone()
+        self.active = torch.ones(n, dtype=torch.int32, device=device)
+        self.best = torch.full((n,), float("inf"), device=device)
+        self.stall = torch.zeros(n, dtype=torch.int32, device=device)
+        B.hr_batch_set_active(batch, self.active)
+        batch.active_mask = self.active   # the context reads it for as long as it lives
         self.ref_verts = ref_verts
         self.err = torch.full((max_iters, n), float("nan"), device=device)
         self.graph = None
@@ -390,15 +411,28 @@ class BatchRefiner:
         self.m2.zero_()
         self.counter.zero_()
         self.err.fill_(float("nan"))
+        self.active.fill_(1)
+        self.lr_scale.copy_(self.lr_scale0)
+        self.best.fill_(float("inf"))
+        self.stall.zero_()
 
     def iteration(self, stream=None):
         bt, m, v = self.batch, self.model, self.views
+        # the batch calls read this refiner's mask (the context may be shared with
+        # another refiner; a captured iteration keeps the pointer given here)
+        B.hr_batch_set_active(bt, self.active)
+        bt.active_mask = self.active
         B.hr_skin_batch(bt, m, self.params, self.verts, stream)
         if self.ref_verts is not None:
             B.hr_vertex_error(self.verts, self.ref_verts, self.err, self.counter, stream)
+            if self.retire == "converged":
+                B.hr_retire_converged(self.err, self.counter, self.retire_m, self.active, self.lr_scale, stream)
         B.hr_update_bvh(bt, m, self.verts, self.counter, REBUILD_EVERY, stream)
         B.hr_render_fwd_batch(bt, m, self.verts, v.cams, v.background, self.opts, self.image, stream)
         B.hr_loss_batch(bt, self.image, v.observed, v.mask, self.loss, self.adjoint, stream)
+        if self.retire == "plateau":
+            B.hr_retire_plateau(self.loss, self.rel_tol, self.patience, self.best, self.stall, self.active,
+                                self.lr_scale, stream)
         B.hr_render_bwd_batch(bt, m, self.verts, v.cams, v.background, self.opts, self.adjoint, self.d_verts, stream)
         B.hr_skin_bwd_batch(bt, m, self.params, self.d_verts, self.d_params, stream)
         B.hr_adam_step_dev(self.params, self.d_params, self.m1, self.m2, self.lr, 0.9, 0.999, 1e-8, self.counter,
@@ -408,6 +442,8 @@ class BatchRefiner:
         """Forward and backward of the current parameters without an update (what the
         autotuner times)."""
         bt, m, v = self.batch, self.model, self.views
+        B.hr_batch_set_active(bt, self.active)
+        bt.active_mask = self.active
         B.hr_skin_batch(bt, m, self.params, self.verts, stream)
         B.hr_build_bvh_batch(bt, m, self.verts, stream)
         B.hr_render_fwd_batch(bt, m, self.verts, v.cams, v.background, self.opts, self.image, stream)
@@ -419,7 +455,10 @@ class BatchRefiner:
         a process load the kernels)."""
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
-        saved = (self.params.clone(), self.m1.clone(), self.m2.clone(), self.counter.clone())
+        # the warm-up iteration's effects are undone afterwards (retirement state too)
+        names = ("params", "m1", "m2", "counter", "active", "lr_scale", "best", "stall")
+        state = [getattr(self, k) for k in names if hasattr(self, k)]
+        saved = [t.clone() for t in state]
         with torch.cuda.stream(s):
             self.iteration(s)
         torch.cuda.current_stream().wait_stream(s)
@@ -427,10 +466,8 @@ class BatchRefiner:
         with torch.cuda.graph(g, stream=s):
             self.iteration(s)
         self.graph = g
-        self.params.copy_(saved[0])
-        self.m1.copy_(saved[1])
-        self.m2.copy_(saved[2])
-        self.counter.copy_(saved[3])
+        for t, v in zip(state, saved):
+            t.copy_(v)
         return g
 
 

@@ -220,6 +220,8 @@ class Proposer:
     def run(self, stream=None):
         r = self.r
         bt, m, v = r.batch, r.model, r.views
+        B.hr_batch_set_active(bt, r.active)
+        bt.active_mask = r.active
         self.cand[0].copy_(r.params)
         for k in range(self.steps + 1):
             x = self.cand[k]

@@ -197,3 +197,81 @@ def test_vertex_error_matches_oracle(setup):
     for k in range(n):
         assert abs(got[2, k] * 1e3 - oracle.vertex_error_mm(a[k], b[k])) <= 1e-5 * oracle.vertex_error_mm(a[k], b[k])
     assert (got[[0, 1, 3]] == -1.0).all()   # only row *iter_dev is written
+
+
+def test_retired_instance_is_skipped_and_the_rest_unchanged(setup):
+    """hr_batch_set_active: a retired instance (mask 0) is skipped by every batch call
+    -- its vertices, image, loss and parameter gradient keep the values they had --
+    while the active instances get exactly what an all-active call gives them."""
+    B, h, insts, bt, model = setup
+    n = len(insts)
+    params = _t(np.stack([i.x for i in insts]))
+    cams = _t(_cat([i.cams for i in insts], (I.CAM_FLOATS,)))
+    bg = _t(_cat([i.bg for i in insts], (3,)))
+    obs = _t(_cat([i.observed for i in insts], (3,)))
+    mask = _t(np.concatenate([i.mask.reshape(-1) for i in insts]))
+    P = bt.total_pixels
+    po = bt.pixel_offsets
+    go = _gopts(B, insts[0].opts, B.HR_DETERMINISTIC)
+
+    def run(sentinel):
+        verts = torch.full((n, h.V, 3), sentinel, device="cuda")
+        img = torch.full((P, 3), sentinel, device="cuda")
+        adj = torch.empty((P, 3), device="cuda")
+        loss = torch.full((n,), sentinel, device="cuda")
+        dv = torch.empty((n, h.V, 3), device="cuda")
+        dp = torch.full((n, 61), sentinel, device="cuda")
+        B.hr_skin_batch(bt, model, params, verts)
+        B.hr_build_bvh_batch(bt, model, verts)
+        B.hr_render_fwd_batch(bt, model, verts, cams, bg, go, img)
+        B.hr_loss_batch(bt, img, obs, mask, loss, adj)
+        B.hr_render_bwd_batch(bt, model, verts, cams, bg, go, adj, dv)
+        B.hr_skin_bwd_batch(bt, model, params, dv, dp)
+        return [t.cpu().numpy() for t in (verts, img, loss, dp)]
+
+    B.hr_batch_set_active(bt, None)
+    full = run(0.0)
+    active = torch.tensor([1, 0, 1], dtype=torch.int32, device="cuda")
+    B.hr_batch_set_active(bt, active)
+    part = run(-7.0)
+    B.hr_batch_set_active(bt, None)
+    verts_f, img_f, loss_f, dp_f = full
+    verts_p, img_p, loss_p, dp_p = part
+    for k in (0, 2):
+        assert np.array_equal(verts_p[k], verts_f[k])
+        assert np.array_equal(img_p[po[k]:po[k + 1]], img_f[po[k]:po[k + 1]])
+        assert loss_p[k] == loss_f[k]
+        assert np.array_equal(dp_p[k], dp_f[k])    # fixed-point sums: order-free
+    assert (verts_p[1] == -7.0).all() and (img_p[po[1]:po[2]] == -7.0).all()
+    assert loss_p[1] == -7.0 and (dp_p[1] == -7.0).all()
+    assert B.hr_get_status(bt) == B.HR_OK
+
+
+def test_retire_converged_and_plateau_kernels(setup):
+    B = setup[0]
+    n = 5
+    err = torch.tensor([[5e-3, 2e-3, 9e-4, 1e-3, 3e-3], [1e-4, 1e-4, 1e-4, 1e-4, 1e-4]], device="cuda")
+    ctr = torch.zeros(1, dtype=torch.int32, device="cuda")
+    active = torch.ones(n, dtype=torch.int32, device="cuda")
+    scale = torch.ones((n, 61), device="cuda")
+    B.hr_retire_converged(err, ctr, 1e-3, active, scale)
+    # row 0: instances 2 and 3 are at or below 1 mm
+    assert active.tolist() == [1, 1, 0, 0, 1]
+    sc = scale.cpu().numpy()
+    assert (sc[[2, 3]] == 0).all() and (sc[[0, 1, 4]] == 1).all()
+    # the plateau rule: retire after `patience` calls without a relative improvement
+    loss = torch.tensor([1.0, 1.0, 1.0, 1.0, 1.0], device="cuda")
+    best = torch.full((n,), float("inf"), device="cuda")
+    stall = torch.zeros(n, dtype=torch.int32, device="cuda")
+    active.fill_(1)
+    seq = [[1.0, 1.0, 1.0, 1.0, 1.0], [0.9, 1.0, 0.9995, 1.0, 0.5], [0.8, 1.0, 0.9993, 0.95, 0.4],
+           [0.7, 1.0, 0.9992, 0.95, 0.3]]
+    for row in seq:
+        loss.copy_(torch.tensor(row, device="cuda"))
+        B.hr_retire_plateau(loss, 1e-3, 3, best, stall, active)
+    # instance 1 never improves and instance 2 by less than 0.1 % of its best: three
+    # stalls each after the first call; instance 3 improves once (a reset), then stalls
+    # twice; instances 0 and 4 keep improving
+    assert active.tolist() == [1, 0, 0, 1, 1]
+    assert stall.tolist()[3] == 1
+    assert B.hr_get_status(setup[3]) == B.HR_OK
