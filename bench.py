@@ -44,8 +44,8 @@ sys.path.insert(0, ROOT)
 METRIC = "render fwd+bwd Mrays/s"
 UNIT = "Mrays/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 FMA peak of a GB300: 152 SMs x 128 lanes x 2 flop x clock
-N_SM, LANES = 152, 128
+# FP32 FMA peak: SMs (read from the device) x 128 FP32 lanes x 2 flop x clock
+LANES = 128
 # modelled FP32 work: per ray made (jitter, screen point, direction), per BVH node
 # visited (two child boxes against a sub-tile frustum or a ray), per candidate
 # screen-box test, per Moller-Trumbore test, per shaded hit (forward) or
@@ -55,17 +55,38 @@ S_SAMPLES, S_RAYS, S_NODES, S_TRIS, S_HITS, S_CANDS = range(6)
 FLOP_TRACE_NODE, FLOP_EDGE = 40, 120   # per-ray traversal node (two slab tests); edge-sample set-up
 KERNEL_NAMES = {"fwd_gather": "k_gather<fwd>", "fwd_shade": "k_shade_fwd", "bwd_gather": "k_items_bwd",
                 "bwd_shade": "k_shade_bwd", "edge_samples": "k_edge_samples"}
-# DRAM bytes (read + write) per launch from the ncu capture summarised under profiles/
-# (None once the kernel has changed since that capture)
-NCU_TRAFFIC = {"k_shade_bwd": 3819264, "k_shade_fwd": 2507264, "k_gather<fwd>": 17721344,
-               "k_items_bwd": 19277312, "k_edge_samples": 2993152}
+# DRAM bytes (read + write) per launch from the ncu capture summarised under profiles/,
+# with the hash of the render kernels' sources at that capture: a kernel whose source
+# has changed since reports no traffic
+NCU_TRAFFIC = {}
+NCU_TRAFFIC_SOURCES = ("paper_2107_05509_gb300/csrc/hr_render.cu", "paper_2107_05509_gb300/csrc/hr_device.cuh")
+
+
+def render_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in NCU_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """(bytes per launch, note) of the committed capture, or (None, why)."""
+    rec = NCU_TRAFFIC.get(kernel)
+    if rec is None:
+        return None, "no capture of this kernel"
+    nbytes, src = rec
+    if src != render_source_hash():
+        return None, "the kernel source changed since the capture"
+    return nbytes, f"ncu dram__bytes_read.sum + dram__bytes_write.sum, sources {src}"
 # kernels of one step: skin 1, BVH + normals 2, forward 4 (gather, shade, overflow,
 # combine), loss 2, backward 8 (items, shade, overflow, reduce, silhouettes, edge
 # samples, normal adjoint 2), skin adjoint 1, Adam 1
 LAUNCHES_PER_STEP = 19
-# a batched iteration: the same kernels (one launch each over all instances) plus the
-# vertex-error kernel
-LAUNCHES_BATCH_ITER = 20
+# a batched iteration: the same kernels (one launch each over all instances), the
+# vertex-error kernel and the active-instance layout before the forward and backward
+LAUNCHES_BATCH_ITER = 22
 
 
 def env_rank():
@@ -102,7 +123,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
@@ -114,7 +135,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -260,7 +281,14 @@ def run_handrt(args):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        time.sleep(0.4)                  # let the sampler start before the timed region
+        # the same replays for ~0.5 s before the timed region: the sampler starts and
+        # records the clocks under this load (the timed region itself lasts only
+        # steps x ~0.5 ms)
+        t_end = time.time() + 0.5
+        while time.time() < t_end:
+            for _ in range(50):
+                graph.replay()
+            torch.cuda.synchronize()
         for k in range(args.steps):
             flush.fill_(float(k))        # evict L2 between timed steps (outside the events)
             ev[k][0].record(stream)
@@ -379,7 +407,8 @@ def run_handrt(args):
     stage_ms = dict(zip(stages, st.mean(0).round(4).tolist()))
     pk, pk_kind = peaks()
     clocks = clk.summary()
-    fp32_peak = N_SM * LANES * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * LANES * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     fwd_row, bwd_row, edge_row = stats
     kflops = {
         "fwd_gather": FLOP_NODE * fwd_row[S_NODES],
@@ -394,18 +423,20 @@ def run_handrt(args):
     dom = max((k for k in kflops if k in kt_mean), key=lambda k: kt_mean[k])
     achieved = kflops[dom] / (kt_mean[dom] * 1e-3) / 1e12
     kernel_name = KERNEL_NAMES[dom]
+    traffic, traffic_note = ncu_traffic(kernel_name)
     roof = {"bound": "alu", "kernel": kernel_name, "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
-            "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": NCU_TRAFFIC.get(kernel_name),
+            "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4), "traffic": traffic,
+            "traffic_note": traffic_note,
             "launch_ms": round(kt_mean[dom], 4), "flops_per_launch": float(kflops[dom]),
-            "peak_note": f"FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x {pk.get('sm_max_mhz', 2070.0):.0f} MHz "
-                         f"(max SM clock, {pk_kind} clock data)",
+            "peak_note": f"FP32 FMA peak: {n_sm} SMs (cudaDevAttrMultiProcessorCount) x {LANES} lanes x 2 flop x "
+                         f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz (max SM clock, {pk_kind} clock data)",
             "flop_model": f"{FLOP_RAY}/ray made + {FLOP_CAND}/candidate box test + {FLOP_TRI}/Moller-Trumbore "
                           f"test + {FLOP_HIT}/shaded hit or {FLOP_HIT_GRAD}/differentiated hit; "
                           f"{FLOP_NODE}/frustum node visit",
             "kernel_ms": {k: round(v, 4) for k, v in kt_mean.items()},
             "frac_at_load_clock": None}
     if clocks:
-        roof["frac_at_load_clock"] = round(achieved / (N_SM * LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12), 4)
+        roof["frac_at_load_clock"] = round(achieved / (n_sm * LANES * 2 * clocks["sm_mhz"] * 1e6 / 1e12), 4)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -425,13 +456,17 @@ def run_handrt(args):
                    "parallelism": f"{world} independent instance(s), one per GPU"},
         "e2e": {"value": round(job_value(rays_step, world, e2e_ms), 3), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_ms, 4),
-                "api": "StreamedRefiner (copy of step k+1 overlaps step k)",
+                "api": "StreamedRefiner (copy of step k+1 overlaps step k): the public Python API; the C-ABI "
+                       "calls take device pointers, the host copies are pinned-memory torch copies on a copy stream",
                 "serial_ms_per_step": round(serial_ms, 4)},
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "roofline": roof,
         "clocks": clocks,
     }
+    if clocks:
+        clocks["window"] = "0.5 s of the same graph replays right before the timed region, then the timed region"
     if not args.no_refine and world == 1:
+        line["paper_refinement"] = run_paper_refinement(dev)
         line["refinement"] = run_refinement(args, dev)
         line["tensor"] = run_tensor(dev)
         line["scale"] = run_scale(dev)
@@ -654,6 +689,47 @@ def run_refinement(args, dev):
                          "(plain: every instance refined that many iterations, one after another); "
                          "time_to_each_1mm: until every instance has been <= 1 mm (plain: per-instance "
                          "stopping), iteration cap counted for instances that never get there"}
+
+
+def run_paper_refinement(dev, iters=300):
+    """The paper-shaped workload refined as a plain Adam loop of 300 iterations from
+    the perturbed estimate (each iteration one replay of the captured step, per-group
+    step sizes), epsilon_v (Section 4.1) recorded on the device every iteration."""
+    import torch
+
+    from paper_2107_05509_gb300 import binding as B
+    from paper_2107_05509_gb300 import inputs as I
+    from paper_2107_05509_gb300 import pipeline as P
+
+    cfg = I.PAPER
+    hand = I.make_hand(0)
+    model = B.Model(hand, device=dev)
+    x_gt = I.gt_params(cfg.seed)
+    views, v_gt = P.make_views(cfg, model, x_gt, device=dev)
+    x0 = torch.as_tensor(I.perturb_params(x_gt, cfg.seed), device=dev)
+    pr = P.PlainRefiner(model, views, cfg, ref_verts=v_gt, max_iters=iters + 8, device=dev)
+    pr.reset(x0)
+    g = pr.capture()
+    pr.reset(x0)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 1)]
+    ev[0].record()
+    for k in range(iters):
+        g.replay()
+        ev[k + 1].record()
+    torch.cuda.synchronize()
+    dt = np.array([ev[k].elapsed_time(ev[k + 1]) for k in range(iters)])
+    err = pr.err[:iters, 0].cpu().numpy() * 1e3
+    if B.hr_get_status(pr.r.ctx) != B.HR_OK:
+        raise RuntimeError("paper refinement device status")
+    k1 = _first_at_or_below(err)
+    pr.r.ctx.close()
+    return {"workload": f"{cfg.name}, {iters} Adam iterations from the perturbed estimate",
+            "eps_v_mm": {str(i): round(float(err[i]), 4) for i in list(range(0, iters, 25)) + [iters - 1]},
+            "iters_to_1mm": k1, "time_to_1mm_ms": round(float(dt[:k1 + 1].sum()), 2) if k1 >= 0 else None,
+            "ms_per_iter": round(float(np.median(dt)), 4), "total_ms": round(float(dt.sum()), 2),
+            "adam_lr_per_group": {"shape": P.LR_GROUPS[0], "pose_rad": P.LR_GROUPS[1],
+                                  "root_rot_rad": P.LR_GROUPS[2], "trans_m": P.LR_GROUPS[3]}}
 
 
 def run_scale(dev, iters=10):

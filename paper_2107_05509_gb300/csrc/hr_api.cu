@@ -45,7 +45,7 @@ void free_ctx(Context* c) {
                   c->status,  c->stats,   c->pool_bb,   c->pool_z,     c->pool_rec,      c->st_info,
                   c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it,
                   c->bvh_parent, c->bvh_valid, c->bvh_keys, c->bvh_flags, c->bvh_bounds, c->bvh_bad,
-                  c->bvh_mode, c->extra64, c->ct_partials, c->dedge, c->ovf_list, c->acc_fx};
+                  c->bvh_mode, c->extra64, c->ct_partials, c->dedge, c->ovf_list, c->acc_fx, c->act_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete[] c->hvt;
@@ -251,6 +251,7 @@ int hr_batch_create(const hr_limits* lim, const hr_instance_desc* desc, int n, h
   c->loss_vec = vec;
   if (cudaMalloc(reinterpret_cast<void**>(&c->vt), sizeof(hr::ViewRec) * views) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&c->it), sizeof(hr::InstRec) * n) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&c->act_off), sizeof(int) * 2 * ((size_t)n + 1)) != cudaSuccess ||
       cudaMemcpy(c->vt, hv, sizeof(hr::ViewRec) * views, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->it, hi, sizeof(hr::InstRec) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaGetLastError();

@@ -74,6 +74,8 @@ struct Context {
   ViewRec* vt;           // device [nviews]
   const int* active;     // device [n_inst] of a batch: instances with 0 are skipped, or
                          // NULL (every instance); hr_batch_set_active
+  int* act_off;          // device [2][n_inst + 1] of a batch: prefix sums over the active
+                         // instances of their sub-tiles (row 0) and views (row 1)
   InstRec* it;           // device [n_inst]
   ViewRec* hvt;          // host copies
   InstRec* hit;

@@ -222,6 +222,7 @@ struct RenderArgs {
   const ViewRec* vt;       // batch view table, nullptr = uniform layout
   const InstRec* it;       // batch instance table
   const int* active;       // batch: instances with 0 are skipped (retired), or null
+  const int* act_off;      // with `active`: [2][n_inst + 1] active sub-tile / view prefix sums
   int n_inst, nviews, total_st;
   int node_stride;
   int cand_per_chunk, max_chunks;   // work-item split (tuning)
@@ -438,6 +439,80 @@ __device__ __forceinline__ SubTile subtile(const RenderArgs& a, int st) {
   t.x0 = (rem % nsx) * kSubW;
   t.y0 = (rem / nsx) * kSubH;
   return t;
+}
+
+// The sub-tiles a kernel visits: all of them, or in a batch with retired instances
+// those of the active instances, numbered 0 .. visit_count - 1 in instance order
+// (prefix sums act_off, made by k_active_layout before the render kernels), so that a
+// mostly retired batch costs no pass over the retired instances' sub-tiles.
+__device__ __forceinline__ int visit_count(const RenderArgs& a) {
+  return a.act_off ? __ldg(&a.act_off[a.n_inst]) : a.total_st;
+}
+// the instance k with off[k] <= i < off[k + 1] (off: n_inst + 1 prefix sums)
+__device__ __forceinline__ int active_inst(const int* off, int n, int i) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(&off[mid]) <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+__device__ __forceinline__ int visit_subtile(const RenderArgs& a, int i) {
+  if (!a.act_off) return i;
+  const int k = active_inst(a.act_off, a.n_inst, i);
+  return __ldg(&a.it[k].st0) + (i - __ldg(&a.act_off[k]));
+}
+// views likewise (the edge-sampling kernel)
+__device__ __forceinline__ int visit_views(const RenderArgs& a) {
+  return a.act_off ? __ldg(&a.act_off[a.n_inst + 1 + a.n_inst]) : a.nviews;
+}
+__device__ __forceinline__ int visit_view(const RenderArgs& a, int j) {
+  if (!a.act_off) return j;
+  const int* off = a.act_off + a.n_inst + 1;
+  const int k = active_inst(off, a.n_inst, j);
+  return __ldg(&a.it[k].view0) + (j - __ldg(&off[k]));
+}
+
+// act_off = prefix sums over the instances of (active ? sub-tiles : 0) and
+// (active ? views : 0); one block, each thread a contiguous run of instances
+constexpr int kLayoutThreads = 1024;
+__global__ void __launch_bounds__(kLayoutThreads) k_active_layout(const InstRec* __restrict__ it,
+                                                                  const int* __restrict__ active, int n,
+                                                                  int* __restrict__ act_off) {
+  __shared__ int sst[kLayoutThreads], svw[kLayoutThreads];
+  const int per = (n + kLayoutThreads - 1) / kLayoutThreads;
+  const int i0 = min(n, threadIdx.x * per), i1 = min(n, i0 + per);
+  int st = 0, vw = 0;
+  for (int i = i0; i < i1; ++i)
+    if (active[i]) {
+      st += it[i].nst;
+      vw += it[i].nviews;
+    }
+  sst[threadIdx.x] = st;
+  svw[threadIdx.x] = vw;
+  __syncthreads();
+  for (int d = 1; d < kLayoutThreads; d <<= 1) {   // inclusive scan
+    const int a = threadIdx.x >= d ? sst[threadIdx.x - d] : 0, b = threadIdx.x >= d ? svw[threadIdx.x - d] : 0;
+    __syncthreads();
+    sst[threadIdx.x] += a;
+    svw[threadIdx.x] += b;
+    __syncthreads();
+  }
+  st = sst[threadIdx.x] - st;
+  vw = svw[threadIdx.x] - vw;
+  for (int i = i0; i < i1; ++i) {
+    act_off[i] = st;
+    act_off[n + 1 + i] = vw;
+    if (active[i]) {
+      st += it[i].nst;
+      vw += it[i].nviews;
+    }
+  }
+  if (threadIdx.x == kLayoutThreads - 1) {
+    act_off[n] = sst[threadIdx.x];
+    act_off[n + 1 + n] = svw[threadIdx.x];
+  }
 }
 
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
@@ -1003,12 +1078,14 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
   GatherSmem& gs = gsm[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   Counts cnt;
-  const int total = subtile_count(a0);
+  const int total = visit_count(a0);
   for (;;) {
-    int st = 0;
-    if (lane == 0) st = (int)atomicAdd(&a0.wk.ctr[0], 1u);
-    st = __shfl_sync(0xffffffffu, st, 0);
-    if (st >= total) break;
+    int vi = 0;
+    if (lane == 0) vi = (int)atomicAdd(&a0.wk.ctr[0], 1u);
+    vi = __shfl_sync(0xffffffffu, vi, 0);
+    if (vi >= total) break;
+    const int st = visit_subtile(a0, vi);
+    if (!in_range(a0.status, st, 0, a0.total_st)) continue;
     const SubTile t = subtile(a0, st);
     if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
     if (!inst_active(a0, t.inst)) {   // a retired instance: nothing to render
@@ -1120,9 +1197,11 @@ __global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, c
   const RenderArgs a0 = with_iter(a_in);
   const int lane = threadIdx.x & 31;
   Counts cnt;
-  const int total = subtile_count(a0);
+  const int total = visit_count(a0);
   const int nw = gridDim.x * kWarps;
-  for (int st = blockIdx.x * kWarps + (threadIdx.x >> 5); st < total; st += nw) {
+  for (int vi = blockIdx.x * kWarps + (threadIdx.x >> 5); vi < total; vi += nw) {
+    const int st = visit_subtile(a0, vi);
+    if (!in_range(a0.status, st, 0, a0.total_st)) continue;
     int2 pk = a0.wk.st[st];
     const SubTile t = subtile(a0, st);
     if (!in_range(a0.status, t.inst, 0, a0.n_inst) || !inst_active(a0, t.inst)) continue;
@@ -1539,11 +1618,14 @@ __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in
   const int lane = threadIdx.x & 31, q = lane % L;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long i = warp * (32 / L) + lane / L;
-  if (warp * (32 / L) >= (long long)a0.nviews * Ne_max) return;   // whole warps leave together
+  const int nv = visit_views(a0);
+  if (warp * (32 / L) >= (long long)nv * Ne_max) return;   // whole warps leave together
   Counts cnt;
   // ---- set-up (group-uniform); `active` groups go on to the search -------------
-  bool active = i < (long long)a0.nviews * Ne_max;
-  const int view = active ? (int)(i / Ne_max) : 0, k = active ? (int)(i - (long long)view * Ne_max) : 0;
+  bool active = i < (long long)nv * Ne_max;
+  const int jv = active ? (int)(i / Ne_max) : 0, k = active ? (int)(i - (long long)jv * Ne_max) : 0;
+  const int view = active ? visit_view(a0, jv) : 0;
+  active = active && in_range(a0.status, view, 0, a0.nviews);
   SubTile vw;
   int st0 = 0, nsx = 1;
   RenderArgs a = a0;
@@ -1852,6 +1934,7 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.tex_h = o->tex_h;
   a.d_tex = a.tex ? o->d_texture : nullptr;
   a.active = ctx->vt ? ctx->active : nullptr;
+  a.act_off = a.active ? ctx->act_off : nullptr;
   if (ctx->vt) {
     a.vt = ctx->vt;
     a.it = ctx->it;
@@ -1889,6 +1972,10 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   Timer tm{ctx, s, (o->flags & HR_TIMING) != 0};
   if (cudaMemsetAsync(ctx->work_ctr, 0, ctr_words(a.n_inst) * sizeof(unsigned), s) != cudaSuccess)
     return HR_ERR_CUDA;
+  if (a.act_off) {   // a batch with a mask: the active instances' sub-tiles and views
+    k_active_layout<<<1, kLayoutThreads, 0, s>>>(ctx->it, ctx->active, ctx->n_inst, ctx->act_off);
+    HR_CHECK_LAUNCH();
+  }
   const int blocks = ctx->num_sms * ctx->tune.blocks_per_sm;
   tm.begin(kTimeFwdGather);
   if (st)
@@ -1940,6 +2027,10 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
                       cudaStream_t s) {
   RenderArgs a = make_args(ctx, m, verts, cams, N, H, W, bg, o);
   a.cand_per_chunk = ctx->tune.bwd_cand_per_chunk;   // the backward's own work-item split
+  if (a.act_off) {   // a batch with a mask: the active instances' sub-tiles and views
+    k_active_layout<<<1, kLayoutThreads, 0, s>>>(ctx->it, ctx->active, ctx->n_inst, ctx->act_off);
+    HR_CHECK_LAUNCH();
+  }
   const int V = m->V, ni = a.n_inst, nv = a.nviews;
   const bool batch = ctx->vt != nullptr;
   const int Ne = batch ? ctx->max_ne : o->edge_samples;
