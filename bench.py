@@ -485,13 +485,15 @@ def _first_at_or_below(err_mm, thr=1.0):
     return int(ok[0]) if ok.size else -1
 
 
-def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
+def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3, texture=None):
     """Refine the instances of `cfgs` from the same initial estimates with the same
     sample streams: plain per-instance refinement through the single-instance calls,
     instance after instance (one CUDA graph each); all instances together through the
     batch calls (one CUDA graph per iteration); and, with `learned` parameters, the
-    batch preceded by the learned proposal steps.  The mean vertex error epsilon_v
-    (Section 4.1) is recorded on the device every iteration."""
+    batch preceded by the learned proposal steps (computed on the proposal rig's views:
+    the instances' own views when they are the rig's, else the rig's cameras among
+    them at reduced resolution).  The mean vertex error epsilon_v (Section 4.1) is
+    recorded on the device every iteration.  texture: the model's albedo texture."""
     import torch
 
     from paper_2107_05509_gb300 import binding as B
@@ -502,15 +504,16 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
     hand = model.hand
     x_gt = [I.gt_params(c.seed) for c in cfgs]
     x0 = torch.as_tensor(np.stack([I.perturb_params(x, c.seed) for x, c in zip(x_gt, cfgs)]), device=dev)
-    views = P.make_batch_views(cfgs, model, x_gt, device=dev)
+    views = P.make_batch_views(cfgs, model, x_gt, device=dev, texture=texture)
     bt = B.Batch(hand.V, hand.F, hand.E, [(c.views, c.width, c.height, c.spp, c.edge_samples, i)
                                           for i, c in enumerate(cfgs)])
     ref = torch.empty((n, hand.V, 3), device=dev)
     B.hr_skin_batch(bt, model, torch.as_tensor(np.stack(x_gt), device=dev), ref)
-    R = P.BatchRefiner(model, bt, views, ref_verts=ref, max_iters=iters + 8, device=dev)
+    R = P.BatchRefiner(model, bt, views, ref_verts=ref, max_iters=iters + 8, device=dev, texture=texture)
     # the same batch with converged instances retired on the device (the per-instance
     # criterion: an instance leaves the batch once its epsilon_v is <= 1 mm)
-    Rr = P.BatchRefiner(model, bt, views, ref_verts=ref, max_iters=iters + 8, device=dev, retire="converged")
+    Rr = P.BatchRefiner(model, bt, views, ref_verts=ref, max_iters=iters + 8, device=dev, retire="converged",
+                        texture=texture)
 
     # work counters of one batched iteration
     R.reset(x0)
@@ -570,15 +573,33 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
     res_learned = res_learned_r = None
     if learned is not None:
         from paper_2107_05509_gb300 import proposal as PR
-        prop = PR.Proposer(R, learned, steps=proposal_steps)
-        prop.run()                       # warm-up of the network's kernels
-        err_l, dt_l, pre_ms = run_batch(prop.run)
+        rig_layout = all((c.views, c.width, c.height) == (PR.RIG.views, PR.RIG.width, PR.RIG.height) for c in cfgs)
+        if rig_layout:
+            prop = PR.Proposer(R, learned, steps=proposal_steps)
+
+            def propose(refiner):
+                prop.r = refiner
+                prop.run()
+        else:
+            # the proposal steps run on the rig's views of these instances (a batch of
+            # that layout); the refinement continues from the chosen candidates
+            rviews = PR.rig_views(cfgs, views, bt.view_offsets, bt.pixel_offsets)
+            rbt = B.Batch(hand.V, hand.F, hand.E, [(PR.RIG.views, PR.RIG.width, PR.RIG.height, PR.RIG.spp,
+                                                    PR.RIG.edge_samples, i) for i in range(n)])
+            RR = P.BatchRefiner(model, rbt, rviews, device=dev, texture=texture)
+            prop = PR.Proposer(RR, learned, steps=proposal_steps)
+
+            def propose(refiner):
+                RR.params.copy_(refiner.params)
+                prop.run()
+                refiner.params.copy_(RR.params)
+        propose(R)                       # warm-up of the network's kernels
+        err_l, dt_l, pre_ms = run_batch(lambda: propose(R))
         chosen = prop.chosen.cpu().numpy()
         if prop.net.status() != B.HR_OK:
             raise RuntimeError("proposal network status")
         res_learned = (err_l, dt_l, pre_ms, chosen)
-        prop.r = Rr                      # the same network and candidates for the retiring batch
-        err_lr, dt_lr, pre_ms_r = run_batch(prop.run, refiner=Rr, graph=g_r)
+        err_lr, dt_lr, pre_ms_r = run_batch(lambda: propose(Rr), refiner=Rr, graph=g_r)
         res_learned_r = (err_lr, dt_lr, pre_ms_r)
 
     # plain per-instance refinement, instance after instance
@@ -590,7 +611,8 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
                      background=views.background[po[i]:po[i + 1]].reshape(c.views, c.height, c.width, 3),
                      observed=views.observed[po[i]:po[i + 1]].reshape(c.views, c.height, c.width, 3),
                      mask=views.mask[po[i]:po[i + 1]].reshape(c.views, c.height, c.width), H=c.height, W=c.width)
-        pr = P.PlainRefiner(model, v1, c, instance=i, ref_verts=ref[i], max_iters=iters + 8, device=dev)
+        pr = P.PlainRefiner(model, v1, c, instance=i, ref_verts=ref[i], max_iters=iters + 8, device=dev,
+                            texture=texture)
         pr.reset(x0[i])
         tune(pr.r.ctx, pr.render_pass, [(c.views, c.width, c.height, c.spp, c.edge_samples)])
         pr.reset(x0[i])
@@ -662,10 +684,14 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3):
 
 
 def run_refinement(args, dev):
-    """Time-to-1 mm on two batched workloads: (1) heterogeneous instances (4-16 views
+    """Time-to-1 mm on three batched workloads: (1) heterogeneous instances (4-16 views
     at 256x256 / 512x384 / 512x512, 8-32 spp): plain per-instance vs batched; (2) the
     learned proposal's rig (8 views at 256x256, 16 spp): plain vs batched vs batched
-    with the learned proposal steps first."""
+    with the learned proposal steps first; (3) instances of the scale workload: plain
+    vs batched vs batched with the learned proposal steps first.  Each batched pipeline
+    also runs with converged instances retired."""
+    import torch
+
     from paper_2107_05509_gb300 import binding as B
     from paper_2107_05509_gb300 import inputs as I
     from paper_2107_05509_gb300 import pipeline as P
@@ -682,7 +708,18 @@ def run_refinement(args, dev):
     lr = refine_compare(rig, model, dev, iters, learned=learned)
     lr["workload"] = f"rig-{n}x(8 views 256x256, 16 spp, 4096 edge samples/view)"
     lr["proposal_training"] = {k: meta[k] for k in ("pairs", "steps", "seconds", "heldout_eps_v_mm") if k in meta}
-    return {"heterogeneous": het, "learned_rig": lr,
+    # the scale workload (subdivided, textured, 16 x 1024^2 at 64 spp): a handful of
+    # instances, plain vs batched vs batched with the learned proposal (on the rig's
+    # views among the instances' own, at 256^2)
+    sub = I.subdivide_hand(hand, 2)
+    smodel = B.Model(sub, device=dev)
+    tex = torch.as_tensor(I.texture(I.SCALE.seed, 256), device=dev)
+    scfgs = [dataclasses.replace(I.SCALE, seed=I.SCALE.seed + i, name=f"{I.SCALE.name}-{i}")
+             for i in range(args.scale_instances)]
+    sc = refine_compare(scfgs, smodel, dev, args.scale_iters, learned=learned, texture=tex)
+    sc["workload"] = (f"scale-{args.scale_instances}x(16 views 1024x1024, 64 spp, 32768 edge samples/view, "
+                      f"12337 V / 24608 F, 256x256 texture)")
+    return {"heterogeneous": het, "learned_rig": lr, "scale": sc,
             "adam_lr_per_group": {"shape": P.LR_GROUPS[0], "pose_rad": P.LR_GROUPS[1],
                                   "root_rot_rad": P.LR_GROUPS[2], "trans_m": P.LR_GROUPS[3]},
             "criterion": "time_to_mean_1mm: device time until the mean over instances of epsilon_v <= 1 mm "
@@ -1057,6 +1094,8 @@ def main():
     ap.add_argument("--no-refine", action="store_true", help="skip the time-to-1 mm refinement comparison")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--refine-iters", type=int, default=150)
+    ap.add_argument("--scale-instances", type=int, default=4)
+    ap.add_argument("--scale-iters", type=int, default=60)
     ap.add_argument("--gemm-only", action="store_true", help="only the tensor-core GEMM timings (for profiling)")
     ap.add_argument("--objective-only", action="store_true", help="only the full-objective schedule")
     ap.add_argument("--edges-only", action="store_true", help="only the edge-term timings (for profiling)")

@@ -468,6 +468,15 @@ int hr_retire_converged(const float* err, const uint32_t* iter_dev, int rows, in
 int hr_retire_plateau(const float* loss, int n, float rel_tol, int patience, float* best, int32_t* stall,
                       int32_t* active, float* lr_scale, int per_instance, hr_stream stream);
 
+/* Lower-resolution copies of a multiframe, for the learned proposal, whose network
+ * takes views of its training rig's resolution: hr_box_downsample writes the f x f
+ * box means of device float[N][H][W][3] images into float[N][H/f][W/f][3] (a pixel
+ * of the result covers the f x f pixels it averages, so the cameras' intrinsics scale
+ * by 1/f); hr_mask_downsample the maximum of f x f blocks of uint8[N][H][W] masks.
+ * H and W multiples of f, else HR_ERR_ARG. */
+int hr_box_downsample(const float* src, int N, int H, int W, int f, float* dst, hr_stream stream);
+int hr_mask_downsample(const uint8_t* src, int N, int H, int W, int f, uint8_t* dst, hr_stream stream);
+
 /* BF16 matrix product on the tensor cores (tcgen05, float32 accumulation), the
  * building block of the learned proposal network:
  *   C[M][N] = act(A[M][K] B[N][K]^T + bias[N]),  act = ReLU when relu != 0.

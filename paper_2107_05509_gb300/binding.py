@@ -46,7 +46,8 @@ EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", 
            "hr_set_tuning", "hr_get_tuning", "hr_loss_ct",
            "hr_skin_joints", "hr_skin_bwd_joints", "hr_joint_prior", "hr_colour_map", "hr_colour_map_bwd",
            "hr_edges", "hr_edge_loss", "hr_model_check",
-           "hr_batch_set_active", "hr_retire_converged", "hr_retire_plateau")
+           "hr_batch_set_active", "hr_retire_converged", "hr_retire_plateau", "hr_box_downsample",
+           "hr_mask_downsample")
 
 
 class HandrtError(RuntimeError):
@@ -107,6 +108,8 @@ def lib():
             "hr_skin_bwd_noalloc": [P, P, P, P, P],
             "hr_model_check": [P],
             "hr_batch_set_active": [P, P],
+            "hr_box_downsample": [P, I, I, I, I, P, P],
+            "hr_mask_downsample": [P, I, I, I, I, P, P],
             "hr_retire_converged": [P, P, I, I, F, P, P, I, P],
             "hr_retire_plateau": [P, I, F, I, P, P, P, P, I, P],
             "hr_build_bvh": [P, P, P, P],
@@ -559,6 +562,19 @@ def hr_retire_plateau(loss, rel_tol, patience, best, stall, active, lr_scale=Non
     _check("hr_retire_plateau", lib().hr_retire_plateau(
         _f32(loss), n, float(rel_tol), int(patience), _f32(best), _ptr(stall), _ptr(active),
         None if lr_scale is None else _f32(lr_scale), per, _stream(stream)))
+
+
+def hr_box_downsample(src, f, dst, stream=None):
+    """src: device float [N][H][W][3]; dst: [N][H/f][W/f][3] box means."""
+    N, H, W, _ = src.shape
+    _check("hr_box_downsample", lib().hr_box_downsample(_f32(src), N, H, W, int(f), _f32(dst), _stream(stream)))
+
+
+def hr_mask_downsample(src, f, dst, stream=None):
+    """src: device uint8 [N][H][W]; dst: [N][H/f][W/f] block maxima."""
+    assert src.dtype == torch.uint8 and dst.dtype == torch.uint8
+    N, H, W = src.shape
+    _check("hr_mask_downsample", lib().hr_mask_downsample(_ptr(src), N, H, W, int(f), _ptr(dst), _stream(stream)))
 
 
 def hr_vertex_mse(verts, ref, loss, d_verts=None, stream=None):

@@ -286,6 +286,18 @@ int hr_retire_plateau(const float* loss, int n, float rel_tol, int patience, flo
                                    (cudaStream_t)stream);
 }
 
+int hr_box_downsample(const float* src, int N, int H, int W, int f, float* dst, hr_stream stream) {
+  if (!src || !dst || N < 1 || f < 1 || H < f || W < f || H % f || W % f || (long long)N * H * W > (1ll << 40))
+    return HR_ERR_ARG;
+  return hr::launch_box_downsample(src, N, H, W, f, dst, (cudaStream_t)stream);
+}
+
+int hr_mask_downsample(const uint8_t* src, int N, int H, int W, int f, uint8_t* dst, hr_stream stream) {
+  if (!src || !dst || N < 1 || f < 1 || H < f || W < f || H % f || W % f || (long long)N * H * W > (1ll << 40))
+    return HR_ERR_ARG;
+  return hr::launch_mask_downsample(src, N, H, W, f, dst, (cudaStream_t)stream);
+}
+
 int hr_batch_layout(hr_context* ctx, int32_t* view_offsets, int64_t* pixel_offsets) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || !c->vt || !view_offsets || !pixel_offsets) return HR_ERR_ARG;

@@ -506,6 +506,54 @@ int launch_retire_plateau(const float* loss, int n, float rel_tol, int patience,
   return HR_OK;
 }
 
+// f x f box mean of [N][H][W][3] images (H, W multiples of f): one thread per output
+// value; and the maximum of f x f blocks of [N][H][W] uint8 masks
+__global__ void k_box_downsample(const float* __restrict__ src, long long n_out, int Ho, int Wo, int f,
+                                 float* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_out) return;
+  const int c = (int)(i % 3);
+  const long long px = i / 3;
+  const int x = (int)(px % Wo);
+  const long long r = px / Wo;
+  const int y = (int)(r % Ho);
+  const long long v = r / Ho;
+  const long long W = (long long)Wo * f, H = (long long)Ho * f;
+  float acc = 0.0f;
+  for (int dy = 0; dy < f; ++dy)
+    for (int dx = 0; dx < f; ++dx) acc += src[((v * H + (long long)y * f + dy) * W + (long long)x * f + dx) * 3 + c];
+  dst[i] = acc / (float)(f * f);
+}
+
+__global__ void k_mask_downsample(const uint8_t* __restrict__ src, long long n_out, int Ho, int Wo, int f,
+                                  uint8_t* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_out) return;
+  const int x = (int)(i % Wo);
+  const long long r = i / Wo;
+  const int y = (int)(r % Ho);
+  const long long v = r / Ho;
+  const long long W = (long long)Wo * f, H = (long long)Ho * f;
+  uint8_t m = 0;
+  for (int dy = 0; dy < f; ++dy)
+    for (int dx = 0; dx < f; ++dx) m = max(m, src[(v * H + (long long)y * f + dy) * W + (long long)x * f + dx]);
+  dst[i] = m;
+}
+
+int launch_box_downsample(const float* src, int N, int H, int W, int f, float* dst, cudaStream_t s) {
+  const long long n = (long long)N * (H / f) * (W / f) * 3;
+  k_box_downsample<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, n, H / f, W / f, f, dst);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_mask_downsample(const uint8_t* src, int N, int H, int W, int f, uint8_t* dst, cudaStream_t s) {
+  const long long n = (long long)N * (H / f) * (W / f);
+  k_mask_downsample<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, n, H / f, W / f, f, dst);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
 int launch_vertex_mse(const float* a, const float* b, int V, int n, float* loss, float* grad, cudaStream_t s) {
   k_vertex_mse<<<n, kErrThreads, 0, s>>>(a, b, V, loss, grad);
   HR_CHECK_LAUNCH();

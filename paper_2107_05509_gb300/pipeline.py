@@ -324,10 +324,11 @@ class BatchViews:
     mask: torch.Tensor        # [P] uint8
 
 
-def make_batch_views(cfgs, model: B.Model, x_gts, device="cuda"):
+def make_batch_views(cfgs, model: B.Model, x_gts, device="cuda", texture=None):
     """Observations of every instance (the recipe of make_views: the GT render at
     cfg.obs_spp with the instance's own Philox instance field, plus noise, and the
-    dilated coverage mask), concatenated in instance order."""
+    dilated coverage mask), concatenated in instance order; `texture`: the albedo
+    texture of the model (its uv) for the observations."""
     hand = model.hand
     cams, bgs, obss, masks = [], [], [], []
     for i, (cfg, x) in enumerate(zip(cfgs, x_gts)):
@@ -340,7 +341,7 @@ def make_batch_views(cfgs, model: B.Model, x_gts, device="cuda"):
         B.hr_skin(ctx, model, torch.as_tensor(np.asarray(x, np.float32), device=device), verts)
         B.hr_build_bvh(ctx, model, verts)
         clean = torch.empty((N, H, W, 3), device=device)
-        o = opts_for(cfg, spp=cfg.obs_spp, seed=cfg.seed * 7919 + 1)
+        o = opts_for(cfg, spp=cfg.obs_spp, seed=cfg.seed * 7919 + 1, texture=texture)
         o.instance = i
         B.hr_render_fwd(ctx, model, verts, c, H, W, bg, o, clean)
         clean_np = clean.cpu().numpy()
@@ -370,7 +371,7 @@ class BatchRefiner:
 
     def __init__(self, model: B.Model, batch: B.Batch, views: BatchViews, seed=17, lr=1.0, lr_groups=LR_GROUPS,
                  ref_verts=None, max_iters=1024, device="cuda", retire=None, retire_mm=1.0, rel_tol=1e-3,
-                 patience=10):
+                 patience=10, texture=None):
         self.model, self.batch, self.views = model, batch, views
         n, V, P = batch.n, model.V, batch.total_pixels
         if retire not in (None, "converged", "plateau"):
@@ -381,7 +382,7 @@ class BatchRefiner:
         self.counter = torch.zeros(1, dtype=torch.int32, device=device)
         self.opts = B.render_opts(seed=seed, ka=I.K_AMBIENT, kd=I.K_DIFFUSE, light_dir=I.LIGHT_DIR,
                                   light_rgb=I.LIGHT_RGB, edge_eps_px=I.EDGE_EPS_PX, iter_dev=self.counter,
-                                  flags=B.HR_BWD_REUSE_FWD)
+                                  flags=B.HR_BWD_REUSE_FWD, texture=texture)
         self.params = torch.zeros((n, I.N_PARAMS), device=device)
         self.verts = torch.empty((n, V, 3), device=device)
         self.image = torch.empty((P, 3), device=device)

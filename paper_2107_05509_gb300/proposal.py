@@ -196,6 +196,46 @@ def evaluate(model: B.Model, params, batches=4, batch=128, seed=12345):
 # inference: proposal steps in front of the plain batched refinement
 # --------------------------------------------------------------------------------------
 
+def rig_views(cfgs, views: P.BatchViews, view_offsets, pixel_offsets):
+    """The training rig's views of instances captured by other rigs: every instance
+    must have a view at each of the rig's cameras (same elevation, radius and
+    azimuths) at an integer multiple f of the rig's resolution.  Those views are
+    reduced by f x f box means (hr_box_downsample; masks by block maxima) and their
+    intrinsics scaled by 1/f, so the network sees its own camera layout.  Returns the
+    rig-layout BatchViews (instances in order, the rig's view order)."""
+    cams, bgs, obss, masks = [], [], [], []
+    for i, cfg in enumerate(cfgs):
+        f = cfg.width // RIG.width
+        if (f < 1 or cfg.width != f * RIG.width or cfg.height != f * RIG.height or
+                cfg.elevation_deg != RIG.elevation_deg or cfg.radius != RIG.radius):
+            raise ValueError(f"instance {i}: its views do not contain the proposal rig's")
+        idx = []
+        for r in RIG.azimuths_deg:
+            k = [j for j, az in enumerate(cfg.azimuths_deg) if abs((az - r + 180.0) % 360.0 - 180.0) < 1e-6]
+            if not k:
+                raise ValueError(f"instance {i}: no view at azimuth {r}")
+            idx.append(k[0])
+        H, W = cfg.height, cfg.width
+        v0, p0 = int(view_offsets[i]), int(pixel_offsets[i])
+        for k in idx:
+            c = views.cams[v0 + k].clone()
+            c[0:4] /= f
+            cams.append(c)
+            sl = slice(p0 + k * H * W, p0 + (k + 1) * H * W)
+            out = []
+            for src in (views.background, views.observed):
+                dst = torch.empty((1, H // f, W // f, 3), device=src.device)
+                B.hr_box_downsample(src[sl].reshape(1, H, W, 3), f, dst)
+                out.append(dst.reshape(-1, 3))
+            m = torch.empty((1, H // f, W // f), dtype=torch.uint8, device=views.mask.device)
+            B.hr_mask_downsample(views.mask[sl].reshape(1, H, W), f, m)
+            bgs.append(out[0])
+            obss.append(out[1])
+            masks.append(m.reshape(-1))
+    return P.BatchViews(cams=torch.stack(cams), background=torch.cat(bgs), observed=torch.cat(obss),
+                        mask=torch.cat(masks))
+
+
 class Proposer:
     """Proposal steps for a BatchRefiner whose instances all use the training rig's
     layout (views x 256 x 256): candidates x_0 (the refiner's parameters) and
