@@ -45,7 +45,8 @@ void free_ctx(Context* c) {
                   c->status,  c->stats,   c->pool_bb,   c->pool_z,     c->pool_rec,      c->st_info,
                   c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it,
                   c->bvh_parent, c->bvh_valid, c->bvh_keys, c->bvh_flags, c->bvh_bounds, c->bvh_bad,
-                  c->bvh_mode, c->extra64, c->ct_partials, c->dedge, c->ovf_list, c->acc_fx, c->act_off};
+                  c->bvh_mode, c->extra64, c->ct_partials, c->dedge, c->ovf_list, c->acc_fx, c->act_off,
+                  c->trace_list, c->st_done, c->cand_st};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete[] c->hvt;
@@ -104,8 +105,8 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
   c->pool_cap = (int)std::min<size_t>((size_t)1 << 28, 16 * subtiles + 4096);
   c->item_cap = (int)items;
   c->loss_blocks = loss_blocks;
-  // block partials of the single-instance backward (V <= kPartialMaxV)
-  const size_t partial_blocks = (n == 1 && V <= (size_t)hr::kPartialMaxV) ? (size_t)c->render_blocks : 1;
+  // partials of the single-instance backward, one per SM (V <= kPartialMaxV)
+  const size_t partial_blocks = (n == 1 && V <= (size_t)hr::kPartialMaxV) ? (size_t)c->num_sms : 1;
   const size_t nviews = views;
   bool ok = dev_alloc(&c->nodes, ni * F, a) && dev_alloc(&c->tris, ni * 3 * F, a) &&
             dev_alloc(&c->normals, ni * 3 * V, a) && dev_alloc(&c->normal_len, ni * V, a) &&
@@ -120,7 +121,8 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
             dev_alloc(&c->pool_rec, c->pool_cap, a) && dev_alloc(&c->st_info, subtiles, a) &&
             dev_alloc(&c->items, c->item_cap, a) && dev_alloc(&c->item_part, (size_t)c->item_cap * 32, a) &&
             dev_alloc(&c->extra, ni * 6 * V, a) && dev_alloc(&c->work_ctr, hr::ctr_words(ni), a) &&
-            dev_alloc(&c->ovf_list, subtiles, a) &&
+            dev_alloc(&c->ovf_list, subtiles, a) && dev_alloc(&c->trace_list, c->item_cap, a) &&
+            dev_alloc(&c->st_done, subtiles, a) && dev_alloc(&c->cand_st, subtiles, a) &&
             dev_alloc(&c->bvh_parent, ni * 2 * F, a) && dev_alloc(&c->bvh_valid, ni, a) &&
             dev_alloc(&c->bvh_bounds, ni * 6, a) && dev_alloc(&c->bvh_bad, ni, a) && dev_alloc(&c->bvh_mode, ni, a);
   // keys of the multi-block build, for meshes beyond one block's shared memory
@@ -134,7 +136,8 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
                cudaMemset(c->status, 0, sizeof(int)) == cudaSuccess &&
                cudaMemset(c->stats, 0, 3 * hr::kStatsPer * sizeof(unsigned long long)) == cudaSuccess &&
                cudaMemset(c->nodes, 0, ni * F * sizeof(hr::Node)) == cudaSuccess &&
-               cudaMemset(c->bvh_valid, 0, ni * sizeof(int)) == cudaSuccess;
+               cudaMemset(c->bvh_valid, 0, ni * sizeof(int)) == cudaSuccess &&
+               cudaMemset(c->st_done, 0, subtiles * sizeof(unsigned)) == cudaSuccess;
   for (int i = 0; ok && i < 2 * hr::kTimeSlots; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
   if (ok)
     ok = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&

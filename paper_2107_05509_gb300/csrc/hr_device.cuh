@@ -121,6 +121,9 @@ struct Context {
   double* extra64;       // [n_inst][max_V][6] backward sums when max_V > 8192
   unsigned* work_ctr;    // [3 + 2 n_inst]
   int* ovf_list;         // [sub-tiles] sub-tiles whose items overflowed their region
+  int* trace_list;       // [item_cap] items of sub-tiles without a candidate list (per-ray traversal)
+  unsigned* st_done;     // [sub-tiles] forward items finished per sub-tile (zero between launches)
+  int* cand_st;          // [sub-tiles] forward sub-tiles whose frustum meets the scene's root boxes
   // backward scratch
   float* partials;       // [render_blocks][max_V][6] (single-instance contexts)
   float* dN;             // [n_inst][max_V][3]
@@ -156,9 +159,12 @@ struct Context {
   unsigned long long* stats;  // [3][kStatsPer]
 };
 
-// work counters of the render kernels for n instances: 3 + 3n words, then (from an
-// even word) one 64-bit item-allocation word per instance
-__host__ __device__ constexpr int ctr_alloc_base(int n) { return (3 + 3 * n + 1) & ~1; }
+// work counters of the render kernels for n instances: 3 + 3n words, the trace-list
+// count, the culled-list count, then (from an even word) one 64-bit item-allocation
+// word per instance
+__host__ __device__ constexpr int ctr_trace(int n) { return 3 + 3 * n; }
+__host__ __device__ constexpr int ctr_cull(int n) { return 4 + 3 * n; }
+__host__ __device__ constexpr int ctr_alloc_base(int n) { return (5 + 3 * n + 1) & ~1; }
 __host__ __device__ constexpr int ctr_words(int n) { return ctr_alloc_base(n) + 2 * n; }
 // meshes up to this many vertices take float backward sums (per block of the shader
 // in a single-instance context); larger ones float64 sums

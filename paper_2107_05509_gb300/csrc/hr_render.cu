@@ -19,7 +19,8 @@
 //                  closest-hit rule as a per-ray traversal on the candidates whose
 //                  box contains the sample, in depth order, and stops when no lane
 //                  can still find a nearer hit; shades, and writes per-item sums.
-//   k_combine_fwd  sums each sub-tile's items in item order (deterministic).
+//   (finish_item)  the warp finishing a sub-tile's last forward item sums the items in
+//                  item order (deterministic) and writes the pixels.
 //   k_shade_bwd    the same samples re-traced (no hit records are kept between
 //                  the passes); every hit is differentiated at the fixed ray and the
 //                  gradient accumulated per triangle in registers, per block in
@@ -205,6 +206,10 @@ struct Work {
                    // items, then per instance a 64-bit allocation word
   int* ovf;        // [sub-tiles] sub-tiles whose items did not fit their instance's
                    // region (k_overflow does them whole)
+  int* trace;      // [items] region slots (+ instance base) of the items of sub-tiles
+                   // without a candidate list (k_overflow traces them ray by ray)
+  unsigned* st_done;   // [sub-tiles] forward items finished (the last one combines)
+  int* cand_st;        // [sub-tiles] forward sub-tiles left by k_cull (count: ctr_cull)
   unsigned long long* fx;   // [n_inst][6V] fixed-point backward sums (HR_DETERMINISTIC)
   bool det;                 // HR_DETERMINISTIC: every vertex-gradient sum goes to fx
 };
@@ -580,24 +585,28 @@ __device__ __forceinline__ void project_record(const RenderArgs& a, const Cam& c
 // planes through the camera centre and the rectangle padded by half a pixel, and
 // the camera's forward plane.  Leaves into gs.leaf; returns their count, or -1 when
 // the sub-tile needs more than kLeafCap candidates or kFrontCap frontier nodes.
+// plane q (0-4) of the sub-tile's frustum: the four planes through the camera centre
+// and the rectangle padded by half a pixel, and the camera's forward plane (n, n . c)
+__device__ __forceinline__ float4 frustum_plane(const Cam& cam, int x0, int y0, int q) {
+  float ax = __fdividef((float)x0 - 0.5f - cam.cx, cam.fx);
+  float bx = __fdividef((float)(x0 + kSubW) + 0.5f - cam.cx, cam.fx);
+  float ay = __fdividef((float)y0 - 0.5f - cam.cy, cam.fy);
+  float by = __fdividef((float)(y0 + kSubH) + 0.5f - cam.cy, cam.fy);
+  float3 nc = q == 0   ? make_float3(1.0f, 0.0f, -ax)
+              : q == 1 ? make_float3(-1.0f, 0.0f, bx)
+              : q == 2 ? make_float3(0.0f, 1.0f, -ay)
+              : q == 3 ? make_float3(0.0f, -1.0f, by)
+                       : make_float3(0.0f, 0.0f, 1.0f);
+  float3 nw = make_float3(cam.R[0] * nc.x + cam.R[3] * nc.y + cam.R[6] * nc.z,
+                          cam.R[1] * nc.x + cam.R[4] * nc.y + cam.R[7] * nc.z,
+                          cam.R[2] * nc.x + cam.R[5] * nc.y + cam.R[8] * nc.z);
+  return make_float4(nw.x, nw.y, nw.z, nw.x * cam.c[0] + nw.y * cam.c[1] + nw.z * cam.c[2]);
+}
+
 template <bool STATS>
 __device__ int frustum_leaves(const RenderArgs& a, const Cam& cam, int x0, int y0, GatherSmem& gs, Counts& cnt) {
   const int lane = threadIdx.x & 31;
-  if (lane < 5) {
-    float ax = __fdividef((float)x0 - 0.5f - cam.cx, cam.fx);
-    float bx = __fdividef((float)(x0 + kSubW) + 0.5f - cam.cx, cam.fx);
-    float ay = __fdividef((float)y0 - 0.5f - cam.cy, cam.fy);
-    float by = __fdividef((float)(y0 + kSubH) + 0.5f - cam.cy, cam.fy);
-    float3 nc = lane == 0   ? make_float3(1.0f, 0.0f, -ax)
-                : lane == 1 ? make_float3(-1.0f, 0.0f, bx)
-                : lane == 2 ? make_float3(0.0f, 1.0f, -ay)
-                : lane == 3 ? make_float3(0.0f, -1.0f, by)
-                            : make_float3(0.0f, 0.0f, 1.0f);
-    float3 nw = make_float3(cam.R[0] * nc.x + cam.R[3] * nc.y + cam.R[6] * nc.z,
-                            cam.R[1] * nc.x + cam.R[4] * nc.y + cam.R[7] * nc.z,
-                            cam.R[2] * nc.x + cam.R[5] * nc.y + cam.R[8] * nc.z);
-    gs.pl[lane] = make_float4(nw.x, nw.y, nw.z, nw.x * cam.c[0] + nw.y * cam.c[1] + nw.z * cam.c[2]);
-  }
+  if (lane < 5) gs.pl[lane] = frustum_plane(cam, x0, y0, lane);
   if (lane == 0) gs.front[0][0] = 0;
   __syncwarp();
   int n = 1, cur = 0, K = 0, levels = 0;
@@ -685,6 +694,17 @@ __device__ __forceinline__ int alloc_items(const RenderArgs& a, int inst, int C,
   atomicAdd(back_count(a, inst), (unsigned)C);
   return (int)(icap - back - C);
 }
+
+// the C items at table index `gi` belong to a sub-tile without a candidate list: list
+// them for k_overflow (all lanes call)
+__device__ __forceinline__ void note_trace_items(const RenderArgs& a, int gi, int C) {
+  int base = 0;
+  if ((threadIdx.x & 31) == 0) base = (int)atomicAdd(&a.wk.ctr[ctr_trace(a.n_inst)], (unsigned)C);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int c = threadIdx.x & 31; c < C; c += 32)
+    if (base + c < a.wk.item_cap) a.wk.trace[base + c] = gi + c;
+}
+
 
 // closest hits of a lane's S rays (same origin) among the K pool candidates at `off`:
 // the warp loads the candidates 32 at a time, one per lane (depth, screen box and
@@ -1065,6 +1085,54 @@ __device__ __forceinline__ float3 lane_adjoint(const RenderArgs& a, const SubTil
   return make_float3(g.x * inv_spp, g.y * inv_spp, g.z * inv_spp);
 }
 
+// Forward, first pass: one warp per sub-tile, each warp a static share of the
+// sub-tiles (no shared counter).  A sub-tile whose frustum meets neither of the
+// scene's two root boxes sees only the background: its pixels are written here.  The
+// others are listed for k_gather, which then claims far fewer sub-tiles from its
+// counter.
+constexpr int kCullThreads = 256;
+template <bool STATS>
+__global__ void __launch_bounds__(kCullThreads) k_cull(RenderArgs a0, float* __restrict__ image,
+                                                       unsigned long long* stats) {
+  __shared__ float4 spl[kCullThreads / 32][5];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  Counts cnt;
+  const int total = visit_count(a0);
+  const int nw = gridDim.x * (kCullThreads / 32);
+  for (int vi = blockIdx.x * (kCullThreads / 32) + w; vi < total; vi += nw) {
+    const int st = visit_subtile(a0, vi);
+    if (!in_range(a0.status, st, 0, a0.total_st)) continue;
+    const SubTile t = subtile(a0, st);
+    if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
+    if (!inst_active(a0, t.inst)) {   // a retired instance: nothing to render
+      if (lane == 0) a0.wk.st[st] = make_int2(0, 0);
+      continue;
+    }
+    const RenderArgs a = for_inst(a0, t.inst);
+    const Cam cam = load_cam(a.cams, t.view);
+    if (lane < 5) spl[w][lane] = frustum_plane(cam, t.x0, t.y0, lane);
+    __syncwarp();
+    bool meets = false;
+    if (lane < 2) {   // the root's two child boxes
+      const float4* np = reinterpret_cast<const float4*>(a.nodes);
+      const float4 p = __ldg(np), q = __ldg(np + 1), r = __ldg(np + 2);
+      meets = lane == 0 ? box_in_frustum(spl[w], p.x, p.y, p.z, p.w, q.x, q.y)
+                        : box_in_frustum(spl[w], q.z, q.w, r.x, r.y, r.z, r.w);
+    }
+    const bool any = __any_sync(0xffffffffu, meets);
+    __syncwarp();
+    if (any) {
+      if (lane == 0) a0.wk.cand_st[atomicAdd(&a0.wk.ctr[ctr_cull(a0.n_inst)], 1u)] = st;
+      continue;
+    }
+    if (lane == 0) a0.wk.st[st] = make_int2(0, 0);
+    const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
+    if (STATS && px < t.W && py < t.H) cnt.samples += t.spp;   // resolved by the frustum test
+    write_pixel(a, t, make_float3(0.0f, 0.0f, 0.0f), t.spp, image);
+  }
+  flush_counts<STATS>(cnt, stats);
+}
+
 // One warp per sub-tile: candidates into the pool, work items for the sub-tile (in
 // its instance's region of the item table).
 // BWD: only sub-tiles with a non-zero adjoint; their zero-candidate case has no
@@ -1078,13 +1146,16 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
   GatherSmem& gs = gsm[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   Counts cnt;
-  const int total = visit_count(a0);
+  // the forward takes the sub-tiles k_cull listed, the backward every sub-tile
+  const int total =
+      BWD ? visit_count(a0)
+          : (int)min(*reinterpret_cast<volatile unsigned*>(&a0.wk.ctr[ctr_cull(a0.n_inst)]), (unsigned)a0.total_st);
   for (;;) {
     int vi = 0;
     if (lane == 0) vi = (int)atomicAdd(&a0.wk.ctr[0], 1u);
     vi = __shfl_sync(0xffffffffu, vi, 0);
     if (vi >= total) break;
-    const int st = visit_subtile(a0, vi);
+    const int st = BWD ? visit_subtile(a0, vi) : a0.wk.cand_st[vi];
     if (!in_range(a0.status, st, 0, a0.total_st)) continue;
     const SubTile t = subtile(a0, st);
     if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
@@ -1179,6 +1250,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
     if (lane == 0) a.wk.st[st] = make_int2(off, K);
     if (first >= 0) {
       for (int c = lane; c < C; c += 32) a.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
+      if (K < 0) note_trace_items(a, ibase + first, C);
     } else if (lane == 0) {
       // item region full: the whole sub-tile goes to k_overflow
       a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
@@ -1221,6 +1293,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, c
     first = __shfl_sync(0xffffffffu, first, 0);
     if (first >= 0) {
       for (int c = lane; c < C; c += 32) a.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
+      if (pk.y < 0) note_trace_items(a, ibase + first, C);
     } else if (lane == 0) {
       a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
     }
@@ -1270,9 +1343,46 @@ __device__ __forceinline__ bool load_item(const RenderArgs& a, int gi, int4& ite
   return true;
 }
 
+// A forward work item is done (all lanes call): a sub-tile with one item writes its
+// pixels at once; otherwise the item's radiance sums go to its slot of the partials,
+// and the warp that finishes the sub-tile's last item (a per-sub-tile counter) adds
+// the C partials in item order and writes the pixels -- the same sums, in the same
+// order, whichever warps traced the items.
+__device__ __forceinline__ void finish_item(const RenderArgs& a, const SubTile& t, const int4& item, int slot,
+                                            float3 acc, int misses, float* __restrict__ image) {
+  const int lane = threadIdx.x & 31;
+  if (item.z == 1) {
+    write_pixel(a, t, acc, misses, image);
+    return;
+  }
+  a.wk.part[(size_t)slot * 32 + lane] = make_float4(acc.x, acc.y, acc.z, (float)misses);
+  // every lane's sums are visible device-wide before lane 0 counts the item (the fence
+  // orders each lane's own store; the warp barrier puts all of them before the count)
+  __threadfence();
+  __syncwarp();
+  unsigned prev = 0;
+  if (lane == 0) prev = atomicAdd(&a.wk.st_done[item.x], 1u);
+  prev = __shfl_sync(0xffffffffu, prev, 0);
+  if (prev != (unsigned)item.z - 1u) return;
+  __threadfence();
+  if (!in_range(a.status, (long long)item.w + item.z - 1, 0, a.wk.item_cap)) return;
+  float3 tot = make_float3(0.0f, 0.0f, 0.0f);
+  float tmiss = 0.0f;
+  for (int c = 0; c < item.z; ++c) {
+    const float4 p = __ldcg(&a.wk.part[(size_t)(item.w + c) * 32 + lane]);   // written on other SMs
+    tot.x += p.x;
+    tot.y += p.y;
+    tot.z += p.z;
+    tmiss += p.w;
+  }
+  write_pixel(a, t, tot, (int)tmiss, image);
+  if (lane == 0) a.wk.st_done[item.x] = 0u;   // ready for the next launch
+}
+
 // warps take work items, instance after instance; S samples per lane at a time
 template <bool STATS, int S>
-__global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in, unsigned long long* stats) {
+__global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in, float* __restrict__ image,
+                                                                  unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
   const int lane = threadIdx.x & 31;
   Counts cnt;
@@ -1294,7 +1404,7 @@ __global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in
       float3 acc = make_float3(0.0f, 0.0f, 0.0f);
       int misses = 0;
       shade_samples<STATS, S, false>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
-      a.wk.part[(size_t)slot * 32 + lane] = make_float4(acc.x, acc.y, acc.z, (float)misses);
+      finish_item(a, t, item, slot, acc, misses, image);
     }
   }
   flush_counts<STATS>(cnt, stats);
@@ -1342,7 +1452,7 @@ __global__ void __launch_bounds__(kRenderThreads, BWD ? kBwdMinBlocks : 8) k_ove
         }
       }
     } else {
-      // the same chunks and the same order of sums as work items and k_combine_fwd
+      // the same chunks and the same order of sums as the work items and finish_item
       // would use, so a pixel's value does not depend on which path rendered it
       const int C = chunks_for(a, pk.y, t.spp);
       float3 tot = make_float3(0.0f, 0.0f, 0.0f);
@@ -1361,73 +1471,49 @@ __global__ void __launch_bounds__(kRenderThreads, BWD ? kBwdMinBlocks : 8) k_ove
       write_pixel(a, t, tot, (int)tmiss, image);
     }
   }
-  // work items of sub-tiles without a candidate list (the shaders skip them): traced
-  // ray by ray, the forward writing the item's partial sums for k_combine_fwd, the
-  // backward adding to the instance's extra sums
-  for (int inst = 0; inst < a0.n_inst; ++inst) {
-    const int ni = item_count(a0, inst), nf = front_count(a0, inst), ibase = inst_ibase(a0, inst);
-    const RenderArgs a = for_inst(a0, inst);
-    for (int it = blockIdx.x * kWarps + (threadIdx.x >> 5); it < ni; it += gridDim.x * kWarps) {
-      const int slot = ibase + item_slot(a, inst, it, nf);
-      int4 item;
-      SubTile t;
-      int2 pk;
-      if (!load_item(a, slot, item, t, pk) || t.inst != inst || pk.y >= 0) continue;
-      const Cam cam = load_cam(a.cams, t.view);
-      int s0, s1;
-      item_samples(item.y, item.z, t.spp, s0, s1);
-      if (BWD) {
-        bool live;
-        const float3 g = lane_adjoint(a, t, adjoint, live);
-        if (a.wk.det) {
-          unsigned long long* ex = a.wk.fx + (size_t)inst * 6 * a.V;
-          grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, live, g, ex, ex + 3 * a.V, cnt);
-        } else {
-          float* ex = a.wk.extra + (size_t)inst * 6 * a.V;
-          grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, live, g, ex, ex + 3 * a.V, cnt);
-        }
+  // work items of sub-tiles without a candidate list (the shaders skip them, the gather
+  // lists them): traced ray by ray, the forward finishing each item as the shader
+  // would, the backward adding to the instance's extra sums
+  const int nt = (int)min(*reinterpret_cast<volatile unsigned*>(&a0.wk.ctr[ctr_trace(a0.n_inst)]),
+                          (unsigned)a0.wk.item_cap);
+  for (int i = blockIdx.x * kWarps + (threadIdx.x >> 5); i < nt; i += gridDim.x * kWarps) {
+    const int slot = a0.wk.trace[i];
+    if (!in_range(a0.status, slot, 0, a0.wk.item_cap)) continue;
+    int4 item;
+    SubTile t;
+    int2 pk;
+    if (!load_item(a0, slot, item, t, pk) || pk.y >= 0) continue;
+    const RenderArgs a = for_inst(a0, t.inst);
+    const Cam cam = load_cam(a.cams, t.view);
+    int s0, s1;
+    item_samples(item.y, item.z, t.spp, s0, s1);
+    if (BWD) {
+      bool live;
+      const float3 g = lane_adjoint(a, t, adjoint, live);
+      if (a.wk.det) {
+        unsigned long long* ex = a.wk.fx + (size_t)t.inst * 6 * a.V;
+        grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, live, g, ex, ex + 3 * a.V, cnt);
       } else {
-        float3 acc = make_float3(0.0f, 0.0f, 0.0f);
-        int misses = 0;
-        shade_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
-        a.wk.part[(size_t)slot * 32 + (threadIdx.x & 31)] = make_float4(acc.x, acc.y, acc.z, (float)misses);
+        float* ex = a.wk.extra + (size_t)t.inst * 6 * a.V;
+        grad_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, live, g, ex, ex + 3 * a.V, cnt);
       }
+    } else {
+      float3 acc = make_float3(0.0f, 0.0f, 0.0f);
+      int misses = 0;
+      shade_samples<STATS, 1>(a, t, cam, pk.x, pk.y, s0, s1, acc, misses, cnt);
+      finish_item(a, t, item, slot, acc, misses, image);
     }
   }
   flush_counts<STATS>(cnt, stats);
-}
-
-__global__ void __launch_bounds__(kRenderThreads) k_combine_fwd(RenderArgs a, float* __restrict__ image) {
-  const int lane = threadIdx.x & 31;
-  const int nw = gridDim.x * kWarps;
-  for (int inst = 0; inst < a.n_inst; ++inst) {
-    const int n = item_count(a, inst), nf = front_count(a, inst), ibase = inst_ibase(a, inst);
-    for (int it = blockIdx.x * kWarps + (threadIdx.x >> 5); it < n; it += nw) {
-      const int4 item = a.wk.items[ibase + item_slot(a, inst, it, nf)];
-      if (item.x < 0 || item.y != 0) continue;
-      if (!in_range(a.status, item.x, 0, subtile_count(a)) ||
-          !in_range(a.status, (long long)item.w + item.z - 1, ibase, ibase + inst_icap(a, inst)))
-        continue;
-      float3 acc = make_float3(0.0f, 0.0f, 0.0f);
-      float misses = 0.0f;
-      for (int c = 0; c < item.z; ++c) {
-        float4 p = a.wk.part[(size_t)(item.w + c) * 32 + lane];
-        acc.x += p.x;
-        acc.y += p.y;
-        acc.z += p.z;
-        misses += p.w;
-      }
-      write_pixel(a, subtile(a, item.x), acc, (int)misses, image);
-    }
-  }
 }
 
 // interior term: warps take work items.  ACC selects where the gradient collects;
 // every mode adds with atomic adds whose result is not read, which retire in L2
 // without holding up the warp (float adds to shared memory cost a read and a
 // compare-and-swap loop each, and made the sums a quarter of this kernel's time):
-//   kAccPartials  each block into its own partial [6V] (L2-resident), summed in block
-//                 order by k_reduce_partials (single instance)
+//   kAccPartials  block b into partial b % nparts of `nparts` partials [6V]
+//                 (L2-resident, zeroed before the launch), summed in partial order by
+//                 k_reduce_partials (single instance)
 //   kAccDirect    every run of hits on one triangle straight into its instance's
 //                 extra [6V] (batches)
 //   kAccGlobal    meshes beyond kPartialMaxV vertices: into the instance's float64
@@ -1438,14 +1524,10 @@ constexpr int kAccPartials = 0, kAccDirect = 1, kAccGlobal = 2, kAccFixed = 3;
 template <bool STATS, int ACC, int S>
 __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(RenderArgs a_in,
                                                                              const float* __restrict__ adjoint,
-                                                                             float* __restrict__ partials,
+                                                                             float* __restrict__ partials, int nparts,
                                                                              unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
-  float* part = partials + (size_t)blockIdx.x * 6 * a0.V;
-  if (ACC == kAccPartials) {
-    for (int i = threadIdx.x; i < 6 * a0.V; i += kRenderThreads) part[i] = 0.0f;
-    __syncthreads();
-  }
+  float* part = partials + (size_t)(blockIdx.x % nparts) * 6 * a0.V;
   Counts cnt;
   for (int inst = 0; inst < a0.n_inst; ++inst) {
     const int n = item_count(a0, inst), nf = front_count(a0, inst), ibase = inst_ibase(a0, inst);
@@ -1923,6 +2005,9 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.wk.extra64 = ctx->extra64;
   a.wk.ctr = ctx->work_ctr;
   a.wk.ovf = ctx->ovf_list;
+  a.wk.trace = ctx->trace_list;
+  a.wk.st_done = ctx->st_done;
+  a.wk.cand_st = ctx->cand_st;
   a.wk.fx = ctx->acc_fx;
   a.wk.det = (o->flags & HR_DETERMINISTIC) != 0;
   a.node_stride = ctx->lim.max_F;
@@ -1978,6 +2063,12 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   }
   const int blocks = ctx->num_sms * ctx->tune.blocks_per_sm;
   tm.begin(kTimeFwdGather);
+  const int cull_blocks = ctx->num_sms * (2048 / kCullThreads);
+  if (st)
+    k_cull<true><<<cull_blocks, kCullThreads, 0, s>>>(a, image, ctx->stats);
+  else
+    k_cull<false><<<cull_blocks, kCullThreads, 0, s>>>(a, image, nullptr);
+  HR_CHECK_LAUNCH();
   if (st)
     k_gather<false, true><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, ctx->stats);
   else
@@ -1989,7 +2080,7 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
     const int S = ctx->tune.rays_per_lane;
     auto kern = st ? (S == 1 ? k_shade_fwd<true, 1> : (S == 2 ? k_shade_fwd<true, 2> : k_shade_fwd<true, 4>))
                    : (S == 1 ? k_shade_fwd<false, 1> : (S == 2 ? k_shade_fwd<false, 2> : k_shade_fwd<false, 4>));
-    kern<<<blocks, kRenderThreads, 0, s>>>(a, st ? ctx->stats : nullptr);
+    kern<<<blocks, kRenderThreads, 0, s>>>(a, image, st ? ctx->stats : nullptr);
   }
   HR_CHECK_LAUNCH();
   if (st)
@@ -1998,9 +2089,8 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
     k_overflow<false, false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, nullptr);
   HR_CHECK_LAUNCH();
   tm.end(kTimeFwdShade);
+  // the item sums are combined inside the shaders (finish_item): the slot stays, empty
   tm.begin(kTimeFwdCombine);
-  k_combine_fwd<<<blocks, kRenderThreads, 0, s>>>(a, image);
-  HR_CHECK_LAUNCH();
   tm.end(kTimeFwdCombine);
   if (tm.on) ctx->ev_ready |= 1;
   ctx->fwd_verts = verts;
@@ -2081,10 +2171,10 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
       return HR_ERR_CUDA;
     if (!det && cudaMemsetAsync(ctx->dedge, 0, sizeof(float) * 3 * V * ni, es) != cudaSuccess) return HR_ERR_CUDA;
   }
-  const auto reduce = [&](int acc, int nblocks) {
+  const auto reduce = [&](int acc, int nparts) {
     k_reduce_partials<<<dim3((6 * V + kRedEntries - 1) / kRedEntries, ni), kRedEntries * kRedGroups, 0, s>>>(
         ctx->partials, ctx->extra, acc == kAccGlobal ? ctx->extra64 : nullptr, det ? ctx->acc_fx : nullptr,
-        acc == kAccPartials ? nblocks : 0, V, d_verts, ctx->dN);
+        acc == kAccPartials ? nparts : 0, V, d_verts, ctx->dN);
   };
   if (interior) {
     // float sums up to kPartialMaxV vertices (per block, or per instance in a batch),
@@ -2104,10 +2194,14 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
                 : acc == kAccGlobal ? HR_BWD_KERNEL(kAccGlobal)
                                     : (acc == kAccDirect ? HR_BWD_KERNEL(kAccDirect) : HR_BWD_KERNEL(kAccPartials));
 #undef HR_BWD_KERNEL
-    // the block partials are sized for kBlocksPerSm blocks per SM
+    // one partial per SM (the blocks of a launch share them round-robin), zeroed first
     const int blocks = ctx->num_sms * ctx->tune.bwd_blocks_per_sm;
+    const int nparts = ctx->num_sms;
+    if (acc == kAccPartials &&
+        cudaMemsetAsync(ctx->partials, 0, sizeof(float) * 6 * V * (size_t)nparts, s) != cudaSuccess)
+      return HR_ERR_CUDA;
     tm.begin(kTimeBwdShade);
-    kern<<<blocks, kRenderThreads, 0, s>>>(a, adjoint, ctx->partials, st ? ctx->stats + kStatsPer : nullptr);
+    kern<<<blocks, kRenderThreads, 0, s>>>(a, adjoint, ctx->partials, nparts, st ? ctx->stats + kStatsPer : nullptr);
     HR_CHECK_LAUNCH();
     if (st)
       k_overflow<true, true><<<blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, ctx->stats + kStatsPer);
@@ -2117,7 +2211,7 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     tm.end(kTimeBwdShade);
     if (!det) {
       tm.begin(kTimeBwdReduce);
-      reduce(acc, blocks);
+      reduce(acc, nparts);
       HR_CHECK_LAUNCH();
       tm.end(kTimeBwdReduce);
     }

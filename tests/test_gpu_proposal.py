@@ -54,3 +54,46 @@ def test_proposal_gain_on_heldout_instances():
     assert k_prop < k_plain, (k_prop, k_plain)
     print(f"initial {mean_plain[0]:.2f} mm -> after proposals {mean_prop[0]:.2f} mm; "
           f"iterations to 1 mm: plain {k_plain}, with proposals {k_prop}")
+
+
+def test_rig_views_from_a_finer_ring():
+    """The proposal's inputs for instances captured by another rig: the views at the
+    rig's cameras, reduced by f x f box means (masks by block maxima) with their
+    intrinsics scaled by 1/f -- checked against the definitions on the host."""
+    require_gpu()
+    from paper_2107_05509_gb300 import binding as B
+    from paper_2107_05509_gb300 import pipeline as P
+    from paper_2107_05509_gb300 import proposal as PR
+    rng = np.random.default_rng(3)
+    # 16 views at 512^2 on the rig's ring: every second one is a rig camera, f = 2
+    cfgs = [dataclasses.replace(PR.RIG, views=16, width=512, height=512, seed=50 + i,
+                                azimuths_deg=tuple(22.5 * k for k in range(16))) for i in range(2)]
+    hv = hand().v_template.mean(0)
+    cams = np.concatenate([I.pack_cameras(I.make_cameras(c, hv)) for c in cfgs])
+    P_ = sum(c.views * c.width * c.height for c in cfgs)
+    bg = rng.random((P_, 3), dtype=np.float32)
+    obs = rng.random((P_, 3), dtype=np.float32)
+    mask = (rng.random(P_) < 0.1).astype(np.uint8)
+    t = lambda a: torch.as_tensor(a, device="cuda")
+    views = P.BatchViews(cams=t(cams), background=t(bg), observed=t(obs), mask=t(mask))
+    vo = np.cumsum([0] + [c.views for c in cfgs])
+    po = np.cumsum([0] + [c.views * c.width * c.height for c in cfgs])
+    rv = PR.rig_views(cfgs, views, vo, po)
+    assert rv.cams.shape == (16, I.CAM_FLOATS) and rv.background.shape == (16 * 256 * 256, 3)
+    for i in range(2):
+        for j in range(8):
+            k = 2 * j                                   # azimuth 45 j
+            src = vo[i] + k
+            c = cams[src].copy()
+            c[0:4] /= 2
+            assert np.allclose(rv.cams[8 * i + j].cpu().numpy(), c)
+            sl = slice(po[i] + k * 512 * 512, po[i] + (k + 1) * 512 * 512)
+            ref = obs[sl].reshape(256, 2, 256, 2, 3).mean(axis=(1, 3))
+            got = rv.observed[(8 * i + j) * 256 * 256:(8 * i + j + 1) * 256 * 256].cpu().numpy().reshape(256, 256, 3)
+            assert np.allclose(got, ref, rtol=0, atol=1e-6)
+            mref = mask[sl].reshape(256, 2, 256, 2).max(axis=(1, 3))
+            mgot = rv.mask[(8 * i + j) * 256 * 256:(8 * i + j + 1) * 256 * 256].cpu().numpy().reshape(256, 256)
+            assert np.array_equal(mgot, mref)
+    # a resolution that is not a multiple of the rig's is refused
+    with pytest.raises(ValueError):
+        PR.rig_views([dataclasses.replace(cfgs[0], width=500)], views, vo, po)
