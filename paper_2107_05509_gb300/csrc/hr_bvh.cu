@@ -79,6 +79,42 @@ __device__ __forceinline__ Box load_union(const Node* nodes, int p) {
   return b;
 }
 
+// unit area-weighted normal of vertex v (incident faces in ascending order, float32
+// decision arithmetic) and its length, into normals[v] and normal_len[v]
+__device__ __forceinline__ void vertex_normal(int v, const float* __restrict__ verts, const int* __restrict__ faces,
+                                              const int* __restrict__ vf_off, const int* __restrict__ vf_faces,
+                                              int V, int F, float* __restrict__ normals,
+                                              float* __restrict__ normal_len, int* status) {
+  float3 m = make_float3(0.0f, 0.0f, 0.0f);
+  int k0 = vf_off[v], k1 = vf_off[v + 1];
+  if (k0 < 0 || k1 < k0 || k1 > 3 * F) {
+    set_status(status, kStatusBadModel);
+    k1 = k0;
+  }
+  for (int k = k0; k < k1; ++k) {
+    int f = vf_faces[k];
+    if (f < 0 || f >= F) {
+      set_status(status, kStatusBadModel);
+      continue;
+    }
+    const int i0 = faces[3 * f], i1 = faces[3 * f + 1], i2 = faces[3 * f + 2];
+    if (i0 < 0 || i0 >= V || i1 < 0 || i1 >= V || i2 < 0 || i2 >= V) {
+      set_status(status, kStatusBadModel);
+      continue;
+    }
+    float3 a = ld3(verts + 3 * i0), b = ld3(verts + 3 * i1), c = ld3(verts + 3 * i2);
+    float3 cf = dcross(dsub(b, a), dsub(c, a));
+    m = make_float3(__fadd_rn(m.x, cf.x), __fadd_rn(m.y, cf.y), __fadd_rn(m.z, cf.z));
+  }
+  float len = __fsqrt_rn(ddot(m, m));
+  float3 n = len > 0.0f ? make_float3(__fdiv_rn(m.x, len), __fdiv_rn(m.y, len), __fdiv_rn(m.z, len))
+                        : make_float3(0.0f, 0.0f, 0.0f);
+  normals[3 * v] = n.x;
+  normals[3 * v + 1] = n.y;
+  normals[3 * v + 2] = n.z;
+  normal_len[v] = len;
+}
+
 // shared memory: keys [P] u64, parent [2F] int, visit flags [F] int, then (when
 // `snodes`) the max(F - 1, 1) nodes.  One block per instance: blockIdx.x selects the instance's
 // vertices ([V][3] at blockIdx.x * 3V), nodes ([node_stride] per instance) and
@@ -90,7 +126,11 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
                                                              float4* __restrict__ tris_all,
                                                              int* __restrict__ parent_all, int* __restrict__ valid,
                                                              const uint32_t* iter_dev, int rebuild_every,
-                                                             int* status, const int* __restrict__ active) {
+                                                             int* status, const int* __restrict__ active,
+                                                             const int* __restrict__ vf_off,
+                                                             const int* __restrict__ vf_faces,
+                                                             float* __restrict__ normals_all,
+                                                             float* __restrict__ normal_len_all) {
   extern __shared__ unsigned long long smem_keys[];
   if (active && !active[blockIdx.x]) return;   // a retired instance of a batch
   unsigned long long* keys = smem_keys;
@@ -114,11 +154,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
   const bool refit = rebuild_every > 1 && iter_dev && valid[blockIdx.x] == 1 && (*iter_dev % rebuild_every) != 0;
   if (refit) {
     const int nn = F > 1 ? F - 1 : 1;
-    if (snodes) {
-      const float4* src = reinterpret_cast<const float4*>(gnodes);
-      float4* dst = reinterpret_cast<float4*>(nodes);
-      for (int i = tid; i < 4 * nn; i += blockDim.x) dst[i] = src[i];
-    }
+    if (snodes)   // the refit rewrites every box: only the child indices are read
+      for (int i = tid; i < nn; i += blockDim.x) nodes[i].d = gnodes[i].d;
     for (int i = tid; i < 2 * F; i += blockDim.x) parent[i] = gparent[i];
     for (int i = tid; i < F; i += blockDim.x) flags[i] = 0;
     __syncthreads();
@@ -249,60 +286,94 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
 
   }
   // 5. triangle records and leaf boxes, then the bottom-up refit (a refit reads the
-  // leaf order from the previous records)
-  for (int k = tid; k < F; k += blockDim.x) {
-    int tri = refit ? __float_as_int(tris[3 * k + 2].y) : (int)(keys[k] & 0xffffffffull);
-    if (tri < 0 || tri >= F) {   // a corrupt record: skip it (reported)
-      set_status(status, kStatusIndex);
-      continue;
+  // leaf order from the previous records).  A thread's leaves (two at F <= 2048) load
+  // their triangles together before either walks up the tree.
+  constexpr int kLeafPer = 2;
+  for (int k0 = tid; k0 < F; k0 += kLeafPer * blockDim.x) {
+    int tri[kLeafPer];
+    float3 v0[kLeafPer], v1[kLeafPer], v2[kLeafPer];
+#pragma unroll
+    for (int j = 0; j < kLeafPer; ++j) {
+      const int k = k0 + j * blockDim.x;
+      tri[j] = -1;
+      if (k >= F) continue;
+      tri[j] = refit ? __float_as_int(tris[3 * k + 2].y) : (int)(keys[k] & 0xffffffffull);
     }
-    float3 v0 = ld3(verts + 3 * faces[3 * tri]);
-    float3 v1 = ld3(verts + 3 * faces[3 * tri + 1]);
-    float3 v2 = ld3(verts + 3 * faces[3 * tri + 2]);
-    float3 e1 = dsub(v1, v0), e2 = dsub(v2, v0);
-    tris[3 * k + 0] = make_float4(v0.x, v0.y, v0.z, e1.x);
-    tris[3 * k + 1] = make_float4(e1.y, e1.z, e2.x, e2.y);
-    tris[3 * k + 2] = make_float4(e2.z, __int_as_float(tri), 0.0f, 0.0f);
-    Box b;
-    float amax = 0.0f;
-    float p0[3] = {v0.x, v0.y, v0.z}, p1[3] = {v1.x, v1.y, v1.z}, p2[3] = {v2.x, v2.y, v2.z};
-    for (int c = 0; c < 3; ++c) {
-      b.lo[c] = fminf(p0[c], fminf(p1[c], p2[c]));
-      b.hi[c] = fmaxf(p0[c], fmaxf(p1[c], p2[c]));
-      amax = fmaxf(amax, fmaxf(fabsf(b.lo[c]), fabsf(b.hi[c])));
+#pragma unroll
+    for (int j = 0; j < kLeafPer; ++j) {
+      const int k = k0 + j * blockDim.x;
+      if (k >= F) continue;
+      if (tri[j] < 0 || tri[j] >= F) {   // a corrupt record: skip it (reported)
+        set_status(status, kStatusIndex);
+        tri[j] = -1;
+        continue;
+      }
+      v0[j] = ld3(verts + 3 * faces[3 * tri[j]]);
+      v1[j] = ld3(verts + 3 * faces[3 * tri[j] + 1]);
+      v2[j] = ld3(verts + 3 * faces[3 * tri[j] + 2]);
     }
-    float pad = 1e-6f + 1e-5f * amax;
-    for (int c = 0; c < 3; ++c) {
-      b.lo[c] -= pad;
-      b.hi[c] += pad;
-    }
-    int p = parent[F + k];
-    int slot = (nodes[p].d.x == ~k) ? 0 : 1;
-    if (F == 1) {
-      store_slot(nodes, 0, 0, b);
-      store_slot(nodes, 0, 1, b);
-      continue;
-    }
-    store_slot(nodes, p, slot, b);
-    __threadfence_block();
-    for (int up = 0; up < F; ++up) {   // a well-formed tree is at most F - 1 levels deep
-      if (atomicAdd(&flags[p], 1) == 0) break;   // the sibling is not done yet
+#pragma unroll 1
+    for (int j = 0; j < kLeafPer; ++j) {
+      const int k = k0 + j * blockDim.x;
+      if (k >= F || tri[j] < 0) continue;
+      float3 e1 = dsub(v1[j], v0[j]), e2 = dsub(v2[j], v0[j]);
+      tris[3 * k + 0] = make_float4(v0[j].x, v0[j].y, v0[j].z, e1.x);
+      tris[3 * k + 1] = make_float4(e1.y, e1.z, e2.x, e2.y);
+      tris[3 * k + 2] = make_float4(e2.z, __int_as_float(tri[j]), 0.0f, 0.0f);
+      Box b;
+      float amax = 0.0f;
+      float p0[3] = {v0[j].x, v0[j].y, v0[j].z}, p1[3] = {v1[j].x, v1[j].y, v1[j].z},
+            p2[3] = {v2[j].x, v2[j].y, v2[j].z};
+      for (int c = 0; c < 3; ++c) {
+        b.lo[c] = fminf(p0[c], fminf(p1[c], p2[c]));
+        b.hi[c] = fmaxf(p0[c], fmaxf(p1[c], p2[c]));
+        amax = fmaxf(amax, fmaxf(fabsf(b.lo[c]), fabsf(b.hi[c])));
+      }
+      float pad = 1e-6f + 1e-5f * amax;
+      for (int c = 0; c < 3; ++c) {
+        b.lo[c] -= pad;
+        b.hi[c] += pad;
+      }
+      int p = parent[F + k];
+      int slot = (nodes[p].d.x == ~k) ? 0 : 1;
+      if (F == 1) {
+        store_slot(nodes, 0, 0, b);
+        store_slot(nodes, 0, 1, b);
+        continue;
+      }
+      store_slot(nodes, p, slot, b);
       __threadfence_block();
-      Box u = load_union(nodes, p);
-      int gp = parent[p];
-      if (gp < 0) break;                          // p is the root
-      int gslot = (nodes[gp].d.x == p) ? 0 : 1;
-      store_slot(nodes, gp, gslot, u);
-      __threadfence_block();
-      p = gp;
+      for (int up = 0; up < F; ++up) {   // a well-formed tree is at most F - 1 levels deep
+        if (atomicAdd(&flags[p], 1) == 0) break;   // the sibling is not done yet
+        __threadfence_block();
+        Box u = load_union(nodes, p);
+        int gp = parent[p];
+        if (gp < 0) break;                          // p is the root
+        int gslot = (nodes[gp].d.x == p) ? 0 : 1;
+        store_slot(nodes, gp, gslot, u);
+        __threadfence_block();
+        p = gp;
+      }
     }
   }
+  // 6. the shading normals of the same vertices (threads that finished their walks
+  // first start on them)
+  if (normals_all) {
+    float* normals = normals_all + (size_t)blockIdx.x * 3 * V;
+    float* normal_len = normal_len_all + (size_t)blockIdx.x * V;
+    for (int v = tid; v < V; v += blockDim.x)
+      vertex_normal(v, verts, faces, vf_off, vf_faces, V, F, normals, normal_len, status);
+  }
   __syncthreads();
-  if (snodes) {
+  if (snodes) {   // a refit changed only the boxes (the first three float4 of a node)
     const int nn = F > 1 ? F - 1 : 1;
     const float4* src = reinterpret_cast<const float4*>(nodes);
     float4* dst = reinterpret_cast<float4*>(gnodes);
-    for (int i = tid; i < 4 * nn; i += blockDim.x) dst[i] = src[i];
+    if (refit) {
+      for (int i = tid; i < 3 * nn; i += blockDim.x) dst[4 * (i / 3) + i % 3] = src[4 * (i / 3) + i % 3];
+    } else {
+      for (int i = tid; i < 4 * nn; i += blockDim.x) dst[i] = src[i];
+    }
   }
   if (!refit) {   // keep the topology for later refits
     for (int i = tid; i < 2 * F; i += blockDim.x) gparent[i] = parent[i];
@@ -319,37 +390,8 @@ __global__ void k_vertex_normals(const float* __restrict__ verts_all, const int*
                                  const int* __restrict__ active) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V || (active && !active[blockIdx.y])) return;
-  const float* verts = verts_all + (size_t)blockIdx.y * 3 * V;
-  float* normals = normals_all + (size_t)blockIdx.y * 3 * V;
-  float* normal_len = normal_len_all + (size_t)blockIdx.y * V;
-  float3 m = make_float3(0.0f, 0.0f, 0.0f);
-  int k0 = vf_off[v], k1 = vf_off[v + 1];
-  if (k0 < 0 || k1 < k0 || k1 > 3 * F) {
-    set_status(status, kStatusBadModel);
-    k1 = k0;
-  }
-  for (int k = k0; k < k1; ++k) {
-    int f = vf_faces[k];
-    if (f < 0 || f >= F) {
-      set_status(status, kStatusBadModel);
-      continue;
-    }
-    const int i0 = faces[3 * f], i1 = faces[3 * f + 1], i2 = faces[3 * f + 2];
-    if (i0 < 0 || i0 >= V || i1 < 0 || i1 >= V || i2 < 0 || i2 >= V) {
-      set_status(status, kStatusBadModel);
-      continue;
-    }
-    float3 a = ld3(verts + 3 * i0), b = ld3(verts + 3 * i1), c = ld3(verts + 3 * i2);
-    float3 cf = dcross(dsub(b, a), dsub(c, a));
-    m = make_float3(__fadd_rn(m.x, cf.x), __fadd_rn(m.y, cf.y), __fadd_rn(m.z, cf.z));
-  }
-  float len = __fsqrt_rn(ddot(m, m));
-  float3 n = len > 0.0f ? make_float3(__fdiv_rn(m.x, len), __fdiv_rn(m.y, len), __fdiv_rn(m.z, len))
-                        : make_float3(0.0f, 0.0f, 0.0f);
-  normals[3 * v] = n.x;
-  normals[3 * v + 1] = n.y;
-  normals[3 * v + 2] = n.z;
-  normal_len[v] = len;
+  vertex_normal(v, verts_all + (size_t)blockIdx.y * 3 * V, faces, vf_off, vf_faces, V, F,
+                normals_all + (size_t)blockIdx.y * 3 * V, normal_len_all + (size_t)blockIdx.y * V, status);
 }
 
 
@@ -689,14 +731,21 @@ int launch_update_bvh(Context* ctx, const hr_model* m, const float* verts, const
     if (cudaMemsetAsync(ctx->bvh_valid, 0, sizeof(int) * ctx->n_inst, s) != cudaSuccess) return HR_ERR_CUDA;
     ctx->bvh_faces = m->faces;
   }
+  // the vertex normals need only the vertices: they are computed on the context's side
+  // stream beside the build (one block per instance), joined before the call returns
+  // (in a captured graph, two parallel branches)
+  if (cudaEventRecord(ctx->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0) != cudaSuccess)
+    return HR_ERR_CUDA;
+  k_vertex_normals<<<dim3((V + 255) / 256, ctx->n_inst), 256, 0, ctx->side>>>(
+      verts, m->faces, m->vf_offsets, m->vf_faces, V, F, ctx->normals, ctx->normal_len, ctx->status, ctx->active);
+  HR_CHECK_LAUNCH();
   k_build_bvh<<<ctx->n_inst, kBuildThreads, smem, s>>>(verts, m->faces, F, V, P, ctx->lim.max_F, snodes,
                                                        ctx->nodes, ctx->tris, ctx->bvh_parent, ctx->bvh_valid,
-                                                       iter_dev, rebuild_every, ctx->status, ctx->active);
+                                                       iter_dev, rebuild_every, ctx->status, ctx->active,
+                                                       nullptr, nullptr, nullptr, nullptr);
   HR_CHECK_LAUNCH();
-  k_vertex_normals<<<dim3((V + 255) / 256, ctx->n_inst), 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces,
-                                                                      V, F, ctx->normals, ctx->normal_len,
-                                                                      ctx->status, ctx->active);
-  HR_CHECK_LAUNCH();
+  if (cudaEventRecord(ctx->ev_join, ctx->side) != cudaSuccess || cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess)
+    return HR_ERR_CUDA;
   ctx->V = V;
   ctx->F = F;
   ++ctx->bvh_gen;
