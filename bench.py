@@ -58,7 +58,8 @@ KERNEL_NAMES = {"fwd_gather": "k_gather<fwd>", "fwd_shade": "k_shade_fwd", "bwd_
 # DRAM bytes (read + write) per launch from the ncu capture summarised under profiles/,
 # with the hash of the render kernels' sources at that capture: a kernel whose source
 # has changed since reports no traffic
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"k_shade_bwd": (5916416, "d77a279df24cfb8d"), "k_shade_fwd": (4424960, "d77a279df24cfb8d"),
+               "k_gather<fwd>": (2526208, "d77a279df24cfb8d"), "k_edge_samples": (2774528, "d77a279df24cfb8d")}
 NCU_TRAFFIC_SOURCES = ("paper_2107_05509_gb300/csrc/hr_render.cu", "paper_2107_05509_gb300/csrc/hr_device.cuh")
 
 
