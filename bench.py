@@ -486,15 +486,17 @@ def _first_at_or_below(err_mm, thr=1.0):
     return int(ok[0]) if ok.size else -1
 
 
-def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3, texture=None):
+def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3, texture=None, proposal_layout="rig"):
     """Refine the instances of `cfgs` from the same initial estimates with the same
     sample streams: plain per-instance refinement through the single-instance calls,
     instance after instance (one CUDA graph each); all instances together through the
     batch calls (one CUDA graph per iteration); and, with `learned` parameters, the
-    batch preceded by the learned proposal steps (computed on the proposal rig's views:
-    the instances' own views when they are the rig's, else the rig's cameras among
-    them at reduced resolution).  The mean vertex error epsilon_v (Section 4.1) is
-    recorded on the device every iteration.  texture: the model's albedo texture."""
+    batch preceded by the learned proposal steps (proposal_layout "rig": computed on
+    the proposal rig's views -- the instances' own views when they are the rig's, else
+    the rig's cameras among them at reduced resolution; "ring": the ring network on
+    each instance's views view_slots(k) area-resampled to 256 x 256).  The mean vertex
+    error epsilon_v (Section 4.1) is recorded on the device every iteration.  texture:
+    the model's albedo texture."""
     import torch
 
     from paper_2107_05509_gb300 import binding as B
@@ -574,7 +576,8 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3, text
     res_learned = res_learned_r = None
     if learned is not None:
         from paper_2107_05509_gb300 import proposal as PR
-        rig_layout = all((c.views, c.width, c.height) == (PR.RIG.views, PR.RIG.width, PR.RIG.height) for c in cfgs)
+        rig_layout = proposal_layout == "rig" and all(
+            (c.views, c.width, c.height) == (PR.RIG.views, PR.RIG.width, PR.RIG.height) for c in cfgs)
         if rig_layout:
             prop = PR.Proposer(R, learned, steps=proposal_steps)
 
@@ -582,10 +585,11 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3, text
                 prop.r = refiner
                 prop.run()
         else:
-            # the proposal steps run on the rig's views of these instances (a batch of
-            # that layout); the refinement continues from the chosen candidates
-            rviews = PR.rig_views(cfgs, views, bt.view_offsets, bt.pixel_offsets)
-            rbt = B.Batch(hand.V, hand.F, hand.E, [(PR.RIG.views, PR.RIG.width, PR.RIG.height, PR.RIG.spp,
+            # the proposal steps run on the network's views of these instances (a batch
+            # of that layout); the refinement continues from the chosen candidates
+            make = PR.rig_views if proposal_layout == "rig" else PR.ring_views
+            rviews = make(cfgs, views, bt.view_offsets, bt.pixel_offsets)
+            rbt = B.Batch(hand.V, hand.F, hand.E, [(PR.SLOTS, PR.NET_SIZE, PR.NET_SIZE, PR.RIG.spp,
                                                     PR.RIG.edge_samples, i) for i in range(n)])
             RR = P.BatchRefiner(model, rbt, rviews, device=dev, texture=texture)
             prop = PR.Proposer(RR, learned, steps=proposal_steps)
@@ -686,7 +690,8 @@ def refine_compare(cfgs, model, dev, iters, learned=None, proposal_steps=3, text
 
 def run_refinement(args, dev):
     """Time-to-1 mm on three batched workloads: (1) heterogeneous instances (4-16 views
-    at 256x256 / 512x384 / 512x512, 8-32 spp): plain per-instance vs batched; (2) the
+    at 256x256 / 512x384 / 512x512, 8-32 spp): plain per-instance vs batched vs batched
+    with the ring network's proposal steps first; (2) the
     learned proposal's rig (8 views at 256x256, 16 spp): plain vs batched vs batched
     with the learned proposal steps first; (3) instances of the scale workload: plain
     vs batched vs batched with the learned proposal steps first.  Each batched pipeline
@@ -702,8 +707,13 @@ def run_refinement(args, dev):
     n, iters = args.batch_instances, args.refine_iters
     hand = I.make_hand(0)
     model = B.Model(hand, device=dev)
-    het = refine_compare(I.batch_configs(n), model, dev, iters)
+    ring, ring_meta = PR.load_weights(PR.WEIGHTS_RING)
+    het = refine_compare(I.batch_configs(n), model, dev, iters, learned=ring, proposal_layout="ring")
     het["workload"] = f"batch-{n}x(4-16 views, 256x256|512x384|512x512, 8-32 spp, 4096 edge samples/view)"
+    het["proposal"] = ("ring network: each instance's views view_slots(k) (8 of them, spread over its ring, "
+                       "repeated when it has fewer) area-resampled to 256x256, intrinsics scaled per axis")
+    het["proposal_training"] = {k: ring_meta[k] for k in ("pairs", "steps", "seconds", "layout", "heldout_eps_v_mm")
+                                if k in ring_meta}
     rig = [dataclasses.replace(PR.RIG, seed=PR.RIG.seed + 100 + i, name=f"{PR.RIG.name}-{i}") for i in range(n)]
     learned, meta = PR.load_weights()
     lr = refine_compare(rig, model, dev, iters, learned=learned)

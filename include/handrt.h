@@ -477,6 +477,19 @@ int hr_retire_plateau(const float* loss, int n, float rel_tol, int patience, flo
 int hr_box_downsample(const float* src, int N, int H, int W, int f, float* dst, hr_stream stream);
 int hr_mask_downsample(const uint8_t* src, int N, int H, int W, int f, uint8_t* dst, hr_stream stream);
 
+/* Area resampling to the proposal network's grid from views of any size (the
+ * heterogeneous batch's 512 x 384 views become 256 x 256 with anisotropic pixels):
+ * hr_area_resample writes into device float[N][Ho][Wo][3] the overlap-weighted mean
+ * of device float[N][H][W][3] over each output pixel's footprint
+ * [x W/Wo, (x+1) W/Wo) x [y H/Ho, (y+1) H/Ho) (pixel (x, y) of an image covers
+ * [x, x+1) x [y, y+1), so a camera's fx, cx scale by Wo/W and fy, cy by Ho/H);
+ * integer factors give the box means of hr_box_downsample.  hr_mask_resample writes
+ * the maximum of uint8[N][H][W] masks over the input pixels each output pixel
+ * overlaps.  Sizes 1 .. 65536 and src != dst, else HR_ERR_ARG (the two buffers must
+ * not overlap at all; only equality is checked); asynchronous. */
+int hr_area_resample(const float* src, int N, int H, int W, float* dst, int Ho, int Wo, hr_stream stream);
+int hr_mask_resample(const uint8_t* src, int N, int H, int W, uint8_t* dst, int Ho, int Wo, hr_stream stream);
+
 /* BF16 matrix product on the tensor cores (tcgen05, float32 accumulation), the
  * building block of the learned proposal network:
  *   C[M][N] = act(A[M][K] B[N][K]^T + bias[N]),  act = ReLU when relu != 0.

@@ -47,7 +47,7 @@ EXPORTS = ("hr_context_create", "hr_context_destroy", "hr_skin", "hr_skin_bwd", 
            "hr_skin_joints", "hr_skin_bwd_joints", "hr_joint_prior", "hr_colour_map", "hr_colour_map_bwd",
            "hr_edges", "hr_edge_loss", "hr_model_check",
            "hr_batch_set_active", "hr_retire_converged", "hr_retire_plateau", "hr_box_downsample",
-           "hr_mask_downsample")
+           "hr_mask_downsample", "hr_area_resample", "hr_mask_resample")
 
 
 class HandrtError(RuntimeError):
@@ -110,6 +110,8 @@ def lib():
             "hr_batch_set_active": [P, P],
             "hr_box_downsample": [P, I, I, I, I, P, P],
             "hr_mask_downsample": [P, I, I, I, I, P, P],
+            "hr_area_resample": [P, I, I, I, P, I, I, P],
+            "hr_mask_resample": [P, I, I, I, P, I, I, P],
             "hr_retire_converged": [P, P, I, I, F, P, P, I, P],
             "hr_retire_plateau": [P, I, F, I, P, P, P, P, I, P],
             "hr_build_bvh": [P, P, P, P],
@@ -575,6 +577,24 @@ def hr_mask_downsample(src, f, dst, stream=None):
     assert src.dtype == torch.uint8 and dst.dtype == torch.uint8
     N, H, W = src.shape
     _check("hr_mask_downsample", lib().hr_mask_downsample(_ptr(src), N, H, W, int(f), _ptr(dst), _stream(stream)))
+
+
+def hr_area_resample(src, dst, stream=None):
+    """src: device float [N][H][W][3]; dst: [N][Ho][Wo][3] area means over each output
+    pixel's footprint."""
+    N, H, W, _ = src.shape
+    No, Ho, Wo, _ = dst.shape
+    assert No == N and src.is_contiguous() and dst.is_contiguous()
+    _check("hr_area_resample", lib().hr_area_resample(_f32(src), N, H, W, _f32(dst), Ho, Wo, _stream(stream)))
+
+
+def hr_mask_resample(src, dst, stream=None):
+    """src: device uint8 [N][H][W]; dst: [N][Ho][Wo] maxima over each footprint."""
+    assert src.dtype == torch.uint8 and dst.dtype == torch.uint8
+    N, H, W = src.shape
+    No, Ho, Wo = dst.shape
+    assert No == N and src.is_contiguous() and dst.is_contiguous()
+    _check("hr_mask_resample", lib().hr_mask_resample(_ptr(src), N, H, W, _ptr(dst), Ho, Wo, _stream(stream)))
 
 
 def hr_vertex_mse(verts, ref, loss, d_verts=None, stream=None):

@@ -301,6 +301,22 @@ int hr_mask_downsample(const uint8_t* src, int N, int H, int W, int f, uint8_t* 
   return hr::launch_mask_downsample(src, N, H, W, f, dst, (cudaStream_t)stream);
 }
 
+static bool resample_args_ok(const void* src, int N, int H, int W, int Ho, int Wo, const void* dst) {
+  return src && dst && src != dst && N >= 1 && H >= 1 && W >= 1 && Ho >= 1 && Wo >= 1 && H <= (1 << 16) && W <= (1 << 16) &&
+         Ho <= (1 << 16) && Wo <= (1 << 16) && (long long)N * H * W <= (1ll << 40) &&
+         (long long)N * Ho * Wo <= (1ll << 40);
+}
+
+int hr_area_resample(const float* src, int N, int H, int W, float* dst, int Ho, int Wo, hr_stream stream) {
+  if (!resample_args_ok(src, N, H, W, Ho, Wo, dst)) return HR_ERR_ARG;
+  return hr::launch_area_resample(src, N, H, W, Ho, Wo, dst, (cudaStream_t)stream);
+}
+
+int hr_mask_resample(const uint8_t* src, int N, int H, int W, uint8_t* dst, int Ho, int Wo, hr_stream stream) {
+  if (!resample_args_ok(src, N, H, W, Ho, Wo, dst)) return HR_ERR_ARG;
+  return hr::launch_mask_resample(src, N, H, W, Ho, Wo, dst, (cudaStream_t)stream);
+}
+
 int hr_batch_layout(hr_context* ctx, int32_t* view_offsets, int64_t* pixel_offsets) {
   Context* c = reinterpret_cast<Context*>(ctx);
   if (!c || !c->vt || !view_offsets || !pixel_offsets) return HR_ERR_ARG;

@@ -48,6 +48,8 @@ int launch_retire_plateau(const float* loss, int n, float rel_tol, int patience,
                           float* lr_scale, int per, cudaStream_t s);
 int launch_box_downsample(const float* src, int N, int H, int W, int f, float* dst, cudaStream_t s);
 int launch_mask_downsample(const uint8_t* src, int N, int H, int W, int f, uint8_t* dst, cudaStream_t s);
+int launch_area_resample(const float* src, int N, int H, int W, int Ho, int Wo, float* dst, cudaStream_t s);
+int launch_mask_resample(const uint8_t* src, int N, int H, int W, int Ho, int Wo, uint8_t* dst, cudaStream_t s);
 int launch_vertex_mse(const float* a, const float* b, int V, int n, float* loss, float* grad, cudaStream_t s);
 int launch_add_noise(float* img, long long n, float sigma, uint64_t seed, cudaStream_t s);
 int launch_select_best(const float* cand, const float* losses, int K, int n, float* out, int* chosen,

@@ -540,6 +540,73 @@ __global__ void k_mask_downsample(const uint8_t* __restrict__ src, long long n_o
   dst[i] = m;
 }
 
+// Area resampling of [N][H][W][3] images to [N][Ho][Wo][3] (any sizes): output pixel
+// (x, y) covers input [x W / Wo, (x + 1) W / Wo) x [y H / Ho, (y + 1) H / Ho) and is
+// the overlap-weighted mean of the input pixels there.  Measured in units of 1/Wo
+// (1/Ho) of an input pixel the overlaps are integers, so the weights are exact; the
+// sum runs over input rows, then columns, in increasing order.  The mask version takes
+// the maximum over the input pixels with a positive overlap.
+__device__ __forceinline__ long long area_overlap(long long o, long long n_in, long long n_out, long long k) {
+  // [o n_in, (o + 1) n_in) against input pixel k's [k n_out, (k + 1) n_out)
+  return min((o + 1) * n_in, (k + 1) * n_out) - max(o * n_in, k * n_out);
+}
+
+__global__ void k_area_resample(const float* __restrict__ src, long long n_out, int H, int W, int Ho, int Wo,
+                                float* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_out) return;
+  const int c = (int)(i % 3);
+  const long long px = i / 3;
+  const int x = (int)(px % Wo);
+  const long long r = px / Wo;
+  const int y = (int)(r % Ho);
+  const long long v = r / Ho;
+  const long long y_lo = (long long)y * H / Ho, x_lo = (long long)x * W / Wo;
+  float acc = 0.0f;
+  for (long long iy = y_lo; iy < H && iy * Ho < (long long)(y + 1) * H; ++iy) {
+    const long long oy = area_overlap(y, H, Ho, iy);
+    if (oy <= 0) continue;
+    const float* row = src + ((v * H + iy) * W) * 3 + c;
+    for (long long ix = x_lo; ix < W && ix * Wo < (long long)(x + 1) * W; ++ix) {
+      const long long ox = area_overlap(x, W, Wo, ix);
+      if (ox > 0) acc = fmaf((float)(oy * ox), row[ix * 3], acc);
+    }
+  }
+  dst[i] = acc / ((float)H * (float)W);
+}
+
+__global__ void k_mask_resample(const uint8_t* __restrict__ src, long long n_out, int H, int W, int Ho, int Wo,
+                                uint8_t* __restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_out) return;
+  const int x = (int)(i % Wo);
+  const long long r = i / Wo;
+  const int y = (int)(r % Ho);
+  const long long v = r / Ho;
+  const long long y_lo = (long long)y * H / Ho, x_lo = (long long)x * W / Wo;
+  uint8_t m = 0;
+  for (long long iy = y_lo; iy < H && iy * Ho < (long long)(y + 1) * H; ++iy) {
+    if (area_overlap(y, H, Ho, iy) <= 0) continue;
+    for (long long ix = x_lo; ix < W && ix * Wo < (long long)(x + 1) * W; ++ix)
+      if (area_overlap(x, W, Wo, ix) > 0) m = max(m, src[(v * H + iy) * W + ix]);
+  }
+  dst[i] = m;
+}
+
+int launch_area_resample(const float* src, int N, int H, int W, int Ho, int Wo, float* dst, cudaStream_t s) {
+  const long long n = (long long)N * Ho * Wo * 3;
+  k_area_resample<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, n, H, W, Ho, Wo, dst);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
+int launch_mask_resample(const uint8_t* src, int N, int H, int W, int Ho, int Wo, uint8_t* dst, cudaStream_t s) {
+  const long long n = (long long)N * Ho * Wo;
+  k_mask_resample<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, n, H, W, Ho, Wo, dst);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
 int launch_box_downsample(const float* src, int N, int H, int W, int f, float* dst, cudaStream_t s) {
   const long long n = (long long)N * (H / f) * (W / f) * 3;
   k_box_downsample<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, n, H / f, W / f, f, dst);

@@ -5,8 +5,13 @@ this library's renderer generates, and used for the first updates of a refinemen
 with the photometric loss deciding per instance whether a proposal is kept -- the
 plain method stays the fallback and the judge of its error.
 
-Training pairs (the training rig: 8 views of 256 x 256 on a ring at 0.6 m, elevation
-30 degrees): ground truth h ~ pose N(0, 0.4 rad) clipped to +-1.2, shape N(0, 1);
+Training pairs, in one of two camera layouts: "rig", the training rig (8 views of
+256 x 256 on a ring at 0.6 m, elevation 30 degrees, azimuths 45 k); or "ring", the
+views of a random ring of 4-16 cameras (elevation 30 degrees, evenly spaced from a
+random start azimuth, native resolution 256 x 256, 512 x 384 or 512 x 512) placed in
+the network's 8 slots by view_slots and area-resampled to 256 x 256 (a 512 x 384
+view's pixels become anisotropic: fy scales by 256/384, fx by 256/512).  Each pair's
+ground truth h ~ pose N(0, 0.4 rad) clipped to +-1.2, shape N(0, 1);
 estimate h0 = h + u (pose and root rotation N(0, 0.1 rad), shape N(0, 0.5),
 translation N(0, 5 mm)) with u ~ U(0.15, 1) per pair.  Each step renders the ground
 truth over a fresh noise plate (observation + N(0, 0.01)) and the estimate, forms the
@@ -30,6 +35,10 @@ from . import pipeline as P
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "weights", "proposal_bf16.npz")
+WEIGHTS_RING = os.path.join(HERE, "weights", "proposal_ring_bf16.npz")
+LAYOUTS = ("rig", "ring")
+SLOTS = 8                # views per instance the network takes (its view maximum)
+NET_SIZE = 256           # their resolution (the network's inputs are 2 x 2 means)
 
 RIG = I.SceneConfig("rig-8x256x256", views=8, width=256, height=256, spp=16, edge_samples=4096,
                     elevation_deg=30.0, azimuths_deg=tuple(45.0 * k for k in range(8)), seed=3000)
@@ -70,6 +79,60 @@ def load_weights(path=WEIGHTS):
     return params, json.loads(str(z["meta"]))
 
 
+def view_slots(k, slots=SLOTS):
+    """The views of a k-view ring that fill the network's slots: evenly spread over
+    the ring, each view taken twice or more when k < slots (a repeated view changes
+    nothing in the maximum over views)."""
+    if k < 1:
+        raise ValueError("an instance needs a view")
+    return [j * k // slots for j in range(slots)]
+
+
+def ring_cameras(azimuths_deg, elevation_deg, radius, target, native_wh, size=NET_SIZE):
+    """Packed cameras [n][20] of views on a ring looking at `target` (as
+    inputs.make_cameras builds them at native resolution (W, H) = native_wh[i]),
+    with the intrinsics scaled to a size x size image of the same field of view:
+    fx, cx by size / W and fy, cy by size / H.  Vectorised: training draws a thousand
+    cameras per step."""
+    az = np.radians(np.asarray(azimuths_deg, np.float64))
+    el = np.radians(elevation_deg)
+    d = np.stack([np.sin(az) * np.cos(el), np.full_like(az, np.sin(el)), np.cos(az) * np.cos(el)], axis=1)
+    pos = np.asarray(target, np.float64)[None, :] + radius * d
+    fwd = np.asarray(target, np.float64)[None, :] - pos
+    fwd /= np.linalg.norm(fwd, axis=1, keepdims=True)
+    right = np.cross(fwd, np.array([0.0, 1.0, 0.0]))
+    right /= np.linalg.norm(right, axis=1, keepdims=True)
+    down = np.cross(fwd, right)
+    R = np.stack([right, down, fwd], axis=1)                 # [n][3][3], rows
+    t = -np.einsum("nij,nj->ni", R, pos)
+    wh = np.asarray(native_wh, np.float64).reshape(-1, 2)
+    f = 1.2 * wh[:, 0]                                      # inputs.look_at_camera's focal length
+    out = np.zeros((az.size, I.CAM_FLOATS), np.float32)
+    out[:, 0] = (f * (size / wh[:, 0])).astype(np.float32)
+    out[:, 1] = (f * (size / wh[:, 1])).astype(np.float32)
+    out[:, 2] = (wh[:, 0] / 2.0 * (size / wh[:, 0])).astype(np.float32)
+    out[:, 3] = (wh[:, 1] / 2.0 * (size / wh[:, 1])).astype(np.float32)
+    out[:, 4:13] = R.reshape(-1, 9)
+    out[:, 13:16] = t
+    out[:, 16:19] = pos
+    return out
+
+
+def sample_ring_layouts(rng, n, target, slots=SLOTS, views=(4, 16)):
+    """Cameras [n * slots][20] of n random ring layouts (the heterogeneous batch's
+    distribution: view count uniform in `views`, start azimuth uniform, native
+    resolution uniform over inputs.BATCH_RESOLUTIONS, elevation 30 degrees, 0.6 m),
+    each instance's views placed in the slots by view_slots."""
+    az, wh = [], []
+    for _ in range(n):
+        k = int(rng.integers(views[0], views[1] + 1))
+        a0 = float(rng.uniform(0.0, 360.0))
+        res = I.BATCH_RESOLUTIONS[int(rng.integers(0, len(I.BATCH_RESOLUTIONS)))]
+        az += [a0 + 360.0 * j / k for j in view_slots(k, slots)]
+        wh += [res] * slots
+    return ring_cameras(az, RIG.elevation_deg, RIG.radius, target, wh)
+
+
 def sample_pairs(rng, n):
     """(ground truth, estimate) parameter arrays [n][61] of the training distribution."""
     gt = np.zeros((n, I.N_PARAMS))
@@ -86,15 +149,19 @@ def sample_pairs(rng, n):
 class Trainer:
     """Training of the proposal network on renderer-generated pairs, B per step."""
 
-    def __init__(self, model: B.Model, batch=128, seed=0, lr=3e-4, device="cuda"):
-        self.model, self.B, self.seed, self.lr = model, batch, seed, lr
+    def __init__(self, model: B.Model, batch=128, seed=0, lr=3e-4, device="cuda", layout="rig"):
+        if layout not in LAYOUTS:
+            raise ValueError(f"layout: {layout}")
+        self.model, self.B, self.seed, self.lr, self.layout = model, batch, seed, lr, layout
         hand = model.hand
+        self.target = hand.v_template.mean(0)
         rig = RIG
         self.bt = B.Batch(hand.V, hand.F, hand.E, [(rig.views, rig.width, rig.height, TRAIN_SPP, 0, i)
                                                     for i in range(batch)])
         self.net = B.Net(batch, rig.views)
         cams1 = I.pack_cameras(I.make_cameras(rig, hand.v_template.mean(0)))
         self.cams = torch.as_tensor(np.concatenate([cams1] * batch), device=device)
+        self.cams_in = torch.empty(tuple(self.cams.shape)).pin_memory()
         Pix = self.bt.total_pixels
         self.plate = torch.empty((Pix, 3), device=device)
         self.obs = torch.empty((Pix, 3), device=device)
@@ -130,10 +197,14 @@ class Trainer:
         distance is the loss; the mm figures come from hr_vertex_error)."""
         rng = np.random.default_rng(np.random.SeedSequence([self.seed, 17, self.step_no]))
         gt, x0 = sample_pairs(rng, self.B)
+        torch.cuda.current_stream().synchronize()    # the pinned staging buffers are free
         self.h_in[0].copy_(torch.from_numpy(gt))
         self.h_in[1].copy_(torch.from_numpy(x0))
         self.x_gt.copy_(self.h_in[0], non_blocking=True)
         self.x0.copy_(self.h_in[1], non_blocking=True)
+        if self.layout == "ring":
+            self.cams_in.copy_(torch.from_numpy(sample_ring_layouts(rng, self.B, self.target)))
+            self.cams.copy_(self.cams_in, non_blocking=True)
         self.opts.iter = self.step_no
         k = 1 + 4 * self.step_no
         # plate ~ 0.5 + N(0, 0.29) (the spread of U(0, 1)), then the observation
@@ -158,9 +229,9 @@ class Trainer:
         return err
 
 
-def train(model: B.Model, pairs=200_000, batch=128, seed=0, lr=3e-4, log=print, init=None):
+def train(model: B.Model, pairs=200_000, batch=128, seed=0, lr=3e-4, log=print, init=None, layout="rig"):
     """Train on `pairs` fresh pairs; returns (float32 parameters, metadata)."""
-    tr = Trainer(model, batch=batch, seed=seed, lr=lr)
+    tr = Trainer(model, batch=batch, seed=seed, lr=lr, layout=layout)
     tr.set_params(init_params(seed) if init is None else init)
     steps = (pairs + batch - 1) // batch
     hist = []
@@ -180,13 +251,13 @@ def train(model: B.Model, pairs=200_000, batch=128, seed=0, lr=3e-4, log=print, 
     tr.net.get_params(params=params)
     torch.cuda.synchronize()
     meta = dict(pairs=steps * batch, batch=batch, steps=steps, lr=lr, seed=seed, train_spp=TRAIN_SPP,
-                seconds=round(time.time() - t0, 1), history=hist)
+                layout=layout, seconds=round(time.time() - t0, 1), history=hist)
     return params.cpu().numpy(), meta
 
 
-def evaluate(model: B.Model, params, batches=4, batch=128, seed=12345):
+def evaluate(model: B.Model, params, batches=4, batch=128, seed=12345, layout="rig"):
     """Mean epsilon_v (mm) of estimates and of one proposal on held-out pairs."""
-    tr = Trainer(model, batch=batch, seed=seed)
+    tr = Trainer(model, batch=batch, seed=seed, layout=layout)
     tr.set_params(params)
     e = np.concatenate([tr.step(train=False).cpu().numpy() for _ in range(batches)], axis=1) * 1e3
     return float(e[0].mean()), float(e[1].mean())
@@ -236,6 +307,41 @@ def rig_views(cfgs, views: P.BatchViews, view_offsets, pixel_offsets):
                         mask=torch.cat(masks))
 
 
+def ring_views(cfgs, views: P.BatchViews, view_offsets, pixel_offsets, slots=SLOTS, size=NET_SIZE):
+    """The network's views of instances on any camera layout (the "ring" network's
+    inputs): each instance's views view_slots(k) area-resampled to size x size
+    (hr_area_resample for plates and observations, hr_mask_resample for masks), with
+    fx, cx scaled by size / W and fy, cy by size / H.  Returns the BatchViews of
+    len(cfgs) x slots views of size x size (instances in order)."""
+    n = len(cfgs)
+    dev = views.cams.device
+    NV, Pv = n * slots, size * size
+    cams = torch.empty((NV, I.CAM_FLOATS), device=dev)
+    bg = torch.empty((NV, size, size, 3), device=dev)
+    obs = torch.empty((NV, size, size, 3), device=dev)
+    mask = torch.empty((NV, size, size), dtype=torch.uint8, device=views.mask.device)
+    scale = torch.empty(I.CAM_FLOATS, device=dev)
+    for i, cfg in enumerate(cfgs):
+        H, W = cfg.height, cfg.width
+        v0, p0 = int(view_offsets[i]), int(pixel_offsets[i])
+        if int(view_offsets[i + 1]) - v0 != cfg.views or int(pixel_offsets[i + 1]) - p0 != cfg.views * H * W:
+            raise ValueError(f"instance {i}: layout does not match its config")
+        scale.fill_(1.0)
+        scale[0] = size / W
+        scale[2] = size / W
+        scale[1] = size / H
+        scale[3] = size / H
+        for j, k in enumerate(view_slots(cfg.views, slots)):
+            d = i * slots + j
+            torch.mul(views.cams[v0 + k], scale, out=cams[d])
+            sl = slice(p0 + k * H * W, p0 + (k + 1) * H * W)
+            B.hr_area_resample(views.background[sl].view(1, H, W, 3), bg[d:d + 1])
+            B.hr_area_resample(views.observed[sl].view(1, H, W, 3), obs[d:d + 1])
+            B.hr_mask_resample(views.mask[sl].view(1, H, W), mask[d:d + 1])
+    return P.BatchViews(cams=cams, background=bg.view(NV * Pv, 3), observed=obs.view(NV * Pv, 3),
+                        mask=mask.view(NV * Pv))
+
+
 class Proposer:
     """Proposal steps for a BatchRefiner whose instances all use the training rig's
     layout (views x 256 x 256): candidates x_0 (the refiner's parameters) and
@@ -282,12 +388,16 @@ def main():
     ap.add_argument("--batch", type=int, default=128)
     ap.add_argument("--lr", type=float, default=3e-4)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--layout", choices=LAYOUTS, default="rig")
+    ap.add_argument("--out", default=None, help="weights file (default: the layout's file in weights/)")
     args = ap.parse_args()
+    if args.out is None:
+        args.out = WEIGHTS if args.layout == "rig" else WEIGHTS_RING
     hand = I.make_hand(0)
     model = B.Model(hand)
-    params, meta = train(model, pairs=args.pairs, batch=args.batch, seed=args.seed, lr=args.lr)
-    e0, e1 = evaluate(model, params)
+    params, meta = train(model, pairs=args.pairs, batch=args.batch, seed=args.seed, lr=args.lr,
+                         layout=args.layout)
+    e0, e1 = evaluate(model, params, layout=args.layout)
     meta["heldout_eps_v_mm"] = {"estimate": round(e0, 3), "proposal": round(e1, 3)}
     print(json.dumps(meta["heldout_eps_v_mm"]), flush=True)
     save_weights(params, meta, args.out)
