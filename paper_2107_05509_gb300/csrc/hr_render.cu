@@ -706,23 +706,63 @@ __device__ __forceinline__ void note_trace_items(const RenderArgs& a, int gi, in
 }
 
 
-// closest hits of a lane's S rays (same origin) among the K pool candidates at `off`:
-// the warp loads the candidates 32 at a time, one per lane (depth, screen box and
-// triangle record in three coalesced loads), and hands each in turn to every lane by
-// shuffles, so the scan waits on no memory load per candidate; the triangle's
-// vertices are loaded only for a candidate whose box holds one of the lane's rays,
-// once for all S rays.  `live[j]` rays take part, the others only vote.  Each ray
-// gets exactly the hit the one-ray search gives it.
+// bit p of the result: candidate box `b` (screen pixels, closed) meets pixel p of the
+// 8x4 sub-tile at (x0, y0), i.e. b.x <= px + 1, b.z >= px, b.y <= py + 1, b.w >= py
+// with pixel p at (x0 + p % 8, y0 + p / 8).  The float subtractions round
+// monotonically and integers are exact, so the column and row bounds never exclude a
+// pixel that meets the box; a NaN bound keeps the whole range.
+__device__ __forceinline__ unsigned box_pixel_mask(float4 b, int x0, int y0) {
+  const int cx0 = (int)fminf(fmaxf(ceilf(__fsub_rn(b.x, (float)(x0 + 1))), 0.0f), 8.0f);
+  const int cx1 = (int)fmaxf(fminf(floorf(__fsub_rn(b.z, (float)x0)), 7.0f), -1.0f);
+  const int ry0 = (int)fminf(fmaxf(ceilf(__fsub_rn(b.y, (float)(y0 + 1))), 0.0f), 4.0f);
+  const int ry1 = (int)fmaxf(fminf(floorf(__fsub_rn(b.w, (float)y0)), 3.0f), -1.0f);
+  if (cx0 > cx1 || ry0 > ry1) return 0u;
+  const unsigned cols = (0xffu >> (7 - cx1)) & (0xffu << cx0);
+  const unsigned rows = (0xffffffffu >> (8 * (3 - ry1))) & (0xffffffffu << (8 * ry0));
+  return rows & (cols * 0x01010101u);
+}
+
+// 32 x 32 bit matrix held one row per lane (bit p of lane l's word) -> its transpose
+// (bit l of lane p's word), by five butterfly stages that swap off-diagonal blocks
+__device__ __forceinline__ unsigned warp_transpose32(unsigned x) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const unsigned t = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & ~m[s]) | ((t & ~m[s]) >> j)) : ((x & m[s]) | ((t & m[s]) << j));
+  }
+  return x;
+}
+
+// closest hits of a lane's S rays (same origin, all in pixel (x0 + lane % 8,
+// y0 + lane / 8)) among the K pool candidates at `off`, which are sorted by nearest
+// depth.  The warp loads the candidates 32 at a time, one per lane (depth, screen box
+// and triangle record in three coalesced loads); each lane tests its candidate's box
+// against the sub-tile's 32 pixel squares, and a bit transpose gives every lane the
+// candidates that can hold a sample of its own pixel.  Each lane then walks only
+// those, in depth order, taking their records by shuffles from the lanes that loaded
+// them, so the lanes of one iteration each test a different candidate instead of
+// idling while the warp steps through candidates that miss their pixel.  A lane stops
+// at the first candidate nearer than none of its rays' hits (the list is depth-sorted,
+// so no later one is nearer).  Every ray tests the same candidates in the same order
+// as a scan of the whole list would, so each gets exactly the hit the one-ray search
+// gives it.  `live[j]` rays take part.
 template <bool STATS, int S>
-__device__ __forceinline__ void closest_candidates(const RenderArgs& a, int off, int K, const bool (&live)[S],
-                                                   const float (&sx)[S], const float (&sy)[S], float3 o,
-                                                   const float3 (&d)[S], Hit (&h)[S], Counts& cnt) {
+__device__ __forceinline__ void closest_candidates(const RenderArgs& a, int off, int K, int x0, int y0,
+                                                   const bool (&live)[S], const float (&sx)[S], const float (&sy)[S],
+                                                   float3 o, const float3 (&d)[S], Hit (&h)[S], Counts& cnt) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  bool done = true;
 #pragma unroll
-  for (int j = 0; j < S; ++j) h[j] = Hit{-1, INFINITY, 0.0f, 0.0f};
-  bool stop = false;
-  for (int c0 = 0; c0 < K && !stop; c0 += 32) {
+  for (int j = 0; j < S; ++j) {
+    h[j] = Hit{-1, INFINITY, 0.0f, 0.0f};
+    done = done && !live[j];
+  }
+  for (int c0 = 0; c0 < K; c0 += 32) {
+    if (!__any_sync(full, !done)) break;
     // this block of candidates, one per lane; a pool index out of range ends the scan
     const int cl = c0 + lane;
     const bool have = cl < K;
@@ -737,15 +777,24 @@ __device__ __forceinline__ void closest_candidates(const RenderArgs& a, int off,
     }
     const unsigned bad = __ballot_sync(full, have && !ok);
     int n = min(32, K - c0);
-    if (bad) {
-      n = min(n, __ffs(bad) - 1);
-      stop = true;
+    if (bad) n = min(n, __ffs(bad) - 1);
+    unsigned pm = 0u;
+    if (lane < n) {
+      pm = box_pixel_mask(bl, x0, y0);
+      if (STATS) ++cnt.cands;
     }
-    for (int i = 0; i < n; ++i) {
+    unsigned m = warp_transpose32(pm);   // bit i: candidate c0 + i meets this lane's pixel
+    if (done) m = 0u;
+    for (;;) {
+      const bool act = m != 0u;
+      if (!__any_sync(full, act)) break;
+      const int i = act ? __ffs(m) - 1 : 0;
+      m &= m - 1u;
       const float zm = __shfl_sync(full, zl, i);
       const float bx0 = __shfl_sync(full, bl.x, i), by0 = __shfl_sync(full, bl.y, i);
       const float bx1 = __shfl_sync(full, bl.z, i), by1 = __shfl_sync(full, bl.w, i);
       const int k = __shfl_sync(full, kl, i);
+      if (!act) continue;
       const float zlim = zm - (1e-4f * fabsf(zm) + 1e-6f);
       bool want[S];
       bool any = false;
@@ -754,11 +803,11 @@ __device__ __forceinline__ void closest_candidates(const RenderArgs& a, int off,
         want[j] = live[j] && !(h[j].t < zlim);
         any = any || want[j];
       }
-      if (!__any_sync(full, any)) {
-        stop = true;
-        break;
+      if (!any) {   // no later candidate is nearer either
+        done = true;
+        m = 0u;
+        continue;
       }
-      if (!any) continue;
       bool inside = false;
 #pragma unroll
       for (int j = 0; j < S; ++j) {
@@ -785,6 +834,7 @@ __device__ __forceinline__ void closest_candidates(const RenderArgs& a, int off,
         }
       }
     }
+    if (bad) break;
   }
 }
 
@@ -819,7 +869,7 @@ __device__ __forceinline__ void shade_samples(const RenderArgs& a, const SubTile
       d[j] = primary_dir(cam, sx[j], sy[j]);
     }
     if (K > 0) {
-      closest_candidates<STATS, S>(a, off, K, live, sx, sy, o, d, h, cnt);
+      closest_candidates<STATS, S>(a, off, K, t.x0, t.y0, live, sx, sy, o, d, h, cnt);
     } else {
 #pragma unroll
       for (int j = 0; j < S; ++j) {
@@ -1023,7 +1073,7 @@ __device__ __forceinline__ void grad_samples(const RenderArgs& a, const SubTile&
       d[j] = primary_dir(cam, sx[j], sy[j]);
     }
     if (K > 0) {
-      closest_candidates<STATS, S>(a, off, K, lv, sx, sy, o, d, h, cnt);
+      closest_candidates<STATS, S>(a, off, K, t.x0, t.y0, lv, sx, sy, o, d, h, cnt);
     } else {
 #pragma unroll
       for (int j = 0; j < S; ++j) {
