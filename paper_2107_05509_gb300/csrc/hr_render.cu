@@ -1135,50 +1135,86 @@ __device__ __forceinline__ float3 lane_adjoint(const RenderArgs& a, const SubTil
   return make_float3(g.x * inv_spp, g.y * inv_spp, g.z * inv_spp);
 }
 
-// Forward, first pass: one warp per sub-tile, each warp a static share of the
-// sub-tiles (no shared counter).  A sub-tile whose frustum meets neither of the
-// scene's two root boxes sees only the background: its pixels are written here.  The
-// others are listed for k_gather, which then claims far fewer sub-tiles from its
-// counter.
+// Forward, first pass: each warp takes kCullGroup consecutive sub-tiles, one per lane
+// of its first lanes, and tests each sub-tile's frustum against the scene's two root
+// boxes in that lane (all the warp's loads in flight at once).  Sub-tiles that can
+// see the mesh are appended for k_gather (one atomic per warp); the others see only
+// the background, and the whole warp writes their pixels, lane = pixel, with every
+// background load issued before the first store.  k_gather then claims far fewer
+// sub-tiles from its counter.
 constexpr int kCullThreads = 256;
+constexpr int kCullGroup = 8;
 template <bool STATS>
-__global__ void __launch_bounds__(kCullThreads) k_cull(RenderArgs a0, float* __restrict__ image,
+__global__ void __launch_bounds__(kCullThreads, 4) k_cull(RenderArgs a0, float* __restrict__ image,
                                                        unsigned long long* stats) {
-  __shared__ float4 spl[kCullThreads / 32][5];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   Counts cnt;
   const int total = visit_count(a0);
   const int nw = gridDim.x * (kCullThreads / 32);
-  for (int vi = blockIdx.x * (kCullThreads / 32) + w; vi < total; vi += nw) {
-    const int st = visit_subtile(a0, vi);
-    if (!in_range(a0.status, st, 0, a0.total_st)) continue;
-    const SubTile t = subtile(a0, st);
-    if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
-    if (!inst_active(a0, t.inst)) {   // a retired instance: nothing to render
-      if (lane == 0) a0.wk.st[st] = make_int2(0, 0);
-      continue;
+  for (int g0 = (blockIdx.x * (kCullThreads / 32) + (threadIdx.x >> 5)) * kCullGroup; g0 < total;
+       g0 += nw * kCullGroup) {
+    int st = -1;
+    bool meets = false, culled = false;
+    SubTile t{};
+    if (lane < kCullGroup && g0 + lane < total) {
+      const int s = visit_subtile(a0, g0 + lane);
+      if (in_range(a0.status, s, 0, a0.total_st)) {
+        t = subtile(a0, s);
+        if (in_range(a0.status, t.inst, 0, a0.n_inst)) {
+          st = s;
+          if (!inst_active(a0, t.inst)) {   // a retired instance: nothing to render
+            a0.wk.st[s] = make_int2(0, 0);
+          } else {
+            const RenderArgs a = for_inst(a0, t.inst);
+            const Cam cam = load_cam(a.cams, t.view);
+            const float4* np = reinterpret_cast<const float4*>(a.nodes);
+            const float4 p = __ldg(np), q = __ldg(np + 1), r = __ldg(np + 2);   // the root's two child boxes
+            float4 pl[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) pl[k] = frustum_plane(cam, t.x0, t.y0, k);
+            meets = box_in_frustum(pl, p.x, p.y, p.z, p.w, q.x, q.y) || box_in_frustum(pl, q.z, q.w, r.x, r.y, r.z, r.w);
+            if (!meets) {
+              a0.wk.st[s] = make_int2(0, 0);
+              culled = true;
+            }
+          }
+        }
+      }
     }
-    const RenderArgs a = for_inst(a0, t.inst);
-    const Cam cam = load_cam(a.cams, t.view);
-    if (lane < 5) spl[w][lane] = frustum_plane(cam, t.x0, t.y0, lane);
-    __syncwarp();
-    bool meets = false;
-    if (lane < 2) {   // the root's two child boxes
-      const float4* np = reinterpret_cast<const float4*>(a.nodes);
-      const float4 p = __ldg(np), q = __ldg(np + 1), r = __ldg(np + 2);
-      meets = lane == 0 ? box_in_frustum(spl[w], p.x, p.y, p.z, p.w, q.x, q.y)
-                        : box_in_frustum(spl[w], q.z, q.w, r.x, r.y, r.z, r.w);
+    const unsigned mm = __ballot_sync(full, meets);
+    int base = 0;
+    if (lane == 0 && mm) base = (int)atomicAdd(&a0.wk.ctr[ctr_cull(a0.n_inst)], (unsigned)__popc(mm));
+    base = __shfl_sync(full, base, 0);
+    if (meets) a0.wk.cand_st[base + __popc(mm & lanemask_lt())] = st;
+    const unsigned cm = __ballot_sync(full, culled);
+    if (!cm) continue;
+    // background sub-tiles: lane = pixel; loads first, then the stores
+    float3 bgv[kCullGroup];
+    size_t pix[kCullGroup];
+    bool valid[kCullGroup];
+#pragma unroll
+    for (int j = 0; j < kCullGroup; ++j) {
+      const int x0 = __shfl_sync(full, t.x0, j), y0 = __shfl_sync(full, t.y0, j);
+      const int W = __shfl_sync(full, t.W, j), H = __shfl_sync(full, t.H, j);
+      const long long p0 = __shfl_sync(full, t.pix0, j);
+      const int px = x0 + (lane % kSubW), py = y0 + (lane / kSubW);
+      valid[j] = ((cm >> j) & 1u) && px < W && py < H;
+      pix[j] = (size_t)p0 + (size_t)py * W + px;
+      bgv[j] = valid[j] ? ld3(a0.bg + 3 * pix[j]) : make_float3(0.0f, 0.0f, 0.0f);
     }
-    const bool any = __any_sync(0xffffffffu, meets);
-    __syncwarp();
-    if (any) {
-      if (lane == 0) a0.wk.cand_st[atomicAdd(&a0.wk.ctr[ctr_cull(a0.n_inst)], 1u)] = st;
-      continue;
+#pragma unroll
+    for (int j = 0; j < kCullGroup; ++j) {
+      const int spp = __shfl_sync(full, t.spp, j);
+      if (!valid[j]) continue;
+      if (STATS) cnt.samples += spp;   // resolved by the frustum test
+      // the pixel write_pixel gives a sub-tile whose samples all miss
+      const float fm = __fdiv_rn((float)spp, (float)spp);
+      const float inv_spp = 1.0f / (float)spp;
+      image[3 * pix[j]] = 0.0f * inv_spp + bgv[j].x * fm;
+      image[3 * pix[j] + 1] = 0.0f * inv_spp + bgv[j].y * fm;
+      image[3 * pix[j] + 2] = 0.0f * inv_spp + bgv[j].z * fm;
     }
-    if (lane == 0) a0.wk.st[st] = make_int2(0, 0);
-    const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
-    if (STATS && px < t.W && py < t.H) cnt.samples += t.spp;   // resolved by the frustum test
-    write_pixel(a, t, make_float3(0.0f, 0.0f, 0.0f), t.spp, image);
   }
   flush_counts<STATS>(cnt, stats);
 }
@@ -1431,7 +1467,7 @@ __device__ __forceinline__ void finish_item(const RenderArgs& a, const SubTile& 
 
 // warps take work items, instance after instance; S samples per lane at a time
 template <bool STATS, int S>
-__global__ void __launch_bounds__(kRenderThreads, 8) k_shade_fwd(RenderArgs a_in, float* __restrict__ image,
+__global__ void __launch_bounds__(kRenderThreads, 6) k_shade_fwd(RenderArgs a_in, float* __restrict__ image,
                                                                   unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
   const int lane = threadIdx.x & 31;
@@ -2113,7 +2149,7 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   }
   const int blocks = ctx->num_sms * ctx->tune.blocks_per_sm;
   tm.begin(kTimeFwdGather);
-  const int cull_blocks = ctx->num_sms * (2048 / kCullThreads);
+  const int cull_blocks = ctx->num_sms * 4;   // one wave at k_cull's 64 registers
   if (st)
     k_cull<true><<<cull_blocks, kCullThreads, 0, s>>>(a, image, ctx->stats);
   else
