@@ -131,7 +131,10 @@ typedef struct hr_render_opts {
     float ka, kd;
     float light_dir[3];
     float light_rgb[3];
-    float edge_eps_px;      /* offset of the two edge-sample rays, in pixels        */
+    float edge_eps_px;      /* offset of the two edge-sample rays, in pixels, in
+                               (0, 0.25]: the offset rays use the candidate list of the
+                               sub-tile holding the sample, which is complete for
+                               screen points within half a pixel of the sub-tile   */
     uint32_t flags;         /* HR_BWD_* bits; 0 = every term                        */
     const uint32_t* iter_dev; /* optional device counter read instead of `iter` (so a
                                  captured iteration replays with fresh samples); NULL = use iter */

@@ -17,7 +17,7 @@ using hr::Context;
 namespace {
 
 struct Alloc {
-  void** slots[40];
+  void** slots[48];
   int n = 0;
 };
 
@@ -46,7 +46,7 @@ void free_ctx(Context* c) {
                   c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it,
                   c->bvh_parent, c->bvh_valid, c->bvh_keys, c->bvh_flags, c->bvh_bounds, c->bvh_bad,
                   c->bvh_mode, c->extra64, c->ct_partials, c->dedge, c->ovf_list, c->acc_fx, c->act_off,
-                  c->trace_list, c->st_done, c->cand_st};
+                  c->trace_list, c->st_done, c->cand_st, c->bin_cnt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete[] c->hvt;
@@ -69,7 +69,8 @@ bool tex_ok(const hr_render_opts* o, const hr_model* m) {
 }
 
 bool opts_ok(const hr_render_opts* o) {
-  return o && o->spp >= 1 && o->spp <= 65536 && o->edge_samples >= 0 && o->edge_eps_px > 0.0f;
+  return o && o->spp >= 1 && o->spp <= 65536 && o->edge_samples >= 0 && o->edge_eps_px > 0.0f &&
+         o->edge_eps_px <= 0.25f;
 }
 
 bool image_ok(const Context* c, int N, int H, int W) {
@@ -123,6 +124,7 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
             dev_alloc(&c->extra, ni * 6 * V, a) && dev_alloc(&c->work_ctr, hr::ctr_words(ni), a) &&
             dev_alloc(&c->ovf_list, subtiles, a) && dev_alloc(&c->trace_list, c->item_cap, a) &&
             dev_alloc(&c->st_done, subtiles, a) && dev_alloc(&c->cand_st, subtiles, a) &&
+            dev_alloc(&c->bin_cnt, subtiles, a) &&
             dev_alloc(&c->bvh_parent, ni * 2 * F, a) && dev_alloc(&c->bvh_valid, ni, a) &&
             dev_alloc(&c->bvh_bounds, ni * 6, a) && dev_alloc(&c->bvh_bad, ni, a) && dev_alloc(&c->bvh_mode, ni, a);
   // keys of the multi-block build, for meshes beyond one block's shared memory

@@ -209,7 +209,8 @@ struct Work {
   int* trace;      // [items] region slots (+ instance base) of the items of sub-tiles
                    // without a candidate list (k_overflow traces them ray by ray)
   unsigned* st_done;   // [sub-tiles] forward items finished (the last one combines)
-  int* cand_st;        // [sub-tiles] forward sub-tiles left by k_cull (count: ctr_cull)
+  int* cand_st;        // [sub-tiles] forward sub-tiles whose lists k_bin_sort orders (count: ctr_cull)
+  unsigned* bin;       // [sub-tiles] records binned per sub-tile, then the fill's slot counter
   unsigned long long* fx;   // [n_inst][6V] fixed-point backward sums (HR_DETERMINISTIC)
   bool det;                 // HR_DETERMINISTIC: every vertex-gradient sum goes to fx
 };
@@ -1135,18 +1136,129 @@ __device__ __forceinline__ float3 lane_adjoint(const RenderArgs& a, const SubTil
   return make_float3(g.x * inv_spp, g.y * inv_spp, g.z * inv_spp);
 }
 
-// Forward, first pass: each warp takes kCullGroup consecutive sub-tiles, one per lane
-// of its first lanes, and tests each sub-tile's frustum against the scene's two root
-// boxes in that lane (all the warp's loads in flight at once).  Sub-tiles that can
-// see the mesh are appended for k_gather (one atomic per warp); the others see only
-// the background, and the whole warp writes their pixels, lane = pixel, with every
-// background load issued before the first store.  k_gather then claims far fewer
-// sub-tiles from its counter.
 constexpr int kCullThreads = 256;
-constexpr int kCullGroup = 8;
+constexpr int kCullGroup = 8;   // sub-tiles per warp in k_bin_alloc
+
+// ---------------------------------------------------------------------------------
+// forward candidate lists by screen-space binning
+// ---------------------------------------------------------------------------------
+// The shaders test every sample against a candidate's screen box (project_record:
+// padded by half a pixel, unbounded when a vertex is not in front of the camera)
+// before intersecting it, so a sub-tile's list needs exactly the triangle records
+// whose box meets the sub-tile's sample square [x0, x0 + 8] x [y0, y0 + 4].  The
+// forward builds the lists by binning each (view, record) pair into the sub-tiles its
+// box meets -- k_bin counts them, k_bin_alloc gives every sub-tile its pool range and
+// work items, k_bin in fill mode writes the records, k_bin_sort orders each list by
+// nearest depth -- instead of a frustum walk of the BVH per sub-tile.
+
+// sub-tile columns [c0, c1] and rows [r0, r1] of a view (nsx x nsy sub-tiles) whose
+// sample squares meet box b: column c meets it iff b.x <= 8c + 8 and b.z >= 8c (rows
+// likewise with 4).  The float subtraction rounds monotonically and the scalings by
+// 1/8 and 1/4 and the integers are exact, so no column or row that meets the box is
+// left out; a NaN bound keeps the whole range.
+struct BinRange {
+  int c0, c1, r0, r1;
+};
+__device__ __forceinline__ BinRange bin_range(float4 b, int nsx, int nsy) {
+  BinRange r;
+  r.c0 = (int)fminf(fmaxf(ceilf(__fmul_rn(__fsub_rn(b.x, (float)kSubW), 1.0f / kSubW)), 0.0f), (float)nsx);
+  r.c1 = (int)fmaxf(fminf(floorf(__fmul_rn(b.z, 1.0f / kSubW)), (float)(nsx - 1)), -1.0f);
+  r.r0 = (int)fminf(fmaxf(ceilf(__fmul_rn(__fsub_rn(b.y, (float)kSubH), 1.0f / kSubH)), 0.0f), (float)nsy);
+  r.r1 = (int)fmaxf(fminf(floorf(__fmul_rn(b.w, 1.0f / kSubH)), (float)(nsy - 1)), -1.0f);
+  return r;
+}
+
+// the camera depth of record k's three vertices all below -1e-3: no primary ray
+// (camera depth t > 0 at parameter t) can meet it
+__device__ __forceinline__ bool record_behind(const RenderArgs& a, const Cam& cam, int k) {
+  const float4 t0 = __ldg(&a.tris[3 * k]), t1 = __ldg(&a.tris[3 * k + 1]), t2 = __ldg(&a.tris[3 * k + 2]);
+  const float3 v[3] = {make_float3(t0.x, t0.y, t0.z), make_float3(t0.x + t0.w, t0.y + t1.x, t0.z + t1.y),
+                       make_float3(t0.x + t1.z, t0.y + t1.w, t0.z + t2.x)};
+  bool behind = true;
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+    behind = behind && cam.R[6] * v[m].x + cam.R[7] * v[m].y + cam.R[8] * v[m].z + cam.t[2] < -1e-3f;
+  return behind;
+}
+
+constexpr int kBinThreads = 256;
+constexpr int kBinBig = 64;   // ranges of more sub-tiles are walked by the whole warp
+
+// one sub-tile of a pair's range: count it, or (FILL) write the record into the
+// sub-tile's pool range at the next free slot
+template <bool FILL>
+__device__ __forceinline__ void bin_visit(const RenderArgs& a, unsigned* __restrict__ bin, int s, int k, float zm) {
+  if (!FILL) {
+    atomicAdd(&bin[s], 1u);
+    return;
+  }
+  const int2 pk = a.wk.st[s];
+  if (pk.y <= 0) return;   // no list: background, per-ray traversal, or no pool room
+  const int slot = (int)atomicAdd(&bin[s], 1u);
+  if (slot >= pk.y || !in_range(a.status, (long long)pk.x + slot, 0, a.wk.pool_cap)) return;
+  a.wk.rec[pk.x + slot] = k;
+  a.wk.z[pk.x + slot] = zm;
+}
+
+// pair i = (active view i / F, record i % F); all lanes of a warp run the same trip
+// count so that large ranges can be shared by the warp
+template <bool FILL>
+__global__ void __launch_bounds__(kBinThreads) k_bin(RenderArgs a0, unsigned* __restrict__ bin) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int F = a0.max_visits - 1;
+  const long long total = (long long)visit_views(a0) * F;
+  const long long stride = (long long)gridDim.x * kBinThreads;
+  for (long long base = (long long)blockIdx.x * kBinThreads + (threadIdx.x & ~31); base < total; base += stride) {
+    const long long i = base + lane;
+    int st0 = 0, nsx = 1, k = 0, area = 0;
+    float zm = 0.0f;
+    BinRange r{0, -1, 0, -1};
+    if (i < total) {
+      const int g = visit_view(a0, (int)(i / F));
+      k = (int)(i % F);
+      SubTile t;
+      view_info(a0, g, t, st0, nsx);
+      if (in_range(a0.status, t.inst, 0, a0.n_inst) && inst_active(a0, t.inst)) {
+        const RenderArgs a = for_inst(a0, t.inst);
+        const Cam cam = load_cam(a.cams, g);
+        if (!record_behind(a, cam, k)) {
+          float4 bb;
+          project_record(a, cam, k, bb, zm);
+          r = bin_range(bb, nsx, (t.H + kSubH - 1) / kSubH);
+          if (r.c0 <= r.c1 && r.r0 <= r.r1) area = (r.c1 - r.c0 + 1) * (r.r1 - r.r0 + 1);
+        }
+      }
+    }
+    if (area > 0 && area <= kBinBig) {
+      for (int y = r.r0; y <= r.r1; ++y)
+        for (int x = r.c0; x <= r.c1; ++x) bin_visit<FILL>(a0, bin, st0 + y * nsx + x, k, zm);
+    }
+    unsigned big = __ballot_sync(full, area > kBinBig);
+    while (big) {
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const int s0 = __shfl_sync(full, st0, src), n = __shfl_sync(full, nsx, src);
+      const int c0 = __shfl_sync(full, r.c0, src), c1 = __shfl_sync(full, r.c1, src);
+      const int r0 = __shfl_sync(full, r.r0, src), na = __shfl_sync(full, area, src);
+      const int kk = __shfl_sync(full, k, src);
+      const float z = __shfl_sync(full, zm, src);
+      const int w = c1 - c0 + 1;
+      for (int q = lane; q < na; q += 32) bin_visit<FILL>(a0, bin, s0 + (r0 + q / w) * n + c0 + q % w, kk, z);
+    }
+  }
+}
+
+// Each warp takes kCullGroup consecutive sub-tiles, one per lane of its first lanes.
+// A sub-tile with no record in its bin sees only the background: the whole warp
+// writes its pixels, lane = pixel, every background load issued before the first
+// store.  The others get a pool range for their K records (one atomic per warp), the
+// work items of their chunks, and a place in the list k_bin_sort orders; the count
+// becomes the fill's slot counter.  A sub-tile with more records than a list holds,
+// or whose records find no pool room, is traced ray by ray (K = -1, -(K + 1)).
 template <bool STATS>
-__global__ void __launch_bounds__(kCullThreads, 4) k_cull(RenderArgs a0, float* __restrict__ image,
-                                                       unsigned long long* stats) {
+__global__ void __launch_bounds__(kCullThreads, 4) k_bin_alloc(RenderArgs a0, unsigned* __restrict__ bin,
+                                                               float* __restrict__ image, unsigned long long* stats) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   Counts cnt;
@@ -1154,8 +1266,8 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_cull(RenderArgs a0, float* 
   const int nw = gridDim.x * (kCullThreads / 32);
   for (int g0 = (blockIdx.x * (kCullThreads / 32) + (threadIdx.x >> 5)) * kCullGroup; g0 < total;
        g0 += nw * kCullGroup) {
-    int st = -1;
-    bool meets = false, culled = false;
+    int st = -1, K = 0;
+    bool culled = false, listed = false;
     SubTile t{};
     if (lane < kCullGroup && g0 + lane < total) {
       const int s = visit_subtile(a0, g0 + lane);
@@ -1166,27 +1278,57 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_cull(RenderArgs a0, float* 
           if (!inst_active(a0, t.inst)) {   // a retired instance: nothing to render
             a0.wk.st[s] = make_int2(0, 0);
           } else {
-            const RenderArgs a = for_inst(a0, t.inst);
-            const Cam cam = load_cam(a.cams, t.view);
-            const float4* np = reinterpret_cast<const float4*>(a.nodes);
-            const float4 p = __ldg(np), q = __ldg(np + 1), r = __ldg(np + 2);   // the root's two child boxes
-            float4 pl[5];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) pl[k] = frustum_plane(cam, t.x0, t.y0, k);
-            meets = box_in_frustum(pl, p.x, p.y, p.z, p.w, q.x, q.y) || box_in_frustum(pl, q.z, q.w, r.x, r.y, r.z, r.w);
-            if (!meets) {
+            K = (int)bin[s];
+            bin[s] = 0u;
+            if (K == 0) {
               a0.wk.st[s] = make_int2(0, 0);
               culled = true;
+            } else {
+              listed = true;
             }
           }
         }
       }
     }
-    const unsigned mm = __ballot_sync(full, meets);
-    int base = 0;
-    if (lane == 0 && mm) base = (int)atomicAdd(&a0.wk.ctr[ctr_cull(a0.n_inst)], (unsigned)__popc(mm));
-    base = __shfl_sync(full, base, 0);
-    if (meets) a0.wk.cand_st[base + __popc(mm & lanemask_lt())] = st;
+    // pool ranges of the warp's lists: exclusive prefix sums of K over the lanes
+    const int want = listed && K <= kLeafCap ? K : 0;
+    int incl = want;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += y;
+    }
+    unsigned base = 0u;
+    if (lane == 31 && incl > 0) base = atomicAdd(&a0.wk.ctr[1], (unsigned)incl);
+    base = __shfl_sync(full, base, 31);
+    bool sorted = false;
+    if (listed) {
+      const RenderArgs a = for_inst(a0, t.inst);
+      const long long off = (long long)base + incl - want;
+      int Kc = K;
+      if (K > kLeafCap) Kc = -1;
+      else if (off + K > a.wk.pool_cap) Kc = -(K + 1);
+      sorted = Kc > 0;
+      a.wk.st[st] = make_int2(sorted ? (int)off : 0, Kc);
+      const int C = chunks_for(a, Kc, t.spp);
+      const int ibase = inst_ibase(a, t.inst);
+      const int first = alloc_items(a, t.inst, C, heavy_item(a, Kc, C, t.spp), inst_icap(a, t.inst));
+      if (first >= 0) {
+        for (int c = 0; c < C; ++c) a.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
+        if (Kc < 0) {   // listed for k_overflow, which traces them ray by ray
+          const int tb = (int)atomicAdd(&a.wk.ctr[ctr_trace(a.n_inst)], (unsigned)C);
+          for (int c = 0; c < C; ++c)
+            if (tb + c < a.wk.item_cap) a.wk.trace[tb + c] = ibase + first + c;
+        }
+      } else {   // item region full: the whole sub-tile goes to k_overflow
+        a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
+      }
+    }
+    const unsigned sm = __ballot_sync(full, sorted);
+    int lb = 0;
+    if (lane == 0 && sm) lb = (int)atomicAdd(&a0.wk.ctr[ctr_cull(a0.n_inst)], (unsigned)__popc(sm));
+    lb = __shfl_sync(full, lb, 0);
+    if (sorted) a0.wk.cand_st[lb + __popc(sm & lanemask_lt())] = st;
     const unsigned cm = __ballot_sync(full, culled);
     if (!cm) continue;
     // background sub-tiles: lane = pixel; loads first, then the stores
@@ -1207,7 +1349,7 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_cull(RenderArgs a0, float* 
     for (int j = 0; j < kCullGroup; ++j) {
       const int spp = __shfl_sync(full, t.spp, j);
       if (!valid[j]) continue;
-      if (STATS) cnt.samples += spp;   // resolved by the frustum test
+      if (STATS) cnt.samples += spp;   // resolved by the binning: no record meets the sub-tile
       // the pixel write_pixel gives a sub-tile whose samples all miss
       const float fm = __fdiv_rn((float)spp, (float)spp);
       const float inv_spp = 1.0f / (float)spp;
@@ -1219,29 +1361,99 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_cull(RenderArgs a0, float* 
   flush_counts<STATS>(cnt, stats);
 }
 
-// One warp per sub-tile: candidates into the pool, work items for the sub-tile (in
-// its instance's region of the item table).
-// BWD: only sub-tiles with a non-zero adjoint; their zero-candidate case has no
-// gradient.  FWD: zero-candidate sub-tiles are written (background) here.  When the
-// pool or the item region is full the warp does the sub-tile's work itself.
-template <bool BWD, bool STATS>
+// one warp per listed sub-tile: its K records (in fill order) sorted by nearest depth
+// (bitonic, padded with +inf), then written back with their screen boxes
+struct SortSmem {   // per warp
+  int leaf[kLeafCap];
+  float key[kLeafCap];
+  int idx[kLeafCap];
+};
+__global__ void __launch_bounds__(kRenderThreads) k_bin_sort(RenderArgs a0) {
+  __shared__ SortSmem ssm[kWarps];
+  SortSmem& ss = ssm[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int n = (int)min(*reinterpret_cast<volatile unsigned*>(&a0.wk.ctr[ctr_cull(a0.n_inst)]),
+                         (unsigned)a0.total_st);
+  for (int vi = blockIdx.x * kWarps + (threadIdx.x >> 5); vi < n; vi += gridDim.x * kWarps) {
+    const int st = a0.wk.cand_st[vi];
+    if (!in_range(a0.status, st, 0, a0.total_st)) continue;
+    const SubTile t = subtile(a0, st);
+    if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
+    const int2 pk = a0.wk.st[st];
+    const int K = pk.y, off = pk.x;
+    if (K <= 0 || K > kLeafCap || off < 0 || !in_range(a0.status, (long long)off + K - 1, 0, a0.wk.pool_cap)) continue;
+    const RenderArgs a = for_inst(a0, t.inst);
+    const Cam cam = load_cam(a.cams, t.view);
+    int P = 1;
+    while (P < K) P <<= 1;
+    for (int j = lane; j < P; j += 32) {
+      int k = 0;
+      float z = INFINITY;
+      if (j < K) {
+        k = a.wk.rec[off + j];
+        z = a.wk.z[off + j];
+        if (!in_range(a.status, k, 0, a.max_visits - 1)) k = 0;
+      }
+      ss.leaf[j] = k;
+      ss.key[j] = z;
+      ss.idx[j] = j;
+    }
+    __syncwarp();
+    for (int q = 2; q <= P; q <<= 1) {
+      for (int j = q >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < P; i += 32) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const float zi = ss.key[i], zj = ss.key[ixj];
+            const bool up = (i & q) == 0;
+            if ((zi > zj) == up) {
+              ss.key[i] = zj;
+              ss.key[ixj] = zi;
+              const int w = ss.idx[i];
+              ss.idx[i] = ss.idx[ixj];
+              ss.idx[ixj] = w;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    for (int c = lane; c < K; c += 32) {
+      int j = ss.idx[c];
+      if (!in_range(a.status, j, 0, K)) j = 0;
+      const int k = ss.leaf[j];
+      float4 bb;
+      float zm;
+      project_record(a, cam, k, bb, zm);
+      a.wk.bb[off + c] = bb;
+      a.wk.z[off + c] = zm;
+      a.wk.rec[off + c] = k;
+    }
+    __syncwarp();
+  }
+}
+
+// The backward's own candidate lists (without HR_BWD_REUSE_FWD): one warp per
+// sub-tile with a non-zero adjoint walks the BVH with the sub-tile's frustum,
+// collects the records it meets into the pool sorted by nearest depth, and allocates
+// the sub-tile's work items in its instance's region of the item table; sub-tiles
+// whose frustum meets nothing have no interior gradient.  When the pool or the item
+// region is full the sub-tile is traced ray by ray or done whole by k_overflow.
+template <bool STATS>
 __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, const float* __restrict__ adjoint,
-                                                          float* __restrict__ image, unsigned long long* stats) {
+                                                          unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
   __shared__ GatherSmem gsm[kWarps];
   GatherSmem& gs = gsm[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   Counts cnt;
-  // the forward takes the sub-tiles k_cull listed, the backward every sub-tile
-  const int total =
-      BWD ? visit_count(a0)
-          : (int)min(*reinterpret_cast<volatile unsigned*>(&a0.wk.ctr[ctr_cull(a0.n_inst)]), (unsigned)a0.total_st);
+  const int total = visit_count(a0);
   for (;;) {
     int vi = 0;
     if (lane == 0) vi = (int)atomicAdd(&a0.wk.ctr[0], 1u);
     vi = __shfl_sync(0xffffffffu, vi, 0);
     if (vi >= total) break;
-    const int st = BWD ? visit_subtile(a0, vi) : a0.wk.cand_st[vi];
+    const int st = visit_subtile(a0, vi);
     if (!in_range(a0.status, st, 0, a0.total_st)) continue;
     const SubTile t = subtile(a0, st);
     if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
@@ -1250,23 +1462,18 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
       continue;
     }
     const RenderArgs a = for_inst(a0, t.inst);
-    bool live = true;
-    float3 g = make_float3(0.0f, 0.0f, 0.0f);
-    if (BWD) {
-      g = lane_adjoint(a, t, adjoint, live);
-      if (!__any_sync(0xffffffffu, live)) {
-        if (lane == 0) a.wk.st[st] = make_int2(0, 0);
-        continue;
-      }
+    bool live;
+    lane_adjoint(a, t, adjoint, live);
+    if (!__any_sync(0xffffffffu, live)) {
+      if (lane == 0) a.wk.st[st] = make_int2(0, 0);
+      continue;
     }
     const Cam cam = load_cam(a.cams, t.view);
     int K = frustum_leaves<STATS>(a, cam, t.x0, t.y0, gs, cnt);
     if (K == 0) {
       if (lane == 0) a.wk.st[st] = make_int2(0, 0);
       const int px = t.x0 + (lane % kSubW), py = t.y0 + (lane / kSubW);
-      const bool valid = px < t.W && py < t.H && live;
-      if (STATS && valid) cnt.samples += t.spp;   // resolved by the frustum test
-      if (!BWD) write_pixel(a, t, make_float3(0.0f, 0.0f, 0.0f), t.spp, image);
+      if (STATS && px < t.W && py < t.H && live) cnt.samples += t.spp;   // resolved by the frustum test
       continue;
     }
     int off = 0;
@@ -1470,7 +1677,6 @@ template <bool STATS, int S>
 __global__ void __launch_bounds__(kRenderThreads, 6) k_shade_fwd(RenderArgs a_in, float* __restrict__ image,
                                                                   unsigned long long* stats) {
   const RenderArgs a0 = with_iter(a_in);
-  const int lane = threadIdx.x & 31;
   Counts cnt;
   for (int inst = 0; inst < a0.n_inst; ++inst) {
     const int n = item_count(a0, inst), nf = front_count(a0, inst), ibase = inst_ibase(a0, inst);
@@ -2094,6 +2300,7 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.wk.trace = ctx->trace_list;
   a.wk.st_done = ctx->st_done;
   a.wk.cand_st = ctx->cand_st;
+  a.wk.bin = ctx->bin_cnt;
   a.wk.fx = ctx->acc_fx;
   a.wk.det = (o->flags & HR_DETERMINISTIC) != 0;
   a.node_stride = ctx->lim.max_F;
@@ -2149,17 +2356,26 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   }
   const int blocks = ctx->num_sms * ctx->tune.blocks_per_sm;
   tm.begin(kTimeFwdGather);
-  const int cull_blocks = ctx->num_sms * 4;   // one wave at k_cull's 64 registers
-  if (st)
-    k_cull<true><<<cull_blocks, kCullThreads, 0, s>>>(a, image, ctx->stats);
-  else
-    k_cull<false><<<cull_blocks, kCullThreads, 0, s>>>(a, image, nullptr);
-  HR_CHECK_LAUNCH();
-  if (st)
-    k_gather<false, true><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, ctx->stats);
-  else
-    k_gather<false, false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, nullptr);
-  HR_CHECK_LAUNCH();
+  // candidate lists: bin the (view, record) pairs into sub-tiles (count), give each
+  // sub-tile its pool range and work items (background sub-tiles written), bin again
+  // into the ranges (fill), order each list by nearest depth
+  if (cudaMemsetAsync(ctx->bin_cnt, 0, (size_t)a.total_st * sizeof(unsigned), s) != cudaSuccess) return HR_ERR_CUDA;
+  {
+    const long long pairs = (long long)a.nviews * (a.max_visits - 1);
+    const int bin_blocks = (int)std::min<long long>((pairs + kBinThreads - 1) / kBinThreads, 8LL * ctx->num_sms);
+    k_bin<false><<<std::max(bin_blocks, 1), kBinThreads, 0, s>>>(a, ctx->bin_cnt);
+    HR_CHECK_LAUNCH();
+    const int alloc_blocks = ctx->num_sms * 4;   // one wave at k_bin_alloc's 64 registers
+    if (st)
+      k_bin_alloc<true><<<alloc_blocks, kCullThreads, 0, s>>>(a, ctx->bin_cnt, image, ctx->stats);
+    else
+      k_bin_alloc<false><<<alloc_blocks, kCullThreads, 0, s>>>(a, ctx->bin_cnt, image, nullptr);
+    HR_CHECK_LAUNCH();
+    k_bin<true><<<std::max(bin_blocks, 1), kBinThreads, 0, s>>>(a, ctx->bin_cnt);
+    HR_CHECK_LAUNCH();
+    k_bin_sort<<<blocks, kRenderThreads, 0, s>>>(a);
+    HR_CHECK_LAUNCH();
+  }
   tm.end(kTimeFwdGather);
   tm.begin(kTimeFwdShade);
   {
@@ -2233,10 +2449,10 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
       else
         k_items_bwd<false><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, nullptr);
     } else if (st) {
-      k_gather<true, true><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, nullptr,
+      k_gather<true><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint,
                                                                           ctx->stats + kStatsPer);
     } else {
-      k_gather<true, false><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
+      k_gather<false><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, nullptr);
     }
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdGather);

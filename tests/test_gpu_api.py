@@ -162,6 +162,9 @@ def test_host_argument_errors(B):
     with pytest.raises(B.HandrtError) as e:           # spp 0
         B.hr_render_fwd(ctx, model, v, cams[:2], 16, 16, bg[:2], B.render_opts(spp=0), img[:2])
     assert e.value.code == B.HR_ERR_ARG
+    with pytest.raises(B.HandrtError) as e:           # edge offset beyond the candidate lists' reach
+        B.hr_render_fwd(ctx, model, v, cams[:2], 16, 16, bg[:2], B.render_opts(edge_eps_px=0.5), img[:2])
+    assert e.value.code == B.HR_ERR_ARG
     lim = B.hr_limits(100000, 10, 10, 1, 8, 8)
     hnd = ctypes.c_void_p()
     assert B.lib().hr_context_create(ctypes.byref(lim), ctypes.byref(hnd)) == B.HR_ERR_UNSUPPORTED
