@@ -1182,7 +1182,7 @@ __device__ __forceinline__ bool record_behind(const RenderArgs& a, const Cam& ca
 }
 
 constexpr int kBinThreads = 256;
-constexpr int kBinBig = 64;   // ranges of more sub-tiles are walked by the whole warp
+constexpr int kBinPairs = 8;   // (view, record) pairs per warp
 
 // one sub-tile of a pair's range: count it, or (FILL) write the record into the
 // sub-tile's pool range at the next free slot
@@ -1200,21 +1200,25 @@ __device__ __forceinline__ void bin_visit(const RenderArgs& a, unsigned* __restr
   a.wk.z[pk.x + slot] = zm;
 }
 
-// pair i = (active view i / F, record i % F); all lanes of a warp run the same trip
-// count so that large ranges can be shared by the warp
+// Each warp takes kBinPairs consecutive pairs i = (active view i / F, record i % F),
+// one per lane of its first lanes, and projects them; the (pair, sub-tile) visits of
+// all its pairs are then spread over the 32 lanes (visit q belongs to the pair whose
+// range of prefix sums holds q), so the visits of one warp are in flight together
+// whatever the sizes of the pairs' ranges.
 template <bool FILL>
 __global__ void __launch_bounds__(kBinThreads) k_bin(RenderArgs a0, unsigned* __restrict__ bin) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int F = a0.max_visits - 1;
   const long long total = (long long)visit_views(a0) * F;
-  const long long stride = (long long)gridDim.x * kBinThreads;
-  for (long long base = (long long)blockIdx.x * kBinThreads + (threadIdx.x & ~31); base < total; base += stride) {
-    const long long i = base + lane;
+  const long long nw = (long long)gridDim.x * (kBinThreads / 32);
+  for (long long w0 = ((long long)blockIdx.x * (kBinThreads / 32) + (threadIdx.x >> 5)) * kBinPairs; w0 < total;
+       w0 += nw * kBinPairs) {
+    const long long i = w0 + lane;
     int st0 = 0, nsx = 1, k = 0, area = 0;
     float zm = 0.0f;
     BinRange r{0, -1, 0, -1};
-    if (i < total) {
+    if (lane < kBinPairs && i < total) {
       const int g = visit_view(a0, (int)(i / F));
       k = (int)(i % F);
       SubTile t;
@@ -1230,22 +1234,91 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(RenderArgs a0, unsigned* __
         }
       }
     }
-    if (area > 0 && area <= kBinBig) {
-      for (int y = r.r0; y <= r.r1; ++y)
-        for (int x = r.c0; x <= r.c1; ++x) bin_visit<FILL>(a0, bin, st0 + y * nsx + x, k, zm);
+    // inclusive prefix sums of the ranges' sizes over the pairs
+    int incl = area;
+#pragma unroll
+    for (int o = 1; o < kBinPairs; o <<= 1) {
+      const int y = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += y;
     }
-    unsigned big = __ballot_sync(full, area > kBinBig);
-    while (big) {
-      const int src = __ffs(big) - 1;
-      big &= big - 1;
-      const int s0 = __shfl_sync(full, st0, src), n = __shfl_sync(full, nsx, src);
-      const int c0 = __shfl_sync(full, r.c0, src), c1 = __shfl_sync(full, r.c1, src);
-      const int r0 = __shfl_sync(full, r.r0, src), na = __shfl_sync(full, area, src);
-      const int kk = __shfl_sync(full, k, src);
-      const float z = __shfl_sync(full, zm, src);
-      const int w = c1 - c0 + 1;
-      for (int q = lane; q < na; q += 32) bin_visit<FILL>(a0, bin, s0 + (r0 + q / w) * n + c0 + q % w, kk, z);
+    const int T = __shfl_sync(full, incl, kBinPairs - 1);
+    for (int q0 = 0; q0 < T; q0 += 32) {
+      const int q = q0 + lane;
+      // owner: the first pair whose inclusive sum exceeds q
+      int lo = 0;
+#pragma unroll
+      for (int step = kBinPairs / 2; step > 0; step >>= 1) {
+        const int v = __shfl_sync(full, incl, lo + step - 1);
+        if (v <= q) lo += step;
+      }
+      const int own = min(lo, kBinPairs - 1);
+      const int s0 = __shfl_sync(full, st0, own), n = __shfl_sync(full, nsx, own);
+      const int c0 = __shfl_sync(full, r.c0, own), c1 = __shfl_sync(full, r.c1, own);
+      const int r0 = __shfl_sync(full, r.r0, own);
+      const int kk = __shfl_sync(full, k, own), end = __shfl_sync(full, incl, own);
+      const int na = __shfl_sync(full, area, own);
+      const float z = __shfl_sync(full, zm, own);
+      if (q >= T) continue;
+      const int w = c1 - c0 + 1, local = q - (end - na);
+      bin_visit<FILL>(a0, bin, s0 + (r0 + local / w) * n + c0 + local % w, kk, z);
     }
+  }
+}
+
+// Work items of the sub-tiles held by lanes 0 .. kCullGroup - 1 (all lanes call): each
+// `need` lane's sub-tile st (instance inst, candidate count K) gets C consecutive
+// items.  One reservation per instance among the lanes -- heavy items from the front
+// of the instance's region, the others from its back -- so the instance's counters
+// see one atomic per warp, not one per sub-tile.  Sub-tiles without a candidate list
+// (K < 0) are listed for k_overflow's per-ray traversal; when the region has no room
+// for a group, its sub-tiles go to k_overflow whole.
+__device__ __forceinline__ void place_items(const RenderArgs& a0, bool need, int st, int inst, int K, int C,
+                                            bool heavy) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int key = need ? inst : -1;
+  int hx = 0, lx = 0, ht = 0, lt = 0, leader = -1;
+#pragma unroll
+  for (int j = 0; j < kCullGroup; ++j) {
+    const int kj = __shfl_sync(full, key, j), cj = __shfl_sync(full, C, j);
+    const bool hj = __shfl_sync(full, (int)heavy, j) != 0;
+    if (need && kj == key) {
+      if (leader < 0) leader = j;
+      if (hj) {
+        ht += cj;
+        if (j < lane) hx += cj;
+      } else {
+        lt += cj;
+        if (j < lane) lx += cj;
+      }
+    }
+  }
+  unsigned long long v = 0ull;
+  if (need && lane == leader) {
+    v = atomicAdd(alloc_word(a0, inst), (unsigned long long)ht | ((unsigned long long)lt << 32));
+    const long long front = (long long)(v & 0xffffffffull), back = (long long)(v >> 32);
+    if (front + back + ht + lt <= inst_icap(a0, inst)) {
+      if (ht) atomicAdd(&a0.wk.ctr[2 + 2 * inst], (unsigned)ht);
+      if (lt) atomicAdd(back_count(a0, inst), (unsigned)lt);
+    }
+  }
+  const int src = leader < 0 ? 0 : leader;
+  const unsigned vlo = __shfl_sync(full, (unsigned)(v & 0xffffffffull), src);
+  const unsigned vhi = __shfl_sync(full, (unsigned)(v >> 32), src);
+  if (!need) return;
+  const int icap = inst_icap(a0, inst), ibase = inst_ibase(a0, inst);
+  const long long front = vlo, back = vhi;
+  const bool fits = front + back + ht + lt <= icap;
+  const int first = fits ? (heavy ? (int)front + hx : icap - (int)back - lt + lx) : -1;
+  if (first >= 0) {
+    for (int c = 0; c < C; ++c) a0.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
+    if (K < 0) {
+      const int tb = (int)atomicAdd(&a0.wk.ctr[ctr_trace(a0.n_inst)], (unsigned)C);
+      for (int c = 0; c < C; ++c)
+        if (tb + c < a0.wk.item_cap) a0.wk.trace[tb + c] = ibase + first + c;
+    }
+  } else {
+    a0.wk.ovf[atomicAdd(&a0.wk.ctr[2 + 2 * a0.n_inst], 1u)] = st;
   }
 }
 
@@ -1301,29 +1374,19 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_bin_alloc(RenderArgs a0, un
     unsigned base = 0u;
     if (lane == 31 && incl > 0) base = atomicAdd(&a0.wk.ctr[1], (unsigned)incl);
     base = __shfl_sync(full, base, 31);
-    bool sorted = false;
+    bool sorted = false, heavy = false;
+    int Kc = 0, C = 0;
     if (listed) {
-      const RenderArgs a = for_inst(a0, t.inst);
       const long long off = (long long)base + incl - want;
-      int Kc = K;
+      Kc = K;
       if (K > kLeafCap) Kc = -1;
-      else if (off + K > a.wk.pool_cap) Kc = -(K + 1);
+      else if (off + K > a0.wk.pool_cap) Kc = -(K + 1);
       sorted = Kc > 0;
-      a.wk.st[st] = make_int2(sorted ? (int)off : 0, Kc);
-      const int C = chunks_for(a, Kc, t.spp);
-      const int ibase = inst_ibase(a, t.inst);
-      const int first = alloc_items(a, t.inst, C, heavy_item(a, Kc, C, t.spp), inst_icap(a, t.inst));
-      if (first >= 0) {
-        for (int c = 0; c < C; ++c) a.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
-        if (Kc < 0) {   // listed for k_overflow, which traces them ray by ray
-          const int tb = (int)atomicAdd(&a.wk.ctr[ctr_trace(a.n_inst)], (unsigned)C);
-          for (int c = 0; c < C; ++c)
-            if (tb + c < a.wk.item_cap) a.wk.trace[tb + c] = ibase + first + c;
-        }
-      } else {   // item region full: the whole sub-tile goes to k_overflow
-        a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
-      }
+      a0.wk.st[st] = make_int2(sorted ? (int)off : 0, Kc);
+      C = chunks_for(a0, Kc, t.spp);
+      heavy = heavy_item(a0, Kc, C, t.spp);
     }
+    place_items(a0, listed, st, t.inst, Kc, C, heavy);
     const unsigned sm = __ballot_sync(full, sorted);
     int lb = 0;
     if (lane == 0 && sm) lb = (int)atomicAdd(&a0.wk.ctr[ctr_cull(a0.n_inst)], (unsigned)__popc(sm));
@@ -1362,7 +1425,8 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_bin_alloc(RenderArgs a0, un
 }
 
 // one warp per listed sub-tile: its K records (in fill order) sorted by nearest depth
-// (bitonic, padded with +inf), then written back with their screen boxes
+// (bitonic, padded with +inf: across the lanes' registers for K <= 32, else in shared
+// memory), then written back with their screen boxes
 struct SortSmem {   // per warp
   int leaf[kLeafCap];
   float key[kLeafCap];
@@ -1384,6 +1448,42 @@ __global__ void __launch_bounds__(kRenderThreads) k_bin_sort(RenderArgs a0) {
     if (K <= 0 || K > kLeafCap || off < 0 || !in_range(a0.status, (long long)off + K - 1, 0, a0.wk.pool_cap)) continue;
     const RenderArgs a = for_inst(a0, t.inst);
     const Cam cam = load_cam(a.cams, t.view);
+    if (K <= 32) {
+      // one record per lane, projected, then a bitonic sort of (depth, lane) across the
+      // warp; lane c then takes the c-th record's box and index from its lane
+      int k = 0;
+      float4 bb = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      float key = INFINITY;
+      if (lane < K) {
+        k = a.wk.rec[off + lane];
+        if (!in_range(a.status, k, 0, a.max_visits - 1)) k = 0;
+        project_record(a, cam, k, bb, key);
+      }
+      int src = lane;
+#pragma unroll
+      for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+          const float ok = __shfl_xor_sync(0xffffffffu, key, stride);
+          const int os = __shfl_xor_sync(0xffffffffu, src, stride);
+          const bool take_min = ((lane & stride) == 0) == ((lane & size) == 0);
+          const bool take = take_min ? (ok < key || (ok == key && os < src)) : (ok > key || (ok == key && os > src));
+          if (take) {
+            key = ok;
+            src = os;
+          }
+        }
+      }
+      const int kc = __shfl_sync(0xffffffffu, k, src);
+      const float4 bc = make_float4(__shfl_sync(0xffffffffu, bb.x, src), __shfl_sync(0xffffffffu, bb.y, src),
+                                    __shfl_sync(0xffffffffu, bb.z, src), __shfl_sync(0xffffffffu, bb.w, src));
+      if (lane < K) {
+        a.wk.bb[off + lane] = bc;
+        a.wk.z[off + lane] = key;
+        a.wk.rec[off + lane] = kc;
+      }
+      continue;
+    }
     int P = 1;
     while (P < K) P <<= 1;
     for (int j = lane; j < P; j += 32) {
@@ -1553,44 +1653,63 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
   flush_counts<STATS>(cnt, stats);
 }
 
-// The backward's work items from the forward's candidate lists (HR_BWD_REUSE_FWD):
-// one warp per sub-tile with candidates and a non-zero adjoint allocates its items in
-// its instance's region; when the region is full the warp does the sub-tile itself.
+// The backward's work items from the forward's candidate lists (HR_BWD_REUSE_FWD).
+// Each warp takes kCullGroup consecutive sub-tiles, one per lane of its first lanes;
+// only sub-tiles with a candidate list (or per-ray traversal) read the adjoint, the
+// whole warp loading all of them first (lane = pixel), and those with a non-zero
+// adjoint get their work items (place_items).
 template <bool STATS>
-__global__ void __launch_bounds__(kRenderThreads) k_items_bwd(RenderArgs a_in, const float* __restrict__ adjoint,
-                                                             unsigned long long* stats) {
-  const RenderArgs a0 = with_iter(a_in);
+__global__ void __launch_bounds__(kCullThreads, 4) k_items_bwd(RenderArgs a0, const float* __restrict__ adjoint,
+                                                               unsigned long long* stats) {
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   Counts cnt;
   const int total = visit_count(a0);
-  const int nw = gridDim.x * kWarps;
-  for (int vi = blockIdx.x * kWarps + (threadIdx.x >> 5); vi < total; vi += nw) {
-    const int st = visit_subtile(a0, vi);
-    if (!in_range(a0.status, st, 0, a0.total_st)) continue;
-    int2 pk = a0.wk.st[st];
-    const SubTile t = subtile(a0, st);
-    if (!in_range(a0.status, t.inst, 0, a0.n_inst) || !inst_active(a0, t.inst)) continue;
-    const RenderArgs a = for_inst(a0, t.inst);
-    bool live;
-    const float3 g = lane_adjoint(a, t, adjoint, live);
-    if (!__any_sync(0xffffffffu, live)) continue;
-    if (pk.y == 0) {   // no ray of the sub-tile can hit: no interior gradient
-      if (STATS && live) cnt.samples += t.spp;
-      continue;
+  const int nw = gridDim.x * (kCullThreads / 32);
+  for (int g0 = (blockIdx.x * (kCullThreads / 32) + (threadIdx.x >> 5)) * kCullGroup; g0 < total;
+       g0 += nw * kCullGroup) {
+    int st = -1;
+    int2 pk = make_int2(0, 0);
+    bool ok = false;
+    SubTile t{};
+    if (lane < kCullGroup && g0 + lane < total) {
+      const int s = visit_subtile(a0, g0 + lane);
+      if (in_range(a0.status, s, 0, a0.total_st)) {
+        t = subtile(a0, s);
+        if (in_range(a0.status, t.inst, 0, a0.n_inst) && inst_active(a0, t.inst)) {
+          st = s;
+          ok = true;
+          pk = a0.wk.st[s];
+          if (pk.y > 0 && !in_range(a0.status, (long long)pk.x + pk.y - 1, 0, a0.wk.pool_cap)) pk.y = -1;
+        }
+      }
     }
-    if (pk.y > 0 && !in_range(a.status, (long long)pk.x + pk.y - 1, 0, a.wk.pool_cap)) pk.y = -1;
-    const int C = chunks_for(a, pk.y, t.spp);
-    const int ibase = inst_ibase(a, t.inst), icap = inst_icap(a, t.inst);
-    int first = 0;
-    if (lane == 0) first = alloc_items(a, t.inst, C, heavy_item(a, pk.y, C, t.spp), icap);
-    first = __shfl_sync(0xffffffffu, first, 0);
-    if (first >= 0) {
-      for (int c = lane; c < C; c += 32) a.wk.items[ibase + first + c] = make_int4(st, c, C, ibase + first);
-      if (pk.y < 0) note_trace_items(a, ibase + first, C);
-    } else if (lane == 0) {
-      a.wk.ovf[atomicAdd(&a.wk.ctr[2 + 2 * a.n_inst], 1u)] = st;
+    // sub-tile j's pixels: lane = pixel; every adjoint load issued before the tests
+    const unsigned look = __ballot_sync(full, ok && (STATS || pk.y != 0));
+    if (!look) continue;
+    float3 g[kCullGroup];
+    bool valid[kCullGroup];
+#pragma unroll
+    for (int j = 0; j < kCullGroup; ++j) {
+      const int x0 = __shfl_sync(full, t.x0, j), y0 = __shfl_sync(full, t.y0, j);
+      const int W = __shfl_sync(full, t.W, j), H = __shfl_sync(full, t.H, j);
+      const long long p0 = __shfl_sync(full, t.pix0, j);
+      const int px = x0 + (lane % kSubW), py = y0 + (lane / kSubW);
+      valid[j] = ((look >> j) & 1u) && px < W && py < H;
+      g[j] = valid[j] ? ld3(adjoint + 3 * ((size_t)p0 + (size_t)py * W + px)) : make_float3(0.0f, 0.0f, 0.0f);
     }
-    __syncwarp();
+    unsigned live = 0u;
+#pragma unroll
+    for (int j = 0; j < kCullGroup; ++j) {
+      const bool lj = valid[j] && (g[j].x != 0.0f || g[j].y != 0.0f || g[j].z != 0.0f);
+      if (__ballot_sync(full, lj)) live |= 1u << j;
+      const int kj = __shfl_sync(full, pk.y, j), sppj = __shfl_sync(full, t.spp, j);
+      if (STATS && lj && kj == 0) cnt.samples += sppj;   // no ray of the sub-tile can hit
+    }
+    const bool need = ok && ((live >> lane) & 1u) && pk.y != 0;
+    const int C = need ? chunks_for(a0, pk.y, t.spp) : 0;
+    const bool heavy = need && heavy_item(a0, pk.y, C, t.spp);
+    place_items(a0, need, st, t.inst, pk.y, C, heavy);
   }
   flush_counts<STATS>(cnt, stats);
 }
@@ -2362,7 +2481,8 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   if (cudaMemsetAsync(ctx->bin_cnt, 0, (size_t)a.total_st * sizeof(unsigned), s) != cudaSuccess) return HR_ERR_CUDA;
   {
     const long long pairs = (long long)a.nviews * (a.max_visits - 1);
-    const int bin_blocks = (int)std::min<long long>((pairs + kBinThreads - 1) / kBinThreads, 8LL * ctx->num_sms);
+    const long long bin_warps = (pairs + kBinPairs - 1) / kBinPairs;
+    const int bin_blocks = (int)std::min<long long>((bin_warps + kBinThreads / 32 - 1) / (kBinThreads / 32), 8LL * ctx->num_sms);
     k_bin<false><<<std::max(bin_blocks, 1), kBinThreads, 0, s>>>(a, ctx->bin_cnt);
     HR_CHECK_LAUNCH();
     const int alloc_blocks = ctx->num_sms * 4;   // one wave at k_bin_alloc's 64 registers
@@ -2445,9 +2565,9 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     tm.begin(kTimeBwdGather);
     if (reuse) {
       if (st)
-        k_items_bwd<true><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, ctx->stats + kStatsPer);
+        k_items_bwd<true><<<ctx->num_sms * 4, kCullThreads, 0, s>>>(a, adjoint, ctx->stats + kStatsPer);
       else
-        k_items_bwd<false><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, nullptr);
+        k_items_bwd<false><<<ctx->num_sms * 4, kCullThreads, 0, s>>>(a, adjoint, nullptr);
     } else if (st) {
       k_gather<true><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint,
                                                                           ctx->stats + kStatsPer);
