@@ -81,13 +81,13 @@ def ncu_traffic(kernel):
     if src != render_source_hash():
         return None, "the kernel source changed since the capture"
     return nbytes, f"ncu dram__bytes_read.sum + dram__bytes_write.sum, sources {src}"
-# kernels of one step: skin 1, BVH + normals 2, forward 6 (bin count, bin alloc, bin
-# fill, bin sort, shade, overflow), loss 2, backward 8 (items, shade, overflow, reduce,
-# silhouettes, edge samples, normal adjoint 2), skin adjoint 1, Adam 1
-LAUNCHES_PER_STEP = 21
+# kernels of one step: skin 1, BVH + normals 2, forward 7 (bin count, bin alloc,
+# background, bin fill, bin sort, shade, overflow), loss 2, backward 8 (items, shade,
+# overflow, reduce, silhouettes, edge samples, normal adjoint 2), skin adjoint 1, Adam 1
+LAUNCHES_PER_STEP = 22
 # a batched iteration: the same kernels (one launch each over all instances), the
 # vertex-error kernel and the active-instance layout before the forward and backward
-LAUNCHES_BATCH_ITER = 24
+LAUNCHES_BATCH_ITER = 25
 
 
 def env_rank():

@@ -139,7 +139,8 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
                cudaMemset(c->stats, 0, 3 * hr::kStatsPer * sizeof(unsigned long long)) == cudaSuccess &&
                cudaMemset(c->nodes, 0, ni * F * sizeof(hr::Node)) == cudaSuccess &&
                cudaMemset(c->bvh_valid, 0, ni * sizeof(int)) == cudaSuccess &&
-               cudaMemset(c->st_done, 0, subtiles * sizeof(unsigned)) == cudaSuccess;
+               cudaMemset(c->st_done, 0, subtiles * sizeof(unsigned)) == cudaSuccess &&
+               cudaMemset(c->bin_cnt, 0, subtiles * sizeof(unsigned)) == cudaSuccess;
   for (int i = 0; ok && i < 2 * hr::kTimeSlots; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
   if (ok)
     ok = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&

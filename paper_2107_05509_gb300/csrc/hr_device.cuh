@@ -123,7 +123,7 @@ struct Context {
   int* ovf_list;         // [sub-tiles] sub-tiles whose items overflowed their region
   int* trace_list;       // [item_cap] items of sub-tiles without a candidate list (per-ray traversal)
   unsigned* st_done;     // [sub-tiles] forward items finished per sub-tile (zero between launches)
-  int* cand_st;          // [sub-tiles] forward sub-tiles whose candidate lists are sorted
+  int4* cand_st;         // [sub-tiles] forward lists to sort: (sub-tile, pool offset, K, 0)
   unsigned* bin_cnt;     // [sub-tiles] records binned per sub-tile (zeroed by every forward)
   // backward scratch
   float* partials;       // [render_blocks][max_V][6] (single-instance contexts)

@@ -209,7 +209,8 @@ struct Work {
   int* trace;      // [items] region slots (+ instance base) of the items of sub-tiles
                    // without a candidate list (k_overflow traces them ray by ray)
   unsigned* st_done;   // [sub-tiles] forward items finished (the last one combines)
-  int* cand_st;        // [sub-tiles] forward sub-tiles whose lists k_bin_sort orders (count: ctr_cull)
+  int4* cand_st;       // [sub-tiles] forward lists k_bin_sort orders: (sub-tile, pool offset, K, 0)
+                       // (count: ctr_cull)
   unsigned* bin;       // [sub-tiles] records binned per sub-tile, then the fill's slot counter
   unsigned long long* fx;   // [n_inst][6V] fixed-point backward sums (HR_DETERMINISTIC)
   bool det;                 // HR_DETERMINISTIC: every vertex-gradient sum goes to fx
@@ -1187,7 +1188,8 @@ constexpr int kBinPairs = 8;   // (view, record) pairs per warp
 // one sub-tile of a pair's range: count it, or (FILL) write the record into the
 // sub-tile's pool range at the next free slot
 template <bool FILL>
-__device__ __forceinline__ void bin_visit(const RenderArgs& a, unsigned* __restrict__ bin, int s, int k, float zm) {
+__device__ __forceinline__ void bin_visit(const RenderArgs& a, unsigned* __restrict__ bin, int s, int k, float zm,
+                                          float4 bb) {
   if (!FILL) {
     atomicAdd(&bin[s], 1u);
     return;
@@ -1198,6 +1200,7 @@ __device__ __forceinline__ void bin_visit(const RenderArgs& a, unsigned* __restr
   if (slot >= pk.y || !in_range(a.status, (long long)pk.x + slot, 0, a.wk.pool_cap)) return;
   a.wk.rec[pk.x + slot] = k;
   a.wk.z[pk.x + slot] = zm;
+  a.wk.bb[pk.x + slot] = bb;
 }
 
 // Each warp takes kBinPairs consecutive pairs i = (active view i / F, record i % F),
@@ -1217,6 +1220,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(RenderArgs a0, unsigned* __
     const long long i = w0 + lane;
     int st0 = 0, nsx = 1, k = 0, area = 0;
     float zm = 0.0f;
+    float4 bb = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     BinRange r{0, -1, 0, -1};
     if (lane < kBinPairs && i < total) {
       const int g = visit_view(a0, (int)(i / F));
@@ -1227,7 +1231,6 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(RenderArgs a0, unsigned* __
         const RenderArgs a = for_inst(a0, t.inst);
         const Cam cam = load_cam(a.cams, g);
         if (!record_behind(a, cam, k)) {
-          float4 bb;
           project_record(a, cam, k, bb, zm);
           r = bin_range(bb, nsx, (t.H + kSubH - 1) / kSubH);
           if (r.c0 <= r.c1 && r.r0 <= r.r1) area = (r.c1 - r.c0 + 1) * (r.r1 - r.r0 + 1);
@@ -1258,9 +1261,16 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(RenderArgs a0, unsigned* __
       const int kk = __shfl_sync(full, k, own), end = __shfl_sync(full, incl, own);
       const int na = __shfl_sync(full, area, own);
       const float z = __shfl_sync(full, zm, own);
+      float4 b = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (FILL) {
+        b.x = __shfl_sync(full, bb.x, own);
+        b.y = __shfl_sync(full, bb.y, own);
+        b.z = __shfl_sync(full, bb.z, own);
+        b.w = __shfl_sync(full, bb.w, own);
+      }
       if (q >= T) continue;
       const int w = c1 - c0 + 1, local = q - (end - na);
-      bin_visit<FILL>(a0, bin, s0 + (r0 + local / w) * n + c0 + local % w, kk, z);
+      bin_visit<FILL>(a0, bin, s0 + (r0 + local / w) * n + c0 + local % w, kk, z, b);
     }
   }
 }
@@ -1323,24 +1333,20 @@ __device__ __forceinline__ void place_items(const RenderArgs& a0, bool need, int
 }
 
 // Each warp takes kCullGroup consecutive sub-tiles, one per lane of its first lanes.
-// A sub-tile with no record in its bin sees only the background: the whole warp
-// writes its pixels, lane = pixel, every background load issued before the first
-// store.  The others get a pool range for their K records (one atomic per warp), the
-// work items of their chunks, and a place in the list k_bin_sort orders; the count
+// A sub-tile with no record in its bin sees only the background (k_background writes
+// it).  The others get a pool range for their K records (one atomic per warp), the
+// work items of their chunks, and an entry in the list k_bin_sort orders; the count
 // becomes the fill's slot counter.  A sub-tile with more records than a list holds,
 // or whose records find no pool room, is traced ray by ray (K = -1, -(K + 1)).
-template <bool STATS>
-__global__ void __launch_bounds__(kCullThreads, 4) k_bin_alloc(RenderArgs a0, unsigned* __restrict__ bin,
-                                                               float* __restrict__ image, unsigned long long* stats) {
+__global__ void __launch_bounds__(kCullThreads) k_bin_alloc(RenderArgs a0, unsigned* __restrict__ bin) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  Counts cnt;
   const int total = visit_count(a0);
   const int nw = gridDim.x * (kCullThreads / 32);
   for (int g0 = (blockIdx.x * (kCullThreads / 32) + (threadIdx.x >> 5)) * kCullGroup; g0 < total;
        g0 += nw * kCullGroup) {
     int st = -1, K = 0;
-    bool culled = false, listed = false;
+    bool listed = false;
     SubTile t{};
     if (lane < kCullGroup && g0 + lane < total) {
       const int s = visit_subtile(a0, g0 + lane);
@@ -1353,12 +1359,8 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_bin_alloc(RenderArgs a0, un
           } else {
             K = (int)bin[s];
             bin[s] = 0u;
-            if (K == 0) {
-              a0.wk.st[s] = make_int2(0, 0);
-              culled = true;
-            } else {
-              listed = true;
-            }
+            if (K == 0) a0.wk.st[s] = make_int2(0, 0);
+            else listed = true;
           }
         }
       }
@@ -1367,17 +1369,19 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_bin_alloc(RenderArgs a0, un
     const int want = listed && K <= kLeafCap ? K : 0;
     int incl = want;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    for (int o = 1; o < kCullGroup; o <<= 1) {
       const int y = __shfl_up_sync(full, incl, o);
       if (lane >= o) incl += y;
     }
     unsigned base = 0u;
-    if (lane == 31 && incl > 0) base = atomicAdd(&a0.wk.ctr[1], (unsigned)incl);
-    base = __shfl_sync(full, base, 31);
+    const int tot = __shfl_sync(full, incl, kCullGroup - 1);
+    if (lane == 0 && tot > 0) base = atomicAdd(&a0.wk.ctr[1], (unsigned)tot);
+    base = __shfl_sync(full, base, 0);
     bool sorted = false, heavy = false;
     int Kc = 0, C = 0;
+    long long off = 0;
     if (listed) {
-      const long long off = (long long)base + incl - want;
+      off = (long long)base + incl - want;
       Kc = K;
       if (K > kLeafCap) Kc = -1;
       else if (off + K > a0.wk.pool_cap) Kc = -(K + 1);
@@ -1391,10 +1395,36 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_bin_alloc(RenderArgs a0, un
     int lb = 0;
     if (lane == 0 && sm) lb = (int)atomicAdd(&a0.wk.ctr[ctr_cull(a0.n_inst)], (unsigned)__popc(sm));
     lb = __shfl_sync(full, lb, 0);
-    if (sorted) a0.wk.cand_st[lb + __popc(sm & lanemask_lt())] = st;
+    if (sorted) a0.wk.cand_st[lb + __popc(sm & lanemask_lt())] = make_int4(st, (int)off, Kc, 0);
+  }
+}
+
+// Pixels of the sub-tiles whose bins hold no record: the background (the value
+// write_pixel gives a sub-tile whose samples all miss).  Each warp takes kCullGroup
+// consecutive sub-tiles, one per lane of its first lanes, then writes the background
+// ones, lane = pixel, every background load issued before the first store.  Runs on
+// the context's second stream beside the fill and the sort, which touch no pixel.
+template <bool STATS>
+__global__ void __launch_bounds__(kCullThreads) k_background(RenderArgs a0, float* __restrict__ image,
+                                                             unsigned long long* stats) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  Counts cnt;
+  const int total = visit_count(a0);
+  const int nw = gridDim.x * (kCullThreads / 32);
+  for (int g0 = (blockIdx.x * (kCullThreads / 32) + (threadIdx.x >> 5)) * kCullGroup; g0 < total;
+       g0 += nw * kCullGroup) {
+    bool culled = false;
+    SubTile t{};
+    if (lane < kCullGroup && g0 + lane < total) {
+      const int s = visit_subtile(a0, g0 + lane);
+      if (in_range(a0.status, s, 0, a0.total_st)) {
+        t = subtile(a0, s);
+        culled = in_range(a0.status, t.inst, 0, a0.n_inst) && inst_active(a0, t.inst) && a0.wk.st[s].y == 0;
+      }
+    }
     const unsigned cm = __ballot_sync(full, culled);
     if (!cm) continue;
-    // background sub-tiles: lane = pixel; loads first, then the stores
     float3 bgv[kCullGroup];
     size_t pix[kCullGroup];
     bool valid[kCullGroup];
@@ -1413,7 +1443,6 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_bin_alloc(RenderArgs a0, un
       const int spp = __shfl_sync(full, t.spp, j);
       if (!valid[j]) continue;
       if (STATS) cnt.samples += spp;   // resolved by the binning: no record meets the sub-tile
-      // the pixel write_pixel gives a sub-tile whose samples all miss
       const float fm = __fdiv_rn((float)spp, (float)spp);
       const float inv_spp = 1.0f / (float)spp;
       image[3 * pix[j]] = 0.0f * inv_spp + bgv[j].x * fm;
@@ -1426,7 +1455,7 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_bin_alloc(RenderArgs a0, un
 
 // one warp per listed sub-tile: its K records (in fill order) sorted by nearest depth
 // (bitonic, padded with +inf: across the lanes' registers for K <= 32, else in shared
-// memory), then written back with their screen boxes
+// memory, the boxes then projected again from the records), written back in order
 struct SortSmem {   // per warp
   int leaf[kLeafCap];
   float key[kLeafCap];
@@ -1439,25 +1468,22 @@ __global__ void __launch_bounds__(kRenderThreads) k_bin_sort(RenderArgs a0) {
   const int n = (int)min(*reinterpret_cast<volatile unsigned*>(&a0.wk.ctr[ctr_cull(a0.n_inst)]),
                          (unsigned)a0.total_st);
   for (int vi = blockIdx.x * kWarps + (threadIdx.x >> 5); vi < n; vi += gridDim.x * kWarps) {
-    const int st = a0.wk.cand_st[vi];
+    const int4 cd = a0.wk.cand_st[vi];
+    const int st = cd.x, off = cd.y, K = cd.z;
     if (!in_range(a0.status, st, 0, a0.total_st)) continue;
-    const SubTile t = subtile(a0, st);
-    if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
-    const int2 pk = a0.wk.st[st];
-    const int K = pk.y, off = pk.x;
+    if (lane == 0) a0.wk.bin[st] = 0u;   // the fill's slot counter, clear for the next forward
     if (K <= 0 || K > kLeafCap || off < 0 || !in_range(a0.status, (long long)off + K - 1, 0, a0.wk.pool_cap)) continue;
-    const RenderArgs a = for_inst(a0, t.inst);
-    const Cam cam = load_cam(a.cams, t.view);
     if (K <= 32) {
-      // one record per lane, projected, then a bitonic sort of (depth, lane) across the
-      // warp; lane c then takes the c-th record's box and index from its lane
+      // one record per lane (depth, box and index as the fill wrote them), a bitonic
+      // sort of (depth, lane) across the warp; lane c then takes the c-th record's box
+      // and index from its lane
       int k = 0;
       float4 bb = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       float key = INFINITY;
       if (lane < K) {
-        k = a.wk.rec[off + lane];
-        if (!in_range(a.status, k, 0, a.max_visits - 1)) k = 0;
-        project_record(a, cam, k, bb, key);
+        k = a0.wk.rec[off + lane];
+        key = a0.wk.z[off + lane];
+        bb = a0.wk.bb[off + lane];
       }
       int src = lane;
 #pragma unroll
@@ -1478,12 +1504,16 @@ __global__ void __launch_bounds__(kRenderThreads) k_bin_sort(RenderArgs a0) {
       const float4 bc = make_float4(__shfl_sync(0xffffffffu, bb.x, src), __shfl_sync(0xffffffffu, bb.y, src),
                                     __shfl_sync(0xffffffffu, bb.z, src), __shfl_sync(0xffffffffu, bb.w, src));
       if (lane < K) {
-        a.wk.bb[off + lane] = bc;
-        a.wk.z[off + lane] = key;
-        a.wk.rec[off + lane] = kc;
+        a0.wk.bb[off + lane] = bc;
+        a0.wk.z[off + lane] = key;
+        a0.wk.rec[off + lane] = kc;
       }
       continue;
     }
+    const SubTile t = subtile(a0, st);
+    if (!in_range(a0.status, t.inst, 0, a0.n_inst)) continue;
+    const RenderArgs a = for_inst(a0, t.inst);
+    const Cam cam = load_cam(a.cams, t.view);
     int P = 1;
     while (P < K) P <<= 1;
     for (int j = lane; j < P; j += 32) {
@@ -2476,21 +2506,31 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   const int blocks = ctx->num_sms * ctx->tune.blocks_per_sm;
   tm.begin(kTimeFwdGather);
   // candidate lists: bin the (view, record) pairs into sub-tiles (count), give each
-  // sub-tile its pool range and work items (background sub-tiles written), bin again
-  // into the ranges (fill), order each list by nearest depth
-  if (cudaMemsetAsync(ctx->bin_cnt, 0, (size_t)a.total_st * sizeof(unsigned), s) != cudaSuccess) return HR_ERR_CUDA;
+  // sub-tile its pool range and work items, bin again into the ranges (fill), order
+  // each list by nearest depth.  The bins are zero between forwards (cleared once at
+  // creation, then by k_bin_alloc and k_bin_sort).  The background sub-tiles' pixels
+  // are written on the context's second stream beside the fill and the sort (with
+  // kernel timing on, on the caller's stream), joined before the call returns.
+  const bool fork = !tm.on;
+  cudaStream_t bs = fork ? ctx->side : s;
   {
     const long long pairs = (long long)a.nviews * (a.max_visits - 1);
     const long long bin_warps = (pairs + kBinPairs - 1) / kBinPairs;
     const int bin_blocks = (int)std::min<long long>((bin_warps + kBinThreads / 32 - 1) / (kBinThreads / 32), 8LL * ctx->num_sms);
     k_bin<false><<<std::max(bin_blocks, 1), kBinThreads, 0, s>>>(a, ctx->bin_cnt);
     HR_CHECK_LAUNCH();
-    const int alloc_blocks = ctx->num_sms * 4;   // one wave at k_bin_alloc's 64 registers
-    if (st)
-      k_bin_alloc<true><<<alloc_blocks, kCullThreads, 0, s>>>(a, ctx->bin_cnt, image, ctx->stats);
-    else
-      k_bin_alloc<false><<<alloc_blocks, kCullThreads, 0, s>>>(a, ctx->bin_cnt, image, nullptr);
+    const int group_blocks = ctx->num_sms * 8;
+    k_bin_alloc<<<group_blocks, kCullThreads, 0, s>>>(a, ctx->bin_cnt);
     HR_CHECK_LAUNCH();
+    if (fork && (cudaEventRecord(ctx->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(bs, ctx->ev_fork, 0) != cudaSuccess))
+      return HR_ERR_CUDA;
+    const int bg_blocks = ctx->num_sms * 4;   // one wave at k_background's 64 registers
+    if (st)
+      k_background<true><<<bg_blocks, kCullThreads, 0, bs>>>(a, image, ctx->stats);
+    else
+      k_background<false><<<bg_blocks, kCullThreads, 0, bs>>>(a, image, nullptr);
+    HR_CHECK_LAUNCH();
+    if (fork && cudaEventRecord(ctx->ev_join, bs) != cudaSuccess) return HR_ERR_CUDA;
     k_bin<true><<<std::max(bin_blocks, 1), kBinThreads, 0, s>>>(a, ctx->bin_cnt);
     HR_CHECK_LAUNCH();
     k_bin_sort<<<blocks, kRenderThreads, 0, s>>>(a);
@@ -2510,6 +2550,7 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
   else
     k_overflow<false, false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, nullptr);
   HR_CHECK_LAUNCH();
+  if (fork && cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess) return HR_ERR_CUDA;
   tm.end(kTimeFwdShade);
   // the item sums are combined inside the shaders (finish_item): the slot stays, empty
   tm.begin(kTimeFwdCombine);
