@@ -245,12 +245,17 @@ int hr_build_bvh(hr_context* ctx, const hr_model* model, const float* verts, hr_
 /* Rebuild or refit: with iter_dev (device uint32) and rebuild_every > 1, the tree is
  * rebuilt when *iter_dev is a multiple of rebuild_every (or when this context has no
  * tree of the model's faces yet) and otherwise refitted -- the topology and leaf
- * order of the last build kept, triangle records and boxes recomputed from verts --
- * the choice taken on the device, so a captured iteration replays it.  Any tree whose
- * boxes contain their children gives the same hits and candidate sets, so refitting
- * changes speed only.  iter_dev NULL or rebuild_every = 1: hr_build_bvh.  Works on
- * single-instance and batch contexts (verts [n][V][3] for a batch); the vertex
- * normals are recomputed every call. */
+ * order of the last build kept, triangle records recomputed from verts -- the choice
+ * taken on the device, so a captured iteration replays it.  On meshes the one-block
+ * build holds (the paper-sized hand), a refit iteration rewrites only the records;
+ * the boxes are refitted from them by the first later call that traverses the tree:
+ * a forward render with a sub-tile left to per-ray traversal, a backward without
+ * HR_BWD_REUSE_FWD, or hr_trace (the forward's candidate lists come from the
+ * records' screen boxes, not from the tree).  Any tree whose boxes contain their
+ * children gives the same hits and candidate sets, so refitting changes speed only.
+ * iter_dev NULL or rebuild_every = 1: hr_build_bvh.  Works on single-instance and
+ * batch contexts (verts [n][V][3] for a batch); the vertex normals are recomputed
+ * every call. */
 int hr_update_bvh(hr_context* ctx, const hr_model* model, const float* verts, const uint32_t* iter_dev,
                   int rebuild_every, hr_stream stream);
 

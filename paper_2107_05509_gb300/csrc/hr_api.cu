@@ -41,12 +41,12 @@ void free_ctx(Context* c) {
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->side) cudaStreamDestroy(c->side);
   void* ptrs[] = {c->nodes,   c->tris,    c->normals,   c->normal_len, c->partials,      c->dN,
-                  c->dm,      c->sil,     c->sil_count, c->loss_partials, c->counters,   c->skin_partials,
+                  c->sil,     c->sil_count, c->loss_partials, c->counters,   c->skin_partials,
                   c->status,  c->stats,   c->pool_bb,   c->pool_z,     c->pool_rec,      c->st_info,
                   c->items,   c->item_part, c->extra,   c->work_ctr,   c->vt,            c->it,
                   c->bvh_parent, c->bvh_valid, c->bvh_keys, c->bvh_flags, c->bvh_bounds, c->bvh_bad,
                   c->bvh_mode, c->extra64, c->ct_partials, c->dedge, c->ovf_list, c->acc_fx, c->act_off,
-                  c->trace_list, c->st_done, c->cand_st, c->bin_cnt};
+                  c->trace_list, c->st_done, c->cand_st, c->bin_cnt, c->bvh_stale, c->bvh_need};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete[] c->hvt;
@@ -113,7 +113,7 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
             dev_alloc(&c->normals, ni * 3 * V, a) && dev_alloc(&c->normal_len, ni * V, a) &&
             dev_alloc(&c->partials, partial_blocks * 6 * V, a) && dev_alloc(&c->dN, ni * 3 * V, a) &&
             dev_alloc(&c->dedge, ni * 3 * V, a) && dev_alloc(&c->acc_fx, ni * 6 * V, a) &&
-            dev_alloc(&c->dm, ni * 3 * V, a) && dev_alloc(&c->sil, nviews * lim->max_E, a) &&
+            dev_alloc(&c->sil, nviews * lim->max_E, a) &&
             dev_alloc(&c->sil_count, nviews, a) &&
             dev_alloc(&c->loss_partials, ni * hr::kLossStride(c->loss_blocks), a) &&
             dev_alloc(&c->counters, ni * 4, a) && dev_alloc(&c->skin_partials, ni * hr::kSkinBlocks * hr::kSkinAcc, a) &&
@@ -126,7 +126,8 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
             dev_alloc(&c->st_done, subtiles, a) && dev_alloc(&c->cand_st, subtiles, a) &&
             dev_alloc(&c->bin_cnt, subtiles, a) &&
             dev_alloc(&c->bvh_parent, ni * 2 * F, a) && dev_alloc(&c->bvh_valid, ni, a) &&
-            dev_alloc(&c->bvh_bounds, ni * 6, a) && dev_alloc(&c->bvh_bad, ni, a) && dev_alloc(&c->bvh_mode, ni, a);
+            dev_alloc(&c->bvh_bounds, ni * 6, a) && dev_alloc(&c->bvh_bad, ni, a) && dev_alloc(&c->bvh_mode, ni, a) &&
+            dev_alloc(&c->bvh_stale, ni, a) && dev_alloc(&c->bvh_need, ni, a);
   // keys of the multi-block build, for meshes beyond one block's shared memory
   c->bvh_pmax = 1;
   while ((size_t)c->bvh_pmax < F) c->bvh_pmax <<= 1;
@@ -140,7 +141,9 @@ int create_ctx(const hr_limits* lim, int n, size_t views, size_t subtiles, size_
                cudaMemset(c->nodes, 0, ni * F * sizeof(hr::Node)) == cudaSuccess &&
                cudaMemset(c->bvh_valid, 0, ni * sizeof(int)) == cudaSuccess &&
                cudaMemset(c->st_done, 0, subtiles * sizeof(unsigned)) == cudaSuccess &&
-               cudaMemset(c->bin_cnt, 0, subtiles * sizeof(unsigned)) == cudaSuccess;
+               cudaMemset(c->bin_cnt, 0, subtiles * sizeof(unsigned)) == cudaSuccess &&
+               cudaMemset(c->bvh_stale, 0, ni * sizeof(int)) == cudaSuccess &&
+               cudaMemset(c->bvh_need, 0, ni * sizeof(int)) == cudaSuccess;
   for (int i = 0; ok && i < 2 * hr::kTimeSlots; ++i) ok = cudaEventCreate(&c->ev[i]) == cudaSuccess;
   if (ok)
     ok = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess &&

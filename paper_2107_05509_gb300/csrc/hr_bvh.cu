@@ -30,6 +30,11 @@ namespace hr {
 namespace {
 
 constexpr int kBuildThreads = 1024;
+// k_build_bvh modes: kBvhFull builds or refits (per the rebuild schedule) with fresh
+// boxes; kBvhRecords builds per the schedule but on refit iterations rewrites only
+// the triangle records and marks the boxes stale; kBvhLazyRefit refits stale boxes
+// from the current records' leaf order when a render call needs traversal
+constexpr int kBvhFull = 0, kBvhRecords = 1, kBvhLazyRefit = 2;
 constexpr int kBuildSmemCap = 200 * 1024;   // opt-in of k_build_bvh
 
 __device__ __forceinline__ unsigned expand_bits10(unsigned v) {
@@ -130,13 +135,15 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
                                                              const int* __restrict__ vf_off,
                                                              const int* __restrict__ vf_faces,
                                                              float* __restrict__ normals_all,
-                                                             float* __restrict__ normal_len_all) {
+                                                             float* __restrict__ normal_len_all, int mode,
+                                                             int* __restrict__ stale_all, int* __restrict__ need_all,
+                                                             int force) {
   extern __shared__ unsigned long long smem_keys[];
   if (active && !active[blockIdx.x]) return;   // a retired instance of a batch
   unsigned long long* keys = smem_keys;
   int* parent = reinterpret_cast<int*>(keys + P);
   int* flags = parent + 2 * F;
-  const float* verts = verts_all + (size_t)blockIdx.x * 3 * V;
+  const float* verts = verts_all ? verts_all + (size_t)blockIdx.x * 3 * V : nullptr;   // null: a lazy refit
   Node* gnodes = nodes_all + (size_t)blockIdx.x * node_stride;
   float4* tris = tris_all + (size_t)blockIdx.x * 3 * node_stride;
   // the node array the hierarchy and refit work on (16-byte aligned after flags)
@@ -151,8 +158,22 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
   const int lane = tid & 31, warp = tid >> 5;
   int* gparent = parent_all + (size_t)blockIdx.x * 2 * node_stride;
   // refit when a tree of these faces exists and this is not a rebuild iteration
-  const bool refit = rebuild_every > 1 && iter_dev && valid[blockIdx.x] == 1 && (*iter_dev % rebuild_every) != 0;
-  if (refit) {
+  bool refit = rebuild_every > 1 && iter_dev && valid[blockIdx.x] == 1 && (*iter_dev % rebuild_every) != 0;
+  if (mode == kBvhLazyRefit) {
+    // a render call: refit the stale boxes of an existing tree when a traversal will
+    // read them (a sub-tile of this forward without a candidate list, or `force`)
+    __shared__ int go;
+    if (tid == 0) {
+      go = valid[blockIdx.x] == 1 && stale_all[blockIdx.x] && (force || need_all[blockIdx.x]);
+      need_all[blockIdx.x] = 0;
+    }
+    __syncthreads();
+    if (!go) return;
+    refit = true;
+  }
+  // hr_update_bvh's refit iterations: the triangle records only, the boxes left stale
+  const bool records_only = mode == kBvhRecords && refit;
+  if (refit && !records_only) {
     const int nn = F > 1 ? F - 1 : 1;
     if (snodes)   // the refit rewrites every box: only the child indices are read
       for (int i = tid; i < nn; i += blockDim.x) nodes[i].d = gnodes[i].d;
@@ -308,18 +329,28 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
         tri[j] = -1;
         continue;
       }
-      v0[j] = ld3(verts + 3 * faces[3 * tri[j]]);
-      v1[j] = ld3(verts + 3 * faces[3 * tri[j] + 1]);
-      v2[j] = ld3(verts + 3 * faces[3 * tri[j] + 2]);
+      if (mode == kBvhLazyRefit) {   // the triangle as the records give it to the intersector
+        const float4 ta = tris[3 * k], tb = tris[3 * k + 1], tc = tris[3 * k + 2];
+        v0[j] = make_float3(ta.x, ta.y, ta.z);
+        v1[j] = make_float3(ta.x + ta.w, ta.y + tb.x, ta.z + tb.y);
+        v2[j] = make_float3(ta.x + tb.z, ta.y + tb.w, ta.z + tc.x);
+      } else {
+        v0[j] = ld3(verts + 3 * faces[3 * tri[j]]);
+        v1[j] = ld3(verts + 3 * faces[3 * tri[j] + 1]);
+        v2[j] = ld3(verts + 3 * faces[3 * tri[j] + 2]);
+      }
     }
 #pragma unroll 1
     for (int j = 0; j < kLeafPer; ++j) {
       const int k = k0 + j * blockDim.x;
       if (k >= F || tri[j] < 0) continue;
-      float3 e1 = dsub(v1[j], v0[j]), e2 = dsub(v2[j], v0[j]);
-      tris[3 * k + 0] = make_float4(v0[j].x, v0[j].y, v0[j].z, e1.x);
-      tris[3 * k + 1] = make_float4(e1.y, e1.z, e2.x, e2.y);
-      tris[3 * k + 2] = make_float4(e2.z, __int_as_float(tri[j]), 0.0f, 0.0f);
+      if (mode != kBvhLazyRefit) {   // a lazy refit leaves the records (read by the render) alone
+        float3 e1 = dsub(v1[j], v0[j]), e2 = dsub(v2[j], v0[j]);
+        tris[3 * k + 0] = make_float4(v0[j].x, v0[j].y, v0[j].z, e1.x);
+        tris[3 * k + 1] = make_float4(e1.y, e1.z, e2.x, e2.y);
+        tris[3 * k + 2] = make_float4(e2.z, __int_as_float(tri[j]), 0.0f, 0.0f);
+      }
+      if (records_only) continue;
       Box b;
       float amax = 0.0f;
       float p0[3] = {v0[j].x, v0[j].y, v0[j].z}, p1[3] = {v1[j].x, v1[j].y, v1[j].z},
@@ -365,6 +396,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
       vertex_normal(v, verts, faces, vf_off, vf_faces, V, F, normals, normal_len, status);
   }
   __syncthreads();
+  if (records_only) {
+    if (tid == 0) stale_all[blockIdx.x] = 1;
+    return;
+  }
   if (snodes) {   // a refit changed only the boxes (the first three float4 of a node)
     const int nn = F > 1 ? F - 1 : 1;
     const float4* src = reinterpret_cast<const float4*>(nodes);
@@ -379,6 +414,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
     for (int i = tid; i < 2 * F; i += blockDim.x) gparent[i] = parent[i];
     if (tid == 0) valid[blockIdx.x] = 1;
   }
+  if (tid == 0 && stale_all) stale_all[blockIdx.x] = 0;
 }
 
 // Faces and the vertex->face table come from the caller: an index out of range is
@@ -672,6 +708,7 @@ int launch_build_bvh_grid(Context* ctx, const hr_model* m, const float* verts, c
     if (cudaMemsetAsync(ctx->bvh_valid, 0, sizeof(int) * ni, s) != cudaSuccess) return HR_ERR_CUDA;
     ctx->bvh_faces = m->faces;
   }
+  ctx->bvh_lazy = false;   // the multi-block build refits its boxes every call
   k_lb_decide<<<ni, 1, 0, s>>>(ctx->bvh_mode, ctx->bvh_valid, ctx->bvh_bounds, ctx->bvh_bad, iter_dev,
                                rebuild_every);
   HR_CHECK_LAUNCH();
@@ -712,6 +749,20 @@ int launch_build_bvh_grid(Context* ctx, const hr_model* m, const float* verts, c
   return HR_OK;
 }
 
+// Refit the boxes of a one-block tree whose last update rewrote only the records,
+// from the records themselves (the triangles the intersector tests), when this
+// forward listed a sub-tile for per-ray traversal (k_bin_alloc sets bvh_need) or
+// `force`; otherwise the kernel returns at once.
+int launch_bvh_lazy_refit(Context* ctx, int force, cudaStream_t s) {
+  if (!ctx->bvh_lazy) return HR_OK;
+  k_build_bvh<<<ctx->n_inst, kBuildThreads, ctx->bvh_smem, s>>>(
+      nullptr, ctx->bvh_faces, ctx->F, ctx->V, ctx->bvh_P, ctx->lim.max_F, ctx->bvh_snodes, ctx->nodes, ctx->tris,
+      ctx->bvh_parent, ctx->bvh_valid, nullptr, 1, ctx->status, ctx->active, nullptr, nullptr, nullptr, nullptr,
+      kBvhLazyRefit, ctx->bvh_stale, ctx->bvh_need, force);
+  HR_CHECK_LAUNCH();
+  return HR_OK;
+}
+
 int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaStream_t s) {
   return launch_update_bvh(ctx, m, verts, nullptr, 1, s);
 }
@@ -739,11 +790,19 @@ int launch_update_bvh(Context* ctx, const hr_model* m, const float* verts, const
   k_vertex_normals<<<dim3((V + 255) / 256, ctx->n_inst), 256, 0, ctx->side>>>(
       verts, m->faces, m->vf_offsets, m->vf_faces, V, F, ctx->normals, ctx->normal_len, ctx->status, ctx->active);
   HR_CHECK_LAUNCH();
+  // with a rebuild schedule, refit iterations rewrite only the records; the render
+  // calls refit the boxes when they need them (launch_bvh_lazy_refit)
+  const int mode = (rebuild_every > 1 && iter_dev) ? kBvhRecords : kBvhFull;
   k_build_bvh<<<ctx->n_inst, kBuildThreads, smem, s>>>(verts, m->faces, F, V, P, ctx->lim.max_F, snodes,
                                                        ctx->nodes, ctx->tris, ctx->bvh_parent, ctx->bvh_valid,
                                                        iter_dev, rebuild_every, ctx->status, ctx->active,
-                                                       nullptr, nullptr, nullptr, nullptr);
+                                                       nullptr, nullptr, nullptr, nullptr, mode, ctx->bvh_stale,
+                                                       ctx->bvh_need, 0);
   HR_CHECK_LAUNCH();
+  ctx->bvh_lazy = true;
+  ctx->bvh_P = P;
+  ctx->bvh_smem = smem;
+  ctx->bvh_snodes = snodes;
   if (cudaEventRecord(ctx->ev_join, ctx->side) != cudaSuccess || cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess)
     return HR_ERR_CUDA;
   ctx->V = V;

@@ -90,6 +90,15 @@ struct Context {
   int* bvh_parent;       // [n_inst][2 max_F] parents of the internal nodes and leaves
   int* bvh_valid;        // [n_inst] 1 once a tree of bvh_faces exists (refits need it)
   const int* bvh_faces;  // the face array of the last build
+  // one-block trees: hr_update_bvh's refit iterations rewrite only the triangle
+  // records and mark the boxes stale; a render call refits them when one of its
+  // sub-tiles needs per-ray traversal (the shared-memory layout of the last update)
+  int* bvh_stale;        // [n_inst] boxes older than the records
+  int* bvh_need;         // [n_inst] this forward has a sub-tile without a candidate list
+  bool bvh_lazy;         // the last update was a one-block build or record update
+  int bvh_P;             // its key count (power of two >= F)
+  size_t bvh_smem;       // its dynamic shared memory
+  bool bvh_snodes;       // its nodes held in shared memory
   // multi-block build (meshes beyond one block's shared memory)
   int bvh_pmax;                  // keys per instance (power of two >= max_F)
   unsigned long long* bvh_keys;  // [n_inst][bvh_pmax]
@@ -132,7 +141,6 @@ struct Context {
   unsigned long long* acc_fx;   // [n_inst][max_V][6] fixed-point backward sums (HR_DETERMINISTIC)
   cudaStream_t side;     // the edge-sampling term runs here, beside the interior term
   cudaEvent_t ev_fork, ev_join;
-  float* dm;             // [n_inst][max_V][3]
   int* sil;              // [views][max_E]
   int* sil_count;        // [views]
   // loss scratch: per instance kLossStride(loss_blocks) floats

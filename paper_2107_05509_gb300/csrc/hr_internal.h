@@ -18,6 +18,7 @@ int launch_colour_map_bwd(const float* d_v, int W, int H, int wl, int hl, float*
 int launch_build_bvh(Context* ctx, const hr_model* m, const float* verts, cudaStream_t s);
 int launch_update_bvh(Context* ctx, const hr_model* m, const float* verts, const uint32_t* iter_dev,
                       int rebuild_every, cudaStream_t s);
+int launch_bvh_lazy_refit(Context* ctx, int force, cudaStream_t s);
 int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,
                       const float* bg, const hr_render_opts* o, float* image, cudaStream_t s);
 int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const Cam* cams, int N, int H, int W,

@@ -3,46 +3,53 @@
 // 2018 that the paper builds on; Section 1 and Section 3.1).
 //
 // Primary rays of a pinhole camera are coherent, so the forward and the interior
-// backward work on 8x4-pixel sub-tiles, one warp per sub-tile, in three steps:
+// backward work on 8x4-pixel sub-tiles, one warp per sub-tile at a time.
 //
-//   k_gather       the warp traverses the LBVH once with the sub-tile's frustum
-//                  (breadth-first, one frontier node per lane) and collects the
-//                  leaf triangles it reaches -- the only ones any sample ray of the
-//                  sub-tile can hit -- with their screen boxes, sorted by their
-//                  nearest camera depth, into a candidate pool; the sub-tile is
-//                  split into 1-16 work items of consecutive samples (more for
-//                  sub-tiles with more candidates: a palm seen edge-on has over a
-//                  hundred), so no single warp holds up the launch.  Sub-tiles that
-//                  no ray can hit are finished here (forward: background).
+// Candidate lists (forward).  A sample can hit a triangle only if the sample lies in
+// the triangle's screen box (padded by half a pixel), and every shader tests that box
+// before intersecting, so a sub-tile needs the triangle records whose boxes meet it:
+//   k_bin (count)  each (view, record) pair counts itself into the sub-tiles its box
+//                  meets;
+//   k_bin_alloc    each sub-tile gets a pool range for its K records and 1-16 work
+//                  items of consecutive samples (more for longer lists, so no single
+//                  warp holds up the launch);
+//   k_background   sub-tiles that no record meets get the background (second stream);
+//   k_bin (fill)   the pairs write their records, boxes and depths into the ranges;
+//   k_bin_sort     each list is sorted by nearest camera depth.
+// k_gather (a frustum walk of the LBVH per sub-tile) makes the backward's own lists
+// when the forward's cannot be reused.
+//
+// Shading:
 //   k_shade_fwd    warps take work items; each lane (pixel) makes its samples
-//                  (Philox jitter), runs the same float32 Moller-Trumbore test and
-//                  closest-hit rule as a per-ray traversal on the candidates whose
-//                  box contains the sample, in depth order, and stops when no lane
-//                  can still find a nearer hit; shades, and writes per-item sums.
-//   (finish_item)  the warp finishing a sub-tile's last forward item sums the items in
+//                  (Philox jitter) and walks the candidates that can hold a sample of
+//                  its pixel (a bit transpose of the warp's box-against-pixel tests),
+//                  in depth order, with the same float32 Moller-Trumbore test and
+//                  closest-hit rule as a per-ray traversal, stopping at the first
+//                  candidate nearer than none of its hits; shades, and writes per-item
+//                  sums.  The warp finishing a sub-tile's last item sums the items in
 //                  item order (deterministic) and writes the pixels.
 //   k_shade_bwd    the same samples re-traced (no hit records are kept between
 //                  the passes); every hit is differentiated at the fixed ray and the
-//                  gradient accumulated per triangle in registers, per block in
-//                  shared memory, and written as one partial per block.
-//   k_reduce_partials  fixed-order sum of the block partials.
+//                  gradient accumulated per run of hits on one triangle in registers,
+//                  summed over the warp, and added into one partial per SM.
+//   k_reduce_partials  fixed-order sum of the partials.
 //
-// Per-ray LBVH traversal (trace) serves the edge-sample rays, the hr_trace entry
-// point and sub-tiles whose candidates exceed the pool.
+// Per-ray LBVH traversal (trace) serves the hr_trace entry point and the sub-tiles
+// with more candidates than a list holds (k_overflow, and edge rays landing there).
 //   k_silhouettes  per view, edges whose faces face opposite ways from the camera
 //                  (plus boundary edges), compacted in edge order.
 //   k_edge_samples the boundary term: samples on silhouette edges, f+ and f- by
-//                  two traced rays, mapped to vertices by the projection Jacobian.
-//   k_normal_dm / k_normal_gather   adjoint of the area-weighted vertex normals.
+//                  two rays over the candidate list of the sample's sub-tile, mapped
+//                  to vertices by the projection Jacobian.
+//   k_normal_gather  adjoint of the area-weighted vertex normals.
 //
 // Batches (hr_batch_create): every kernel runs over all instances of the batch in
 // one launch.  Sub-tiles are numbered over all views of all instances (a view table
 // maps a sub-tile to its view, instance, resolution and samples per pixel); each
 // instance has its own BVH, vertices, normals and region of the work-item table.
-// Forward warps take items instance after instance; backward blocks take them
-// instance after instance too and add their shared-memory sums into the instance's
-// gradient when they move on.  A single-instance call is a batch of one with a
-// uniform view layout (no table).
+// Warps take items instance after instance; a batch's backward adds each run's sums
+// straight into its instance's gradient.  A single-instance call is a batch of one
+// with a uniform view layout (no table).
 #include <type_traits>
 
 #include "hr_internal.h"
@@ -212,6 +219,7 @@ struct Work {
   int4* cand_st;       // [sub-tiles] forward lists k_bin_sort orders: (sub-tile, pool offset, K, 0)
                        // (count: ctr_cull)
   unsigned* bin;       // [sub-tiles] records binned per sub-tile, then the fill's slot counter
+  int* bvh_need;       // [n_inst] set when a sub-tile is listed for per-ray traversal
   unsigned long long* fx;   // [n_inst][6V] fixed-point backward sums (HR_DETERMINISTIC)
   bool det;                 // HR_DETERMINISTIC: every vertex-gradient sum goes to fx
 };
@@ -1386,6 +1394,7 @@ __global__ void __launch_bounds__(kCullThreads) k_bin_alloc(RenderArgs a0, unsig
       if (K > kLeafCap) Kc = -1;
       else if (off + K > a0.wk.pool_cap) Kc = -(K + 1);
       sorted = Kc > 0;
+      if (Kc < 0) a0.wk.bvh_need[t.inst] = 1;   // traced ray by ray: the BVH boxes must be current
       a0.wk.st[st] = make_int2(sorted ? (int)off : 0, Kc);
       C = chunks_for(a0, Kc, t.spp);
       heavy = heavy_item(a0, Kc, C, t.spp);
@@ -2316,47 +2325,39 @@ __global__ void __launch_bounds__(kRenderThreads) k_edge_samples(RenderArgs a_in
   }
 }
 
-// dm_v = (I - n n^T) dN_v / |m_v|; blockIdx.y selects the instance
-__global__ void k_normal_dm(const float* __restrict__ normals_all, const float* __restrict__ normal_len_all,
-                            const float* __restrict__ dN_all, int V, float* __restrict__ dm_all,
-                            const int* __restrict__ active) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= V || (active && !active[blockIdx.y])) return;
-  const size_t o = (size_t)blockIdx.y * V;
-  const float *normals = normals_all + 3 * o, *normal_len = normal_len_all + o, *dN = dN_all + 3 * o;
-  float* dm = dm_all + 3 * o;
-  float len = normal_len[v];
-  float3 n = ld3(normals + 3 * v), g = ld3(dN + 3 * v);
-  float3 r = make_float3(0.0f, 0.0f, 0.0f);
-  if (len > 0.0f) {
-    float pr = dot3(n, g);
-    float il = 1.0f / len;
-    r = make_float3((g.x - n.x * pr) * il, (g.y - n.y * pr) * il, (g.z - n.z * pr) * il);
-  }
-  dm[3 * v] = r.x;
-  dm[3 * v + 1] = r.y;
-  dm[3 * v + 2] = r.z;
+// dm_u = (I - n n^T) dN_u / |m_u|: the adjoint of the unnormalised normal m_u of
+// vertex u from that of its unit normal
+__device__ __forceinline__ float3 normal_dm(const float* __restrict__ normals, const float* __restrict__ normal_len,
+                                           const float* __restrict__ dN, int u) {
+  const float len = normal_len[u];
+  const float3 n = ld3(normals + 3 * u), g = ld3(dN + 3 * u);
+  if (!(len > 0.0f)) return make_float3(0.0f, 0.0f, 0.0f);
+  const float pr = dot3(n, g);
+  const float il = 1.0f / len;
+  return make_float3((g.x - n.x * pr) * il, (g.y - n.y * pr) * il, (g.z - n.z * pr) * il);
 }
 
 // d_verts[v] += sum over incident faces of d(e1 x e2)/dv . dc_f, dc_f = sum of dm
-// over f; blockIdx.y selects the instance
-// d_verts += the normals' vertex adjoint, and the edge term's sums when dedge is given
+// over f's vertices (dm computed here from dN for each of them: no pass of its own);
+// plus the edge term's sums when dedge is given.  blockIdx.y selects the instance.
 __global__ void k_normal_gather(const float* __restrict__ verts_all, const int* __restrict__ faces,
                                 const int* __restrict__ vf_off, const int* __restrict__ vf_faces,
-                                const float* __restrict__ dm_all, int V, const float* __restrict__ dedge_all,
+                                const float* __restrict__ normals_all, const float* __restrict__ normal_len_all,
+                                const float* __restrict__ dN_all, int V, const float* __restrict__ dedge_all,
                                 float* __restrict__ d_verts_all, const int* __restrict__ active) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V || (active && !active[blockIdx.y])) return;
   const size_t o = (size_t)blockIdx.y * 3 * V;
-  const float *verts = verts_all + o, *dm = dm_all + o;
+  const float *verts = verts_all + o, *normals = normals_all + o, *dN = dN_all + o;
+  const float* normal_len = normal_len_all + (size_t)blockIdx.y * V;
   float* d_verts = d_verts_all + o;
   float3 acc = make_float3(0.0f, 0.0f, 0.0f);
   if (dedge_all) acc = ld3(dedge_all + o + 3 * v);
   for (int k = vf_off[v]; k < vf_off[v + 1]; ++k) {
     int f = vf_faces[k];
     int i0 = faces[3 * f], i1 = faces[3 * f + 1], i2 = faces[3 * f + 2];
-    float3 dc = ld3(dm + 3 * i0);
-    float3 t1 = ld3(dm + 3 * i1), t2 = ld3(dm + 3 * i2);
+    float3 dc = normal_dm(normals, normal_len, dN, i0);
+    float3 t1 = normal_dm(normals, normal_len, dN, i1), t2 = normal_dm(normals, normal_len, dN, i2);
     dc = make_float3(dc.x + t1.x + t2.x, dc.y + t1.y + t2.y, dc.z + t1.z + t2.z);
     float3 p0 = ld3(verts + 3 * i0), p1 = ld3(verts + 3 * i1), p2 = ld3(verts + 3 * i2);
     float3 e1 = make_float3(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z);
@@ -2450,6 +2451,7 @@ RenderArgs make_args(Context* ctx, const hr_model* m, const float* verts, const 
   a.wk.st_done = ctx->st_done;
   a.wk.cand_st = ctx->cand_st;
   a.wk.bin = ctx->bin_cnt;
+  a.wk.bvh_need = ctx->bvh_need;
   a.wk.fx = ctx->acc_fx;
   a.wk.det = (o->flags & HR_DETERMINISTIC) != 0;
   a.node_stride = ctx->lim.max_F;
@@ -2530,6 +2532,10 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
     else
       k_background<false><<<bg_blocks, kCullThreads, 0, bs>>>(a, image, nullptr);
     HR_CHECK_LAUNCH();
+    // the boxes of a tree whose update rewrote only the records, refitted if a sub-tile
+    // was listed for per-ray traversal (k_overflow is the first to traverse)
+    const int rc = launch_bvh_lazy_refit(ctx, 0, bs);
+    if (rc != HR_OK) return rc;
     if (fork && cudaEventRecord(ctx->ev_join, bs) != cudaSuccess) return HR_ERR_CUDA;
     k_bin<true><<<std::max(bin_blocks, 1), kBinThreads, 0, s>>>(a, ctx->bin_cnt);
     HR_CHECK_LAUNCH();
@@ -2545,12 +2551,12 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
     kern<<<blocks, kRenderThreads, 0, s>>>(a, image, st ? ctx->stats : nullptr);
   }
   HR_CHECK_LAUNCH();
+  if (fork && cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess) return HR_ERR_CUDA;
   if (st)
     k_overflow<false, true><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, ctx->stats);
   else
     k_overflow<false, false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, nullptr);
   HR_CHECK_LAUNCH();
-  if (fork && cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess) return HR_ERR_CUDA;
   tm.end(kTimeFwdShade);
   // the item sums are combined inside the shaders (finish_item): the slot stays, empty
   tm.begin(kTimeFwdCombine);
@@ -2609,11 +2615,15 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
         k_items_bwd<true><<<ctx->num_sms * 4, kCullThreads, 0, s>>>(a, adjoint, ctx->stats + kStatsPer);
       else
         k_items_bwd<false><<<ctx->num_sms * 4, kCullThreads, 0, s>>>(a, adjoint, nullptr);
-    } else if (st) {
-      k_gather<true><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint,
-                                                                          ctx->stats + kStatsPer);
     } else {
-      k_gather<false><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, nullptr);
+      // its own lists from a frustum walk of the BVH: the boxes must be current
+      const int rc = launch_bvh_lazy_refit(ctx, 1, s);
+      if (rc != HR_OK) return rc;
+      if (st)
+        k_gather<true><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint,
+                                                                            ctx->stats + kStatsPer);
+      else
+        k_gather<false><<<ctx->num_sms * ctx->tune.blocks_per_sm, kRenderThreads, 0, s>>>(a, adjoint, nullptr);
     }
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdGather);
@@ -2723,9 +2733,8 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     tm.begin(kTimeBwdNormals);
     const dim3 g((V + 255) / 256, ni);
     const int* act = batch ? ctx->active : nullptr;
-    k_normal_dm<<<g, 256, 0, s>>>(ctx->normals, ctx->normal_len, ctx->dN, V, ctx->dm, act);
-    HR_CHECK_LAUNCH();
-    k_normal_gather<<<g, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, ctx->dm, V,
+    k_normal_gather<<<g, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, ctx->normals, ctx->normal_len,
+                                      ctx->dN, V,
                                       edges && !det ? ctx->dedge : nullptr, d_verts, act);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdNormals);
@@ -2739,6 +2748,8 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
 }
 
 int launch_trace(Context* ctx, const float* o, const float* d, int n, int* tri, float* tuv, cudaStream_t s) {
+  const int rc = launch_bvh_lazy_refit(ctx, 1, s);   // traversal reads the boxes
+  if (rc != HR_OK) return rc;
   k_trace<<<(n + 127) / 128, 128, 0, s>>>(ctx->nodes, ctx->tris, o, d, n, tri, tuv, ctx->status, ctx->F + 1);
   HR_CHECK_LAUNCH();
   return HR_OK;

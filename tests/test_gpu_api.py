@@ -213,6 +213,42 @@ def test_refit_gives_the_rebuilt_tree_results(B):
     assert B.hr_get_status(ctx) == B.HR_OK
 
 
+def test_lazy_refit_serves_per_ray_traversal(B):
+    """On a refit iteration hr_update_bvh rewrites only the triangle records.  A
+    forward whose sub-tiles meet more triangles than a candidate list holds (the
+    whole hand inside a 16x16 view) traces them ray by ray through the BVH, whose
+    boxes -- still those of another pose -- the render refits first.  The image
+    equals the one after a full rebuild bit for bit and matches the oracle, and the
+    forward's counters show the traversal."""
+    import oracle
+    from paper_2107_05509_gb300 import inputs as I
+    from tests.gpu_common import Scene, pixel_ok
+    cfg = I.SceneConfig("far-2x16x16-4spp", views=2, width=16, height=16, spp=4, edge_samples=64,
+                        elevation_deg=20.0, azimuths_deg=(0.0, 90.0), seed=5)
+    sc = Scene(cfg)
+    h = hand()
+    model = B.Model(h)
+    ctx = B.Context(h.V, h.F, h.E, sc.N, sc.W, sc.H)
+    vb_np = oracle.skin(h, sc.x_gt).astype(np.float32)     # another pose, same faces
+    v_a, v_b = _t(sc.verts), _t(vb_np)
+    cams, bg = _t(sc.cams), _t(sc.bg)
+    img_lazy = torch.empty((sc.N, sc.H, sc.W, 3), device="cuda")
+    img_full = torch.empty_like(img_lazy)
+    B.hr_build_bvh(ctx, model, v_a)
+    counter = torch.full((1,), 3, dtype=torch.int32, device="cuda")
+    B.hr_update_bvh(ctx, model, v_b, counter, 8)            # 3 % 8 != 0: records only
+    B.hr_get_stats(ctx)                                     # clears the counters
+    B.hr_render_fwd(ctx, model, v_b, cams, sc.H, sc.W, bg, sc.gpu_opts(sc.opts(), flags=B.HR_STATS), img_lazy)
+    assert B.hr_get_stats(ctx)[0, 2] > 0                    # BVH nodes visited by per-ray traversal
+    B.hr_build_bvh(ctx, model, v_b)
+    B.hr_render_fwd(ctx, model, v_b, cams, sc.H, sc.W, bg, sc.gpu_opts(sc.opts()), img_full)
+    assert torch.equal(img_lazy, img_full)
+    n_b = oracle.vertex_normals(vb_np, h.faces, h.vf_offsets, h.vf_faces)
+    ref = oracle.render_fwd(vb_np, h.faces, n_b, h.albedo, sc.cams, sc.H, sc.W, sc.bg, sc.opts())
+    assert pixel_ok(img_lazy.cpu().numpy(), ref).all()
+    assert B.hr_get_status(ctx) == B.HR_OK
+
+
 def test_tunings_keep_results(B):
     """Every launch-shape setting renders and differentiates to the oracle's values
     (work-item splits change only the float32 summation grouping); invalid settings
