@@ -324,6 +324,16 @@ __device__ __forceinline__ Cam load_cam(const Cam* cams, int view) {
   return c;
 }
 
+// a work item's camera, copied into the warp's shared-memory slot (lane i < 20 copies
+// word i) so that the shaders read it from there instead of holding 20 registers
+__device__ __forceinline__ const Cam& warp_cam(Cam* slot, const Cam* cams, int view) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  if (lane < 20) reinterpret_cast<float*>(slot)[lane] = __ldg(reinterpret_cast<const float*>(cams + view) + lane);
+  __syncwarp();
+  return *slot;
+}
+
 // sample-stream iteration: the device counter when the caller gave one
 __device__ __forceinline__ RenderArgs with_iter(RenderArgs a) {
   if (a.iter_dev) a.iter4 = (*a.iter_dev) << 4;
@@ -1834,6 +1844,7 @@ __device__ __forceinline__ void finish_item(const RenderArgs& a, const SubTile& 
 template <bool STATS, int S>
 __global__ void __launch_bounds__(kRenderThreads, 6) k_shade_fwd(RenderArgs a_in, float* __restrict__ image,
                                                                   unsigned long long* stats) {
+  __shared__ Cam scam[kWarps];
   const RenderArgs a0 = with_iter(a_in);
   Counts cnt;
   for (int inst = 0; inst < a0.n_inst; ++inst) {
@@ -1848,7 +1859,7 @@ __global__ void __launch_bounds__(kRenderThreads, 6) k_shade_fwd(RenderArgs a_in
       int2 pk;
       if (!load_item(a, slot, item, t, pk) || t.inst != inst) continue;
       if (pk.y < 0) continue;   // no candidate list: k_overflow traces this item
-      const Cam cam = load_cam(a.cams, t.view);
+      const Cam& cam = warp_cam(&scam[threadIdx.x >> 5], a.cams, t.view);
       int s0, s1;
       item_samples(item.y, item.z, t.spp, s0, s1);
       float3 acc = make_float3(0.0f, 0.0f, 0.0f);
@@ -1976,6 +1987,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
                                                                              const float* __restrict__ adjoint,
                                                                              float* __restrict__ partials, int nparts,
                                                                              unsigned long long* stats) {
+  __shared__ Cam scam[kWarps];
   const RenderArgs a0 = with_iter(a_in);
   float* part = partials + (size_t)(blockIdx.x % nparts) * 6 * a0.V;
   Counts cnt;
@@ -2005,7 +2017,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
       if (pk.y < 0) continue;   // no candidate list: k_overflow traces this item
       bool live;
       const float3 g = lane_adjoint(a, t, adjoint, live);
-      const Cam cam = load_cam(a.cams, t.view);
+      const Cam& cam = warp_cam(&scam[threadIdx.x >> 5], a.cams, t.view);
       int s0, s1;
       item_samples(item.y, item.z, t.spp, s0, s1);
       grad_samples<STATS, S, AccT, false>(a, t, cam, pk.x, pk.y, s0, s1, live, g, sdV, sdN, cnt);
