@@ -178,7 +178,7 @@ __host__ __device__ constexpr int ctr_words(int n) { return ctr_alloc_base(n) + 
 // meshes up to this many vertices take float backward sums (per block of the shader
 // in a single-instance context); larger ones float64 sums
 constexpr int kPartialMaxV = 8192;
-constexpr int kLossBlocks = 1024;        // loss blocks of a single-instance context
+constexpr int kLossBlocks = 304;         // loss blocks of a single-instance context (2 per SM of a GB300)
 constexpr int kLossBlocksBatch = 128;    // per instance in a batch
 // per-instance loss scratch: block counts (u64), block sums, 1 / (3 sum M), padding
 __host__ __device__ constexpr int kLossStride(int blocks) { return 4 * blocks + 8; }

@@ -70,8 +70,22 @@ __global__ void __launch_bounds__(kLossThreads) k_mask_count(const uint8_t* __re
   float* scale = scratch + 3 * gridDim.x;
   unsigned* counter = counters_all + 4 * blockIdx.y;
   unsigned long long c = 0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    c += mask[i] != 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long head = 0;
+  if ((reinterpret_cast<uintptr_t>(mask) & 15) == 0) {
+    // 16 mask bytes per load; a byte is non-zero iff the high bit of
+    // ((b & 0x7f) + 0x7f) | b is set
+    const uint4* m16 = reinterpret_cast<const uint4*>(mask);
+    const long long q = n / 16;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < q; i += stride) {
+      const uint4 w = m16[i];
+      const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) c += __popc((((ws[k] & 0x7f7f7f7fu) + 0x7f7f7f7fu) | ws[k]) & 0x80808080u);
+    }
+    head = 16 * q;
+  }
+  for (long long i = head + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) c += mask[i] != 0;
   unsigned long long s = block_sum_u64(c, red);
   if (threadIdx.x == 0) {
     counts[blockIdx.x] = s;
