@@ -53,13 +53,13 @@ LANES = 128
 FLOP_RAY, FLOP_NODE, FLOP_CAND, FLOP_TRI, FLOP_HIT, FLOP_HIT_GRAD = 40, 60, 4, 50, 60, 250
 S_SAMPLES, S_RAYS, S_NODES, S_TRIS, S_HITS, S_CANDS = range(6)
 FLOP_TRACE_NODE, FLOP_EDGE = 40, 120   # per-ray traversal node (two slab tests); edge-sample set-up
-KERNEL_NAMES = {"fwd_gather": "k_gather<fwd>", "fwd_shade": "k_shade_fwd", "bwd_gather": "k_items_bwd",
+KERNEL_NAMES = {"fwd_gather": "k_bin_*", "fwd_shade": "k_shade_fwd", "bwd_gather": "k_items_bwd",
                 "bwd_shade": "k_shade_bwd", "edge_samples": "k_edge_samples"}
 # DRAM bytes (read + write) per launch from the ncu capture summarised under profiles/,
 # with the hash of the render kernels' sources at that capture: a kernel whose source
 # has changed since reports no traffic
-NCU_TRAFFIC = {"k_shade_bwd": (5916416, "d77a279df24cfb8d"), "k_shade_fwd": (4424960, "d77a279df24cfb8d"),
-               "k_gather<fwd>": (2526208, "d77a279df24cfb8d"), "k_edge_samples": (2774528, "d77a279df24cfb8d")}
+NCU_TRAFFIC = {"k_shade_bwd": (4962560, "51f44ac6bf9da7da"), "k_shade_fwd": (2941184, "51f44ac6bf9da7da"),
+               "k_edge_samples": (2447616, "51f44ac6bf9da7da")}
 NCU_TRAFFIC_SOURCES = ("paper_2107_05509_gb300/csrc/hr_render.cu", "paper_2107_05509_gb300/csrc/hr_device.cuh")
 
 
