@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(kLossThreads) k_mask_count(const uint8_t* __re
                                                              const InstRec* __restrict__ it, long long P,
                                                              float* __restrict__ scratch_all, int lstride,
                                                              unsigned* counters_all, const int* __restrict__ active) {
+  pdl_wait();
   __shared__ unsigned long long red[32];
   __shared__ bool last;
   if (active && !active[blockIdx.y]) return;   // a retired instance of a batch
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(kLossThreads) k_loss_adjoint(const float* __re
                                                                float* __restrict__ adjoint_all,
                                                                float* __restrict__ loss_all, bool vec,
                                                                const int* __restrict__ active) {
+  pdl_wait();
   __shared__ float red[32];
   __shared__ bool last;
   if (active && !active[blockIdx.y]) return;   // a retired instance of a batch
@@ -220,6 +222,7 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 __global__ void k_adam_dev(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                            float* __restrict__ v, int n, float lr, float b1, float b2, float eps,
                            const float* __restrict__ lr_scale, int scale_len, uint32_t* __restrict__ iter_dev) {
+  pdl_wait();
   const float step = (float)(*iter_dev + 1u);
   const float c1 = 1.0f - powf(b1, step), c2 = 1.0f - powf(b2, step);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -497,7 +500,8 @@ int launch_adam_dev(float* p, const float* g, float* m, float* v, int n, float l
   // instances), else enough blocks to stream the five arrays at memory speed
   constexpr int kThreads = 256;
   const int blocks = n <= 16 * kThreads ? 1 : (int)std::min<long long>((n + kThreads - 1) / kThreads, 152LL * 8);
-  k_adam_dev<<<blocks, kThreads, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, lr_scale, scale_len, iter_dev);
+  launch_pdl(k_adam_dev, dim3(blocks), dim3(kThreads), 0, s, p, g, m, v, n, lr, b1, b2, eps, lr_scale, scale_len,
+             iter_dev);
   HR_CHECK_LAUNCH();
   if (blocks > 1) {
     k_counter_advance<<<1, 1, 0, s>>>(iter_dev);
@@ -703,11 +707,11 @@ int launch_loss(Context* ctx, const float* image, const float* obs, const uint8_
   const int lstride = kLossStride(ctx->loss_blocks);
   const dim3 grid(blocks, ctx->vt ? ctx->n_inst : 1);
   const InstRec* it = ctx->vt ? ctx->it : nullptr;
-  k_mask_count<<<grid, kLossThreads, 0, s>>>(mask, it, P, ctx->loss_partials, lstride, ctx->counters,
-                                             ctx->vt ? ctx->active : nullptr);
+  launch_pdl(k_mask_count, grid, dim3(kLossThreads), 0, s, mask, it, P, ctx->loss_partials, lstride, ctx->counters,
+             (const int*)(ctx->vt ? ctx->active : nullptr));
   HR_CHECK_LAUNCH();
-  k_loss_adjoint<<<grid, kLossThreads, 0, s>>>(image, obs, mask, it, P, ctx->loss_partials, lstride, ctx->counters,
-                                               adjoint, loss, vec, ctx->vt ? ctx->active : nullptr);
+  launch_pdl(k_loss_adjoint, grid, dim3(kLossThreads), 0, s, image, obs, mask, it, P, ctx->loss_partials, lstride,
+             ctx->counters, adjoint, loss, vec, (const int*)(ctx->vt ? ctx->active : nullptr));
   HR_CHECK_LAUNCH();
   return HR_OK;
 }

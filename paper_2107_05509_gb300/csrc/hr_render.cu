@@ -1228,6 +1228,7 @@ __device__ __forceinline__ void bin_visit(const RenderArgs& a, unsigned* __restr
 // whatever the sizes of the pairs' ranges.
 template <bool FILL>
 __global__ void __launch_bounds__(kBinThreads) k_bin(RenderArgs a0, unsigned* __restrict__ bin) {
+  pdl_wait();
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int F = a0.max_visits - 1;
@@ -1357,6 +1358,7 @@ __device__ __forceinline__ void place_items(const RenderArgs& a0, bool need, int
 // becomes the fill's slot counter.  A sub-tile with more records than a list holds,
 // or whose records find no pool room, is traced ray by ray (K = -1, -(K + 1)).
 __global__ void __launch_bounds__(kCullThreads) k_bin_alloc(RenderArgs a0, unsigned* __restrict__ bin) {
+  pdl_wait();
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int total = visit_count(a0);
@@ -1481,6 +1483,7 @@ struct SortSmem {   // per warp
   int idx[kLeafCap];
 };
 __global__ void __launch_bounds__(kRenderThreads) k_bin_sort(RenderArgs a0) {
+  pdl_wait();
   __shared__ SortSmem ssm[kWarps];
   SortSmem& ss = ssm[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
@@ -1710,6 +1713,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
 template <bool STATS>
 __global__ void __launch_bounds__(kCullThreads, 4) k_items_bwd(RenderArgs a0, const float* __restrict__ adjoint,
                                                                unsigned long long* stats) {
+  pdl_wait();
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   Counts cnt;
@@ -1844,6 +1848,7 @@ __device__ __forceinline__ void finish_item(const RenderArgs& a, const SubTile& 
 template <bool STATS, int S>
 __global__ void __launch_bounds__(kRenderThreads, 6) k_shade_fwd(RenderArgs a_in, float* __restrict__ image,
                                                                   unsigned long long* stats) {
+  pdl_wait();
   __shared__ Cam scam[kWarps];
   const RenderArgs a0 = with_iter(a_in);
   Counts cnt;
@@ -1882,6 +1887,7 @@ template <bool BWD, bool STATS>
 __global__ void __launch_bounds__(kRenderThreads, BWD ? kBwdMinBlocks : 8) k_overflow(RenderArgs a_in,
                                                                                      const float* __restrict__ adjoint,
                                                             float* __restrict__ image, unsigned long long* stats) {
+  pdl_wait();
   const RenderArgs a0 = with_iter(a_in);
   const int total = subtile_count(a0);
   const int n = (int)min(*reinterpret_cast<volatile unsigned*>(&a0.wk.ctr[2 + 2 * a0.n_inst]), (unsigned)total);
@@ -1987,6 +1993,7 @@ __global__ void __launch_bounds__(kRenderThreads, kBwdMinBlocks) k_shade_bwd(Ren
                                                                              const float* __restrict__ adjoint,
                                                                              float* __restrict__ partials, int nparts,
                                                                              unsigned long long* stats) {
+  pdl_wait();
   __shared__ Cam scam[kWarps];
   const RenderArgs a0 = with_iter(a_in);
   float* part = partials + (size_t)(blockIdx.x % nparts) * 6 * a0.V;
@@ -2035,6 +2042,7 @@ __global__ void __launch_bounds__(kRedEntries * kRedGroups) k_reduce_partials(
     const float* __restrict__ partials, const float* __restrict__ extra_all, const double* __restrict__ extra64_all,
     const unsigned long long* __restrict__ fx_all, int nblocks, int V, float* __restrict__ d_verts_all,
     float* __restrict__ dN_all) {
+  pdl_wait();
   __shared__ float red[kRedGroups][kRedEntries];
   const int j = threadIdx.x % kRedEntries, g = threadIdx.x / kRedEntries;
   const int i = blockIdx.x * kRedEntries + j;
@@ -2357,6 +2365,7 @@ __global__ void k_normal_gather(const float* __restrict__ verts_all, const int* 
                                 const float* __restrict__ normals_all, const float* __restrict__ normal_len_all,
                                 const float* __restrict__ dN_all, int V, const float* __restrict__ dedge_all,
                                 float* __restrict__ d_verts_all, const int* __restrict__ active) {
+  pdl_wait();
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V || (active && !active[blockIdx.y])) return;
   const size_t o = (size_t)blockIdx.y * 3 * V;
@@ -2531,10 +2540,10 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
     const long long pairs = (long long)a.nviews * (a.max_visits - 1);
     const long long bin_warps = (pairs + kBinPairs - 1) / kBinPairs;
     const int bin_blocks = (int)std::min<long long>((bin_warps + kBinThreads / 32 - 1) / (kBinThreads / 32), 8LL * ctx->num_sms);
-    k_bin<false><<<std::max(bin_blocks, 1), kBinThreads, 0, s>>>(a, ctx->bin_cnt);
+    launch_pdl(k_bin<false>, dim3(std::max(bin_blocks, 1)), dim3(kBinThreads), 0, s, a, ctx->bin_cnt);
     HR_CHECK_LAUNCH();
     const int group_blocks = ctx->num_sms * 8;
-    k_bin_alloc<<<group_blocks, kCullThreads, 0, s>>>(a, ctx->bin_cnt);
+    launch_pdl(k_bin_alloc, dim3(group_blocks), dim3(kCullThreads), 0, s, a, ctx->bin_cnt);
     HR_CHECK_LAUNCH();
     if (fork && (cudaEventRecord(ctx->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(bs, ctx->ev_fork, 0) != cudaSuccess))
       return HR_ERR_CUDA;
@@ -2549,9 +2558,9 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
     const int rc = launch_bvh_lazy_refit(ctx, 0, bs);
     if (rc != HR_OK) return rc;
     if (fork && cudaEventRecord(ctx->ev_join, bs) != cudaSuccess) return HR_ERR_CUDA;
-    k_bin<true><<<std::max(bin_blocks, 1), kBinThreads, 0, s>>>(a, ctx->bin_cnt);
+    launch_pdl(k_bin<true>, dim3(std::max(bin_blocks, 1)), dim3(kBinThreads), 0, s, a, ctx->bin_cnt);
     HR_CHECK_LAUNCH();
-    k_bin_sort<<<blocks, kRenderThreads, 0, s>>>(a);
+    launch_pdl(k_bin_sort, dim3(blocks), dim3(kRenderThreads), 0, s, a);
     HR_CHECK_LAUNCH();
   }
   tm.end(kTimeFwdGather);
@@ -2560,14 +2569,15 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
     const int S = ctx->tune.rays_per_lane;
     auto kern = st ? (S == 1 ? k_shade_fwd<true, 1> : (S == 2 ? k_shade_fwd<true, 2> : k_shade_fwd<true, 4>))
                    : (S == 1 ? k_shade_fwd<false, 1> : (S == 2 ? k_shade_fwd<false, 2> : k_shade_fwd<false, 4>));
-    kern<<<blocks, kRenderThreads, 0, s>>>(a, image, st ? ctx->stats : nullptr);
+    launch_pdl(kern, dim3(blocks), dim3(kRenderThreads), 0, s, a, image, st ? ctx->stats : nullptr);
   }
   HR_CHECK_LAUNCH();
   if (fork && cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess) return HR_ERR_CUDA;
   if (st)
-    k_overflow<false, true><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, ctx->stats);
+    launch_pdl(k_overflow<false, true>, dim3(blocks), dim3(kRenderThreads), 0, s, a, nullptr, image, ctx->stats);
   else
-    k_overflow<false, false><<<blocks, kRenderThreads, 0, s>>>(a, nullptr, image, nullptr);
+    launch_pdl(k_overflow<false, false>, dim3(blocks), dim3(kRenderThreads), 0, s, a, nullptr, image,
+               (unsigned long long*)nullptr);
   HR_CHECK_LAUNCH();
   tm.end(kTimeFwdShade);
   // the item sums are combined inside the shaders (finish_item): the slot stays, empty
@@ -2624,9 +2634,10 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     tm.begin(kTimeBwdGather);
     if (reuse) {
       if (st)
-        k_items_bwd<true><<<ctx->num_sms * 4, kCullThreads, 0, s>>>(a, adjoint, ctx->stats + kStatsPer);
+        launch_pdl(k_items_bwd<true>, dim3(ctx->num_sms * 4), dim3(kCullThreads), 0, s, a, adjoint, ctx->stats + kStatsPer);
       else
-        k_items_bwd<false><<<ctx->num_sms * 4, kCullThreads, 0, s>>>(a, adjoint, nullptr);
+        launch_pdl(k_items_bwd<false>, dim3(ctx->num_sms * 4), dim3(kCullThreads), 0, s, a, adjoint,
+                   (unsigned long long*)nullptr);
     } else {
       // its own lists from a frustum walk of the BVH: the boxes must be current
       const int rc = launch_bvh_lazy_refit(ctx, 1, s);
@@ -2657,9 +2668,11 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     if (!det && cudaMemsetAsync(ctx->dedge, 0, sizeof(float) * 3 * V * ni, es) != cudaSuccess) return HR_ERR_CUDA;
   }
   const auto reduce = [&](int acc, int nparts) {
-    k_reduce_partials<<<dim3((6 * V + kRedEntries - 1) / kRedEntries, ni), kRedEntries * kRedGroups, 0, s>>>(
-        ctx->partials, ctx->extra, acc == kAccGlobal ? ctx->extra64 : nullptr, det ? ctx->acc_fx : nullptr,
-        acc == kAccPartials ? nparts : 0, V, d_verts, ctx->dN);
+    launch_pdl(k_reduce_partials, dim3((6 * V + kRedEntries - 1) / kRedEntries, ni), dim3(kRedEntries * kRedGroups), 0,
+               s, (const float*)ctx->partials, (const float*)ctx->extra,
+               (const double*)(acc == kAccGlobal ? ctx->extra64 : nullptr),
+               (const unsigned long long*)(det ? ctx->acc_fx : nullptr), acc == kAccPartials ? nparts : 0, V, d_verts,
+               ctx->dN);
   };
   if (interior) {
     // float sums up to kPartialMaxV vertices (per block, or per instance in a batch),
@@ -2686,12 +2699,15 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
         cudaMemsetAsync(ctx->partials, 0, sizeof(float) * 6 * V * (size_t)nparts, s) != cudaSuccess)
       return HR_ERR_CUDA;
     tm.begin(kTimeBwdShade);
-    kern<<<blocks, kRenderThreads, 0, s>>>(a, adjoint, ctx->partials, nparts, st ? ctx->stats + kStatsPer : nullptr);
+    launch_pdl(kern, dim3(blocks), dim3(kRenderThreads), 0, s, a, adjoint, ctx->partials, nparts,
+               st ? ctx->stats + kStatsPer : nullptr);
     HR_CHECK_LAUNCH();
     if (st)
-      k_overflow<true, true><<<blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, ctx->stats + kStatsPer);
+      launch_pdl(k_overflow<true, true>, dim3(blocks), dim3(kRenderThreads), 0, s, a, adjoint, (float*)nullptr,
+                 ctx->stats + kStatsPer);
     else
-      k_overflow<true, false><<<blocks, kRenderThreads, 0, s>>>(a, adjoint, nullptr, nullptr);
+      launch_pdl(k_overflow<true, false>, dim3(blocks), dim3(kRenderThreads), 0, s, a, adjoint, (float*)nullptr,
+                 (unsigned long long*)nullptr);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdShade);
     if (!det) {
@@ -2745,9 +2761,9 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     tm.begin(kTimeBwdNormals);
     const dim3 g((V + 255) / 256, ni);
     const int* act = batch ? ctx->active : nullptr;
-    k_normal_gather<<<g, 256, 0, s>>>(verts, m->faces, m->vf_offsets, m->vf_faces, ctx->normals, ctx->normal_len,
-                                      ctx->dN, V,
-                                      edges && !det ? ctx->dedge : nullptr, d_verts, act);
+    launch_pdl(k_normal_gather, g, dim3(256), 0, s, verts, m->faces, m->vf_offsets, m->vf_faces,
+               (const float*)ctx->normals, (const float*)ctx->normal_len, (const float*)ctx->dN, V,
+               (const float*)(edges && !det ? ctx->dedge : nullptr), d_verts, act);
     HR_CHECK_LAUNCH();
     tm.end(kTimeBwdNormals);
   } else if (edges && !det) {

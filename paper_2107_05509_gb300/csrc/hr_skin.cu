@@ -222,6 +222,7 @@ __device__ __forceinline__ float3 shaped_vertex(const ModelArgs& m, const Chain&
 __global__ void __launch_bounds__(kSkinThreads) k_skin(ModelArgs m, const float* __restrict__ params_all,
                                                        float* __restrict__ verts_all, float* __restrict__ joints_all,
                                                        int* status, const int* __restrict__ active) {
+  pdl_wait();
   __shared__ Chain ch;
   if (active && !active[blockIdx.y]) return;   // a retired instance of a batch
   const float* params = params_all + (size_t)blockIdx.y * 61;
@@ -260,6 +261,7 @@ __global__ void __launch_bounds__(kSkinThreads) k_skin_bwd(ModelArgs m, const fl
                                                            float* __restrict__ partials_all, unsigned* counter_all,
                                                            int cstride, float* __restrict__ dparams_all,
                                                            int* status, const int* __restrict__ active) {
+  pdl_wait();
   __shared__ Chain ch;
   if (active && !active[blockIdx.y]) return;   // a retired instance of a batch
   const float* params = params_all + (size_t)blockIdx.y * 61;
@@ -480,8 +482,8 @@ ModelArgs model_args(const hr_model* m) {
 
 int launch_skin(Context* ctx, const hr_model* m, const float* params, float* verts, float* joints, cudaStream_t s) {
   int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
-  k_skin<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, verts, joints, ctx->status,
-                                                            ctx->active);
+  launch_pdl(k_skin, dim3(blocks, ctx->n_inst), dim3(kSkinThreads), 0, s, model_args(m), params, verts, joints,
+             ctx->status, (const int*)ctx->active);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
@@ -490,9 +492,8 @@ int launch_skin_bwd(Context* ctx, const hr_model* m, const float* params, const 
                     const float* d_joints, float* d_params, cudaStream_t s) {
   int blocks = (m->V + kSkinThreads - 1) / kSkinThreads;
   if (blocks > kSkinBlocks) blocks = kSkinBlocks;
-  k_skin_bwd<<<dim3(blocks, ctx->n_inst), kSkinThreads, 0, s>>>(model_args(m), params, d_verts, d_joints,
-                                                                ctx->skin_partials, ctx->counters + 2, 4, d_params,
-                                                                ctx->status, ctx->active);
+  launch_pdl(k_skin_bwd, dim3(blocks, ctx->n_inst), dim3(kSkinThreads), 0, s, model_args(m), params, d_verts,
+             d_joints, ctx->skin_partials, ctx->counters + 2, 4, d_params, ctx->status, (const int*)ctx->active);
   HR_CHECK_LAUNCH();
   return HR_OK;
 }
