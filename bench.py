@@ -58,8 +58,8 @@ KERNEL_NAMES = {"fwd_gather": "k_bin_*", "fwd_shade": "k_shade_fwd", "bwd_gather
 # DRAM bytes (read + write) per launch from the ncu capture summarised under profiles/,
 # with the hash of the render kernels' sources at that capture: a kernel whose source
 # has changed since reports no traffic
-NCU_TRAFFIC = {"k_shade_bwd": (4963328, "cea5412bf91dd497"), "k_shade_fwd": (2932736, "cea5412bf91dd497"),
-               "k_edge_samples": (2450688, "cea5412bf91dd497")}
+NCU_TRAFFIC = {"k_shade_bwd": (4941824, "369d3913b55475c9"), "k_shade_fwd": (2931712, "369d3913b55475c9"),
+               "k_edge_samples": (2455040, "369d3913b55475c9")}
 NCU_TRAFFIC_SOURCES = ("paper_2107_05509_gb300/csrc/hr_render.cu", "paper_2107_05509_gb300/csrc/hr_device.cuh")
 
 

@@ -156,8 +156,8 @@ typedef struct hr_render_opts {
 #define HR_STATS 8u            /* count rays, BVH nodes, triangle tests and hits   */
 #define HR_TIMING 16u          /* record CUDA events around the internal kernels   */
 #define HR_BWD_REUSE_FWD 32u   /* hr_render_bwd: take the candidate lists of the last
-                                  hr_render_fwd on this context instead of traversing
-                                  the BVH again -- honoured only when that forward used
+                                  hr_render_fwd on this context instead of gathering
+                                  its own from the BVH -- honoured only when that forward used
                                   the same vertex and camera pointers, sizes and spp and
                                   no hr_build_bvh came after it; the caller guarantees
                                   that the contents of both arrays are unchanged      */
@@ -191,7 +191,8 @@ typedef struct hr_context hr_context;
  *                      against a candidate (1, 2, 4)
  *   cand_per_chunk     candidates per work item when splitting a sub-tile (>= 1)
  *   max_chunks         work items per sub-tile at most (1 .. 16)
- *   blocks_per_sm      persistent blocks per SM of the gather / forward kernels (1 .. 8)
+ *   blocks_per_sm      persistent blocks per SM of the forward shader, the list sort
+ *                      and the backward's own list gather (1 .. 8)
  *   bwd_blocks_per_sm  persistent blocks per SM of the backward shader (1 .. 8)
  *   bwd_rays_per_lane  rays_per_lane of the backward shader (1, 2, 4)
  *   bwd_cand_per_chunk cand_per_chunk of the backward's work items (>= 1)
@@ -591,12 +592,13 @@ int hr_silhouettes(hr_context* ctx, const hr_model* model, const float* verts, c
  * out[6..11] = the interior backward, out[12..17] = the edge-sample rays, each
  * (estimator samples resolved, rays made individually, BVH nodes visited,
  * Moller-Trumbore tests, hits, candidate screen-box tests).  A sample is resolved
- * without its own ray when its sub-tile's frustum misses the scene. */
+ * without its own ray when no triangle's screen box meets its sub-tile (the forward)
+ * or its sub-tile's frustum misses the scene (the backward's own lists). */
 int hr_get_stats(hr_context* ctx, uint64_t* out, hr_stream stream);
 
 /* Device times (ms) of the internal kernels of the most recent hr_render_fwd and
  * hr_render_bwd made with HR_TIMING, from CUDA events recorded on their stream:
- * ms[0..2] forward candidate gather / shading / combine, ms[3..5] backward gather /
+ * ms[0..2] forward candidate lists / shading / combine, ms[3..5] backward work items /
  * shading / partial reduction, ms[6] silhouettes, ms[7] edge samples, ms[8] normal
  * adjoint; -1 for a kernel that did not run.  n >= 9.  Waits for those events. */
 int hr_kernel_times(hr_context* ctx, float* ms, int n);

@@ -169,10 +169,10 @@ struct Context {
 };
 
 // work counters of the render kernels for n instances: 3 + 3n words, the trace-list
-// count, the culled-list count, then (from an even word) one 64-bit item-allocation
+// count, the count of lists to sort, then (from an even word) one 64-bit item-allocation
 // word per instance
 __host__ __device__ constexpr int ctr_trace(int n) { return 3 + 3 * n; }
-__host__ __device__ constexpr int ctr_cull(int n) { return 4 + 3 * n; }
+__host__ __device__ constexpr int ctr_sort(int n) { return 4 + 3 * n; }
 __host__ __device__ constexpr int ctr_alloc_base(int n) { return (5 + 3 * n + 1) & ~1; }
 __host__ __device__ constexpr int ctr_words(int n) { return ctr_alloc_base(n) + 2 * n; }
 // meshes up to this many vertices take float backward sums (per block of the shader

@@ -217,7 +217,7 @@ struct Work {
                    // without a candidate list (k_overflow traces them ray by ray)
   unsigned* st_done;   // [sub-tiles] forward items finished (the last one combines)
   int4* cand_st;       // [sub-tiles] forward lists k_bin_sort orders: (sub-tile, pool offset, K, 0)
-                       // (count: ctr_cull)
+                       // (count: ctr_sort)
   unsigned* bin;       // [sub-tiles] records binned per sub-tile, then the fill's slot counter
   int* bvh_need;       // [n_inst] set when a sub-tile is listed for per-ray traversal
   unsigned long long* fx;   // [n_inst][6V] fixed-point backward sums (HR_DETERMINISTIC)
@@ -1155,8 +1155,10 @@ __device__ __forceinline__ float3 lane_adjoint(const RenderArgs& a, const SubTil
   return make_float3(g.x * inv_spp, g.y * inv_spp, g.z * inv_spp);
 }
 
-constexpr int kCullThreads = 256;
-constexpr int kCullGroup = 8;   // sub-tiles per warp in k_bin_alloc
+// kernels that take a group of consecutive sub-tiles per warp (k_bin_alloc, k_background,
+// k_items_bwd): one per lane of the first kGroupSubtiles lanes
+constexpr int kGroupThreads = 256;
+constexpr int kGroupSubtiles = 8;
 
 // ---------------------------------------------------------------------------------
 // forward candidate lists by screen-space binning
@@ -1294,7 +1296,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin(RenderArgs a0, unsigned* __
   }
 }
 
-// Work items of the sub-tiles held by lanes 0 .. kCullGroup - 1 (all lanes call): each
+// Work items of the sub-tiles held by lanes 0 .. kGroupSubtiles - 1 (all lanes call): each
 // `need` lane's sub-tile st (instance inst, candidate count K) gets C consecutive
 // items.  One reservation per instance among the lanes -- heavy items from the front
 // of the instance's region, the others from its back -- so the instance's counters
@@ -1308,7 +1310,7 @@ __device__ __forceinline__ void place_items(const RenderArgs& a0, bool need, int
   const int key = need ? inst : -1;
   int hx = 0, lx = 0, ht = 0, lt = 0, leader = -1;
 #pragma unroll
-  for (int j = 0; j < kCullGroup; ++j) {
+  for (int j = 0; j < kGroupSubtiles; ++j) {
     const int kj = __shfl_sync(full, key, j), cj = __shfl_sync(full, C, j);
     const bool hj = __shfl_sync(full, (int)heavy, j) != 0;
     if (need && kj == key) {
@@ -1351,24 +1353,24 @@ __device__ __forceinline__ void place_items(const RenderArgs& a0, bool need, int
   }
 }
 
-// Each warp takes kCullGroup consecutive sub-tiles, one per lane of its first lanes.
+// Each warp takes kGroupSubtiles consecutive sub-tiles, one per lane of its first lanes.
 // A sub-tile with no record in its bin sees only the background (k_background writes
 // it).  The others get a pool range for their K records (one atomic per warp), the
 // work items of their chunks, and an entry in the list k_bin_sort orders; the count
 // becomes the fill's slot counter.  A sub-tile with more records than a list holds,
 // or whose records find no pool room, is traced ray by ray (K = -1, -(K + 1)).
-__global__ void __launch_bounds__(kCullThreads) k_bin_alloc(RenderArgs a0, unsigned* __restrict__ bin) {
+__global__ void __launch_bounds__(kGroupThreads) k_bin_alloc(RenderArgs a0, unsigned* __restrict__ bin) {
   pdl_wait();
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int total = visit_count(a0);
-  const int nw = gridDim.x * (kCullThreads / 32);
-  for (int g0 = (blockIdx.x * (kCullThreads / 32) + (threadIdx.x >> 5)) * kCullGroup; g0 < total;
-       g0 += nw * kCullGroup) {
+  const int nw = gridDim.x * (kGroupThreads / 32);
+  for (int g0 = (blockIdx.x * (kGroupThreads / 32) + (threadIdx.x >> 5)) * kGroupSubtiles; g0 < total;
+       g0 += nw * kGroupSubtiles) {
     int st = -1, K = 0;
     bool listed = false;
     SubTile t{};
-    if (lane < kCullGroup && g0 + lane < total) {
+    if (lane < kGroupSubtiles && g0 + lane < total) {
       const int s = visit_subtile(a0, g0 + lane);
       if (in_range(a0.status, s, 0, a0.total_st)) {
         t = subtile(a0, s);
@@ -1389,12 +1391,12 @@ __global__ void __launch_bounds__(kCullThreads) k_bin_alloc(RenderArgs a0, unsig
     const int want = listed && K <= kLeafCap ? K : 0;
     int incl = want;
 #pragma unroll
-    for (int o = 1; o < kCullGroup; o <<= 1) {
+    for (int o = 1; o < kGroupSubtiles; o <<= 1) {
       const int y = __shfl_up_sync(full, incl, o);
       if (lane >= o) incl += y;
     }
     unsigned base = 0u;
-    const int tot = __shfl_sync(full, incl, kCullGroup - 1);
+    const int tot = __shfl_sync(full, incl, kGroupSubtiles - 1);
     if (lane == 0 && tot > 0) base = atomicAdd(&a0.wk.ctr[1], (unsigned)tot);
     base = __shfl_sync(full, base, 0);
     bool sorted = false, heavy = false;
@@ -1414,43 +1416,43 @@ __global__ void __launch_bounds__(kCullThreads) k_bin_alloc(RenderArgs a0, unsig
     place_items(a0, listed, st, t.inst, Kc, C, heavy);
     const unsigned sm = __ballot_sync(full, sorted);
     int lb = 0;
-    if (lane == 0 && sm) lb = (int)atomicAdd(&a0.wk.ctr[ctr_cull(a0.n_inst)], (unsigned)__popc(sm));
+    if (lane == 0 && sm) lb = (int)atomicAdd(&a0.wk.ctr[ctr_sort(a0.n_inst)], (unsigned)__popc(sm));
     lb = __shfl_sync(full, lb, 0);
     if (sorted) a0.wk.cand_st[lb + __popc(sm & lanemask_lt())] = make_int4(st, (int)off, Kc, 0);
   }
 }
 
 // Pixels of the sub-tiles whose bins hold no record: the background (the value
-// write_pixel gives a sub-tile whose samples all miss).  Each warp takes kCullGroup
+// write_pixel gives a sub-tile whose samples all miss).  Each warp takes kGroupSubtiles
 // consecutive sub-tiles, one per lane of its first lanes, then writes the background
 // ones, lane = pixel, every background load issued before the first store.  Runs on
 // the context's second stream beside the fill and the sort, which touch no pixel.
 template <bool STATS>
-__global__ void __launch_bounds__(kCullThreads) k_background(RenderArgs a0, float* __restrict__ image,
+__global__ void __launch_bounds__(kGroupThreads) k_background(RenderArgs a0, float* __restrict__ image,
                                                              unsigned long long* stats) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   Counts cnt;
   const int total = visit_count(a0);
-  const int nw = gridDim.x * (kCullThreads / 32);
-  for (int g0 = (blockIdx.x * (kCullThreads / 32) + (threadIdx.x >> 5)) * kCullGroup; g0 < total;
-       g0 += nw * kCullGroup) {
-    bool culled = false;
+  const int nw = gridDim.x * (kGroupThreads / 32);
+  for (int g0 = (blockIdx.x * (kGroupThreads / 32) + (threadIdx.x >> 5)) * kGroupSubtiles; g0 < total;
+       g0 += nw * kGroupSubtiles) {
+    bool background = false;
     SubTile t{};
-    if (lane < kCullGroup && g0 + lane < total) {
+    if (lane < kGroupSubtiles && g0 + lane < total) {
       const int s = visit_subtile(a0, g0 + lane);
       if (in_range(a0.status, s, 0, a0.total_st)) {
         t = subtile(a0, s);
-        culled = in_range(a0.status, t.inst, 0, a0.n_inst) && inst_active(a0, t.inst) && a0.wk.st[s].y == 0;
+        background = in_range(a0.status, t.inst, 0, a0.n_inst) && inst_active(a0, t.inst) && a0.wk.st[s].y == 0;
       }
     }
-    const unsigned cm = __ballot_sync(full, culled);
+    const unsigned cm = __ballot_sync(full, background);
     if (!cm) continue;
-    float3 bgv[kCullGroup];
-    size_t pix[kCullGroup];
-    bool valid[kCullGroup];
+    float3 bgv[kGroupSubtiles];
+    size_t pix[kGroupSubtiles];
+    bool valid[kGroupSubtiles];
 #pragma unroll
-    for (int j = 0; j < kCullGroup; ++j) {
+    for (int j = 0; j < kGroupSubtiles; ++j) {
       const int x0 = __shfl_sync(full, t.x0, j), y0 = __shfl_sync(full, t.y0, j);
       const int W = __shfl_sync(full, t.W, j), H = __shfl_sync(full, t.H, j);
       const long long p0 = __shfl_sync(full, t.pix0, j);
@@ -1460,7 +1462,7 @@ __global__ void __launch_bounds__(kCullThreads) k_background(RenderArgs a0, floa
       bgv[j] = valid[j] ? ld3(a0.bg + 3 * pix[j]) : make_float3(0.0f, 0.0f, 0.0f);
     }
 #pragma unroll
-    for (int j = 0; j < kCullGroup; ++j) {
+    for (int j = 0; j < kGroupSubtiles; ++j) {
       const int spp = __shfl_sync(full, t.spp, j);
       if (!valid[j]) continue;
       if (STATS) cnt.samples += spp;   // resolved by the binning: no record meets the sub-tile
@@ -1487,7 +1489,7 @@ __global__ void __launch_bounds__(kRenderThreads) k_bin_sort(RenderArgs a0) {
   __shared__ SortSmem ssm[kWarps];
   SortSmem& ss = ssm[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  const int n = (int)min(*reinterpret_cast<volatile unsigned*>(&a0.wk.ctr[ctr_cull(a0.n_inst)]),
+  const int n = (int)min(*reinterpret_cast<volatile unsigned*>(&a0.wk.ctr[ctr_sort(a0.n_inst)]),
                          (unsigned)a0.total_st);
   for (int vi = blockIdx.x * kWarps + (threadIdx.x >> 5); vi < n; vi += gridDim.x * kWarps) {
     const int4 cd = a0.wk.cand_st[vi];
@@ -1706,26 +1708,26 @@ __global__ void __launch_bounds__(kRenderThreads) k_gather(RenderArgs a_in, cons
 }
 
 // The backward's work items from the forward's candidate lists (HR_BWD_REUSE_FWD).
-// Each warp takes kCullGroup consecutive sub-tiles, one per lane of its first lanes;
+// Each warp takes kGroupSubtiles consecutive sub-tiles, one per lane of its first lanes;
 // only sub-tiles with a candidate list (or per-ray traversal) read the adjoint, the
 // whole warp loading all of them first (lane = pixel), and those with a non-zero
 // adjoint get their work items (place_items).
 template <bool STATS>
-__global__ void __launch_bounds__(kCullThreads, 4) k_items_bwd(RenderArgs a0, const float* __restrict__ adjoint,
+__global__ void __launch_bounds__(kGroupThreads, 4) k_items_bwd(RenderArgs a0, const float* __restrict__ adjoint,
                                                                unsigned long long* stats) {
   pdl_wait();
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   Counts cnt;
   const int total = visit_count(a0);
-  const int nw = gridDim.x * (kCullThreads / 32);
-  for (int g0 = (blockIdx.x * (kCullThreads / 32) + (threadIdx.x >> 5)) * kCullGroup; g0 < total;
-       g0 += nw * kCullGroup) {
+  const int nw = gridDim.x * (kGroupThreads / 32);
+  for (int g0 = (blockIdx.x * (kGroupThreads / 32) + (threadIdx.x >> 5)) * kGroupSubtiles; g0 < total;
+       g0 += nw * kGroupSubtiles) {
     int st = -1;
     int2 pk = make_int2(0, 0);
     bool ok = false;
     SubTile t{};
-    if (lane < kCullGroup && g0 + lane < total) {
+    if (lane < kGroupSubtiles && g0 + lane < total) {
       const int s = visit_subtile(a0, g0 + lane);
       if (in_range(a0.status, s, 0, a0.total_st)) {
         t = subtile(a0, s);
@@ -1740,10 +1742,10 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_items_bwd(RenderArgs a0, co
     // sub-tile j's pixels: lane = pixel; every adjoint load issued before the tests
     const unsigned look = __ballot_sync(full, ok && (STATS || pk.y != 0));
     if (!look) continue;
-    float3 g[kCullGroup];
-    bool valid[kCullGroup];
+    float3 g[kGroupSubtiles];
+    bool valid[kGroupSubtiles];
 #pragma unroll
-    for (int j = 0; j < kCullGroup; ++j) {
+    for (int j = 0; j < kGroupSubtiles; ++j) {
       const int x0 = __shfl_sync(full, t.x0, j), y0 = __shfl_sync(full, t.y0, j);
       const int W = __shfl_sync(full, t.W, j), H = __shfl_sync(full, t.H, j);
       const long long p0 = __shfl_sync(full, t.pix0, j);
@@ -1753,7 +1755,7 @@ __global__ void __launch_bounds__(kCullThreads, 4) k_items_bwd(RenderArgs a0, co
     }
     unsigned live = 0u;
 #pragma unroll
-    for (int j = 0; j < kCullGroup; ++j) {
+    for (int j = 0; j < kGroupSubtiles; ++j) {
       const bool lj = valid[j] && (g[j].x != 0.0f || g[j].y != 0.0f || g[j].z != 0.0f);
       if (__ballot_sync(full, lj)) live |= 1u << j;
       const int kj = __shfl_sync(full, pk.y, j), sppj = __shfl_sync(full, t.spp, j);
@@ -2543,15 +2545,15 @@ int launch_render_fwd(Context* ctx, const hr_model* m, const float* verts, const
     launch_pdl(k_bin<false>, dim3(std::max(bin_blocks, 1)), dim3(kBinThreads), 0, s, a, ctx->bin_cnt);
     HR_CHECK_LAUNCH();
     const int group_blocks = ctx->num_sms * 8;
-    launch_pdl(k_bin_alloc, dim3(group_blocks), dim3(kCullThreads), 0, s, a, ctx->bin_cnt);
+    launch_pdl(k_bin_alloc, dim3(group_blocks), dim3(kGroupThreads), 0, s, a, ctx->bin_cnt);
     HR_CHECK_LAUNCH();
     if (fork && (cudaEventRecord(ctx->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(bs, ctx->ev_fork, 0) != cudaSuccess))
       return HR_ERR_CUDA;
     const int bg_blocks = ctx->num_sms * 4;   // one wave at k_background's 64 registers
     if (st)
-      k_background<true><<<bg_blocks, kCullThreads, 0, bs>>>(a, image, ctx->stats);
+      k_background<true><<<bg_blocks, kGroupThreads, 0, bs>>>(a, image, ctx->stats);
     else
-      k_background<false><<<bg_blocks, kCullThreads, 0, bs>>>(a, image, nullptr);
+      k_background<false><<<bg_blocks, kGroupThreads, 0, bs>>>(a, image, nullptr);
     HR_CHECK_LAUNCH();
     // the boxes of a tree whose update rewrote only the records, refitted if a sub-tile
     // was listed for per-ray traversal (k_overflow is the first to traverse)
@@ -2634,9 +2636,9 @@ int launch_render_bwd(Context* ctx, const hr_model* m, const float* verts, const
     tm.begin(kTimeBwdGather);
     if (reuse) {
       if (st)
-        launch_pdl(k_items_bwd<true>, dim3(ctx->num_sms * 4), dim3(kCullThreads), 0, s, a, adjoint, ctx->stats + kStatsPer);
+        launch_pdl(k_items_bwd<true>, dim3(ctx->num_sms * 4), dim3(kGroupThreads), 0, s, a, adjoint, ctx->stats + kStatsPer);
       else
-        launch_pdl(k_items_bwd<false>, dim3(ctx->num_sms * 4), dim3(kCullThreads), 0, s, a, adjoint,
+        launch_pdl(k_items_bwd<false>, dim3(ctx->num_sms * 4), dim3(kGroupThreads), 0, s, a, adjoint,
                    (unsigned long long*)nullptr);
     } else {
       // its own lists from a frustum walk of the BVH: the boxes must be current
