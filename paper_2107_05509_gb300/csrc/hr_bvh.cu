@@ -50,6 +50,38 @@ __device__ __forceinline__ int delta(const unsigned long long* keys, int n, int 
   return __clzll(keys[i] ^ keys[j]);
 }
 
+// Internal node i (0 <= i < F - 1) of the hierarchy over F sorted Morton keys
+// (Karras 2012, "Maximizing parallelism in the construction of BVHs, octrees, and k-d
+// trees"): the direction of its key range from the common-prefix lengths of its
+// neighbours, the range's far end by an exponential then a binary search, the split
+// position by a binary search for the longest common prefix; children are internal
+// nodes or leaves (encoded ~k, k = sorted position), and both record i as their
+// parent (leaf k at parent[F + k]).  Keys, nodes and parents may live in shared or
+// global memory.
+__device__ __forceinline__ void karras_node(const unsigned long long* keys, int F, int i, Node* nodes, int* parent) {
+  const int d = (delta(keys, F, i, i + 1) - delta(keys, F, i, i - 1)) > 0 ? 1 : -1;
+  const int dmin = delta(keys, F, i, i - d);
+  int lmax = 2;
+  while (delta(keys, F, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, F, i, i + (l + t) * d) > dmin) l += t;
+  const int j = i + l * d;
+  const int dnode = delta(keys, F, i, j);
+  int s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta(keys, F, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  const int gamma = i + s * d + min(d, 0);
+  const int left = (min(i, j) == gamma) ? ~gamma : gamma;
+  const int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+  nodes[i].d = make_int4(left, right, 0, 0);
+  if (left >= 0) parent[left] = i; else parent[F + ~left] = i;
+  if (right >= 0) parent[right] = i; else parent[F + ~right] = i;
+  if (i == 0) parent[0] = -1;
+}
+
 __device__ __forceinline__ float warp_min(float v) {
   for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
@@ -280,29 +312,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_bvh(const float* __rest
         parent[F + 0] = 0;
       }
     }
-    for (int i = tid; i < F - 1; i += blockDim.x) {
-      int d = (delta(keys, F, i, i + 1) - delta(keys, F, i, i - 1)) > 0 ? 1 : -1;
-      int dmin = delta(keys, F, i, i - d);
-      int lmax = 2;
-      while (delta(keys, F, i, i + lmax * d) > dmin) lmax <<= 1;
-      int l = 0;
-      for (int t = lmax >> 1; t >= 1; t >>= 1)
-        if (delta(keys, F, i, i + (l + t) * d) > dmin) l += t;
-      int j = i + l * d;
-      int dnode = delta(keys, F, i, j);
-      int s = 0, t = l;
-      do {
-        t = (t + 1) >> 1;
-        if (delta(keys, F, i, i + (s + t) * d) > dnode) s += t;
-      } while (t > 1);
-      int gamma = i + s * d + min(d, 0);
-      int left = (min(i, j) == gamma) ? ~gamma : gamma;
-      int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
-      nodes[i].d = make_int4(left, right, 0, 0);
-      if (left >= 0) parent[left] = i; else parent[F + ~left] = i;
-      if (right >= 0) parent[right] = i; else parent[F + ~right] = i;
-      if (i == 0) parent[0] = -1;
-    }
+    for (int i = tid; i < F - 1; i += blockDim.x) karras_node(keys, F, i, nodes, parent);
     __syncthreads();
 
   }
@@ -585,27 +595,7 @@ __global__ void k_lb_hierarchy(const unsigned long long* __restrict__ keys_all, 
     return;
   }
   if (i >= F - 1) return;
-  int d = (delta(keys, F, i, i + 1) - delta(keys, F, i, i - 1)) > 0 ? 1 : -1;
-  int dmin = delta(keys, F, i, i - d);
-  int lmax = 2;
-  while (delta(keys, F, i, i + lmax * d) > dmin) lmax <<= 1;
-  int l = 0;
-  for (int t = lmax >> 1; t >= 1; t >>= 1)
-    if (delta(keys, F, i, i + (l + t) * d) > dmin) l += t;
-  int j = i + l * d;
-  int dnode = delta(keys, F, i, j);
-  int s = 0, t = l;
-  do {
-    t = (t + 1) >> 1;
-    if (delta(keys, F, i, i + (s + t) * d) > dnode) s += t;
-  } while (t > 1);
-  int gamma = i + s * d + min(d, 0);
-  int left = (min(i, j) == gamma) ? ~gamma : gamma;
-  int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
-  nodes[i].d = make_int4(left, right, 0, 0);
-  if (left >= 0) parent[left] = i; else parent[F + ~left] = i;
-  if (right >= 0) parent[right] = i; else parent[F + ~right] = i;
-  if (i == 0) parent[0] = -1;
+  karras_node(keys, F, i, nodes, parent);
 }
 
 // triangle records and leaf boxes, then the bottom-up refit with global flags (zeroed
